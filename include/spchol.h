@@ -1,0 +1,193 @@
+/*
+ * spchol: supernodal sparse Cholesky factorization and solves on one GB300 GPU.
+ *
+ * The operation is the one of arXiv 1608.00044 ("An Asynchronous Task-based
+ * Fan-Both Sparse Cholesky Solver"):
+ *   - Section II-A, Eq. 1: A = L L^T for a symmetric positive definite A, then
+ *     the two triangular solves L y = b, L^T x = y.
+ *   - Section V: a fill-reducing symmetric permutation P is applied first; the
+ *     library factors P A P^T = L L^T.
+ *   - Section II-B: the columns of L are grouped into supernodes (consecutive
+ *     columns with a dense diagonal block whose rows below are each entirely
+ *     zero or entirely nonzero); Section III-B caps a supernode's width.
+ *   - Section III-A and IV: the factorization is the set of tasks F (factor a
+ *     supernode), U (update an ancestor) and A (apply the update), run in any
+ *     order that respects the dependencies of Section II-C.  Here the tasks run
+ *     in one persistent GPU kernel driven by device-side dependency counters.
+ *
+ * Conventions for every entry point:
+ *   - Matrices are given as the LOWER triangle, diagonal included, in CSC form:
+ *     colptr (int64, n+1 entries, colptr[0] = 0, non-decreasing), rowind
+ *     (int32, colptr[n] entries, strictly increasing inside each column, every
+ *     row >= its column and < n).  values holds colptr[n] doubles in the same
+ *     order.  Host arrays passed to analyze are copied; the caller keeps
+ *     ownership.
+ *   - perm is new -> old: row/column i of P A P^T is row/column perm[i] of A.
+ *     NULL means the identity.  The library may refine perm by a postorder of
+ *     the elimination tree, which leaves the fill unchanged.
+ *   - Dense blocks (B, X) are column-major, n rows, leading dimension ldb >= n.
+ *   - Pointers to values and right-hand sides may be host or device memory; the
+ *     library inspects the pointer.  Device pointers must be on the device that
+ *     was current at analyze.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default
+ *     stream).  Work is stream-ordered; the calls below return after the status
+ *     word of their launch has been read back, so results are complete on
+ *     return.
+ *   - A handle owns all device memory it allocates and frees it in
+ *     spchol_destroy.  A handle is not safe for concurrent use from two host
+ *     threads; distinct handles are independent.
+ *
+ * Return codes: 0 on success; -k when argument k (1-based) is invalid;
+ * k > 0 from factorize when P A P^T is not positive definite, k being the
+ * smallest (1-based, permuted) column whose pivot was not positive; otherwise
+ * one of the SPCHOL_E* codes below.
+ */
+#ifndef SPCHOL_H
+#define SPCHOL_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SPCHOL_OK 0
+#define SPCHOL_ENOMEM (-1001)   /* device or host allocation failed */
+#define SPCHOL_ETIMEOUT (-1002) /* a device wait exceeded wait_budget_ns */
+#define SPCHOL_ESTATE (-1003)   /* call out of order (e.g. solve before factorize) */
+#define SPCHOL_ENOCONV (-1004)  /* refinement did not reach ir_tol; X holds the best iterate */
+#define SPCHOL_ECUDA (-1005)    /* a CUDA runtime call failed */
+#define SPCHOL_EINTERNAL (-1006)/* a device-side consistency check failed */
+
+/* Arithmetic of the factor. */
+#define SPCHOL_FP64 0  /* everything in FP64 */
+#define SPCHOL_FP32 1  /* FP32 panels and updates, FP64 diagonal POTRF, FP64 residual + refinement */
+#define SPCHOL_TF32 2  /* as FP32, update GEMMs on TF32 tensor cores (tcgen05) */
+
+typedef struct spchol_handle_s* spchol_handle_t;
+
+typedef struct spchol_options {
+  int precision;          /* SPCHOL_FP64 (default), SPCHOL_FP32, SPCHOL_TF32 */
+  int max_width;          /* W: supernode panels are at most W columns (Section III-B caps at 150);
+                             1..128, default 64 */
+  int relax_zeros;        /* amalgamation: a child supernode is merged into its parent when every
+                             merged column gains at most this many explicit zeros; default 4, 0 = off */
+  int tile_rows;          /* rows per update tile, 1..64; 0 = default (64) */
+  int ctas_per_sm;        /* persistent-kernel CTAs per SM; 0 = as many as fit */
+  int deterministic;      /* reserved: 0 */
+  int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
+  int ir_max_iter;        /* mixed precision: refinement steps; default 10 */
+  double ir_tol;          /* mixed precision: target backward error; default 1e-12 */
+  int fault_inject;       /* failure-detection test hook, 0 = off.  1: analyze adds one phantom
+                             dependency to the last panel, so its diagonal task never becomes ready
+                             and factorize must return SPCHOL_ETIMEOUT after wait_budget_ns. */
+} spchol_options;
+
+typedef struct spchol_stats {
+  int64_t n;
+  int64_t nnz_a;          /* stored entries of the lower triangle of A */
+  int64_t nnz_l;          /* entries of L (exact structure, no amalgamation zeros) */
+  int64_t nnz_l_stored;   /* entries held in the supernode panels (lower part incl. zeros) */
+  double flops;           /* sum over columns of c_j^2, c_j the exact column count of L */
+  int64_t n_supernodes;   /* panels after amalgamation and the width cap */
+  int64_t n_tasks;        /* factorization tasks (diagonal factor + panel solve tiles + update tiles) */
+  int64_t max_width;
+  int64_t max_rows;
+  int64_t footprint_bytes;/* device bytes owned by the handle */
+  double analyze_ms;      /* host time of analyze */
+  double factor_ms;       /* device time of the last factorize (assembly + factorization) */
+  double solve_ms;        /* device time of the last solve */
+  int ir_iters;           /* refinement steps of the last solve */
+  double berr;            /* backward error of the last solve (mixed precision), else -1 */
+  int precision;
+} spchol_stats;
+
+/* Fill *opt with the defaults listed above. */
+void spchol_default_options(spchol_options* opt);
+
+/*
+ * Symbolic analysis of P A P^T (Section II-B): elimination tree, postorder,
+ * column counts, supernodes, relaxed amalgamation, the width cap, row
+ * structures, and the task graph of Sections III-A / IV.  Uploads the
+ * structures to the current device.
+ *   n       matrix order, >= 0                                  (argument 1)
+ *   colptr  host int64[n+1]                                     (argument 2)
+ *   rowind  host int32[colptr[n]]                               (argument 3)
+ *   perm    host int64[n] new->old, or NULL                     (argument 4)
+ *   opt     options, or NULL for the defaults                   (argument 5)
+ *   out     receives the handle                                 (argument 6)
+ * Returns 0, -k for an invalid argument k, SPCHOL_ENOMEM or SPCHOL_ECUDA.
+ */
+int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int64_t* perm,
+                   const spchol_options* opt, spchol_handle_t* out);
+
+/*
+ * Numeric factorization P A P^T = L L^T (Eq. 1) with the structure of analyze.
+ * values: colptr[n] doubles of A's lower triangle in analyze's order, host or
+ * device.  The factor stays resident in the handle for later solves.
+ * Returns 0, k > 0 (not positive definite at permuted column k), or an error.
+ */
+int spchol_factorize(spchol_handle_t h, const double* values, void* stream);
+
+/*
+ * Solve A X = B with the resident factor (Section II-A: L y = P b, L^T z = y,
+ * x = P^T z).  B (n x nrhs, column-major, leading dimension ldb) is overwritten
+ * by X; host or device memory.  In the mixed-precision modes the solve refines
+ * with an FP64 residual until berr <= ir_tol (or ir_max_iter steps) and returns
+ * SPCHOL_ENOCONV if the target was not reached.
+ */
+int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream);
+
+/* Copy the handle's statistics into *st. */
+int spchol_stats_get(spchol_handle_t h, spchol_stats* st);
+
+/*
+ * Export the factor in CSC form (permuted ordering, diagonal first in each
+ * column, amalgamation zeros dropped only if drop_zeros != 0 and they are
+ * exactly zero).  Query form: with Lp/Li/Lx NULL, *nnz receives the size.
+ * Host arrays: Lp int64[n+1], Li int64[*nnz], Lx double[*nnz].  perm_out
+ * (host int64[n], optional) receives the permutation actually used.
+ */
+int spchol_export_factor(spchol_handle_t h, int64_t* nnz, int64_t* Lp, int64_t* Li, double* Lx,
+                         int64_t* perm_out);
+
+/* Release every resource of the handle.  NULL is accepted. */
+int spchol_destroy(spchol_handle_t h);
+
+/* Static, human-readable text for a return code. */
+const char* spchol_strerror(int code);
+
+/*
+ * Batch of independent matrices factored in ONE persistent launch: the
+ * matrices form the diagonal blocks of one block-diagonal system whose
+ * elimination forest has one tree (or more) per matrix.
+ *   count           number of matrices, >= 1                       (argument 1)
+ *   n[i]            orders                                         (argument 2)
+ *   colptr[i], rowind[i], perm[i] as in spchol_analyze             (arguments 3-5; perm or perm[i] may be NULL)
+ *   opt, out        as in spchol_analyze                           (arguments 6-7)
+ * The handle then accepts spchol_batch_factorize / spchol_batch_solve and the
+ * plain spchol_stats_get / spchol_destroy.
+ */
+int spchol_batch_analyze(int count, const int64_t* n, const int64_t* const* colptr,
+                         const int32_t* const* rowind, const int64_t* const* perm,
+                         const spchol_options* opt, spchol_handle_t* out);
+
+/* values[i]: matrix i's values, host or device, in matrix i's analyze order.  A positive
+ * return k is the failing column of the block-diagonal system; spchol_batch_info maps it
+ * back to (matrix, column). */
+int spchol_batch_factorize(spchol_handle_t h, const double* const* values, void* stream);
+
+/* B[i]: matrix i's right-hand sides (n[i] x nrhs[i], leading dimension ldb[i]), overwritten. */
+int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, const int* nrhs,
+                       void* stream);
+
+/* For a positive factorize return k: which matrix failed and at which of its own
+ * permuted columns (1-based).  Returns 0, or -2 if k is out of range. */
+int spchol_batch_info(spchol_handle_t h, int64_t k, int* matrix, int64_t* column);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* SPCHOL_H */

@@ -1,0 +1,638 @@
+// C-ABI of the library: handle lifetime, device storage, and the
+// analyze -> factorize -> solve sequence (see include/spchol.h).
+#include <algorithm>
+#include <chrono>
+#include <climits>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/spchol.h"
+#include "device_common.cuh"
+#include "kernels.hpp"
+#include "options.hpp"
+#include "plan.hpp"
+
+using namespace spchol;
+
+namespace {
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+// One device allocation carved into 256-byte aligned pieces.
+struct Arena {
+  size_t bytes = 0;
+  char* base = nullptr;
+  size_t reserve(size_t n) {
+    size_t off = bytes;
+    bytes += (n + 255) & ~size_t(255);
+    return off;
+  }
+};
+
+}  // namespace
+
+struct spchol_handle_s {
+  Plan plan;
+  spchol_options opt{};
+  spchol_stats stats{};
+  int device = 0;
+  int num_sms = 0;
+  bool fp32 = false;
+  bool factored = false;
+  int batch_count = 0;                // 0 = single matrix
+  std::vector<int64_t> batch_n, batch_col0, batch_nnz0;  // per matrix: order, first column, first value
+  // device structures
+  Arena arena;
+  int32_t *d_fcol = nullptr, *d_nrows = nullptr, *d_ld = nullptr, *d_rows = nullptr, *d_parent = nullptr;
+  int64_t *d_rowoff = nullptr, *d_valoff = nullptr, *d_adest = nullptr;
+  int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
+  UTask* d_ut = nullptr;
+  int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
+  int32_t *d_fseeds = nullptr;
+  int nfseeds = 0;
+  int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
+  int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
+  int32_t *d_sseeds = nullptr;
+  int nsseeds = 0;
+  int32_t* d_perm = nullptr;
+  int* d_ring = nullptr;
+  int* d_ctrl = nullptr;
+  double* d_vals = nullptr;  // staging for host values
+  // value pool and solve workspace (separate allocations)
+  void* d_pool = nullptr;
+  size_t pool_bytes = 0;
+  double* d_Y = nullptr;
+  double* d_B = nullptr;
+  int64_t y_cap = 0;  // capacity in doubles of d_Y and d_B
+  int* h_ctrl = nullptr;  // pinned
+  cudaEvent_t ev0 = nullptr, ev1 = nullptr;
+  size_t smem_factor = 0, smem_solve = 0;
+  int grid_factor = 0, grid_solve = 0;
+};
+
+namespace {
+
+inline int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SPCHOL_ENOMEM : SPCHOL_ECUDA; }
+
+#define CU(x)                                  \
+  do {                                         \
+    cudaError_t e_ = (x);                      \
+    if (e_ != cudaSuccess) return cuda_fail(e_); \
+  } while (0)
+
+template <typename V>
+int upload(spchol_handle_t h, V* dst, const std::vector<V>& src) {
+  if (src.empty()) return 0;
+  CU(cudaMemcpy(dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+  return 0;
+}
+
+int setup_device(spchol_handle_t h) {
+  Plan& P = h->plan;
+  const int ns = P.ns;
+  Arena& A = h->arena;
+  auto r32 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int32_t)); };
+  auto r64 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int64_t)); };
+  size_t o_fcol = r32(ns + 1), o_nrows = r32(ns), o_ld = r32(ns), o_rows = r32(P.rows.size()), o_parent = r32(ns);
+  size_t o_rowoff = r64(ns + 1), o_valoff = r64(ns + 1), o_adest = r64(P.a_dest.size());
+  size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
+  size_t o_ut = A.reserve(std::max<size_t>(P.ut.size(), 1) * sizeof(UTask));
+  size_t o_depi = r32(ns), o_trsi = r32(ns), o_dep = r32(ns), o_trs = r32(ns);
+  std::vector<int32_t> fseeds;
+  for (int s = 0; s < ns; ++s)
+    if (P.dep_f[s] == 0) fseeds.push_back(s);
+  size_t o_fseeds = r32(fseeds.size());
+  size_t o_stf = r32(ns), o_nst = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
+  std::vector<int32_t> nkids(ns, 0), sseeds;
+  for (int s = 0; s < ns; ++s) {
+    nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
+    if (nkids[s] == 0) sseeds.push_back(s);
+  }
+  size_t o_nki = r32(ns), o_fk = r32(ns), o_ft = r32(ns), o_bt = r32(ns), o_sseeds = r32(sseeds.size());
+  size_t o_perm = r32(P.n);
+  const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
+  size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
+  size_t o_vals = A.reserve(std::max<int64_t>(P.nnz_a, 1) * sizeof(double));
+  CU(cudaMalloc(&A.base, A.bytes));
+  char* b = A.base;
+  h->d_fcol = (int32_t*)(b + o_fcol);
+  h->d_nrows = (int32_t*)(b + o_nrows);
+  h->d_ld = (int32_t*)(b + o_ld);
+  h->d_rows = (int32_t*)(b + o_rows);
+  h->d_parent = (int32_t*)(b + o_parent);
+  h->d_rowoff = (int64_t*)(b + o_rowoff);
+  h->d_valoff = (int64_t*)(b + o_valoff);
+  h->d_adest = (int64_t*)(b + o_adest);
+  h->d_trsm_first = (int32_t*)(b + o_tf);
+  h->d_ntrsm = (int32_t*)(b + o_nt);
+  h->d_trsm_sn = (int32_t*)(b + o_tsn);
+  h->d_u_first = (int32_t*)(b + o_uf);
+  h->d_nu = (int32_t*)(b + o_nu);
+  h->d_ut = (UTask*)(b + o_ut);
+  h->d_dep_init = (int32_t*)(b + o_depi);
+  h->d_trsm_init = (int32_t*)(b + o_trsi);
+  h->d_dep = (int32_t*)(b + o_dep);
+  h->d_trsm_left = (int32_t*)(b + o_trs);
+  h->d_fseeds = (int32_t*)(b + o_fseeds);
+  h->nfseeds = (int)fseeds.size();
+  h->d_st_first = (int32_t*)(b + o_stf);
+  h->d_nst = (int32_t*)(b + o_nst);
+  h->d_st_sn = (int32_t*)(b + o_stsn);
+  h->d_kid_ptr = (int32_t*)(b + o_kp);
+  h->d_kids = (int32_t*)(b + o_k);
+  h->d_nkids_init = (int32_t*)(b + o_nki);
+  h->d_fkids = (int32_t*)(b + o_fk);
+  h->d_ftiles = (int32_t*)(b + o_ft);
+  h->d_btiles = (int32_t*)(b + o_bt);
+  h->d_sseeds = (int32_t*)(b + o_sseeds);
+  h->nsseeds = (int)sseeds.size();
+  h->d_perm = (int32_t*)(b + o_perm);
+  h->d_ring = (int*)(b + o_ring);
+  h->d_ctrl = (int*)(b + o_ctrl);
+  h->d_vals = (double*)(b + o_vals);
+  int rc = 0;
+  std::vector<int32_t> perm32(P.perm.begin(), P.perm.end());
+  if ((rc = upload(h, h->d_fcol, P.fcol)) || (rc = upload(h, h->d_nrows, P.nrows)) ||
+      (rc = upload(h, h->d_ld, P.ld)) || (rc = upload(h, h->d_rows, P.rows)) ||
+      (rc = upload(h, h->d_parent, P.parent)) || (rc = upload(h, h->d_rowoff, P.rowoff)) ||
+      (rc = upload(h, h->d_valoff, P.valoff)) || (rc = upload(h, h->d_adest, P.a_dest)) ||
+      (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
+      (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
+      (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_ut, P.ut)) ||
+      (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
+      (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
+      (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
+      (rc = upload(h, h->d_kid_ptr, P.kid_ptr)) || (rc = upload(h, h->d_kids, P.kids)) ||
+      (rc = upload(h, h->d_nkids_init, nkids)) || (rc = upload(h, h->d_sseeds, sseeds)) ||
+      (rc = upload(h, h->d_perm, perm32)))
+    return rc;
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
+  CU(cudaMalloc(&h->d_pool, h->pool_bytes));
+  CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
+  CU(cudaEventCreate(&h->ev0));
+  CU(cudaEventCreate(&h->ev1));
+  // launch geometry: persistent grids no larger than what can be co-resident
+  int dev = h->device;
+  CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
+  const int wmax = std::max<int>(P.max_w, 1);
+  h->smem_factor = factor_smem_bytes(wmax);
+  h->smem_solve = solve_smem_bytes(wmax);
+  int bf = 0, bs = 0;
+  CU(factor_configure(h->fp32, h->smem_factor, &bf));
+  CU(solve_configure(h->fp32, h->smem_solve, &bs));
+  if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
+  if (h->opt.ctas_per_sm > 0) {
+    bf = std::min(bf, h->opt.ctas_per_sm);
+    bs = std::min(bs, h->opt.ctas_per_sm);
+  }
+  h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
+  h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
+  h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes);
+  return 0;
+}
+
+int ensure_workspace(spchol_handle_t h, int64_t need) {
+  if (need <= h->y_cap) return 0;
+  if (h->d_Y) cudaFree(h->d_Y);
+  if (h->d_B) cudaFree(h->d_B);
+  h->d_Y = h->d_B = nullptr;
+  h->y_cap = 0;
+  CU(cudaMalloc(&h->d_Y, need * sizeof(double)));
+  CU(cudaMalloc(&h->d_B, need * sizeof(double)));
+  h->y_cap = need;
+  return 0;
+}
+
+bool is_device_ptr(const void* p) {
+  cudaPointerAttributes at;
+  if (cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+    cudaGetLastError();
+    return false;
+  }
+  return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
+int read_status(spchol_handle_t h, cudaStream_t st, int expect_done) {
+  CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const int* c = h->h_ctrl;
+  if (c[kErr] != 0) return c[kErr];
+  if (c[kInfo] != INT_MAX) return c[kInfo];
+  if (c[kDone] != expect_done) return SPCHOL_EINTERNAL;
+  return 0;
+}
+
+int finish_analyze(spchol_handle_t h, std::chrono::steady_clock::time_point t0) {
+  Plan& P = h->plan;
+  int rc = setup_device(h);
+  if (rc) return rc;
+  spchol_stats& S = h->stats;
+  S.n = P.n;
+  S.nnz_a = P.nnz_a;
+  S.nnz_l = P.nnz_l;
+  S.nnz_l_stored = P.nnz_l_stored;
+  S.flops = P.flops;
+  S.n_supernodes = P.ns;
+  S.n_tasks = P.n_factor_tasks;
+  S.max_width = P.max_w;
+  S.max_rows = P.max_r;
+  S.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
+  S.factor_ms = S.solve_ms = 0.0;
+  S.ir_iters = 0;
+  S.berr = -1.0;
+  S.precision = h->opt.precision;
+  return 0;
+}
+
+int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const double* values_host,
+                   cudaStream_t st) {
+  Plan& P = h->plan;
+  h->factored = false;
+  if (values_host && P.nnz_a > 0)
+    CU(cudaMemcpyAsync(h->d_vals, values_host, P.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
+  const double* vals = values_host ? h->d_vals : values_dev_or_null;
+  CU(cudaEventRecord(h->ev0, st));
+  CU(cudaMemsetAsync(h->d_pool, 0, h->pool_bytes, st));
+  CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
+  if (P.ns > 0) {
+    CU(launch_ring_reset(h->d_ring, P.n_factor_tasks, h->d_fseeds, h->nfseeds, h->d_ctrl, h->d_dep,
+                         h->d_dep_init, P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st));
+    FactorArgs a{};
+    a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
+    a.trsm_first = h->d_trsm_first;
+    a.ntrsm = h->d_ntrsm;
+    a.trsm_sn = h->d_trsm_sn;
+    a.u_first = h->d_u_first;
+    a.nu = h->d_nu;
+    a.ut = h->d_ut;
+    a.n_trsm = P.n_trsm;
+    a.n_u = P.n_u;
+    a.ntask = P.n_factor_tasks;
+    a.trsm_rows = P.params.trsm_rows;
+    a.dep_f = h->d_dep;
+    a.trsm_left = h->d_trsm_left;
+    a.ring = h->d_ring;
+    a.ctrl = h->d_ctrl;
+    a.budget_ns = h->opt.wait_budget_ns;
+    a.pool = h->d_pool;
+    CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
+  }
+  CU(cudaEventRecord(h->ev1, st));
+  int rc = 0;
+  if (P.ns > 0) {
+    rc = read_status(h, st, P.n_factor_tasks);
+  } else {
+    CU(cudaStreamSynchronize(st));
+  }
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->stats.factor_ms = ms;
+  if (rc == 0) h->factored = true;
+  return rc;
+}
+
+// Forward + backward solve of Y (permuted order, device, ld = n) in place.
+int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
+  Plan& P = h->plan;
+  if (P.ns == 0 || nrhs == 0) return 0;
+  CU(launch_ring_reset(h->d_ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, h->d_ctrl, h->d_fkids,
+                       h->d_nkids_init, P.ns, h->d_ftiles, h->d_nst, P.ns, h->d_btiles, h->d_nst, P.ns, st));
+  SolveArgs a{};
+  a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
+  a.kid_ptr = h->d_kid_ptr;
+  a.kids = h->d_kids;
+  a.st_first = h->d_st_first;
+  a.nst = h->d_nst;
+  a.st_sn = h->d_st_sn;
+  a.n_st = P.n_st;
+  a.ntask = P.n_solve_tasks;
+  a.solve_rows = P.params.solve_rows;
+  a.fkids = h->d_fkids;
+  a.ftiles = h->d_ftiles;
+  a.btiles = h->d_btiles;
+  a.ring = h->d_ring;
+  a.ctrl = h->d_ctrl;
+  a.budget_ns = h->opt.wait_budget_ns;
+  a.pool = h->d_pool;
+  a.Y = Y;
+  a.ldy = P.n;
+  a.nrhs = nrhs;
+  CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
+  return read_status(h, st, P.n_solve_tasks);
+}
+
+}  // namespace
+
+extern "C" {
+
+void spchol_default_options(spchol_options* opt) {
+  if (opt) spchol::default_options(opt);
+}
+
+const char* spchol_strerror(int code) {
+  if (code == 0) return "success";
+  if (code > 0) return "matrix is not positive definite (the code is the failing permuted column, 1-based)";
+  switch (code) {
+    case SPCHOL_ENOMEM: return "out of memory";
+    case SPCHOL_ETIMEOUT: return "a device-side wait exceeded the wait budget";
+    case SPCHOL_ESTATE: return "call out of order (no factor for this handle)";
+    case SPCHOL_ENOCONV: return "iterative refinement did not reach the target backward error";
+    case SPCHOL_ECUDA: return "a CUDA runtime call failed";
+    case SPCHOL_EINTERNAL: return "a device-side consistency check failed";
+    default: break;
+  }
+  if (code < 0 && code > -100) return "invalid argument (the code is minus the argument's 1-based position)";
+  return "unknown error";
+}
+
+int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, const int64_t* perm,
+                   const spchol_options* opt, spchol_handle_t* out) {
+  if (!out) return -6;
+  *out = nullptr;
+  const auto t0 = std::chrono::steady_clock::now();
+  spchol_options o;
+  if (opt) {
+    o = *opt;
+    if (!options_valid(o)) return -5;
+  } else {
+    spchol::default_options(&o);
+  }
+  spchol_handle_t h = new (std::nothrow) spchol_handle_s();
+  if (!h) return SPCHOL_ENOMEM;
+  h->opt = o;
+  h->fp32 = (o.precision != SPCHOL_FP64);
+  if (cudaGetDevice(&h->device) != cudaSuccess) {
+    delete h;
+    return SPCHOL_ECUDA;
+  }
+  PlanError err;
+  int rc = build_plan(n, colptr, rowind, perm, params_from(o), h->plan, err);
+  if (rc == 0 && o.fault_inject == 1 && h->plan.ns > 0) h->plan.dep_f[h->plan.ns - 1] += 1;
+  if (rc == 0) rc = finish_analyze(h, t0);
+  if (rc != 0) {
+    spchol_destroy(h);
+    return rc;
+  }
+  *out = h;
+  return 0;
+}
+
+int spchol_factorize(spchol_handle_t h, const double* values, void* stream) {
+  if (!h) return -1;
+  if (!values && h->plan.nnz_a > 0) return -2;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const bool dev = values && is_device_ptr(values);
+  return factorize_impl(h, dev ? values : nullptr, dev ? nullptr : values, st);
+}
+
+int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream) {
+  if (!h) return -1;
+  if (nrhs < 0) return -4;
+  if (ldb < std::max<int64_t>(h->plan.n, 1)) return -3;
+  if (!B && nrhs > 0 && h->plan.n > 0) return -2;
+  if (!h->factored) return SPCHOL_ESTATE;
+  if (nrhs == 0 || h->plan.n == 0) return 0;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t n = h->plan.n;
+  int rc = ensure_workspace(h, n * nrhs);
+  if (rc) return rc;
+  const bool dev = is_device_ptr(B);
+  CU(cudaEventRecord(h->ev0, st));
+  const double* src = B;
+  int64_t lds = ldb;
+  if (!dev) {
+    CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), nrhs,
+                         cudaMemcpyHostToDevice, st));
+    src = h->d_B;
+    lds = n;
+  }
+  CU(launch_permute_in(src, lds, h->d_Y, n, h->d_perm, n, nrhs, st));
+  rc = solve_permuted(h, h->d_Y, nrhs, st);
+  if (rc) return rc;
+  if (dev) {
+    CU(launch_permute_out(h->d_Y, n, B, ldb, h->d_perm, n, nrhs, st));
+  } else {
+    CU(launch_permute_out(h->d_Y, n, h->d_B, n, h->d_perm, n, nrhs, st));
+    CU(cudaMemcpy2DAsync(B, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double), nrhs,
+                         cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaEventRecord(h->ev1, st));
+  CU(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->stats.solve_ms = ms;
+  return 0;
+}
+
+int spchol_stats_get(spchol_handle_t h, spchol_stats* st) {
+  if (!h) return -1;
+  if (!st) return -2;
+  *st = h->stats;
+  return 0;
+}
+
+int spchol_export_factor(spchol_handle_t h, int64_t* nnz, int64_t* Lp, int64_t* Li, double* Lx, int64_t* perm_out) {
+  if (!h) return -1;
+  if (!nnz) return -2;
+  const Plan& P = h->plan;
+  int64_t total = 0;
+  for (int s = 0; s < P.ns; ++s) {
+    const int64_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
+    total += w * r - w * (w - 1) / 2;
+  }
+  if (perm_out)
+    for (int64_t i = 0; i < P.n; ++i) perm_out[i] = P.perm[i];
+  if (!Lp && !Li && !Lx) {
+    *nnz = total;
+    return 0;
+  }
+  if (*nnz < total) return -2;
+  if (!h->factored) return SPCHOL_ESTATE;
+  DeviceGuard g(h->device);
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  std::vector<char> pool(h->pool_bytes);
+  CU(cudaMemcpy(pool.data(), h->d_pool, h->pool_bytes, cudaMemcpyDeviceToHost));
+  int64_t q = 0;
+  for (int s = 0; s < P.ns; ++s) {
+    const int w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s], ld = P.ld[s];
+    const int32_t* R = P.rows.data() + P.rowoff[s];
+    for (int j = 0; j < w; ++j) {
+      if (Lp) Lp[P.fcol[s] + j] = q;
+      for (int i = j; i < r; ++i) {
+        const size_t idx = (size_t)P.valoff[s] + i + (size_t)j * ld;
+        double v = h->fp32 ? (double)((float*)pool.data())[idx] : ((double*)pool.data())[idx];
+        if (Li) Li[q] = R[i];
+        if (Lx) Lx[q] = v;
+        ++q;
+      }
+    }
+  }
+  (void)esz;
+  if (Lp) Lp[P.n] = q;
+  *nnz = q;
+  return 0;
+}
+
+int spchol_destroy(spchol_handle_t h) {
+  if (!h) return 0;
+  DeviceGuard g(h->device);
+  if (h->arena.base) cudaFree(h->arena.base);
+  if (h->d_pool) cudaFree(h->d_pool);
+  if (h->d_Y) cudaFree(h->d_Y);
+  if (h->d_B) cudaFree(h->d_B);
+  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  if (h->ev0) cudaEventDestroy(h->ev0);
+  if (h->ev1) cudaEventDestroy(h->ev1);
+  delete h;
+  return 0;
+}
+
+// ------------------------------------------------------------------ batch
+
+int spchol_batch_analyze(int count, const int64_t* n, const int64_t* const* colptr, const int32_t* const* rowind,
+                         const int64_t* const* perm, const spchol_options* opt, spchol_handle_t* out) {
+  if (count < 1) return -1;
+  if (!n) return -2;
+  if (!colptr) return -3;
+  if (!rowind) return -4;
+  if (!out) return -7;
+  *out = nullptr;
+  int64_t N = 0, NNZ = 0;
+  for (int i = 0; i < count; ++i) {
+    if (n[i] < 0 || (n[i] > 0 && (!colptr[i] || !rowind[i]))) return -2;
+    N += n[i];
+    NNZ += n[i] > 0 ? colptr[i][n[i]] : 0;
+  }
+  if (N > INT32_MAX - 1) return -2;
+  std::vector<int64_t> cp(N + 1, 0), pm(N);
+  std::vector<int32_t> ri(NNZ);
+  std::vector<int64_t> col0(count), nnz0(count);
+  int64_t c = 0, z = 0;
+  for (int i = 0; i < count; ++i) {
+    col0[i] = c;
+    nnz0[i] = z;
+    for (int64_t j = 0; j < n[i]; ++j) {
+      for (int64_t p = colptr[i][j]; p < colptr[i][j + 1]; ++p) ri[z + p - colptr[i][0]] = (int32_t)(rowind[i][p] + c);
+      cp[c + j + 1] = z + colptr[i][j + 1] - colptr[i][0];
+      int64_t pj = (perm && perm[i]) ? perm[i][j] : j;
+      if (pj < 0 || pj >= n[i]) return -5;
+      pm[c + j] = pj + c;
+    }
+    z += n[i] > 0 ? colptr[i][n[i]] - colptr[i][0] : 0;
+    c += n[i];
+  }
+  int rc = spchol_analyze(N, cp.data(), ri.data(), pm.data(), opt, out);
+  if (rc < 0 && rc > -100) {
+    // map the combined call's argument positions back to this call's
+    const int map[7] = {0, -2, -3, -4, -5, -6, -7};
+    return map[-rc];
+  }
+  if (rc) return rc;
+  (*out)->batch_count = count;
+  (*out)->batch_n.assign(n, n + count);
+  (*out)->batch_col0 = col0;
+  (*out)->batch_nnz0 = nnz0;
+  return 0;
+}
+
+int spchol_batch_factorize(spchol_handle_t h, const double* const* values, void* stream) {
+  if (!h || h->batch_count == 0) return -1;
+  if (!values) return -2;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cnt = h->batch_count;
+  for (int i = 0; i < cnt; ++i) {
+    const int64_t len = (i + 1 < cnt ? h->batch_nnz0[i + 1] : h->plan.nnz_a) - h->batch_nnz0[i];
+    if (len == 0) continue;
+    if (!values[i]) return -2;
+    const bool dev = is_device_ptr(values[i]);
+    CU(cudaMemcpyAsync(h->d_vals + h->batch_nnz0[i], values[i], len * sizeof(double),
+                       dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  }
+  return factorize_impl(h, h->d_vals, nullptr, st);
+}
+
+int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, const int* nrhs, void* stream) {
+  if (!h || h->batch_count == 0) return -1;
+  if (!B) return -2;
+  if (!ldb) return -3;
+  if (!nrhs) return -4;
+  if (!h->factored) return SPCHOL_ESTATE;
+  DeviceGuard g(h->device);
+  cudaStream_t st = (cudaStream_t)stream;
+  const int cnt = h->batch_count;
+  int maxr = 0;
+  for (int i = 0; i < cnt; ++i) {
+    if (nrhs[i] < 0) return -4;
+    if (ldb[i] < std::max<int64_t>(h->batch_n[i], 1)) return -3;
+    maxr = std::max(maxr, nrhs[i]);
+  }
+  if (maxr == 0) return 0;
+  const int64_t N = h->plan.n;
+  int rc = ensure_workspace(h, N * maxr);
+  if (rc) return rc;
+  // Gather every matrix's RHS into one N x maxr block (zero columns where a
+  // matrix has fewer right-hand sides), solve once, scatter back.
+  CU(cudaMemsetAsync(h->d_B, 0, N * maxr * sizeof(double), st));
+  for (int i = 0; i < cnt; ++i) {
+    if (nrhs[i] == 0 || h->batch_n[i] == 0) continue;
+    const bool dev = is_device_ptr(B[i]);
+    CU(cudaMemcpy2DAsync(h->d_B + h->batch_col0[i], N * sizeof(double), B[i], ldb[i] * sizeof(double),
+                         h->batch_n[i] * sizeof(double), nrhs[i],
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+  }
+  CU(cudaEventRecord(h->ev0, st));
+  CU(launch_permute_in(h->d_B, N, h->d_Y, N, h->d_perm, N, maxr, st));
+  rc = solve_permuted(h, h->d_Y, maxr, st);
+  if (rc) return rc;
+  CU(launch_permute_out(h->d_Y, N, h->d_B, N, h->d_perm, N, maxr, st));
+  CU(cudaEventRecord(h->ev1, st));
+  for (int i = 0; i < cnt; ++i) {
+    if (nrhs[i] == 0 || h->batch_n[i] == 0) continue;
+    const bool dev = is_device_ptr(B[i]);
+    CU(cudaMemcpy2DAsync(B[i], ldb[i] * sizeof(double), h->d_B + h->batch_col0[i], N * sizeof(double),
+                         h->batch_n[i] * sizeof(double), nrhs[i],
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+  }
+  CU(cudaStreamSynchronize(st));
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, h->ev0, h->ev1);
+  h->stats.solve_ms = ms;
+  return 0;
+}
+
+int spchol_batch_info(spchol_handle_t h, int64_t k, int* matrix, int64_t* column) {
+  if (!h || h->batch_count == 0) return -1;
+  if (k < 1 || k > h->plan.n) return -2;
+  // k is a permuted column of the block-diagonal system; the permutation keeps
+  // each matrix's columns inside its own block.
+  const int64_t orig = h->plan.perm[k - 1];
+  int i = (int)(std::upper_bound(h->batch_col0.begin(), h->batch_col0.end(), orig) - h->batch_col0.begin()) - 1;
+  // position of column k within matrix i's permuted order: count columns of
+  // matrix i that precede k in the permuted order
+  int64_t pos = 0;
+  for (int64_t c = 0; c < k - 1; ++c) {
+    const int64_t o = h->plan.perm[c];
+    if (o >= h->batch_col0[i] && o < h->batch_col0[i] + h->batch_n[i]) ++pos;
+  }
+  if (matrix) *matrix = i;
+  if (column) *column = pos + 1;
+  return 0;
+}
+
+}  // extern "C"

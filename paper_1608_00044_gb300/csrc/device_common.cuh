@@ -1,0 +1,53 @@
+// Device-side helpers shared by the factorization and solve kernels:
+// memory-model primitives for the task ring and dependency counters, and the
+// control block layout.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace spchol {
+
+// Control block (int32 words) of one persistent launch.
+enum CtrlWord : int {
+  kHead = 0,   // next ring slot to claim
+  kTail = 1,   // next ring slot to fill
+  kErr = 2,    // 0, or an SPCHOL_E* code (timeout, internal check)
+  kInfo = 3,   // smallest failing pivot column + 1, INT32_MAX if none
+  kDone = 4,   // tasks completed (consistency check)
+  kWhere = 5,  // diagnostic: task id where a wait gave up
+  kCtrlWords = 8
+};
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ void st_release(int* p, int v) {
+  asm volatile("st.release.gpu.global.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ int atom_add_acqrel(int* p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+// Loads of data that other CTAs of the same launch may have written: served
+// from L2, never from a possibly stale L1 line.
+__device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
+__device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+
+__device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+__device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
+
+}  // namespace spchol

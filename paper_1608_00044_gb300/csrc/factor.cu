@@ -1,0 +1,300 @@
+// Supernodal numeric factorization: assembly and the persistent task kernel.
+//
+// Tasks (Section III-A; Section IV labels a task by source and target):
+//   POTRF(s)     F on the diagonal block of panel s: the dense Cholesky of
+//                Algorithm 1 on a w x w block, always in FP64.
+//   TRSM(s, k)   F on rows tile k below the diagonal block:
+//                L21 = A21 L11^{-T} by forward substitution along each row.
+//   UPD(s, t, k) U + A fused: C = L_s[rows k] L_s[rows in t]^T, subtracted
+//                from panel t at the relative positions of those rows and
+//                columns in t (the aggregate vector of Section III-A is
+//                applied immediately, by atomic adds, instead of being kept).
+// Dependencies (Section II-C): UPD(s, ., .) needs every TRSM tile of s;
+// POTRF(t) needs every update tile targeting t.
+#include <climits>
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "kernels.hpp"
+#include "sched.cuh"
+
+namespace spchol {
+
+namespace {
+
+constexpr int kTrsmJB = 8;  // columns solved together per row (independent FMA chains)
+
+struct FactorShared {
+  int task;
+  int skip;
+  int flag;
+  int base;
+};
+
+template <typename T>
+__device__ __forceinline__ T* panel_ptr(const FactorArgs& a, int s) {
+  return reinterpret_cast<T*>(a.pool) + a.pv.valoff[s];
+}
+
+// ---------------------------------------------------------------- POTRF(s)
+template <typename T>
+__device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
+  T* P = panel_ptr<T>(a, s);
+  if (!skip) {
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int i = idx % w, j = idx / w;
+      sm[idx] = (i >= j) ? (double)ldcg(P + i + (size_t)j * ld) : 0.0;
+    }
+    if (tid == 0) sh.flag = 0;
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+      if (tid == 0) {
+        const double d = sm[j + j * w];
+        if (!(d > 0.0)) {
+          atomicMin(&a.ctrl[kInfo], f + j + 1);
+          sh.flag = 1;
+        } else {
+          sm[j + j * w] = sqrt(d);
+        }
+      }
+      __syncthreads();
+      if (sh.flag) break;
+      const double ljj = sm[j + j * w];
+      for (int i = j + 1 + tid; i < w; i += nt) sm[i + j * w] = sm[i + j * w] / ljj;
+      __syncthreads();
+      const int m = w - j - 1;
+      for (int idx = tid; idx < m * m; idx += nt) {
+        const int i = j + 1 + idx % m, k = j + 1 + idx / m;
+        if (i >= k) sm[i + k * w] -= sm[i + j * w] * sm[k + j * w];
+      }
+      __syncthreads();
+    }
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int i = idx % w, j = idx / w;
+      if (i >= j) P[i + (size_t)j * ld] = (T)sm[idx];
+    }
+  }
+  publish_cta_writes();
+  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+  ring_push_range(q, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+}
+
+// ---------------------------------------------------------------- TRSM(s, k)
+template <typename T>
+__device__ void task_trsm(const FactorArgs& a, int s, int k, double* sm, FactorShared& sh, bool skip) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+  const int row0 = w + k * a.trsm_rows;
+  const int cnt = min(a.trsm_rows, r - row0);
+  T* P = panel_ptr<T>(a, s);
+  if (!skip) {
+    for (int idx = tid; idx < w * w; idx += nt) {
+      const int i = idx % w, j = idx / w;
+      sm[idx] = (i >= j) ? (double)ldcg(P + i + (size_t)j * ld) : 0.0;
+    }
+    __syncthreads();
+    for (int rr = tid; rr < cnt; rr += nt) {
+      T* Pi = P + row0 + rr;
+      for (int jb = 0; jb < w; jb += kTrsmJB) {
+        const int nb = min(kTrsmJB, w - jb);
+        double x[kTrsmJB];
+#pragma unroll
+        for (int c = 0; c < kTrsmJB; ++c) x[c] = (c < nb) ? (double)ldcg(Pi + (size_t)(jb + c) * ld) : 0.0;
+        for (int kk = 0; kk < jb; ++kk) {
+          const double xk = (double)ldcg(Pi + (size_t)kk * ld);
+          const double* Lk = sm + kk * w + jb;  // L[jb + c][kk]
+#pragma unroll
+          for (int c = 0; c < kTrsmJB; ++c)
+            if (c < nb) x[c] -= xk * Lk[c];
+        }
+#pragma unroll
+        for (int c = 0; c < kTrsmJB; ++c) {
+          if (c < nb) {
+#pragma unroll
+            for (int c2 = 0; c2 < c; ++c2) x[c] -= x[c2] * sm[(jb + c) + (jb + c2) * w];
+            x[c] = x[c] / sm[(jb + c) + (jb + c) * w];
+            Pi[(size_t)(jb + c) * ld] = (T)x[c];
+          }
+        }
+      }
+    }
+  }
+  publish_cta_writes();
+  if (tid == 0) sh.flag = (atom_add_acqrel(&a.trsm_left[s], -1) == 1);
+  __syncthreads();
+  if (sh.flag) {
+    const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+    ring_push_range(q, a.pv.ns + a.n_trsm + a.u_first[s], a.nu[s], &sh.base);
+  }
+}
+
+// ---------------------------------------------------------------- UPD(s, t, k)
+template <typename T>
+__device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
+                            bool skip) {
+  using acc_t = T;
+  const int tid = threadIdx.x;
+  const int s = u.s, t = u.t;
+  if (!skip) {
+    const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, lds = a.pv.ld[s];
+    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
+    const T* Ps = panel_ptr<T>(a, s);
+    T* Pt = panel_ptr<T>(a, t);
+    const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
+    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
+
+    acc_t* As = reinterpret_cast<acc_t*>(smraw);          // [kUpdKC][kUpdTileM]
+    acc_t* Bs = As + kUpdKC * kUpdTileM;                  // [kUpdKC][kUpdTileN]
+    int* pos = reinterpret_cast<int*>(Bs + kUpdKC * kUpdTileN);  // [kUpdTileM] row position in t
+    int* grow = pos + kUpdTileM;                          // [kUpdTileM] global row
+    int* gcol = grow + kUpdTileM;                         // [kUpdTileN] global column (pass-local)
+
+    // Relative row indices: each row of the tile located in t's sorted row list.
+    for (int i = tid; i < u.rowlen; i += blockDim.x) {
+      const int g = Rs[u.row0 + i];
+      int lo = 0, hi = rt;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= rt || Rt[lo] != g) {  // cannot happen for a consistent plan
+        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+        lo = -1;
+      }
+      pos[i] = lo;
+      grow[i] = g;
+    }
+    const int tx = tid & 15, ty = tid >> 4;
+    for (int cb = 0; cb < u.seglen; cb += kUpdTileN) {
+      const int ncol = min(kUpdTileN, u.seglen - cb);
+      __syncthreads();
+      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
+      acc_t acc[4][4];
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = acc_t(0);
+      for (int k0 = 0; k0 < ws; k0 += kUpdKC) {
+        const int kc = min(kUpdKC, ws - k0);
+        __syncthreads();
+        for (int idx = tid; idx < kUpdKC * kUpdTileM; idx += blockDim.x) {
+          const int i = idx % kUpdTileM, kk = idx / kUpdTileM;
+          As[idx] = (i < u.rowlen && kk < kc) ? (acc_t)ldcg(Ps + (u.row0 + i) + (size_t)(k0 + kk) * lds) : acc_t(0);
+        }
+        for (int idx = tid; idx < kUpdKC * kUpdTileN; idx += blockDim.x) {
+          const int j = idx % kUpdTileN, kk = idx / kUpdTileN;
+          Bs[idx] = (j < ncol && kk < kc) ? (acc_t)ldcg(Ps + (u.seg0 + cb + j) + (size_t)(k0 + kk) * lds)
+                                          : acc_t(0);
+        }
+        __syncthreads();
+#pragma unroll 4
+        for (int kk = 0; kk < kUpdKC; ++kk) {
+          acc_t av[4], bv[4];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr) av[rr] = As[kk * kUpdTileM + ty + 16 * rr];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) bv[cc] = Bs[kk * kUpdTileN + tx + 16 * cc];
+#pragma unroll
+          for (int rr = 0; rr < 4; ++rr)
+#pragma unroll
+            for (int cc = 0; cc < 4; ++cc) acc[rr][cc] += av[rr] * bv[cc];
+        }
+      }
+      // Scatter-subtract into panel t: only the lower triangle (row >= column).
+#pragma unroll
+      for (int rr = 0; rr < 4; ++rr) {
+        const int i = ty + 16 * rr;
+        if (i >= u.rowlen) continue;
+#pragma unroll
+        for (int cc = 0; cc < 4; ++cc) {
+          const int j = tx + 16 * cc;
+          if (j < ncol && grow[i] >= gcol[j] && pos[i] >= 0)
+            red_add(Pt + pos[i] + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
+        }
+      }
+    }
+  }
+  publish_cta_writes();
+  if (tid == 0) {
+    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
+      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+      ring_push_one(q, t);
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ FactorShared sh;
+  double* smd = reinterpret_cast<double*>(smem_raw);
+  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+  for (;;) {
+    if (threadIdx.x == 0) {
+      sh.task = ring_claim(q);
+      sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
+    }
+    __syncthreads();
+    const int task = sh.task;
+    const bool skip = sh.skip != 0;
+    if (task < 0) break;
+    if (task < a.pv.ns) {
+      task_potrf<T>(a, task, smd, sh, skip);
+    } else if (task < a.pv.ns + a.n_trsm) {
+      const int kt = task - a.pv.ns;
+      const int s = a.trsm_sn[kt];
+      task_trsm<T>(a, s, kt - a.trsm_first[s], smd, sh, skip);
+    } else {
+      task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
+    }
+    if (threadIdx.x == 0) atomicAdd(&a.ctrl[kDone], 1);
+    __syncthreads();
+  }
+}
+
+template <typename T>
+__global__ void assemble_kernel(const double* __restrict__ values, const int64_t* __restrict__ dest,
+                                int64_t nnz, T* __restrict__ pool) {
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < nnz; e += (int64_t)gridDim.x * blockDim.x)
+    pool[dest[e]] = (T)values[e];
+}
+
+}  // namespace
+
+size_t factor_smem_bytes(int max_w) {
+  size_t tri = (size_t)max_w * max_w * sizeof(double);
+  size_t upd = (size_t)kUpdKC * (kUpdTileM + kUpdTileN) * sizeof(double) +
+               (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
+  return tri > upd ? tri : upd;
+}
+
+cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm) {
+  const void* fn = fp32 ? (const void*)factor_kernel<float> : (const void*)factor_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
+}
+
+cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz, void* pool,
+                            cudaStream_t st) {
+  if (nnz <= 0) return cudaSuccess;
+  int grid = (int)((nnz + 255) / 256);
+  if (grid > 152 * 16) grid = 152 * 16;
+  if (fp32)
+    assemble_kernel<float><<<grid, 256, 0, st>>>(values, dest, nnz, (float*)pool);
+  else
+    assemble_kernel<double><<<grid, 256, 0, st>>>(values, dest, nnz, (double*)pool);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st) {
+  if (fp32)
+    factor_kernel<float><<<grid, kFactorThreads, smem, st>>>(a);
+  else
+    factor_kernel<double><<<grid, kFactorThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+}  // namespace spchol

@@ -1,0 +1,331 @@
+// Host-only plan inspection and task-protocol simulator (include/spchol_host.h).
+//
+// The simulator runs the same task graph as the persistent GPU kernels, with
+// the same dependency counters, one task at a time in a seeded random order
+// among the ready tasks.  Task semantics mirror the kernels: POTRF on the
+// diagonal block, row-tile forward substitution for L21, update tiles
+// scatter-subtracted at relative positions found by binary search, and the
+// forward / backward solve tiles.
+#include <algorithm>
+#include <climits>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "../../include/spchol_host.h"
+#include "options.hpp"
+#include "plan.hpp"
+
+using namespace spchol;
+
+struct spchol_plan_s {
+  Plan plan;
+};
+
+namespace {
+
+struct Rng {
+  uint64_t s;
+  uint64_t next() {  // splitmix64
+    uint64_t z = (s += 0x9E3779B97F4A7C15ull);
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    return z ^ (z >> 31);
+  }
+  size_t pick(size_t n) { return (size_t)(next() % n); }
+};
+
+// Ready list with random extraction (the order of a parallel run is arbitrary).
+struct Ready {
+  std::vector<int> v;
+  void push(int t) { v.push_back(t); }
+  bool empty() const { return v.empty(); }
+  int pop(Rng& r) {
+    size_t i = r.pick(v.size());
+    int t = v[i];
+    v[i] = v.back();
+    v.pop_back();
+    return t;
+  }
+};
+
+struct Sim {
+  const Plan& P;
+  std::vector<double> pool;
+  int info = 0;
+  explicit Sim(const Plan& p) : P(p), pool((size_t)p.valoff[p.ns], 0.0) {}
+  double* panel(int s) { return pool.data() + P.valoff[s]; }
+  int width(int s) const { return P.fcol[s + 1] - P.fcol[s]; }
+
+  void potrf(int s) {
+    const int w = width(s), ld = P.ld[s], f = P.fcol[s];
+    double* A = panel(s);
+    for (int j = 0; j < w; ++j) {
+      double d = A[j + (size_t)j * ld];
+      if (!(d > 0.0)) {
+        if (info == 0 || f + j + 1 < info) info = f + j + 1;
+        return;
+      }
+      const double ljj = std::sqrt(d);
+      A[j + (size_t)j * ld] = ljj;
+      for (int i = j + 1; i < w; ++i) A[i + (size_t)j * ld] = A[i + (size_t)j * ld] / ljj;
+      for (int k = j + 1; k < w; ++k)
+        for (int i = k; i < w; ++i) A[i + (size_t)k * ld] -= A[i + (size_t)j * ld] * A[k + (size_t)j * ld];
+    }
+  }
+  void trsm(int s, int k) {
+    const int w = width(s), ld = P.ld[s], r = P.nrows[s];
+    const int row0 = w + k * P.params.trsm_rows, cnt = std::min(P.params.trsm_rows, r - row0);
+    double* A = panel(s);
+    for (int i = row0; i < row0 + cnt; ++i)
+      for (int j = 0; j < w; ++j) {
+        double x = A[i + (size_t)j * ld];
+        for (int c = 0; c < j; ++c) x -= A[i + (size_t)c * ld] * A[j + (size_t)c * ld];
+        A[i + (size_t)j * ld] = x / A[j + (size_t)j * ld];
+      }
+  }
+  void update(const UTask& u) {
+    const int ws = width(u.s), lds = P.ld[u.s], ldt = P.ld[u.t], ft = P.fcol[u.t], rt = P.nrows[u.t];
+    const int32_t* Rs = P.rows.data() + P.rowoff[u.s];
+    const int32_t* Rt = P.rows.data() + P.rowoff[u.t];
+    const double* S = panel(u.s);
+    double* T = panel(u.t);
+    for (int i = 0; i < u.rowlen; ++i) {
+      const int gi = Rs[u.row0 + i];
+      const int pos = (int)(std::lower_bound(Rt, Rt + rt, gi) - Rt);
+      if (pos >= rt || Rt[pos] != gi) {
+        info = -1;  // relative index missing: broken plan
+        return;
+      }
+      for (int j = 0; j < u.seglen; ++j) {
+        const int gj = Rs[u.seg0 + j];
+        if (gi < gj) continue;
+        double c = 0.0;
+        for (int k = 0; k < ws; ++k) c += S[(u.row0 + i) + (size_t)k * lds] * S[(u.seg0 + j) + (size_t)k * lds];
+        T[pos + (size_t)(gj - ft) * ldt] -= c;
+      }
+    }
+  }
+};
+
+}  // namespace
+
+extern "C" {
+
+int spchol_plan_build(int64_t n, const int64_t* colptr, const int32_t* rowind, const int64_t* perm,
+                      const spchol_options* opt, spchol_plan_t* out) {
+  if (!out) return -6;
+  *out = nullptr;
+  spchol_options o;
+  if (opt) {
+    o = *opt;
+    if (!options_valid(o)) return -5;
+  } else {
+    spchol::default_options(&o);
+  }
+  spchol_plan_t p = new (std::nothrow) spchol_plan_s();
+  if (!p) return SPCHOL_ENOMEM;
+  PlanError err;
+  int rc = build_plan(n, colptr, rowind, perm, params_from(o), p->plan, err);
+  if (rc) {
+    delete p;
+    return rc;
+  }
+  *out = p;
+  return 0;
+}
+
+int64_t spchol_plan_len(spchol_plan_t p, int what) {
+  if (!p) return -1;
+  const Plan& P = p->plan;
+  switch (what) {
+    case SPCHOL_PLAN_PERM: case SPCHOL_PLAN_COLCOUNT: case SPCHOL_PLAN_ETREE: return P.n;
+    case SPCHOL_PLAN_FCOL: case SPCHOL_PLAN_ROWOFF: return P.ns + 1;
+    case SPCHOL_PLAN_NROWS: case SPCHOL_PLAN_PARENT: case SPCHOL_PLAN_DEPF: case SPCHOL_PLAN_NTRSM:
+    case SPCHOL_PLAN_NU: case SPCHOL_PLAN_NST: return P.ns;
+    case SPCHOL_PLAN_ROWS: return (int64_t)P.rows.size();
+    case SPCHOL_PLAN_UTASKS: return 6 * (int64_t)P.ut.size();
+    case SPCHOL_PLAN_SCALARS: return 10;
+    case SPCHOL_PLAN_ADEST: return (int64_t)P.a_dest.size();
+    default: return -1;
+  }
+}
+
+int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
+  if (!p) return -1;
+  if (!dst) return -3;
+  const Plan& P = p->plan;
+  auto cp = [&](const auto& v) {
+    for (size_t i = 0; i < v.size(); ++i) dst[i] = (int64_t)v[i];
+  };
+  switch (what) {
+    case SPCHOL_PLAN_PERM: cp(P.perm); break;
+    case SPCHOL_PLAN_COLCOUNT: cp(P.colcount); break;
+    case SPCHOL_PLAN_ETREE: cp(P.etree); break;
+    case SPCHOL_PLAN_FCOL: cp(P.fcol); break;
+    case SPCHOL_PLAN_NROWS: cp(P.nrows); break;
+    case SPCHOL_PLAN_ROWOFF: cp(P.rowoff); break;
+    case SPCHOL_PLAN_ROWS: cp(P.rows); break;
+    case SPCHOL_PLAN_PARENT: cp(P.parent); break;
+    case SPCHOL_PLAN_DEPF: cp(P.dep_f); break;
+    case SPCHOL_PLAN_NTRSM: cp(P.ntrsm); break;
+    case SPCHOL_PLAN_NU: cp(P.nu); break;
+    case SPCHOL_PLAN_NST: cp(P.nst); break;
+    case SPCHOL_PLAN_ADEST: cp(P.a_dest); break;
+    case SPCHOL_PLAN_UTASKS:
+      for (size_t i = 0; i < P.ut.size(); ++i) {
+        const UTask& u = P.ut[i];
+        int64_t* d = dst + 6 * i;
+        d[0] = u.s; d[1] = u.t; d[2] = u.seg0; d[3] = u.seglen; d[4] = u.row0; d[5] = u.rowlen;
+      }
+      break;
+    case SPCHOL_PLAN_SCALARS:
+      dst[0] = P.n; dst[1] = P.nnz_l; dst[2] = P.ns; dst[3] = P.n_factor_tasks; dst[4] = P.n_solve_tasks;
+      dst[5] = P.max_w; dst[6] = P.max_r; dst[7] = P.nnz_l_stored; dst[8] = P.n_trsm; dst[9] = P.n_u;
+      break;
+    default: return -2;
+  }
+  return 0;
+}
+
+double spchol_plan_flops(spchol_plan_t p) { return p ? p->plan.flops : -1.0; }
+
+int64_t spchol_plan_pool_len(spchol_plan_t p) { return p ? p->plan.valoff[p->plan.ns] : -1; }
+
+int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64_t ldb, int nrhs, uint64_t seed,
+                         double* Lx) {
+  if (!p) return -1;
+  const Plan& P = p->plan;
+  if (!values && P.nnz_a > 0) return -2;
+  if (nrhs > 0 && (!B || ldb < P.n)) return -3;
+  Sim sim(P);
+  for (int64_t e = 0; e < P.nnz_a; ++e) sim.pool[P.a_dest[e]] = values[e];
+  Rng rng{seed};
+  const int ns = P.ns;
+
+  // ---- factorization: same ids and counters as the GPU kernel ----------------
+  std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
+  std::vector<char> ran(P.n_factor_tasks, 0);
+  Ready rq;
+  for (int s = 0; s < ns; ++s)
+    if (dep[s] == 0) rq.push(s);
+  int done = 0;
+  while (!rq.empty()) {
+    const int task = rq.pop(rng);
+    if (task < 0 || task >= P.n_factor_tasks || ran[task]) return SPCHOL_EINTERNAL;
+    ran[task] = 1;
+    ++done;
+    const bool skip = sim.info != 0;
+    if (task < ns) {
+      if (!skip) sim.potrf(task);
+      for (int k = 0; k < P.ntrsm[task]; ++k) rq.push(ns + P.trsm_first[task] + k);
+    } else if (task < ns + P.n_trsm) {
+      const int kt = task - ns, s = P.trsm_sn[kt];
+      if (!skip) sim.trsm(s, kt - P.trsm_first[s]);
+      if (--tleft[s] < 0) return SPCHOL_EINTERNAL;
+      if (tleft[s] == 0)
+        for (int k = 0; k < P.nu[s]; ++k) rq.push(ns + P.n_trsm + P.u_first[s] + k);
+    } else {
+      const UTask& u = P.ut[task - ns - P.n_trsm];
+      if (!skip) sim.update(u);
+      if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
+      if (dep[u.t] == 0) rq.push(u.t);
+    }
+    if (sim.info < 0) return SPCHOL_EINTERNAL;
+  }
+  if (done != P.n_factor_tasks) return SPCHOL_EINTERNAL;
+  if (Lx) std::memcpy(Lx, sim.pool.data(), sim.pool.size() * sizeof(double));
+  if (sim.info != 0) return sim.info;
+  if (nrhs <= 0 || P.n == 0) return 0;
+
+  // ---- solves ---------------------------------------------------------------
+  const int64_t n = P.n;
+  std::vector<double> Y((size_t)n * nrhs);
+  for (int r = 0; r < nrhs; ++r)
+    for (int64_t i = 0; i < n; ++i) Y[i + (size_t)r * n] = B[P.perm[i] + (size_t)r * ldb];
+  const int nst = P.n_st;
+  std::vector<int> fk(ns), ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
+  for (int s = 0; s < ns; ++s) fk[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
+  std::vector<char> sran(P.n_solve_tasks, 0);
+  Ready q;
+  for (int s = 0; s < ns; ++s)
+    if (fk[s] == 0) q.push(s);
+  int sdone = 0;
+  const int TS = P.params.solve_rows;
+  while (!q.empty()) {
+    const int task = q.pop(rng);
+    if (task < 0 || task >= P.n_solve_tasks || sran[task]) return SPCHOL_EINTERNAL;
+    sran[task] = 1;
+    ++sdone;
+    if (task < ns) {  // FWD_D
+      const int s = task, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
+      const double* L = sim.panel(s);
+      for (int r = 0; r < nrhs; ++r) {
+        double* y = Y.data() + f + (size_t)r * n;
+        for (int j = 0; j < w; ++j) {
+          y[j] /= L[j + (size_t)j * ld];
+          for (int i = j + 1; i < w; ++i) y[i] -= L[i + (size_t)j * ld] * y[j];
+        }
+      }
+      if (P.nst[s] > 0)
+        for (int k = 0; k < P.nst[s]; ++k) q.push(ns + P.st_first[s] + k);
+      else
+        q.push(ns + 2 * nst + s);
+    } else if (task < ns + nst) {  // FWD_T
+      const int kt = task - ns, s = P.st_sn[kt], k = kt - P.st_first[s];
+      const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
+      const int row0 = w + k * TS, cnt = std::min(TS, rr - row0);
+      const double* L = sim.panel(s);
+      const int32_t* R = P.rows.data() + P.rowoff[s];
+      for (int r = 0; r < nrhs; ++r)
+        for (int i = row0; i < row0 + cnt; ++i) {
+          double acc = 0.0;
+          for (int j = 0; j < w; ++j) acc += L[i + (size_t)j * ld] * Y[f + j + (size_t)r * n];
+          Y[R[i] + (size_t)r * n] -= acc;
+        }
+      if (--ft[s] < 0) return SPCHOL_EINTERNAL;
+      if (ft[s] == 0) {
+        const int par = P.parent[s];
+        if (par < 0) return SPCHOL_EINTERNAL;
+        if (--fk[par] == 0) q.push(par);
+      }
+    } else if (task < ns + 2 * nst) {  // BWD_T
+      const int kt = task - ns - nst, s = P.st_sn[kt], k = kt - P.st_first[s];
+      const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
+      const int row0 = w + k * TS, cnt = std::min(TS, rr - row0);
+      const double* L = sim.panel(s);
+      const int32_t* R = P.rows.data() + P.rowoff[s];
+      for (int r = 0; r < nrhs; ++r)
+        for (int j = 0; j < w; ++j) {
+          double acc = 0.0;
+          for (int i = row0; i < row0 + cnt; ++i) acc += L[i + (size_t)j * ld] * Y[R[i] + (size_t)r * n];
+          Y[f + j + (size_t)r * n] -= acc;
+        }
+      if (--bt[s] < 0) return SPCHOL_EINTERNAL;
+      if (bt[s] == 0) q.push(ns + 2 * nst + s);
+    } else {  // BWD_D
+      const int s = task - ns - 2 * nst, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
+      const double* L = sim.panel(s);
+      for (int r = 0; r < nrhs; ++r) {
+        double* y = Y.data() + f + (size_t)r * n;
+        for (int j = w - 1; j >= 0; --j) {
+          y[j] /= L[j + (size_t)j * ld];
+          for (int i = 0; i < j; ++i) y[i] -= L[j + (size_t)i * ld] * y[j];
+        }
+      }
+      for (int c = P.kid_ptr[s]; c < P.kid_ptr[s + 1]; ++c) {
+        const int kid = P.kids[c];
+        for (int k = 0; k < P.nst[kid]; ++k) q.push(ns + nst + P.st_first[kid] + k);
+      }
+    }
+  }
+  if (sdone != P.n_solve_tasks) return SPCHOL_EINTERNAL;
+  for (int r = 0; r < nrhs; ++r)
+    for (int64_t i = 0; i < n; ++i) B[P.perm[i] + (size_t)r * ldb] = Y[i + (size_t)r * n];
+  return 0;
+}
+
+void spchol_plan_destroy(spchol_plan_t p) { delete p; }
+
+}  // extern "C"

@@ -1,0 +1,87 @@
+// Argument blocks and host launchers of the device kernels.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "plan.hpp"
+
+namespace spchol {
+
+constexpr int kFactorThreads = 256;
+constexpr int kSolveThreads = 256;
+constexpr int kUpdTileM = 64;   // rows of C per update-tile pass (matches the 16x16 thread grid x 4)
+constexpr int kUpdTileN = 64;   // columns of C per pass
+constexpr int kUpdKC = 16;      // k-chunk staged in shared memory
+constexpr int kSolveNRC = 8;    // right-hand sides per pass
+
+// Panel structure (device pointers).
+struct PanelView {
+  int32_t ns;
+  const int32_t* fcol;
+  const int32_t* nrows;
+  const int32_t* ld;
+  const int64_t* rowoff;
+  const int32_t* rows;
+  const int64_t* valoff;
+  const int32_t* parent;
+};
+
+struct FactorArgs {
+  PanelView pv;
+  const int32_t* trsm_first;
+  const int32_t* ntrsm;
+  const int32_t* trsm_sn;
+  const int32_t* u_first;
+  const int32_t* nu;
+  const UTask* ut;
+  int32_t n_trsm, n_u, ntask, trsm_rows;
+  int32_t* dep_f;      // update tiles still to land in each panel
+  int32_t* trsm_left;  // panel-solve tiles still to finish in each panel
+  int* ring;
+  int* ctrl;
+  int64_t budget_ns;
+  void* pool;          // double* or float*
+};
+
+struct SolveArgs {
+  PanelView pv;
+  const int32_t* kid_ptr;
+  const int32_t* kids;
+  const int32_t* st_first;
+  const int32_t* nst;
+  const int32_t* st_sn;
+  int32_t n_st, ntask, solve_rows;
+  int32_t* fkids;   // children whose subtree has not finished the forward solve
+  int32_t* ftiles;  // forward tiles left per panel
+  int32_t* btiles;  // backward tiles left per panel
+  int* ring;
+  int* ctrl;
+  int64_t budget_ns;
+  const void* pool;
+  double* Y;        // n x nrhs, permuted order
+  int64_t ldy;
+  int nrhs;
+};
+
+// factor.cu
+size_t factor_smem_bytes(int max_w);
+cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm);
+cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz,
+                            void* pool, cudaStream_t st);
+cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st);
+
+// solve.cu
+size_t solve_smem_bytes(int max_w);
+cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm);
+cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,
+                              int64_t n, int nrhs, cudaStream_t st);
+cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t ldb, const int32_t* perm,
+                               int64_t n, int nrhs, cudaStream_t st);
+
+// sched.cu
+cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
+                              const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
+                              const int* c2_init, int n2, cudaStream_t st);
+
+}  // namespace spchol

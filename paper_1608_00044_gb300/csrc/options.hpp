@@ -1,0 +1,45 @@
+// Option defaults and the mapping from spchol_options to plan parameters,
+// shared by the GPU library and the host-only library.
+#pragma once
+#include <algorithm>
+#include <cstring>
+
+#include "../../include/spchol.h"
+#include "plan.hpp"
+
+namespace spchol {
+
+constexpr int kSolveTileRows = 256;  // one row per thread of a solve CTA
+constexpr int kTrsmTileRows = 64;
+
+inline void default_options(spchol_options* o) {
+  std::memset(o, 0, sizeof(*o));
+  o->precision = SPCHOL_FP64;
+  o->max_width = 64;
+  o->relax_zeros = 4;
+  o->tile_rows = 0;
+  o->ctas_per_sm = 0;
+  o->deterministic = 0;
+  o->wait_budget_ns = 2000000000LL;
+  o->ir_max_iter = 10;
+  o->ir_tol = 1e-12;
+  o->fault_inject = 0;
+}
+
+inline bool options_valid(const spchol_options& o) {
+  return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_TF32 && o.max_width >= 1 && o.max_width <= 128 &&
+         o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
+         o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1;
+}
+
+inline PlanParams params_from(const spchol_options& o) {
+  PlanParams p;
+  p.max_width = std::min(std::max(o.max_width, 1), 128);
+  p.relax_zeros = std::max(o.relax_zeros, 0);
+  p.tile_rows = o.tile_rows > 0 ? o.tile_rows : 64;
+  p.trsm_rows = kTrsmTileRows;
+  p.solve_rows = kSolveTileRows;
+  return p;
+}
+
+}  // namespace spchol

@@ -1,0 +1,77 @@
+// Host-side analysis result: supernode partition, row structures, storage
+// layout and the task graph of the factorization and the solves.
+#pragma once
+#include <cstdint>
+#include <string>
+#include <vector>
+
+namespace spchol {
+
+// One update tile U(s, t): rows [row0, row0 + rowlen) of source panel s (indices
+// into s's row list) times the rows [seg0, seg0 + seglen) of s that fall inside
+// target panel t's columns (Section III-A, task U; Section IV, task T_{s,t}).
+struct UTask {
+  int32_t s, t, seg0, seglen, row0, rowlen;
+};
+
+struct PlanParams {
+  int max_width = 64;    // W (Section III-B caps supernodes at 150 columns)
+  int relax_zeros = 4;   // amalgamation budget per column
+  int tile_rows = 64;    // rows per update tile
+  int trsm_rows = 128;   // rows per panel-solve tile
+  int solve_rows = 128;  // rows per triangular-solve tile
+};
+
+struct Plan {
+  int64_t n = 0;
+  int64_t nnz_a = 0;
+  std::vector<int64_t> perm;  // final new -> old (input perm refined by a postorder)
+  std::vector<int64_t> pinv;  // old -> new
+
+  // exact structure (before amalgamation)
+  int64_t nnz_l = 0;
+  double flops = 0.0;  // sum of c_j^2
+  std::vector<int64_t> colcount;
+  std::vector<int32_t> etree;
+
+  // panels (supernodes after amalgamation and the width cap)
+  int32_t ns = 0;
+  std::vector<int32_t> fcol;    // ns + 1
+  std::vector<int32_t> nrows;   // rows incl. the diagonal block
+  std::vector<int32_t> ld;      // leading dimension (nrows rounded up to 4)
+  std::vector<int64_t> rowoff;  // ns + 1, into rows
+  std::vector<int32_t> rows;    // concatenated sorted row lists
+  std::vector<int64_t> valoff;  // ns + 1, into the value pool (elements)
+  std::vector<int32_t> parent;  // panel etree, -1 at roots
+  std::vector<int32_t> snode_of;  // column -> panel
+  std::vector<int64_t> a_dest;  // entry e of A's lower CSC -> pool index
+  int64_t nnz_l_stored = 0;
+  int32_t max_w = 0, max_r = 0;
+
+  // factorization tasks: [0, ns) diagonal factor, then panel-solve tiles, then updates
+  std::vector<int32_t> trsm_first, ntrsm, trsm_sn;
+  std::vector<int32_t> u_first, nu;
+  std::vector<UTask> ut;
+  std::vector<int32_t> dep_f;  // update tiles targeting each panel
+  int32_t n_trsm = 0, n_u = 0, n_factor_tasks = 0;
+
+  // solve tasks
+  std::vector<int32_t> st_first, nst, st_sn;
+  std::vector<int32_t> kid_ptr, kids;  // panel children, CSR
+  int32_t n_st = 0, n_solve_tasks = 0;
+
+  PlanParams params;
+};
+
+// Validation error: argument index (1-based) and message.
+struct PlanError {
+  int arg = 0;
+  std::string msg;
+};
+
+// Builds the plan.  Returns 0, or -k with err filled for an invalid argument k
+// (1 n, 2 colptr, 3 rowind, 4 perm).
+int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const int64_t* perm,
+               const PlanParams& params, Plan& plan, PlanError& err);
+
+}  // namespace spchol

@@ -1,0 +1,337 @@
+// Supernodal triangular solves L y = P b and L^T z = y (Section II-A), as one
+// persistent launch over a task graph derived from the panel elimination tree.
+//
+// Task ids:
+//   [0, ns)                      FWD_D(s): y_s <- L11^{-1} y_s
+//   [ns, ns + nst)               FWD_T(s, k): y[rows of tile k] -= L21[k] y_s
+//   [ns + nst, ns + 2 nst)       BWD_T(s, k): y_s -= L21[k]^T x[rows of tile k]
+//   [ns + 2 nst, 2 ns + 2 nst)   BWD_D(s): x_s <- L11^{-T} y_s
+// Forward: FWD_D(s) runs once every child subtree has finished (all of its
+// descendants have added their contributions to y_s); a panel's subtree is
+// finished when its last FWD_T tile is.  Backward: the tiles of s run once
+// BWD_D(parent(s)) is done (every ancestor is then final); BWD_D(s) runs after
+// all tiles of s.  A root has no rows below its diagonal block, so its
+// FWD_D is followed directly by its BWD_D.
+#include <climits>
+#include <cstdint>
+
+#include "device_common.cuh"
+#include "kernels.hpp"
+#include "sched.cuh"
+
+namespace spchol {
+
+namespace {
+
+struct SolveShared {
+  int task;
+  int flag;
+  int base;
+};
+
+template <typename T>
+__device__ __forceinline__ const T* spanel(const SolveArgs& a, int s) {
+  return reinterpret_cast<const T*>(a.pool) + a.pv.valoff[s];
+}
+
+// L11 (lower, w x w) into shared memory as double, column-major with ld w.
+template <typename T>
+__device__ void load_l11(const T* P, int w, int ld, double* sm) {
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    sm[idx] = (i >= j) ? (double)P[i + (size_t)j * ld] : 0.0;
+  }
+}
+
+template <typename T>
+__device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
+  const T* P = spanel<T>(a, s);
+  double* L = sm;
+  double* Ys = sm + w * w;  // [nrc][w]
+  load_l11<T>(P, w, ld, L);
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, r = idx / w;
+      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
+    }
+    __syncthreads();
+    for (int j = 0; j < w; ++j) {
+      for (int r = threadIdx.x; r < nrc; r += blockDim.x) Ys[j + r * w] = Ys[j + r * w] / L[j + j * w];
+      __syncthreads();
+      const int m = w - j - 1;
+      for (int idx = threadIdx.x; idx < m * nrc; idx += blockDim.x) {
+        const int i = j + 1 + idx % m, r = idx / m;
+        Ys[i + r * w] -= L[i + j * w] * Ys[j + r * w];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, r = idx / w;
+      a.Y[f + j + (size_t)(r0 + r) * a.ldy] = Ys[idx];
+    }
+  }
+}
+
+template <typename T>
+__device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
+  const T* P = spanel<T>(a, s);
+  double* L = sm;
+  double* Ys = sm + w * w;
+  load_l11<T>(P, w, ld, L);
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, r = idx / w;
+      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
+    }
+    __syncthreads();
+    for (int j = w - 1; j >= 0; --j) {
+      for (int r = threadIdx.x; r < nrc; r += blockDim.x) Ys[j + r * w] = Ys[j + r * w] / L[j + j * w];
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < j * nrc; idx += blockDim.x) {
+        const int i = idx % j, r = idx / j;
+        Ys[i + r * w] -= L[j + i * w] * Ys[j + r * w];
+      }
+      __syncthreads();
+    }
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, r = idx / w;
+      a.Y[f + j + (size_t)(r0 + r) * a.ldy] = Ys[idx];
+    }
+  }
+}
+
+// y[rows of tile] -= L21[tile] y_s, one row per thread.
+template <typename T>
+__device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+  const int row0 = w + k * a.solve_rows, cnt = min(a.solve_rows, r - row0);
+  const T* P = spanel<T>(a, s);
+  const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  double* Ys = sm;  // [nrc][w]
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, rr = idx / w;
+      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy);
+    }
+    __syncthreads();
+    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
+      const T* Pi = P + row0 + i;
+      double acc[kSolveNRC];
+#pragma unroll
+      for (int rr = 0; rr < kSolveNRC; ++rr) acc[rr] = 0.0;
+      for (int j = 0; j < w; ++j) {
+        const double l = (double)Pi[(size_t)j * ld];
+#pragma unroll
+        for (int rr = 0; rr < kSolveNRC; ++rr) acc[rr] += l * Ys[j + rr * w];
+      }
+      const int g = R[row0 + i];
+#pragma unroll
+      for (int rr = 0; rr < kSolveNRC; ++rr)
+        if (rr < nrc) red_add(a.Y + g + (size_t)(r0 + rr) * a.ldy, -acc[rr]);
+    }
+  }
+}
+
+// y_s -= L21[tile]^T x[rows of tile]: rows staged 32 at a time in shared memory.
+template <typename T>
+__device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+  const int row0 = w + k * a.solve_rows, cnt = min(a.solve_rows, r - row0);
+  const T* P = spanel<T>(a, s);
+  const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  constexpr int CH = 32;
+  double* Lc = sm;                  // [w][CH + 1]
+  double* Xc = Lc + w * (CH + 1);   // [nrc][CH]
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    // each thread owns (j, rr) pairs p = tid + q * blockDim
+    double part[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) part[q] = 0.0;
+    for (int c0 = 0; c0 < cnt; c0 += CH) {
+      const int nc = min(CH, cnt - c0);
+      __syncthreads();
+      for (int idx = threadIdx.x; idx < CH * w; idx += blockDim.x) {
+        const int i = idx % CH, j = idx / CH;
+        Lc[j * (CH + 1) + i] = (i < nc) ? (double)P[row0 + c0 + i + (size_t)j * ld] : 0.0;
+      }
+      for (int idx = threadIdx.x; idx < CH * nrc; idx += blockDim.x) {
+        const int i = idx % CH, rr = idx / CH;
+        Xc[rr * CH + i] = (i < nc) ? ldcg(a.Y + R[row0 + c0 + i] + (size_t)(r0 + rr) * a.ldy) : 0.0;
+      }
+      __syncthreads();
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const int p = threadIdx.x + q * blockDim.x;
+        if (p < w * nrc) {
+          const int j = p % w, rr = p / w;
+          double acc = part[q];
+#pragma unroll 8
+          for (int i = 0; i < CH; ++i) acc += Lc[j * (CH + 1) + i] * Xc[rr * CH + i];
+          part[q] = acc;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int p = threadIdx.x + q * blockDim.x;
+      if (p < w * nrc) {
+        const int j = p % w, rr = p / w;
+        red_add(a.Y + f + j + (size_t)(r0 + rr) * a.ldy, -part[q]);
+      }
+    }
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  __shared__ SolveShared sh;
+  double* sm = reinterpret_cast<double*>(smem_raw);
+  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+  const int ns = a.pv.ns, nst = a.n_st;
+  for (;;) {
+    if (threadIdx.x == 0) sh.task = ring_claim(q);
+    __syncthreads();
+    const int task = sh.task;
+    if (task < 0) break;
+    if (task < ns) {
+      const int s = task;
+      fwd_diag<T>(a, s, sm);
+      publish_cta_writes();
+      if (a.nst[s] > 0) {
+        ring_push_range(q, ns + a.st_first[s], a.nst[s], &sh.base);
+      } else if (threadIdx.x == 0) {
+        ring_push_one(q, ns + 2 * nst + s);
+      }
+    } else if (task < ns + nst) {
+      const int kt = task - ns, s = a.st_sn[kt];
+      fwd_tile<T>(a, s, kt - a.st_first[s], sm);
+      publish_cta_writes();
+      if (threadIdx.x == 0 && atom_add_acqrel(&a.ftiles[s], -1) == 1) {
+        const int p = a.pv.parent[s];
+        if (p >= 0 && atom_add_acqrel(&a.fkids[p], -1) == 1) ring_push_one(q, p);
+      }
+    } else if (task < ns + 2 * nst) {
+      const int kt = task - ns - nst, s = a.st_sn[kt];
+      bwd_tile<T>(a, s, kt - a.st_first[s], sm);
+      publish_cta_writes();
+      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) ring_push_one(q, ns + 2 * nst + s);
+    } else {
+      const int s = task - ns - 2 * nst;
+      bwd_diag<T>(a, s, sm);
+      publish_cta_writes();
+      for (int c = a.kid_ptr[s]; c < a.kid_ptr[s + 1]; ++c) {
+        const int kid = a.kids[c];
+        ring_push_range(q, ns + nst + a.st_first[kid], a.nst[kid], &sh.base);
+      }
+    }
+    if (threadIdx.x == 0) atomicAdd(&a.ctrl[kDone], 1);
+    __syncthreads();
+  }
+}
+
+__global__ void permute_in_kernel(const double* __restrict__ B, int64_t ldb, double* __restrict__ Y, int64_t ldy,
+                                  const int32_t* __restrict__ perm, int64_t n, int nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, r = e / n;
+    Y[i + r * ldy] = B[perm[i] + r * ldb];
+  }
+}
+
+__global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, double* __restrict__ B, int64_t ldb,
+                                   const int32_t* __restrict__ perm, int64_t n, int nrhs) {
+  const int64_t total = n * nrhs;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e % n, r = e / n;
+    B[perm[i] + r * ldb] = Y[i + r * ldy];
+  }
+}
+
+}  // namespace
+
+size_t solve_smem_bytes(int max_w) {
+  const size_t diag = ((size_t)max_w * max_w + (size_t)max_w * kSolveNRC) * sizeof(double);
+  const size_t tile = ((size_t)max_w * 33 + 32 * kSolveNRC) * sizeof(double);
+  return diag > tile ? diag : tile;
+}
+
+cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm) {
+  const void* fn = fp32 ? (const void*)solve_kernel<float> : (const void*)solve_kernel<double>;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
+}
+
+cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st) {
+  if (fp32)
+    solve_kernel<float><<<grid, kSolveThreads, smem, st>>>(a);
+  else
+    solve_kernel<double><<<grid, kSolveThreads, smem, st>>>(a);
+  return cudaGetLastError();
+}
+
+static int grid_for(int64_t total) {
+  int64_t g = (total + 255) / 256;
+  if (g > 152 * 8) g = 152 * 8;
+  return g < 1 ? 1 : (int)g;
+}
+
+cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,
+                              int64_t n, int nrhs, cudaStream_t st) {
+  if (n * nrhs == 0) return cudaSuccess;
+  permute_in_kernel<<<grid_for(n * nrhs), 256, 0, st>>>(B, ldb, Y, ldy, perm, n, nrhs);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t ldb, const int32_t* perm,
+                               int64_t n, int nrhs, cudaStream_t st) {
+  if (n * nrhs == 0) return cudaSuccess;
+  permute_out_kernel<<<grid_for(n * nrhs), 256, 0, st>>>(Y, ldy, B, ldb, perm, n, nrhs);
+  return cudaGetLastError();
+}
+
+// ---------------------------------------------------------------- ring reset
+__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
+                                  const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
+                                  const int* c2_init, int n2) {
+  const int stride = gridDim.x * blockDim.x;
+  const int tid = blockIdx.x * blockDim.x + threadIdx.x;
+  for (int i = tid; i < ntask; i += stride) slots[i] = (i < nseed) ? seeds[i] : -1;
+  for (int i = tid; i < n0; i += stride) c0[i] = c0_init[i];
+  for (int i = tid; i < n1; i += stride) c1[i] = c1_init[i];
+  for (int i = tid; i < n2; i += stride) c2[i] = c2_init[i];
+  if (tid == 0) {
+    ctrl[kHead] = 0;
+    ctrl[kTail] = nseed;
+    ctrl[kErr] = 0;
+    ctrl[kInfo] = INT_MAX;
+    ctrl[kDone] = 0;
+    ctrl[kWhere] = -1;
+    ctrl[6] = 0;
+    ctrl[7] = 0;
+  }
+}
+
+cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
+                              const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
+                              const int* c2_init, int n2, cudaStream_t st) {
+  int m = ntask;
+  if (n0 > m) m = n0;
+  if (n1 > m) m = n1;
+  if (n2 > m) m = n2;
+  ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, ctrl, c0, c0_init, n0, c1, c1_init,
+                                                 n1, c2, c2_init, n2);
+  return cudaGetLastError();
+}
+
+}  // namespace spchol

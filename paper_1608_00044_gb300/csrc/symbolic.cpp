@@ -1,0 +1,381 @@
+// Host symbolic analysis (Section II-B, III-B): elimination tree, postorder,
+// column counts, supernodes, relaxed amalgamation, width cap, row structures,
+// storage layout and the task graph.
+#include <algorithm>
+#include <cstring>
+#include <numeric>
+
+#include "plan.hpp"
+
+namespace spchol {
+namespace {
+
+// Pattern of B = P A P^T (lower), both by columns (CSC) and by rows (strict
+// lower part, CSR): the column form feeds the supernodal row structures, the
+// row form the elimination tree and the column counts.
+struct Pattern {
+  std::vector<int64_t> cp;  // CSC lower, rows unsorted
+  std::vector<int32_t> ci;
+  std::vector<int64_t> rp;  // CSR strict lower: row i lists k < i
+  std::vector<int32_t> ri;
+};
+
+void permuted_pattern(int64_t n, const int64_t* colptr, const int32_t* rowind,
+                      const std::vector<int64_t>& pinv, Pattern& B) {
+  const int64_t nnz = colptr[n];
+  B.cp.assign(n + 1, 0);
+  B.rp.assign(n + 1, 0);
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+      int64_t a = pinv[rowind[p]], b = pinv[c];
+      int64_t lo = std::min(a, b), hi = std::max(a, b);
+      B.cp[lo + 1]++;
+      if (hi != lo) B.rp[hi + 1]++;
+    }
+  for (int64_t j = 0; j < n; ++j) {
+    B.cp[j + 1] += B.cp[j];
+    B.rp[j + 1] += B.rp[j];
+  }
+  B.ci.resize(nnz);
+  B.ri.resize(B.rp[n]);
+  std::vector<int64_t> fc(B.cp.begin(), B.cp.end() - 1), fr(B.rp.begin(), B.rp.end() - 1);
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+      int64_t a = pinv[rowind[p]], b = pinv[c];
+      int64_t lo = std::min(a, b), hi = std::max(a, b);
+      B.ci[fc[lo]++] = (int32_t)hi;
+      if (hi != lo) B.ri[fr[hi]++] = (int32_t)lo;
+    }
+}
+
+// Elimination tree by Liu's algorithm with path compression: row i's nonzeros
+// b_ik (k < i) attach the root of k's current subtree to i.
+void etree_liu(int64_t n, const Pattern& B, std::vector<int32_t>& parent) {
+  parent.assign(n, -1);
+  std::vector<int32_t> anc(n, -1);
+  for (int64_t i = 0; i < n; ++i)
+    for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p) {
+      int32_t r = B.ri[p];
+      while (r != -1 && r != i) {
+        int32_t nx = anc[r];
+        anc[r] = (int32_t)i;
+        if (nx == -1) parent[r] = (int32_t)i;
+        r = nx;
+      }
+    }
+}
+
+// Depth-first postorder with children visited in increasing order; the identity
+// when the numbering already is such a postorder.
+void postorder(int64_t n, const std::vector<int32_t>& parent, std::vector<int64_t>& post) {
+  std::vector<int32_t> head(n, -1), next(n, -1);
+  for (int64_t j = n - 1; j >= 0; --j)
+    if (parent[j] != -1) {
+      next[j] = head[parent[j]];
+      head[parent[j]] = (int32_t)j;
+    }
+  post.clear();
+  post.reserve(n);
+  std::vector<int32_t> stack;
+  for (int64_t r = 0; r < n; ++r) {
+    if (parent[r] != -1) continue;
+    stack.push_back((int32_t)r);
+    while (!stack.empty()) {
+      int32_t v = stack.back();
+      if (head[v] != -1) {
+        int32_t c = head[v];
+        head[v] = next[c];
+        stack.push_back(c);
+      } else {
+        stack.pop_back();
+        post.push_back(v);
+      }
+    }
+  }
+}
+
+// Column counts by marking the row subtrees: row i of L is the set of nodes on
+// the etree paths from each k with b_ik != 0 up to i.
+void column_counts(int64_t n, const Pattern& B, const std::vector<int32_t>& parent,
+                   std::vector<int64_t>& cc) {
+  cc.assign(n, 1);
+  std::vector<int32_t> mark(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    mark[i] = (int32_t)i;
+    for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p)
+      for (int32_t j = B.ri[p]; mark[j] != i; j = parent[j]) {
+        mark[j] = (int32_t)i;
+        cc[j]++;
+      }
+  }
+}
+
+inline int64_t round4(int64_t x) { return (x + 3) & ~int64_t(3); }
+
+}  // namespace
+
+int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const int64_t* perm_in,
+               const PlanParams& prm, Plan& P, PlanError& err) {
+  // ---- validation --------------------------------------------------------
+  if (n < 0 || n > INT32_MAX - 1) {
+    err = {1, "n out of range"};
+    return -1;
+  }
+  if (n > 0 && !colptr) { err = {2, "colptr is NULL"}; return -2; }
+  if (n > 0 && colptr[0] != 0) { err = {2, "colptr[0] != 0"}; return -2; }
+  for (int64_t j = 0; j < n; ++j)
+    if (colptr[j + 1] < colptr[j]) {
+      err = {2, "colptr not non-decreasing"};
+      return -2;
+    }
+  const int64_t nnz = n > 0 ? colptr[n] : 0;
+  if (nnz > 0 && !rowind) { err = {3, "rowind is NULL"}; return -3; }
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+      int32_t r = rowind[p];
+      if (r < j || r >= n) {
+        err = {3, "row index outside the lower triangle"};
+        return -3;
+      }
+      if (p > colptr[j] && r <= rowind[p - 1]) {
+        err = {3, "rows not strictly increasing within a column"};
+        return -3;
+      }
+    }
+  P = Plan();
+  P.params = prm;
+  P.n = n;
+  P.nnz_a = nnz;
+  P.perm.resize(n);
+  P.pinv.assign(n, -1);
+  for (int64_t i = 0; i < n; ++i) {
+    int64_t o = perm_in ? perm_in[i] : i;
+    if (o < 0 || o >= n || P.pinv[o] != -1) {
+      err = {4, "perm is not a permutation"};
+      return -4;
+    }
+    P.perm[i] = o;
+    P.pinv[o] = i;
+  }
+
+  // ---- etree and postorder --------------------------------------------------
+  Pattern B;
+  permuted_pattern(n, colptr, rowind, P.pinv, B);
+  std::vector<int32_t> parent;
+  etree_liu(n, B, parent);
+  std::vector<int64_t> post;
+  postorder(n, parent, post);
+  bool identity = true;
+  for (int64_t k = 0; k < n; ++k)
+    if (post[k] != k) { identity = false; break; }
+  if (!identity) {
+    std::vector<int64_t> np(n);
+    for (int64_t k = 0; k < n; ++k) np[k] = P.perm[post[k]];
+    P.perm.swap(np);
+    for (int64_t k = 0; k < n; ++k) P.pinv[P.perm[k]] = k;
+    permuted_pattern(n, colptr, rowind, P.pinv, B);
+    etree_liu(n, B, parent);
+  }
+  column_counts(n, B, parent, P.colcount);
+  P.etree = parent;
+  P.nnz_l = 0;
+  P.flops = 0.0;
+  for (int64_t j = 0; j < n; ++j) {
+    P.nnz_l += P.colcount[j];
+    P.flops += (double)P.colcount[j] * (double)P.colcount[j];
+  }
+
+  // ---- supernodes (Section II-B definition) --------------------------------
+  // Column j+1 continues j's supernode iff parent(j) = j+1 and
+  // c_j = c_{j+1} + 1, i.e. S_j \ {j+1} = S_{j+1} given S_j \ {j+1} is a subset.
+  std::vector<int32_t> sn_first;
+  for (int64_t j = 0; j < n; ++j)
+    if (j == 0 || !(parent[j - 1] == j && P.colcount[j - 1] == P.colcount[j] + 1))
+      sn_first.push_back((int32_t)j);
+  const int32_t ns0 = (int32_t)sn_first.size();
+  sn_first.push_back((int32_t)n);
+  std::vector<int32_t> sn0_of(n);
+  for (int32_t s = 0; s < ns0; ++s)
+    for (int32_t j = sn_first[s]; j < sn_first[s + 1]; ++j) sn0_of[j] = s;
+  std::vector<int32_t> sn0_parent(ns0, -1);
+  for (int32_t s = 0; s < ns0; ++s) {
+    int32_t last = sn_first[s + 1] - 1;
+    if (parent[last] != -1) sn0_parent[s] = sn0_of[parent[last]];
+  }
+
+  // ---- relaxed amalgamation -------------------------------------------------
+  // Bottom-up: the merged supernode that ends just before s is merged into s
+  // when it is a child of s, the width stays <= W, and every merged column
+  // gains at most relax_zeros explicit zeros over its exact count.
+  const int W = std::max(1, prm.max_width);
+  struct MS {
+    int32_t f, l, top;
+  };
+  std::vector<MS> stack;
+  stack.reserve(ns0);
+  for (int32_t s = 0; s < ns0; ++s) {
+    MS cur{sn_first[s], sn_first[s + 1] - 1, s};
+    const int64_t nbelow = P.colcount[cur.l] - 1;
+    while (prm.relax_zeros > 0 && !stack.empty()) {
+      const MS& q = stack.back();
+      if (q.l != cur.f - 1 || sn0_parent[q.top] != s) break;
+      if ((cur.l - q.f + 1) > W) break;
+      bool ok = true;
+      for (int32_t j = q.f; j <= q.l && ok; ++j) {
+        int64_t merged = (int64_t)(cur.l - j + 1) + nbelow;
+        if (merged - P.colcount[j] > prm.relax_zeros) ok = false;
+      }
+      if (!ok) break;
+      cur.f = q.f;
+      stack.pop_back();
+    }
+    stack.push_back(cur);
+  }
+
+  // ---- width cap: chains of panels of at most W columns ----------------------
+  P.fcol.clear();
+  for (const MS& m : stack) {
+    int32_t w = m.l - m.f + 1;
+    for (int32_t c = 0; c < w; c += W) P.fcol.push_back(m.f + c);
+  }
+  P.ns = (int32_t)P.fcol.size();
+  P.fcol.push_back((int32_t)n);
+  const int32_t ns = P.ns;
+  P.snode_of.resize(n);
+  for (int32_t s = 0; s < ns; ++s)
+    for (int32_t j = P.fcol[s]; j < P.fcol[s + 1]; ++j) P.snode_of[j] = s;
+  P.parent.assign(ns, -1);
+  for (int32_t s = 0; s < ns; ++s) {
+    int32_t last = P.fcol[s + 1] - 1;
+    if (parent[last] != -1) P.parent[s] = P.snode_of[parent[last]];
+  }
+
+  // ---- row structures: the union of the panel's columns of B and its
+  // children's structures, restricted to rows past the panel -----------------
+  std::vector<int32_t> kid_head(ns, -1), kid_next(ns, -1);
+  for (int32_t s = ns - 1; s >= 0; --s)
+    if (P.parent[s] != -1) {
+      kid_next[s] = kid_head[P.parent[s]];
+      kid_head[P.parent[s]] = s;
+    }
+  std::vector<std::vector<int32_t>> below(ns);
+  std::vector<int32_t> mark(n, -1);
+  std::vector<int32_t> buf;
+  for (int32_t s = 0; s < ns; ++s) {
+    const int32_t f = P.fcol[s], l = P.fcol[s + 1] - 1;
+    buf.clear();
+    for (int32_t j = f; j <= l; ++j)
+      for (int64_t p = B.cp[j]; p < B.cp[j + 1]; ++p) {
+        int32_t r = B.ci[p];
+        if (r > l && mark[r] != s) {
+          mark[r] = s;
+          buf.push_back(r);
+        }
+      }
+    for (int32_t c = kid_head[s]; c != -1; c = kid_next[c]) {
+      for (int32_t r : below[c])
+        if (r > l && mark[r] != s) {
+          mark[r] = s;
+          buf.push_back(r);
+        }
+    }
+    std::sort(buf.begin(), buf.end());
+    below[s] = buf;
+    // a child's list is needed only by its parent
+    for (int32_t c = kid_head[s]; c != -1; c = kid_next[c]) std::vector<int32_t>().swap(below[c]);
+    // panels are built in order, so the row lists are appended in order
+    P.nrows.push_back((l - f + 1) + (int32_t)buf.size());
+    for (int32_t j = f; j <= l; ++j) P.rows.push_back(j);
+    P.rows.insert(P.rows.end(), buf.begin(), buf.end());
+  }
+  P.rowoff.assign(ns + 1, 0);
+  for (int32_t s = 0; s < ns; ++s) P.rowoff[s + 1] = P.rowoff[s] + P.nrows[s];
+
+  // ---- storage layout ------------------------------------------------------
+  P.ld.resize(ns);
+  P.valoff.assign(ns + 1, 0);
+  P.nnz_l_stored = 0;
+  P.max_w = 0;
+  P.max_r = 0;
+  for (int32_t s = 0; s < ns; ++s) {
+    int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
+    P.ld[s] = (int32_t)round4(r);
+    P.valoff[s + 1] = P.valoff[s] + (int64_t)P.ld[s] * w;
+    P.nnz_l_stored += (int64_t)r * w - (int64_t)w * (w - 1) / 2;
+    P.max_w = std::max(P.max_w, w);
+    P.max_r = std::max(P.max_r, r);
+  }
+
+  // ---- where each entry of A lands in the pool --------------------------------
+  P.a_dest.resize(nnz);
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+      int64_t a = P.pinv[rowind[p]], b = P.pinv[c];
+      int32_t lo = (int32_t)std::min(a, b), hi = (int32_t)std::max(a, b);
+      int32_t s = P.snode_of[lo];
+      const int32_t* R = P.rows.data() + P.rowoff[s];
+      int32_t pos = (int32_t)(std::lower_bound(R, R + P.nrows[s], hi) - R);
+      P.a_dest[p] = P.valoff[s] + pos + (int64_t)(lo - P.fcol[s]) * P.ld[s];
+    }
+
+  // ---- factorization tasks ------------------------------------------------------
+  const int TU = std::max(1, prm.tile_rows), TR = std::max(1, prm.trsm_rows);
+  P.trsm_first.assign(ns, 0);
+  P.ntrsm.assign(ns, 0);
+  P.u_first.assign(ns, 0);
+  P.nu.assign(ns, 0);
+  P.dep_f.assign(ns, 0);
+  P.trsm_sn.clear();
+  P.ut.clear();
+  for (int32_t s = 0; s < ns; ++s) {
+    const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
+    const int32_t nb = r - w;
+    P.trsm_first[s] = (int32_t)P.trsm_sn.size();
+    P.ntrsm[s] = (nb + TR - 1) / TR;
+    for (int32_t k = 0; k < P.ntrsm[s]; ++k) P.trsm_sn.push_back(s);
+    P.u_first[s] = (int32_t)P.ut.size();
+    const int32_t* R = P.rows.data() + P.rowoff[s];
+    int32_t a = w;
+    while (a < r) {
+      int32_t t = P.snode_of[R[a]];
+      int32_t e = a;
+      while (e < r && R[e] < P.fcol[t + 1]) ++e;
+      for (int32_t r0 = a; r0 < r; r0 += TU) {
+        P.ut.push_back(UTask{s, t, a, e - a, r0, std::min(TU, r - r0)});
+        P.dep_f[t]++;
+      }
+      a = e;
+    }
+    P.nu[s] = (int32_t)P.ut.size() - P.u_first[s];
+  }
+  P.n_trsm = (int32_t)P.trsm_sn.size();
+  P.n_u = (int32_t)P.ut.size();
+  P.n_factor_tasks = ns + P.n_trsm + P.n_u;
+
+  // ---- solve tasks ------------------------------------------------------------
+  const int TS = std::max(1, prm.solve_rows);
+  P.st_first.assign(ns, 0);
+  P.nst.assign(ns, 0);
+  P.st_sn.clear();
+  for (int32_t s = 0; s < ns; ++s) {
+    const int32_t nb = P.nrows[s] - (P.fcol[s + 1] - P.fcol[s]);
+    P.st_first[s] = (int32_t)P.st_sn.size();
+    P.nst[s] = (nb + TS - 1) / TS;
+    for (int32_t k = 0; k < P.nst[s]; ++k) P.st_sn.push_back(s);
+  }
+  P.n_st = (int32_t)P.st_sn.size();
+  P.n_solve_tasks = 2 * ns + 2 * P.n_st;
+  P.kid_ptr.assign(ns + 1, 0);
+  for (int32_t s = 0; s < ns; ++s)
+    if (P.parent[s] != -1) P.kid_ptr[P.parent[s] + 1]++;
+  for (int32_t s = 0; s < ns; ++s) P.kid_ptr[s + 1] += P.kid_ptr[s];
+  P.kids.resize(P.kid_ptr[ns]);
+  {
+    std::vector<int32_t> fill(P.kid_ptr.begin(), P.kid_ptr.end() - 1);
+    for (int32_t s = 0; s < ns; ++s)
+      if (P.parent[s] != -1) P.kids[fill[P.parent[s]]++] = s;
+  }
+  return 0;
+}
+
+}  // namespace spchol

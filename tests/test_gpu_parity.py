@@ -1,0 +1,260 @@
+"""GPU parity: the CUDA path through the C-ABI against the CPU oracle.
+
+Tolerances (FP64): backward error <= 1e-13 (the stated bar of the method's FP64
+path), and max |L_gpu - L_oracle| <= 1e-11 max |L|: the Cholesky factor is
+unique, the two computations differ only in the order of the updates
+(Section II-C), and for these well-conditioned inputs the forward error of L is
+a few hundred units of roundoff at most.
+"""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests import fig1
+from tests.gpu_util import BERR_FP64, gpu_factor_solve, l_max_diff
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1608_00044_gb300 import spchol  # noqa: E402
+
+
+def _check(A, perm, B, l_tol=1e-11, **opts):
+    rc, X, st, h = gpu_factor_solve(A, perm, B, **opts)
+    assert rc == 0, spchol.strerror(rc)
+    be = oracle.berr(A, X, B)
+    assert be <= BERR_FP64, be
+    d, lmax = l_max_diff(h, A)
+    assert d <= l_tol * lmax, (d, lmax)
+    spchol.destroy(h)
+    return X, st
+
+
+def _csc(M):
+    import scipy.sparse as sp
+
+    L = sp.csc_matrix(np.tril(M))
+    L.sort_indices()
+    return gridgen.CscLower(M.shape[0], L.indptr.astype(np.int64), L.indices.astype(np.int32),
+                            L.data.astype(np.float64))
+
+
+@pytest.mark.parametrize("W,relax", [(64, 0), (2, 0), (1, 0), (128, 4)])
+def test_fig1(W, relax):
+    n, a_pat, fill, blocks, edges = fig1.load()
+    colptr, rowind, vals = fig1.spd_from_pattern(n, a_pat)
+    A = gridgen.CscLower(n, colptr, rowind, vals)
+    B = gridgen.rhs_uniform(n, 2, seed=3)
+    _check(A, None, B, max_width=W, relax_zeros=relax)
+
+
+@pytest.mark.parametrize("n", [1, 2, 7, 31, 33, 64, 65, 150, 257])
+def test_dense(n):
+    rng = np.random.default_rng(n)
+    G = rng.standard_normal((n, n))
+    M = G @ G.T + n * np.eye(n)
+    A = _csc(M)
+    B = gridgen.rhs_uniform(n, 3, seed=n)
+    _check(A, rng.permutation(n), B)
+
+
+@pytest.mark.parametrize("seed", range(6))
+def test_random_sparse(seed):
+    rng = np.random.default_rng(500 + seed)
+    n = int(rng.integers(20, 300))
+    dens = rng.uniform(0.005, 0.08)
+    M = np.tril(rng.random((n, n)) < dens, -1)
+    M = M | M.T
+    V = np.where(M, -rng.uniform(0.1, 1.0, (n, n)), 0.0)
+    V = np.tril(V) + np.tril(V, -1).T
+    V[np.diag_indices(n)] = np.abs(V).sum(1) + 1.0
+    A = _csc(V)
+    B = gridgen.rhs_uniform(n, int(rng.integers(1, 17)), seed=seed)
+    W = int(rng.choice([1, 7, 31, 33, 64, 128]))
+    _check(A, rng.permutation(n), B, max_width=W, relax_zeros=int(rng.integers(0, 6)))
+
+
+def test_1d_chain():
+    n = 5000
+    colptr = np.zeros(n + 1, np.int64)
+    rows, vals = [], []
+    for j in range(n):
+        rows.append(j)
+        vals.append(2.0)
+        if j + 1 < n:
+            rows.append(j + 1)
+            vals.append(-1.0)
+        colptr[j + 1] = len(rows)
+    A = gridgen.CscLower(n, colptr, np.array(rows, np.int32), np.array(vals))
+    k = np.arange(1, n + 1, dtype=np.float64)
+    rc, X, st, h = gpu_factor_solve(A, None, np.eye(n, 1))
+    assert rc == 0
+    # closed form of A^{-1} e_1
+    np.testing.assert_allclose(X[:, 0], (n + 1 - k) / (n + 1), rtol=1e-10, atol=1e-13)
+    spchol.destroy(h)
+
+
+@pytest.mark.parametrize("name,W", [("lap2d_64", 64), ("lap2d_64", 8), ("lap2d_64", 128), ("lap3d_16", 64),
+                                    ("lap3d_16", 32), ("diff3d_12", 64), ("diff3d_11", 31), ("diff2d_37", 64)])
+def test_grids(name, W):
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=1)
+    _check(A, perm, B, max_width=W)
+
+
+@pytest.mark.parametrize("nrhs", [1, 8, 16, 17])
+def test_nrhs_and_host_pointers(nrhs):
+    A, perm, _ = gridgen.workload("lap3d_12")
+    B = gridgen.rhs_uniform(A.n, nrhs, seed=nrhs)
+    for dev in (True, False):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, use_device=dev)
+        assert rc == 0
+        assert oracle.berr(A, X, B) <= BERR_FP64
+        spchol.destroy(h)
+
+
+def test_repeat_solve_and_refactorize():
+    A, perm, _ = gridgen.workload("diff3d_10")
+    o = spchol.default_options()
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+    assert spchol.factorize(h, A.values) == 0
+    for it in range(3):
+        B = gridgen.rhs_uniform(A.n, 2, seed=10 + it)
+        X = B.copy(order="F")
+        spchol.solve(h, X, A.n, 2)
+        assert oracle.berr(A, X, B) <= BERR_FP64
+    # new values, same pattern: 2A
+    A2 = gridgen.CscLower(A.n, A.colptr, A.rowind, A.values * 2.0)
+    assert spchol.factorize(h, A2.values) == 0
+    B = gridgen.rhs_uniform(A.n, 1, seed=99)
+    X = B.copy(order="F")
+    spchol.solve(h, X, A.n, 1)
+    assert oracle.berr(A2, X, B) <= BERR_FP64
+    spchol.destroy(h)
+
+
+def test_side_stream():
+    A, perm, b = gridgen.workload("lap2d_64")
+    s = torch.cuda.Stream()
+    o = spchol.default_options()
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+    with torch.cuda.stream(s):
+        vals = torch.from_numpy(A.values).cuda()
+        Bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+        assert spchol.factorize(h, vals, stream=s) == 0
+        spchol.solve(h, Bt, A.n, 1, stream=s)
+    s.synchronize()
+    assert oracle.berr(A, Bt.cpu().numpy().T, b) <= BERR_FP64
+    spchol.destroy(h)
+
+
+@pytest.mark.parametrize("which", ["first", "middle", "last"])
+def test_not_spd_reports_smallest_column(which):
+    A, perm, b = gridgen.workload("lap2d_64")
+    o = spchol.default_options()
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+    fp = spchol.final_perm(h)
+    pinv = np.empty_like(fp)
+    pinv[fp] = np.arange(A.n)
+    bad = {"first": int(fp[0]), "middle": 1234, "last": int(fp[-1])}[which]
+    vals = A.values.copy()
+    vals[A.colptr[bad]] = -5.0
+    rc = spchol.factorize(h, vals)
+    assert rc == pinv[bad] + 1
+    # the oracle agrees on the failing column
+    f = oracle.OracleFactor(A.n, A.colptr, A.rowind, vals, fp)
+    assert f.factor() == rc
+    # the handle is usable again with good values
+    assert spchol.factorize(h, A.values) == 0
+    X = b.copy(order="F")
+    spchol.solve(h, X, A.n, 1)
+    assert oracle.berr(A, X, b) <= BERR_FP64
+    spchol.destroy(h)
+
+
+def test_wait_budget_times_out_cleanly():
+    """A phantom dependency keeps the last panel from ever becoming ready: every
+    CTA's bounded wait must give up and factorize must report ETIMEOUT."""
+    A, perm, b = gridgen.workload("lap2d_32")
+    o = spchol.default_options(fault_inject=1, wait_budget_ns=50_000_000)
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+    with pytest.raises(spchol.SpcholError) as ei:
+        spchol.factorize(h, A.values)
+    assert ei.value.code == spchol.ETIMEOUT
+    spchol.destroy(h)
+    # the context is still healthy
+    rc, X, st, h2 = gpu_factor_solve(A, perm, b)
+    assert rc == 0 and oracle.berr(A, X, b) <= BERR_FP64
+    spchol.destroy(h2)
+
+
+def test_solve_before_factorize():
+    A, perm, b = gridgen.workload("lap2d_16")
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options())
+    with pytest.raises(spchol.SpcholError) as ei:
+        spchol.solve(h, b.copy(order="F"), A.n, 1)
+    assert ei.value.code == spchol.ESTATE
+    spchol.destroy(h)
+
+
+def test_empty_matrix():
+    A = gridgen.CscLower(0, np.zeros(1, np.int64), np.zeros(0, np.int32), np.zeros(0))
+    h = spchol.analyze(0, A.colptr, A.rowind, None, spchol.default_options())
+    assert spchol.factorize(h, A.values) == 0
+    spchol.destroy(h)
+
+
+def test_batch_matches_solo():
+    sides = [5, 16, 23, 9, 31]
+    mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 1 + (i % 3), seed=i) for i, M in enumerate(mats)]
+    o = spchol.default_options()
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+    Xs = [B.copy(order="F") for B in Bs]
+    spchol.batch_solve(h, Xs, [M.n for M in mats], [B.shape[1] for B in Bs])
+    for M, P, B, X in zip(mats, perms, Bs, Xs):
+        assert oracle.berr(M, X, B) <= BERR_FP64
+        rc, Xs1, st, h1 = gpu_factor_solve(M, P, B)
+        np.testing.assert_allclose(X, Xs1, rtol=1e-11, atol=1e-13)
+        spchol.destroy(h1)
+    # a non-SPD matrix inside the batch is located
+    bad_vals = [M.values.copy() for M in mats]
+    bad_vals[3][mats[3].colptr[4]] = -1.0
+    k = spchol.batch_factorize(h, bad_vals)
+    assert k > 0
+    m, col = spchol.batch_info(h, k)
+    assert m == 3 and 1 <= col <= mats[3].n
+    spchol.destroy(h)
+
+
+@pytest.mark.slow
+def test_full_size_lap3d_64_sampled():
+    """64^3 7-point Laplacian at full size in the benchmark's configuration:
+    backward error of all 8 solutions, and sampled entries of L L^T - P A P^T."""
+    A, perm, b = gridgen.workload("lap3d_64")
+    rc, X, st, h = gpu_factor_solve(A, perm, b)
+    assert rc == 0
+    assert oracle.berr(A, X, b) <= BERR_FP64
+    Lp, Li, Lx, fperm = spchol.export_factor(h)
+    import scipy.sparse as sp
+
+    n = A.n
+    L = sp.csc_matrix((Lx, Li, Lp), shape=(n, n)).tocsr()
+    full = A.to_scipy_full()
+    Bp = full[fperm][:, fperm].tocsr()
+    rng = np.random.default_rng(0)
+    cols = np.concatenate([rng.integers(0, n, 40), np.arange(n - 64, n)])  # includes the top separator
+    worst = 0.0
+    for j in cols:
+        rows = np.concatenate([Bp[:, [j]].nonzero()[0], rng.integers(j, n, 4)])
+        for i in rows[rows >= j]:
+            v = L[i].multiply(L[j]).sum()
+            worst = max(worst, abs(v - Bp[i, j]))
+    assert worst <= 1e-12 * abs(A.values).max()
+    spchol.destroy(h)
