@@ -3,6 +3,7 @@
 #include <algorithm>
 #include <chrono>
 #include <climits>
+#include <cmath>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -51,6 +52,7 @@ struct spchol_handle_s {
   int num_sms = 0;
   bool fp32 = false;
   bool factored = false;
+  std::vector<int32_t> a_row, a_col;  // A's lower entries (original order); dropped after analyze
   int batch_count = 0;                // 0 = single matrix
   std::vector<int64_t> batch_n, batch_col0, batch_nnz0;  // per matrix: order, first column, first value
   // device structures
@@ -76,6 +78,15 @@ struct spchol_handle_s {
   double* d_Y = nullptr;
   double* d_B = nullptr;
   int64_t y_cap = 0;  // capacity in doubles of d_Y and d_B
+  // mixed precision: full symmetric CSR of A (original order) for the FP64 residual
+  int64_t* d_csr_rp = nullptr;
+  int32_t* d_csr_ci = nullptr;
+  int64_t* d_csr_vmap = nullptr;
+  unsigned long long* d_norms = nullptr;  // [0] = ||A||_inf, then 3 per right-hand side
+  unsigned long long* h_norms = nullptr;  // pinned
+  int norms_cap = 0;                      // right-hand sides the norm buffers hold
+  double* d_X = nullptr;
+  double* d_R = nullptr;
   int* h_ctrl = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t smem_factor = 0, smem_solve = 0;
@@ -125,6 +136,34 @@ int setup_device(spchol_handle_t h) {
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
   size_t o_vals = A.reserve(std::max<int64_t>(P.nnz_a, 1) * sizeof(double));
+  // full symmetric CSR of A for the refinement residual (mixed precision only)
+  std::vector<int64_t> crp, cvm;
+  std::vector<int32_t> cci;
+  size_t o_crp = 0, o_cci = 0, o_cvm = 0;
+  if (h->fp32) {
+    const int64_t n = P.n;
+    crp.assign(n + 1, 0);
+    for (int64_t e = 0; e < P.nnz_a; ++e) {
+      crp[h->a_row[e] + 1]++;
+      if (h->a_row[e] != h->a_col[e]) crp[h->a_col[e] + 1]++;
+    }
+    for (int64_t i = 0; i < n; ++i) crp[i + 1] += crp[i];
+    cci.resize(crp[n]);
+    cvm.resize(crp[n]);
+    std::vector<int64_t> fill(crp.begin(), crp.end() - 1);
+    for (int64_t e = 0; e < P.nnz_a; ++e) {
+      const int64_t i = h->a_row[e], j = h->a_col[e];
+      cci[fill[i]] = (int32_t)j;
+      cvm[fill[i]++] = e;
+      if (i != j) {
+        cci[fill[j]] = (int32_t)i;
+        cvm[fill[j]++] = e;
+      }
+    }
+    o_crp = r64(crp.size());
+    o_cci = r32(cci.size());
+    o_cvm = r64(cvm.size());
+  }
   CU(cudaMalloc(&A.base, A.bytes));
   char* b = A.base;
   h->d_fcol = (int32_t*)(b + o_fcol);
@@ -162,7 +201,17 @@ int setup_device(spchol_handle_t h) {
   h->d_ring = (int*)(b + o_ring);
   h->d_ctrl = (int*)(b + o_ctrl);
   h->d_vals = (double*)(b + o_vals);
+  if (h->fp32) {
+    h->d_csr_rp = (int64_t*)(b + o_crp);
+    h->d_csr_ci = (int32_t*)(b + o_cci);
+    h->d_csr_vmap = (int64_t*)(b + o_cvm);
+  }
   int rc = 0;
+  if (h->fp32 && ((rc = upload(h, h->d_csr_rp, crp)) || (rc = upload(h, h->d_csr_ci, cci)) ||
+                  (rc = upload(h, h->d_csr_vmap, cvm))))
+    return rc;
+  std::vector<int32_t>().swap(h->a_row);
+  std::vector<int32_t>().swap(h->a_col);
   std::vector<int32_t> perm32(P.perm.begin(), P.perm.end());
   if ((rc = upload(h, h->d_fcol, P.fcol)) || (rc = upload(h, h->d_nrows, P.nrows)) ||
       (rc = upload(h, h->d_ld, P.ld)) || (rc = upload(h, h->d_rows, P.rows)) ||
@@ -204,15 +253,32 @@ int setup_device(spchol_handle_t h) {
   return 0;
 }
 
-int ensure_workspace(spchol_handle_t h, int64_t need) {
-  if (need <= h->y_cap) return 0;
-  if (h->d_Y) cudaFree(h->d_Y);
-  if (h->d_B) cudaFree(h->d_B);
-  h->d_Y = h->d_B = nullptr;
-  h->y_cap = 0;
-  CU(cudaMalloc(&h->d_Y, need * sizeof(double)));
-  CU(cudaMalloc(&h->d_B, need * sizeof(double)));
-  h->y_cap = need;
+int ensure_workspace(spchol_handle_t h, int64_t need, int nrhs) {
+  if (need > h->y_cap) {
+    for (double** p : {&h->d_Y, &h->d_B, &h->d_X, &h->d_R})
+      if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+      }
+    h->y_cap = 0;
+    CU(cudaMalloc(&h->d_Y, need * sizeof(double)));
+    CU(cudaMalloc(&h->d_B, need * sizeof(double)));
+    if (h->fp32) {
+      CU(cudaMalloc(&h->d_X, need * sizeof(double)));
+      CU(cudaMalloc(&h->d_R, need * sizeof(double)));
+    }
+    h->y_cap = need;
+  }
+  if (h->fp32 && nrhs > h->norms_cap) {
+    if (h->d_norms) cudaFree(h->d_norms);
+    if (h->h_norms) cudaFreeHost(h->h_norms);
+    h->d_norms = nullptr;
+    h->h_norms = nullptr;
+    h->norms_cap = 0;
+    CU(cudaMalloc(&h->d_norms, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long)));
+    CU(cudaMallocHost(&h->h_norms, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long)));
+    h->norms_cap = nrhs;
+  }
   return 0;
 }
 
@@ -264,6 +330,11 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
   if (values_host && P.nnz_a > 0)
     CU(cudaMemcpyAsync(h->d_vals, values_host, P.nnz_a * sizeof(double), cudaMemcpyHostToDevice, st));
   const double* vals = values_host ? h->d_vals : values_dev_or_null;
+  if (h->fp32 && !values_host && P.nnz_a > 0 && vals != h->d_vals) {
+    // the refinement residual needs A's FP64 values after the caller's buffer is gone
+    CU(cudaMemcpyAsync(h->d_vals, vals, P.nnz_a * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    vals = h->d_vals;
+  }
   CU(cudaEventRecord(h->ev0, st));
   CU(cudaMemsetAsync(h->d_pool, 0, h->pool_bytes, st));
   CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
@@ -334,6 +405,56 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   return read_status(h, st, P.n_solve_tasks);
 }
 
+// Mixed precision: X = A^{-1} B by the low-precision factor plus FP64
+// refinement.  B0 = d_B (original order, ld n, nrhs columns); X ends in d_B.
+int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
+  Plan& P = h->plan;
+  const int64_t n = P.n;
+  const size_t nb = (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long);
+  CU(launch_anorm(n, h->d_csr_rp, h->d_csr_vmap, h->d_vals, h->d_norms, st));
+  CU(launch_permute_in(h->d_B, n, h->d_Y, n, h->d_perm, n, nrhs, st));
+  int rc = solve_permuted(h, h->d_Y, nrhs, st);
+  if (rc) return rc;
+  CU(cudaMemsetAsync(h->d_X, 0, n * nrhs * sizeof(double), st));
+  CU(launch_correct(h->d_Y, n, h->d_X, n, h->d_perm, n, nrhs, st));
+  double prev = INFINITY, berr = INFINITY;
+  int iters = 0;
+  rc = 0;
+  for (;;) {
+    CU(launch_residual(n, nrhs, h->d_csr_rp, h->d_csr_ci, h->d_csr_vmap, h->d_vals, h->d_X, n, h->d_B, n, h->d_R, n,
+                       h->d_norms + 1, st));
+    CU(cudaMemcpyAsync(h->h_norms, h->d_norms, nb, cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double anorm;
+    std::memcpy(&anorm, &h->h_norms[0], sizeof(double));
+    berr = 0.0;
+    for (int r = 0; r < nrhs; ++r) {
+      double rn, xn, bn;
+      std::memcpy(&rn, &h->h_norms[1 + 3 * r], sizeof(double));
+      std::memcpy(&xn, &h->h_norms[2 + 3 * r], sizeof(double));
+      std::memcpy(&bn, &h->h_norms[3 + 3 * r], sizeof(double));
+      const double den = anorm * xn + bn;
+      const double e = den > 0.0 ? rn / den : (rn > 0.0 ? INFINITY : 0.0);
+      if (!(e <= berr)) berr = e;  // NaN propagates
+    }
+    if (berr <= h->opt.ir_tol) break;
+    if (!(berr == berr) || iters >= h->opt.ir_max_iter || berr > 0.5 * prev) {
+      rc = SPCHOL_ENOCONV;
+      break;
+    }
+    prev = berr;
+    CU(launch_permute_in(h->d_R, n, h->d_Y, n, h->d_perm, n, nrhs, st));
+    int r2 = solve_permuted(h, h->d_Y, nrhs, st);
+    if (r2) return r2;
+    CU(launch_correct(h->d_Y, n, h->d_X, n, h->d_perm, n, nrhs, st));
+    ++iters;
+  }
+  h->stats.ir_iters = iters;
+  h->stats.berr = berr;
+  CU(cudaMemcpyAsync(h->d_B, h->d_X, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st));
+  return rc;
+}
+
 }  // namespace
 
 extern "C" {
@@ -380,6 +501,15 @@ int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, cons
   }
   PlanError err;
   int rc = build_plan(n, colptr, rowind, perm, params_from(o), h->plan, err);
+  if (rc == 0 && h->fp32) {
+    h->a_row.resize(h->plan.nnz_a);
+    h->a_col.resize(h->plan.nnz_a);
+    for (int64_t j = 0; j < n; ++j)
+      for (int64_t p = colptr[j]; p < colptr[j + 1]; ++p) {
+        h->a_row[p] = rowind[p];
+        h->a_col[p] = (int32_t)j;
+      }
+  }
   if (rc == 0 && o.fault_inject == 1 && h->plan.ns > 0) h->plan.dep_f[h->plan.ns - 1] += 1;
   if (rc == 0) rc = finish_analyze(h, t0);
   if (rc != 0) {
@@ -409,34 +539,39 @@ int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stre
   DeviceGuard g(h->device);
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->plan.n;
-  int rc = ensure_workspace(h, n * nrhs);
+  int rc = ensure_workspace(h, n * nrhs, nrhs);
   if (rc) return rc;
   const bool dev = is_device_ptr(B);
   CU(cudaEventRecord(h->ev0, st));
-  const double* src = B;
-  int64_t lds = ldb;
-  if (!dev) {
-    CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), nrhs,
-                         cudaMemcpyHostToDevice, st));
-    src = h->d_B;
-    lds = n;
-  }
-  CU(launch_permute_in(src, lds, h->d_Y, n, h->d_perm, n, nrhs, st));
-  rc = solve_permuted(h, h->d_Y, nrhs, st);
-  if (rc) return rc;
-  if (dev) {
+  if (dev && !h->fp32) {
+    // FP64 fast path: permute straight from and back into the caller's buffer
+    CU(launch_permute_in(B, ldb, h->d_Y, n, h->d_perm, n, nrhs, st));
+    rc = solve_permuted(h, h->d_Y, nrhs, st);
+    if (rc) return rc;
     CU(launch_permute_out(h->d_Y, n, B, ldb, h->d_perm, n, nrhs, st));
   } else {
-    CU(launch_permute_out(h->d_Y, n, h->d_B, n, h->d_perm, n, nrhs, st));
+    CU(cudaMemcpy2DAsync(h->d_B, n * sizeof(double), B, ldb * sizeof(double), n * sizeof(double), nrhs,
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    int core;
+    if (h->fp32) {
+      core = solve_refined(h, nrhs, st);
+      if (core != 0 && core != SPCHOL_ENOCONV) return core;
+    } else {
+      CU(launch_permute_in(h->d_B, n, h->d_Y, n, h->d_perm, n, nrhs, st));
+      core = solve_permuted(h, h->d_Y, nrhs, st);
+      if (core) return core;
+      CU(launch_permute_out(h->d_Y, n, h->d_B, n, h->d_perm, n, nrhs, st));
+    }
     CU(cudaMemcpy2DAsync(B, ldb * sizeof(double), h->d_B, n * sizeof(double), n * sizeof(double), nrhs,
-                         cudaMemcpyDeviceToHost, st));
+                         dev ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    rc = core;
   }
   CU(cudaEventRecord(h->ev1, st));
   CU(cudaStreamSynchronize(st));
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.solve_ms = ms;
-  return 0;
+  return rc;
 }
 
 int spchol_stats_get(spchol_handle_t h, spchol_stats* st) {
@@ -496,6 +631,10 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->d_Y) cudaFree(h->d_Y);
   if (h->d_B) cudaFree(h->d_B);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  if (h->d_X) cudaFree(h->d_X);
+  if (h->d_R) cudaFree(h->d_R);
+  if (h->d_norms) cudaFree(h->d_norms);
+  if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -584,7 +723,7 @@ int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, 
   }
   if (maxr == 0) return 0;
   const int64_t N = h->plan.n;
-  int rc = ensure_workspace(h, N * maxr);
+  int rc = ensure_workspace(h, N * maxr, maxr);
   if (rc) return rc;
   // Gather every matrix's RHS into one N x maxr block (zero columns where a
   // matrix has fewer right-hand sides), solve once, scatter back.
@@ -597,10 +736,16 @@ int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, 
                          dev ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
   }
   CU(cudaEventRecord(h->ev0, st));
-  CU(launch_permute_in(h->d_B, N, h->d_Y, N, h->d_perm, N, maxr, st));
-  rc = solve_permuted(h, h->d_Y, maxr, st);
-  if (rc) return rc;
-  CU(launch_permute_out(h->d_Y, N, h->d_B, N, h->d_perm, N, maxr, st));
+  int core = 0;
+  if (h->fp32) {
+    core = solve_refined(h, maxr, st);
+    if (core != 0 && core != SPCHOL_ENOCONV) return core;
+  } else {
+    CU(launch_permute_in(h->d_B, N, h->d_Y, N, h->d_perm, N, maxr, st));
+    rc = solve_permuted(h, h->d_Y, maxr, st);
+    if (rc) return rc;
+    CU(launch_permute_out(h->d_Y, N, h->d_B, N, h->d_perm, N, maxr, st));
+  }
   CU(cudaEventRecord(h->ev1, st));
   for (int i = 0; i < cnt; ++i) {
     if (nrhs[i] == 0 || h->batch_n[i] == 0) continue;
@@ -613,7 +758,7 @@ int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, 
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.solve_ms = ms;
-  return 0;
+  return core;
 }
 
 int spchol_batch_info(spchol_handle_t h, int64_t k, int* matrix, int64_t* column) {

@@ -82,29 +82,34 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
 }
 
 // ---------------------------------------------------------------- TRSM(s, k)
+// Arithmetic in the panel's type: FP64 panels solve in FP64, FP32 panels (the
+// mixed-precision modes) in FP32.
 template <typename T>
-__device__ void task_trsm(const FactorArgs& a, int s, int k, double* sm, FactorShared& sh, bool skip) {
+__device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, FactorShared& sh, bool skip) {
+  using ct = T;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int row0 = w + k * a.trsm_rows;
   const int cnt = min(a.trsm_rows, r - row0);
   T* P = panel_ptr<T>(a, s);
+  ct* sm = reinterpret_cast<ct*>(smd);
+  (void)f;
   if (!skip) {
     for (int idx = tid; idx < w * w; idx += nt) {
       const int i = idx % w, j = idx / w;
-      sm[idx] = (i >= j) ? (double)ldcg(P + i + (size_t)j * ld) : 0.0;
+      sm[idx] = (i >= j) ? (ct)ldcg(P + i + (size_t)j * ld) : ct(0);
     }
     __syncthreads();
     for (int rr = tid; rr < cnt; rr += nt) {
       T* Pi = P + row0 + rr;
       for (int jb = 0; jb < w; jb += kTrsmJB) {
         const int nb = min(kTrsmJB, w - jb);
-        double x[kTrsmJB];
+        ct x[kTrsmJB];
 #pragma unroll
-        for (int c = 0; c < kTrsmJB; ++c) x[c] = (c < nb) ? (double)ldcg(Pi + (size_t)(jb + c) * ld) : 0.0;
+        for (int c = 0; c < kTrsmJB; ++c) x[c] = (c < nb) ? (ct)ldcg(Pi + (size_t)(jb + c) * ld) : ct(0);
         for (int kk = 0; kk < jb; ++kk) {
-          const double xk = (double)ldcg(Pi + (size_t)kk * ld);
-          const double* Lk = sm + kk * w + jb;  // L[jb + c][kk]
+          const ct xk = (ct)ldcg(Pi + (size_t)kk * ld);
+          const ct* Lk = sm + kk * w + jb;  // L[jb + c][kk]
 #pragma unroll
           for (int c = 0; c < kTrsmJB; ++c)
             if (c < nb) x[c] -= xk * Lk[c];

@@ -79,6 +79,15 @@ cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t l
 cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t ldb, const int32_t* perm,
                                int64_t n, int nrhs, cudaStream_t st);
 
+// mixed.cu
+cudaError_t launch_residual(int64_t n, int nrhs, const int64_t* rp, const int32_t* ci, const int64_t* vmap,
+                            const double* aval, const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,
+                            int64_t ldr, unsigned long long* colmax, cudaStream_t st);
+cudaError_t launch_anorm(int64_t n, const int64_t* rp, const int64_t* vmap, const double* aval,
+                         unsigned long long* out, cudaStream_t st);
+cudaError_t launch_correct(const double* Y, int64_t ldy, double* X, int64_t ldx, const int32_t* perm, int64_t n,
+                           int nrhs, cudaStream_t st);
+
 // sched.cu
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,

@@ -1,0 +1,77 @@
+"""Mixed precision: FP32 panels and updates, FP64 diagonal factorization, FP64
+residual and iterative refinement.  The bar is a backward error <= 1e-12 after
+refinement against the same right-hand sides, with the iteration count stated."""
+import numpy as np
+import pytest
+
+import gridgen
+import oracle
+from tests.gpu_util import gpu_factor_solve
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+if not torch.cuda.is_available():  # pragma: no cover
+    pytest.skip("no CUDA device", allow_module_level=True)
+
+from paper_1608_00044_gb300 import spchol  # noqa: E402
+
+BERR_MIXED = 1e-12
+
+
+@pytest.mark.parametrize("name", ["lap2d_64", "lap3d_16", "diff3d_12", "diff2d_40"])
+@pytest.mark.parametrize("dev", [True, False])
+def test_fp32_refined_reaches_target(name, dev):
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=5)
+    rc, X, st, h = gpu_factor_solve(A, perm, B, use_device=dev, precision=spchol.FP32)
+    assert rc == 0
+    st = spchol.stats(h)
+    be = oracle.berr(A, X, B)
+    assert be <= BERR_MIXED, (be, st["ir_iters"])
+    # the library's own FP64 estimate agrees with the oracle's
+    assert st["berr"] <= BERR_MIXED and st["ir_iters"] >= 1
+    assert abs(st["berr"] - be) <= 0.5 * max(be, 1e-16) + 1e-16
+    spchol.destroy(h)
+
+
+def test_fp32_ill_conditioned_diffusion():
+    """27-point diffusion with log-normal conductivity (contrast 1e4)."""
+    A, perm, b = gridgen.workload("diff3d_16")
+    rc, X, st, h = gpu_factor_solve(A, perm, b, precision=spchol.FP32, ir_max_iter=30)
+    assert rc == 0
+    st = spchol.stats(h)
+    assert oracle.berr(A, X, b) <= BERR_MIXED, st
+    spchol.destroy(h)
+
+
+def test_refinement_reports_non_convergence():
+    """With no refinement steps allowed, the FP32 factor alone cannot reach 1e-12:
+    the solve must say so (ENOCONV) and still return its iterate."""
+    A, perm, b = gridgen.workload("diff3d_12")
+    o = spchol.default_options(precision=spchol.FP32, ir_max_iter=0)
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+    assert spchol.factorize(h, A.values) == 0
+    X = b.copy(order="F")
+    with pytest.raises(spchol.SpcholError) as ei:
+        spchol.solve(h, X, A.n, 1)
+    assert ei.value.code == spchol.ENOCONV
+    be = oracle.berr(A, X, b)
+    assert 1e-12 < be < 1e-4
+    assert abs(spchol.stats(h)["berr"] - be) <= 0.5 * be
+    spchol.destroy(h)
+
+
+def test_mixed_batch():
+    sides = [12, 20, 7, 33]
+    mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=i) for i, M in enumerate(mats)]
+    o = spchol.default_options(precision=spchol.FP32)
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+    Xs = [B.copy(order="F") for B in Bs]
+    spchol.batch_solve(h, Xs, [M.n for M in mats], [2] * len(mats))
+    for M, B, X in zip(mats, Bs, Xs):
+        assert oracle.berr(M, X, B) <= BERR_MIXED
+    spchol.destroy(h)
