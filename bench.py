@@ -187,7 +187,8 @@ def run_ours(args):
     prec = {"fp64": spchol.FP64, "fp32": spchol.FP32, "tf32": spchol.TF32}[args.precision]
     A, perm, b = _workload(args.workload)
     nrhs = b.shape[1]
-    opt = spchol.default_options(precision=prec, max_width=args.width)
+    opt = spchol.default_options(precision=prec, max_width=args.width, relax_zeros=args.relax,
+                                 profile=1 if args.profile else 0)
     h = spchol.analyze(A.n, A.colptr, A.rowind, perm, opt)
     st0 = spchol.stats(h)
     flops = st0["flops"]
@@ -248,7 +249,7 @@ def run_ours(args):
     vals_h = torch.from_numpy(A.values).pin_memory()
     Bh = torch.empty((nrhs, A.n), dtype=torch.float64).pin_memory()
     e2e_t = []
-    for it in range(args.warmup + args.steps):
+    for it in range(0 if args.no_e2e else args.warmup + args.steps):
         Bh.copy_(torch.from_numpy(np.ascontiguousarray(b.T)))
         t0 = time.perf_counter()
         rc = spchol.factorize(h, vals_h.numpy())
@@ -256,7 +257,7 @@ def run_ours(args):
         t1 = time.perf_counter()
         if it >= args.warmup:
             e2e_t.append(t1 - t0)
-    e2e_value = flops / (sum(e2e_t) / len(e2e_t)) / 1e12
+    e2e_value = flops / (sum(e2e_t) / len(e2e_t)) / 1e12 if e2e_t else None
     h2d = A.nnz * 8 + A.n * nrhs * 8
     d2h = A.n * nrhs * 8
 
@@ -288,8 +289,8 @@ def run_ours(args):
         "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32"}[args.precision],
         "data": "synthetic",
         "config": {"workload": f"{args.workload}: 3D 7-point Laplacian 64^3, n={A.n}, nnz(lower)={A.nnz}, "
-                               f"geometric ND, relax 4 zeros/col, {nrhs} RHS",
-                   "max_width": args.width, "precision": args.precision, "nrhs": nrhs,
+                               f"geometric ND, relax {args.relax} zeros/col, {nrhs} RHS",
+                   "max_width": args.width, "relax_zeros": args.relax, "precision": args.precision, "nrhs": nrhs,
                    "l2": "inputs larger than L2 (value pool %.2f GB)" % (st0["footprint_bytes"] / 1e9),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "fp64_peak_frac": value / peak_fp64,
@@ -310,6 +311,11 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if args.profile:
+        sp = spchol.stats(h)
+        line["task_profile"] = {k: sp[k] for k in ("factor_task_ms", "factor_task_count", "factor_wait_ms",
+                                                   "solve_task_ms", "solve_wait_ms", "grid_factor", "grid_solve",
+                                                   "n_supernodes", "n_tasks")}
     if rank == 0:
         print(json.dumps(line))
     spchol.destroy(h)
@@ -326,11 +332,14 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="lap3d_64")
     ap.add_argument("--width", type=int, default=64)
+    ap.add_argument("--relax", type=int, default=4, help="amalgamation: explicit zeros allowed per column")
     ap.add_argument("--precision", default="fp64", choices=["fp64", "fp32", "tf32"])
     ap.add_argument("--solve-reps", type=int, default=50)
     ap.add_argument("--cpu-sample", default="lap3d_36")
     ap.add_argument("--ref-sample", default="lap3d_28")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
+    ap.add_argument("--profile", action="store_true", help="time every task inside the persistent kernels")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

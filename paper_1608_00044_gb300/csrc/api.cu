@@ -75,6 +75,8 @@ struct spchol_handle_s {
   // value pool and solve workspace (separate allocations)
   void* d_pool = nullptr;
   size_t pool_bytes = 0;
+  double* d_inv = nullptr;  // diagonal-block inverses (FP64)
+  int64_t* d_invoff = nullptr;
   double* d_Y = nullptr;
   double* d_B = nullptr;
   int64_t y_cap = 0;  // capacity in doubles of d_Y and d_B
@@ -87,6 +89,8 @@ struct spchol_handle_s {
   int norms_cap = 0;                      // right-hand sides the norm buffers hold
   double* d_X = nullptr;
   double* d_R = nullptr;
+  unsigned long long* d_prof = nullptr;  // [0..7] factorization, [8..15] solve
+  unsigned long long* h_prof = nullptr;
   int* h_ctrl = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t smem_factor = 0, smem_solve = 0;
@@ -117,7 +121,7 @@ int setup_device(spchol_handle_t h) {
   auto r32 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int32_t)); };
   auto r64 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int64_t)); };
   size_t o_fcol = r32(ns + 1), o_nrows = r32(ns), o_ld = r32(ns), o_rows = r32(P.rows.size()), o_parent = r32(ns);
-  size_t o_rowoff = r64(ns + 1), o_valoff = r64(ns + 1), o_adest = r64(P.a_dest.size());
+  size_t o_rowoff = r64(ns + 1), o_valoff = r64(ns + 1), o_adest = r64(P.a_dest.size()), o_invoff = r64(ns + 1);
   size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
   size_t o_ut = A.reserve(std::max<size_t>(P.ut.size(), 1) * sizeof(UTask));
   size_t o_depi = r32(ns), o_trsi = r32(ns), o_dep = r32(ns), o_trs = r32(ns);
@@ -135,6 +139,7 @@ int setup_device(spchol_handle_t h) {
   size_t o_perm = r32(P.n);
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
+  size_t o_prof = A.reserve(16 * sizeof(unsigned long long));
   size_t o_vals = A.reserve(std::max<int64_t>(P.nnz_a, 1) * sizeof(double));
   // full symmetric CSR of A for the refinement residual (mixed precision only)
   std::vector<int64_t> crp, cvm;
@@ -174,6 +179,7 @@ int setup_device(spchol_handle_t h) {
   h->d_rowoff = (int64_t*)(b + o_rowoff);
   h->d_valoff = (int64_t*)(b + o_valoff);
   h->d_adest = (int64_t*)(b + o_adest);
+  h->d_invoff = (int64_t*)(b + o_invoff);
   h->d_trsm_first = (int32_t*)(b + o_tf);
   h->d_ntrsm = (int32_t*)(b + o_nt);
   h->d_trsm_sn = (int32_t*)(b + o_tsn);
@@ -200,6 +206,7 @@ int setup_device(spchol_handle_t h) {
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
   h->d_ctrl = (int*)(b + o_ctrl);
+  h->d_prof = (unsigned long long*)(b + o_prof);
   h->d_vals = (double*)(b + o_vals);
   if (h->fp32) {
     h->d_csr_rp = (int64_t*)(b + o_crp);
@@ -217,6 +224,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_ld, P.ld)) || (rc = upload(h, h->d_rows, P.rows)) ||
       (rc = upload(h, h->d_parent, P.parent)) || (rc = upload(h, h->d_rowoff, P.rowoff)) ||
       (rc = upload(h, h->d_valoff, P.valoff)) || (rc = upload(h, h->d_adest, P.a_dest)) ||
+      (rc = upload(h, h->d_invoff, P.invoff)) ||
       (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
       (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
       (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_ut, P.ut)) ||
@@ -230,7 +238,9 @@ int setup_device(spchol_handle_t h) {
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
+  CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
   CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
+  CU(cudaMallocHost(&h->h_prof, 16 * sizeof(unsigned long long)));
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));
   // launch geometry: persistent grids no larger than what can be co-resident
@@ -249,7 +259,9 @@ int setup_device(spchol_handle_t h) {
   }
   h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
-  h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes);
+  h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double));
+  h->stats.grid_factor = h->grid_factor;
+  h->stats.grid_solve = h->grid_solve;
   return 0;
 }
 
@@ -359,12 +371,24 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     a.ctrl = h->d_ctrl;
     a.budget_ns = h->opt.wait_budget_ns;
     a.pool = h->d_pool;
+    a.inv = h->d_inv;
+    a.invoff = h->d_invoff;
+    a.prof = h->opt.profile ? h->d_prof : nullptr;
+    if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), st));
     CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   }
   CU(cudaEventRecord(h->ev1, st));
   int rc = 0;
   if (P.ns > 0) {
     rc = read_status(h, st, P.n_factor_tasks);
+    if (h->opt.profile) {
+      CU(cudaMemcpy(h->h_prof, h->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+      for (int k = 0; k < 3; ++k) {
+        h->stats.factor_task_ms[k] = h->h_prof[k] * 1e-6;
+        h->stats.factor_task_count[k] = (int64_t)h->h_prof[4 + k];
+      }
+      h->stats.factor_wait_ms = h->h_prof[3] * 1e-6;
+    }
   } else {
     CU(cudaStreamSynchronize(st));
   }
@@ -398,11 +422,21 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.ctrl = h->d_ctrl;
   a.budget_ns = h->opt.wait_budget_ns;
   a.pool = h->d_pool;
+  a.inv = h->d_inv;
+  a.invoff = h->d_invoff;
   a.Y = Y;
   a.ldy = P.n;
   a.nrhs = nrhs;
+  a.prof = h->opt.profile ? h->d_prof + 8 : nullptr;
+  if (a.prof) CU(cudaMemsetAsync(h->d_prof + 8, 0, 8 * sizeof(unsigned long long), st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
-  return read_status(h, st, P.n_solve_tasks);
+  int rc = read_status(h, st, P.n_solve_tasks);
+  if (h->opt.profile) {
+    CU(cudaMemcpy(h->h_prof + 8, h->d_prof + 8, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; ++k) h->stats.solve_task_ms[k] = h->h_prof[8 + k] * 1e-6;
+    h->stats.solve_wait_ms = h->h_prof[12] * 1e-6;
+  }
+  return rc;
 }
 
 // Mixed precision: X = A^{-1} B by the low-precision factor plus FP64
@@ -628,9 +662,11 @@ int spchol_destroy(spchol_handle_t h) {
   DeviceGuard g(h->device);
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
+  if (h->d_inv) cudaFree(h->d_inv);
   if (h->d_Y) cudaFree(h->d_Y);
   if (h->d_B) cudaFree(h->d_B);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
+  if (h->h_prof) cudaFreeHost(h->h_prof);
   if (h->d_X) cudaFree(h->d_X);
   if (h->d_R) cudaFree(h->d_R);
   if (h->d_norms) cudaFree(h->d_norms);

@@ -75,6 +75,29 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
       const int i = idx % w, j = idx / w;
       if (i >= j) P[i + (size_t)j * ld] = (T)sm[idx];
     }
+    if (!sh.flag) {
+      // L11^{-1} for the solves: thread j forms column j, X e_j = L11^{-1} e_j, by
+      // forward substitution (right-looking, so the updates of one step are
+      // independent).  X[i][j], i > j, goes to the unused upper triangle at
+      // (j, i); the diagonal 1 / l_jj to xd[j].
+      double* xd = sm + w * w;
+      for (int j = tid; j < w; j += nt) {
+        const double xjj = 1.0 / sm[j + j * w];
+        xd[j] = xjj;
+        for (int i = j + 1; i < w; ++i) sm[j + i * w] = -sm[i + j * w] * xjj;
+        for (int k = j + 1; k < w; ++k) {
+          const double xk = sm[j + k * w] / sm[k + k * w];
+          sm[j + k * w] = xk;
+          for (int i = k + 1; i < w; ++i) sm[j + i * w] -= sm[i + k * w] * xk;
+        }
+      }
+      __syncthreads();
+      double* X = a.inv + a.invoff[s];
+      for (int idx = tid; idx < w * w; idx += nt) {
+        const int i = idx % w, j = idx / w;
+        if (i >= j) X[idx] = (i == j) ? xd[j] : sm[j + i * w];
+      }
+    }
   }
   publish_cta_writes();
   const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
@@ -136,6 +159,38 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
 }
 
 // ---------------------------------------------------------------- UPD(s, t, k)
+// C = A B^T for one tile, A = L_s[row tile] (rowlen x ws), B = L_s[segment]
+// (ncol x ws), staged through shared memory in k-chunks.  The 16 x 16 thread
+// grid covers C in 16-row / 16-column groups; NR x NC groups are computed, so
+// a small tile does not pay for a full 64 x 64 one.
+template <typename acc_t, int NR, int NC>
+__device__ __forceinline__ void upd_chunk(const acc_t* __restrict__ As, const acc_t* __restrict__ Bs, int kc, int tx,
+                                          int ty, acc_t (&acc)[4][4]) {
+#pragma unroll 4
+  for (int kk = 0; kk < kc; ++kk) {
+    acc_t av[NR], bv[NC];
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr) av[rr] = As[kk * kUpdTileM + ty + 16 * rr];
+#pragma unroll
+    for (int cc = 0; cc < NC; ++cc) bv[cc] = Bs[kk * kUpdTileN + tx + 16 * cc];
+#pragma unroll
+    for (int rr = 0; rr < NR; ++rr)
+#pragma unroll
+      for (int cc = 0; cc < NC; ++cc) acc[rr][cc] += av[rr] * bv[cc];
+  }
+}
+
+template <typename acc_t, int NR>
+__device__ __forceinline__ void upd_chunk_nc(int nc, const acc_t* As, const acc_t* Bs, int kc, int tx, int ty,
+                                             acc_t (&acc)[4][4]) {
+  switch (nc) {
+    case 1: upd_chunk<acc_t, NR, 1>(As, Bs, kc, tx, ty, acc); break;
+    case 2: upd_chunk<acc_t, NR, 2>(As, Bs, kc, tx, ty, acc); break;
+    case 3: upd_chunk<acc_t, NR, 3>(As, Bs, kc, tx, ty, acc); break;
+    default: upd_chunk<acc_t, NR, 4>(As, Bs, kc, tx, ty, acc); break;
+  }
+}
+
 template <typename T>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
                             bool skip) {
@@ -172,8 +227,12 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       grow[i] = g;
     }
     const int tx = tid & 15, ty = tid >> 4;
+    const int nrg = (u.rowlen + 15) >> 4;  // 16-row groups in use (1..4)
+    const int mrow = 16 * nrg;
     for (int cb = 0; cb < u.seglen; cb += kUpdTileN) {
       const int ncol = min(kUpdTileN, u.seglen - cb);
+      const int ncg = (ncol + 15) >> 4;
+      const int mcol = 16 * ncg;
       __syncthreads();
       for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
       acc_t acc[4][4];
@@ -184,38 +243,31 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       for (int k0 = 0; k0 < ws; k0 += kUpdKC) {
         const int kc = min(kUpdKC, ws - k0);
         __syncthreads();
-        for (int idx = tid; idx < kUpdKC * kUpdTileM; idx += blockDim.x) {
-          const int i = idx % kUpdTileM, kk = idx / kUpdTileM;
-          As[idx] = (i < u.rowlen && kk < kc) ? (acc_t)ldcg(Ps + (u.row0 + i) + (size_t)(k0 + kk) * lds) : acc_t(0);
+        for (int idx = tid; idx < kc * mrow; idx += blockDim.x) {
+          const int i = idx % mrow, kk = idx / mrow;
+          As[kk * kUpdTileM + i] = (i < u.rowlen) ? (acc_t)ldcg(Ps + (u.row0 + i) + (size_t)(k0 + kk) * lds) : acc_t(0);
         }
-        for (int idx = tid; idx < kUpdKC * kUpdTileN; idx += blockDim.x) {
-          const int j = idx % kUpdTileN, kk = idx / kUpdTileN;
-          Bs[idx] = (j < ncol && kk < kc) ? (acc_t)ldcg(Ps + (u.seg0 + cb + j) + (size_t)(k0 + kk) * lds)
-                                          : acc_t(0);
+        for (int idx = tid; idx < kc * mcol; idx += blockDim.x) {
+          const int j = idx % mcol, kk = idx / mcol;
+          Bs[kk * kUpdTileN + j] = (j < ncol) ? (acc_t)ldcg(Ps + (u.seg0 + cb + j) + (size_t)(k0 + kk) * lds) : acc_t(0);
         }
         __syncthreads();
-#pragma unroll 4
-        for (int kk = 0; kk < kUpdKC; ++kk) {
-          acc_t av[4], bv[4];
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr) av[rr] = As[kk * kUpdTileM + ty + 16 * rr];
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) bv[cc] = Bs[kk * kUpdTileN + tx + 16 * cc];
-#pragma unroll
-          for (int rr = 0; rr < 4; ++rr)
-#pragma unroll
-            for (int cc = 0; cc < 4; ++cc) acc[rr][cc] += av[rr] * bv[cc];
+        switch (nrg) {
+          case 1: upd_chunk_nc<acc_t, 1>(ncg, As, Bs, kc, tx, ty, acc); break;
+          case 2: upd_chunk_nc<acc_t, 2>(ncg, As, Bs, kc, tx, ty, acc); break;
+          case 3: upd_chunk_nc<acc_t, 3>(ncg, As, Bs, kc, tx, ty, acc); break;
+          default: upd_chunk_nc<acc_t, 4>(ncg, As, Bs, kc, tx, ty, acc); break;
         }
       }
       // Scatter-subtract into panel t: only the lower triangle (row >= column).
 #pragma unroll
       for (int rr = 0; rr < 4; ++rr) {
         const int i = ty + 16 * rr;
-        if (i >= u.rowlen) continue;
+        if (rr >= nrg || i >= u.rowlen) continue;
 #pragma unroll
         for (int cc = 0; cc < 4; ++cc) {
           const int j = tx + 16 * cc;
-          if (j < ncol && grow[i] >= gcol[j] && pos[i] >= 0)
+          if (cc < ncg && j < ncol && grow[i] >= gcol[j] && pos[i] >= 0)
             red_add(Pt + pos[i] + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
         }
       }
@@ -236,26 +288,56 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
   const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+  // per-CTA task timing (thread 0 only), flushed once at exit
+  unsigned long long busy[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, wait = 0;
   for (;;) {
+    uint64_t t0 = 0, t1 = 0;
     if (threadIdx.x == 0) {
+      if (a.prof) t0 = global_ns();
       sh.task = ring_claim(q);
       sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
+      if (a.prof) {
+        t1 = global_ns();
+        wait += t1 - t0;
+      }
     }
     __syncthreads();
     const int task = sh.task;
     const bool skip = sh.skip != 0;
     if (task < 0) break;
+    int type;
     if (task < a.pv.ns) {
+      type = 0;
       task_potrf<T>(a, task, smd, sh, skip);
     } else if (task < a.pv.ns + a.n_trsm) {
+      type = 1;
       const int kt = task - a.pv.ns;
       const int s = a.trsm_sn[kt];
       task_trsm<T>(a, s, kt - a.trsm_first[s], smd, sh, skip);
     } else {
+      type = 2;
       task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
     }
-    if (threadIdx.x == 0) atomicAdd(&a.ctrl[kDone], 1);
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.ctrl[kDone], 1);
+      if (a.prof) {
+        const unsigned long long d = global_ns() - t1;
+#pragma unroll
+        for (int k = 0; k < 3; ++k)
+          if (k == type) {
+            busy[k] += d;
+            cnt[k] += 1;
+          }
+      }
+    }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && a.prof) {
+    for (int k = 0; k < 3; ++k) {
+      atomicAdd(&a.prof[k], busy[k]);
+      atomicAdd(&a.prof[4 + k], cnt[k]);
+    }
+    atomicAdd(&a.prof[3], wait);
   }
 }
 
@@ -269,7 +351,7 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 }  // namespace
 
 size_t factor_smem_bytes(int max_w) {
-  size_t tri = (size_t)max_w * max_w * sizeof(double);
+  size_t tri = ((size_t)max_w * max_w + max_w) * sizeof(double);
   size_t upd = (size_t)kUpdKC * (kUpdTileM + kUpdTileN) * sizeof(double) +
                (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
   return tri > upd ? tri : upd;

@@ -41,6 +41,9 @@ struct FactorArgs {
   int* ctrl;
   int64_t budget_ns;
   void* pool;          // double* or float*
+  double* inv;         // per panel: L11^{-1} (w x w, column-major, lower part)
+  const int64_t* invoff;
+  unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts
 };
 
 struct SolveArgs {
@@ -58,9 +61,12 @@ struct SolveArgs {
   int* ctrl;
   int64_t budget_ns;
   const void* pool;
+  const double* inv;     // per panel: L11^{-1}
+  const int64_t* invoff;
   double* Y;        // n x nrhs, permuted order
   int64_t ldy;
   int nrhs;
+  unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
 };
 
 // factor.cu

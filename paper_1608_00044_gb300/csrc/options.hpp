@@ -24,12 +24,14 @@ inline void default_options(spchol_options* o) {
   o->ir_max_iter = 10;
   o->ir_tol = 1e-12;
   o->fault_inject = 0;
+  o->profile = 0;
 }
 
 inline bool options_valid(const spchol_options& o) {
   return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_TF32 && o.max_width >= 1 && o.max_width <= 128 &&
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
-         o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1;
+         o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 &&
+         o.profile >= 0 && o.profile <= 1;
 }
 
 inline PlanParams params_from(const spchol_options& o) {

@@ -42,6 +42,7 @@ struct Plan {
   std::vector<int64_t> rowoff;  // ns + 1, into rows
   std::vector<int32_t> rows;    // concatenated sorted row lists
   std::vector<int64_t> valoff;  // ns + 1, into the value pool (elements)
+  std::vector<int64_t> invoff;  // ns + 1, into the diagonal-block inverse buffer (w x w per panel)
   std::vector<int32_t> parent;  // panel etree, -1 at roots
   std::vector<int32_t> snode_of;  // column -> panel
   std::vector<int64_t> a_dest;  // entry e of A's lower CSC -> pool index

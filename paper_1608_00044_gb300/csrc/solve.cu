@@ -43,13 +43,17 @@ __device__ void load_l11(const T* P, int w, int ld, double* sm) {
   }
 }
 
-template <typename T>
+// y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
+// every entry is an independent dot product, no sequential substitution.
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
-  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
-  const T* P = spanel<T>(a, s);
-  double* L = sm;
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
+  const double* X = a.inv + a.invoff[s];
+  double* Xs = sm;          // [w][w] column-major, lower part
   double* Ys = sm + w * w;  // [nrc][w]
-  load_l11<T>(P, w, ld, L);
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    Xs[idx] = (i >= j) ? X[idx] : 0.0;
+  }
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -58,30 +62,31 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     __syncthreads();
-    for (int j = 0; j < w; ++j) {
-      for (int r = threadIdx.x; r < nrc; r += blockDim.x) Ys[j + r * w] = Ys[j + r * w] / L[j + j * w];
-      __syncthreads();
-      const int m = w - j - 1;
-      for (int idx = threadIdx.x; idx < m * nrc; idx += blockDim.x) {
-        const int i = j + 1 + idx % m, r = idx / m;
-        Ys[i + r * w] -= L[i + j * w] * Ys[j + r * w];
+    for (int p = threadIdx.x; p < w * nrc; p += blockDim.x) {
+      const int i = p % w, r = p / w;
+      const double* y = Ys + r * w;
+      double a0 = 0.0, a1 = 0.0;
+      int k = 0;
+      for (; k + 1 <= i; k += 2) {
+        a0 += Xs[i + k * w] * y[k];
+        a1 += Xs[i + (k + 1) * w] * y[k + 1];
       }
-      __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
-      const int j = idx % w, r = idx / w;
-      a.Y[f + j + (size_t)(r0 + r) * a.ldy] = Ys[idx];
+      if (k <= i) a0 += Xs[i + k * w] * y[k];
+      a.Y[f + i + (size_t)(r0 + r) * a.ldy] = a0 + a1;
     }
   }
 }
 
-template <typename T>
+// x_s <- L11^{-T} y_s with the stored inverse.
 __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
-  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
-  const T* P = spanel<T>(a, s);
-  double* L = sm;
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
+  const double* X = a.inv + a.invoff[s];
+  double* Xs = sm;
   double* Ys = sm + w * w;
-  load_l11<T>(P, w, ld, L);
+  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    Xs[idx] = (i >= j) ? X[idx] : 0.0;
+  }
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -90,18 +95,18 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     __syncthreads();
-    for (int j = w - 1; j >= 0; --j) {
-      for (int r = threadIdx.x; r < nrc; r += blockDim.x) Ys[j + r * w] = Ys[j + r * w] / L[j + j * w];
-      __syncthreads();
-      for (int idx = threadIdx.x; idx < j * nrc; idx += blockDim.x) {
-        const int i = idx % j, r = idx / j;
-        Ys[i + r * w] -= L[j + i * w] * Ys[j + r * w];
+    for (int p = threadIdx.x; p < w * nrc; p += blockDim.x) {
+      const int kcol = p % w, r = p / w;
+      const double* y = Ys + r * w;
+      const double* xc = Xs + kcol * w;  // column kcol of L11^{-1}: rows kcol..w-1
+      double a0 = 0.0, a1 = 0.0;
+      int i = kcol;
+      for (; i + 1 < w; i += 2) {
+        a0 += xc[i] * y[i];
+        a1 += xc[i + 1] * y[i + 1];
       }
-      __syncthreads();
-    }
-    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
-      const int j = idx % w, r = idx / w;
-      a.Y[f + j + (size_t)(r0 + r) * a.ldy] = Ys[idx];
+      if (i < w) a0 += xc[i] * y[i];
+      a.Y[f + kcol + (size_t)(r0 + r) * a.ldy] = a0 + a1;
     }
   }
 }
@@ -198,14 +203,24 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
   double* sm = reinterpret_cast<double*>(smem_raw);
   const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
   const int ns = a.pv.ns, nst = a.n_st;
+  unsigned long long busy[4] = {0, 0, 0, 0}, wait = 0;
   for (;;) {
-    if (threadIdx.x == 0) sh.task = ring_claim(q);
+    uint64_t t1 = 0;
+    if (threadIdx.x == 0) {
+      const uint64_t t0 = a.prof ? global_ns() : 0;
+      sh.task = ring_claim(q);
+      if (a.prof) {
+        t1 = global_ns();
+        wait += t1 - t0;
+      }
+    }
     __syncthreads();
     const int task = sh.task;
     if (task < 0) break;
+    const int type = task < ns ? 0 : task < ns + nst ? 1 : task < ns + 2 * nst ? 2 : 3;
     if (task < ns) {
       const int s = task;
-      fwd_diag<T>(a, s, sm);
+      fwd_diag(a, s, sm);
       publish_cta_writes();
       if (a.nst[s] > 0) {
         ring_push_range(q, ns + a.st_first[s], a.nst[s], &sh.base);
@@ -227,15 +242,22 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
       if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) ring_push_one(q, ns + 2 * nst + s);
     } else {
       const int s = task - ns - 2 * nst;
-      bwd_diag<T>(a, s, sm);
+      bwd_diag(a, s, sm);
       publish_cta_writes();
       for (int c = a.kid_ptr[s]; c < a.kid_ptr[s + 1]; ++c) {
         const int kid = a.kids[c];
         ring_push_range(q, ns + nst + a.st_first[kid], a.nst[kid], &sh.base);
       }
     }
-    if (threadIdx.x == 0) atomicAdd(&a.ctrl[kDone], 1);
+    if (threadIdx.x == 0) {
+      atomicAdd(&a.ctrl[kDone], 1);
+      if (a.prof) busy[type] += global_ns() - t1;
+    }
     __syncthreads();
+  }
+  if (threadIdx.x == 0 && a.prof) {
+    for (int k = 0; k < 4; ++k) atomicAdd(&a.prof[k], busy[k]);
+    atomicAdd(&a.prof[4], wait);
   }
 }
 

@@ -294,6 +294,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   // ---- storage layout ------------------------------------------------------
   P.ld.resize(ns);
   P.valoff.assign(ns + 1, 0);
+  P.invoff.assign(ns + 1, 0);
   P.nnz_l_stored = 0;
   P.max_w = 0;
   P.max_r = 0;
@@ -301,6 +302,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
     P.ld[s] = (int32_t)round4(r);
     P.valoff[s + 1] = P.valoff[s] + (int64_t)P.ld[s] * w;
+    P.invoff[s + 1] = P.invoff[s] + (int64_t)w * w;
     P.nnz_l_stored += (int64_t)r * w - (int64_t)w * (w - 1) / 2;
     P.max_w = std::max(P.max_w, w);
     P.max_r = std::max(P.max_r, r);

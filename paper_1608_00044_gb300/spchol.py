@@ -32,6 +32,7 @@ class Options(ctypes.Structure):
         ("ir_max_iter", ctypes.c_int),
         ("ir_tol", ctypes.c_double),
         ("fault_inject", ctypes.c_int),
+        ("profile", ctypes.c_int),
     ]
 
 
@@ -53,10 +54,21 @@ class Stats(ctypes.Structure):
         ("ir_iters", ctypes.c_int),
         ("berr", ctypes.c_double),
         ("precision", ctypes.c_int),
+        ("factor_task_ms", ctypes.c_double * 3),
+        ("factor_task_count", ctypes.c_int64 * 3),
+        ("factor_wait_ms", ctypes.c_double),
+        ("solve_task_ms", ctypes.c_double * 4),
+        ("solve_wait_ms", ctypes.c_double),
+        ("grid_factor", ctypes.c_int),
+        ("grid_solve", ctypes.c_int),
     ]
 
     def as_dict(self):
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        out = {}
+        for k, _ in self._fields_:
+            v = getattr(self, k)
+            out[k] = list(v) if hasattr(v, "__len__") else v
+        return out
 
 
 class SpcholError(RuntimeError):
@@ -119,7 +131,7 @@ def default_options(**kw) -> Options:
 def default_options_host(**kw) -> Options:
     """The defaults of include/spchol.h filled without loading the GPU library."""
     o = Options(precision=FP64, max_width=64, relax_zeros=4, tile_rows=0, ctas_per_sm=0, deterministic=0,
-                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12)
+                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
