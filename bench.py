@@ -164,6 +164,120 @@ def run_reference(args):
     return 0
 
 
+def measure_mixed(spchol, oracle, torch, dev, name="diff3d_48", width=64):
+    """Mixed-precision row: FP64 factor+solve vs FP32 factor + solve + FP64 refinement to 1e-12,
+    same matrix and right-hand side, device time of each."""
+    A, perm, b = _workload(name)
+    out = {"workload": f"{name}: 3D 27-point variable-coefficient diffusion {A.dims}, n={A.n}, "
+                       f"log-normal kappa sigma=2 clipped (contrast 1e4), 1 RHS"}
+    vals = torch.from_numpy(A.values).to(dev)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
+    res = {}
+    for label, prec in (("fp64", spchol.FP64), ("fp32_ir", spchol.FP32)):
+        o = spchol.default_options(precision=prec, max_width=width, ir_max_iter=30)
+        h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
+        times, ok = [], True
+        for it in range(4):
+            spchol.factorize(h, vals)
+            X = bt.clone()
+            try:
+                spchol.solve(h, X, A.n, 1)
+                ok = True
+            except spchol.SpcholError as e:
+                if e.code != spchol.ENOCONV:
+                    raise
+                ok = False
+            st = spchol.stats(h)
+            if it >= 1:
+                times.append(st["factor_ms"] + st["solve_ms"])
+        be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), b)
+        res[label] = {"ms": sum(times) / len(times), "factor_ms": st["factor_ms"], "solve_ms": st["solve_ms"],
+                      "berr": be, "ir_iters": st["ir_iters"], "converged": bool(ok and be <= 1e-12)}
+        spchol.destroy(h)
+    out.update(res)
+    out["flops"] = float(_flops_of(spchol, A, perm))
+    out["fp32_ir_speedup"] = res["fp64"]["ms"] / res["fp32_ir"]["ms"]
+    return out
+
+
+def _flops_of(spchol, A, perm):
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options())
+    f = spchol.stats(h)["flops"]
+    spchol.destroy(h)
+    return f
+
+
+def measure_batch(spchol, oracle, torch, dev, count=512, width=64):
+    """Batch row: 512 independent 2D 5-point variable-coefficient grids (sides from
+    default_rng(1234) in [16, 128]) factored in ONE persistent launch."""
+    import gridgen
+
+    sides = gridgen.batch_sides(count)
+    mats = [gridgen.diffusion_2d_5pt(int(sd), sigma=1.0, seed=1000 + i) for i, sd in enumerate(sides)]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    out = {"workload": f"{count} x 2D 5-point variable-coefficient grids, sides U[16,128] (rng 1234), sigma=1",
+           "n_total": int(sum(M.n for M in mats))}
+    for label, prec in (("fp64", spchol.FP64), ("fp32_ir", spchol.FP32)):
+        o = spchol.default_options(precision=prec, max_width=width)
+        t0 = time.perf_counter()
+        h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+        ana = time.perf_counter() - t0
+        st0 = spchol.stats(h)
+        dvals = [torch.from_numpy(M.values).to(dev) for M in mats]
+        fms = []
+        for it in range(4):
+            rc = spchol.batch_factorize(h, dvals)
+            if it >= 1:
+                fms.append(spchol.stats(h)["factor_ms"])
+        Bs = [gridgen.rhs_uniform(M.n, 1, seed=i) for i, M in enumerate(mats)]
+        Xs = [B.copy(order="F") for B in Bs]
+        try:
+            spchol.batch_solve(h, Xs, [M.n for M in mats], [1] * count)
+        except spchol.SpcholError:
+            pass
+        st = spchol.stats(h)
+        worst = max(oracle.berr(M, X, B) for M, X, B in zip(mats, Xs, Bs))
+        ms = sum(fms) / len(fms)
+        out[label] = {"factor_ms_one_launch": ms, "tflops": st0["flops"] / (ms * 1e-3) / 1e12,
+                      "solve_ms": st["solve_ms"], "worst_berr": worst, "analyze_s": ana, "rc": rc,
+                      "panels": st0["n_supernodes"], "tasks": st0["n_tasks"]}
+        spchol.destroy(h)
+    out["flops"] = float(st0["flops"])
+    return out
+
+
+def measure_serving(full=False, slots=4):
+    """Serving row: Poisson arrivals of mixed 2D/3D problems, 30% repeat solves,
+    admission by device footprint; p50/p99 latency next to solves/s.  The maximum
+    throughput is measured closed-loop first, then the stream runs at fractions of it."""
+    from paper_1608_00044_gb300 import serve
+
+    n_req, warm = (2000, 200) if full else (160, 40)
+    fracs = (0.25, 0.5, 0.75, 0.9) if full else (0.5,)
+    srv = serve.Server(slots=slots)
+    # closed loop: all requests at t = 0 (warm-up part discarded)
+    reqs = serve.make_stream(n_req + warm, rate=0, seed=4321)
+    srv.run(reqs)
+    done = sorted(reqs, key=lambda q: q.done)[warm:]
+    span = done[-1].done - done[0].done
+    max_tp = (len(done) - 1) / span if span > 0 else 0.0
+    out = {"workload": "Poisson stream: 50% 2D (32^2..256^2) / 50% 3D (16^3..48^3), Laplacian or diffusion, "
+                       "1..16 RHS, 30% repeat solves, seed 4321",
+           "slots": slots, "max_requests_per_s": max_tp, "budget_bytes": srv.budget, "runs": []}
+    for f in fracs:
+        reqs = serve.make_stream(n_req + warm, rate=f * max_tp, seed=4321 + int(100 * f))
+        srv.run(reqs)
+        summ = serve.latency_summary(reqs[warm:])
+        summ["rate_frac_of_max"] = f
+        summ["rate_per_s"] = f * max_tp
+        summ["errors"] = int(sum(q.rc not in (0,) for q in reqs))
+        out["runs"].append(summ)
+    out["factorizations"] = srv.factorizations
+    out["peak_resident_bytes"] = srv.peak_used
+    srv.close()
+    return out
+
+
 def run_ours(args):
     import torch
 
@@ -311,6 +425,10 @@ def run_ours(args):
     }
     if cpu is not None:
         line["cpu_baseline"] = cpu
+    if not args.no_rows:
+        line["mixed_precision_row"] = measure_mixed(spchol, oracle, torch, dev, width=args.width)
+        line["batch_row"] = measure_batch(spchol, oracle, torch, dev, width=args.width)
+        line["serving_row"] = measure_serving(full=args.serve_full)
     if args.profile:
         sp = spchol.stats(h)
         line["task_profile"] = {k: sp[k] for k in ("factor_task_ms", "factor_task_count", "factor_wait_ms",
@@ -340,6 +458,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--profile", action="store_true", help="time every task inside the persistent kernels")
+    ap.add_argument("--no-rows", action="store_true", help="skip the mixed-precision, batch and serving rows")
+    ap.add_argument("--serve-full", action="store_true", help="serving row with 2000 requests at 4 rates")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)

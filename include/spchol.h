@@ -63,17 +63,20 @@ extern "C" {
 /* Arithmetic of the factor. */
 #define SPCHOL_FP64 0  /* everything in FP64 */
 #define SPCHOL_FP32 1  /* FP32 panels and updates, FP64 diagonal POTRF, FP64 residual + refinement */
-#define SPCHOL_TF32 2  /* as FP32, update GEMMs on TF32 tensor cores (tcgen05) */
+#define SPCHOL_TF32 2  /* as FP32, update GEMMs on TF32 tensor cores (tcgen05.mma kind::tf32) */
+#define SPCHOL_TF32X3 3 /* as TF32, each operand split into a TF32 head and tail, three products per
+                           tile: FP32-level accuracy on the tensor cores */
 
 typedef struct spchol_handle_s* spchol_handle_t;
 
 typedef struct spchol_options {
-  int precision;          /* SPCHOL_FP64 (default), SPCHOL_FP32, SPCHOL_TF32 */
+  int precision;          /* SPCHOL_FP64 (default), SPCHOL_FP32, SPCHOL_TF32, SPCHOL_TF32X3 */
   int max_width;          /* W: supernode panels are at most W columns (Section III-B caps at 150);
-                             1..128, default 64 */
+                             1..128 (1..64 with the tensor-core precisions), default 64 */
   int relax_zeros;        /* amalgamation: a child supernode is merged into its parent when every
                              merged column gains at most this many explicit zeros; default 4, 0 = off */
-  int tile_rows;          /* rows per update tile, 1..64; 0 = default (64) */
+  int tile_rows;          /* rows per update tile, 1..64; 0 = default (64; 128 with the tensor-core
+                             precisions, which ignore this field) */
   int ctas_per_sm;        /* persistent-kernel CTAs per SM; 0 = as many as fit */
   int deterministic;      /* reserved: 0 */
   int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
@@ -82,6 +85,9 @@ typedef struct spchol_options {
   int fault_inject;       /* failure-detection test hook, 0 = off.  1: analyze adds one phantom
                              dependency to the last panel, so its diagonal task never becomes ready
                              and factorize must return SPCHOL_ETIMEOUT after wait_budget_ns. */
+  int profile;            /* 1: the persistent kernels time every task (per-type busy time and the
+                             time spent waiting for a ready task, summed over CTAs) into the stats;
+                             2: additionally record each task's start and end (spchol_trace_get) */
 } spchol_options;
 
 typedef struct spchol_stats {
@@ -101,6 +107,14 @@ typedef struct spchol_stats {
   int ir_iters;           /* refinement steps of the last solve */
   double berr;            /* backward error of the last solve (mixed precision), else -1 */
   int precision;
+  /* filled when spchol_options.profile = 1; CTA-milliseconds summed over all CTAs */
+  double factor_task_ms[3];   /* diagonal factor, panel-solve tiles, update tiles */
+  int64_t factor_task_count[3];
+  double factor_wait_ms;      /* waiting for a ready task */
+  double solve_task_ms[4];    /* forward diagonal, forward tiles, backward tiles, backward diagonal */
+  double solve_wait_ms;
+  int grid_factor;            /* CTAs of the persistent factorization launch */
+  int grid_solve;
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */
@@ -152,11 +166,26 @@ int spchol_stats_get(spchol_handle_t h, spchol_stats* st);
 int spchol_export_factor(spchol_handle_t h, int64_t* nnz, int64_t* Lp, int64_t* Li, double* Lx,
                          int64_t* perm_out);
 
+/*
+ * Per-task trace of the last factorization (which = 0) or solve (which = 1),
+ * recorded when spchol_options.profile = 2: out[2*i] and out[2*i+1] are the
+ * device-clock start and end (ns, %globaltimer) of task i, in the task
+ * numbering of the launch (factorization: diagonal tasks, then panel-solve
+ * tiles, then update tiles).  Query form: out = NULL sets *count to the number
+ * of tasks.  Returns 0, -2 for a bad `which`, SPCHOL_ESTATE if not traced.
+ */
+int spchol_trace_get(spchol_handle_t h, int which, uint64_t* out, int64_t* count);
+
 /* Release every resource of the handle.  NULL is accepted. */
 int spchol_destroy(spchol_handle_t h);
 
 /* Static, human-readable text for a return code. */
 const char* spchol_strerror(int code);
+
+/* The CUDA error name and call site of the last SPCHOL_ECUDA / SPCHOL_ENOMEM
+ * returned to this host thread ("" if none).  Valid until the thread's next
+ * failing call. */
+const char* spchol_last_cuda_error(void);
 
 /*
  * Batch of independent matrices factored in ONE persistent launch: the

@@ -9,6 +9,7 @@ from .spchol import (
     FP32,
     FP64,
     TF32,
+    TF32X3,
     SparseCholesky,
     SpcholError,
     analyze,
@@ -30,6 +31,7 @@ __all__ = [
     "FP32",
     "FP64",
     "TF32",
+    "TF32X3",
     "SparseCholesky",
     "SpcholError",
     "analyze",

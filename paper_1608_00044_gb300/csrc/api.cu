@@ -4,6 +4,7 @@
 #include <chrono>
 #include <climits>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
@@ -90,6 +91,9 @@ struct spchol_handle_s {
   double* d_X = nullptr;
   double* d_R = nullptr;
   unsigned long long* d_prof = nullptr;  // [0..7] factorization, [8..15] solve
+  unsigned long long* d_trace_f = nullptr;  // profile = 2: per factorization task start/end
+  unsigned long long* d_trace_s = nullptr;  // profile = 2: per solve task start/end
+  bool traced_f = false, traced_s = false;
   unsigned long long* h_prof = nullptr;
   int* h_ctrl = nullptr;  // pinned
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -99,19 +103,38 @@ struct spchol_handle_s {
 
 namespace {
 
-inline int cuda_fail(cudaError_t e) { return e == cudaErrorMemoryAllocation ? SPCHOL_ENOMEM : SPCHOL_ECUDA; }
+// Text of the last failing CUDA call of this host thread (spchol_last_cuda_error).
+thread_local char g_cuda_err[256] = "";
 
-#define CU(x)                                  \
-  do {                                         \
-    cudaError_t e_ = (x);                      \
-    if (e_ != cudaSuccess) return cuda_fail(e_); \
+inline int cuda_fail(cudaError_t e, const char* what, int line) {
+  snprintf(g_cuda_err, sizeof(g_cuda_err), "%s (%d) at api.cu:%d in %s", cudaGetErrorName(e), (int)e, line, what);
+  return e == cudaErrorMemoryAllocation ? SPCHOL_ENOMEM : SPCHOL_ECUDA;
+}
+
+#define CU(x)                                                 \
+  do {                                                        \
+    cudaError_t e_ = (x);                                     \
+    if (e_ != cudaSuccess) return cuda_fail(e_, #x, __LINE__); \
   } while (0)
+
+// A non-sticky error left in this thread's CUDA error slot by another library
+// must not be reported as the failure of our next launch.
+inline void clear_stale_error() { (void)cudaGetLastError(); }
+
+// Structure uploads go through a private non-blocking stream so that analyze
+// never orders itself behind work that other threads run on other streams.
+thread_local cudaStream_t g_upload_stream = nullptr;
 
 template <typename V>
 int upload(spchol_handle_t h, V* dst, const std::vector<V>& src) {
+  (void)h;
   if (src.empty()) return 0;
-  CU(cudaMemcpy(dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice));
+  CU(cudaMemcpyAsync(dst, src.data(), src.size() * sizeof(V), cudaMemcpyHostToDevice, g_upload_stream));
   return 0;
+}
+
+int mma_mode_of(int precision) {
+  return precision == SPCHOL_TF32 ? 1 : precision == SPCHOL_TF32X3 ? 2 : 0;
 }
 
 int setup_device(spchol_handle_t h) {
@@ -170,6 +193,16 @@ int setup_device(spchol_handle_t h) {
     o_cvm = r64(cvm.size());
   }
   CU(cudaMalloc(&A.base, A.bytes));
+  CU(cudaStreamCreateWithFlags(&g_upload_stream, cudaStreamNonBlocking));
+  struct StreamGuard {
+    ~StreamGuard() {
+      if (g_upload_stream) {
+        cudaStreamSynchronize(g_upload_stream);
+        cudaStreamDestroy(g_upload_stream);
+        g_upload_stream = nullptr;
+      }
+    }
+  } upload_guard;
   char* b = A.base;
   h->d_fcol = (int32_t*)(b + o_fcol);
   h->d_nrows = (int32_t*)(b + o_nrows);
@@ -241,13 +274,17 @@ int setup_device(spchol_handle_t h) {
   CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
   CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
   CU(cudaMallocHost(&h->h_prof, 16 * sizeof(unsigned long long)));
+  if (h->opt.profile == 2) {
+    CU(cudaMalloc(&h->d_trace_f, 2 * (size_t)std::max(P.n_factor_tasks, 1) * sizeof(unsigned long long)));
+    CU(cudaMalloc(&h->d_trace_s, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long)));
+  }
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));
   // launch geometry: persistent grids no larger than what can be co-resident
   int dev = h->device;
   CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
   const int wmax = std::max<int>(P.max_w, 1);
-  h->smem_factor = factor_smem_bytes(wmax);
+  h->smem_factor = factor_smem_bytes(wmax, mma_mode_of(h->opt.precision));
   h->smem_solve = solve_smem_bytes(wmax);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, h->smem_factor, &bf));
@@ -365,6 +402,7 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     a.n_u = P.n_u;
     a.ntask = P.n_factor_tasks;
     a.trsm_rows = P.params.trsm_rows;
+    a.mma_mode = mma_mode_of(h->opt.precision);
     a.dep_f = h->d_dep;
     a.trsm_left = h->d_trsm_left;
     a.ring = h->d_ring;
@@ -374,6 +412,7 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     a.inv = h->d_inv;
     a.invoff = h->d_invoff;
     a.prof = h->opt.profile ? h->d_prof : nullptr;
+    a.trace = h->d_trace_f;
     if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), st));
     CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   }
@@ -396,6 +435,7 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.factor_ms = ms;
   if (rc == 0) h->factored = true;
+  h->traced_f = h->d_trace_f != nullptr && P.ns > 0;
   return rc;
 }
 
@@ -428,9 +468,11 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.ldy = P.n;
   a.nrhs = nrhs;
   a.prof = h->opt.profile ? h->d_prof + 8 : nullptr;
+  a.trace = h->d_trace_s;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof + 8, 0, 8 * sizeof(unsigned long long), st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
   int rc = read_status(h, st, P.n_solve_tasks);
+  h->traced_s = h->d_trace_s != nullptr;
   if (h->opt.profile) {
     CU(cudaMemcpy(h->h_prof + 8, h->d_prof + 8, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
     for (int k = 0; k < 4; ++k) h->stats.solve_task_ms[k] = h->h_prof[8 + k] * 1e-6;
@@ -497,6 +539,8 @@ void spchol_default_options(spchol_options* opt) {
   if (opt) spchol::default_options(opt);
 }
 
+const char* spchol_last_cuda_error(void) { return g_cuda_err; }
+
 const char* spchol_strerror(int code) {
   if (code == 0) return "success";
   if (code > 0) return "matrix is not positive definite (the code is the failing permuted column, 1-based)";
@@ -527,6 +571,7 @@ int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, cons
   }
   spchol_handle_t h = new (std::nothrow) spchol_handle_s();
   if (!h) return SPCHOL_ENOMEM;
+  clear_stale_error();
   h->opt = o;
   h->fp32 = (o.precision != SPCHOL_FP64);
   if (cudaGetDevice(&h->device) != cudaSuccess) {
@@ -558,6 +603,7 @@ int spchol_factorize(spchol_handle_t h, const double* values, void* stream) {
   if (!h) return -1;
   if (!values && h->plan.nnz_a > 0) return -2;
   DeviceGuard g(h->device);
+  clear_stale_error();
   cudaStream_t st = (cudaStream_t)stream;
   const bool dev = values && is_device_ptr(values);
   return factorize_impl(h, dev ? values : nullptr, dev ? nullptr : values, st);
@@ -571,6 +617,7 @@ int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stre
   if (!h->factored) return SPCHOL_ESTATE;
   if (nrhs == 0 || h->plan.n == 0) return 0;
   DeviceGuard g(h->device);
+  clear_stale_error();
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->plan.n;
   int rc = ensure_workspace(h, n * nrhs, nrhs);
@@ -657,12 +704,32 @@ int spchol_export_factor(spchol_handle_t h, int64_t* nnz, int64_t* Lp, int64_t* 
   return 0;
 }
 
+int spchol_trace_get(spchol_handle_t h, int which, uint64_t* out, int64_t* count) {
+  if (!h) return -1;
+  if (which != 0 && which != 1) return -2;
+  if (!count) return -4;
+  const int64_t nt = which == 0 ? h->plan.n_factor_tasks : h->plan.n_solve_tasks;
+  if (!out) {
+    *count = nt;
+    return 0;
+  }
+  if (*count < nt) return -4;
+  if (!(which == 0 ? h->traced_f : h->traced_s)) return SPCHOL_ESTATE;
+  DeviceGuard g(h->device);
+  CU(cudaMemcpy(out, which == 0 ? h->d_trace_f : h->d_trace_s, 2 * (size_t)nt * sizeof(uint64_t),
+                cudaMemcpyDeviceToHost));
+  *count = nt;
+  return 0;
+}
+
 int spchol_destroy(spchol_handle_t h) {
   if (!h) return 0;
   DeviceGuard g(h->device);
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
   if (h->d_inv) cudaFree(h->d_inv);
+  if (h->d_trace_f) cudaFree(h->d_trace_f);
+  if (h->d_trace_s) cudaFree(h->d_trace_s);
   if (h->d_Y) cudaFree(h->d_Y);
   if (h->d_B) cudaFree(h->d_B);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
@@ -729,6 +796,7 @@ int spchol_batch_factorize(spchol_handle_t h, const double* const* values, void*
   if (!h || h->batch_count == 0) return -1;
   if (!values) return -2;
   DeviceGuard g(h->device);
+  clear_stale_error();
   cudaStream_t st = (cudaStream_t)stream;
   const int cnt = h->batch_count;
   for (int i = 0; i < cnt; ++i) {

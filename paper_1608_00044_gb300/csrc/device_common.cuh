@@ -48,6 +48,19 @@ __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
+
+// Raise a kernel's dynamic shared-memory limit to the device maximum (host).
+inline cudaError_t raise_smem_limit(const void* fn) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, fn);
+  if (e != cudaSuccess) return e;
+  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
+}
 __device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
 
 }  // namespace spchol

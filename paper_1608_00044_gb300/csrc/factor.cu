@@ -282,6 +282,184 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
   }
 }
 
+// ---------------------------------------------------------------- UPD on tensor cores (FP32 panels)
+// The same update tile computed with tcgen05.mma kind::tf32: A (tile rows, up
+// to 128) and B (segment rows, up to 64 per pass) are staged K-major in shared
+// memory (8-row x 16-byte core matrices, no swizzle), one elected thread issues
+// the MMAs into a TMEM accumulator (128 lanes x 64 columns, allocated once per
+// CTA), the commit arrives on an mbarrier, and the epilogue reads TMEM by warp
+// quadrant and scatter-adds into the target panel.  With split = 1 each operand
+// is also split into a TF32 high part and a TF32 remainder, and three products
+// (hi*hi + hi*lo + lo*hi) recover FP32-level accuracy.
+struct TcState {
+  uint32_t tmem;   // TMEM base address of this CTA's accumulator
+  uint32_t mbar;   // shared address of the MMA-completion mbarrier
+  uint32_t phase;  // parity of the next completion
+};
+
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+// Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance of
+// K-adjacent core matrices, SBO = byte distance of row-adjacent core matrices.
+__device__ __forceinline__ uint64_t kmajor_desc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((saddr >> 4) & 0x3FFF) | ((uint64_t)((lbo >> 4) & 0x3FFF) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFF) << 32) | ((uint64_t)1 << 46);
+}
+
+// Instruction descriptor: FP32 accumulator, TF32 A and B, both K-major, M x N.
+__device__ __forceinline__ uint32_t tf32_idesc(int m, int n) {
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of element (r, k) in a K-major tile whose rows hold kpad fp32 values.
+__device__ __forceinline__ uint32_t kmaj_off(int r, int k, int kpad) {
+  return (uint32_t)((r >> 3) * (kpad * 32) + (k >> 2) * 128 + (r & 7) * 16 + (k & 3) * 4);
+}
+
+constexpr int kTcM = 128;      // MMA rows (tile rows are padded up to it)
+constexpr int kTcN = 64;       // accumulator columns per pass
+constexpr int kTcKmax = 64;    // panel width bound for the tensor-core path
+
+__device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(phase)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
+
+__device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
+                               TcState& tc) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = u.s, t = u.t;
+  if (!skip) {
+    const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, lds = a.pv.ld[s];
+    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
+    const float* Ps = reinterpret_cast<const float*>(a.pool) + a.pv.valoff[s];
+    float* Pt = reinterpret_cast<float*>(a.pool) + a.pv.valoff[t];
+    const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
+    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
+    const int split = a.mma_mode == 2 ? 1 : 0;
+    const int kpad = (ws + 7) & ~7;
+    const int abytes = kTcM * kpad * 4, bbytes = kTcN * kpad * 4;
+    // operand tiles start on a 128-byte boundary of shared memory
+    unsigned char* Ah = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
+    unsigned char* Bh = Ah + abytes;
+    unsigned char* Al = Bh + bbytes;           // remainders (split only)
+    unsigned char* Bl = Al + abytes;
+    int* pos = reinterpret_cast<int*>(Ah + 2 * (abytes + bbytes));
+    int* grow = pos + kTcM;
+    int* gcol = grow + kTcM;
+
+    for (int i = tid; i < u.rowlen; i += blockDim.x) {
+      const int g = Rs[u.row0 + i];
+      int lo = 0, hi = rt;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= rt || Rt[lo] != g) {
+        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+        lo = -1;
+      }
+      pos[i] = lo;
+      grow[i] = g;
+    }
+    // A: tile rows x k (rows >= rowlen and k >= ws are zero)
+    for (int idx = tid; idx < kTcM * kpad; idx += blockDim.x) {
+      const int i = idx % kTcM, k = idx / kTcM;
+      const float v = (i < u.rowlen && k < ws) ? ldcg(Ps + (u.row0 + i) + (size_t)k * lds) : 0.f;
+      const float h = to_tf32(v);
+      *reinterpret_cast<float*>(Ah + kmaj_off(i, k, kpad)) = h;
+      if (split) *reinterpret_cast<float*>(Al + kmaj_off(i, k, kpad)) = to_tf32(v - h);
+    }
+    for (int cb = 0; cb < u.seglen; cb += kTcN) {
+      const int ncol = min(kTcN, u.seglen - cb);
+      const int npad = kTcN;  // the MMA always spans the full accumulator width; unused B rows are zero
+      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
+      for (int idx = tid; idx < npad * kpad; idx += blockDim.x) {
+        const int j = idx % npad, k = idx / npad;
+        const float v = (j < ncol && k < ws) ? ldcg(Ps + (u.seg0 + cb + j) + (size_t)k * lds) : 0.f;
+        const float h = to_tf32(v);
+        *reinterpret_cast<float*>(Bh + kmaj_off(j, k, kpad)) = h;
+        if (split) *reinterpret_cast<float*>(Bl + kmaj_off(j, k, kpad)) = to_tf32(v - h);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t idesc = tf32_idesc(kTcM, npad);
+        const uint32_t sbo = (uint32_t)kpad * 32;
+        const uint32_t ah = smem_addr(Ah), bh = smem_addr(Bh), al = smem_addr(Al), bl = smem_addr(Bl);
+        int first = 1;
+        for (int k0 = 0; k0 < kpad; k0 += 8) {
+          const uint32_t off = (uint32_t)(k0 >> 2) * 128;  // two K-adjacent core matrices per MMA
+          const int nprod = split ? 3 : 1;
+          for (int pr = 0; pr < nprod; ++pr) {
+            const uint32_t aa = (pr == 2) ? al : ah;
+            const uint32_t bb = (pr == 1) ? bl : bh;
+            const uint64_t ad = kmajor_desc(aa + off, 128, sbo);
+            const uint64_t bd = kmajor_desc(bb + off, 128, sbo);
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile("{\n.reg .pred p;\nsetp.ne.u32 p, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tc.tmem),
+                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                         : "memory");
+            first = 0;
+          }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar)
+                     : "memory");
+      }
+      const bool ok = mbar_wait_bounded(tc.mbar, tc.phase);
+      tc.phase ^= 1u;
+      if (!ok && tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // epilogue: warp w reads TMEM lanes 32*(w%4).. (tile rows), columns half (w/4)
+      const int quad = warp & 3, half = warp >> 2;
+      const int row = 32 * quad + lane;
+      for (int c0 = half * 32; c0 < half * 32 + 32; c0 += 16) {
+        uint32_t v[16];
+        const uint32_t taddr = tc.tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(taddr));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (ok && row < u.rowlen && pos[row] >= 0) {
+#pragma unroll
+          for (int q = 0; q < 16; ++q) {
+            const int j = c0 + q;
+            if (j < ncol && grow[row] >= gcol[j])
+              atomicAdd(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -__uint_as_float(v[q]));
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();  // TMEM and the B tile are reused by the next pass / task
+    }
+  }
+  publish_cta_writes();
+  if (tid == 0) {
+    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
+      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+      ring_push_one(q, t);
+    }
+  }
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -290,6 +468,28 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
   const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
   // per-CTA task timing (thread 0 only), flushed once at exit
   unsigned long long busy[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, wait = 0;
+  // tensor-core state (FP32 panels with mma_mode 1 / 2): TMEM accumulator + mbarrier
+  __shared__ __align__(8) uint64_t tc_mbar;
+  __shared__ uint32_t tc_tmem;
+  TcState tc{0u, 0u, 0u};
+  const bool use_tc = sizeof(T) == 4 && a.mma_mode != 0;
+  if (use_tc) {
+    if (threadIdx.x < 32) {
+      asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc_tmem)),
+                   "r"(kTcN)
+                   : "memory");
+      asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(&tc_mbar)), "r"(1) : "memory");
+      asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tc.tmem = tc_tmem;
+    tc.mbar = smem_addr(&tc_mbar);
+  }
   for (;;) {
     uint64_t t0 = 0, t1 = 0;
     if (threadIdx.x == 0) {
@@ -316,10 +516,17 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
       task_trsm<T>(a, s, kt - a.trsm_first[s], smd, sh, skip);
     } else {
       type = 2;
-      task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
+      if (use_tc)
+        task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
+      else
+        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
+      if (a.trace) {
+        a.trace[2 * (size_t)task] = t1;
+        a.trace[2 * (size_t)task + 1] = global_ns();
+      }
       if (a.prof) {
         const unsigned long long d = global_ns() - t1;
 #pragma unroll
@@ -339,6 +546,12 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
     }
     atomicAdd(&a.prof[3], wait);
   }
+  if (use_tc) {
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kTcN) : "memory");
+  }
 }
 
 template <typename T>
@@ -350,17 +563,25 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 
 }  // namespace
 
-size_t factor_smem_bytes(int max_w) {
+size_t factor_smem_bytes(int max_w, int mma_mode) {
   size_t tri = ((size_t)max_w * max_w + max_w) * sizeof(double);
+  if (mma_mode != 0) {
+    const size_t kpad = ((size_t)max_w + 7) & ~size_t(7);
+    const size_t tcb = 2 * (kTcM + kTcN) * kpad * 4 + (2 * kTcM + kTcN) * sizeof(int) + 1024;
+    if (tcb > tri) tri = tcb;
+  }
   size_t upd = (size_t)kUpdKC * (kUpdTileM + kUpdTileN) * sizeof(double) +
                (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
   return tri > upd ? tri : upd;
 }
 
+// The dynamic shared-memory limit is a per-kernel setting shared by every
+// handle, so it is raised once to the device's opt-in maximum and never
+// lowered; each launch then passes its own size.
 cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm) {
   const void* fn = fp32 ? (const void*)factor_kernel<float> : (const void*)factor_kernel<double>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t once[2] = {raise_smem_limit((const void*)factor_kernel<double>), raise_smem_limit((const void*)factor_kernel<float>)};
+  if (once[fp32 ? 1 : 0] != cudaSuccess) return once[fp32 ? 1 : 0];
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
 }
 

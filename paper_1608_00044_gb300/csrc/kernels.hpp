@@ -35,6 +35,7 @@ struct FactorArgs {
   const int32_t* nu;
   const UTask* ut;
   int32_t n_trsm, n_u, ntask, trsm_rows;
+  int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products)
   int32_t* dep_f;      // update tiles still to land in each panel
   int32_t* trsm_left;  // panel-solve tiles still to finish in each panel
   int* ring;
@@ -44,6 +45,7 @@ struct FactorArgs {
   double* inv;         // per panel: L11^{-1} (w x w, column-major, lower part)
   const int64_t* invoff;
   unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts
+  unsigned long long* trace; // optional: per task id, start and end ns
 };
 
 struct SolveArgs {
@@ -67,10 +69,11 @@ struct SolveArgs {
   int64_t ldy;
   int nrhs;
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
+  unsigned long long* trace; // optional: per task id, start and end ns
 };
 
 // factor.cu
-size_t factor_smem_bytes(int max_w);
+size_t factor_smem_bytes(int max_w, int mma_mode);
 cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm);
 cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz,
                             void* pool, cudaStream_t st);

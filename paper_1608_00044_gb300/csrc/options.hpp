@@ -28,10 +28,12 @@ inline void default_options(spchol_options* o) {
 }
 
 inline bool options_valid(const spchol_options& o) {
-  return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_TF32 && o.max_width >= 1 && o.max_width <= 128 &&
+  const bool tc = o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3;
+  return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_TF32X3 && o.max_width >= 1 &&
+         o.max_width <= (tc ? 64 : 128) &&
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
          o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 &&
-         o.profile >= 0 && o.profile <= 1;
+         o.profile >= 0 && o.profile <= 2;
 }
 
 inline PlanParams params_from(const spchol_options& o) {
@@ -39,6 +41,7 @@ inline PlanParams params_from(const spchol_options& o) {
   p.max_width = std::min(std::max(o.max_width, 1), 128);
   p.relax_zeros = std::max(o.relax_zeros, 0);
   p.tile_rows = o.tile_rows > 0 ? o.tile_rows : 64;
+  if (o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3) p.tile_rows = 128;  // one MMA M-tile
   p.trsm_rows = kTrsmTileRows;
   p.solve_rows = kSolveTileRows;
   return p;

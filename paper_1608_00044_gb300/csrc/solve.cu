@@ -251,6 +251,10 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
+      if (a.trace) {
+        a.trace[2 * (size_t)task] = t1;
+        a.trace[2 * (size_t)task + 1] = global_ns();
+      }
       if (a.prof) busy[type] += global_ns() - t1;
     }
     __syncthreads();
@@ -287,10 +291,13 @@ size_t solve_smem_bytes(int max_w) {
   return diag > tile ? diag : tile;
 }
 
+// The dynamic shared-memory limit is a per-kernel setting shared by every
+// handle, so it is raised once to the device's opt-in maximum and never
+// lowered; each launch then passes its own size.
 cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm) {
   const void* fn = fp32 ? (const void*)solve_kernel<float> : (const void*)solve_kernel<double>;
-  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
+  static const cudaError_t once[2] = {raise_smem_limit((const void*)solve_kernel<double>), raise_smem_limit((const void*)solve_kernel<float>)};
+  if (once[fp32 ? 1 : 0] != cudaSuccess) return once[fp32 ? 1 : 0];
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
 }
 

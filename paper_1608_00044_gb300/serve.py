@@ -1,0 +1,260 @@
+"""Continuous-batching request loop for factor/solve requests on one GPU.
+
+Requests arrive over time (factor + solve of a new matrix, or a repeat solve
+on a factor that is already resident).  A fixed number of slots run requests
+concurrently, each slot a host thread with its own CUDA stream; the library
+calls release the GIL, so the persistent kernels of different slots overlap
+on the device.  Each handle's persistent grid is capped (ctas_per_sm) so that
+several launches fit on the GPU at once.  A request is admitted when a slot
+is free and the device bytes of all resident factors plus its own stay within
+the memory budget; least-recently-used idle factors are evicted to make room.
+Latency is measured from arrival to the moment the result is on the host.
+"""
+from __future__ import annotations
+
+import collections
+import dataclasses
+import queue
+import threading
+import time
+
+import numpy as np
+
+from . import spchol
+
+
+@dataclasses.dataclass
+class Request:
+    rid: int
+    arrival: float            # seconds, relative to the start of the run
+    key: str                  # identity of the sparsity pattern (the analysis is shared)
+    vkey: str                 # identity of the values (the factor)
+    make: object              # callable returning (CscLower, perm) for this request's matrix
+    B: np.ndarray             # n x nrhs, Fortran order
+    repeat: bool = False      # True: a repeat solve with a factor that was computed before
+    # filled by the server
+    X: np.ndarray | None = None
+    start: float = 0.0
+    done: float = 0.0
+    rc: int = 0
+    factored: bool = False
+
+
+class _Resident:
+    def __init__(self, handle, footprint):
+        self.h = handle
+        self.footprint = footprint
+        self.vkey = None  # values currently factored in the handle
+        self.lock = threading.Lock()
+        self.last_use = time.perf_counter()
+        self.busy = 0
+
+
+class Server:
+    def __init__(self, slots: int = 4, budget_bytes: int | None = None, ctas_per_sm: int = 1,
+                 precision: int = spchol.FP64, max_width: int = 64, device: int = 0):
+        import torch
+
+        self.torch = torch
+        self.device = device
+        torch.cuda.set_device(device)
+        if budget_bytes is None:
+            free, _ = torch.cuda.mem_get_info(device)
+            budget_bytes = int(0.8 * free)
+        self.budget = budget_bytes
+        self.slots = slots
+        self.opt_kw = dict(precision=precision, max_width=max_width, ctas_per_sm=ctas_per_sm)
+        self.resident: dict[str, _Resident] = collections.OrderedDict()
+        self.used = 0
+        self.mem_cv = threading.Condition()
+        self.factorizations = 0
+        self.peak_used = 0
+
+    # -------------------------------------------------------------- memory
+    def _evict_locked(self, need: int) -> bool:
+        """Free idle resident factors (least recently used first) until `need` fits."""
+        while self.used + need > self.budget:
+            victims = [k for k, r in self.resident.items() if r.busy == 0]
+            if not victims:
+                return False
+            k = min(victims, key=lambda kk: self.resident[kk].last_use)
+            r = self.resident.pop(k)
+            spchol.destroy(r.h)
+            self.used -= r.footprint
+        return True
+
+    def _acquire(self, req: Request, A, perm):
+        """Resident handle of the request's pattern, analyzing it if needed."""
+        with self.mem_cv:
+            r = self.resident.get(req.key)
+            if r is not None:
+                r.busy += 1
+                r.last_use = time.perf_counter()
+                return r, False
+        h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(**self.opt_kw))
+        fp = spchol.stats(h)["footprint_bytes"] + 2 * A.n * max(req.B.shape[1], 1) * 8 * 2
+        with self.mem_cv:
+            while True:
+                r = self.resident.get(req.key)
+                if r is not None:  # another slot created it meanwhile
+                    spchol.destroy(h)
+                    r.busy += 1
+                    return r, False
+                if self._evict_locked(fp):
+                    break
+                self.mem_cv.wait(timeout=0.05)
+            r = _Resident(h, fp)
+            r.busy = 1
+            self.resident[req.key] = r
+            self.used += fp
+            self.peak_used = max(self.peak_used, self.used)
+            return r, True
+
+    def _release(self, r: _Resident):
+        with self.mem_cv:
+            r.busy -= 1
+            r.last_use = time.perf_counter()
+            self.mem_cv.notify_all()
+
+    # -------------------------------------------------------------- request execution
+    def _run_one(self, req: Request, stream, t0: float):
+        torch = self.torch
+        req.start = time.perf_counter() - t0
+        A, perm = req.make()
+        r, fresh = self._acquire(req, A, perm)
+        try:
+            with r.lock:  # one slot at a time per handle
+                with torch.cuda.stream(stream):
+                    if r.vkey != req.vkey:
+                        vals = torch.from_numpy(np.ascontiguousarray(A.values)).cuda(non_blocking=True)
+                        rc = spchol.factorize(r.h, vals, stream=stream)
+                        r.vkey = req.vkey if rc == 0 else None
+                        req.factored = True
+                        with self.mem_cv:
+                            self.factorizations += 1
+                        if rc != 0:
+                            req.rc = rc
+                            return
+                    nrhs = req.B.shape[1]
+                    Bt = torch.from_numpy(np.ascontiguousarray(req.B.T)).cuda(non_blocking=True)
+                    try:
+                        spchol.solve(r.h, Bt, A.n, nrhs, stream=stream)
+                    except spchol.SpcholError as e:
+                        if e.code != spchol.ENOCONV:
+                            raise
+                        req.rc = e.code
+                    req.X = np.asfortranarray(Bt.cpu().numpy().T)
+        finally:
+            self._release(r)
+            req.done = time.perf_counter() - t0
+
+    def run(self, requests: list[Request]) -> list[Request]:
+        """Release requests at their arrival times and serve them with `slots` workers."""
+        torch = self.torch
+        pending: queue.Queue = queue.Queue()
+        t0 = time.perf_counter()
+        errors = []
+
+        def worker():
+            torch.cuda.set_device(self.device)
+            stream = torch.cuda.Stream()
+            while True:
+                req = pending.get()
+                if req is None:
+                    return
+                try:
+                    self._run_one(req, stream, t0)
+                except Exception as e:  # surface to the caller
+                    errors.append(e)
+                    req.rc = -1
+
+        threads = [threading.Thread(target=worker, daemon=True) for _ in range(self.slots)]
+        for th in threads:
+            th.start()
+        for req in sorted(requests, key=lambda q: q.arrival):
+            delay = req.arrival - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            pending.put(req)
+        for _ in threads:
+            pending.put(None)
+        for th in threads:
+            th.join()
+        if errors:
+            raise errors[0]
+        return requests
+
+    def close(self):
+        with self.mem_cv:
+            for r in self.resident.values():
+                spchol.destroy(r.h)
+            self.resident.clear()
+            self.used = 0
+
+
+def latency_summary(reqs: list[Request]) -> dict:
+    lat = np.array([q.done - q.arrival for q in reqs]) * 1e3
+    rep = np.array([q.done - q.arrival for q in reqs if q.repeat]) * 1e3
+    span = max(q.done for q in reqs) - min(q.arrival for q in reqs)
+    out = {"requests": len(reqs), "p50_ms": float(np.percentile(lat, 50)), "p99_ms": float(np.percentile(lat, 99)),
+           "solves_per_s": len(reqs) / span if span > 0 else None}
+    if rep.size:
+        out["repeat_p50_ms"] = float(np.percentile(rep, 50))
+        out["repeat_p99_ms"] = float(np.percentile(rep, 99))
+    return out
+
+
+def make_stream(n_requests: int, rate: float, seed: int = 4321, repeat_frac: float = 0.3, patterns: int = 32,
+                small: bool = False) -> list[Request]:
+    """Poisson stream (rate requests/s; 0 = all at once) of mixed 2D (32^2..256^2) and
+    3D (16^3..48^3) Laplacian / diffusion problems with 1..16 right-hand sides.
+    A fresh request carries new values on one of `patterns` sparsity patterns
+    (a shift of the Laplacian, a new conductivity field of the diffusion) and
+    needs a factorization; `repeat_frac` of the requests repeat a solve with
+    the values of an earlier request, whose factor may still be resident.
+    `small` shrinks the size ranges (used by the tests)."""
+    import gridgen
+
+    rng = np.random.default_rng(seed)
+    t = np.cumsum(rng.exponential(1.0 / rate, n_requests)) if rate > 0 else np.zeros(n_requests)
+    specs = []
+    for i in range(patterns):
+        dim3 = rng.random() < 0.5
+        lap = rng.random() < 0.5
+        if dim3:
+            side = int(rng.integers(6, 13)) if small else int(rng.integers(16, 49))
+        else:
+            side = int(rng.integers(10, 33)) if small else int(rng.integers(32, 257))
+        specs.append((dim3, lap, side))
+
+    def maker(j, v):
+        dim3, lap, side = specs[j]
+
+        def make():
+            if dim3:
+                A = gridgen.laplacian_3d(side, shift=1e-3 * v) if lap else \
+                    gridgen.diffusion_3d_27pt(side, sigma=2.0, seed=1000 * j + v)
+            else:
+                A = gridgen.laplacian_2d(side, shift=1e-3 * v) if lap else \
+                    gridgen.diffusion_2d_5pt(side, sigma=2.0, seed=1000 * j + v)
+            return A, gridgen.geometric_nd(A.dims)
+
+        return make
+
+    reqs, issued = [], []
+    nvals = [0] * patterns
+    for rid in range(n_requests):
+        repeat = bool(issued) and rng.random() < repeat_frac
+        if repeat:
+            j, v = issued[int(rng.integers(0, len(issued)))]
+        else:
+            j = int(rng.integers(0, patterns))
+            v = nvals[j]
+            nvals[j] += 1
+            issued.append((j, v))
+        dim3, lap, side = specs[j]
+        n = side ** 3 if dim3 else side ** 2
+        nrhs = int(rng.integers(1, 17))
+        B = np.asfortranarray(rng.uniform(-1, 1, (nrhs, n)).T)
+        reqs.append(Request(rid, float(t[rid]), f"p{j}", f"p{j}v{v}", maker(j, v), B, repeat=repeat))
+    return reqs

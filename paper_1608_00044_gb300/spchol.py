@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspchol.so")
 
-FP64, FP32, TF32 = 0, 1, 2
+FP64, FP32, TF32, TF32X3 = 0, 1, 2, 3
 OK = 0
 ENOMEM, ETIMEOUT, ESTATE, ENOCONV, ECUDA, EINTERNAL = -1001, -1002, -1003, -1004, -1005, -1006
 
@@ -74,7 +74,10 @@ class Stats(ctypes.Structure):
 class SpcholError(RuntimeError):
     def __init__(self, code: int, where: str):
         self.code = int(code)
-        super().__init__(f"{where}: {strerror(code)} (code {code})")
+        detail = ""
+        if code in (ECUDA, ENOMEM):
+            detail = " [" + load().spchol_last_cuda_error().decode() + "]"
+        super().__init__(f"{where}: {strerror(code)} (code {code}){detail}")
 
 
 _lib = None
@@ -89,8 +92,10 @@ SIGNATURES = [
     ("spchol_solve", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     ("spchol_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     ("spchol_export_factor", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
+    ("spchol_trace_get", ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_i64)]),
     ("spchol_destroy", ctypes.c_int, [_vp]),
     ("spchol_strerror", ctypes.c_char_p, [ctypes.c_int]),
+    ("spchol_last_cuda_error", ctypes.c_char_p, []),
     ("spchol_batch_analyze", ctypes.c_int, [ctypes.c_int, _vp, _vp, _vp, _vp, ctypes.POINTER(Options),
                                             ctypes.POINTER(_vp)]),
     ("spchol_batch_factorize", ctypes.c_int, [_vp, _vp, _vp]),
@@ -242,6 +247,20 @@ def export_factor(h):
     if rc != 0:
         raise SpcholError(rc, "spchol_export_factor")
     return Lp, Li[: nnz.value], Lx[: nnz.value], perm
+
+
+def trace_get(h, which: int) -> np.ndarray:
+    """(ntask, 2) start/end device-clock ns of each task of the last factorization (0) or solve (1)."""
+    lib = load()
+    cnt = ctypes.c_int64(0)
+    rc = lib.spchol_trace_get(h, which, None, ctypes.byref(cnt))
+    if rc != 0:
+        raise SpcholError(rc, "spchol_trace_get")
+    out = np.empty((cnt.value, 2), np.uint64)
+    rc = lib.spchol_trace_get(h, which, out.ctypes.data, ctypes.byref(cnt))
+    if rc != 0:
+        raise SpcholError(rc, "spchol_trace_get")
+    return out
 
 
 def final_perm(h) -> np.ndarray:

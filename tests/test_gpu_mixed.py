@@ -75,3 +75,43 @@ def test_mixed_batch():
     for M, B, X in zip(mats, Bs, Xs):
         assert oracle.berr(M, X, B) <= BERR_MIXED
     spchol.destroy(h)
+
+
+def _l_rel_diff(h, A):
+    import scipy.sparse as sp
+
+    Lp, Li, Lx, perm = spchol.export_factor(h)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    op, oi, ox = f.L()
+    Lg = sp.csc_matrix((Lx, Li, Lp), shape=(A.n, A.n))
+    Lo = sp.csc_matrix((ox, oi, op), shape=(A.n, A.n))
+    return abs(Lg - Lo).max() / abs(Lo).max()
+
+
+@pytest.mark.parametrize("prec,l_tol", [(spchol.FP32, 1e-5), (spchol.TF32X3, 1e-5), (spchol.TF32, 3e-2)])
+@pytest.mark.parametrize("name", ["lap3d_12", "diff3d_10", "lap2d_40"])
+def test_tensor_core_factor_accuracy(prec, l_tol, name):
+    """The factor itself against the oracle's FP64 L: FP32 and split-TF32 updates
+    keep FP32-level accuracy (unit roundoff 6e-8, times a modest growth), plain
+    TF32 (unit roundoff 4.9e-4) a few 1e-3.  Refinement then reaches 1e-12."""
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 2, seed=9)
+    rc, X, st, h = gpu_factor_solve(A, perm, B, precision=prec, ir_max_iter=40)
+    assert rc == 0
+    d = _l_rel_diff(h, A)
+    assert d <= l_tol, d
+    assert oracle.berr(A, X, B) <= BERR_MIXED
+    spchol.destroy(h)
+
+
+@pytest.mark.parametrize("W", [7, 16, 33, 64])
+def test_tensor_core_ragged_widths(W):
+    """Panel widths that are not multiples of the MMA K step (8) and segments that
+    are not multiples of 16 columns exercise the zero padding of the operand tiles."""
+    A, perm, b = gridgen.workload("diff3d_11")
+    rc, X, st, h = gpu_factor_solve(A, perm, b, precision=spchol.TF32X3, max_width=W)
+    assert rc == 0
+    assert _l_rel_diff(h, A) <= 1e-5
+    assert oracle.berr(A, X, b) <= BERR_MIXED
+    spchol.destroy(h)

@@ -258,3 +258,23 @@ def test_full_size_lap3d_64_sampled():
             worst = max(worst, abs(v - Bp[i, j]))
     assert worst <= 1e-12 * abs(A.values).max()
     spchol.destroy(h)
+
+
+def test_handles_with_different_panel_widths_coexist():
+    """A handle with wide panels (large shared-memory tiles) stays usable after
+    another handle with narrow panels has been analyzed: the kernels' shared
+    memory limits are not owned by one handle."""
+    rng = np.random.default_rng(3)
+    G = rng.standard_normal((120, 120))
+    wide = _csc(G @ G.T + 120 * np.eye(120))
+    narrow, nperm, nb = gridgen.workload("lap2d_16")
+    hw = spchol.analyze(wide.n, wide.colptr, wide.rowind, None, spchol.default_options(max_width=128))
+    hn = spchol.analyze(narrow.n, narrow.colptr, narrow.rowind, nperm, spchol.default_options(max_width=4))
+    assert spchol.factorize(hw, wide.values) == 0
+    assert spchol.factorize(hn, narrow.values) == 0
+    B = gridgen.rhs_uniform(wide.n, 2, seed=1)
+    X = B.copy(order="F")
+    spchol.solve(hw, X, wide.n, 2)
+    assert oracle.berr(wide, X, B) <= BERR_FP64
+    spchol.destroy(hw)
+    spchol.destroy(hn)
