@@ -66,11 +66,14 @@ extern "C" {
 #define SPCHOL_TF32 2  /* as FP32, update GEMMs on TF32 tensor cores (tcgen05.mma kind::tf32) */
 #define SPCHOL_TF32X3 3 /* as TF32, each operand split into a TF32 head and tail, three products per
                            tile: FP32-level accuracy on the tensor cores */
+#define SPCHOL_FP64_TC 4 /* FP64 panels and FP64 result; the update GEMMs run on BF16 tensor cores
+                            (tcgen05.mma kind::f16) on an exact 7-way 8-bit split of each FP64 row
+                            (Ozaki-style error-free transformation), recombined exactly in integers */
 
 typedef struct spchol_handle_s* spchol_handle_t;
 
 typedef struct spchol_options {
-  int precision;          /* SPCHOL_FP64 (default), SPCHOL_FP32, SPCHOL_TF32, SPCHOL_TF32X3 */
+  int precision;          /* SPCHOL_FP64 (default), SPCHOL_FP32, SPCHOL_TF32, SPCHOL_TF32X3, SPCHOL_FP64_TC */
   int max_width;          /* W: supernode panels are at most W columns (Section III-B caps at 150);
                              1..128 (1..64 with the tensor-core precisions), default 64 */
   int relax_zeros;        /* amalgamation: a child supernode is merged into its parent when every

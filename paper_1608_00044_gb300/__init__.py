@@ -10,6 +10,7 @@ from .spchol import (
     FP64,
     TF32,
     TF32X3,
+    FP64_TC,
     SparseCholesky,
     SpcholError,
     analyze,
@@ -32,6 +33,7 @@ __all__ = [
     "FP64",
     "TF32",
     "TF32X3",
+    "FP64_TC",
     "SparseCholesky",
     "SpcholError",
     "analyze",

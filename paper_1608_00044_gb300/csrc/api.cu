@@ -61,6 +61,7 @@ struct spchol_handle_s {
   int32_t *d_fcol = nullptr, *d_nrows = nullptr, *d_ld = nullptr, *d_rows = nullptr, *d_parent = nullptr;
   int64_t *d_rowoff = nullptr, *d_valoff = nullptr, *d_adest = nullptr;
   int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
+  int32_t* d_trsm_rows = nullptr;
   UTask* d_ut = nullptr;
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
   int32_t *d_fseeds = nullptr;
@@ -77,6 +78,9 @@ struct spchol_handle_s {
   void* d_pool = nullptr;
   size_t pool_bytes = 0;
   double* d_inv = nullptr;  // diagonal-block inverses (FP64)
+  uint16_t* d_slices = nullptr;  // FP64_TC: BF16 digit slices of the rows below each diagonal block
+  int32_t* d_rexp = nullptr;     // FP64_TC: row exponents
+  int64_t* d_sliceoff = nullptr;
   int64_t* d_invoff = nullptr;
   double* d_Y = nullptr;
   double* d_B = nullptr;
@@ -134,7 +138,7 @@ int upload(spchol_handle_t h, V* dst, const std::vector<V>& src) {
 }
 
 int mma_mode_of(int precision) {
-  return precision == SPCHOL_TF32 ? 1 : precision == SPCHOL_TF32X3 ? 2 : 0;
+  return precision == SPCHOL_TF32 ? 1 : precision == SPCHOL_TF32X3 ? 2 : precision == SPCHOL_FP64_TC ? 3 : 0;
 }
 
 int setup_device(spchol_handle_t h) {
@@ -145,7 +149,10 @@ int setup_device(spchol_handle_t h) {
   auto r64 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int64_t)); };
   size_t o_fcol = r32(ns + 1), o_nrows = r32(ns), o_ld = r32(ns), o_rows = r32(P.rows.size()), o_parent = r32(ns);
   size_t o_rowoff = r64(ns + 1), o_valoff = r64(ns + 1), o_adest = r64(P.a_dest.size()), o_invoff = r64(ns + 1);
+  const bool oz = h->opt.precision == SPCHOL_FP64_TC;
+  size_t o_sliceoff = r64(ns + 1), o_rexp = oz ? r32(P.rows.size()) : 0;
   size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
+  size_t o_trows = r32(ns);
   size_t o_ut = A.reserve(std::max<size_t>(P.ut.size(), 1) * sizeof(UTask));
   size_t o_depi = r32(ns), o_trsi = r32(ns), o_dep = r32(ns), o_trs = r32(ns);
   std::vector<int32_t> fseeds;
@@ -213,9 +220,12 @@ int setup_device(spchol_handle_t h) {
   h->d_valoff = (int64_t*)(b + o_valoff);
   h->d_adest = (int64_t*)(b + o_adest);
   h->d_invoff = (int64_t*)(b + o_invoff);
+  h->d_sliceoff = (int64_t*)(b + o_sliceoff);
+  if (oz) h->d_rexp = (int32_t*)(b + o_rexp);
   h->d_trsm_first = (int32_t*)(b + o_tf);
   h->d_ntrsm = (int32_t*)(b + o_nt);
   h->d_trsm_sn = (int32_t*)(b + o_tsn);
+  h->d_trsm_rows = (int32_t*)(b + o_trows);
   h->d_u_first = (int32_t*)(b + o_uf);
   h->d_nu = (int32_t*)(b + o_nu);
   h->d_ut = (UTask*)(b + o_ut);
@@ -257,9 +267,10 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_ld, P.ld)) || (rc = upload(h, h->d_rows, P.rows)) ||
       (rc = upload(h, h->d_parent, P.parent)) || (rc = upload(h, h->d_rowoff, P.rowoff)) ||
       (rc = upload(h, h->d_valoff, P.valoff)) || (rc = upload(h, h->d_adest, P.a_dest)) ||
-      (rc = upload(h, h->d_invoff, P.invoff)) ||
+      (rc = upload(h, h->d_invoff, P.invoff)) || (rc = upload(h, h->d_sliceoff, P.sliceoff)) ||
       (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
       (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
+      (rc = upload(h, h->d_trsm_rows, P.trsm_rows)) ||
       (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_ut, P.ut)) ||
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
@@ -272,6 +283,7 @@ int setup_device(spchol_handle_t h) {
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
   CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
+  if (oz) CU(cudaMalloc(&h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256)));
   CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
   CU(cudaMallocHost(&h->h_prof, 16 * sizeof(unsigned long long)));
   if (h->opt.profile == 2) {
@@ -285,9 +297,16 @@ int setup_device(spchol_handle_t h) {
   CU(cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, dev));
   const int wmax = std::max<int>(P.max_w, 1);
   h->smem_factor = factor_smem_bytes(wmax, mma_mode_of(h->opt.precision));
+  if (mma_mode_of(h->opt.precision) == 3) {
+    // each CTA of this mode owns all 512 TMEM columns of its SM: request more
+    // than half of the SM's shared memory so that two CTAs can never share one
+    int smem_sm = 0;
+    CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
+    h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 2 + 1024);
+  }
   h->smem_solve = solve_smem_bytes(wmax);
   int bf = 0, bs = 0;
-  CU(factor_configure(h->fp32, h->smem_factor, &bf));
+  CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), h->smem_factor, &bf));
   CU(solve_configure(h->fp32, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
   if (h->opt.ctas_per_sm > 0) {
@@ -296,7 +315,8 @@ int setup_device(spchol_handle_t h) {
   }
   h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
-  h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double));
+  h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
+                                       (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0));
   h->stats.grid_factor = h->grid_factor;
   h->stats.grid_solve = h->grid_solve;
   return 0;
@@ -395,6 +415,7 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     a.trsm_first = h->d_trsm_first;
     a.ntrsm = h->d_ntrsm;
     a.trsm_sn = h->d_trsm_sn;
+    a.trsm_rows_of = h->d_trsm_rows;
     a.u_first = h->d_u_first;
     a.nu = h->d_nu;
     a.ut = h->d_ut;
@@ -403,6 +424,10 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     a.ntask = P.n_factor_tasks;
     a.trsm_rows = P.params.trsm_rows;
     a.mma_mode = mma_mode_of(h->opt.precision);
+    a.slices = h->d_slices;
+    a.sliceoff = h->d_sliceoff;
+    a.rexp = h->d_rexp;
+    a.tc_min_width = P.params.tc_min_width;
     a.dep_f = h->d_dep;
     a.trsm_left = h->d_trsm_left;
     a.ring = h->d_ring;
@@ -573,7 +598,7 @@ int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, cons
   if (!h) return SPCHOL_ENOMEM;
   clear_stale_error();
   h->opt = o;
-  h->fp32 = (o.precision != SPCHOL_FP64);
+  h->fp32 = (o.precision == SPCHOL_FP32 || o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3);
   if (cudaGetDevice(&h->device) != cudaSuccess) {
     delete h;
     return SPCHOL_ECUDA;
@@ -728,6 +753,7 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
   if (h->d_inv) cudaFree(h->d_inv);
+  if (h->d_slices) cudaFree(h->d_slices);
   if (h->d_trace_f) cudaFree(h->d_trace_f);
   if (h->d_trace_s) cudaFree(h->d_trace_s);
   if (h->d_Y) cudaFree(h->d_Y);

@@ -46,21 +46,16 @@ __device__ __forceinline__ uint64_t global_ns() {
 // from L2, never from a possibly stale L1 line.
 __device__ __forceinline__ double ldcg(const double* p) { return __ldcg(p); }
 __device__ __forceinline__ float ldcg(const float* p) { return __ldcg(p); }
+__device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
 
-// Raise a kernel's dynamic shared-memory limit to the device maximum (host).
-inline cudaError_t raise_smem_limit(const void* fn) {
-  int dev = 0, optin = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
-  if (e != cudaSuccess) return e;
-  cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, fn);
-  if (e != cudaSuccess) return e;
-  return cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, optin - (int)fa.sharedSizeBytes);
-}
+// Raise a kernel's dynamic shared-memory limit to at least `need` bytes (host).
+// The limit is a per-kernel setting shared by every handle of the process; it
+// only ever grows, to the largest size any handle has needed, so a launch
+// never finds it lowered by another handle.  (Raising it straight to the
+// device maximum would lower the occupancy the runtime reports.)
+cudaError_t ensure_smem_limit(const void* fn, size_t need);
 __device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
 
 }  // namespace spchol

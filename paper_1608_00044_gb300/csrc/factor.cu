@@ -14,6 +14,8 @@
 #include <climits>
 #include <cstdint>
 
+#include <cuda_bf16.h>
+
 #include "device_common.cuh"
 #include "kernels.hpp"
 #include "sched.cuh"
@@ -49,6 +51,11 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
     }
     if (tid == 0) sh.flag = 0;
     __syncthreads();
+    // Right-looking (Algorithm 1) on the block in shared memory.  Thread
+    // (tx, ty) = (tid % 64, tid / 64) updates rows j+1+tx (+64...) of the
+    // trailing triangle in the columns j+1+ty, j+5+ty, ...: independent FMAs,
+    // no index division.
+    const int tx = tid & 63, ty = tid >> 6, nty = nt >> 6;
     for (int j = 0; j < w; ++j) {
       if (tid == 0) {
         const double d = sm[j + j * w];
@@ -64,10 +71,9 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
       const double ljj = sm[j + j * w];
       for (int i = j + 1 + tid; i < w; i += nt) sm[i + j * w] = sm[i + j * w] / ljj;
       __syncthreads();
-      const int m = w - j - 1;
-      for (int idx = tid; idx < m * m; idx += nt) {
-        const int i = j + 1 + idx % m, k = j + 1 + idx / m;
-        if (i >= k) sm[i + k * w] -= sm[i + j * w] * sm[k + j * w];
+      for (int i = j + 1 + tx; i < w; i += 64) {
+        const double lij = sm[i + j * w];
+        for (int k = j + 1 + ty; k <= i; k += nty) sm[i + k * w] -= lij * sm[k + j * w];
       }
       __syncthreads();
     }
@@ -104,16 +110,81 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
   ring_push_range(q, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
 }
 
+// ---------------------------------------------------------------- FP64 operand slicing
+// Error-free splitting of a row of L for the BF16 tensor cores (the splitting
+// step of Ozaki, Ogita, Oishi and Rump, "Error-free transformations of matrix
+// multiplication by using fast routines of matrix multiplication", Numer.
+// Algorithms 2012).  With e the smallest integer such that every |x_k| of the
+// row is below 2^e, x_k * 2^(56-e) is written as a 56-bit fixed-point integer
+// q_k (truncated below 2^(e-56), a relative perturbation of the row of at most
+// 2^-56) and cut into kSlices 8-bit digits; digit p carries weight
+// 2^(e - 8(p+1)).  Each digit, with the sign of x_k, is an integer in
+// [-255, 255] and is exact in BF16.  Products of two digit matrices summed over
+// k <= 64 stay below 2^22 and are exact in the FP32 accumulator.
+__device__ __forceinline__ int row_exponent_bits(const double* Pi, int w, int ld) {
+  int emax = 0;
+  for (int k = 0; k < w; ++k) {
+    const int ex = (int)((__double_as_longlong(ldcg(Pi + (size_t)k * ld)) >> 52) & 0x7FF);
+    emax = max(emax, ex);
+  }
+  return emax;  // 0: the row is zero (or denormal)
+}
+
+__device__ __forceinline__ unsigned long long fixed56(double x, int e, bool& neg) {
+  const unsigned long long bits = (unsigned long long)__double_as_longlong(x);
+  neg = (bits >> 63) != 0;
+  const int ex = (int)((bits >> 52) & 0x7FF);
+  if (ex == 0) return 0ull;
+  const unsigned long long mant = (bits & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+  const int sh = ex - 1019 - e;  // q = mant * 2^sh < 2^56
+  if (sh >= 0) return mant << sh;
+  return (-sh < 64) ? (mant >> (-sh)) : 0ull;
+}
+
+__device__ __forceinline__ uint32_t bf16_digit(unsigned long long q, int p, bool neg) {
+  const int d = (int)((q >> (56 - kSliceBits * (p + 1))) & 0xFF);
+  return (uint32_t)__bfloat16_as_ushort(__float2bfloat16_rn((float)(neg ? -d : d)));
+}
+
+// Slice one row (Pi[k * ld], k < w) into the panel's slice block: slice p of
+// below-row ib at sl[(p * nb + ib) * kpad + k], zero for k >= w.
+__device__ void slice_row(const double* Pi, int w, int ld, int kpad, int nb, int ib, uint16_t* sl, int32_t* rexp) {
+  const int emax = row_exponent_bits(Pi, w, ld);
+  const int e = emax ? emax - 1022 : 0;
+  *rexp = e;
+  for (int k0 = 0; k0 < kpad; k0 += 8) {
+    uint32_t packed[kSlices][4];
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) packed[p][c] = 0u;
+#pragma unroll
+    for (int c = 0; c < 8; ++c) {
+      const int k = k0 + c;
+      bool neg = false;
+      const unsigned long long q = (k < w && emax) ? fixed56(ldcg(Pi + (size_t)k * ld), e, neg) : 0ull;
+#pragma unroll
+      for (int p = 0; p < kSlices; ++p) packed[p][c >> 1] |= bf16_digit(q, p, neg) << (16 * (c & 1));
+    }
+#pragma unroll
+    for (int p = 0; p < kSlices; ++p) {
+      uint4 v = make_uint4(packed[p][0], packed[p][1], packed[p][2], packed[p][3]);
+      *reinterpret_cast<uint4*>(sl + ((size_t)p * nb + ib) * kpad + k0) = v;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- TRSM(s, k)
 // Arithmetic in the panel's type: FP64 panels solve in FP64, FP32 panels (the
 // mixed-precision modes) in FP32.
-template <typename T>
+template <typename T, int MODE>
 __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, FactorShared& sh, bool skip) {
   using ct = T;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
-  const int row0 = w + k * a.trsm_rows;
-  const int cnt = min(a.trsm_rows, r - row0);
+  const int tr = a.trsm_rows_of[s];
+  const int row0 = w + k * tr;
+  const int cnt = min(tr, r - row0);
   T* P = panel_ptr<T>(a, s);
   ct* sm = reinterpret_cast<ct*>(smd);
   (void)f;
@@ -145,6 +216,13 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
             x[c] = x[c] / sm[(jb + c) + (jb + c) * w];
             Pi[(size_t)(jb + c) * ld] = (T)x[c];
           }
+        }
+      }
+      if constexpr (sizeof(T) == 8 && MODE == 3) {
+        if (w >= a.tc_min_width) {
+          const int kpad = (w + 15) & ~15, nbel = r - w, ib = row0 + rr - w;
+          slice_row(reinterpret_cast<const double*>(Pi), w, ld, kpad, nbel, ib, a.slices + a.sliceoff[s],
+                    a.rexp + a.pv.rowoff[s] + row0 + rr);
         }
       }
     }
@@ -460,8 +538,198 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
   }
 }
 
-template <typename T>
-__global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
+// ---------------------------------------------------------------- UPD, FP64 on BF16 tensor cores
+// C = A B^T with A, B given by their kSlices digit matrices (see slice_row):
+// C_ij = 2^(e_i + e_j) sum_{p,q} 2^(-8(p+q+2)) (A_p B_q^T)_ij.  The products
+// with p + q <= kSlices - 1 are kept (the dropped ones weigh below 2^-64 of
+// the leading one); products of equal p + q share one TMEM accumulator
+// (group d = p + q, 64 columns each), in which the integer sums stay exact
+// for d <= 3 and round at most at 2^-56 relative beyond.  The epilogue
+// combines the seven group values per entry exactly in two 64-bit integers,
+// converts once to FP64 and scales by 2^(e_i + e_j).
+// The double nearest to t * 2^k for a 128-bit integer t, with integer
+// operations only (round to nearest, ties to even; no FP64 pipe use).
+__device__ __forceinline__ double fixed128_to_double(__int128 t, int k) {
+  if (t == 0) return 0.0;
+  const bool neg = t < 0;
+  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
+  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
+  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  unsigned long long m;
+  if (msb <= 52) {
+    m = lo << (52 - msb);
+  } else {
+    const int sh = msb - 52;
+    m = (unsigned long long)(u >> sh);
+    const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
+    const unsigned __int128 halfw = (unsigned __int128)1 << (sh - 1);
+    if (rem > halfw || (rem == halfw && (m & 1ull))) {
+      ++m;
+      if (m >> 53) {
+        m >>= 1;
+        ++msb;
+      }
+    }
+  }
+  const int be = msb + k + 1023;  // biased exponent of m 2^(msb - 52) 2^k
+  if (be <= 0 || be >= 2047) {
+    const double r = ldexp((double)m, msb - 52 + k);  // subnormal / overflow: outside the path's range
+    return neg ? -r : r;
+  }
+  const unsigned long long bits =
+      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
+  return __longlong_as_double((long long)bits);
+}
+
+constexpr int kOzM = 128, kOzN = 64;
+constexpr int kOzCols = 512;  // TMEM columns: kSlices groups x 64, rounded to a power of two
+
+__device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
+                               TcState& tc) {
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int s = u.s, t = u.t;
+  if (!skip) {
+    const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, rs = a.pv.nrows[s];
+    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
+    double* Pt = reinterpret_cast<double*>(a.pool) + a.pv.valoff[t];
+    const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
+    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
+    const int32_t* ex = a.rexp + a.pv.rowoff[s];
+    const int kpad = (ws + 15) & ~15, nb = rs - ws;
+    const uint16_t* sl = a.slices + a.sliceoff[s];
+    const int arow = kOzM * kpad * 2, brow = kOzN * kpad * 2;  // bytes of one slice tile
+    unsigned char* A0 = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
+    unsigned char* B0 = A0 + kSlices * arow;
+    int* pos = reinterpret_cast<int*>(B0 + kSlices * brow);
+    int* grow = pos + kOzM;
+    int* gcol = grow + kOzM;
+    int* ea = gcol + kOzN;
+    int* eb = ea + kOzM;
+    const uint32_t sbo = (uint32_t)kpad * 16;  // 8 rows x (kpad bf16) bytes
+    const int chunks = kpad / 8;               // 16-byte chunks per row
+
+    for (int i = tid; i < u.rowlen; i += blockDim.x) {
+      const int g = Rs[u.row0 + i];
+      int lo = 0, hi = rt;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
+      }
+      if (lo >= rt || Rt[lo] != g) {
+        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+        lo = -1;
+      }
+      pos[i] = lo;
+      grow[i] = g;
+      ea[i] = ldcg(ex + u.row0 + i);
+    }
+    // A digits: kSlices x rowlen rows x kpad, K-major core matrices (8 rows x
+    // 16 bytes).  Rows past rowlen are left as they are: they only feed rows
+    // of the product that are never scattered.  Columns past ws are zero in
+    // the slices themselves.
+    for (int pr = tid; pr < kSlices * u.rowlen; pr += blockDim.x) {
+      const int p = pr / u.rowlen, r = pr - p * u.rowlen;
+      const uint4* src = reinterpret_cast<const uint4*>(sl + ((size_t)p * nb + (u.row0 - ws + r)) * kpad);
+      unsigned char* dst = A0 + p * arow + (r >> 3) * sbo + (r & 7) * 16;
+      for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(dst + c * 128) = __ldcg(src + c);
+    }
+    for (int cb = 0; cb < u.seglen; cb += kOzN) {
+      const int ncol = min(kOzN, u.seglen - cb);
+      for (int j = tid; j < ncol; j += blockDim.x) {
+        gcol[j] = Rs[u.seg0 + cb + j];
+        eb[j] = ldcg(ex + u.seg0 + cb + j);
+      }
+      for (int pr = tid; pr < kSlices * ncol; pr += blockDim.x) {
+        const int p = pr / ncol, r = pr - p * ncol;
+        const uint4* src = reinterpret_cast<const uint4*>(sl + ((size_t)p * nb + (u.seg0 + cb - ws + r)) * kpad);
+        unsigned char* dst = B0 + p * brow + (r >> 3) * sbo + (r & 7) * 16;
+        for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(dst + c * 128) = __ldcg(src + c);
+      }
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      if (tid == 0) {
+        const uint32_t idesc = bf16_idesc(kOzM, kOzN);
+        const uint32_t a0 = smem_addr(A0), b0 = smem_addr(B0);
+        for (int p = 0; p < kSlices; ++p)
+          for (int q = 0; p + q < kSlices; ++q) {
+            const uint32_t dcol = tc.tmem + (uint32_t)((p + q) * kOzN);
+            for (int k0 = 0; k0 < kpad; k0 += 16) {
+              const uint32_t off = (uint32_t)(k0 >> 3) * 128;  // 16 bf16 = two K-adjacent core matrices
+              const uint64_t ad = kmajor_desc(a0 + p * arow + off, 128, sbo);
+              const uint64_t bd = kmajor_desc(b0 + q * brow + off, 128, sbo);
+              const uint32_t acc = (p == 0 && k0 == 0) ? 0u : 1u;  // first product of group p+q
+              asm volatile("{\n.reg .pred pp;\nsetp.ne.u32 pp, %4, 0;\n"
+                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}" ::"r"(dcol),
+                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                           : "memory");
+            }
+          }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar)
+                     : "memory");
+      }
+      const bool ok = mbar_wait_bounded(tc.mbar, tc.phase);
+      tc.phase ^= 1u;
+      if (!ok && tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      // Epilogue: warp w reads TMEM lanes 32*(w%4).. (tile rows) and a column
+      // half; warps whose rows or columns are all unused skip (tcgen05.ld is
+      // warp-collective, so the condition is warp-uniform).
+      const int quad = warp & 3, half = warp >> 2;
+      const int row = 32 * quad + lane;
+      if (32 * quad < u.rowlen) {
+        for (int c0 = half * 32; c0 < half * 32 + 32 && c0 < ncol; c0 += 8) {
+          uint32_t v[kSlices][8];
+#pragma unroll
+          for (int d = 0; d < kSlices; ++d) {
+            const uint32_t taddr = tc.tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)(d * kOzN + c0);
+            asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                         : "=r"(v[d][0]), "=r"(v[d][1]), "=r"(v[d][2]), "=r"(v[d][3]), "=r"(v[d][4]),
+                           "=r"(v[d][5]), "=r"(v[d][6]), "=r"(v[d][7])
+                         : "r"(taddr));
+          }
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+          if (ok && row < u.rowlen && pos[row] >= 0) {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) {
+              const int j = c0 + q;
+              if (j < ncol && grow[row] >= gcol[j]) {
+                // t = sum_d v_d 2^(8 (6 - d)) exactly; C = t 2^(e_i + e_j - 64)
+                __int128 acc = 0;
+#pragma unroll
+                for (int d = 0; d < kSlices; ++d) acc = acc * 256 + (__int128)__float2ll_rn(__uint_as_float(v[d][q]));
+                const double c = fixed128_to_double(acc, ea[row] + eb[j] - 64);
+                red_add(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -c);
+              }
+            }
+          }
+        }
+      }
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncthreads();
+    }
+  }
+  publish_cta_writes();
+  if (tid == 0) {
+    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
+      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+      ring_push_one(q, t);
+    }
+  }
+}
+
+// MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
+// panels, split or not), 3 = BF16 tensor cores on split FP64 operands.
+// At least four CTAs per SM (64 registers a thread) for the CUDA-core and TF32
+// modes, whose tasks hide latency across CTAs; the BF16-split mode owns the
+// whole SM (all TMEM columns) with one CTA.
+template <typename T, int MODE>
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
@@ -472,11 +740,12 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
   TcState tc{0u, 0u, 0u};
-  const bool use_tc = sizeof(T) == 4 && a.mma_mode != 0;
+  constexpr bool use_tc = MODE != 0;
+  constexpr uint32_t tmem_cols = MODE == 3 ? kOzCols : kTcN;
   if (use_tc) {
     if (threadIdx.x < 32) {
       asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_addr(&tc_tmem)),
-                   "r"(kTcN)
+                   "r"(tmem_cols)
                    : "memory");
       asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
     }
@@ -513,10 +782,17 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
       type = 1;
       const int kt = task - a.pv.ns;
       const int s = a.trsm_sn[kt];
-      task_trsm<T>(a, s, kt - a.trsm_first[s], smd, sh, skip);
+      task_trsm<T, MODE>(a, s, kt - a.trsm_first[s], smd, sh, skip);
     } else {
       type = 2;
-      if (use_tc)
+      if constexpr (MODE == 3) {
+        const UTask u = a.ut[task - a.pv.ns - a.n_trsm];
+        if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width)
+          task_update_oz(a, u, smem_raw, sh, skip, tc);
+        else
+          task_update<T>(a, u, smem_raw, sh, skip);
+      }
+      else if constexpr (MODE == 1)
         task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
       else
         task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
@@ -550,7 +826,7 @@ __global__ void __launch_bounds__(kFactorThreads) factor_kernel(FactorArgs a) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x < 32)
-      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(kTcN) : "memory");
+      asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tc.tmem), "r"(tmem_cols) : "memory");
   }
 }
 
@@ -565,7 +841,11 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {
   size_t tri = ((size_t)max_w * max_w + max_w) * sizeof(double);
-  if (mma_mode != 0) {
+  if (mma_mode == 3) {
+    const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);
+    const size_t oz = (size_t)kSlices * (kOzM + kOzN) * kpad * 2 + (3 * kOzM + 2 * kOzN) * sizeof(int) + 1024;
+    if (oz > tri) tri = oz;
+  } else if (mma_mode != 0) {
     const size_t kpad = ((size_t)max_w + 7) & ~size_t(7);
     const size_t tcb = 2 * (kTcM + kTcN) * kpad * 4 + (2 * kTcM + kTcN) * sizeof(int) + 1024;
     if (tcb > tri) tri = tcb;
@@ -575,13 +855,15 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
   return tri > upd ? tri : upd;
 }
 
-// The dynamic shared-memory limit is a per-kernel setting shared by every
-// handle, so it is raised once to the device's opt-in maximum and never
-// lowered; each launch then passes its own size.
-cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm) {
-  const void* fn = fp32 ? (const void*)factor_kernel<float> : (const void*)factor_kernel<double>;
-  static const cudaError_t once[2] = {raise_smem_limit((const void*)factor_kernel<double>), raise_smem_limit((const void*)factor_kernel<float>)};
-  if (once[fp32 ? 1 : 0] != cudaSuccess) return once[fp32 ? 1 : 0];
+static const void* factor_fn(bool fp32, int mma_mode) {
+  if (fp32) return mma_mode == 0 ? (const void*)factor_kernel<float, 0> : (const void*)factor_kernel<float, 1>;
+  return mma_mode == 3 ? (const void*)factor_kernel<double, 3> : (const void*)factor_kernel<double, 0>;
+}
+
+cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_per_sm) {
+  const void* fn = factor_fn(fp32, mma_mode);
+  cudaError_t e = ensure_smem_limit(fn, smem);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
 }
 
@@ -598,10 +880,14 @@ cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest
 }
 
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st) {
-  if (fp32)
-    factor_kernel<float><<<grid, kFactorThreads, smem, st>>>(a);
+  if (fp32 && a.mma_mode == 0)
+    factor_kernel<float, 0><<<grid, kFactorThreads, smem, st>>>(a);
+  else if (fp32)
+    factor_kernel<float, 1><<<grid, kFactorThreads, smem, st>>>(a);
+  else if (a.mma_mode == 3)
+    factor_kernel<double, 3><<<grid, kFactorThreads, smem, st>>>(a);
   else
-    factor_kernel<double><<<grid, kFactorThreads, smem, st>>>(a);
+    factor_kernel<double, 0><<<grid, kFactorThreads, smem, st>>>(a);
   return cudaGetLastError();
 }
 

@@ -76,7 +76,7 @@ struct Sim {
   }
   void trsm(int s, int k) {
     const int w = width(s), ld = P.ld[s], r = P.nrows[s];
-    const int row0 = w + k * P.params.trsm_rows, cnt = std::min(P.params.trsm_rows, r - row0);
+    const int row0 = w + k * P.trsm_rows[s], cnt = std::min(P.trsm_rows[s], r - row0);
     double* A = panel(s);
     for (int i = row0; i < row0 + cnt; ++i)
       for (int j = 0; j < w; ++j) {

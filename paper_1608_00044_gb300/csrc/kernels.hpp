@@ -31,11 +31,17 @@ struct FactorArgs {
   const int32_t* trsm_first;
   const int32_t* ntrsm;
   const int32_t* trsm_sn;
+  const int32_t* trsm_rows_of;  // rows per panel-solve tile, per panel
   const int32_t* u_first;
   const int32_t* nu;
   const UTask* ut;
   int32_t n_trsm, n_u, ntask, trsm_rows;
-  int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products)
+  int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products);
+                       // FP64 panels: 0 DFMA update tiles, 3 BF16 tensor cores on 7-way split operands
+  uint16_t* slices;    // mode 3: BF16 slices of the rows below each diagonal block
+  const int64_t* sliceoff;
+  int32_t* rexp;       // mode 3: row exponent of every panel row (indexed like rows)
+  int32_t tc_min_width;  // mode 3: update tiles of panels at least this wide run on the tensor cores
   int32_t* dep_f;      // update tiles still to land in each panel
   int32_t* trsm_left;  // panel-solve tiles still to finish in each panel
   int* ring;
@@ -74,7 +80,7 @@ struct SolveArgs {
 
 // factor.cu
 size_t factor_smem_bytes(int max_w, int mma_mode);
-cudaError_t factor_configure(bool fp32, size_t smem, int* blocks_per_sm);
+cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_per_sm);
 cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz,
                             void* pool, cudaStream_t st);
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st);

@@ -11,6 +11,7 @@ namespace spchol {
 
 constexpr int kSolveTileRows = 256;  // one row per thread of a solve CTA
 constexpr int kTrsmTileRows = 64;
+constexpr int kFp64TcMinWidth = 32;
 
 inline void default_options(spchol_options* o) {
   std::memset(o, 0, sizeof(*o));
@@ -28,8 +29,8 @@ inline void default_options(spchol_options* o) {
 }
 
 inline bool options_valid(const spchol_options& o) {
-  const bool tc = o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3;
-  return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_TF32X3 && o.max_width >= 1 &&
+  const bool tc = o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3 || o.precision == SPCHOL_FP64_TC;
+  return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_FP64_TC && o.max_width >= 1 &&
          o.max_width <= (tc ? 64 : 128) &&
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
          o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 &&
@@ -41,7 +42,13 @@ inline PlanParams params_from(const spchol_options& o) {
   p.max_width = std::min(std::max(o.max_width, 1), 128);
   p.relax_zeros = std::max(o.relax_zeros, 0);
   p.tile_rows = o.tile_rows > 0 ? o.tile_rows : 64;
-  if (o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3) p.tile_rows = 128;  // one MMA M-tile
+  if (o.precision == SPCHOL_TF32 || o.precision == SPCHOL_TF32X3) p.tc_min_width = 1;  // every tile on TF32
+  if (o.precision == SPCHOL_FP64_TC) {
+    // panels of at least 32 columns carry almost all update work and go to the
+    // tensor cores; narrower ones keep DFMA tiles, whose cost scales with size
+    p.tc_min_width = kFp64TcMinWidth;
+    p.slice_fp64 = true;
+  }
   p.trsm_rows = kTrsmTileRows;
   p.solve_rows = kSolveTileRows;
   return p;

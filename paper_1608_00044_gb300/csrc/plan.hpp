@@ -7,6 +7,11 @@
 
 namespace spchol {
 
+// FP64 tensor-core mode: every FP64 value of L below a diagonal block is split
+// into this many 8-bit slices relative to its row's largest magnitude.
+constexpr int kSlices = 7;
+constexpr int kSliceBits = 8;
+
 // One update tile U(s, t): rows [row0, row0 + rowlen) of source panel s (indices
 // into s's row list) times the rows [seg0, seg0 + seglen) of s that fall inside
 // target panel t's columns (Section III-A, task U; Section IV, task T_{s,t}).
@@ -20,6 +25,17 @@ struct PlanParams {
   int tile_rows = 64;    // rows per update tile
   int trsm_rows = 128;   // rows per panel-solve tile
   int solve_rows = 128;  // rows per triangular-solve tile
+  // Panels within top_depth of the root of the panel etree (the chains of the
+  // top separators: the critical path) get smaller tiles, so that each step of
+  // the chain spreads over more CTAs.
+  int top_depth = 128;
+  int top_tile_rows = 16;
+  int top_trsm_rows = 32;
+  // Tensor-core update tiles: source panels at least tc_min_width wide (0 =
+  // none) use tc_tile_rows-row tiles (one MMA M-tile) on the tensor cores.
+  int tc_min_width = 0;
+  int tc_tile_rows = 128;
+  bool slice_fp64 = false;  // FP64 tensor-core mode: split those panels into BF16 digits
 };
 
 struct Plan {
@@ -43,6 +59,7 @@ struct Plan {
   std::vector<int32_t> rows;    // concatenated sorted row lists
   std::vector<int64_t> valoff;  // ns + 1, into the value pool (elements)
   std::vector<int64_t> invoff;  // ns + 1, into the diagonal-block inverse buffer (w x w per panel)
+  std::vector<int64_t> sliceoff;  // ns + 1, into the BF16 slice buffer (FP64 tensor-core mode)
   std::vector<int32_t> parent;  // panel etree, -1 at roots
   std::vector<int32_t> snode_of;  // column -> panel
   std::vector<int64_t> a_dest;  // entry e of A's lower CSC -> pool index
@@ -50,7 +67,7 @@ struct Plan {
   int32_t max_w = 0, max_r = 0;
 
   // factorization tasks: [0, ns) diagonal factor, then panel-solve tiles, then updates
-  std::vector<int32_t> trsm_first, ntrsm, trsm_sn;
+  std::vector<int32_t> trsm_first, ntrsm, trsm_sn, trsm_rows;  // trsm_rows: tile rows per panel
   std::vector<int32_t> u_first, nu;
   std::vector<UTask> ut;
   std::vector<int32_t> dep_f;  // update tiles targeting each panel

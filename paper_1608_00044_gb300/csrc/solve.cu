@@ -14,6 +14,8 @@
 // FWD_D is followed directly by its BWD_D.
 #include <climits>
 #include <cstdint>
+#include <map>
+#include <mutex>
 
 #include "device_common.cuh"
 #include "kernels.hpp"
@@ -291,13 +293,10 @@ size_t solve_smem_bytes(int max_w) {
   return diag > tile ? diag : tile;
 }
 
-// The dynamic shared-memory limit is a per-kernel setting shared by every
-// handle, so it is raised once to the device's opt-in maximum and never
-// lowered; each launch then passes its own size.
 cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm) {
   const void* fn = fp32 ? (const void*)solve_kernel<float> : (const void*)solve_kernel<double>;
-  static const cudaError_t once[2] = {raise_smem_limit((const void*)solve_kernel<double>), raise_smem_limit((const void*)solve_kernel<float>)};
-  if (once[fp32 ? 1 : 0] != cudaSuccess) return once[fp32 ? 1 : 0];
+  cudaError_t e = ensure_smem_limit(fn, smem);
+  if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
 }
 
@@ -307,6 +306,17 @@ cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, c
   else
     solve_kernel<double><<<grid, kSolveThreads, smem, st>>>(a);
   return cudaGetLastError();
+}
+
+cudaError_t ensure_smem_limit(const void* fn, size_t need) {
+  static std::mutex mu;
+  static std::map<const void*, size_t> current;
+  std::lock_guard<std::mutex> lock(mu);
+  size_t& cur = current[fn];
+  if (need <= cur) return cudaSuccess;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)need);
+  if (e == cudaSuccess) cur = need;
+  return e;
 }
 
 static int grid_for(int64_t total) {

@@ -295,6 +295,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.ld.resize(ns);
   P.valoff.assign(ns + 1, 0);
   P.invoff.assign(ns + 1, 0);
+  P.sliceoff.assign(ns + 1, 0);
   P.nnz_l_stored = 0;
   P.max_w = 0;
   P.max_r = 0;
@@ -303,6 +304,10 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     P.ld[s] = (int32_t)round4(r);
     P.valoff[s + 1] = P.valoff[s] + (int64_t)P.ld[s] * w;
     P.invoff[s + 1] = P.invoff[s] + (int64_t)w * w;
+    // BF16 slices of the rows below the diagonal block (panels on the tensor
+    // cores in the FP64 tensor-core mode): kSlices x nb x kpad16
+    const bool sliced = prm.slice_fp64 && w >= prm.tc_min_width;
+    P.sliceoff[s + 1] = P.sliceoff[s] + (sliced ? (int64_t)kSlices * (r - w) * (((int64_t)w + 15) & ~int64_t(15)) : 0);
     P.nnz_l_stored += (int64_t)r * w - (int64_t)w * (w - 1) / 2;
     P.max_w = std::max(P.max_w, w);
     P.max_r = std::max(P.max_r, r);
@@ -321,7 +326,9 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     }
 
   // ---- factorization tasks ------------------------------------------------------
-  const int TU = std::max(1, prm.tile_rows), TR = std::max(1, prm.trsm_rows);
+  std::vector<int32_t> depth(ns, 0);
+  for (int32_t s = ns - 1; s >= 0; --s) depth[s] = P.parent[s] < 0 ? 0 : depth[P.parent[s]] + 1;
+  P.trsm_rows.assign(ns, 0);
   P.trsm_first.assign(ns, 0);
   P.ntrsm.assign(ns, 0);
   P.u_first.assign(ns, 0);
@@ -332,6 +339,11 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
     const int32_t nb = r - w;
+    const bool top = depth[s] < prm.top_depth;
+    const bool tc = prm.tc_min_width > 0 && w >= prm.tc_min_width;
+    const int TU = std::max(1, tc ? prm.tc_tile_rows : top ? std::min(prm.top_tile_rows, prm.tile_rows) : prm.tile_rows);
+    const int TR = std::max(1, top ? std::min(prm.top_trsm_rows, prm.trsm_rows) : prm.trsm_rows);
+    P.trsm_rows[s] = TR;
     P.trsm_first[s] = (int32_t)P.trsm_sn.size();
     P.ntrsm[s] = (nb + TR - 1) / TR;
     for (int32_t k = 0; k < P.ntrsm[s]; ++k) P.trsm_sn.push_back(s);

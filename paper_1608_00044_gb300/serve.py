@@ -256,5 +256,5 @@ def make_stream(n_requests: int, rate: float, seed: int = 4321, repeat_frac: flo
         n = side ** 3 if dim3 else side ** 2
         nrhs = int(rng.integers(1, 17))
         B = np.asfortranarray(rng.uniform(-1, 1, (nrhs, n)).T)
-        reqs.append(Request(rid, float(t[rid]), f"p{j}", f"p{j}v{v}", maker(j, v), B, repeat=repeat))
+        reqs.append(Request(rid, float(t[rid]), f"s{seed}p{j}", f"s{seed}p{j}v{v}", maker(j, v), B, repeat=repeat))
     return reqs

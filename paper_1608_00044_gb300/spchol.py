@@ -15,7 +15,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "libspchol.so")
 
-FP64, FP32, TF32, TF32X3 = 0, 1, 2, 3
+FP64, FP32, TF32, TF32X3, FP64_TC = 0, 1, 2, 3, 4
 OK = 0
 ENOMEM, ETIMEOUT, ESTATE, ENOCONV, ECUDA, EINTERNAL = -1001, -1002, -1003, -1004, -1005, -1006
 

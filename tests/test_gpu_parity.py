@@ -278,3 +278,39 @@ def test_handles_with_different_panel_widths_coexist():
     assert oracle.berr(wide, X, B) <= BERR_FP64
     spchol.destroy(hw)
     spchol.destroy(hn)
+
+
+# ---------------------------------------------------------------- FP64 result, BF16 tensor-core updates
+
+
+@pytest.mark.parametrize("name,W", [("lap2d_64", 64), ("lap3d_16", 64), ("diff3d_12", 64), ("diff3d_11", 33),
+                                    ("lap3d_12", 16), ("diff2d_37", 7)])
+def test_fp64_tc_matches_oracle(name, W):
+    """The split-operand tensor-core updates keep the FP64 bar: backward error
+    <= 1e-13 with no refinement and L within 1e-11 of the oracle's."""
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=2)
+    _check(A, perm, B, precision=spchol.FP64_TC, max_width=W)
+
+
+@pytest.mark.parametrize("n", [1, 9, 64, 130])
+def test_fp64_tc_dense(n):
+    rng = np.random.default_rng(40 + n)
+    G = rng.standard_normal((n, n))
+    A = _csc(G @ G.T + n * np.eye(n))
+    _check(A, rng.permutation(n), gridgen.rhs_uniform(n, 2, seed=n), precision=spchol.FP64_TC)
+
+
+def test_fp64_tc_wide_dynamic_range():
+    """Rows whose entries span many orders of magnitude: the row-relative split
+    must still deliver FP64 backward error (diagonal scaling by 10^[-4, 4])."""
+    A0, perm, b = gridgen.workload("lap3d_10")
+    rng = np.random.default_rng(5)
+    d = 10.0 ** rng.uniform(-4, 4, A0.n)
+    cols = np.repeat(np.arange(A0.n), np.diff(A0.colptr))
+    vals = A0.values * d[A0.rowind] * d[cols]
+    A = gridgen.CscLower(A0.n, A0.colptr, A0.rowind, vals)
+    rc, X, st, h = gpu_factor_solve(A, perm, b, precision=spchol.FP64_TC)
+    assert rc == 0
+    assert oracle.berr(A, X, b) <= BERR_FP64
+    spchol.destroy(h)
