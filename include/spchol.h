@@ -59,6 +59,7 @@ extern "C" {
 #define SPCHOL_ENOCONV (-1004)  /* refinement did not reach ir_tol; X holds the best iterate */
 #define SPCHOL_ECUDA (-1005)    /* a CUDA runtime call failed */
 #define SPCHOL_EINTERNAL (-1006)/* a device-side consistency check failed */
+#define SPCHOL_ESCRATCH (-1007) /* spchol_solve_noalloc: n * nrhs too large for its fixed scratch */
 
 /* Arithmetic of the factor. */
 #define SPCHOL_FP64 0  /* everything in FP64 */
@@ -155,6 +156,30 @@ int spchol_factorize(spchol_handle_t h, const double* values, void* stream);
  * SPCHOL_ENOCONV if the target was not reached.
  */
 int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream);
+
+/*
+ * The solve of spchol_solve, for callers that cannot allocate device memory at
+ * the time they solve: a service that reserves all of its device memory up
+ * front, or code running where cudaMalloc is not allowed.  spchol_solve may
+ * allocate its workspace on first use or when nrhs grows; this entry point
+ * allocates nothing.  Its workspace (the permuted right-hand sides and the
+ * task queue of the solve kernel) lives in one fixed 32 MiB array in device
+ * memory that every GPU loading the library holds until the process exits.
+ * The paper has no counterpart; it is an interface convenience.
+ *   h      a handle with a resident FP64 factor (SPCHOL_FP64 or SPCHOL_FP64_TC;
+ *          other precisions return -1), factored by spchol_factorize
+ *   B      DEVICE memory, n x nrhs column-major, leading dimension ldb, overwritten
+ *          by X (a host pointer returns -2)
+ * Returns 0, -k for an invalid argument k, SPCHOL_ESTATE without a factor,
+ * SPCHOL_ESCRATCH when 8 n nrhs bytes plus the task queue exceed the scratch
+ * (about n * nrhs <= 3.5e6 for grid matrices), SPCHOL_ETIMEOUT, SPCHOL_ECUDA.
+ * The first call on a device looks up the array's device address (a CUDA
+ * runtime query, no allocation); make that first call before any stream
+ * capture.  All calls share the one array: calls whose work overlaps on the
+ * GPU (different streams, threads or handles at the same time) race on it and
+ * must be serialised by the caller.
+ */
+int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream);
 
 /* Copy the handle's statistics into *st. */
 int spchol_stats_get(spchol_handle_t h, spchol_stats* st);

@@ -576,6 +576,7 @@ const char* spchol_strerror(int code) {
     case SPCHOL_ENOCONV: return "iterative refinement did not reach the target backward error";
     case SPCHOL_ECUDA: return "a CUDA runtime call failed";
     case SPCHOL_EINTERNAL: return "a device-side consistency check failed";
+    case SPCHOL_ESCRATCH: return "the problem does not fit the fixed 32 MiB scratch of spchol_solve_noalloc";
     default: break;
   }
   if (code < 0 && code > -100) return "invalid argument (the code is minus the argument's 1-based position)";
@@ -678,6 +679,75 @@ int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stre
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
   h->stats.solve_ms = ms;
   return rc;
+}
+
+int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream) {
+  if (!h) return -1;
+  if (nrhs < 0) return -4;
+  if (ldb < std::max<int64_t>(h->plan.n, 1)) return -3;
+  if (!B && nrhs > 0 && h->plan.n > 0) return -2;
+  if (h->fp32) return -1;  // FP64 factors only (the refined mixed solve needs more workspace)
+  if (!h->factored) return SPCHOL_ESTATE;
+  if (nrhs == 0 || h->plan.n == 0) return 0;
+  DeviceGuard g(h->device);
+  clear_stale_error();
+  if (!is_device_ptr(B)) return -2;
+  const Plan& P = h->plan;
+  const int64_t n = P.n;
+  // scratch layout: Y (n x nrhs doubles) | ring | fkids | ftiles | btiles | control words
+  auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t y_bytes = up((size_t)n * nrhs * sizeof(double));
+  const size_t ring_bytes = up((size_t)P.n_solve_tasks * sizeof(int));
+  const size_t cnt_bytes = up((size_t)P.ns * sizeof(int32_t));
+  const size_t need = y_bytes + ring_bytes + 3 * cnt_bytes + up(kCtrlWords * sizeof(int));
+  if (need > kNoallocScratchBytes) return SPCHOL_ESCRATCH;
+  void* base = nullptr;
+  CU(noalloc_scratch(h->device, &base));
+  char* b = (char*)base;
+  double* Y = (double*)b;
+  int* ring = (int*)(b + y_bytes);
+  int32_t* fkids = (int32_t*)(b + y_bytes + ring_bytes);
+  int32_t* ftiles = (int32_t*)((char*)fkids + cnt_bytes);
+  int32_t* btiles = (int32_t*)((char*)ftiles + cnt_bytes);
+  int* ctrl = (int*)((char*)btiles + cnt_bytes);
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: the reset kernel re-initialises
+  // the ring, the counters and the control words before every launch
+  CU(launch_ring_reset(ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, ctrl, fkids, h->d_nkids_init, P.ns, ftiles,
+                       h->d_nst, P.ns, btiles, h->d_nst, P.ns, st));
+  CU(launch_permute_in(B, ldb, Y, n, h->d_perm, n, nrhs, st));
+  SolveArgs a{};
+  a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
+  a.kid_ptr = h->d_kid_ptr;
+  a.kids = h->d_kids;
+  a.st_first = h->d_st_first;
+  a.nst = h->d_nst;
+  a.st_sn = h->d_st_sn;
+  a.n_st = P.n_st;
+  a.ntask = P.n_solve_tasks;
+  a.solve_rows = P.params.solve_rows;
+  a.fkids = fkids;
+  a.ftiles = ftiles;
+  a.btiles = btiles;
+  a.ring = ring;
+  a.ctrl = ctrl;
+  a.budget_ns = h->opt.wait_budget_ns;
+  a.pool = h->d_pool;
+  a.inv = h->d_inv;
+  a.invoff = h->d_invoff;
+  a.Y = Y;
+  a.ldy = n;
+  a.nrhs = nrhs;
+  a.prof = nullptr;
+  a.trace = nullptr;
+  CU(launch_solve(false, a, h->grid_solve, h->smem_solve, st));
+  CU(launch_permute_out(Y, n, B, ldb, h->d_perm, n, nrhs, st));
+  CU(cudaMemcpyAsync(h->h_ctrl, ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const int* c = h->h_ctrl;
+  if (c[kErr] != 0) return c[kErr];
+  if (c[kDone] != P.n_solve_tasks) return SPCHOL_EINTERNAL;
+  return 0;
 }
 
 int spchol_stats_get(spchol_handle_t h, spchol_stats* st) {

@@ -94,6 +94,10 @@ cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t l
 cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t ldb, const int32_t* perm,
                                int64_t n, int nrhs, cudaStream_t st);
 
+// Fixed device scratch of spchol_solve_noalloc (solve.cu): 32 MiB.
+constexpr size_t kNoallocScratchBytes = size_t(32) << 20;
+cudaError_t noalloc_scratch(int device, void** ptr);
+
 // mixed.cu
 cudaError_t launch_residual(int64_t n, int nrhs, const int64_t* rp, const int32_t* ci, const int64_t* vmap,
                             const double* aval, const double* X, int64_t ldx, const double* B, int64_t ldb, double* R,

@@ -361,6 +361,40 @@ __global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int n
   }
 }
 
+// ---------------------------------------------------------------- fixed scratch for spchol_solve_noalloc
+// Callers that must not allocate device memory during a solve (a process whose
+// device memory is fully reserved up front, or code running where allocation
+// calls are not permitted) use spchol_solve_noalloc, whose workspace lives in
+// this file-scope array instead of memory from cudaMalloc.  Every GPU that
+// loads the library holds it until the process exits.  All calls share it, so
+// calls whose work overlaps on the GPU race on it.
+__device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+cudaError_t noalloc_scratch(int device, void** ptr) {
+  // One address per device, looked up once with that device current: in host
+  // code the array's name is only a host-side stand-in, never a device address.
+  constexpr int kMaxDevices = 64;
+  static std::mutex mu;
+  static void* addr[kMaxDevices] = {};
+  if (device < 0 || device >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(mu);
+  if (addr[device]) {
+    *ptr = addr[device];
+    return cudaSuccess;
+  }
+  int prev = -1;
+  cudaError_t e = cudaGetDevice(&prev);
+  if (e != cudaSuccess) return e;
+  if (prev != device && (e = cudaSetDevice(device)) != cudaSuccess) return e;
+  void* p = nullptr;
+  e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+  if (prev != device) cudaSetDevice(prev);
+  if (e != cudaSuccess) return e;
+  addr[device] = p;
+  *ptr = p;
+  return cudaSuccess;
+}
+
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                               const int* c2_init, int n2, cudaStream_t st) {

@@ -17,7 +17,7 @@ LIB_PATH = os.path.join(_HERE, "libspchol.so")
 
 FP64, FP32, TF32, TF32X3, FP64_TC = 0, 1, 2, 3, 4
 OK = 0
-ENOMEM, ETIMEOUT, ESTATE, ENOCONV, ECUDA, EINTERNAL = -1001, -1002, -1003, -1004, -1005, -1006
+ENOMEM, ETIMEOUT, ESTATE, ENOCONV, ECUDA, EINTERNAL, ESCRATCH = -1001, -1002, -1003, -1004, -1005, -1006, -1007
 
 
 class Options(ctypes.Structure):
@@ -90,6 +90,7 @@ SIGNATURES = [
     ("spchol_analyze", ctypes.c_int, [_i64, _vp, _vp, _vp, ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
     ("spchol_factorize", ctypes.c_int, [_vp, _vp, _vp]),
     ("spchol_solve", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
+    ("spchol_solve_noalloc", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     ("spchol_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
     ("spchol_export_factor", ctypes.c_int, [_vp, ctypes.POINTER(_i64), _vp, _vp, _vp, _vp]),
     ("spchol_trace_get", ctypes.c_int, [_vp, ctypes.c_int, _vp, ctypes.POINTER(_i64)]),
@@ -220,6 +221,16 @@ def solve(h, B, ldb=None, nrhs=None, stream=None) -> int:
     rc = load().spchol_solve(h, _ptr(B), int(ldb), int(nrhs), _stream(stream))
     if rc != 0:
         raise SpcholError(rc, "spchol_solve")
+    return rc
+
+
+def solve_noalloc(h, B, ldb=None, nrhs=None, stream=None) -> int:
+    """spchol_solve_noalloc: the solve without any device allocation, B in device memory."""
+    if nrhs is None or ldb is None:
+        raise ValueError("give ldb and nrhs explicitly")
+    rc = load().spchol_solve_noalloc(h, _ptr(B), int(ldb), int(nrhs), _stream(stream))
+    if rc != 0:
+        raise SpcholError(rc, "spchol_solve_noalloc")
     return rc
 
 
