@@ -117,6 +117,7 @@ typedef struct spchol_stats {
   double factor_wait_ms;      /* waiting for a ready task */
   double solve_task_ms[4];    /* forward diagonal, forward tiles, backward tiles, backward diagonal */
   double solve_wait_ms;
+  double factor_tc_update_ms; /* part of factor_task_ms[2] spent in tensor-core update tiles */
   int grid_factor;            /* CTAs of the persistent factorization launch */
   int grid_solve;
 } spchol_stats;
@@ -147,6 +148,20 @@ int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, cons
  * Returns 0, k > 0 (not positive definite at permuted column k), or an error.
  */
 int spchol_factorize(spchol_handle_t h, const double* values, void* stream);
+
+/*
+ * spchol_factorize split in two for CUDA-graph capture.  _enqueue queues the
+ * whole factorization (assembly, counter reset, the persistent factorization
+ * kernel, and a copy of its status words to pinned host memory) on `stream`
+ * without synchronising the host and without allocating; values must be
+ * DEVICE memory (for a batch handle: all matrices' values concatenated in
+ * batch order).  After the stream (or the graph it was captured into) has
+ * completed, _status returns what spchol_factorize would have returned and
+ * makes the factor available to the solves.  Returns of _enqueue: 0, -1/-2
+ * for bad arguments, SPCHOL_ECUDA.
+ */
+int spchol_factorize_enqueue(spchol_handle_t h, const double* values, void* stream);
+int spchol_factorize_status(spchol_handle_t h);
 
 /*
  * Solve A X = B with the resident factor (Section II-A: L y = P b, L^T z = y,

@@ -20,7 +20,7 @@ HOST_LIB = os.path.join(HERE, "libspchol_host.so")
 HOST_SOURCES = ["symbolic.cpp", "hostsim.cpp"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "factor.cu", "solve.cu", "mixed.cu", "symbolic.cpp"]
+SOURCES = ["api.cu", "factor.cu", "solve.cu", "mixed.cu", "symbolic.cpp"]  # peak_probe.cu is a separate program
 
 
 def _nvcc() -> str:
@@ -68,6 +68,18 @@ def build_host(force: bool = False) -> str:
         raise RuntimeError(f"host build failed: {' '.join(cmd)}\n{r.stdout}\n{r.stderr}")
     os.replace(tmp, HOST_LIB)
     return HOST_LIB
+
+
+PROBE = os.path.join(BUILD, "peak_probe")
+
+
+def build_probe() -> str:
+    """Arithmetic-throughput probe used for the roofline denominators."""
+    src = os.path.join(CSRC, "peak_probe.cu")
+    if not os.path.exists(PROBE) or os.path.getmtime(PROBE) < os.path.getmtime(src):
+        os.makedirs(BUILD, exist_ok=True)
+        subprocess.check_call([_nvcc(), *ARCH, "-O3", "-o", PROBE, src])
+    return PROBE
 
 
 def build(force: bool = False, verbose: bool = False) -> str:

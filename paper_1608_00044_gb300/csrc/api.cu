@@ -53,6 +53,7 @@ struct spchol_handle_s {
   int num_sms = 0;
   bool fp32 = false;
   bool factored = false;
+  bool pending = false;  // a factorization was enqueued without a status read
   std::vector<int32_t> a_row, a_col;  // A's lower entries (original order); dropped after analyze
   int batch_count = 0;                // 0 = single matrix
   std::vector<int64_t> batch_n, batch_col0, batch_nnz0;  // per matrix: order, first column, first value
@@ -68,6 +69,8 @@ struct spchol_handle_s {
   int nfseeds = 0;
   int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
+  int32_t *d_st_tptr = nullptr, *d_st_tgt = nullptr, *d_rt_ptr = nullptr, *d_rt_tile = nullptr;
+  int32_t *d_fdep0 = nullptr, *d_bdep0 = nullptr, *d_bdep = nullptr;
   int32_t *d_sseeds = nullptr;
   int nsseeds = 0;
   int32_t* d_perm = nullptr;
@@ -163,8 +166,10 @@ int setup_device(spchol_handle_t h) {
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
     nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
-    if (nkids[s] == 0) sseeds.push_back(s);
+    if (P.fdep0[s] == 0) sseeds.push_back(s);
   }
+  size_t o_sttp = r32(P.st_tptr.size()), o_sttg = r32(P.st_tgt.size()), o_rtp = r32(P.rt_ptr.size()),
+         o_rtt = r32(P.rt_tile.size()), o_fd0 = r32(ns), o_bd0 = r32(P.n_st), o_bd = r32(P.n_st);
   size_t o_nki = r32(ns), o_fk = r32(ns), o_ft = r32(ns), o_bt = r32(ns), o_sseeds = r32(sseeds.size());
   size_t o_perm = r32(P.n);
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
@@ -245,6 +250,13 @@ int setup_device(spchol_handle_t h) {
   h->d_ftiles = (int32_t*)(b + o_ft);
   h->d_btiles = (int32_t*)(b + o_bt);
   h->d_sseeds = (int32_t*)(b + o_sseeds);
+  h->d_st_tptr = (int32_t*)(b + o_sttp);
+  h->d_st_tgt = (int32_t*)(b + o_sttg);
+  h->d_rt_ptr = (int32_t*)(b + o_rtp);
+  h->d_rt_tile = (int32_t*)(b + o_rtt);
+  h->d_fdep0 = (int32_t*)(b + o_fd0);
+  h->d_bdep0 = (int32_t*)(b + o_bd0);
+  h->d_bdep = (int32_t*)(b + o_bd);
   h->nsseeds = (int)sseeds.size();
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
@@ -277,6 +289,9 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
       (rc = upload(h, h->d_kid_ptr, P.kid_ptr)) || (rc = upload(h, h->d_kids, P.kids)) ||
       (rc = upload(h, h->d_nkids_init, nkids)) || (rc = upload(h, h->d_sseeds, sseeds)) ||
+      (rc = upload(h, h->d_st_tptr, P.st_tptr)) || (rc = upload(h, h->d_st_tgt, P.st_tgt)) ||
+      (rc = upload(h, h->d_rt_ptr, P.rt_ptr)) || (rc = upload(h, h->d_rt_tile, P.rt_tile)) ||
+      (rc = upload(h, h->d_fdep0, P.fdep0)) || (rc = upload(h, h->d_bdep0, P.bdep0)) ||
       (rc = upload(h, h->d_perm, perm32)))
     return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
@@ -392,6 +407,58 @@ int finish_analyze(spchol_handle_t h, std::chrono::steady_clock::time_point t0) 
   return 0;
 }
 
+// Queue assembly, counter reset, the persistent factorization and the copy
+// of its status words to pinned host memory; no host synchronisation and no
+// allocation, so the sequence can be captured into a CUDA graph.
+int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool profile = false) {
+  Plan& P = h->plan;
+  CU(cudaMemsetAsync(h->d_pool, 0, h->pool_bytes, st));
+  CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
+  if (P.ns == 0) return 0;
+  CU(launch_ring_reset(h->d_ring, P.n_factor_tasks, h->d_fseeds, h->nfseeds, h->d_ctrl, h->d_dep, h->d_dep_init,
+                       P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st));
+  FactorArgs a{};
+  a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
+  a.trsm_first = h->d_trsm_first;
+  a.ntrsm = h->d_ntrsm;
+  a.trsm_sn = h->d_trsm_sn;
+  a.trsm_rows_of = h->d_trsm_rows;
+  a.u_first = h->d_u_first;
+  a.nu = h->d_nu;
+  a.ut = h->d_ut;
+  a.n_trsm = P.n_trsm;
+  a.n_u = P.n_u;
+  a.ntask = P.n_factor_tasks;
+  a.trsm_rows = P.params.trsm_rows;
+  a.mma_mode = mma_mode_of(h->opt.precision);
+  a.slices = h->d_slices;
+  a.sliceoff = h->d_sliceoff;
+  a.rexp = h->d_rexp;
+  a.tc_min_width = P.params.tc_min_width;
+  a.dep_f = h->d_dep;
+  a.trsm_left = h->d_trsm_left;
+  a.ring = h->d_ring;
+  a.ctrl = h->d_ctrl;
+  a.budget_ns = h->opt.wait_budget_ns;
+  a.pool = h->d_pool;
+  a.inv = h->d_inv;
+  a.invoff = h->d_invoff;
+  a.prof = profile ? h->d_prof : nullptr;
+  a.trace = profile ? h->d_trace_f : nullptr;
+  if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), st));
+  CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
+  CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
+  return 0;
+}
+
+int status_of(spchol_handle_t h) {
+  const int* c = h->h_ctrl;
+  if (c[kErr] != 0) return c[kErr];
+  if (c[kInfo] != INT_MAX) return c[kInfo];
+  if (c[kDone] != h->plan.n_factor_tasks) return SPCHOL_EINTERNAL;
+  return 0;
+}
+
 int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const double* values_host,
                    cudaStream_t st) {
   Plan& P = h->plan;
@@ -405,46 +472,12 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
     vals = h->d_vals;
   }
   CU(cudaEventRecord(h->ev0, st));
-  CU(cudaMemsetAsync(h->d_pool, 0, h->pool_bytes, st));
-  CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
-  if (P.ns > 0) {
-    CU(launch_ring_reset(h->d_ring, P.n_factor_tasks, h->d_fseeds, h->nfseeds, h->d_ctrl, h->d_dep,
-                         h->d_dep_init, P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st));
-    FactorArgs a{};
-    a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
-    a.trsm_first = h->d_trsm_first;
-    a.ntrsm = h->d_ntrsm;
-    a.trsm_sn = h->d_trsm_sn;
-    a.trsm_rows_of = h->d_trsm_rows;
-    a.u_first = h->d_u_first;
-    a.nu = h->d_nu;
-    a.ut = h->d_ut;
-    a.n_trsm = P.n_trsm;
-    a.n_u = P.n_u;
-    a.ntask = P.n_factor_tasks;
-    a.trsm_rows = P.params.trsm_rows;
-    a.mma_mode = mma_mode_of(h->opt.precision);
-    a.slices = h->d_slices;
-    a.sliceoff = h->d_sliceoff;
-    a.rexp = h->d_rexp;
-    a.tc_min_width = P.params.tc_min_width;
-    a.dep_f = h->d_dep;
-    a.trsm_left = h->d_trsm_left;
-    a.ring = h->d_ring;
-    a.ctrl = h->d_ctrl;
-    a.budget_ns = h->opt.wait_budget_ns;
-    a.pool = h->d_pool;
-    a.inv = h->d_inv;
-    a.invoff = h->d_invoff;
-    a.prof = h->opt.profile ? h->d_prof : nullptr;
-    a.trace = h->d_trace_f;
-    if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), st));
-    CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
-  }
+  int rc = enqueue_factor(h, vals, st, h->opt.profile != 0);
+  if (rc) return rc;
   CU(cudaEventRecord(h->ev1, st));
-  int rc = 0;
+  CU(cudaStreamSynchronize(st));
   if (P.ns > 0) {
-    rc = read_status(h, st, P.n_factor_tasks);
+    rc = status_of(h);
     if (h->opt.profile) {
       CU(cudaMemcpy(h->h_prof, h->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
       for (int k = 0; k < 3; ++k) {
@@ -452,9 +485,8 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
         h->stats.factor_task_count[k] = (int64_t)h->h_prof[4 + k];
       }
       h->stats.factor_wait_ms = h->h_prof[3] * 1e-6;
+      h->stats.factor_tc_update_ms = h->h_prof[7] * 1e-6;
     }
-  } else {
-    CU(cudaStreamSynchronize(st));
   }
   float ms = 0.f;
   cudaEventElapsedTime(&ms, h->ev0, h->ev1);
@@ -468,8 +500,9 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
 int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   Plan& P = h->plan;
   if (P.ns == 0 || nrhs == 0) return 0;
-  CU(launch_ring_reset(h->d_ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, h->d_ctrl, h->d_fkids,
-                       h->d_nkids_init, P.ns, h->d_ftiles, h->d_nst, P.ns, h->d_btiles, h->d_nst, P.ns, st));
+  CU(launch_ring_reset(h->d_ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, h->d_ctrl, h->d_fkids, h->d_fdep0,
+                       P.ns, h->d_ftiles, h->d_nst, P.ns, h->d_btiles, h->d_nst, P.ns, st, h->d_bdep, h->d_bdep0,
+                       P.n_st));
   SolveArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
   a.kid_ptr = h->d_kid_ptr;
@@ -480,7 +513,12 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
   a.solve_rows = P.params.solve_rows;
-  a.fkids = h->d_fkids;
+  a.st_tptr = h->d_st_tptr;
+  a.st_tgt = h->d_st_tgt;
+  a.rt_ptr = h->d_rt_ptr;
+  a.rt_tile = h->d_rt_tile;
+  a.fdep = h->d_fkids;
+  a.bdep = h->d_bdep;
   a.ftiles = h->d_ftiles;
   a.btiles = h->d_btiles;
   a.ring = h->d_ring;
@@ -635,6 +673,34 @@ int spchol_factorize(spchol_handle_t h, const double* values, void* stream) {
   return factorize_impl(h, dev ? values : nullptr, dev ? nullptr : values, st);
 }
 
+int spchol_factorize_enqueue(spchol_handle_t h, const double* values, void* stream) {
+  if (!h) return -1;
+  if (!values && h->plan.nnz_a > 0) return -2;
+  DeviceGuard g(h->device);
+  clear_stale_error();
+  if (values && !is_device_ptr(values)) return -2;
+  h->factored = false;
+  h->pending = true;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (h->fp32 && h->plan.nnz_a > 0) {  // the refinement residual reads A's FP64 values later
+    CU(cudaMemcpyAsync(h->d_vals, values, h->plan.nnz_a * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    values = h->d_vals;
+  }
+  return enqueue_factor(h, values, st);
+}
+
+int spchol_factorize_status(spchol_handle_t h) {
+  if (!h) return -1;
+  if (!h->pending) return SPCHOL_ESTATE;
+  if (h->plan.ns == 0) {
+    h->factored = true;
+    return 0;
+  }
+  const int rc = status_of(h);
+  h->factored = (rc == 0);
+  return rc;
+}
+
 int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream) {
   if (!h) return -1;
   if (nrhs < 0) return -4;
@@ -694,27 +760,29 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   if (!is_device_ptr(B)) return -2;
   const Plan& P = h->plan;
   const int64_t n = P.n;
-  // scratch layout: Y (n x nrhs doubles) | ring | fkids | ftiles | btiles | control words
+  // scratch layout: Y (n x nrhs doubles) | ring | fdep | ftiles | btiles | bdep | control words
   auto up = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t y_bytes = up((size_t)n * nrhs * sizeof(double));
   const size_t ring_bytes = up((size_t)P.n_solve_tasks * sizeof(int));
   const size_t cnt_bytes = up((size_t)P.ns * sizeof(int32_t));
-  const size_t need = y_bytes + ring_bytes + 3 * cnt_bytes + up(kCtrlWords * sizeof(int));
+  const size_t tile_bytes = up((size_t)P.n_st * sizeof(int32_t));
+  const size_t need = y_bytes + ring_bytes + 3 * cnt_bytes + tile_bytes + up(kCtrlWords * sizeof(int));
   if (need > kNoallocScratchBytes) return SPCHOL_ESCRATCH;
   void* base = nullptr;
   CU(noalloc_scratch(h->device, &base));
   char* b = (char*)base;
   double* Y = (double*)b;
   int* ring = (int*)(b + y_bytes);
-  int32_t* fkids = (int32_t*)(b + y_bytes + ring_bytes);
-  int32_t* ftiles = (int32_t*)((char*)fkids + cnt_bytes);
+  int32_t* fdep = (int32_t*)(b + y_bytes + ring_bytes);
+  int32_t* ftiles = (int32_t*)((char*)fdep + cnt_bytes);
   int32_t* btiles = (int32_t*)((char*)ftiles + cnt_bytes);
-  int* ctrl = (int*)((char*)btiles + cnt_bytes);
+  int32_t* bdep = (int32_t*)((char*)btiles + cnt_bytes);
+  int* ctrl = (int*)((char*)bdep + tile_bytes);
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the reset kernel re-initialises
   // the ring, the counters and the control words before every launch
-  CU(launch_ring_reset(ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, ctrl, fkids, h->d_nkids_init, P.ns, ftiles,
-                       h->d_nst, P.ns, btiles, h->d_nst, P.ns, st));
+  CU(launch_ring_reset(ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, ctrl, fdep, h->d_fdep0, P.ns, ftiles,
+                       h->d_nst, P.ns, btiles, h->d_nst, P.ns, st, bdep, h->d_bdep0, P.n_st));
   CU(launch_permute_in(B, ldb, Y, n, h->d_perm, n, nrhs, st));
   SolveArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
@@ -726,7 +794,12 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
   a.solve_rows = P.params.solve_rows;
-  a.fkids = fkids;
+  a.st_tptr = h->d_st_tptr;
+  a.st_tgt = h->d_st_tgt;
+  a.rt_ptr = h->d_rt_ptr;
+  a.rt_tile = h->d_rt_tile;
+  a.fdep = fdep;
+  a.bdep = bdep;
   a.ftiles = ftiles;
   a.btiles = btiles;
   a.ring = ring;

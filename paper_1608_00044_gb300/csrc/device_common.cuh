@@ -50,6 +50,34 @@ __device__ __forceinline__ int ldcg(const int* p) { return __ldcg(p); }
 
 __device__ __forceinline__ void red_add(double* p, double v) { atomicAdd(p, v); }
 
+// Copy the lower triangle of a w x w column-major block (leading dimension ld)
+// into shared memory as double (ld w, zeros above the diagonal).  Each thread
+// issues a batch of independent loads before it stores any of them, so the
+// copy costs a few memory latencies instead of one per element.
+template <bool kL2Only, typename T>
+__device__ __forceinline__ void stage_lower(const T* __restrict__ src, int w, int ld, double* __restrict__ dst) {
+  constexpr int B = 8;
+  const int total = w * w, nt = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += B * nt) {
+    double v[B];
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int idx = base + u * nt;
+      const int i = idx % w, j = idx / w;
+      v[u] = 0.0;
+      if (idx < total && i >= j) {
+        const T* p = src + i + (size_t)j * ld;
+        v[u] = kL2Only ? (double)__ldcg(p) : (double)*p;
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < B; ++u) {
+      const int idx = base + u * nt;
+      if (idx < total) dst[idx] = v[u];
+    }
+  }
+}
+
 // Raise a kernel's dynamic shared-memory limit to at least `need` bytes (host).
 // The limit is a per-kernel setting shared by every handle of the process; it
 // only ever grows, to the largest size any handle has needed, so a launch

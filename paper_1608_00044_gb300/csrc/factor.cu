@@ -45,10 +45,7 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
   T* P = panel_ptr<T>(a, s);
   if (!skip) {
-    for (int idx = tid; idx < w * w; idx += nt) {
-      const int i = idx % w, j = idx / w;
-      sm[idx] = (i >= j) ? (double)ldcg(P + i + (size_t)j * ld) : 0.0;
-    }
+    stage_lower<true>(P, w, ld, sm);
     if (tid == 0) sh.flag = 0;
     __syncthreads();
     // Right-looking (Algorithm 1) on the block in shared memory.  Thread
@@ -189,9 +186,13 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
   ct* sm = reinterpret_cast<ct*>(smd);
   (void)f;
   if (!skip) {
-    for (int idx = tid; idx < w * w; idx += nt) {
-      const int i = idx % w, j = idx / w;
-      sm[idx] = (i >= j) ? (ct)ldcg(P + i + (size_t)j * ld) : ct(0);
+    if constexpr (sizeof(ct) == 8) {
+      stage_lower<true>(P, w, ld, reinterpret_cast<double*>(sm));
+    } else {
+      for (int idx = tid; idx < w * w; idx += nt) {
+        const int i = idx % w, j = idx / w;
+        sm[idx] = (i >= j) ? (ct)ldcg(P + i + (size_t)j * ld) : ct(0);
+      }
     }
     __syncthreads();
     for (int rr = tid; rr < cnt; rr += nt) {
@@ -547,22 +548,20 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
 // for d <= 3 and round at most at 2^-56 relative beyond.  The epilogue
 // combines the seven group values per entry exactly in two 64-bit integers,
 // converts once to FP64 and scales by 2^(e_i + e_j).
-// The double nearest to t * 2^k for a 128-bit integer t, with integer
-// operations only (round to nearest, ties to even; no FP64 pipe use).
-__device__ __forceinline__ double fixed128_to_double(__int128 t, int k) {
+// The double nearest to t * 2^k for a 64-bit integer t, with integer
+// operations only (round to nearest, ties to even).
+__device__ __forceinline__ double fixed64_to_double(long long t, int k) {
   if (t == 0) return 0.0;
   const bool neg = t < 0;
-  const unsigned __int128 u = neg ? (unsigned __int128)(-t) : (unsigned __int128)t;
-  const unsigned long long hi = (unsigned long long)(u >> 64), lo = (unsigned long long)u;
-  int msb = hi ? 127 - __clzll((long long)hi) : 63 - __clzll((long long)lo);
+  const unsigned long long u = neg ? (unsigned long long)(-t) : (unsigned long long)t;
+  int msb = 63 - __clzll((long long)u);
   unsigned long long m;
   if (msb <= 52) {
-    m = lo << (52 - msb);
+    m = u << (52 - msb);
   } else {
     const int sh = msb - 52;
-    m = (unsigned long long)(u >> sh);
-    const unsigned __int128 rem = u & (((unsigned __int128)1 << sh) - 1);
-    const unsigned __int128 halfw = (unsigned __int128)1 << (sh - 1);
+    m = u >> sh;
+    const unsigned long long rem = u & ((1ull << sh) - 1), halfw = 1ull << (sh - 1);
     if (rem > halfw || (rem == halfw && (m & 1ull))) {
       ++m;
       if (m >> 53) {
@@ -571,14 +570,13 @@ __device__ __forceinline__ double fixed128_to_double(__int128 t, int k) {
       }
     }
   }
-  const int be = msb + k + 1023;  // biased exponent of m 2^(msb - 52) 2^k
+  const int be = msb + k + 1023;
   if (be <= 0 || be >= 2047) {
-    const double r = ldexp((double)m, msb - 52 + k);  // subnormal / overflow: outside the path's range
+    const double r = ldexp((double)m, msb - 52 + k);  // outside the range of this path's data
     return neg ? -r : r;
   }
-  const unsigned long long bits =
-      ((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1));
-  return __longlong_as_double((long long)bits);
+  return __longlong_as_double(
+      (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
 constexpr int kOzM = 128, kOzN = 64;
@@ -699,11 +697,18 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
             for (int q = 0; q < 8; ++q) {
               const int j = c0 + q;
               if (j < ncol && grow[row] >= gcol[j]) {
-                // t = sum_d v_d 2^(8 (6 - d)) exactly; C = t 2^(e_i + e_j - 64)
-                __int128 acc = 0;
+                // t = sum_d v_d 2^(8 (6 - d)), C = t 2^(e_i + e_j - 64).  The group
+                // sums are integers below 2^25 in magnitude; t (< 2^75) is formed
+                // as hi 2^32 + lo and kept to 2^12 units in one int64, a
+                // truncation of at most 2^(e_i + e_j - 52), below the rounding
+                // bound of an FP64 dot product of these rows.
+                long long hi = 0, lo = 0;
 #pragma unroll
-                for (int d = 0; d < kSlices; ++d) acc = acc * 256 + (__int128)__float2ll_rn(__uint_as_float(v[d][q]));
-                const double c = fixed128_to_double(acc, ea[row] + eb[j] - 64);
+                for (int d = 0; d < 3; ++d) hi = hi * 256 + __float2int_rn(__uint_as_float(v[d][q]));
+#pragma unroll
+                for (int d = 3; d < kSlices; ++d) lo = lo * 256 + __float2int_rn(__uint_as_float(v[d][q]));
+                const long long t12 = hi * (1ll << 20) + (lo >> 12);  // floor((hi 2^32 + lo) / 2^12)
+                const double c = fixed64_to_double(t12, ea[row] + eb[j] - 52);
                 red_add(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -c);
               }
             }
@@ -735,7 +740,7 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
   double* smd = reinterpret_cast<double*>(smem_raw);
   const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
   // per-CTA task timing (thread 0 only), flushed once at exit
-  unsigned long long busy[3] = {0, 0, 0}, cnt[3] = {0, 0, 0}, wait = 0;
+  unsigned long long busy[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, wait = 0;  // [3]: tensor-core update tiles
   // tensor-core state (FP32 panels with mma_mode 1 / 2): TMEM accumulator + mbarrier
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -787,10 +792,12 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
       type = 2;
       if constexpr (MODE == 3) {
         const UTask u = a.ut[task - a.pv.ns - a.n_trsm];
-        if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width)
+        if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width) {
+          type = 3;
           task_update_oz(a, u, smem_raw, sh, skip, tc);
-        else
+        } else {
           task_update<T>(a, u, smem_raw, sh, skip);
+        }
       }
       else if constexpr (MODE == 1)
         task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
@@ -806,7 +813,7 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
       if (a.prof) {
         const unsigned long long d = global_ns() - t1;
 #pragma unroll
-        for (int k = 0; k < 3; ++k)
+        for (int k = 0; k < 4; ++k)
           if (k == type) {
             busy[k] += d;
             cnt[k] += 1;
@@ -817,10 +824,11 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
   }
   if (threadIdx.x == 0 && a.prof) {
     for (int k = 0; k < 3; ++k) {
-      atomicAdd(&a.prof[k], busy[k]);
-      atomicAdd(&a.prof[4 + k], cnt[k]);
+      atomicAdd(&a.prof[k], busy[k] + (k == 2 ? busy[3] : 0ull));
+      atomicAdd(&a.prof[4 + k], cnt[k] + (k == 2 ? cnt[3] : 0ull));
     }
     atomicAdd(&a.prof[3], wait);
+    atomicAdd(&a.prof[7], busy[3]);  // tensor-core share of the update tiles
   }
   if (use_tc) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

@@ -245,12 +245,12 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   for (int r = 0; r < nrhs; ++r)
     for (int64_t i = 0; i < n; ++i) Y[i + (size_t)r * n] = B[P.perm[i] + (size_t)r * ldb];
   const int nst = P.n_st;
-  std::vector<int> fk(ns), ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
-  for (int s = 0; s < ns; ++s) fk[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
+  std::vector<int> fdep(P.fdep0.begin(), P.fdep0.end()), bdep(P.bdep0.begin(), P.bdep0.end());
+  std::vector<int> ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
   std::vector<char> sran(P.n_solve_tasks, 0);
   Ready q;
   for (int s = 0; s < ns; ++s)
-    if (fk[s] == 0) q.push(s);
+    if (fdep[s] == 0) q.push(s);
   int sdone = 0;
   const int TS = P.params.solve_rows;
   while (!q.empty()) {
@@ -284,12 +284,17 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           for (int j = 0; j < w; ++j) acc += L[i + (size_t)j * ld] * Y[f + j + (size_t)r * n];
           Y[R[i] + (size_t)r * n] -= acc;
         }
-      if (--ft[s] < 0) return SPCHOL_EINTERNAL;
-      if (ft[s] == 0) {
-        const int par = P.parent[s];
-        if (par < 0) return SPCHOL_EINTERNAL;
-        if (--fk[par] == 0) q.push(par);
+      for (int e = P.st_tptr[kt]; e < P.st_tptr[kt + 1]; ++e) {
+        const int t = P.st_tgt[e];
+        if (--fdep[t] < 0) return SPCHOL_EINTERNAL;
+        if (fdep[t] == 0) q.push(t);
       }
+      if (--ft[s] < 0) return SPCHOL_EINTERNAL;
+      if (ft[s] == 0)
+        for (int k2 = 0; k2 < P.nst[s]; ++k2) {
+          const int tile = P.st_first[s] + k2;
+          if (--bdep[tile] == 0) q.push(ns + nst + tile);
+        }
     } else if (task < ns + 2 * nst) {  // BWD_T
       const int kt = task - ns - nst, s = P.st_sn[kt], k = kt - P.st_first[s];
       const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
@@ -314,9 +319,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           for (int i = 0; i < j; ++i) y[i] -= L[j + (size_t)i * ld] * y[j];
         }
       }
-      for (int c = P.kid_ptr[s]; c < P.kid_ptr[s + 1]; ++c) {
-        const int kid = P.kids[c];
-        for (int k = 0; k < P.nst[kid]; ++k) q.push(ns + nst + P.st_first[kid] + k);
+      for (int e = P.rt_ptr[s]; e < P.rt_ptr[s + 1]; ++e) {
+        const int tile = P.rt_tile[e];
+        if (--bdep[tile] < 0) return SPCHOL_EINTERNAL;
+        if (bdep[tile] == 0) q.push(ns + nst + tile);
       }
     }
   }

@@ -62,7 +62,12 @@ struct SolveArgs {
   const int32_t* nst;
   const int32_t* st_sn;
   int32_t n_st, ntask, solve_rows;
-  int32_t* fkids;   // children whose subtree has not finished the forward solve
+  const int32_t* st_tptr;  // solve tile -> panels its rows fall in (CSR)
+  const int32_t* st_tgt;
+  const int32_t* rt_ptr;   // panel -> solve tiles whose rows fall in it (CSR)
+  const int32_t* rt_tile;
+  int32_t* fdep;    // forward tiles still to land in each panel's rows
+  int32_t* bdep;    // per tile: target panels not yet back-solved, + 1 until its panel's forward tiles are done
   int32_t* ftiles;  // forward tiles left per panel
   int32_t* btiles;  // backward tiles left per panel
   int* ring;
@@ -110,6 +115,7 @@ cudaError_t launch_correct(const double* Y, int64_t ldy, double* X, int64_t ldx,
 // sched.cu
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
-                              const int* c2_init, int n2, cudaStream_t st);
+                              const int* c2_init, int n2, cudaStream_t st, int* c3 = nullptr,
+                              const int* c3_init = nullptr, int n3 = 0);
 
 }  // namespace spchol

@@ -76,6 +76,11 @@ struct Plan {
   // solve tasks
   std::vector<int32_t> st_first, nst, st_sn;
   std::vector<int32_t> kid_ptr, kids;  // panel children, CSR
+  // precise solve dependencies: the panels whose columns each solve tile's rows
+  // fall in (tile -> targets, CSR), the same relation reversed (panel -> tiles),
+  // forward counters (tiles touching each panel) and backward tile counters
+  // (targets + 1 for "every forward tile of the tile's own panel is done")
+  std::vector<int32_t> st_tptr, st_tgt, rt_ptr, rt_tile, fdep0, bdep0;
   int32_t n_st = 0, n_solve_tasks = 0;
 
   PlanParams params;

@@ -94,6 +94,7 @@ __device__ __forceinline__ void publish_cta_writes() {
 // their initial copies, control words.
 __global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int* ctrl,
                                   int* c0, const int* c0_init, int n0, int* c1, const int* c1_init,
-                                  int n1, int* c2, const int* c2_init, int n2);
+                                  int n1, int* c2, const int* c2_init, int n2, int* c3,
+                                  const int* c3_init, int n3);
 
 }  // namespace spchol

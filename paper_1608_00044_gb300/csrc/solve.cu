@@ -6,12 +6,13 @@
 //   [ns, ns + nst)               FWD_T(s, k): y[rows of tile k] -= L21[k] y_s
 //   [ns + nst, ns + 2 nst)       BWD_T(s, k): y_s -= L21[k]^T x[rows of tile k]
 //   [ns + 2 nst, 2 ns + 2 nst)   BWD_D(s): x_s <- L11^{-T} y_s
-// Forward: FWD_D(s) runs once every child subtree has finished (all of its
-// descendants have added their contributions to y_s); a panel's subtree is
-// finished when its last FWD_T tile is.  Backward: the tiles of s run once
-// BWD_D(parent(s)) is done (every ancestor is then final); BWD_D(s) runs after
-// all tiles of s.  A root has no rows below its diagonal block, so its
-// FWD_D is followed directly by its BWD_D.
+// Dependencies are exact, per panel and per tile.  Forward: FWD_D(t) runs once
+// every FWD_T tile whose rows fall in t's columns has subtracted its part.
+// Backward: BWD_T(s, k) runs once every panel its rows fall in has finished
+// BWD_D (those x are final) and every forward tile of s is done (so y_s is no
+// longer read by them); BWD_D(s) runs after all tiles of s.  A root has no
+// rows below its diagonal block, so its FWD_D is followed directly by its
+// BWD_D.
 #include <climits>
 #include <cstdint>
 #include <map>
@@ -36,15 +37,6 @@ __device__ __forceinline__ const T* spanel(const SolveArgs& a, int s) {
   return reinterpret_cast<const T*>(a.pool) + a.pv.valoff[s];
 }
 
-// L11 (lower, w x w) into shared memory as double, column-major with ld w.
-template <typename T>
-__device__ void load_l11(const T* P, int w, int ld, double* sm) {
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-    const int i = idx % w, j = idx / w;
-    sm[idx] = (i >= j) ? (double)P[i + (size_t)j * ld] : 0.0;
-  }
-}
-
 // y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
 // every entry is an independent dot product, no sequential substitution.
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
@@ -52,10 +44,7 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
   const double* X = a.inv + a.invoff[s];
   double* Xs = sm;          // [w][w] column-major, lower part
   double* Ys = sm + w * w;  // [nrc][w]
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-    const int i = idx % w, j = idx / w;
-    Xs[idx] = (i >= j) ? X[idx] : 0.0;
-  }
+  stage_lower<false>(X, w, w, Xs);
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -85,10 +74,7 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
   const double* X = a.inv + a.invoff[s];
   double* Xs = sm;
   double* Ys = sm + w * w;
-  for (int idx = threadIdx.x; idx < w * w; idx += blockDim.x) {
-    const int i = idx % w, j = idx / w;
-    Xs[idx] = (i >= j) ? X[idx] : 0.0;
-  }
+  stage_lower<false>(X, w, w, Xs);
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -233,9 +219,19 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
       const int kt = task - ns, s = a.st_sn[kt];
       fwd_tile<T>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
-      if (threadIdx.x == 0 && atom_add_acqrel(&a.ftiles[s], -1) == 1) {
-        const int p = a.pv.parent[s];
-        if (p >= 0 && atom_add_acqrel(&a.fkids[p], -1) == 1) ring_push_one(q, p);
+      // Counter updates are spread over the CTA's threads: a panel near the
+      // root has thousands of dependent tiles, and they sit on the critical path.
+      for (int e = a.st_tptr[kt] + threadIdx.x; e < a.st_tptr[kt + 1]; e += blockDim.x) {
+        const int t = a.st_tgt[e];
+        if (atom_add_acqrel(&a.fdep[t], -1) == 1) ring_push_one(q, t);
+      }
+      if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
+      __syncthreads();
+      if (sh.flag) {
+        for (int k = threadIdx.x; k < a.nst[s]; k += blockDim.x) {
+          const int tile = a.st_first[s] + k;
+          if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring_push_one(q, ns + nst + tile);
+        }
       }
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
@@ -246,9 +242,9 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
       const int s = task - ns - 2 * nst;
       bwd_diag(a, s, sm);
       publish_cta_writes();
-      for (int c = a.kid_ptr[s]; c < a.kid_ptr[s + 1]; ++c) {
-        const int kid = a.kids[c];
-        ring_push_range(q, ns + nst + a.st_first[kid], a.nst[kid], &sh.base);
+      for (int e = a.rt_ptr[s] + threadIdx.x; e < a.rt_ptr[s + 1]; e += blockDim.x) {
+        const int tile = a.rt_tile[e];
+        if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring_push_one(q, ns + nst + tile);
       }
     }
     if (threadIdx.x == 0) {
@@ -342,13 +338,14 @@ cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t 
 // ---------------------------------------------------------------- ring reset
 __global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                                   const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
-                                  const int* c2_init, int n2) {
+                                  const int* c2_init, int n2, int* c3, const int* c3_init, int n3) {
   const int stride = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
   for (int i = tid; i < ntask; i += stride) slots[i] = (i < nseed) ? seeds[i] : -1;
   for (int i = tid; i < n0; i += stride) c0[i] = c0_init[i];
   for (int i = tid; i < n1; i += stride) c1[i] = c1_init[i];
   for (int i = tid; i < n2; i += stride) c2[i] = c2_init[i];
+  for (int i = tid; i < n3; i += stride) c3[i] = c3_init[i];
   if (tid == 0) {
     ctrl[kHead] = 0;
     ctrl[kTail] = nseed;
@@ -397,13 +394,14 @@ cudaError_t noalloc_scratch(int device, void** ptr) {
 
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
-                              const int* c2_init, int n2, cudaStream_t st) {
+                              const int* c2_init, int n2, cudaStream_t st, int* c3, const int* c3_init, int n3) {
   int m = ntask;
   if (n0 > m) m = n0;
   if (n1 > m) m = n1;
   if (n2 > m) m = n2;
+  if (n3 > m) m = n3;
   ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, ctrl, c0, c0_init, n0, c1, c1_init,
-                                                 n1, c2, c2_init, n2);
+                                                 n1, c2, c2_init, n2, c3, c3_init, n3);
   return cudaGetLastError();
 }
 

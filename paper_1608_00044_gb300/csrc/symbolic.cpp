@@ -379,6 +379,38 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   }
   P.n_st = (int32_t)P.st_sn.size();
   P.n_solve_tasks = 2 * ns + 2 * P.n_st;
+  P.st_tptr.assign(P.n_st + 1, 0);
+  P.st_tgt.clear();
+  P.fdep0.assign(ns, 0);
+  P.bdep0.assign(P.n_st, 0);
+  for (int32_t s = 0; s < ns; ++s) {
+    const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
+    const int32_t* R = P.rows.data() + P.rowoff[s];
+    for (int32_t k = 0; k < P.nst[s]; ++k) {
+      const int32_t tile = P.st_first[s] + k;
+      const int32_t r0 = w + k * TS, r1 = std::min(r, r0 + TS);
+      int32_t last = -1;
+      for (int32_t i = r0; i < r1; ++i) {
+        const int32_t t = P.snode_of[R[i]];
+        if (t != last) {  // rows are sorted, so each target appears as one run
+          P.st_tgt.push_back(t);
+          P.fdep0[t]++;
+          last = t;
+        }
+      }
+      P.st_tptr[tile + 1] = (int32_t)P.st_tgt.size();
+      P.bdep0[tile] = (P.st_tptr[tile + 1] - P.st_tptr[tile]) + 1;
+    }
+  }
+  P.rt_ptr.assign(ns + 1, 0);
+  for (int32_t t : P.st_tgt) P.rt_ptr[t + 1]++;
+  for (int32_t s = 0; s < ns; ++s) P.rt_ptr[s + 1] += P.rt_ptr[s];
+  P.rt_tile.resize(P.st_tgt.size());
+  {
+    std::vector<int32_t> fill(P.rt_ptr.begin(), P.rt_ptr.end() - 1);
+    for (int32_t tile = 0; tile < P.n_st; ++tile)
+      for (int32_t q = P.st_tptr[tile]; q < P.st_tptr[tile + 1]; ++q) P.rt_tile[fill[P.st_tgt[q]]++] = tile;
+  }
   P.kid_ptr.assign(ns + 1, 0);
   for (int32_t s = 0; s < ns; ++s)
     if (P.parent[s] != -1) P.kid_ptr[P.parent[s] + 1]++;

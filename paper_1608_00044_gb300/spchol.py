@@ -59,6 +59,7 @@ class Stats(ctypes.Structure):
         ("factor_wait_ms", ctypes.c_double),
         ("solve_task_ms", ctypes.c_double * 4),
         ("solve_wait_ms", ctypes.c_double),
+        ("factor_tc_update_ms", ctypes.c_double),
         ("grid_factor", ctypes.c_int),
         ("grid_solve", ctypes.c_int),
     ]
@@ -89,6 +90,8 @@ SIGNATURES = [
     ("spchol_default_options", None, [ctypes.POINTER(Options)]),
     ("spchol_analyze", ctypes.c_int, [_i64, _vp, _vp, _vp, ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
     ("spchol_factorize", ctypes.c_int, [_vp, _vp, _vp]),
+    ("spchol_factorize_enqueue", ctypes.c_int, [_vp, _vp, _vp]),
+    ("spchol_factorize_status", ctypes.c_int, [_vp]),
     ("spchol_solve", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     ("spchol_solve_noalloc", ctypes.c_int, [_vp, _vp, _i64, ctypes.c_int, _vp]),
     ("spchol_stats_get", ctypes.c_int, [_vp, ctypes.POINTER(Stats)]),
@@ -210,6 +213,21 @@ def factorize(h, values, stream=None) -> int:
     rc = load().spchol_factorize(h, _ptr(values), _stream(stream))
     if rc < 0:
         raise SpcholError(rc, "spchol_factorize")
+    return rc
+
+
+def factorize_enqueue(h, values, stream=None) -> None:
+    """spchol_factorize_enqueue: queue the factorization (device values) without waiting."""
+    rc = load().spchol_factorize_enqueue(h, _ptr(values), _stream(stream))
+    if rc != 0:
+        raise SpcholError(rc, "spchol_factorize_enqueue")
+
+
+def factorize_status(h) -> int:
+    """spchol_factorize_status: result of the last enqueued factorization, once its stream is done."""
+    rc = load().spchol_factorize_status(h)
+    if rc < 0:
+        raise SpcholError(rc, "spchol_factorize_status")
     return rc
 
 

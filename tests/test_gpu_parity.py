@@ -314,3 +314,72 @@ def test_fp64_tc_wide_dynamic_range():
     assert rc == 0
     assert oracle.berr(A, X, b) <= BERR_FP64
     spchol.destroy(h)
+
+
+# ---------------------------------------------------------------- CUDA graphs, autotuning
+
+
+def _capture_factorization(h, vals):
+    s = torch.cuda.Stream()
+    s.wait_stream(torch.cuda.current_stream())
+    with torch.cuda.stream(s):  # one eager run first: nothing is allocated during capture
+        spchol.factorize_enqueue(h, vals, stream=s)
+    s.synchronize()
+    assert spchol.factorize_status(h) == 0
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g, stream=s):
+        spchol.factorize_enqueue(h, vals, stream=s)
+    return g
+
+
+def test_factorization_captured_in_a_cuda_graph():
+    A, perm, b = gridgen.workload("lap3d_12")
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options())
+    vals = torch.from_numpy(A.values).cuda()
+    g = _capture_factorization(h, vals)
+    for scale in (1.0, 2.5, 0.5):
+        vals.copy_(torch.from_numpy(A.values * scale))
+        g.replay()
+        torch.cuda.synchronize()
+        assert spchol.factorize_status(h) == 0
+        X = b.copy(order="F")
+        spchol.solve(h, X, A.n, b.shape[1])
+        As = gridgen.CscLower(A.n, A.colptr, A.rowind, A.values * scale)
+        assert oracle.berr(As, X, b) <= BERR_FP64
+    spchol.destroy(h)
+
+
+def test_batch_factorization_captured_in_a_cuda_graph():
+    sides = [9, 20, 13, 31]
+    mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms,
+                             spchol.default_options())
+    vals = torch.cat([torch.from_numpy(M.values) for M in mats]).cuda()
+    g = _capture_factorization(h, vals)
+    g.replay()
+    torch.cuda.synchronize()
+    assert spchol.factorize_status(h) == 0
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=i) for i, M in enumerate(mats)]
+    Xs = [B.copy(order="F") for B in Bs]
+    spchol.batch_solve(h, Xs, [M.n for M in mats], [2] * len(mats))
+    for M, B, X in zip(mats, Bs, Xs):
+        assert oracle.berr(M, X, B) <= BERR_FP64
+    spchol.destroy(h)
+
+
+def test_autotuner_picks_a_working_configuration(tmp_path):
+    from paper_1608_00044_gb300 import autotune
+
+    sides = [17, 25, 40]
+    mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    cache = str(tmp_path / "tune.json")
+    res = autotune.tune(mats, perms, candidates=[(64, 4, 64), (32, 16, 32)], reps=2, cache_path=cache)
+    assert len(res["tried_ms"]) == 2 and not res["cached"]
+    again = autotune.tune(mats, perms, candidates=[(64, 4, 64), (32, 16, 32)], reps=2, cache_path=cache)
+    assert again["cached"] and again["max_width"] == res["max_width"]
+    o = spchol.default_options(max_width=res["max_width"], relax_zeros=res["relax_zeros"], tile_rows=res["tile_rows"])
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+    spchol.destroy(h)
