@@ -42,6 +42,25 @@ def _peaks():
         return {}
 
 
+KERNEL_SOURCES = ["factor.cu", "device_common.cuh", "sched.cuh", "kernels.hpp", "plan.hpp"]
+
+
+def _measured_traffic(kernel: str):
+    """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
+    when the kernel sources changed since that capture."""
+    import hashlib
+
+    try:
+        rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+    except Exception:
+        return None
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1608_00044_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return rec["bytes_per_launch"] if h.hexdigest() == rec["kernel_sources_sha1"] else None
+
+
 def _dist():
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -487,7 +506,9 @@ def run_ours(args):
         "flops": flops,
         "nnz_l": st0["nnz_l"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": UNIT,
-                     "frac": achieved / peak_fp64, "traffic": None,
+                     "frac": achieved / peak_fp64,
+                     "traffic": _measured_traffic("factor_kernel<double, 0>")
+                     if args.precision == "fp64" and args.workload == "lap3d_64" else None,
                      "kernel": "factor_kernel<double> (persistent; includes assembly)",
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (NVIDIA's 1.25 TFLOP/s FP64 "
                                   "figure); the probe's measured DFMA rate is in peak_measured",
