@@ -62,6 +62,7 @@ struct spchol_handle_s {
   int32_t *d_fcol = nullptr, *d_nrows = nullptr, *d_ld = nullptr, *d_rows = nullptr, *d_parent = nullptr;
   int64_t *d_rowoff = nullptr, *d_valoff = nullptr, *d_adest = nullptr;
   int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
+  int32_t* d_nu_hi = nullptr;
   int32_t* d_trsm_rows = nullptr;
   UTask* d_ut = nullptr;
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
@@ -155,7 +156,7 @@ int setup_device(spchol_handle_t h) {
   const bool oz = h->opt.precision == SPCHOL_FP64_TC;
   size_t o_sliceoff = r64(ns + 1), o_rexp = oz ? r32(P.rows.size()) : 0;
   size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
-  size_t o_trows = r32(ns);
+  size_t o_trows = r32(ns), o_nuhi = r32(ns);
   size_t o_ut = A.reserve(std::max<size_t>(P.ut.size(), 1) * sizeof(UTask));
   size_t o_depi = r32(ns), o_trsi = r32(ns), o_dep = r32(ns), o_trs = r32(ns);
   std::vector<int32_t> fseeds;
@@ -233,6 +234,7 @@ int setup_device(spchol_handle_t h) {
   h->d_trsm_rows = (int32_t*)(b + o_trows);
   h->d_u_first = (int32_t*)(b + o_uf);
   h->d_nu = (int32_t*)(b + o_nu);
+  h->d_nu_hi = (int32_t*)(b + o_nuhi);
   h->d_ut = (UTask*)(b + o_ut);
   h->d_dep_init = (int32_t*)(b + o_depi);
   h->d_trsm_init = (int32_t*)(b + o_trsi);
@@ -283,7 +285,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
       (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
       (rc = upload(h, h->d_trsm_rows, P.trsm_rows)) ||
-      (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_ut, P.ut)) ||
+      (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_nu_hi, P.nu_hi)) || (rc = upload(h, h->d_ut, P.ut)) ||
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
@@ -416,7 +418,8 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
   if (P.ns == 0) return 0;
   CU(launch_ring_reset(h->d_ring, P.n_factor_tasks, h->d_fseeds, h->nfseeds, h->d_ctrl, h->d_dep, h->d_dep_init,
-                       P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st));
+                       P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st, nullptr, nullptr, 0,
+                       /*seeds_hi=*/1));
   FactorArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
   a.trsm_first = h->d_trsm_first;
@@ -425,6 +428,8 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.trsm_rows_of = h->d_trsm_rows;
   a.u_first = h->d_u_first;
   a.nu = h->d_nu;
+  a.nu_hi = h->d_nu_hi;
+  a.n_hi = P.n_hi_tasks;
   a.ut = h->d_ut;
   a.n_trsm = P.n_trsm;
   a.n_u = P.n_u;

@@ -9,13 +9,15 @@ namespace spchol {
 
 // Control block (int32 words) of one persistent launch.
 enum CtrlWord : int {
-  kHead = 0,   // next ring slot to claim
-  kTail = 1,   // next ring slot to fill
-  kErr = 2,    // 0, or an SPCHOL_E* code (timeout, internal check)
-  kInfo = 3,   // smallest failing pivot column + 1, INT32_MAX if none
-  kDone = 4,   // tasks completed (consistency check)
-  kWhere = 5,  // diagnostic: task id where a wait gave up
-  kCtrlWords = 8
+  kHead = 0,     // next ring slot to claim (the factorization's normal-priority ring)
+  kTail = 1,     // next ring slot to fill
+  kErr = 2,      // 0, or an SPCHOL_E* code (timeout, internal check)
+  kInfo = 3,     // smallest failing pivot column + 1, INT32_MAX if none
+  kDone = 4,     // tasks completed (consistency check)
+  kWhere = 5,    // diagnostic: task id where a wait gave up
+  kHiHead = 32,  // the factorization's high-priority ring, in its own 128-byte line
+  kHiTail = 33,
+  kCtrlWords = 64
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {
@@ -34,6 +36,12 @@ __device__ __forceinline__ int atom_add_acqrel(int* p, int v) {
 __device__ __forceinline__ int ld_relaxed(const int* p) {
   int v;
   asm volatile("ld.relaxed.gpu.global.b32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+// Two adjacent words (8-byte aligned) in one load: x = p[0], y = p[1].
+__device__ __forceinline__ int2 ld_relaxed_pair(const int* p) {
+  int2 v;
+  asm volatile("ld.relaxed.gpu.global.v2.b32 {%0, %1}, [%2];" : "=r"(v.x), "=r"(v.y) : "l"(p) : "memory");
   return v;
 }
 __device__ __forceinline__ uint64_t global_ns() {

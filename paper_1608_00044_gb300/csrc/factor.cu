@@ -11,6 +11,7 @@
 //                applied immediately, by atomic adds, instead of being kept).
 // Dependencies (Section II-C): UPD(s, ., .) needs every TRSM tile of s;
 // POTRF(t) needs every update tile targeting t.
+#include <algorithm>
 #include <climits>
 #include <cstdint>
 
@@ -24,7 +25,8 @@ namespace spchol {
 
 namespace {
 
-constexpr int kTrsmJB = 8;  // columns solved together per row (independent FMA chains)
+constexpr int kTrsmJB = 8;     // wide panels: columns solved together per row (independent FMA chains)
+constexpr int kTrsmMaxW = 64;  // panels up to this width take the register-resident panel solve
 
 struct FactorShared {
   int task;
@@ -33,78 +35,130 @@ struct FactorShared {
   int base;
 };
 
+__device__ __forceinline__ Ring2 rings_of(const FactorArgs& a) {
+  return Ring2{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
+}
+
 template <typename T>
 __device__ __forceinline__ T* panel_ptr(const FactorArgs& a, int s) {
   return reinterpret_cast<T*>(a.pool) + a.pv.valoff[s];
 }
 
 // ---------------------------------------------------------------- POTRF(s)
+// Right-looking Cholesky (Algorithm 1) of the w x w diagonal block in shared
+// memory, one barrier per column.  Step j: warps 0..6 form the scaled column
+// j (l_ij = a_ij / l_jj, into a double-buffered vector), write column j - 1
+// back in place, and apply the rank-1 update of the trailing triangle;
+// meanwhile warp 7 already updates a_{j+1,j+1} and takes its square root
+// (look-ahead), so the pivot chain overlaps the update instead of following it.
+// The update is enumerated by the pair index p of the trailing triangle in
+// column-major order from its bottom-right corner, so that p < m (m + 1) / 2
+// is exactly the triangle of order m and consecutive p touch consecutive rows.
+constexpr int kPivotWarp = 7;
+constexpr int kUpdWarps = 7;
+
+__device__ __forceinline__ void tri_pair(int p, int& ei, int& ek) {
+  int e = (int)((sqrtf((float)(8 * p + 1)) - 1.0f) * 0.5f);
+  if ((e + 1) * (e + 2) / 2 <= p) ++e;
+  if (e * (e + 1) / 2 > p) --e;
+  ek = e;
+  ei = p - e * (e + 1) / 2;
+}
+
+// Pivot of column j: l_jj = sqrt(d) and its reciprocal; false when d is not
+// positive (the block is not positive definite at this column).
+__device__ __forceinline__ bool take_pivot(double d, double& l, double& r) {
+  if (!(d > 0.0)) return false;
+  l = sqrt(d);
+  r = 1.0 / l;
+  return true;
+}
+
 template <typename T>
 __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip) {
-  const int tid = threadIdx.x, nt = blockDim.x;
+  const int tid = threadIdx.x;
+  const int warp = tid >> 5, lane = tid & 31;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
   T* P = panel_ptr<T>(a, s);
+  double* xd = sm + w * w;  // r_j = 1 / l_jj (the diagonal of L11^{-1})
+  double* cb = xd + w;      // 2 x w: scaled column of the current step, by parity
+  bool ok = true;
   if (!skip) {
-    stage_lower<true>(P, w, ld, sm);
+    stage_lower<true>(P, w, ld, sm);  // lower triangle; zeros above (used below for L11^{-1})
     if (tid == 0) sh.flag = 0;
     __syncthreads();
-    // Right-looking (Algorithm 1) on the block in shared memory.  Thread
-    // (tx, ty) = (tid % 64, tid / 64) updates rows j+1+tx (+64...) of the
-    // trailing triangle in the columns j+1+ty, j+5+ty, ...: independent FMAs,
-    // no index division.
-    const int tx = tid & 63, ty = tid >> 6, nty = nt >> 6;
-    for (int j = 0; j < w; ++j) {
-      if (tid == 0) {
-        const double d = sm[j + j * w];
-        if (!(d > 0.0)) {
-          atomicMin(&a.ctrl[kInfo], f + j + 1);
-          sh.flag = 1;
+    if (tid == kPivotWarp * 32) {
+      double l, r;
+      if (take_pivot(sm[0], l, r)) {
+        sm[0] = l;
+        xd[0] = r;
+      } else {
+        atomicMin(&a.ctrl[kInfo], f + 1);
+        sh.flag = 1;
+      }
+    }
+    __syncthreads();
+    for (int j = 0; j < w && !sh.flag; ++j) {
+      const double rj = xd[j];
+      if (warp < kUpdWarps) {
+        double* cj = cb + (j & 1) * w;
+        const double* cprev = cb + ((j + 1) & 1) * w;
+        for (int i = j + 1 + tid; i < w; i += kUpdWarps * 32) cj[i] = sm[i + j * w] * rj;
+        if (j > 0)
+          for (int i = j + tid; i < w; i += kUpdWarps * 32) sm[i + (j - 1) * w] = cprev[i];
+        asm volatile("bar.sync 1, %0;" ::"n"(kUpdWarps * 32) : "memory");
+        const int m = w - 1 - j;
+        const int np = m * (m + 1) / 2 - 1;  // all but (j + 1, j + 1), which warp 7 owns
+        for (int p = tid; p < np; p += kUpdWarps * 32) {
+          int ei, ek;
+          tri_pair(p, ei, ek);
+          const int i = w - 1 - ei, k = w - 1 - ek;
+          sm[i + k * w] = fma(-cj[i], cj[k], sm[i + k * w]);
+        }
+      } else if (lane == 0 && j + 1 < w) {
+        const double l1 = sm[(j + 1) + j * w] * rj;
+        const double d = fma(-l1, l1, sm[(j + 1) * (w + 1)]);
+        double l, r;
+        if (take_pivot(d, l, r)) {
+          sm[(j + 1) * (w + 1)] = l;
+          xd[j + 1] = r;
         } else {
-          sm[j + j * w] = sqrt(d);
+          atomicMin(&a.ctrl[kInfo], f + j + 2);
+          sh.flag = 1;
         }
       }
       __syncthreads();
-      if (sh.flag) break;
-      const double ljj = sm[j + j * w];
-      for (int i = j + 1 + tid; i < w; i += nt) sm[i + j * w] = sm[i + j * w] / ljj;
-      __syncthreads();
-      for (int i = j + 1 + tx; i < w; i += 64) {
-        const double lij = sm[i + j * w];
-        for (int k = j + 1 + ty; k <= i; k += nty) sm[i + k * w] -= lij * sm[k + j * w];
-      }
-      __syncthreads();
     }
-    for (int idx = tid; idx < w * w; idx += nt) {
-      const int i = idx % w, j = idx / w;
-      if (i >= j) P[i + (size_t)j * ld] = (T)sm[idx];
-    }
-    if (!sh.flag) {
-      // L11^{-1} for the solves: thread j forms column j, X e_j = L11^{-1} e_j, by
-      // forward substitution (right-looking, so the updates of one step are
-      // independent).  X[i][j], i > j, goes to the unused upper triangle at
-      // (j, i); the diagonal 1 / l_jj to xd[j].
-      double* xd = sm + w * w;
-      for (int j = tid; j < w; j += nt) {
-        const double xjj = 1.0 / sm[j + j * w];
-        xd[j] = xjj;
-        for (int i = j + 1; i < w; ++i) sm[j + i * w] = -sm[i + j * w] * xjj;
-        for (int k = j + 1; k < w; ++k) {
-          const double xk = sm[j + k * w] / sm[k + k * w];
-          sm[j + k * w] = xk;
-          for (int i = k + 1; i < w; ++i) sm[j + i * w] -= sm[i + k * w] * xk;
-        }
-      }
-      __syncthreads();
-      double* X = a.inv + a.invoff[s];
-      for (int idx = tid; idx < w * w; idx += nt) {
-        const int i = idx % w, j = idx / w;
-        if (i >= j) X[idx] = (i == j) ? xd[j] : sm[j + i * w];
-      }
-    }
+    ok = !sh.flag;
+    for (int j = warp; j < w; j += kFactorThreads / 32)
+      for (int i = j + lane; i < w; i += 32) P[i + (size_t)j * ld] = (T)sm[i + j * w];
   }
   publish_cta_writes();
-  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-  ring_push_range(q, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+  ring2_push_range(rings_of(a), true, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+  if (!skip && ok) {
+    // L11^{-1} for the solves, off the critical path (the panel-solve tiles are
+    // already released).  X = L11^{-1} by right-looking forward substitution
+    // on all columns at once: after row k of X is final, every row i > k
+    // subtracts l_ik X[k][:]; the row k + 1 is finished (scaled by r_{k+1}) by
+    // the same thread that applies its last update.  X[i][c], i > c, lives in
+    // the zeroed upper triangle at (c, i); the diagonal is xd.
+    for (int k = 0; k < w - 1; ++k) {
+      for (int i = k + 1 + warp; i < w; i += kFactorThreads / 32) {
+        const double lik = sm[i + k * w];
+        const double ri = xd[i];
+        for (int c = lane; c <= k; c += 32) {
+          const double xkc = (c == k) ? xd[k] : sm[c + k * w];
+          double v = fma(-lik, xkc, sm[c + i * w]);
+          if (i == k + 1) v *= ri;
+          sm[c + i * w] = v;
+        }
+      }
+      __syncthreads();
+    }
+    double* X = a.inv + a.invoff[s];
+    for (int j = warp; j < w; j += kFactorThreads / 32)
+      for (int i = j + lane; i < w; i += 32) X[i + (size_t)j * w] = (i == j) ? xd[j] : sm[j + i * w];
+  }
 }
 
 // ---------------------------------------------------------------- FP64 operand slicing
@@ -185,7 +239,66 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
   T* P = panel_ptr<T>(a, s);
   ct* sm = reinterpret_cast<ct*>(smd);
   (void)f;
-  if (!skip) {
+  if (!skip && w <= kTrsmMaxW) {
+    // L21 = A21 L11^{-T}, row by row: forward substitution along each row with
+    // the columns in registers.  Warp q takes 4-row strips 4 (q + 8 v); lane
+    // (lr, lc) holds row lr of the strip at columns lc + 8 cc.  Step c: the lane
+    // holding column c scales it by 1 / l_cc, the value is broadcast within the
+    // 8 lanes of the row, and every later column subtracts it times l_qc.
+    const int warp = tid >> 5, lane = tid & 31, lr = lane >> 3, lc = lane & 7;
+    ct* Ls = sm;                        // Ls[q + 64 c] = l_qc for q > c, else 0
+    ct* rinv = sm + kTrsmMaxW * w;      // 1 / l_cc
+    for (int idx = tid; idx < kTrsmMaxW * w; idx += nt) {
+      const int qq = idx & (kTrsmMaxW - 1), c = idx >> 6;
+      Ls[idx] = (qq < w && qq > c) ? (ct)ldcg(P + qq + (size_t)c * ld) : ct(0);
+    }
+    for (int c = tid; c < w; c += nt) rinv[c] = ct(1) / (ct)ldcg(P + c + (size_t)c * ld);
+    __syncthreads();
+    const int nstrip = (cnt + 3) >> 2;
+    for (int st = warp; st < nstrip; st += nt >> 5) {
+      const int rloc = 4 * st + lr;
+      const bool rv = rloc < cnt;
+      T* Pi = P + row0 + rloc;
+      ct x[8];
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = lc + 8 * cc;
+        x[cc] = (rv && c < w) ? (ct)ldcg(Pi + (size_t)c * ld) : ct(0);
+      }
+#pragma unroll
+      for (int cbk = 0; cbk < 8; ++cbk) {
+        if (8 * cbk >= w) break;
+        for (int c8 = 0; c8 < 8; ++c8) {
+          const int c = 8 * cbk + c8;
+          if (c >= w) break;
+          if (lc == c8) x[cbk] *= rinv[c];
+          const ct xc = __shfl_sync(0xffffffffu, x[cbk], (lr << 3) | c8);
+          const ct* Lc = Ls + kTrsmMaxW * c;
+          if (lc > c8) x[cbk] -= xc * Lc[lc + 8 * cbk];
+#pragma unroll
+          for (int cc = cbk + 1; cc < 8; ++cc) {
+            if (8 * cc >= w) break;
+            x[cc] -= xc * Lc[lc + 8 * cc];
+          }
+        }
+      }
+#pragma unroll
+      for (int cc = 0; cc < 8; ++cc) {
+        const int c = lc + 8 * cc;
+        if (rv && c < w) Pi[(size_t)c * ld] = (T)x[cc];
+      }
+    }
+    if constexpr (sizeof(T) == 8 && MODE == 3) {
+      if (w >= a.tc_min_width) {
+        __syncthreads();  // the tile's rows are written (visible to this CTA through L2)
+        const int kpad = (w + 15) & ~15, nbel = r - w;
+        for (int rr = tid; rr < cnt; rr += nt)
+          slice_row(reinterpret_cast<const double*>(P + row0 + rr), w, ld, kpad, nbel, row0 + rr - w,
+                    a.slices + a.sliceoff[s], a.rexp + a.pv.rowoff[s] + row0 + rr);
+      }
+    }
+  } else if (!skip) {
+    // Panels wider than kTrsmMaxW: one thread per row, columns in blocks.
     if constexpr (sizeof(ct) == 8) {
       stage_lower<true>(P, w, ld, reinterpret_cast<double*>(sm));
     } else {
@@ -232,47 +345,57 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
   if (tid == 0) sh.flag = (atom_add_acqrel(&a.trsm_left[s], -1) == 1);
   __syncthreads();
   if (sh.flag) {
-    const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-    ring_push_range(q, a.pv.ns + a.n_trsm + a.u_first[s], a.nu[s], &sh.base);
+    const Ring2 q = rings_of(a);
+    const int first = a.pv.ns + a.n_trsm + a.u_first[s], nhi = a.nu_hi[s];
+    ring2_push_range(q, true, first, nhi, &sh.base);
+    ring2_push_range(q, false, first + nhi, a.nu[s] - nhi, &sh.base);
   }
 }
 
 // ---------------------------------------------------------------- UPD(s, t, k)
 // C = A B^T for one tile, A = L_s[row tile] (rowlen x ws), B = L_s[segment]
-// (ncol x ws), staged through shared memory in k-chunks.  The 16 x 16 thread
-// grid covers C in 16-row / 16-column groups; NR x NC groups are computed, so
-// a small tile does not pay for a full 64 x 64 one.
+// (ncol x ws), staged through shared memory in k-chunks.  Warp q owns the
+// 8-row strip [8q, 8q + 8) of C; lane (lr, lc) = (lane / 8, lane % 8) holds
+// rows 8q + lr + 4 rr (rr < NR) and columns lc + 8 cc (cc < NC).  Strips past
+// rowlen, the second half of a strip with at most 4 valid rows, column blocks
+// past ncol and, where the row tile overlaps the segment (the diagonal tiles),
+// column blocks entirely above the diagonal are never computed: the FP64 pipe
+// only runs on entries of the lower triangle, padded to 4 x 8 blocks.
 template <typename acc_t, int NR, int NC>
-__device__ __forceinline__ void upd_chunk(const acc_t* __restrict__ As, const acc_t* __restrict__ Bs, int kc, int tx,
-                                          int ty, acc_t (&acc)[4][4]) {
-#pragma unroll 4
+__device__ __forceinline__ void upd_strip(const acc_t* __restrict__ As, const acc_t* __restrict__ Bs, int kc, int r0,
+                                          int lc, acc_t (&acc)[2][8]) {
+#pragma unroll 1
   for (int kk = 0; kk < kc; ++kk) {
-    acc_t av[NR], bv[NC];
+    acc_t av[NR];
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) av[rr] = As[kk * kUpdTileM + ty + 16 * rr];
+    for (int rr = 0; rr < NR; ++rr) av[rr] = As[kk * kUpdTileM + r0 + 4 * rr];
 #pragma unroll
-    for (int cc = 0; cc < NC; ++cc) bv[cc] = Bs[kk * kUpdTileN + tx + 16 * cc];
+    for (int cc = 0; cc < NC; ++cc) {
+      const acc_t bv = Bs[kk * kUpdTileN + lc + 8 * cc];
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr)
-#pragma unroll
-      for (int cc = 0; cc < NC; ++cc) acc[rr][cc] += av[rr] * bv[cc];
+      for (int rr = 0; rr < NR; ++rr) acc[rr][cc] += av[rr] * bv;
+    }
   }
 }
 
 template <typename acc_t, int NR>
-__device__ __forceinline__ void upd_chunk_nc(int nc, const acc_t* As, const acc_t* Bs, int kc, int tx, int ty,
-                                             acc_t (&acc)[4][4]) {
+__device__ __forceinline__ void upd_strip_nc(int nc, const acc_t* As, const acc_t* Bs, int kc, int r0, int lc,
+                                             acc_t (&acc)[2][8]) {
   switch (nc) {
-    case 1: upd_chunk<acc_t, NR, 1>(As, Bs, kc, tx, ty, acc); break;
-    case 2: upd_chunk<acc_t, NR, 2>(As, Bs, kc, tx, ty, acc); break;
-    case 3: upd_chunk<acc_t, NR, 3>(As, Bs, kc, tx, ty, acc); break;
-    default: upd_chunk<acc_t, NR, 4>(As, Bs, kc, tx, ty, acc); break;
+    case 1: upd_strip<acc_t, NR, 1>(As, Bs, kc, r0, lc, acc); break;
+    case 2: upd_strip<acc_t, NR, 2>(As, Bs, kc, r0, lc, acc); break;
+    case 3: upd_strip<acc_t, NR, 3>(As, Bs, kc, r0, lc, acc); break;
+    case 4: upd_strip<acc_t, NR, 4>(As, Bs, kc, r0, lc, acc); break;
+    case 5: upd_strip<acc_t, NR, 5>(As, Bs, kc, r0, lc, acc); break;
+    case 6: upd_strip<acc_t, NR, 6>(As, Bs, kc, r0, lc, acc); break;
+    case 7: upd_strip<acc_t, NR, 7>(As, Bs, kc, r0, lc, acc); break;
+    default: upd_strip<acc_t, NR, 8>(As, Bs, kc, r0, lc, acc); break;
   }
 }
 
 template <typename T>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
-                            bool skip) {
+                            bool skip, int rot) {
   using acc_t = T;
   const int tid = threadIdx.x;
   const int s = u.s, t = u.t;
@@ -305,49 +428,61 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       pos[i] = lo;
       grow[i] = g;
     }
-    const int tx = tid & 15, ty = tid >> 4;
-    const int nrg = (u.rowlen + 15) >> 4;  // 16-row groups in use (1..4)
-    const int mrow = 16 * nrg;
+    // Strip q goes to warp (q + rot) % 8: tiles of fewer than 8 strips load the
+    // four SM sub-partitions (warp % 4) evenly over many tasks, not always the first.
+    const int lane = tid & 31, q = ((tid >> 5) - rot) & 7;
+    const int lr = lane >> 3, lc = lane & 7;
+    const int r0 = 8 * q + lr;                         // first row of this lane
+    const int srows = min(8, u.rowlen - 8 * q);        // valid rows of this warp's strip
+    const int nr = srows > 4 ? 2 : 1;
+    const int off = u.row0 - u.seg0;                   // >= 0: tile row i >= segment column j iff off + i >= j
+    const int si = tid & 63, sk = tid >> 6;            // staging: row/column si, k offsets sk + 4 v
     for (int cb = 0; cb < u.seglen; cb += kUpdTileN) {
       const int ncol = min(kUpdTileN, u.seglen - cb);
-      const int ncg = (ncol + 15) >> 4;
-      const int mcol = 16 * ncg;
+      // column blocks of 8 this warp computes: all of ncol, or up to the diagonal
+      const int dd = off - cb + 8 * q + 7;  // last column any row of the strip needs
+      const int ncb = dd < 0 ? 0 : min((ncol + 7) >> 3, dd / 8 + 1);
+      const bool active = srows > 0 && ncb > 0;
       __syncthreads();
       for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
-      acc_t acc[4][4];
+      acc_t acc[2][8];
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr)
+      for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) acc[rr][cc] = acc_t(0);
+        for (int cc = 0; cc < 8; ++cc) acc[rr][cc] = acc_t(0);
       for (int k0 = 0; k0 < ws; k0 += kUpdKC) {
         const int kc = min(kUpdKC, ws - k0);
         __syncthreads();
-        for (int idx = tid; idx < kc * mrow; idx += blockDim.x) {
-          const int i = idx % mrow, kk = idx / mrow;
-          As[kk * kUpdTileM + i] = (i < u.rowlen) ? (acc_t)ldcg(Ps + (u.row0 + i) + (size_t)(k0 + kk) * lds) : acc_t(0);
-        }
-        for (int idx = tid; idx < kc * mcol; idx += blockDim.x) {
-          const int j = idx % mcol, kk = idx / mcol;
-          Bs[kk * kUpdTileN + j] = (j < ncol) ? (acc_t)ldcg(Ps + (u.seg0 + cb + j) + (size_t)(k0 + kk) * lds) : acc_t(0);
+#pragma unroll
+        for (int v = 0; v < kUpdKC / 4; ++v) {
+          const int kk = sk + 4 * v;
+          if (kk < kc) {
+            const size_t col = (size_t)(k0 + kk) * lds;
+            As[kk * kUpdTileM + si] = (si < u.rowlen) ? (acc_t)ldcg(Ps + (u.row0 + si) + col) : acc_t(0);
+            Bs[kk * kUpdTileN + si] = (si < ncol) ? (acc_t)ldcg(Ps + (u.seg0 + cb + si) + col) : acc_t(0);
+          }
         }
         __syncthreads();
-        switch (nrg) {
-          case 1: upd_chunk_nc<acc_t, 1>(ncg, As, Bs, kc, tx, ty, acc); break;
-          case 2: upd_chunk_nc<acc_t, 2>(ncg, As, Bs, kc, tx, ty, acc); break;
-          case 3: upd_chunk_nc<acc_t, 3>(ncg, As, Bs, kc, tx, ty, acc); break;
-          default: upd_chunk_nc<acc_t, 4>(ncg, As, Bs, kc, tx, ty, acc); break;
+        if (active) {
+          if (nr == 2)
+            upd_strip_nc<acc_t, 2>(ncb, As, Bs, kc, r0, lc, acc);
+          else
+            upd_strip_nc<acc_t, 1>(ncb, As, Bs, kc, r0, lc, acc);
         }
       }
       // Scatter-subtract into panel t: only the lower triangle (row >= column).
+      if (active) {
 #pragma unroll
-      for (int rr = 0; rr < 4; ++rr) {
-        const int i = ty + 16 * rr;
-        if (rr >= nrg || i >= u.rowlen) continue;
+        for (int rr = 0; rr < 2; ++rr) {
+          const int i = r0 + 4 * rr;
+          if (rr >= nr || i >= u.rowlen || pos[i] < 0) continue;
+          T* dst = Pt + pos[i];
+          const int gi = grow[i];
 #pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const int j = tx + 16 * cc;
-          if (cc < ncg && j < ncol && grow[i] >= gcol[j] && pos[i] >= 0)
-            red_add(Pt + pos[i] + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
+          for (int cc = 0; cc < 8; ++cc) {
+            const int j = lc + 8 * cc;
+            if (cc < ncb && j < ncol && gi >= gcol[j]) red_add(dst + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
+          }
         }
       }
     }
@@ -355,8 +490,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
   publish_cta_writes();
   if (tid == 0) {
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-      ring_push_one(q, t);
+      ring2_push_one(rings_of(a), true, t);
     }
   }
 }
@@ -533,8 +667,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
   publish_cta_writes();
   if (tid == 0) {
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-      ring_push_one(q, t);
+      ring2_push_one(rings_of(a), true, t);
     }
   }
 }
@@ -722,8 +855,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
   publish_cta_writes();
   if (tid == 0) {
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-      ring_push_one(q, t);
+      ring2_push_one(rings_of(a), true, t);
     }
   }
 }
@@ -738,9 +870,16 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
-  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
-  // per-CTA task timing (thread 0 only), flushed once at exit
-  unsigned long long busy[4] = {0, 0, 0, 0}, cnt[4] = {0, 0, 0, 0}, wait = 0;  // [3]: tensor-core update tiles
+  const Ring2 q = rings_of(a);
+  __shared__ int pend[2];  // claimed, still empty ring slots (thread 0)
+  if (threadIdx.x == 0) pend[0] = pend[1] = -1;
+  // per-CTA task timing (thread 0 only, in shared memory so that no register
+  // stays live across the tasks), flushed once at exit: [0..3] busy ns per task
+  // type ([3]: tensor-core update tiles), [4..7] counts, [8] wait ns, [9] start
+  // of the current task
+  __shared__ unsigned long long tprof[10];
+  if (threadIdx.x == 0)
+    for (int k = 0; k < 10; ++k) tprof[k] = 0ull;
   // tensor-core state (FP32 panels with mma_mode 1 / 2): TMEM accumulator + mbarrier
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -765,14 +904,15 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
     tc.mbar = smem_addr(&tc_mbar);
   }
   for (;;) {
-    uint64_t t0 = 0, t1 = 0;
     if (threadIdx.x == 0) {
-      if (a.prof) t0 = global_ns();
-      sh.task = ring_claim(q);
+      const bool timed = a.prof || a.trace;
+      const uint64_t t0 = timed ? global_ns() : 0;
+      sh.task = ring2_claim(q, pend);
       sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
-      if (a.prof) {
-        t1 = global_ns();
-        wait += t1 - t0;
+      if (timed) {
+        const uint64_t t1 = global_ns();
+        tprof[8] += t1 - t0;
+        tprof[9] = t1;
       }
     }
     __syncthreads();
@@ -796,39 +936,34 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
           type = 3;
           task_update_oz(a, u, smem_raw, sh, skip, tc);
         } else {
-          task_update<T>(a, u, smem_raw, sh, skip);
+          task_update<T>(a, u, smem_raw, sh, skip, task & 7);
         }
       }
       else if constexpr (MODE == 1)
         task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
       else
-        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip);
+        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, task & 7);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
       if (a.trace) {
-        a.trace[2 * (size_t)task] = t1;
+        a.trace[2 * (size_t)task] = tprof[9];
         a.trace[2 * (size_t)task + 1] = global_ns();
       }
       if (a.prof) {
-        const unsigned long long d = global_ns() - t1;
-#pragma unroll
-        for (int k = 0; k < 4; ++k)
-          if (k == type) {
-            busy[k] += d;
-            cnt[k] += 1;
-          }
+        tprof[type] += global_ns() - tprof[9];
+        tprof[4 + type] += 1;
       }
     }
     __syncthreads();
   }
   if (threadIdx.x == 0 && a.prof) {
     for (int k = 0; k < 3; ++k) {
-      atomicAdd(&a.prof[k], busy[k] + (k == 2 ? busy[3] : 0ull));
-      atomicAdd(&a.prof[4 + k], cnt[k] + (k == 2 ? cnt[3] : 0ull));
+      atomicAdd(&a.prof[k], tprof[k] + (k == 2 ? tprof[3] : 0ull));
+      atomicAdd(&a.prof[4 + k], tprof[4 + k] + (k == 2 ? tprof[7] : 0ull));
     }
-    atomicAdd(&a.prof[3], wait);
-    atomicAdd(&a.prof[7], busy[3]);  // tensor-core share of the update tiles
+    atomicAdd(&a.prof[3], tprof[8]);
+    atomicAdd(&a.prof[7], tprof[3]);  // tensor-core share of the update tiles
   }
   if (use_tc) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -848,7 +983,10 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 }  // namespace
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {
-  size_t tri = ((size_t)max_w * max_w + max_w) * sizeof(double);
+  // POTRF: the block, 1 / l_jj and two scaled columns; TRSM: L11 with 64-row
+  // columns and 1 / l_cc.
+  size_t tri = ((size_t)max_w * max_w + 3 * (size_t)max_w) * sizeof(double);
+  if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 1) * max_w * sizeof(double));
   if (mma_mode == 3) {
     const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);
     const size_t oz = (size_t)kSlices * (kOzM + kOzN) * kpad * 2 + (3 * kOzM + 2 * kOzN) * sizeof(int) + 1024;

@@ -143,10 +143,10 @@ int64_t spchol_plan_len(spchol_plan_t p, int what) {
     case SPCHOL_PLAN_PERM: case SPCHOL_PLAN_COLCOUNT: case SPCHOL_PLAN_ETREE: return P.n;
     case SPCHOL_PLAN_FCOL: case SPCHOL_PLAN_ROWOFF: return P.ns + 1;
     case SPCHOL_PLAN_NROWS: case SPCHOL_PLAN_PARENT: case SPCHOL_PLAN_DEPF: case SPCHOL_PLAN_NTRSM:
-    case SPCHOL_PLAN_NU: case SPCHOL_PLAN_NST: return P.ns;
+    case SPCHOL_PLAN_NU: case SPCHOL_PLAN_NST: case SPCHOL_PLAN_NUHI: return P.ns;
     case SPCHOL_PLAN_ROWS: return (int64_t)P.rows.size();
     case SPCHOL_PLAN_UTASKS: return 6 * (int64_t)P.ut.size();
-    case SPCHOL_PLAN_SCALARS: return 10;
+    case SPCHOL_PLAN_SCALARS: return 11;
     case SPCHOL_PLAN_ADEST: return (int64_t)P.a_dest.size();
     default: return -1;
   }
@@ -172,6 +172,7 @@ int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
     case SPCHOL_PLAN_NTRSM: cp(P.ntrsm); break;
     case SPCHOL_PLAN_NU: cp(P.nu); break;
     case SPCHOL_PLAN_NST: cp(P.nst); break;
+    case SPCHOL_PLAN_NUHI: cp(P.nu_hi); break;
     case SPCHOL_PLAN_ADEST: cp(P.a_dest); break;
     case SPCHOL_PLAN_UTASKS:
       for (size_t i = 0; i < P.ut.size(); ++i) {
@@ -183,6 +184,7 @@ int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
     case SPCHOL_PLAN_SCALARS:
       dst[0] = P.n; dst[1] = P.nnz_l; dst[2] = P.ns; dst[3] = P.n_factor_tasks; dst[4] = P.n_solve_tasks;
       dst[5] = P.max_w; dst[6] = P.max_r; dst[7] = P.nnz_l_stored; dst[8] = P.n_trsm; dst[9] = P.n_u;
+      dst[10] = P.n_hi_tasks;
       break;
     default: return -2;
   }
@@ -204,37 +206,54 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   Rng rng{seed};
   const int ns = P.ns;
 
-  // ---- factorization: same ids and counters as the GPU kernel ----------------
+  // ---- factorization: same ids, counters and two ready rings as the GPU kernel
+  // (high priority: diagonal and panel-solve tasks and the first nu_hi[s]
+  // update tiles of each panel).  Every push is counted against its ring's
+  // size, and each ring must receive exactly as many tasks as it holds.
   std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
   std::vector<char> ran(P.n_factor_tasks, 0);
-  Ready rq;
+  Ready hi, lo;
+  const int64_t n_hi = P.n_hi_tasks, n_lo = (int64_t)P.n_factor_tasks - P.n_hi_tasks;
+  int64_t hi_pushed = 0, lo_pushed = 0;
+  bool overflow = false;
+  auto push = [&](bool to_hi, int t) {
+    if (to_hi) {
+      hi.push(t);
+      overflow |= ++hi_pushed > n_hi;
+    } else {
+      lo.push(t);
+      overflow |= ++lo_pushed > n_lo;
+    }
+  };
   for (int s = 0; s < ns; ++s)
-    if (dep[s] == 0) rq.push(s);
+    if (dep[s] == 0) push(true, s);
   int done = 0;
-  while (!rq.empty()) {
-    const int task = rq.pop(rng);
+  while (!hi.empty() || !lo.empty()) {
+    if (overflow) return SPCHOL_EINTERNAL;
+    const bool from_hi = !hi.empty() && (lo.empty() || (rng.next() & 1));
+    const int task = from_hi ? hi.pop(rng) : lo.pop(rng);
     if (task < 0 || task >= P.n_factor_tasks || ran[task]) return SPCHOL_EINTERNAL;
     ran[task] = 1;
     ++done;
     const bool skip = sim.info != 0;
     if (task < ns) {
       if (!skip) sim.potrf(task);
-      for (int k = 0; k < P.ntrsm[task]; ++k) rq.push(ns + P.trsm_first[task] + k);
+      for (int k = 0; k < P.ntrsm[task]; ++k) push(true, ns + P.trsm_first[task] + k);
     } else if (task < ns + P.n_trsm) {
       const int kt = task - ns, s = P.trsm_sn[kt];
       if (!skip) sim.trsm(s, kt - P.trsm_first[s]);
       if (--tleft[s] < 0) return SPCHOL_EINTERNAL;
       if (tleft[s] == 0)
-        for (int k = 0; k < P.nu[s]; ++k) rq.push(ns + P.n_trsm + P.u_first[s] + k);
+        for (int k = 0; k < P.nu[s]; ++k) push(k < P.nu_hi[s], ns + P.n_trsm + P.u_first[s] + k);
     } else {
       const UTask& u = P.ut[task - ns - P.n_trsm];
       if (!skip) sim.update(u);
       if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
-      if (dep[u.t] == 0) rq.push(u.t);
+      if (dep[u.t] == 0) push(true, u.t);
     }
     if (sim.info < 0) return SPCHOL_EINTERNAL;
   }
-  if (done != P.n_factor_tasks) return SPCHOL_EINTERNAL;
+  if (done != P.n_factor_tasks || overflow || hi_pushed != n_hi || lo_pushed != n_lo) return SPCHOL_EINTERNAL;
   if (Lx) std::memcpy(Lx, sim.pool.data(), sim.pool.size() * sizeof(double));
   if (sim.info != 0) return sim.info;
   if (nrhs <= 0 || P.n == 0) return 0;

@@ -35,7 +35,9 @@ struct FactorArgs {
   const int32_t* u_first;
   const int32_t* nu;
   const UTask* ut;
+  const int32_t* nu_hi;  // leading update tiles of each panel that go to the high-priority ring
   int32_t n_trsm, n_u, ntask, trsm_rows;
+  int32_t n_hi;          // high-priority ring size: ring[0, n_hi); the other ring is ring[n_hi, ntask)
   int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products);
                        // FP64 panels: 0 DFMA update tiles, 3 BF16 tensor cores on 7-way split operands
   uint16_t* slices;    // mode 3: BF16 slices of the rows below each diagonal block
@@ -116,6 +118,6 @@ cudaError_t launch_correct(const double* Y, int64_t ldy, double* X, int64_t ldx,
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                               const int* c2_init, int n2, cudaStream_t st, int* c3 = nullptr,
-                              const int* c3_init = nullptr, int n3 = 0);
+                              const int* c3_init = nullptr, int n3 = 0, int seeds_hi = 0);
 
 }  // namespace spchol

@@ -71,7 +71,12 @@ struct Plan {
   std::vector<int32_t> u_first, nu;
   std::vector<UTask> ut;
   std::vector<int32_t> dep_f;  // update tiles targeting each panel
-  int32_t n_trsm = 0, n_u = 0, n_factor_tasks = 0;
+  // Scheduling priority: diagonal and panel-solve tasks, and the first nu_hi[s]
+  // update tiles of panel s (those into its etree parent, for panels within
+  // top_depth of the root), go to the high-priority ready ring; n_hi_tasks of
+  // them in all.  The remaining update tiles go to the other ring.
+  std::vector<int32_t> nu_hi;
+  int32_t n_trsm = 0, n_u = 0, n_factor_tasks = 0, n_hi_tasks = 0;
 
   // solve tasks
   std::vector<int32_t> st_first, nst, st_sn;

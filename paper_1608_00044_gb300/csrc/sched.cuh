@@ -83,6 +83,102 @@ __device__ __forceinline__ void ring_push_range(const Ring& q, int first, int co
   __syncthreads();
 }
 
+// The factorization's two ready rings.  High priority: diagonal and panel-solve
+// tasks and the update tiles that gate the next diagonal task near the root
+// (the critical path); normal priority: all other update tiles.  An idle CTA
+// takes a visible high-priority task first.  A CTA claims a slot only when the
+// ring shows an unclaimed filled or reserved slot, so it holds a claimed slot
+// that is still empty only after losing a race for the last one, and a ready
+// task never waits behind a busy CTA for longer than such a race.  Every
+// claimed slot is filled eventually (a pusher reserves slots in order, so the
+// lowest claimed empty slot is the next to be filled), and a CTA waiting on a
+// claimed empty slot keeps serving the other ring: no CTA blocks the progress
+// of another.
+struct Ring2 {
+  int* hi;  // n_hi slots, -1 while empty
+  int* lo;  // n_lo slots
+  int n_hi, n_lo;
+  int* ctrl;
+  int64_t budget_ns;
+};
+
+// Thread 0 only.  pend[0..1]: this CTA's claimed, not yet filled slot of each
+// ring (-1 none), kept across calls.  Returns a task id, or -1 when every task
+// has been claimed, another CTA reported an error, or the wait ran out.
+__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend) {
+  const uint64_t t0 = global_ns();
+  const uint64_t max_iter = (uint64_t)(q.budget_ns / 32) + 100000;
+  unsigned backoff = 32;
+  for (uint64_t it = 0;; ++it) {
+    const int2 hi = ld_relaxed_pair(&q.ctrl[kHiHead]);  // (head, tail)
+    if (pend[0] < 0 && hi.x < hi.y && hi.x < q.n_hi) {
+      const int s = atomicAdd(&q.ctrl[kHiHead], 1);
+      pend[0] = s < q.n_hi ? s : -1;
+    }
+    if (pend[0] >= 0) {
+      const int v = ld_acquire(&q.hi[pend[0]]);
+      if (v >= 0) {
+        pend[0] = -1;
+        __threadfence();
+        return v;
+      }
+    }
+    const int2 lo = ld_relaxed_pair(&q.ctrl[kHead]);
+    if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
+      const int s = atomicAdd(&q.ctrl[kHead], 1);
+      pend[1] = s < q.n_lo ? s : -1;
+    }
+    if (pend[1] >= 0) {
+      const int v = ld_acquire(&q.lo[pend[1]]);
+      if (v >= 0) {
+        pend[1] = -1;
+        __threadfence();
+        return v;
+      }
+    }
+    if (pend[0] < 0 && pend[1] < 0 && hi.x >= q.n_hi && lo.x >= q.n_lo) return -1;  // all claimed
+    if (ld_relaxed(&q.ctrl[kErr]) != 0) return -1;
+    if (it > max_iter || (int64_t)(global_ns() - t0) > q.budget_ns) {
+      atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
+      atomicExch(&q.ctrl[kWhere], pend[0] >= 0 ? pend[0] : pend[1]);
+      return -1;
+    }
+    __nanosleep(backoff);
+    if (backoff < 256) backoff <<= 1;
+  }
+}
+
+// Push ready tasks first .. first+count-1 to one ring of a Ring2 (hi: the
+// high-priority one).  Whole CTA; s_base is a shared int.  Same visibility
+// precondition as ring_push_one.
+__device__ __forceinline__ void ring2_push_range(const Ring2& q, bool hi, int first, int count, int* s_base) {
+  if (count <= 0) return;
+  int* tail = &q.ctrl[hi ? kHiTail : kTail];
+  int* slots = hi ? q.hi : q.lo;
+  const int n = hi ? q.n_hi : q.n_lo;
+  if (threadIdx.x == 0) *s_base = atomicAdd(tail, count);
+  __syncthreads();
+  const int base = *s_base;
+  for (int i = threadIdx.x; i < count; i += blockDim.x) {
+    if (base + i < n) {
+      st_release(&slots[base + i], first + i);
+    } else {
+      atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+    }
+  }
+  __syncthreads();
+}
+
+// Thread 0 only: push one ready task to one ring of a Ring2.
+__device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task) {
+  const int slot = atomicAdd(&q.ctrl[hi ? kHiTail : kTail], 1);
+  if (slot < (hi ? q.n_hi : q.n_lo)) {
+    st_release(&(hi ? q.hi : q.lo)[slot], task);
+  } else {
+    atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+  }
+}
+
 // Make this CTA's global writes visible before a counter update or a push.
 __device__ __forceinline__ void publish_cta_writes() {
   __threadfence();
@@ -91,8 +187,9 @@ __device__ __forceinline__ void publish_cta_writes() {
 }
 
 // Reset kernel: ring slots to -1 with the seed tasks in front, counters from
-// their initial copies, control words.
-__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int* ctrl,
+// their initial copies, control words.  seeds_hi: the seeds fill the front of
+// a Ring2's high-priority ring (slots[0, n_hi)) instead of a single ring.
+__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seeds_hi, int* ctrl,
                                   int* c0, const int* c0_init, int n0, int* c1, const int* c1_init,
                                   int n1, int* c2, const int* c2_init, int n2, int* c3,
                                   const int* c3_init, int n3);

@@ -336,8 +336,8 @@ cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t 
 }
 
 // ---------------------------------------------------------------- ring reset
-__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
-                                  const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
+__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seeds_hi, int* ctrl,
+                                  int* c0, const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                                   const int* c2_init, int n2, int* c3, const int* c3_init, int n3) {
   const int stride = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
@@ -346,15 +346,13 @@ __global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int n
   for (int i = tid; i < n1; i += stride) c1[i] = c1_init[i];
   for (int i = tid; i < n2; i += stride) c2[i] = c2_init[i];
   for (int i = tid; i < n3; i += stride) c3[i] = c3_init[i];
-  if (tid == 0) {
-    ctrl[kHead] = 0;
-    ctrl[kTail] = nseed;
-    ctrl[kErr] = 0;
-    ctrl[kInfo] = INT_MAX;
-    ctrl[kDone] = 0;
-    ctrl[kWhere] = -1;
-    ctrl[6] = 0;
-    ctrl[7] = 0;
+  if (tid < kCtrlWords) {  // one thread per control word
+    int v = 0;
+    if (tid == kTail) v = seeds_hi ? 0 : nseed;
+    if (tid == kHiTail) v = seeds_hi ? nseed : 0;
+    if (tid == kInfo) v = INT_MAX;
+    if (tid == kWhere) v = -1;
+    ctrl[tid] = v;
   }
 }
 
@@ -394,14 +392,15 @@ cudaError_t noalloc_scratch(int device, void** ptr) {
 
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
-                              const int* c2_init, int n2, cudaStream_t st, int* c3, const int* c3_init, int n3) {
-  int m = ntask;
+                              const int* c2_init, int n2, cudaStream_t st, int* c3, const int* c3_init, int n3,
+                              int seeds_hi) {
+  int m = ntask > kCtrlWords ? ntask : kCtrlWords;
   if (n0 > m) m = n0;
   if (n1 > m) m = n1;
   if (n2 > m) m = n2;
   if (n3 > m) m = n3;
-  ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, ctrl, c0, c0_init, n0, c1, c1_init,
-                                                 n1, c2, c2_init, n2, c3, c3_init, n3);
+  ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, seeds_hi, ctrl, c0, c0_init, n0, c1,
+                                                 c1_init, n1, c2, c2_init, n2, c3, c3_init, n3);
   return cudaGetLastError();
 }
 

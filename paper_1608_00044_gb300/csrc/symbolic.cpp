@@ -334,6 +334,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.u_first.assign(ns, 0);
   P.nu.assign(ns, 0);
   P.dep_f.assign(ns, 0);
+  P.nu_hi.assign(ns, 0);
   P.trsm_sn.clear();
   P.ut.clear();
   for (int32_t s = 0; s < ns; ++s) {
@@ -358,6 +359,9 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
         P.ut.push_back(UTask{s, t, a, e - a, r0, std::min(TU, r - r0)});
         P.dep_f[t]++;
       }
+      // the first target is the etree parent (it holds the first row below the
+      // diagonal block); near the root its tiles are on the critical path
+      if (a == w && top) P.nu_hi[s] = (int32_t)P.ut.size() - P.u_first[s];
       a = e;
     }
     P.nu[s] = (int32_t)P.ut.size() - P.u_first[s];
@@ -365,6 +369,8 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.n_trsm = (int32_t)P.trsm_sn.size();
   P.n_u = (int32_t)P.ut.size();
   P.n_factor_tasks = ns + P.n_trsm + P.n_u;
+  P.n_hi_tasks = ns + P.n_trsm;
+  for (int32_t s = 0; s < ns; ++s) P.n_hi_tasks += P.nu_hi[s];
 
   // ---- solve tasks ------------------------------------------------------------
   const int TS = std::max(1, prm.solve_rows);

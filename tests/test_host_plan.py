@@ -168,3 +168,29 @@ def test_amalgamation_reduces_panels_within_budget():
     p4 = _plan(A, perm, relax_zeros=4).scalars()
     assert p4["ns"] < p0["ns"]
     assert p4["nnz_l_stored"] >= p4["nnz_l"] == p0["nnz_l"]
+
+
+@pytest.mark.parametrize("name,W", [("lap3d_12", 16), ("diff3d_9", 8), ("lap2d_64", 64)])
+def test_high_priority_tiles_are_parent_tiles_near_the_root(name, W):
+    """The update tiles scheduled with high priority are, for the panels within
+    128 levels of the root, the leading tiles of each panel, exactly those into
+    its etree parent; the ring sizes add up to the task count."""
+    A, perm, b = gridgen.workload(name)
+    P = _plan(A, perm, max_width=W)
+    sc = P.scalars()
+    par = P.get(hp.PARENT)
+    nu, nuhi = P.get(hp.NU), P.get(hp.NUHI)
+    ut = P.get(hp.UTASKS).reshape(-1, 6)
+    ns = len(par)
+    depth = np.zeros(ns, int)
+    for s in range(ns - 1, -1, -1):
+        depth[s] = 0 if par[s] < 0 else depth[par[s]] + 1
+    first = np.concatenate([[0], np.cumsum(nu)])
+    for s in range(ns):
+        tiles = ut[first[s]:first[s + 1]]
+        n_par = int(np.sum(tiles[:, 1] == par[s])) if par[s] >= 0 else 0
+        assert nuhi[s] == (n_par if depth[s] < 128 else 0)
+        assert np.all(tiles[:nuhi[s], 1] == par[s])
+    assert sc["n_hi_tasks"] == ns + sc["n_trsm"] + int(nuhi.sum())
+    assert sc["factor_tasks"] == ns + sc["n_trsm"] + sc["n_u"]
+    assert 0 < sc["n_hi_tasks"] <= sc["factor_tasks"]
