@@ -63,6 +63,7 @@ struct spchol_handle_s {
   int64_t *d_rowoff = nullptr, *d_valoff = nullptr, *d_adest = nullptr;
   int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
   int32_t* d_nu_hi = nullptr;
+  int32_t* d_relpos = nullptr;  // relative row indices of the update tiles
   int32_t* d_trsm_rows = nullptr;
   UTask* d_ut = nullptr;
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
@@ -300,6 +301,8 @@ int setup_device(spchol_handle_t h) {
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
   CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
+  CU(cudaMalloc(&h->d_relpos, std::max<size_t>((size_t)P.n_rel * sizeof(int32_t), 256)));
+  CU(launch_relpos(h->d_ut, P.n_u, h->d_rows, h->d_rowoff, h->d_nrows, h->d_relpos, g_upload_stream));
   if (oz) CU(cudaMalloc(&h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256)));
   CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
   CU(cudaMallocHost(&h->h_prof, 16 * sizeof(unsigned long long)));
@@ -333,6 +336,7 @@ int setup_device(spchol_handle_t h) {
   h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
   h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
+                                       (size_t)P.n_rel * sizeof(int32_t) +
                                        (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0));
   h->stats.grid_factor = h->grid_factor;
   h->stats.grid_solve = h->grid_solve;
@@ -429,6 +433,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.u_first = h->d_u_first;
   a.nu = h->d_nu;
   a.nu_hi = h->d_nu_hi;
+  a.relpos = h->d_relpos;
   a.n_hi = P.n_hi_tasks;
   a.ut = h->d_ut;
   a.n_trsm = P.n_trsm;
@@ -901,6 +906,7 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
   if (h->d_inv) cudaFree(h->d_inv);
+  if (h->d_relpos) cudaFree(h->d_relpos);
   if (h->d_slices) cudaFree(h->d_slices);
   if (h->d_trace_f) cudaFree(h->d_trace_f);
   if (h->d_trace_s) cudaFree(h->d_trace_s);

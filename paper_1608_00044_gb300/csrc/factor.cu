@@ -352,6 +352,42 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
   }
 }
 
+// ---------------------------------------------------------------- relative indices
+// The relative index of row g of panel s in a target panel t is the position
+// of g in t's sorted row list (the relative-index maps of the supernodal
+// update, Section III-A).  They are fixed by the structure, so one kernel at
+// analysis time finds them for every row of every update tile (a binary search
+// each), and an update tile only loads its rowlen of them.
+__device__ __forceinline__ void load_relpos(const FactorArgs& a, const UTask& u, int* pos, int* grow,
+                                            const int32_t* Rs) {
+  for (int i = threadIdx.x; i < u.rowlen; i += blockDim.x) {
+    const int p = __ldg(a.relpos + u.rel + i);
+    if (p < 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // cannot happen for a consistent plan
+    pos[i] = p;
+    grow[i] = __ldg(Rs + u.row0 + i);
+  }
+}
+
+__global__ void relpos_kernel(const UTask* __restrict__ ut, int n_u, const int32_t* __restrict__ rows,
+                              const int64_t* __restrict__ rowoff, const int32_t* __restrict__ nrows,
+                              int32_t* __restrict__ relpos) {
+  for (int k = blockIdx.x; k < n_u; k += gridDim.x) {
+    const UTask u = ut[k];
+    const int32_t* Rs = rows + rowoff[u.s];
+    const int32_t* Rt = rows + rowoff[u.t];
+    const int rt = nrows[u.t];
+    for (int i = threadIdx.x; i < u.rowlen; i += blockDim.x) {
+      const int g = Rs[u.row0 + i];
+      int lo = 0, hi = rt;
+      while (lo < hi) {
+        const int mid = (lo + hi) >> 1;
+        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
+      }
+      relpos[u.rel + i] = (lo < rt && Rt[lo] == g) ? lo : -1;
+    }
+  }
+}
+
 // ---------------------------------------------------------------- UPD(s, t, k)
 // C = A B^T for one tile, A = L_s[row tile] (rowlen x ws), B = L_s[segment]
 // (ncol x ws), staged through shared memory in k-chunks.  Warp q owns the
@@ -413,21 +449,9 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     int* grow = pos + kUpdTileM;                          // [kUpdTileM] global row
     int* gcol = grow + kUpdTileM;                         // [kUpdTileN] global column (pass-local)
 
-    // Relative row indices: each row of the tile located in t's sorted row list.
-    for (int i = tid; i < u.rowlen; i += blockDim.x) {
-      const int g = Rs[u.row0 + i];
-      int lo = 0, hi = rt;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
-      }
-      if (lo >= rt || Rt[lo] != g) {  // cannot happen for a consistent plan
-        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-        lo = -1;
-      }
-      pos[i] = lo;
-      grow[i] = g;
-    }
+    // Relative row indices (computed once per analysis): position of each
+    // row of the tile in t's sorted row list.
+    load_relpos(a, u, pos, grow, Rs);
     // Strip q goes to warp (q + rot) % 8: tiles of fewer than 8 strips load the
     // four SM sub-partitions (warp % 4) evenly over many tasks, not always the first.
     const int lane = tid & 31, q = ((tid >> 5) - rot) & 7;
@@ -574,20 +598,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     int* grow = pos + kTcM;
     int* gcol = grow + kTcM;
 
-    for (int i = tid; i < u.rowlen; i += blockDim.x) {
-      const int g = Rs[u.row0 + i];
-      int lo = 0, hi = rt;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
-      }
-      if (lo >= rt || Rt[lo] != g) {
-        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-        lo = -1;
-      }
-      pos[i] = lo;
-      grow[i] = g;
-    }
+    load_relpos(a, u, pos, grow, Rs);
     // A: tile rows x k (rows >= rowlen and k >= ws are zero)
     for (int idx = tid; idx < kTcM * kpad; idx += blockDim.x) {
       const int i = idx % kTcM, k = idx / kTcM;
@@ -743,21 +754,8 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     const uint32_t sbo = (uint32_t)kpad * 16;  // 8 rows x (kpad bf16) bytes
     const int chunks = kpad / 8;               // 16-byte chunks per row
 
-    for (int i = tid; i < u.rowlen; i += blockDim.x) {
-      const int g = Rs[u.row0 + i];
-      int lo = 0, hi = rt;
-      while (lo < hi) {
-        const int mid = (lo + hi) >> 1;
-        if (Rt[mid] < g) lo = mid + 1; else hi = mid;
-      }
-      if (lo >= rt || Rt[lo] != g) {
-        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-        lo = -1;
-      }
-      pos[i] = lo;
-      grow[i] = g;
-      ea[i] = ldcg(ex + u.row0 + i);
-    }
+    load_relpos(a, u, pos, grow, Rs);
+    for (int i = tid; i < u.rowlen; i += blockDim.x) ea[i] = ldcg(ex + u.row0 + i);
     // A digits: kSlices x rowlen rows x kpad, K-major core matrices (8 rows x
     // 16 bytes).  Rows past rowlen are left as they are: they only feed rows
     // of the product that are never scattered.  Columns past ws are zero in
@@ -1011,6 +1009,17 @@ cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_p
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
+}
+
+cudaError_t launch_relpos(const UTask* ut, int n_u, const int32_t* rows, const int64_t* rowoff,
+                          const int32_t* nrows, int32_t* relpos, cudaStream_t st) {
+  if (n_u <= 0) return cudaSuccess;
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int grid = std::max(1, std::min(n_u, 32 * std::max(sms, 1)));
+  relpos_kernel<<<grid, 64, 0, st>>>(ut, n_u, rows, rowoff, nrows, relpos);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz, void* pool,

@@ -35,6 +35,7 @@ struct FactorArgs {
   const int32_t* u_first;
   const int32_t* nu;
   const UTask* ut;
+  const int32_t* relpos;  // relative row indices of the update tiles (UTask::rel)
   const int32_t* nu_hi;  // leading update tiles of each panel that go to the high-priority ring
   int32_t n_trsm, n_u, ntask, trsm_rows;
   int32_t n_hi;          // high-priority ring size: ring[0, n_hi); the other ring is ring[n_hi, ntask)
@@ -115,6 +116,8 @@ cudaError_t launch_correct(const double* Y, int64_t ldy, double* X, int64_t ldx,
                            int nrhs, cudaStream_t st);
 
 // sched.cu
+cudaError_t launch_relpos(const UTask* ut, int n_u, const int32_t* rows, const int64_t* rowoff,
+                          const int32_t* nrows, int32_t* relpos, cudaStream_t st);
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                               const int* c2_init, int n2, cudaStream_t st, int* c3 = nullptr,

@@ -17,6 +17,7 @@ constexpr int kSliceBits = 8;
 // target panel t's columns (Section III-A, task U; Section IV, task T_{s,t}).
 struct UTask {
   int32_t s, t, seg0, seglen, row0, rowlen;
+  int64_t rel;  // offset of the tile's relative row indices (rowlen of them) in the relative-index array
 };
 
 struct PlanParams {
@@ -71,6 +72,7 @@ struct Plan {
   std::vector<int32_t> u_first, nu;
   std::vector<UTask> ut;
   std::vector<int32_t> dep_f;  // update tiles targeting each panel
+  int64_t n_rel = 0;           // relative row indices of all update tiles (sum of rowlen)
   // Scheduling priority: diagonal and panel-solve tasks, and the first nu_hi[s]
   // update tiles of panel s (those into its etree parent, for panels within
   // top_depth of the root), go to the high-priority ready ring; n_hi_tasks of

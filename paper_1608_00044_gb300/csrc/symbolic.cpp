@@ -337,6 +337,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.nu_hi.assign(ns, 0);
   P.trsm_sn.clear();
   P.ut.clear();
+  P.n_rel = 0;
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
     const int32_t nb = r - w;
@@ -356,7 +357,9 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       int32_t e = a;
       while (e < r && R[e] < P.fcol[t + 1]) ++e;
       for (int32_t r0 = a; r0 < r; r0 += TU) {
-        P.ut.push_back(UTask{s, t, a, e - a, r0, std::min(TU, r - r0)});
+        const int32_t len = std::min(TU, r - r0);
+        P.ut.push_back(UTask{s, t, a, e - a, r0, len, P.n_rel});
+        P.n_rel += len;
         P.dep_f[t]++;
       }
       // the first target is the etree parent (it holds the first row below the
