@@ -35,6 +35,8 @@ struct FactorShared {
   int base;
 };
 
+__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
 __device__ __forceinline__ Ring2 rings_of(const FactorArgs& a) {
   return Ring2{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
 }
@@ -397,17 +399,69 @@ __global__ void relpos_kernel(const UTask* __restrict__ ut, int n_u, const int32
 // past ncol and, where the row tile overlaps the segment (the diagonal tiles),
 // column blocks entirely above the diagonal are never computed: the FP64 pipe
 // only runs on entries of the lower triangle, padded to 4 x 8 blocks.
+// Operand staging.  A k-column of the tile (rows row0 .. row0 + len - 1 of one
+// column of panel s) is copied in 16-byte pieces by cp.async (L2 only, no
+// register round trip), starting at the 16-byte boundary at or below row0:
+// the rows sit at offset row0 % E (E = 16 / sizeof(T)) of a shared-memory row
+// of kStageStr elements.  A piece that would reach past the column's padded
+// length ld is shortened to the elements inside it (the rest zero-filled), so
+// no copy leaves the panel's storage.
+template <typename T>
+struct Stage {
+  static constexpr int E = 16 / (int)sizeof(T);
+  static constexpr int kStr = kUpdTileM + E;  // row stride, a multiple of E
+  static constexpr int kPieces = (kUpdTileM + E - 1) / E + 1;  // pieces per k-column, worst alignment
+};
+
+template <typename T>
+__device__ __forceinline__ void cp_async16(T* dst, const T* src, int valid_elems) {
+  const int bytes = valid_elems * (int)sizeof(T);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;" ::"r"(smem_addr(dst)), "l"(src), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// Issue the copies of k-columns k0 .. k0 + kc - 1 of rows r0 .. r0 + len - 1 of
+// a panel (column-major, leading dimension ld) into dst[kk][...].
+template <typename T>
+__device__ __forceinline__ void stage_cols(const T* __restrict__ P, int ld, int r0, int len, int k0, int kc,
+                                           T* __restrict__ dst) {
+  constexpr int E = Stage<T>::E, NP = Stage<T>::kPieces, STR = Stage<T>::kStr;
+  const int base = r0 - (r0 % E);
+  const int np = (r0 % E + len + E - 1) / E;  // pieces that cover the rows
+  for (int idx = threadIdx.x; idx < kc * NP; idx += blockDim.x) {
+    const int kk = idx / NP, pc = idx - kk * NP;
+    if (pc < np) {
+      const int row = base + pc * E;
+      const int valid = min(E, ld - row);
+      cp_async16(dst + kk * STR + pc * E, P + row + (size_t)(k0 + kk) * ld, valid);
+    }
+  }
+}
+
+// C = A B^T for one tile, A = L_s[row tile] (rowlen x ws), B = L_s[segment]
+// (ncol x ws), staged through shared memory in k-chunks, double-buffered (the
+// copies of chunk c + 1 are in flight while chunk c is multiplied).  Warp q owns
+// the 8-row strip [8q, 8q + 8) of C; lane (lr, lc) = (lane / 8, lane % 8) holds
+// rows 8q + lr + 4 rr (rr < NR) and columns lc + 8 cc (cc < NC).  Strips past
+// rowlen, the second half of a strip with at most 4 valid rows, column blocks
+// past ncol and, where the row tile overlaps the segment (the diagonal tiles),
+// column blocks entirely above the diagonal are never computed: the FP64 pipe
+// only runs on entries of the lower triangle, padded to 4 x 8 blocks.
 template <typename acc_t, int NR, int NC>
 __device__ __forceinline__ void upd_strip(const acc_t* __restrict__ As, const acc_t* __restrict__ Bs, int kc, int r0,
                                           int lc, acc_t (&acc)[2][8]) {
+  constexpr int STR = Stage<acc_t>::kStr;
 #pragma unroll 1
   for (int kk = 0; kk < kc; ++kk) {
     acc_t av[NR];
 #pragma unroll
-    for (int rr = 0; rr < NR; ++rr) av[rr] = As[kk * kUpdTileM + r0 + 4 * rr];
+    for (int rr = 0; rr < NR; ++rr) av[rr] = As[kk * STR + r0 + 4 * rr];
 #pragma unroll
     for (int cc = 0; cc < NC; ++cc) {
-      const acc_t bv = Bs[kk * kUpdTileN + lc + 8 * cc];
+      const acc_t bv = Bs[kk * STR + lc + 8 * cc];
 #pragma unroll
       for (int rr = 0; rr < NR; ++rr) acc[rr][cc] += av[rr] * bv;
     }
@@ -433,19 +487,19 @@ template <typename T>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
                             bool skip, int rot) {
   using acc_t = T;
+  constexpr int STR = Stage<T>::kStr, E = Stage<T>::E;
   const int tid = threadIdx.x;
   const int s = u.s, t = u.t;
   if (!skip) {
     const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, lds = a.pv.ld[s];
-    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
+    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t];
     const T* Ps = panel_ptr<T>(a, s);
     T* Pt = panel_ptr<T>(a, t);
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
-    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
 
-    acc_t* As = reinterpret_cast<acc_t*>(smraw);          // [kUpdKC][kUpdTileM]
-    acc_t* Bs = As + kUpdKC * kUpdTileM;                  // [kUpdKC][kUpdTileN]
-    int* pos = reinterpret_cast<int*>(Bs + kUpdKC * kUpdTileN);  // [kUpdTileM] row position in t
+    T* buf = reinterpret_cast<T*>(smraw);                 // [2][A, B][kUpdKC][STR]
+    constexpr int kBuf = 2 * kUpdKC * STR;                // one buffer: A and B chunks
+    int* pos = reinterpret_cast<int*>(buf + 2 * kBuf);    // [kUpdTileM] row position in t
     int* grow = pos + kUpdTileM;                          // [kUpdTileM] global row
     int* gcol = grow + kUpdTileM;                         // [kUpdTileN] global column (pass-local)
 
@@ -456,49 +510,58 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     // four SM sub-partitions (warp % 4) evenly over many tasks, not always the first.
     const int lane = tid & 31, q = ((tid >> 5) - rot) & 7;
     const int lr = lane >> 3, lc = lane & 7;
-    const int r0 = 8 * q + lr;                         // first row of this lane
     const int srows = min(8, u.rowlen - 8 * q);        // valid rows of this warp's strip
     const int nr = srows > 4 ? 2 : 1;
     const int off = u.row0 - u.seg0;                   // >= 0: tile row i >= segment column j iff off + i >= j
-    const int si = tid & 63, sk = tid >> 6;            // staging: row/column si, k offsets sk + 4 v
+    const int oa = u.row0 % E;                         // row offset of the A rows in shared memory
+    const int r0 = oa + 8 * q + lr;                    // this lane's first A row in shared memory
+    const int nchunk = (ws + kUpdKC - 1) / kUpdKC;
     for (int cb = 0; cb < u.seglen; cb += kUpdTileN) {
       const int ncol = min(kUpdTileN, u.seglen - cb);
-      // column blocks of 8 this warp computes: all of ncol, or up to the diagonal
+      const int c0 = u.seg0 + cb;
+      const int ob = c0 % E;
       const int dd = off - cb + 8 * q + 7;  // last column any row of the strip needs
       const int ncb = dd < 0 ? 0 : min((ncol + 7) >> 3, dd / 8 + 1);
       const bool active = srows > 0 && ncb > 0;
-      __syncthreads();
-      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
+      __syncthreads();  // the previous pass is done with the buffers and gcol
+      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[c0 + j];
       acc_t acc[2][8];
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) acc[rr][cc] = acc_t(0);
-      for (int k0 = 0; k0 < ws; k0 += kUpdKC) {
-        const int kc = min(kUpdKC, ws - k0);
-        __syncthreads();
-#pragma unroll
-        for (int v = 0; v < kUpdKC / 4; ++v) {
-          const int kk = sk + 4 * v;
-          if (kk < kc) {
-            const size_t col = (size_t)(k0 + kk) * lds;
-            As[kk * kUpdTileM + si] = (si < u.rowlen) ? (acc_t)ldcg(Ps + (u.row0 + si) + col) : acc_t(0);
-            Bs[kk * kUpdTileN + si] = (si < ncol) ? (acc_t)ldcg(Ps + (u.seg0 + cb + si) + col) : acc_t(0);
-          }
+      // chunk 0 into buffer 0
+      stage_cols(Ps, lds, u.row0, u.rowlen, 0, min(kUpdKC, ws), buf);
+      stage_cols(Ps, lds, c0, ncol, 0, min(kUpdKC, ws), buf + kUpdKC * STR);
+      cp_async_commit();
+      for (int c = 0; c < nchunk; ++c) {
+        const int k0 = c * kUpdKC, kc = min(kUpdKC, ws - k0);
+        if (c + 1 < nchunk) {
+          T* nb = buf + ((c + 1) & 1) * kBuf;
+          const int k1 = k0 + kUpdKC, kc1 = min(kUpdKC, ws - k1);
+          stage_cols(Ps, lds, u.row0, u.rowlen, k1, kc1, nb);
+          stage_cols(Ps, lds, c0, ncol, k1, kc1, nb + kUpdKC * STR);
+          cp_async_commit();
+          cp_async_wait<1>();  // chunk c has landed (this thread's copies)
+        } else {
+          cp_async_wait<0>();
         }
-        __syncthreads();
+        __syncthreads();       // ... and every thread's
         if (active) {
+          const T* As = buf + (c & 1) * kBuf;
+          const T* Bs = As + kUpdKC * STR + ob;
           if (nr == 2)
             upd_strip_nc<acc_t, 2>(ncb, As, Bs, kc, r0, lc, acc);
           else
             upd_strip_nc<acc_t, 1>(ncb, As, Bs, kc, r0, lc, acc);
         }
+        __syncthreads();  // buffer c & 1 is refilled by the next iteration's copies
       }
       // Scatter-subtract into panel t: only the lower triangle (row >= column).
       if (active) {
 #pragma unroll
         for (int rr = 0; rr < 2; ++rr) {
-          const int i = r0 + 4 * rr;
+          const int i = 8 * q + lr + 4 * rr;
           if (rr >= nr || i >= u.rowlen || pos[i] < 0) continue;
           T* dst = Pt + pos[i];
           const int gi = grow[i];
@@ -534,7 +597,6 @@ struct TcState {
   uint32_t phase;  // parity of the next completion
 };
 
-__device__ __forceinline__ uint32_t smem_addr(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
 // Shared-memory matrix descriptor: K-major, no swizzle; LBO = byte distance of
 // K-adjacent core matrices, SBO = byte distance of row-adjacent core matrices.
@@ -901,11 +963,21 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kern
     tc.tmem = tc_tmem;
     tc.mbar = smem_addr(&tc_mbar);
   }
+  // Thread 0: a normal-priority slot claimed ahead while the ring is deep, so
+  // that the claim's round trip overlaps the current task; it joins pend[1] at
+  // the next claim (a deep ring fills it long before).
+  int ahead = -1;
   for (;;) {
     if (threadIdx.x == 0) {
       const bool timed = a.prof || a.trace;
       const uint64_t t0 = timed ? global_ns() : 0;
-      sh.task = ring2_claim(q, pend);
+      if (ahead >= 0) {
+        pend[1] = ahead < q.n_lo ? ahead : -1;
+        ahead = -1;
+      }
+      int lo_ready;
+      sh.task = ring2_claim(q, pend, &lo_ready);
+      if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
       sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
       if (timed) {
         const uint64_t t1 = global_ns();
@@ -994,7 +1066,7 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
     const size_t tcb = 2 * (kTcM + kTcN) * kpad * 4 + (2 * kTcM + kTcN) * sizeof(int) + 1024;
     if (tcb > tri) tri = tcb;
   }
-  size_t upd = (size_t)kUpdKC * (kUpdTileM + kUpdTileN) * sizeof(double) +
+  size_t upd = (size_t)4 * kUpdKC * Stage<double>::kStr * sizeof(double) +
                (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
   return tri > upd ? tri : upd;
 }

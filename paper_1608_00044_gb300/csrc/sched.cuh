@@ -105,7 +105,10 @@ struct Ring2 {
 // Thread 0 only.  pend[0..1]: this CTA's claimed, not yet filled slot of each
 // ring (-1 none), kept across calls.  Returns a task id, or -1 when every task
 // has been claimed, another CTA reported an error, or the wait ran out.
-__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend) {
+// *lo_ready: unclaimed slots of the normal-priority ring at the last look (0
+// if the task came from the high-priority ring before the other was read).
+__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_ready) {
+  *lo_ready = 0;
   const uint64_t t0 = global_ns();
   const uint64_t max_iter = (uint64_t)(q.budget_ns / 32) + 100000;
   unsigned backoff = 32;
@@ -124,6 +127,7 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend) {
       }
     }
     const int2 lo = ld_relaxed_pair(&q.ctrl[kHead]);
+    *lo_ready = lo.y - lo.x;
     if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
       const int s = atomicAdd(&q.ctrl[kHead], 1);
       pend[1] = s < q.n_lo ? s : -1;
