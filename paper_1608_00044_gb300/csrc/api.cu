@@ -69,7 +69,7 @@ struct spchol_handle_s {
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
   int32_t *d_fseeds = nullptr;
   int nfseeds = 0;
-  int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
+  int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_st_rows = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
   int32_t *d_st_tptr = nullptr, *d_st_tgt = nullptr, *d_rt_ptr = nullptr, *d_rt_tile = nullptr;
   int32_t *d_fdep0 = nullptr, *d_bdep0 = nullptr, *d_bdep = nullptr;
@@ -164,7 +164,7 @@ int setup_device(spchol_handle_t h) {
   for (int s = 0; s < ns; ++s)
     if (P.dep_f[s] == 0) fseeds.push_back(s);
   size_t o_fseeds = r32(fseeds.size());
-  size_t o_stf = r32(ns), o_nst = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
+  size_t o_stf = r32(ns), o_nst = r32(ns), o_strows = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
     nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
@@ -246,6 +246,7 @@ int setup_device(spchol_handle_t h) {
   h->d_st_first = (int32_t*)(b + o_stf);
   h->d_nst = (int32_t*)(b + o_nst);
   h->d_st_sn = (int32_t*)(b + o_stsn);
+  h->d_st_rows = (int32_t*)(b + o_strows);
   h->d_kid_ptr = (int32_t*)(b + o_kp);
   h->d_kids = (int32_t*)(b + o_k);
   h->d_nkids_init = (int32_t*)(b + o_nki);
@@ -290,6 +291,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
+      (rc = upload(h, h->d_st_rows, P.st_rows)) ||
       (rc = upload(h, h->d_kid_ptr, P.kid_ptr)) || (rc = upload(h, h->d_kids, P.kids)) ||
       (rc = upload(h, h->d_nkids_init, nkids)) || (rc = upload(h, h->d_sseeds, sseeds)) ||
       (rc = upload(h, h->d_st_tptr, P.st_tptr)) || (rc = upload(h, h->d_st_tgt, P.st_tgt)) ||
@@ -510,9 +512,10 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
 int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   Plan& P = h->plan;
   if (P.ns == 0 || nrhs == 0) return 0;
+  const int n_hi = P.n_solve_tasks - h->nsseeds;  // seeds: the normal-priority ring, after the other
   CU(launch_ring_reset(h->d_ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, h->d_ctrl, h->d_fkids, h->d_fdep0,
                        P.ns, h->d_ftiles, h->d_nst, P.ns, h->d_btiles, h->d_nst, P.ns, st, h->d_bdep, h->d_bdep0,
-                       P.n_st));
+                       P.n_st, /*seeds_hi=*/0, /*seed_off=*/n_hi));
   SolveArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
   a.kid_ptr = h->d_kid_ptr;
@@ -522,7 +525,8 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.st_sn = h->d_st_sn;
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
-  a.solve_rows = P.params.solve_rows;
+  a.st_rows = h->d_st_rows;
+  a.n_hi = P.n_solve_tasks - h->nsseeds;
   a.st_tptr = h->d_st_tptr;
   a.st_tgt = h->d_st_tgt;
   a.rt_ptr = h->d_rt_ptr;
@@ -792,7 +796,8 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   // the array keeps the previous call's contents: the reset kernel re-initialises
   // the ring, the counters and the control words before every launch
   CU(launch_ring_reset(ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, ctrl, fdep, h->d_fdep0, P.ns, ftiles,
-                       h->d_nst, P.ns, btiles, h->d_nst, P.ns, st, bdep, h->d_bdep0, P.n_st));
+                       h->d_nst, P.ns, btiles, h->d_nst, P.ns, st, bdep, h->d_bdep0, P.n_st, /*seeds_hi=*/0,
+                       /*seed_off=*/P.n_solve_tasks - h->nsseeds));
   CU(launch_permute_in(B, ldb, Y, n, h->d_perm, n, nrhs, st));
   SolveArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
@@ -803,7 +808,8 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.st_sn = h->d_st_sn;
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
-  a.solve_rows = P.params.solve_rows;
+  a.st_rows = h->d_st_rows;
+  a.n_hi = P.n_solve_tasks - h->nsseeds;
   a.st_tptr = h->d_st_tptr;
   a.st_tgt = h->d_st_tgt;
   a.rt_ptr = h->d_rt_ptr;

@@ -64,7 +64,9 @@ struct SolveArgs {
   const int32_t* st_first;
   const int32_t* nst;
   const int32_t* st_sn;
-  int32_t n_st, ntask, solve_rows;
+  int32_t n_st, ntask;
+  const int32_t* st_rows;  // solve tile rows per panel
+  int32_t n_hi;            // tasks made ready by other tasks: ring[0, n_hi); the seeds: ring[n_hi, ntask)
   const int32_t* st_tptr;  // solve tile -> panels its rows fall in (CSR)
   const int32_t* st_tgt;
   const int32_t* rt_ptr;   // panel -> solve tiles whose rows fall in it (CSR)
@@ -121,6 +123,6 @@ cudaError_t launch_relpos(const UTask* ut, int n_u, const int32_t* rows, const i
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                               const int* c2_init, int n2, cudaStream_t st, int* c3 = nullptr,
-                              const int* c3_init = nullptr, int n3 = 0, int seeds_hi = 0);
+                              const int* c3_init = nullptr, int n3 = 0, int seeds_hi = 0, int seed_off = 0);
 
 }  // namespace spchol

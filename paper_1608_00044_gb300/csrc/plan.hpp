@@ -32,6 +32,7 @@ struct PlanParams {
   int top_depth = 128;
   int top_tile_rows = 16;
   int top_trsm_rows = 32;
+  int top_solve_rows = 64;  // rows per triangular-solve tile of those panels
   // Tensor-core update tiles: source panels at least tc_min_width wide (0 =
   // none) use tc_tile_rows-row tiles (one MMA M-tile) on the tensor cores.
   int tc_min_width = 0;
@@ -81,7 +82,7 @@ struct Plan {
   int32_t n_trsm = 0, n_u = 0, n_factor_tasks = 0, n_hi_tasks = 0;
 
   // solve tasks
-  std::vector<int32_t> st_first, nst, st_sn;
+  std::vector<int32_t> st_first, nst, st_sn, st_rows;  // st_rows: solve tile rows per panel
   std::vector<int32_t> kid_ptr, kids;  // panel children, CSR
   // precise solve dependencies: the panels whose columns each solve tile's rows
   // fall in (tile -> targets, CSR), the same relation reversed (panel -> tiles),

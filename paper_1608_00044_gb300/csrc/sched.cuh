@@ -190,10 +190,13 @@ __device__ __forceinline__ void publish_cta_writes() {
   if (threadIdx.x == 0) __threadfence();
 }
 
-// Reset kernel: ring slots to -1 with the seed tasks in front, counters from
-// their initial copies, control words.  seeds_hi: the seeds fill the front of
-// a Ring2's high-priority ring (slots[0, n_hi)) instead of a single ring.
-__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seeds_hi, int* ctrl,
+// Reset kernel: ring slots to -1 with the seed tasks at slots[seed_off ..],
+// counters from their initial copies, control words.  seeds_hi: the seeds
+// fill the front of a Ring2's high-priority ring (seed_off 0); otherwise they
+// fill the front of a single ring (seed_off 0) or of a Ring2's normal-priority
+// ring (seed_off = n_hi).
+__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seed_off, int seeds_hi,
+                                  int* ctrl,
                                   int* c0, const int* c0_init, int n0, int* c1, const int* c1_init,
                                   int n1, int* c2, const int* c2_init, int n2, int* c3,
                                   const int* c3_init, int n3);

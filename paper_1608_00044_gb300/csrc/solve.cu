@@ -37,14 +37,37 @@ __device__ __forceinline__ const T* spanel(const SolveArgs& a, int s) {
   return reinterpret_cast<const T*>(a.pool) + a.pv.valoff[s];
 }
 
+// L11^{-1} (w x w, column-major, read-only here) into shared memory with
+// leading dimension lx, the lower triangle only; loads in batches of 8.
+__device__ __forceinline__ void stage_inverse(const double* __restrict__ X, int w, double* __restrict__ Xs, int lx) {
+  const int total = w * w, nt = blockDim.x;
+  for (int base = threadIdx.x; base < total; base += 8 * nt) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nt, i = idx % w, j = idx / w;
+      v[u] = (idx < total && i >= j) ? X[idx] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * nt, i = idx % w, j = idx / w;
+      if (idx < total) Xs[i + j * lx] = v[u];
+    }
+  }
+}
+
 // y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
 // every entry is an independent dot product, no sequential substitution.
+// Thread (r, c) computes rows c and w - 1 - c for right-hand side r: i + 1
+// and w - i terms, w + 1 in all, so every thread and warp does the same work.
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
-  double* Xs = sm;          // [w][w] column-major, lower part
-  double* Ys = sm + w * w;  // [nrc][w]
-  stage_lower<false>(X, w, w, Xs);
+  const int lx = w + 1;           // padded: lanes that walk a row or a column both avoid bank conflicts
+  double* Xs = sm;                // [w][lx] column-major, lower part
+  double* Ys = sm + w * lx;       // [nrc][w]
+  stage_inverse(X, w, Xs, lx);
+  const int half = (w + 1) >> 1;
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -53,28 +76,41 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < w * nrc; p += blockDim.x) {
-      const int i = p % w, r = p / w;
+    for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
+      const int c = p % half, r = p / half;
       const double* y = Ys + r * w;
-      double a0 = 0.0, a1 = 0.0;
+      const int i1 = c, i2 = w - 1 - c;
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
       int k = 0;
-      for (; k + 1 <= i; k += 2) {
-        a0 += Xs[i + k * w] * y[k];
-        a1 += Xs[i + (k + 1) * w] * y[k + 1];
+      for (; k + 1 <= i1; k += 2) {
+        a0 += Xs[i1 + k * lx] * y[k];
+        a1 += Xs[i1 + (k + 1) * lx] * y[k + 1];
       }
-      if (k <= i) a0 += Xs[i + k * w] * y[k];
-      a.Y[f + i + (size_t)(r0 + r) * a.ldy] = a0 + a1;
+      if (k <= i1) a0 += Xs[i1 + k * lx] * y[k];
+      if (i2 != i1) {
+        for (k = 0; k + 1 <= i2; k += 2) {
+          b0 += Xs[i2 + k * lx] * y[k];
+          b1 += Xs[i2 + (k + 1) * lx] * y[k + 1];
+        }
+        if (k <= i2) b0 += Xs[i2 + k * lx] * y[k];
+      }
+      a.Y[f + i1 + (size_t)(r0 + r) * a.ldy] = a0 + a1;
+      if (i2 != i1) a.Y[f + i2 + (size_t)(r0 + r) * a.ldy] = b0 + b1;
     }
   }
 }
 
-// x_s <- L11^{-T} y_s with the stored inverse.
+// x_s <- L11^{-T} y_s with the stored inverse: entry k is the dot product of
+// column k of L11^{-1} (rows k .. w-1) with y_s; thread (r, c) takes columns c
+// and w - 1 - c.
 __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
+  const int lx = w + 1;
   double* Xs = sm;
-  double* Ys = sm + w * w;
-  stage_lower<false>(X, w, w, Xs);
+  double* Ys = sm + w * lx;
+  stage_inverse(X, w, Xs, lx);
+  const int half = (w + 1) >> 1;
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -83,53 +119,93 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     __syncthreads();
-    for (int p = threadIdx.x; p < w * nrc; p += blockDim.x) {
-      const int kcol = p % w, r = p / w;
+    for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
+      const int c = p % half, r = p / half;
       const double* y = Ys + r * w;
-      const double* xc = Xs + kcol * w;  // column kcol of L11^{-1}: rows kcol..w-1
-      double a0 = 0.0, a1 = 0.0;
-      int i = kcol;
+      const int k1 = c, k2 = w - 1 - c;
+      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
+      const double* x1 = Xs + k1 * lx;
+      int i = k1;
       for (; i + 1 < w; i += 2) {
-        a0 += xc[i] * y[i];
-        a1 += xc[i + 1] * y[i + 1];
+        a0 += x1[i] * y[i];
+        a1 += x1[i + 1] * y[i + 1];
       }
-      if (i < w) a0 += xc[i] * y[i];
-      a.Y[f + kcol + (size_t)(r0 + r) * a.ldy] = a0 + a1;
+      if (i < w) a0 += x1[i] * y[i];
+      if (k2 != k1) {
+        const double* x2 = Xs + k2 * lx;
+        for (i = k2; i + 1 < w; i += 2) {
+          b0 += x2[i] * y[i];
+          b1 += x2[i + 1] * y[i + 1];
+        }
+        if (i < w) b0 += x2[i] * y[i];
+      }
+      a.Y[f + k1 + (size_t)(r0 + r) * a.ldy] = a0 + a1;
+      if (k2 != k1) a.Y[f + k2 + (size_t)(r0 + r) * a.ldy] = b0 + b1;
     }
   }
 }
 
-// y[rows of tile] -= L21[tile] y_s, one row per thread.
+// y[rows of tile] -= L21[tile] y_s.  A thread owns one row and NPER of the
+// right-hand sides, g + G q (q < NPER) for its group g of G: with 8
+// right-hand sides, four groups of 64 threads take two each (every warp busy on
+// the 64-row tiles near the root); with one, all threads take rows.  The group
+// is uniform in a warp and the right-hand sides a thread owns are fixed at
+// compile time, so no FMA is spent on another group's right-hand sides.
+template <typename T, int NPER>
+__device__ void fwd_tile_rows(const SolveArgs& a, const T* P, int ld, int row0, int cnt, const int32_t* R, int w,
+                              const double* Ys, int r0, int nrc, int G) {
+  const int rows_per = blockDim.x / G;
+  const int g = threadIdx.x / rows_per, il = threadIdx.x - g * rows_per;
+  int nv = 0;  // right-hand sides of this thread that exist
+#pragma unroll
+  for (int q = 0; q < NPER; ++q) nv += (g + G * q < nrc) ? 1 : 0;
+  if (nv == 0) return;
+  for (int i = il; i < cnt; i += rows_per) {
+    const T* Pi = P + row0 + i;
+    double acc[NPER];
+#pragma unroll
+    for (int q = 0; q < NPER; ++q) acc[q] = 0.0;
+    // the row's entries in batches of 8 independent loads, so that their
+    // latencies overlap instead of following one another
+    for (int j0 = 0; j0 < w; j0 += 8) {
+      double l[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) l[u] = (j0 + u < w) ? (double)Pi[(size_t)(j0 + u) * ld] : 0.0;
+      const int nu = min(8, w - j0);
+      for (int u = 0; u < nu; ++u) {
+#pragma unroll
+        for (int q = 0; q < NPER; ++q) acc[q] += l[u] * Ys[j0 + u + (g + G * q) * w];
+      }
+    }
+    const int gr = R[row0 + i];
+#pragma unroll
+    for (int q = 0; q < NPER; ++q)
+      if (q < nv) red_add(a.Y + gr + (size_t)(r0 + g + G * q) * a.ldy, -acc[q]);
+  }
+}
+
 template <typename T>
 __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
-  const int row0 = w + k * a.solve_rows, cnt = min(a.solve_rows, r - row0);
+  const int ts = a.st_rows[s];
+  const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
-  double* Ys = sm;  // [nrc][w]
+  double* Ys = sm;  // [kSolveNRC][w], zero past nrc
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
-    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+    for (int idx = threadIdx.x; idx < w * kSolveNRC; idx += blockDim.x) {
       const int j = idx % w, rr = idx / w;
-      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy);
+      Ys[idx] = rr < nrc ? ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy) : 0.0;
     }
     __syncthreads();
-    for (int i = threadIdx.x; i < cnt; i += blockDim.x) {
-      const T* Pi = P + row0 + i;
-      double acc[kSolveNRC];
-#pragma unroll
-      for (int rr = 0; rr < kSolveNRC; ++rr) acc[rr] = 0.0;
-      for (int j = 0; j < w; ++j) {
-        const double l = (double)Pi[(size_t)j * ld];
-#pragma unroll
-        for (int rr = 0; rr < kSolveNRC; ++rr) acc[rr] += l * Ys[j + rr * w];
-      }
-      const int g = R[row0 + i];
-#pragma unroll
-      for (int rr = 0; rr < kSolveNRC; ++rr)
-        if (rr < nrc) red_add(a.Y + g + (size_t)(r0 + rr) * a.ldy, -acc[rr]);
-    }
+    if (nrc >= 5)
+      fwd_tile_rows<T, 2>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
+    else if (nrc >= 3)
+      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
+    else
+      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, nrc);
   }
 }
 
@@ -137,7 +213,8 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
 template <typename T>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
-  const int row0 = w + k * a.solve_rows, cnt = min(a.solve_rows, r - row0);
+  const int ts = a.st_rows[s];
+  const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
   constexpr int CH = 32;
@@ -152,9 +229,19 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
     for (int c0 = 0; c0 < cnt; c0 += CH) {
       const int nc = min(CH, cnt - c0);
       __syncthreads();
-      for (int idx = threadIdx.x; idx < CH * w; idx += blockDim.x) {
-        const int i = idx % CH, j = idx / CH;
-        Lc[j * (CH + 1) + i] = (i < nc) ? (double)P[row0 + c0 + i + (size_t)j * ld] : 0.0;
+      // CH x w entries, 8 per thread per batch, all loads of a batch in flight together
+      for (int base = threadIdx.x; base < CH * w; base += 8 * blockDim.x) {
+        double v[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * blockDim.x, i = idx % CH, j = idx / CH;
+          v[u] = (idx < CH * w && i < nc) ? (double)P[row0 + c0 + i + (size_t)j * ld] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          const int idx = base + u * blockDim.x, i = idx % CH, j = idx / CH;
+          if (idx < CH * w) Lc[j * (CH + 1) + i] = v[u];
+        }
       }
       for (int idx = threadIdx.x; idx < CH * nrc; idx += blockDim.x) {
         const int i = idx % CH, rr = idx / CH;
@@ -185,18 +272,24 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
 }
 
 template <typename T>
-__global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
+__global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveShared sh;
   double* sm = reinterpret_cast<double*>(smem_raw);
-  const Ring q{a.ring, a.ctrl, a.ntask, a.budget_ns};
+  // Two rings: tasks made ready by a finished task (high priority) ahead of
+  // the seeds, so that chains up the tree advance instead of queueing behind
+  // every leaf.
+  const Ring2 q{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
+  __shared__ int pend[2];
+  if (threadIdx.x == 0) pend[0] = pend[1] = -1;
   const int ns = a.pv.ns, nst = a.n_st;
   unsigned long long busy[4] = {0, 0, 0, 0}, wait = 0;
   for (;;) {
     uint64_t t1 = 0;
     if (threadIdx.x == 0) {
       const uint64_t t0 = a.prof ? global_ns() : 0;
-      sh.task = ring_claim(q);
+      int lo_ready;
+      sh.task = ring2_claim(q, pend, &lo_ready);
       if (a.prof) {
         t1 = global_ns();
         wait += t1 - t0;
@@ -211,9 +304,9 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
       fwd_diag(a, s, sm);
       publish_cta_writes();
       if (a.nst[s] > 0) {
-        ring_push_range(q, ns + a.st_first[s], a.nst[s], &sh.base);
+        ring2_push_range(q, true, ns + a.st_first[s], a.nst[s], &sh.base);
       } else if (threadIdx.x == 0) {
-        ring_push_one(q, ns + 2 * nst + s);
+        ring2_push_one(q, true, ns + 2 * nst + s);
       }
     } else if (task < ns + nst) {
       const int kt = task - ns, s = a.st_sn[kt];
@@ -223,28 +316,28 @@ __global__ void __launch_bounds__(kSolveThreads) solve_kernel(SolveArgs a) {
       // root has thousands of dependent tiles, and they sit on the critical path.
       for (int e = a.st_tptr[kt] + threadIdx.x; e < a.st_tptr[kt + 1]; e += blockDim.x) {
         const int t = a.st_tgt[e];
-        if (atom_add_acqrel(&a.fdep[t], -1) == 1) ring_push_one(q, t);
+        if (atom_add_acqrel(&a.fdep[t], -1) == 1) ring2_push_one(q, true, t);
       }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
       if (sh.flag) {
         for (int k = threadIdx.x; k < a.nst[s]; k += blockDim.x) {
           const int tile = a.st_first[s] + k;
-          if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring_push_one(q, ns + nst + tile);
+          if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring2_push_one(q, true, ns + nst + tile);
         }
       }
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
-      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) ring_push_one(q, ns + 2 * nst + s);
+      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) ring2_push_one(q, true, ns + 2 * nst + s);
     } else {
       const int s = task - ns - 2 * nst;
       bwd_diag(a, s, sm);
       publish_cta_writes();
       for (int e = a.rt_ptr[s] + threadIdx.x; e < a.rt_ptr[s + 1]; e += blockDim.x) {
         const int tile = a.rt_tile[e];
-        if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring_push_one(q, ns + nst + tile);
+        if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring2_push_one(q, true, ns + nst + tile);
       }
     }
     if (threadIdx.x == 0) {
@@ -284,7 +377,7 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 }  // namespace
 
 size_t solve_smem_bytes(int max_w) {
-  const size_t diag = ((size_t)max_w * max_w + (size_t)max_w * kSolveNRC) * sizeof(double);
+  const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double);
   const size_t tile = ((size_t)max_w * 33 + 32 * kSolveNRC) * sizeof(double);
   return diag > tile ? diag : tile;
 }
@@ -336,12 +429,13 @@ cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t 
 }
 
 // ---------------------------------------------------------------- ring reset
-__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seeds_hi, int* ctrl,
+__global__ void ring_reset_kernel(int* slots, int ntask, const int* seeds, int nseed, int seed_off, int seeds_hi,
+                                  int* ctrl,
                                   int* c0, const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                                   const int* c2_init, int n2, int* c3, const int* c3_init, int n3) {
   const int stride = gridDim.x * blockDim.x;
   const int tid = blockIdx.x * blockDim.x + threadIdx.x;
-  for (int i = tid; i < ntask; i += stride) slots[i] = (i < nseed) ? seeds[i] : -1;
+  for (int i = tid; i < ntask; i += stride) slots[i] = (i >= seed_off && i < seed_off + nseed) ? seeds[i - seed_off] : -1;
   for (int i = tid; i < n0; i += stride) c0[i] = c0_init[i];
   for (int i = tid; i < n1; i += stride) c1[i] = c1_init[i];
   for (int i = tid; i < n2; i += stride) c2[i] = c2_init[i];
@@ -393,14 +487,14 @@ cudaError_t noalloc_scratch(int device, void** ptr) {
 cudaError_t launch_ring_reset(int* slots, int ntask, const int* seeds, int nseed, int* ctrl, int* c0,
                               const int* c0_init, int n0, int* c1, const int* c1_init, int n1, int* c2,
                               const int* c2_init, int n2, cudaStream_t st, int* c3, const int* c3_init, int n3,
-                              int seeds_hi) {
+                              int seeds_hi, int seed_off) {
   int m = ntask > kCtrlWords ? ntask : kCtrlWords;
   if (n0 > m) m = n0;
   if (n1 > m) m = n1;
   if (n2 > m) m = n2;
   if (n3 > m) m = n3;
-  ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, seeds_hi, ctrl, c0, c0_init, n0, c1,
-                                                 c1_init, n1, c2, c2_init, n2, c3, c3_init, n3);
+  ring_reset_kernel<<<grid_for(m), 256, 0, st>>>(slots, ntask, seeds, nseed, seed_off, seeds_hi, ctrl, c0, c0_init,
+                                                 n0, c1, c1_init, n1, c2, c2_init, n2, c3, c3_init, n3);
   return cudaGetLastError();
 }
 

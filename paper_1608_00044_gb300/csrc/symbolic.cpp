@@ -376,12 +376,16 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   for (int32_t s = 0; s < ns; ++s) P.n_hi_tasks += P.nu_hi[s];
 
   // ---- solve tasks ------------------------------------------------------------
-  const int TS = std::max(1, prm.solve_rows);
+  // near the root (the critical path of both sweeps) the tiles are shorter
   P.st_first.assign(ns, 0);
   P.nst.assign(ns, 0);
+  P.st_rows.assign(ns, 0);
   P.st_sn.clear();
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t nb = P.nrows[s] - (P.fcol[s + 1] - P.fcol[s]);
+    const bool top = depth[s] < prm.top_depth;
+    const int TS = std::max(1, top ? std::min(prm.top_solve_rows, prm.solve_rows) : prm.solve_rows);
+    P.st_rows[s] = TS;
     P.st_first[s] = (int32_t)P.st_sn.size();
     P.nst[s] = (nb + TS - 1) / TS;
     for (int32_t k = 0; k < P.nst[s]; ++k) P.st_sn.push_back(s);
@@ -395,6 +399,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
     const int32_t* R = P.rows.data() + P.rowoff[s];
+    const int32_t TS = P.st_rows[s];
     for (int32_t k = 0; k < P.nst[s]; ++k) {
       const int32_t tile = P.st_first[s] + k;
       const int32_t r0 = w + k * TS, r1 = std::min(r, r0 + TS);
