@@ -32,7 +32,7 @@ struct PlanParams {
   int top_depth = 128;
   int top_tile_rows = 16;
   int top_trsm_rows = 32;
-  int top_solve_rows = 64;  // rows per triangular-solve tile of those panels
+  int top_solve_rows = 32;  // rows per triangular-solve tile of those panels
   // Tensor-core update tiles: source panels at least tc_min_width wide (0 =
   // none) use tc_tile_rows-row tiles (one MMA M-tile) on the tensor cores.
   int tc_min_width = 0;

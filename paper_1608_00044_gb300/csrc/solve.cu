@@ -200,7 +200,9 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
       Ys[idx] = rr < nrc ? ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy) : 0.0;
     }
     __syncthreads();
-    if (nrc >= 5)
+    if (nrc >= 5 && cnt <= 32)
+      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 8);
+    else if (nrc >= 5)
       fwd_tile_rows<T, 2>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
     else if (nrc >= 3)
       fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
@@ -209,7 +211,11 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   }
 }
 
-// y_s -= L21[tile]^T x[rows of tile]: rows staged 32 at a time in shared memory.
+// y_s -= L21[tile]^T x[rows of tile]: rows staged kBwdCH at a time in shared
+// memory (one batched pass and one barrier per chunk); thread (j, rr) sums
+// column j of the chunk against x with four accumulators.
+constexpr int kBwdCH = 64;
+
 template <typename T>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
@@ -217,9 +223,9 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
-  constexpr int CH = 32;
-  double* Lc = sm;                  // [w][CH + 1]
-  double* Xc = Lc + w * (CH + 1);   // [nrc][CH]
+  constexpr int CH = kBwdCH, LD = CH + 1;
+  double* Lc = sm;                 // [w][LD]: Lc[i + j LD] = L21[c0 + i][j]
+  double* Xc = Lc + w * LD;        // [nrc][CH]
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     // each thread owns (j, rr) pairs p = tid + q * blockDim
@@ -229,7 +235,6 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
     for (int c0 = 0; c0 < cnt; c0 += CH) {
       const int nc = min(CH, cnt - c0);
       __syncthreads();
-      // CH x w entries, 8 per thread per batch, all loads of a batch in flight together
       for (int base = threadIdx.x; base < CH * w; base += 8 * blockDim.x) {
         double v[8];
 #pragma unroll
@@ -240,7 +245,7 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
           const int idx = base + u * blockDim.x, i = idx % CH, j = idx / CH;
-          if (idx < CH * w) Lc[j * (CH + 1) + i] = v[u];
+          if (idx < CH * w) Lc[i + j * LD] = v[u];
         }
       }
       for (int idx = threadIdx.x; idx < CH * nrc; idx += blockDim.x) {
@@ -253,10 +258,16 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
         const int p = threadIdx.x + q * blockDim.x;
         if (p < w * nrc) {
           const int j = p % w, rr = p / w;
-          double acc = part[q];
-#pragma unroll 8
-          for (int i = 0; i < CH; ++i) acc += Lc[j * (CH + 1) + i] * Xc[rr * CH + i];
-          part[q] = acc;
+          const double* lj = Lc + j * LD;
+          const double* xr = Xc + rr * CH;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          for (int i = 0; i < nc; i += 4) {  // rows past nc are zero in both
+            s0 += lj[i] * xr[i];
+            s1 += lj[i + 1] * xr[i + 1];
+            s2 += lj[i + 2] * xr[i + 2];
+            s3 += lj[i + 3] * xr[i + 3];
+          }
+          part[q] += (s0 + s1) + (s2 + s3);
         }
       }
     }
@@ -268,6 +279,27 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
         red_add(a.Y + f + j + (size_t)(r0 + rr) * a.ldy, -part[q]);
       }
     }
+  }
+}
+
+// Lower the counters cnt[id] of ids list[e] (or e itself when list is null),
+// e in [e0, e1), by one, and push task task0 + id for each that reaches zero.
+// Whole CTA; each thread issues its decrements in batches of 8 whose round
+// trips overlap (a panel near the root releases thousands of tiles).
+__device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* list, int e0, int e1, int32_t* cnt,
+                                              int task0) {
+  for (int base = e0 + threadIdx.x; base < e1; base += 8 * blockDim.x) {
+    int id[8], old[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int e = base + u * blockDim.x;
+      id[u] = e < e1 ? (list ? list[e] : e) : -1;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_acqrel(&cnt[id[u]], -1) : 0;
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (id[u] >= 0 && old[u] == 1) ring2_push_one(q, true, task0 + id[u]);
   }
 }
 
@@ -320,12 +352,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
-      if (sh.flag) {
-        for (int k = threadIdx.x; k < a.nst[s]; k += blockDim.x) {
-          const int tile = a.st_first[s] + k;
-          if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring2_push_one(q, true, ns + nst + tile);
-        }
-      }
+      if (sh.flag) release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst);
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T>(a, s, kt - a.st_first[s], sm);
@@ -335,10 +362,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       const int s = task - ns - 2 * nst;
       bwd_diag(a, s, sm);
       publish_cta_writes();
-      for (int e = a.rt_ptr[s] + threadIdx.x; e < a.rt_ptr[s + 1]; e += blockDim.x) {
-        const int tile = a.rt_tile[e];
-        if (atom_add_acqrel(&a.bdep[tile], -1) == 1) ring2_push_one(q, true, ns + nst + tile);
-      }
+      release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
@@ -378,7 +402,7 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 
 size_t solve_smem_bytes(int max_w) {
   const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double);
-  const size_t tile = ((size_t)max_w * 33 + 32 * kSolveNRC) * sizeof(double);
+  const size_t tile = ((size_t)max_w * (kBwdCH + 1) + kBwdCH * kSolveNRC) * sizeof(double);
   return diag > tile ? diag : tile;
 }
 
