@@ -67,12 +67,29 @@ __device__ __forceinline__ void tri_pair(int p, int& ei, int& ek) {
   ei = p - e * (e + 1) / 2;
 }
 
-// Pivot of column j: l_jj = sqrt(d) and its reciprocal; false when d is not
-// positive (the block is not positive definite at this column).
+// Pivot of column j: l_jj = sqrt(d) and r = 1 / l_jj; false when d is not
+// positive (the block is not positive definite at this column).  The pivot is
+// the serial chain of the diagonal factorization (one per column), so it
+// avoids a square root followed by a division: r is the reciprocal square root
+// by Newton's iteration y <- y (3 - d y^2) / 2 from a single-precision seed
+// (relative error below 2^-22; two steps take it below the FP64 rounding
+// error), l = d r, then one residual correction l += (r / 2)(d - l^2)
+// (P. Markstein, IA-64 and Elementary Functions, 2000).  Outside the range
+// where the seed is representable the plain square root and division are used.
 __device__ __forceinline__ bool take_pivot(double d, double& l, double& r) {
   if (!(d > 0.0)) return false;
-  l = sqrt(d);
-  r = 1.0 / l;
+  if (d > 1e-30 && d < 1e30) {
+    double y = (double)rsqrtf((float)d);
+    const double hd = 0.5 * d;
+    y = y * fma(-hd, y * y, 1.5);
+    y = y * fma(-hd, y * y, 1.5);
+    const double l0 = d * y;
+    l = fma(0.5 * y, fma(-l0, l0, d), l0);
+    r = y;
+  } else {
+    l = sqrt(d);
+    r = 1.0 / l;
+  }
   return true;
 }
 
@@ -506,9 +523,14 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     // Relative row indices (computed once per analysis): position of each
     // row of the tile in t's sorted row list.
     load_relpos(a, u, pos, grow, Rs);
-    // Strip q goes to warp (q + rot) % 8: tiles of fewer than 8 strips load the
-    // four SM sub-partitions (warp % 4) evenly over many tasks, not always the first.
-    const int lane = tid & 31, q = ((tid >> 5) - rot) & 7;
+    // Warp slot q' = (warp - rot) % 8 (tiles of few strips load the four SM
+    // sub-partitions, warp % 4, evenly over many tasks).  A tile of S strips
+    // gives each strip C = 8 / S (rounded down to a power of two) warps, which
+    // split its column blocks: short tiles near the root keep every warp busy.
+    const int lane = tid & 31, qs = ((tid >> 5) - rot) & 7;
+    const int nstrip = (u.rowlen + 7) >> 3;
+    const int C = nstrip >= 5 ? 1 : nstrip >= 3 ? 2 : nstrip == 2 ? 4 : 8;
+    const int q = qs / C, cg = qs - q * C;              // strip and column group of this warp
     const int lr = lane >> 3, lc = lane & 7;
     const int srows = min(8, u.rowlen - 8 * q);        // valid rows of this warp's strip
     const int nr = srows > 4 ? 2 : 1;
@@ -521,7 +543,10 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       const int c0 = u.seg0 + cb;
       const int ob = c0 % E;
       const int dd = off - cb + 8 * q + 7;  // last column any row of the strip needs
-      const int ncb = dd < 0 ? 0 : min((ncol + 7) >> 3, dd / 8 + 1);
+      const int nall = (ncol + 7) >> 3;
+      const int nper = (nall + C - 1) / C;
+      const int b0 = cg * nper;             // this warp's column blocks b0 .. b0 + ncb - 1
+      const int ncb = dd < 0 ? 0 : max(0, min(min(nall, b0 + nper), dd / 8 + 1) - b0);
       const bool active = srows > 0 && ncb > 0;
       __syncthreads();  // the previous pass is done with the buffers and gcol
       for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[c0 + j];
@@ -549,7 +574,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
         __syncthreads();       // ... and every thread's
         if (active) {
           const T* As = buf + (c & 1) * kBuf;
-          const T* Bs = As + kUpdKC * STR + ob;
+          const T* Bs = As + kUpdKC * STR + ob + 8 * b0;
           if (nr == 2)
             upd_strip_nc<acc_t, 2>(ncb, As, Bs, kc, r0, lc, acc);
           else
@@ -567,7 +592,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
           const int gi = grow[i];
 #pragma unroll
           for (int cc = 0; cc < 8; ++cc) {
-            const int j = lc + 8 * cc;
+            const int j = lc + 8 * (b0 + cc);
             if (cc < ncb && j < ncol && gi >= gcol[j]) red_add(dst + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
           }
         }

@@ -31,7 +31,7 @@ struct PlanParams {
   // the chain spreads over more CTAs.
   int top_depth = 128;
   int top_tile_rows = 16;
-  int top_trsm_rows = 32;
+  int top_trsm_rows = 16;
   int top_solve_rows = 32;  // rows per triangular-solve tile of those panels
   // Tensor-core update tiles: source panels at least tc_min_width wide (0 =
   // none) use tc_tile_rows-row tiles (one MMA M-tile) on the tensor cores.

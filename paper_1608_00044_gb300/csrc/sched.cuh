@@ -141,14 +141,17 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
       }
     }
     if (pend[0] < 0 && pend[1] < 0 && hi.x >= q.n_hi && lo.x >= q.n_lo) return -1;  // all claimed
-    if (ld_relaxed(&q.ctrl[kErr]) != 0) return -1;
+    // An idle grid polls these words from every CTA: the error word is read on
+    // every 8th round only, and the backoff grows to 2 us, so that the polling
+    // does not queue up the claims and pushes on the same L2 lines.
+    if ((it & 7) == 7 && ld_relaxed(&q.ctrl[kErr]) != 0) return -1;
     if (it > max_iter || (int64_t)(global_ns() - t0) > q.budget_ns) {
       atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
       atomicExch(&q.ctrl[kWhere], pend[0] >= 0 ? pend[0] : pend[1]);
       return -1;
     }
     __nanosleep(backoff);
-    if (backoff < 256) backoff <<= 1;
+    if (backoff < 2048) backoff <<= 1;
   }
 }
 

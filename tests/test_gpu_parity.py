@@ -62,6 +62,28 @@ def test_dense(n):
     _check(A, rng.permutation(n), B)
 
 
+@pytest.mark.parametrize("W", [1, 64])
+def test_pivot_square_root_accuracy(W):
+    """The diagonal factorization's pivot (Newton reciprocal square root with a
+    residual correction in the normal range, square root and division outside
+    it) against the correctly rounded square root: a diagonal matrix whose
+    entries span 1e-60 .. 1e60 gives l_jj within 2 units in the last place and
+    exact reciprocals within 4 (the solve uses them)."""
+    n = 512
+    rng = np.random.default_rng(7)
+    d = 10.0 ** rng.uniform(-60, 60, n)
+    M = np.diag(d)
+    A = _csc(M)
+    rc, X, st, h = gpu_factor_solve(A, np.arange(n), np.ones((n, 1)), max_width=W)
+    assert rc == 0
+    Lp, Li, Lx, perm = spchol.export_factor(h)
+    ljj = Lx[Lp[:-1]]  # the diagonal heads each column
+    dp = d[perm]
+    np.testing.assert_allclose(ljj, np.sqrt(dp), rtol=2 * np.finfo(float).eps, atol=0)
+    np.testing.assert_allclose(X[:, 0], 1.0 / d, rtol=4 * np.finfo(float).eps, atol=0)
+    spchol.destroy(h)
+
+
 @pytest.mark.parametrize("seed", range(6))
 def test_random_sparse(seed):
     rng = np.random.default_rng(500 + seed)
