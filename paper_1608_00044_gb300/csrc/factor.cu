@@ -47,15 +47,18 @@ __device__ __forceinline__ T* panel_ptr(const FactorArgs& a, int s) {
 }
 
 // ---------------------------------------------------------------- POTRF(s)
-// Right-looking Cholesky (Algorithm 1) of the w x w diagonal block in shared
-// memory, one barrier per column.  Step j: warps 0..6 form the scaled column
-// j (l_ij = a_ij / l_jj, into a double-buffered vector), write column j - 1
-// back in place, and apply the rank-1 update of the trailing triangle;
-// meanwhile warp 7 already updates a_{j+1,j+1} and takes its square root
-// (look-ahead), so the pivot chain overlaps the update instead of following it.
-// The update is enumerated by the pair index p of the trailing triangle in
-// column-major order from its bottom-right corner, so that p < m (m + 1) / 2
-// is exactly the triangle of order m and consecutive p touch consecutive rows.
+// Cholesky of the w x w diagonal block in shared memory (Algorithm 1), taken
+// right-looking in the square-root-free form A = M D M^T, one barrier per
+// column, then L = M D^{1/2}.  Step j: warps 0..6 form the multipliers
+// m_ij = a_ij / d_j (into a double-buffered vector), write column j - 1 of M
+// back in place, and apply the rank-1 update a_ik -= m_ij a_kj of the
+// trailing triangle; meanwhile warp 7 already updates d_{j+1} and forms
+// 1 / d_{j+1} (look-ahead).  The serial chain from one column to the next is
+// a multiply, an FMA and a reciprocal; the square roots come after the loop,
+// all columns at once.  The update is enumerated by the pair index p of the
+// trailing triangle in column-major order from its bottom-right corner, so
+// that p < m (m + 1) / 2 is exactly the triangle of order m and consecutive p
+// touch consecutive rows; the pairs are decoded once into a table.
 constexpr int kPivotWarp = 7;
 constexpr int kUpdWarps = 7;
 
@@ -67,30 +70,20 @@ __device__ __forceinline__ void tri_pair(int p, int& ei, int& ek) {
   ei = p - e * (e + 1) / 2;
 }
 
-// Pivot of column j: l_jj = sqrt(d) and r = 1 / l_jj; false when d is not
-// positive (the block is not positive definite at this column).  The pivot is
-// the serial chain of the diagonal factorization (one per column), so it
-// avoids a square root followed by a division: r is the reciprocal square root
-// by Newton's iteration y <- y (3 - d y^2) / 2 from a single-precision seed
-// (relative error below 2^-22; two steps take it below the FP64 rounding
-// error), l = d r, then one residual correction l += (r / 2)(d - l^2)
-// (P. Markstein, IA-64 and Elementary Functions, 2000).  Outside the range
-// where the seed is representable the plain square root and division are used.
-__device__ __forceinline__ bool take_pivot(double d, double& l, double& r) {
-  if (!(d > 0.0)) return false;
+// 1 / d for the pivot d > 0 by Newton's iteration y <- y (2 - d y) from the
+// single-precision approximate reciprocal (relative error below 2^-22; two
+// steps take it below the FP64 rounding error); outside the range where the
+// seed is representable, the division.
+__device__ __forceinline__ double pivot_recip(double d) {
   if (d > 1e-30 && d < 1e30) {
-    double y = (double)rsqrtf((float)d);
-    const double hd = 0.5 * d;
-    y = y * fma(-hd, y * y, 1.5);
-    y = y * fma(-hd, y * y, 1.5);
-    const double l0 = d * y;
-    l = fma(0.5 * y, fma(-l0, l0, d), l0);
-    r = y;
-  } else {
-    l = sqrt(d);
-    r = 1.0 / l;
+    float y0;
+    asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(y0) : "f"((float)d));
+    double y = (double)y0;
+    y = fma(y, fma(-d, y, 1.0), y);
+    y = fma(y, fma(-d, y, 1.0), y);
+    return y;
   }
-  return true;
+  return 1.0 / d;
 }
 
 template <typename T>
@@ -99,18 +92,25 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
   const int warp = tid >> 5, lane = tid & 31;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
   T* P = panel_ptr<T>(a, s);
-  double* xd = sm + w * w;  // r_j = 1 / l_jj (the diagonal of L11^{-1})
-  double* cb = xd + w;      // 2 x w: scaled column of the current step, by parity
+  double* xd = sm + w * w;  // during the loop 1 / d_j; after it r_j = 1 / l_jj (the diagonal of L11^{-1})
+  double* cb = xd + w;      // 2 x w: multipliers of the current step, by parity
+  // pair table: pair p of the trailing triangle as (ei << 8) | ek, decoded once
+  uint16_t* pt = reinterpret_cast<uint16_t*>(cb + 2 * w);
+  const int npair = w * (w - 1) / 2;  // pairs of the largest trailing triangle (step 0)
   bool ok = true;
   if (!skip) {
     stage_lower<true>(P, w, ld, sm);  // lower triangle; zeros above (used below for L11^{-1})
+    for (int p = tid; p < npair; p += blockDim.x) {
+      int ei, ek;
+      tri_pair(p, ei, ek);
+      pt[p] = (uint16_t)((ei << 8) | ek);
+    }
     if (tid == 0) sh.flag = 0;
     __syncthreads();
     if (tid == kPivotWarp * 32) {
-      double l, r;
-      if (take_pivot(sm[0], l, r)) {
-        sm[0] = l;
-        xd[0] = r;
+      const double d0 = sm[0];
+      if (d0 > 0.0) {
+        xd[0] = pivot_recip(d0);
       } else {
         atomicMin(&a.ctrl[kInfo], f + 1);
         sh.flag = 1;
@@ -118,29 +118,37 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
     }
     __syncthreads();
     for (int j = 0; j < w && !sh.flag; ++j) {
-      const double rj = xd[j];
+      const double qj = xd[j];
       if (warp < kUpdWarps) {
         double* cj = cb + (j & 1) * w;
         const double* cprev = cb + ((j + 1) & 1) * w;
-        for (int i = j + 1 + tid; i < w; i += kUpdWarps * 32) cj[i] = sm[i + j * w] * rj;
+        for (int i = j + 1 + tid; i < w; i += kUpdWarps * 32) cj[i] = sm[i + j * w] * qj;
         if (j > 0)
           for (int i = j + tid; i < w; i += kUpdWarps * 32) sm[i + (j - 1) * w] = cprev[i];
         asm volatile("bar.sync 1, %0;" ::"n"(kUpdWarps * 32) : "memory");
         const int m = w - 1 - j;
         const int np = m * (m + 1) / 2 - 1;  // all but (j + 1, j + 1), which warp 7 owns
-        for (int p = tid; p < np; p += kUpdWarps * 32) {
-          int ei, ek;
-          tri_pair(p, ei, ek);
-          const int i = w - 1 - ei, k = w - 1 - ek;
-          sm[i + k * w] = fma(-cj[i], cj[k], sm[i + k * w]);
+        const double* aj = sm + j * w;       // column j, not yet divided by d_j
+        constexpr int kStep = kUpdWarps * 32;
+        // two pairs per round, every load issued before the arithmetic: the
+        // pairs are distinct entries, so the rounds' chains overlap
+        for (int p = tid; p < np; p += 2 * kStep) {
+          const int p2 = p + kStep;
+          const unsigned e1 = pt[p], e2 = p2 < np ? pt[p2] : pt[p];
+          const int i1 = w - 1 - (int)(e1 >> 8), k1 = w - 1 - (int)(e1 & 255u);
+          const int i2 = w - 1 - (int)(e2 >> 8), k2 = w - 1 - (int)(e2 & 255u);
+          const double a1 = cj[i1], b1 = aj[k1], s1 = sm[i1 + k1 * w];
+          const double a2 = cj[i2], b2 = aj[k2], s2 = sm[i2 + k2 * w];
+          sm[i1 + k1 * w] = fma(-a1, b1, s1);
+          if (p2 < np) sm[i2 + k2 * w] = fma(-a2, b2, s2);
         }
       } else if (lane == 0 && j + 1 < w) {
-        const double l1 = sm[(j + 1) + j * w] * rj;
-        const double d = fma(-l1, l1, sm[(j + 1) * (w + 1)]);
-        double l, r;
-        if (take_pivot(d, l, r)) {
-          sm[(j + 1) * (w + 1)] = l;
-          xd[j + 1] = r;
+        const double a1 = sm[(j + 1) + j * w];
+        const double d = fma(-(a1 * qj), a1, sm[(j + 1) * (w + 1)]);
+        const double q = pivot_recip(d);
+        if (d > 0.0) {
+          sm[(j + 1) * (w + 1)] = d;
+          xd[j + 1] = q;
         } else {
           atomicMin(&a.ctrl[kInfo], f + j + 2);
           sh.flag = 1;
@@ -149,6 +157,21 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
       __syncthreads();
     }
     ok = !sh.flag;
+    if (ok) {
+      // L = M D^{1/2}: l_jj = sqrt(d_j) (and r_j = 1 / l_jj for the solves),
+      // then l_ij = m_ij l_jj below the diagonal
+      for (int j = tid; j < w; j += blockDim.x) {
+        const double l = sqrt(sm[j * (w + 1)]);
+        sm[j * (w + 1)] = l;
+        xd[j] = 1.0 / l;
+      }
+      __syncthreads();
+      for (int j = warp; j < w; j += kFactorThreads / 32) {
+        const double l = sm[j * (w + 1)];
+        for (int i = j + 1 + lane; i < w; i += 32) sm[i + j * w] *= l;
+      }
+      __syncthreads();
+    }
     for (int j = warp; j < w; j += kFactorThreads / 32)
       for (int i = j + lane; i < w; i += 32) P[i + (size_t)j * ld] = (T)sm[i + j * w];
   }
@@ -1078,9 +1101,10 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 }  // namespace
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {
-  // POTRF: the block, 1 / l_jj and two scaled columns; TRSM: L11 with 64-row
-  // columns and 1 / l_cc.
-  size_t tri = ((size_t)max_w * max_w + 3 * (size_t)max_w) * sizeof(double);
+  // POTRF: the block, 1 / l_jj, two scaled columns and the 16-bit pair table;
+  // TRSM: L11 with 64-row columns and 1 / l_cc.
+  size_t tri = ((size_t)max_w * max_w + 3 * (size_t)max_w) * sizeof(double) +
+               (((size_t)max_w * (max_w - 1) / 2 * sizeof(uint16_t) + 15) & ~size_t(15));
   if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 1) * max_w * sizeof(double));
   if (mma_mode == 3) {
     const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);

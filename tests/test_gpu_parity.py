@@ -64,11 +64,11 @@ def test_dense(n):
 
 @pytest.mark.parametrize("W", [1, 64])
 def test_pivot_square_root_accuracy(W):
-    """The diagonal factorization's pivot (Newton reciprocal square root with a
-    residual correction in the normal range, square root and division outside
-    it) against the correctly rounded square root: a diagonal matrix whose
-    entries span 1e-60 .. 1e60 gives l_jj within 2 units in the last place and
-    exact reciprocals within 4 (the solve uses them)."""
+    """The diagonal factorization's pivots (reciprocals by Newton's iteration in
+    the normal range, a division outside it; square roots after the loop)
+    against the correctly rounded square root: a diagonal matrix whose entries
+    span 1e-60 .. 1e60 gives l_jj within 2 units in the last place and exact
+    reciprocals within 4 (the solve uses them)."""
     n = 512
     rng = np.random.default_rng(7)
     d = 10.0 ** rng.uniform(-60, 60, n)
