@@ -970,11 +970,13 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 
 // MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
 // panels, split or not), 3 = BF16 tensor cores on split FP64 operands.
-// At least four CTAs per SM (64 registers a thread) for the CUDA-core and TF32
-// modes, whose tasks hide latency across CTAs; the BF16-split mode owns the
-// whole SM (all TMEM columns) with one CTA.
+// Five CTAs per SM (48 registers a thread; a few live values of the update
+// tile's epilogue spill to L1) for the CUDA-core and TF32 modes, whose tasks
+// hide each other's latencies across CTAs (measured: FP32 factor -12 %, FP64
+// -0.8 % against four); the BF16-split mode owns the whole SM (all TMEM
+// columns) with one CTA.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 4) factor_kernel(FactorArgs a) {
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 5) factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
