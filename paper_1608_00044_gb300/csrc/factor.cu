@@ -94,8 +94,9 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
   T* P = panel_ptr<T>(a, s);
   double* xd = sm + w * w;  // during the loop 1 / d_j; after it r_j = 1 / l_jj (the diagonal of L11^{-1})
   double* cb = xd + w;      // 2 x w: multipliers of the current step, by parity
-  // pair table: pair p of the trailing triangle as (ei << 8) | ek, decoded once
-  uint16_t* pt = reinterpret_cast<uint16_t*>(cb + 2 * w);
+  // pair table: the column index ek of pair p of the trailing triangle (its
+  // row index is p - ek (ek + 1) / 2), decoded once
+  uint8_t* pt = reinterpret_cast<uint8_t*>(cb + 2 * w);
   const int npair = w * (w - 1) / 2;  // pairs of the largest trailing triangle (step 0)
   bool ok = true;
   if (!skip) {
@@ -103,7 +104,7 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
     for (int p = tid; p < npair; p += blockDim.x) {
       int ei, ek;
       tri_pair(p, ei, ek);
-      pt[p] = (uint16_t)((ei << 8) | ek);
+      pt[p] = (uint8_t)ek;
     }
     if (tid == 0) sh.flag = 0;
     __syncthreads();
@@ -134,9 +135,10 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
         // pairs are distinct entries, so the rounds' chains overlap
         for (int p = tid; p < np; p += 2 * kStep) {
           const int p2 = p + kStep;
-          const unsigned e1 = pt[p], e2 = p2 < np ? pt[p2] : pt[p];
-          const int i1 = w - 1 - (int)(e1 >> 8), k1 = w - 1 - (int)(e1 & 255u);
-          const int i2 = w - 1 - (int)(e2 >> 8), k2 = w - 1 - (int)(e2 & 255u);
+          const int q2 = p2 < np ? p2 : p;
+          const int ek1 = pt[p], ek2 = pt[q2];
+          const int i1 = w - 1 - (p - ek1 * (ek1 + 1) / 2), k1 = w - 1 - ek1;
+          const int i2 = w - 1 - (q2 - ek2 * (ek2 + 1) / 2), k2 = w - 1 - ek2;
           const double a1 = cj[i1], b1 = aj[k1], s1 = sm[i1 + k1 * w];
           const double a2 = cj[i2], b2 = aj[k2], s2 = sm[i2 + k2 * w];
           sm[i1 + k1 * w] = fma(-a1, b1, s1);
@@ -971,12 +973,14 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
 // panels, split or not), 3 = BF16 tensor cores on split FP64 operands.
 // Five CTAs per SM (48 registers a thread; a few live values of the update
-// tile's epilogue spill to L1) for the CUDA-core and TF32 modes, whose tasks
-// hide each other's latencies across CTAs (measured: FP32 factor -12 %, FP64
-// -0.8 % against four); the BF16-split mode owns the whole SM (all TMEM
+// tile's epilogue spill to L1) for the DFMA and TF32 modes, six (40
+// registers) for FP32 panels on FFMA, whose tasks are shortest: more resident
+// CTAs hide each other's latencies (measured: FP32 factor -12 %, FP64 -0.8 %
+// for five against four); the BF16-split mode owns the whole SM (all TMEM
 // columns) with one CTA.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : 5) factor_kernel(FactorArgs a) {
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : (MODE == 0 && sizeof(T) == 4) ? 6 : 5)
+    factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
@@ -1103,10 +1107,10 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 }  // namespace
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {
-  // POTRF: the block, 1 / l_jj, two scaled columns and the 16-bit pair table;
+  // POTRF: the block, 1 / l_jj, two scaled columns and the 8-bit pair table;
   // TRSM: L11 with 64-row columns and 1 / l_cc.
   size_t tri = ((size_t)max_w * max_w + 3 * (size_t)max_w) * sizeof(double) +
-               (((size_t)max_w * (max_w - 1) / 2 * sizeof(uint16_t) + 15) & ~size_t(15));
+               (((size_t)max_w * (max_w - 1) / 2 + 15) & ~size_t(15));
   if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 1) * max_w * sizeof(double));
   if (mma_mode == 3) {
     const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);
