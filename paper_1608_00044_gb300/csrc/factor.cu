@@ -800,7 +800,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
 // C_ij = 2^(e_i + e_j) sum_{p,q} 2^(-8(p+q+2)) (A_p B_q^T)_ij.  The products
 // with p + q <= kSlices - 1 are kept (the dropped ones weigh below 2^-64 of
 // the leading one); products of equal p + q share one TMEM accumulator
-// (group d = p + q, 64 columns each), in which the integer sums stay exact
+// (group d = p + q, kOzN columns each), in which the integer sums stay exact
 // for d <= 3 and round at most at 2^-56 relative beyond.  The epilogue
 // combines the seven group values per entry exactly in two 64-bit integers,
 // converts once to FP64 and scales by 2^(e_i + e_j).
@@ -835,8 +835,12 @@ __device__ __forceinline__ double fixed64_to_double(long long t, int k) {
       (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-constexpr int kOzM = 128, kOzN = 64;
-constexpr int kOzCols = 512;  // TMEM columns: kSlices groups x 64, rounded to a power of two
+// The MMA is M = 128 x N = 32; a tile has at most kOzRows = 64 rows, whose
+// digits are the only A rows kept in shared memory: the MMA's rows 64..127 read
+// whatever follows (in bounds) and land in TMEM lanes that are never read
+// back.  7 groups x 32 columns fit 256 TMEM columns, so two CTAs share an SM.
+constexpr int kOzM = 128, kOzN = 32, kOzRows = 64;
+constexpr int kOzCols = 256;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
 
 __device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -855,14 +859,14 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     const int32_t* ex = a.rexp + a.pv.rowoff[s];
     const int kpad = (ws + 15) & ~15, nb = rs - ws;
     const uint16_t* sl = a.slices + a.sliceoff[s];
-    const int arow = kOzM * kpad * 2, brow = kOzN * kpad * 2;  // bytes of one slice tile
+    const int arow = kOzRows * kpad * 2, brow = kOzN * kpad * 2;  // bytes of one slice tile
     unsigned char* A0 = smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u);
     unsigned char* B0 = A0 + kSlices * arow;
     int* pos = reinterpret_cast<int*>(B0 + kSlices * brow);
-    int* grow = pos + kOzM;
-    int* gcol = grow + kOzM;
+    int* grow = pos + kOzRows;
+    int* gcol = grow + kOzRows;
     int* ea = gcol + kOzN;
-    int* eb = ea + kOzM;
+    int* eb = ea + kOzRows;
     const uint32_t sbo = (uint32_t)kpad * 16;  // 8 rows x (kpad bf16) bytes
     const int chunks = kpad / 8;               // 16-byte chunks per row
 
@@ -923,8 +927,9 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
       // warp-collective, so the condition is warp-uniform).
       const int quad = warp & 3, half = warp >> 2;
       const int row = 32 * quad + lane;
+      constexpr int kHalf = kOzN / 2;
       if (32 * quad < u.rowlen) {
-        for (int c0 = half * 32; c0 < half * 32 + 32 && c0 < ncol; c0 += 8) {
+        for (int c0 = half * kHalf; c0 < half * kHalf + kHalf && c0 < ncol; c0 += 8) {
           uint32_t v[kSlices][8];
 #pragma unroll
           for (int d = 0; d < kSlices; ++d) {
@@ -976,10 +981,10 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // tile's epilogue spill to L1) for the DFMA and TF32 modes, six (40
 // registers) for FP32 panels on FFMA, whose tasks are shortest: more resident
 // CTAs hide each other's latencies (measured: FP32 factor -12 %, FP64 -0.8 %
-// for five against four); the BF16-split mode owns the whole SM (all TMEM
-// columns) with one CTA.
+// for five against four); the BF16-split mode runs two CTAs per SM, each
+// owning half of the SM's TMEM columns.
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 1 : (MODE == 0 && sizeof(T) == 4) ? 6 : 5)
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 2 : (MODE == 0 && sizeof(T) == 4) ? 6 : 5)
     factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
@@ -1114,7 +1119,7 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
   if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 1) * max_w * sizeof(double));
   if (mma_mode == 3) {
     const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);
-    const size_t oz = (size_t)kSlices * (kOzM + kOzN) * kpad * 2 + (3 * kOzM + 2 * kOzN) * sizeof(int) + 1024;
+    const size_t oz = (size_t)kSlices * (kOzRows + kOzN) * kpad * 2 + (3 * kOzRows + 2 * kOzN) * sizeof(int) + 1024;
     if (oz > tri) tri = oz;
   } else if (mma_mode != 0) {
     const size_t kpad = ((size_t)max_w + 7) & ~size_t(7);
@@ -1135,7 +1140,26 @@ cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_p
   const void* fn = factor_fn(fp32, mma_mode);
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
+  if (e != cudaSuccess || mma_mode != 3 || *blocks_per_sm >= 2) return e;
+  // The runtime's occupancy query reports one block per SM for this kernel
+  // (it allocates TMEM), while its registers and shared memory allow two (the
+  // profiler's launch statistics agree).  Two is also the design: each CTA
+  // owns 256 of the 512 TMEM columns, and the shared-memory request (over a
+  // third of the SM) keeps a third CTA out.  Count the two limits directly.
+  cudaFuncAttributes fa{};
+  int dev = 0, regs_sm = 0, smem_sm = 0;
+  if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess || (e = cudaGetDevice(&dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&regs_sm, cudaDevAttrMaxRegistersPerMultiprocessor, dev)) != cudaSuccess ||
+      (e = cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, dev)) != cudaSuccess)
+    return e;
+  const int regs_cta = ((fa.numRegs + 7) / 8) * 8 * kFactorThreads;
+  const size_t smem_cta = smem + fa.sharedSizeBytes + 1024;  // + the driver's per-block reserve
+  const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 0;
+  const int by_smem = (int)((size_t)smem_sm / smem_cta);
+  const int direct = std::min(2, std::min(by_regs, by_smem));
+  if (direct > *blocks_per_sm) *blocks_per_sm = direct;
+  return cudaSuccess;
 }
 
 cudaError_t launch_relpos(const UTask* ut, int n_u, const int32_t* rows, const int64_t* rowoff,

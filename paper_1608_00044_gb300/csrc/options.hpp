@@ -47,6 +47,7 @@ inline PlanParams params_from(const spchol_options& o) {
     // panels of at least 32 columns carry almost all update work and go to the
     // tensor cores; narrower ones keep DFMA tiles, whose cost scales with size
     p.tc_min_width = kFp64TcMinWidth;
+    p.tc_tile_rows = 64;  // the BF16-split tile keeps 64 rows of digits in shared memory
     p.slice_fp64 = true;
   }
   p.trsm_rows = kTrsmTileRows;
