@@ -978,13 +978,13 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
 // panels, split or not), 3 = BF16 tensor cores on split FP64 operands.
 // Five CTAs per SM (48 registers a thread; a few live values of the update
-// tile's epilogue spill to L1) for the DFMA and TF32 modes, six (40
-// registers) for FP32 panels on FFMA, whose tasks are shortest: more resident
-// CTAs hide each other's latencies (measured: FP32 factor -12 %, FP64 -0.8 %
-// for five against four); the BF16-split mode runs two CTAs per SM, each
-// owning half of the SM's TMEM columns.
+// tile's epilogue spill to L1) for the DFMA mode, six (40 registers) for FP32
+// panels on FFMA, whose tasks are shortest: more resident CTAs hide each
+// other's latencies (measured: FP32 factor -12 %, FP64 -0.8 % for five against
+// four).  The tensor-core modes run two CTAs per SM, as their operand tiles'
+// shared memory allows (the BF16-split CTAs own half of the TMEM each).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 2 : (MODE == 0 && sizeof(T) == 4) ? 6 : 5)
+__global__ void __launch_bounds__(kFactorThreads, MODE != 0 ? 2 : sizeof(T) == 4 ? 6 : 5)
     factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
@@ -1141,12 +1141,12 @@ cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_p
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
-  if (e != cudaSuccess || mma_mode != 3 || *blocks_per_sm >= 2) return e;
-  // The runtime's occupancy query reports one block per SM for this kernel
-  // (it allocates TMEM), while its registers and shared memory allow two (the
-  // profiler's launch statistics agree).  Two is also the design: each CTA
-  // owns 256 of the 512 TMEM columns, and the shared-memory request (over a
-  // third of the SM) keeps a third CTA out.  Count the two limits directly.
+  if (e != cudaSuccess || mma_mode == 0) return e;
+  // The runtime's occupancy query reports one block per SM for the kernels
+  // that allocate TMEM, while their registers and shared memory allow more
+  // (the profiler's launch statistics agree).  Count those limits directly,
+  // capped by the TMEM columns a CTA holds (512 per SM; the BF16-split mode's
+  // shared-memory request, over a third of the SM, also keeps a third CTA out).
   cudaFuncAttributes fa{};
   int dev = 0, regs_sm = 0, smem_sm = 0;
   if ((e = cudaFuncGetAttributes(&fa, fn)) != cudaSuccess || (e = cudaGetDevice(&dev)) != cudaSuccess ||
@@ -1157,7 +1157,8 @@ cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_p
   const size_t smem_cta = smem + fa.sharedSizeBytes + 1024;  // + the driver's per-block reserve
   const int by_regs = regs_cta > 0 ? regs_sm / regs_cta : 0;
   const int by_smem = (int)((size_t)smem_sm / smem_cta);
-  const int direct = std::min(2, std::min(by_regs, by_smem));
+  const int by_tmem = 512 / (mma_mode == 3 ? kOzCols : kTcN);
+  const int direct = std::min(by_tmem, std::min(by_regs, by_smem));
   if (direct > *blocks_per_sm) *blocks_per_sm = direct;
   return cudaSuccess;
 }
