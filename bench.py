@@ -586,7 +586,7 @@ def run_ours(args):
         line["task_profile"] = {k: sp[k] for k in ("factor_task_ms", "factor_task_count", "factor_wait_ms",
                                                    "factor_tc_update_ms",
                                                    "solve_task_ms", "solve_wait_ms", "grid_factor", "grid_solve",
-                                                   "n_supernodes", "n_tasks")}
+                                                   "n_supernodes", "n_tasks", "tma_staging")}
     if rank == 0:
         print(json.dumps(line))
     spchol.destroy(h)

@@ -120,6 +120,7 @@ typedef struct spchol_stats {
   double factor_tc_update_ms; /* part of factor_task_ms[2] spent in tensor-core update tiles */
   int grid_factor;            /* CTAs of the persistent factorization launch */
   int grid_solve;
+  int tma_staging;            /* 1: update-tile operands arrive by TMA (a tensor map per panel); 0: cp.async */
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -9,6 +9,7 @@
 #include <new>
 #include <vector>
 
+#include <cuda.h>  // CUtensorMap and its encoder's signature (called through the runtime's driver entry point)
 #include <cuda_runtime.h>
 
 #include "../../include/spchol.h"
@@ -64,6 +65,7 @@ struct spchol_handle_s {
   int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
   int32_t* d_nu_hi = nullptr;
   int32_t* d_relpos = nullptr;  // relative row indices of the update tiles
+  unsigned char* d_tmaps = nullptr;  // TMA tensor maps, one per panel (null: operands staged by cp.async)
   int32_t* d_trsm_rows = nullptr;
   UTask* d_ut = nullptr;
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
@@ -144,6 +146,45 @@ int upload(spchol_handle_t h, V* dst, const std::vector<V>& src) {
 
 int mma_mode_of(int precision) {
   return precision == SPCHOL_TF32 ? 1 : precision == SPCHOL_TF32X3 ? 2 : precision == SPCHOL_FP64_TC ? 3 : 0;
+}
+
+// One TMA tensor map per panel: the column-major panel as a 2-D tensor of
+// ld rows x w columns (row stride ld elements), box kUpdBoxRows x kUpdKC,
+// zero fill outside.  The encoder is a driver function, reached through the
+// runtime's entry-point query.  Returns false (and the update tiles stage
+// their operands with cp.async) if it is unavailable or rejects a panel.
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+bool build_tensor_maps(spchol_handle_t h, std::vector<CUtensorMap>& maps) {
+  static EncodeTiledFn encode = [] {
+    void* fn = nullptr;
+    cudaDriverEntryPointQueryResult q{};
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &fn, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      fn = nullptr;
+    cudaGetLastError();
+    return reinterpret_cast<EncodeTiledFn>(fn);
+  }();
+  if (!encode) return false;
+  const Plan& P = h->plan;
+  const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  const CUtensorMapDataType dt = h->fp32 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32 : CU_TENSOR_MAP_DATA_TYPE_FLOAT64;
+  maps.resize(P.ns);
+  for (int32_t s = 0; s < P.ns; ++s) {
+    const int w = P.fcol[s + 1] - P.fcol[s];
+    const cuuint64_t dims[2] = {(cuuint64_t)P.ld[s], (cuuint64_t)w};
+    const cuuint64_t strides[1] = {(cuuint64_t)P.ld[s] * esz};
+    const cuuint32_t box[2] = {(cuuint32_t)kUpdBoxRows((int)esz), (cuuint32_t)kUpdKC};
+    const cuuint32_t estr[2] = {1, 1};
+    void* base = static_cast<unsigned char*>(h->d_pool) + (size_t)P.valoff[s] * esz;
+    if (encode(&maps[s], dt, 2, base, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+               CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+               CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+      return false;
+  }
+  return true;
 }
 
 int setup_device(spchol_handle_t h) {
@@ -303,6 +344,16 @@ int setup_device(spchol_handle_t h) {
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
   CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
+  if (mma_mode_of(h->opt.precision) != 1 && mma_mode_of(h->opt.precision) != 2 && P.ns > 0) {
+    std::vector<CUtensorMap> maps;
+    if (build_tensor_maps(h, maps)) {
+      static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
+      CU(cudaMalloc(&h->d_tmaps, maps.size() * sizeof(CUtensorMap)));
+      CU(cudaMemcpyAsync(h->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
+                         g_upload_stream));
+      CU(cudaStreamSynchronize(g_upload_stream));  // the host vector goes out of scope
+    }
+  }
   CU(cudaMalloc(&h->d_relpos, std::max<size_t>((size_t)P.n_rel * sizeof(int32_t), 256)));
   CU(launch_relpos(h->d_ut, P.n_u, h->d_rows, h->d_rowoff, h->d_nrows, h->d_relpos, g_upload_stream));
   if (oz) CU(cudaMalloc(&h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256)));
@@ -339,10 +390,11 @@ int setup_device(spchol_handle_t h) {
   h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
   h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
-                                       (size_t)P.n_rel * sizeof(int32_t) +
+                                       (size_t)P.n_rel * sizeof(int32_t) + (size_t)P.ns * (h->d_tmaps ? 128 : 0) +
                                        (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0));
   h->stats.grid_factor = h->grid_factor;
   h->stats.grid_solve = h->grid_solve;
+  h->stats.tma_staging = h->d_tmaps != nullptr ? 1 : 0;
   return 0;
 }
 
@@ -437,6 +489,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.nu = h->d_nu;
   a.nu_hi = h->d_nu_hi;
   a.relpos = h->d_relpos;
+  a.tmaps = h->d_tmaps;
   a.n_hi = P.n_hi_tasks;
   a.ut = h->d_ut;
   a.n_trsm = P.n_trsm;
@@ -914,6 +967,7 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->d_pool) cudaFree(h->d_pool);
   if (h->d_inv) cudaFree(h->d_inv);
   if (h->d_relpos) cudaFree(h->d_relpos);
+  if (h->d_tmaps) cudaFree(h->d_tmaps);
   if (h->d_slices) cudaFree(h->d_slices);
   if (h->d_trace_f) cudaFree(h->d_trace_f);
   if (h->d_trace_s) cudaFree(h->d_trace_s);

@@ -451,7 +451,7 @@ __global__ void relpos_kernel(const UTask* __restrict__ ut, int n_u, const int32
 template <typename T>
 struct Stage {
   static constexpr int E = 16 / (int)sizeof(T);
-  static constexpr int kStr = kUpdTileM + E;  // row stride, a multiple of E
+  static constexpr int kStr = kUpdBoxRows((int)sizeof(T));  // row stride: 64 + E, a multiple of E
   static constexpr int kPieces = (kUpdTileM + E - 1) / E + 1;  // pieces per k-column, worst alignment
 };
 
@@ -464,6 +464,39 @@ __device__ __forceinline__ void cp_async16(T* dst, const T* src, int valid_elems
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
 template <int N>
 __device__ __forceinline__ void cp_async_wait() { asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory"); }
+
+// TMA staging.  When the handle has a tensor map per panel (a 2-D view of
+// the column-major panel: ld rows x w columns, box kStr rows x kUpdKC
+// columns), one thread loads a k-chunk of an operand with one
+// cp.async.bulk.tensor whose x coordinate (the first row) is rounded down to
+// a 16-byte boundary; rows past ld and columns past w arrive as zeros.  The
+// copies complete on an mbarrier per buffer.
+struct UpdTma {
+  uint32_t mbar[2];  // shared addresses of the two buffers' mbarriers
+  uint32_t* phase;   // shared: parity bits of the next completion of each
+};
+
+__device__ __forceinline__ void tma_load_2d(void* dst, const void* tmap, int x, int y, uint32_t mbar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::
+          "r"(smem_addr(dst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(mbar)
+      : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t mbar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(mbar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_wait_parity(uint32_t mbar, uint32_t phase) {
+  for (int it = 0; it < (1 << 24); ++it) {
+    uint32_t done;
+    asm volatile("{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+                 : "=r"(done)
+                 : "r"(mbar), "r"(phase)
+                 : "memory");
+    if (done) return true;
+  }
+  return false;
+}
 
 // Issue the copies of k-columns k0 .. k0 + kc - 1 of rows r0 .. r0 + len - 1 of
 // a panel (column-major, leading dimension ld) into dst[kk][...].
@@ -527,9 +560,10 @@ __device__ __forceinline__ void upd_strip_nc(int nc, const acc_t* As, const acc_
 
 template <typename T>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
-                            bool skip, int rot) {
+                            bool skip, int rot, const UpdTma& tma) {
   using acc_t = T;
   constexpr int STR = Stage<T>::kStr, E = Stage<T>::E;
+  constexpr uint32_t kBoxBytes = (uint32_t)(kUpdKC * STR * sizeof(T));
   const int tid = threadIdx.x;
   const int s = u.s, t = u.t;
   if (!skip) {
@@ -539,7 +573,10 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     T* Pt = panel_ptr<T>(a, t);
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
 
-    T* buf = reinterpret_cast<T*>(smraw);                 // [2][A, B][kUpdKC][STR]
+    // [2][A, B][kUpdKC][STR], 128-byte aligned (each chunk is a multiple of 128 bytes)
+    T* buf = reinterpret_cast<T*>(smraw + ((128u - (smem_addr(smraw) & 127u)) & 127u));
+    const void* tmap = a.tmaps ? (const void*)(a.tmaps + 128 * (size_t)s) : nullptr;
+    uint32_t ph = tmap ? *tma.phase : 0u;
     constexpr int kBuf = 2 * kUpdKC * STR;                // one buffer: A and B chunks
     int* pos = reinterpret_cast<int*>(buf + 2 * kBuf);    // [kUpdTileM] row position in t
     int* grow = pos + kUpdTileM;                          // [kUpdTileM] global row
@@ -581,12 +618,34 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) acc[rr][cc] = acc_t(0);
       // chunk 0 into buffer 0
-      stage_cols(Ps, lds, u.row0, u.rowlen, 0, min(kUpdKC, ws), buf);
-      stage_cols(Ps, lds, c0, ncol, 0, min(kUpdKC, ws), buf + kUpdKC * STR);
-      cp_async_commit();
+      if (tmap) {
+        if (tid == 0) {
+          asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+          mbar_expect_tx(tma.mbar[0], 2 * kBoxBytes);
+          tma_load_2d(buf, tmap, u.row0 - oa, 0, tma.mbar[0]);
+          tma_load_2d(buf + kUpdKC * STR, tmap, c0 - ob, 0, tma.mbar[0]);
+        }
+      } else {
+        stage_cols(Ps, lds, u.row0, u.rowlen, 0, min(kUpdKC, ws), buf);
+        stage_cols(Ps, lds, c0, ncol, 0, min(kUpdKC, ws), buf + kUpdKC * STR);
+        cp_async_commit();
+      }
       for (int c = 0; c < nchunk; ++c) {
         const int k0 = c * kUpdKC, kc = min(kUpdKC, ws - k0);
-        if (c + 1 < nchunk) {
+        if (tmap) {
+          if (c + 1 < nchunk && tid == 0) {
+            const int b1 = (c + 1) & 1;
+            T* nb = buf + b1 * kBuf;
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(tma.mbar[b1], 2 * kBoxBytes);
+            tma_load_2d(nb, tmap, u.row0 - oa, k0 + kUpdKC, tma.mbar[b1]);
+            tma_load_2d(nb + kUpdKC * STR, tmap, c0 - ob, k0 + kUpdKC, tma.mbar[b1]);
+          }
+          const int b = c & 1;
+          if (!mbar_wait_parity(tma.mbar[b], (ph >> b) & 1u) && tid == 0)
+            atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
+          ph ^= 1u << b;
+        } else if (c + 1 < nchunk) {
           T* nb = buf + ((c + 1) & 1) * kBuf;
           const int k1 = k0 + kUpdKC, kc1 = min(kUpdKC, ws - k1);
           stage_cols(Ps, lds, u.row0, u.rowlen, k1, kc1, nb);
@@ -607,6 +666,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
         }
         __syncthreads();  // buffer c & 1 is refilled by the next iteration's copies
       }
+      if (tmap && tid == 0) *tma.phase = ph;  // every thread has waited on the last chunk
       // Scatter-subtract into panel t: only the lower triangle (row >= column).
       if (active) {
 #pragma unroll
@@ -999,6 +1059,17 @@ __global__ void __launch_bounds__(kFactorThreads, MODE != 0 ? 2 : sizeof(T) == 4
   __shared__ unsigned long long tprof[10];
   if (threadIdx.x == 0)
     for (int k = 0; k < 10; ++k) tprof[k] = 0ull;
+  // TMA staging of the CUDA-core update tiles: one mbarrier per operand buffer
+  __shared__ __align__(8) uint64_t upd_mbar[2];
+  __shared__ uint32_t upd_phase;
+  UpdTma utma{{smem_addr(&upd_mbar[0]), smem_addr(&upd_mbar[1])}, &upd_phase};
+  if (a.tmaps && threadIdx.x == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(utma.mbar[0]), "r"(1) : "memory");
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(utma.mbar[1]), "r"(1) : "memory");
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    upd_phase = 0u;
+  }
+  __syncthreads();
   // tensor-core state (FP32 panels with mma_mode 1 / 2): TMEM accumulator + mbarrier
   __shared__ __align__(8) uint64_t tc_mbar;
   __shared__ uint32_t tc_tmem;
@@ -1065,13 +1136,13 @@ __global__ void __launch_bounds__(kFactorThreads, MODE != 0 ? 2 : sizeof(T) == 4
           type = 3;
           task_update_oz(a, u, smem_raw, sh, skip, tc);
         } else {
-          task_update<T>(a, u, smem_raw, sh, skip, task & 7);
+          task_update<T>(a, u, smem_raw, sh, skip, task & 7, utma);
         }
       }
       else if constexpr (MODE == 1)
         task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
       else
-        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, task & 7);
+        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, task & 7, utma);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
@@ -1126,7 +1197,7 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
     const size_t tcb = 2 * (kTcM + kTcN) * kpad * 4 + (2 * kTcM + kTcN) * sizeof(int) + 1024;
     if (tcb > tri) tri = tcb;
   }
-  size_t upd = (size_t)4 * kUpdKC * Stage<double>::kStr * sizeof(double) +
+  size_t upd = (size_t)4 * kUpdKC * Stage<double>::kStr * sizeof(double) + 128 +
                (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
   return tri > upd ? tri : upd;
 }

@@ -12,6 +12,9 @@ constexpr int kSolveThreads = 256;
 constexpr int kUpdTileM = 64;   // rows of C per update-tile pass (matches the 16x16 thread grid x 4)
 constexpr int kUpdTileN = 64;   // columns of C per pass
 constexpr int kUpdKC = 16;      // k-chunk staged in shared memory
+// TMA box of an update-tile operand chunk: rows (tile rows + the alignment
+// slack of one 16-byte piece) x kUpdKC columns, per element size
+constexpr int kUpdBoxRows(int elem_bytes) { return kUpdTileM + 16 / elem_bytes; }
 constexpr int kSolveNRC = 8;    // right-hand sides per pass
 
 // Panel structure (device pointers).
@@ -36,6 +39,7 @@ struct FactorArgs {
   const int32_t* nu;
   const UTask* ut;
   const int32_t* relpos;  // relative row indices of the update tiles (UTask::rel)
+  const unsigned char* tmaps;  // optional: one 128-byte TMA tensor map per panel (2-D view, see kUpdBox*)
   const int32_t* nu_hi;  // leading update tiles of each panel that go to the high-priority ring
   int32_t n_trsm, n_u, ntask, trsm_rows;
   int32_t n_hi;          // high-priority ring size: ring[0, n_hi); the other ring is ring[n_hi, ntask)

@@ -62,6 +62,7 @@ class Stats(ctypes.Structure):
         ("factor_tc_update_ms", ctypes.c_double),
         ("grid_factor", ctypes.c_int),
         ("grid_solve", ctypes.c_int),
+        ("tma_staging", ctypes.c_int),
     ]
 
     def as_dict(self):
