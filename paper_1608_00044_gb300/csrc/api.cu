@@ -371,12 +371,12 @@ int setup_device(spchol_handle_t h) {
   const int wmax = std::max<int>(P.max_w, 1);
   h->smem_factor = factor_smem_bytes(wmax, mma_mode_of(h->opt.precision));
   if (mma_mode_of(h->opt.precision) == 3) {
-    // each CTA of this mode owns half of the SM's 512 TMEM columns: request
-    // more than a third of the SM's shared memory so that three CTAs can never
-    // share one (a third CTA's allocation would wait)
+    // each CTA of this mode owns a quarter of the SM's 512 TMEM columns:
+    // request more than a fifth of the SM's shared memory so that five CTAs can
+    // never share one (a fifth CTA's allocation would wait)
     int smem_sm = 0;
     CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
-    h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 3 + 1024);
+    h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 5 + 1024);
   }
   h->smem_solve = solve_smem_bytes(wmax);
   int bf = 0, bs = 0;

@@ -895,12 +895,13 @@ __device__ __forceinline__ double fixed64_to_double(long long t, int k) {
       (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// The MMA is M = 128 x N = 32; a tile has at most kOzRows = 64 rows, whose
+// The MMA is M = 128 x N = 16; a tile has at most kOzRows = 64 rows, whose
 // digits are the only A rows kept in shared memory: the MMA's rows 64..127 read
 // whatever follows (in bounds) and land in TMEM lanes that are never read
-// back.  7 groups x 32 columns fit 256 TMEM columns, so two CTAs share an SM.
-constexpr int kOzM = 128, kOzN = 32, kOzRows = 64;
-constexpr int kOzCols = 256;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
+// back.  7 groups x 16 columns fit 128 TMEM columns, and a CTA needs 73 KB of
+// shared memory, so three CTAs share an SM.
+constexpr int kOzM = 128, kOzN = 16, kOzRows = 64;
+constexpr int kOzCols = 128;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
 
 __device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
@@ -1041,10 +1042,11 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // tile's epilogue spill to L1) for the DFMA mode, six (40 registers) for FP32
 // panels on FFMA, whose tasks are shortest: more resident CTAs hide each
 // other's latencies (measured: FP32 factor -12 %, FP64 -0.8 % for five against
-// four).  The tensor-core modes run two CTAs per SM, as their operand tiles'
-// shared memory allows (the BF16-split CTAs own half of the TMEM each).
+// four).  The TF32 mode runs two CTAs per SM and the BF16-split mode three, as
+// their operand tiles' shared memory allows (a BF16-split CTA holds 128 of the
+// SM's 512 TMEM columns).
 template <typename T, int MODE>
-__global__ void __launch_bounds__(kFactorThreads, MODE != 0 ? 2 : sizeof(T) == 4 ? 6 : 5)
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 : sizeof(T) == 4 ? 6 : 5)
     factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
