@@ -937,24 +937,31 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     // 16 bytes).  Rows past rowlen are left as they are: they only feed rows
     // of the product that are never scattered.  Columns past ws are zero in
     // the slices themselves.
-    for (int pr = tid; pr < kSlices * u.rowlen; pr += blockDim.x) {
+    // 16-byte pieces by cp.async (L2 only): every piece of the tile is in
+    // flight at once instead of one load's latency per piece
+    for (int idx = tid; idx < kSlices * u.rowlen * chunks; idx += blockDim.x) {
+      const int c = idx % chunks, pr = idx / chunks;
       const int p = pr / u.rowlen, r = pr - p * u.rowlen;
-      const uint4* src = reinterpret_cast<const uint4*>(sl + ((size_t)p * nb + (u.row0 - ws + r)) * kpad);
-      unsigned char* dst = A0 + p * arow + (r >> 3) * sbo + (r & 7) * 16;
-      for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(dst + c * 128) = __ldcg(src + c);
+      const uint16_t* src = sl + ((size_t)p * nb + (u.row0 - ws + r)) * kpad + 8 * c;
+      unsigned char* dst = A0 + p * arow + (r >> 3) * sbo + (r & 7) * 16 + c * 128;
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
     }
+    cp_async_commit();
     for (int cb = 0; cb < u.seglen; cb += kOzN) {
       const int ncol = min(kOzN, u.seglen - cb);
       for (int j = tid; j < ncol; j += blockDim.x) {
         gcol[j] = Rs[u.seg0 + cb + j];
         eb[j] = ldcg(ex + u.seg0 + cb + j);
       }
-      for (int pr = tid; pr < kSlices * ncol; pr += blockDim.x) {
+      for (int idx = tid; idx < kSlices * ncol * chunks; idx += blockDim.x) {
+        const int c = idx % chunks, pr = idx / chunks;
         const int p = pr / ncol, r = pr - p * ncol;
-        const uint4* src = reinterpret_cast<const uint4*>(sl + ((size_t)p * nb + (u.seg0 + cb - ws + r)) * kpad);
-        unsigned char* dst = B0 + p * brow + (r >> 3) * sbo + (r & 7) * 16;
-        for (int c = 0; c < chunks; ++c) *reinterpret_cast<uint4*>(dst + c * 128) = __ldcg(src + c);
+        const uint16_t* src = sl + ((size_t)p * nb + (u.seg0 + cb - ws + r)) * kpad + 8 * c;
+        unsigned char* dst = B0 + p * brow + (r >> 3) * sbo + (r & 7) * 16 + c * 128;
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(dst)), "l"(src) : "memory");
       }
+      cp_async_commit();
+      cp_async_wait<0>();  // this thread's A (first pass) and B pieces have landed
       asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
       asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
       __syncthreads();
