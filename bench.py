@@ -262,7 +262,7 @@ def _flops_of(spchol, A, perm):
 
 def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, width=64, relax=4):
     """FP64 factorization of the headline matrix with the update tiles of panels
-    at least 32 wide on the BF16 tensor cores (7-way digit split, FP64-accurate
+    at least 16 wide on the BF16 tensor cores (7-way digit split, FP64-accurate
     result; `SPCHOL_FP64_TC`): factor time, the same flop count over it, and the
     backward error of an 8-RHS solve against the oracle's definition."""
     o = spchol.default_options(precision=spchol.FP64_TC, max_width=min(width, 64), relax_zeros=relax)
@@ -280,7 +280,7 @@ def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, wi
     spchol.destroy(h)
     ms = statistics.median(times)
     tf = flops / (ms * 1e-3) / 1e12
-    return {"workload": "same matrix and right-hand sides as the headline; update tiles of panels >= 32 columns on "
+    return {"workload": "same matrix and right-hand sides as the headline; update tiles of panels >= 16 columns on "
                         "BF16 tensor cores (Ozaki-style 7-way split, exact products, 64-bit integer combination)",
             "factor_ms": ms, "tflops_effective": tf, "frac_of_fp64_peak": tf / peak_fp64, "berr": be,
             "solve_ms": st["solve_ms"], "grid_factor": st["grid_factor"],

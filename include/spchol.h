@@ -67,9 +67,10 @@ extern "C" {
 #define SPCHOL_TF32 2  /* as FP32, update GEMMs on TF32 tensor cores (tcgen05.mma kind::tf32) */
 #define SPCHOL_TF32X3 3 /* as TF32, each operand split into a TF32 head and tail, three products per
                            tile: FP32-level accuracy on the tensor cores */
-#define SPCHOL_FP64_TC 4 /* FP64 panels and FP64 result; the update GEMMs run on BF16 tensor cores
-                            (tcgen05.mma kind::f16) on an exact 7-way 8-bit split of each FP64 row
-                            (Ozaki-style error-free transformation), recombined exactly in integers */
+#define SPCHOL_FP64_TC 4 /* FP64 panels and FP64 result; the update GEMMs of panels at least 16 columns
+                            wide run on BF16 tensor cores (tcgen05.mma kind::f16) on an exact 7-way
+                            8-bit split of each FP64 row (Ozaki-style error-free transformation),
+                            recombined exactly in integers; narrower panels keep DFMA tiles */
 
 typedef struct spchol_handle_s* spchol_handle_t;
 
@@ -79,8 +80,8 @@ typedef struct spchol_options {
                              1..128 (1..64 with the tensor-core precisions), default 64 */
   int relax_zeros;        /* amalgamation: a child supernode is merged into its parent when every
                              merged column gains at most this many explicit zeros; default 4, 0 = off */
-  int tile_rows;          /* rows per update tile, 1..64; 0 = default (64; 128 with the tensor-core
-                             precisions, which ignore this field) */
+  int tile_rows;          /* rows per update tile, 1..64; 0 = default (64).  The tensor-core tiles
+                             ignore it: 128 rows for TF32, 64 for SPCHOL_FP64_TC */
   int ctas_per_sm;        /* persistent-kernel CTAs per SM; 0 = as many as fit */
   int deterministic;      /* reserved: 0 */
   int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
