@@ -397,7 +397,9 @@ def measure_serving(full=False, slots=4):
     max_tp = (len(done) - 1) / span if span > 0 else 0.0
     out = {"workload": "Poisson stream: 50% 2D (32^2..256^2) / 50% 3D (16^3..48^3), Laplacian or diffusion, "
                        "1..16 RHS, 30% repeat solves, seed 4321",
-           "slots": slots, "max_requests_per_s": max_tp, "budget_bytes": srv.budget, "runs": []}
+           "slots": slots, "ctas_per_sm": srv.opt_kw["ctas_per_sm"], "max_requests_per_s": max_tp,
+           "budget_bytes": srv.budget, "latency": "arrival (matrix in host memory) to result on the host",
+           "runs": []}
     for f in fracs:
         reqs = serve.make_stream(n_req + warm, rate=f * max_tp, seed=4321 + int(100 * f))
         srv.run(reqs)
