@@ -122,6 +122,9 @@ typedef struct spchol_stats {
   int grid_factor;            /* CTAs of the persistent factorization launch */
   int grid_solve;
   int tma_staging;            /* 1: update-tile operands arrive by TMA (a tensor map per panel); 0: cp.async */
+  int n_subtrees;             /* subtree tasks: small subtrees of the panel tree factored by one CTA each */
+  double factor_subtree_ms;   /* profile: time in subtree tasks (summed over CTAs) */
+  int64_t factor_subtree_count;
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -39,10 +39,13 @@ enum {
   SPCHOL_PLAN_NU = 10,       /* ns: update tiles issued by each panel */
   SPCHOL_PLAN_UTASKS = 11,   /* 6 * n_u: (s, t, seg0, seglen, row0, rowlen) per update tile */
   SPCHOL_PLAN_NST = 12,      /* ns: solve tiles per panel */
-  SPCHOL_PLAN_SCALARS = 13,  /* 11: n, nnz_l, ns, factor tasks, solve tasks, max width, max rows,
-                                nnz_l_stored, n_trsm, n_u, high-priority factor tasks */
+  SPCHOL_PLAN_SCALARS = 13,  /* 12: n, nnz_l, ns, factor tasks (scheduled), solve tasks, max width,
+                                max rows, nnz_l_stored, n_trsm, n_u, high-priority factor tasks,
+                                subtree tasks */
   SPCHOL_PLAN_ADEST = 14,    /* nnz(A): pool index of each entry of A */
-  SPCHOL_PLAN_NUHI = 15      /* ns: leading update tiles of each panel scheduled with high priority */
+  SPCHOL_PLAN_NUHI = 15,     /* ns: leading update tiles of each panel scheduled with high priority */
+  SPCHOL_PLAN_SUBLO = 16,    /* subtree tasks: first panel of each (a subtree is a contiguous range) */
+  SPCHOL_PLAN_SUBHI = 17     /* subtree tasks: last panel (the subtree's root) of each */
 };
 
 /* Host-only analysis; same arguments and return codes as spchol_analyze. */

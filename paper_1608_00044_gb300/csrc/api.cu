@@ -64,6 +64,7 @@ struct spchol_handle_s {
   int64_t *d_rowoff = nullptr, *d_valoff = nullptr, *d_adest = nullptr;
   int32_t *d_trsm_first = nullptr, *d_ntrsm = nullptr, *d_trsm_sn = nullptr, *d_u_first = nullptr, *d_nu = nullptr;
   int32_t* d_nu_hi = nullptr;
+  int32_t *d_sub_lo = nullptr, *d_sub_hi = nullptr;  // subtree tasks' panel ranges
   int32_t* d_relpos = nullptr;  // relative row indices of the update tiles
   unsigned char* d_tmaps = nullptr;  // TMA tensor maps, one per panel (null: operands staged by cp.async)
   int32_t* d_trsm_rows = nullptr;
@@ -101,7 +102,7 @@ struct spchol_handle_s {
   int norms_cap = 0;                      // right-hand sides the norm buffers hold
   double* d_X = nullptr;
   double* d_R = nullptr;
-  unsigned long long* d_prof = nullptr;  // [0..7] factorization, [8..15] solve
+  unsigned long long* d_prof = nullptr;  // [0..9] factorization, [16..23] solve
   unsigned long long* d_trace_f = nullptr;  // profile = 2: per factorization task start/end
   unsigned long long* d_trace_s = nullptr;  // profile = 2: per solve task start/end
   bool traced_f = false, traced_s = false;
@@ -198,12 +199,21 @@ int setup_device(spchol_handle_t h) {
   const bool oz = h->opt.precision == SPCHOL_FP64_TC;
   size_t o_sliceoff = r64(ns + 1), o_rexp = oz ? r32(P.rows.size()) : 0;
   size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
-  size_t o_trows = r32(ns), o_nuhi = r32(ns);
+  size_t o_trows = r32(ns), o_nuhi = r32(ns), o_sublo = r32(P.sub_lo.size()), o_subhi = r32(P.sub_hi.size());
   size_t o_ut = A.reserve(std::max<size_t>(P.ut.size(), 1) * sizeof(UTask));
   size_t o_depi = r32(ns), o_trsi = r32(ns), o_dep = r32(ns), o_trs = r32(ns);
+  // seeds: every subtree task, and the panels outside subtrees with no
+  // incoming update
   std::vector<int32_t> fseeds;
+  for (int32_t k = 0; k < P.n_sub; ++k) fseeds.push_back(ns + P.n_trsm + P.n_u + k);
   for (int s = 0; s < ns; ++s)
-    if (P.dep_f[s] == 0) fseeds.push_back(s);
+    if (P.dep_f[s] == 0 && P.in_sub[s] < 0) fseeds.push_back(s);
+  if (h->opt.fault_inject == 1 && ns > 0 && P.in_sub[ns - 1] >= 0) {
+    // fault injection when the root belongs to a subtree task: that task is
+    // never released (its seed is withheld), so the run must time out
+    const int32_t missing = ns + P.n_trsm + P.n_u + P.in_sub[ns - 1];
+    fseeds.erase(std::find(fseeds.begin(), fseeds.end(), missing));
+  }
   size_t o_fseeds = r32(fseeds.size());
   size_t o_stf = r32(ns), o_nst = r32(ns), o_strows = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
   std::vector<int32_t> nkids(ns, 0), sseeds;
@@ -217,7 +227,7 @@ int setup_device(spchol_handle_t h) {
   size_t o_perm = r32(P.n);
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
-  size_t o_prof = A.reserve(16 * sizeof(unsigned long long));
+  size_t o_prof = A.reserve(24 * sizeof(unsigned long long));
   size_t o_vals = A.reserve(std::max<int64_t>(P.nnz_a, 1) * sizeof(double));
   // full symmetric CSR of A for the refinement residual (mixed precision only)
   std::vector<int64_t> crp, cvm;
@@ -277,6 +287,8 @@ int setup_device(spchol_handle_t h) {
   h->d_u_first = (int32_t*)(b + o_uf);
   h->d_nu = (int32_t*)(b + o_nu);
   h->d_nu_hi = (int32_t*)(b + o_nuhi);
+  h->d_sub_lo = (int32_t*)(b + o_sublo);
+  h->d_sub_hi = (int32_t*)(b + o_subhi);
   h->d_ut = (UTask*)(b + o_ut);
   h->d_dep_init = (int32_t*)(b + o_depi);
   h->d_trsm_init = (int32_t*)(b + o_trsi);
@@ -328,7 +340,8 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
       (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
       (rc = upload(h, h->d_trsm_rows, P.trsm_rows)) ||
-      (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_nu_hi, P.nu_hi)) || (rc = upload(h, h->d_ut, P.ut)) ||
+      (rc = upload(h, h->d_nu, P.nu)) || (rc = upload(h, h->d_nu_hi, P.nu_hi)) ||
+      (rc = upload(h, h->d_sub_lo, P.sub_lo)) || (rc = upload(h, h->d_sub_hi, P.sub_hi)) || (rc = upload(h, h->d_ut, P.ut)) ||
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
@@ -358,9 +371,9 @@ int setup_device(spchol_handle_t h) {
   CU(launch_relpos(h->d_ut, P.n_u, h->d_rows, h->d_rowoff, h->d_nrows, h->d_relpos, g_upload_stream));
   if (oz) CU(cudaMalloc(&h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256)));
   CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
-  CU(cudaMallocHost(&h->h_prof, 16 * sizeof(unsigned long long)));
+  CU(cudaMallocHost(&h->h_prof, 24 * sizeof(unsigned long long)));
   if (h->opt.profile == 2) {
-    CU(cudaMalloc(&h->d_trace_f, 2 * (size_t)std::max(P.n_factor_tasks, 1) * sizeof(unsigned long long)));
+    CU(cudaMalloc(&h->d_trace_f, 2 * (size_t)std::max(P.n_task_ids, 1) * sizeof(unsigned long long)));
     CU(cudaMalloc(&h->d_trace_s, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long)));
   }
   CU(cudaEventCreate(&h->ev0));
@@ -458,6 +471,7 @@ int finish_analyze(spchol_handle_t h, std::chrono::steady_clock::time_point t0) 
   S.flops = P.flops;
   S.n_supernodes = P.ns;
   S.n_tasks = P.n_factor_tasks;
+  S.n_subtrees = P.n_sub;
   S.max_width = P.max_w;
   S.max_rows = P.max_r;
   S.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -488,6 +502,8 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.u_first = h->d_u_first;
   a.nu = h->d_nu;
   a.nu_hi = h->d_nu_hi;
+  a.sub_lo = h->d_sub_lo;
+  a.sub_hi = h->d_sub_hi;
   a.relpos = h->d_relpos;
   a.tmaps = h->d_tmaps;
   a.n_hi = P.n_hi_tasks;
@@ -511,7 +527,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.invoff = h->d_invoff;
   a.prof = profile ? h->d_prof : nullptr;
   a.trace = profile ? h->d_trace_f : nullptr;
-  if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 8 * sizeof(unsigned long long), st));
+  if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 10 * sizeof(unsigned long long), st));
   CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   return 0;
@@ -545,13 +561,15 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
   if (P.ns > 0) {
     rc = status_of(h);
     if (h->opt.profile) {
-      CU(cudaMemcpy(h->h_prof, h->d_prof, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+      CU(cudaMemcpy(h->h_prof, h->d_prof, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
       for (int k = 0; k < 3; ++k) {
         h->stats.factor_task_ms[k] = h->h_prof[k] * 1e-6;
         h->stats.factor_task_count[k] = (int64_t)h->h_prof[4 + k];
       }
       h->stats.factor_wait_ms = h->h_prof[3] * 1e-6;
       h->stats.factor_tc_update_ms = h->h_prof[7] * 1e-6;
+      h->stats.factor_subtree_ms = h->h_prof[8] * 1e-6;
+      h->stats.factor_subtree_count = (int64_t)h->h_prof[9];
     }
   }
   float ms = 0.f;
@@ -598,16 +616,16 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.Y = Y;
   a.ldy = P.n;
   a.nrhs = nrhs;
-  a.prof = h->opt.profile ? h->d_prof + 8 : nullptr;
+  a.prof = h->opt.profile ? h->d_prof + 16 : nullptr;
   a.trace = h->d_trace_s;
-  if (a.prof) CU(cudaMemsetAsync(h->d_prof + 8, 0, 8 * sizeof(unsigned long long), st));
+  if (a.prof) CU(cudaMemsetAsync(h->d_prof + 16, 0, 8 * sizeof(unsigned long long), st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
   int rc = read_status(h, st, P.n_solve_tasks);
   h->traced_s = h->d_trace_s != nullptr;
   if (h->opt.profile) {
-    CU(cudaMemcpy(h->h_prof + 8, h->d_prof + 8, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
-    for (int k = 0; k < 4; ++k) h->stats.solve_task_ms[k] = h->h_prof[8 + k] * 1e-6;
-    h->stats.solve_wait_ms = h->h_prof[12] * 1e-6;
+    CU(cudaMemcpy(h->h_prof + 16, h->d_prof + 16, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+    for (int k = 0; k < 4; ++k) h->stats.solve_task_ms[k] = h->h_prof[16 + k] * 1e-6;
+    h->stats.solve_wait_ms = h->h_prof[20] * 1e-6;
   }
   return rc;
 }
@@ -946,7 +964,7 @@ int spchol_trace_get(spchol_handle_t h, int which, uint64_t* out, int64_t* count
   if (!h) return -1;
   if (which != 0 && which != 1) return -2;
   if (!count) return -4;
-  const int64_t nt = which == 0 ? h->plan.n_factor_tasks : h->plan.n_solve_tasks;
+  const int64_t nt = which == 0 ? h->plan.n_task_ids : h->plan.n_solve_tasks;
   if (!out) {
     *count = nt;
     return 0;

@@ -87,7 +87,7 @@ __device__ __forceinline__ double pivot_recip(double d) {
 }
 
 template <typename T>
-__device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip) {
+__device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip, bool release = true) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s];
@@ -178,7 +178,7 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
       for (int i = j + lane; i < w; i += 32) P[i + (size_t)j * ld] = (T)sm[i + j * w];
   }
   publish_cta_writes();
-  ring2_push_range(rings_of(a), true, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+  if (release) ring2_push_range(rings_of(a), true, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
   if (!skip && ok) {
     // L11^{-1} for the solves, off the critical path (the panel-solve tiles are
     // already released).  X = L11^{-1} by right-looking forward substitution
@@ -273,7 +273,8 @@ __device__ void slice_row(const double* Pi, int w, int ld, int kpad, int nb, int
 // Arithmetic in the panel's type: FP64 panels solve in FP64, FP32 panels (the
 // mixed-precision modes) in FP32.
 template <typename T, int MODE>
-__device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, FactorShared& sh, bool skip) {
+__device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, FactorShared& sh, bool skip,
+                          bool release = true) {
   using ct = T;
   const int tid = threadIdx.x, nt = blockDim.x;
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
@@ -386,6 +387,7 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
     }
   }
   publish_cta_writes();
+  if (!release) return;  // inside a subtree task: no counters, the same CTA goes on
   if (tid == 0) sh.flag = (atom_add_acqrel(&a.trsm_left[s], -1) == 1);
   __syncthreads();
   if (sh.flag) {
@@ -560,7 +562,7 @@ __device__ __forceinline__ void upd_strip_nc(int nc, const acc_t* As, const acc_
 
 template <typename T>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
-                            bool skip, int rot, const UpdTma& tma) {
+                            bool skip, int rot, const UpdTma& tma, bool release = true) {
   using acc_t = T;
   constexpr int STR = Stage<T>::kStr, E = Stage<T>::E;
   constexpr uint32_t kBoxBytes = (uint32_t)(kUpdKC * STR * sizeof(T));
@@ -620,6 +622,9 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       // chunk 0 into buffer 0
       if (tmap) {
         if (tid == 0) {
+          // the panel was written through the generic proxy (by other CTAs, or
+          // by this one inside a subtree task); order that before the TMA reads
+          asm volatile("fence.proxy.async.global;" ::: "memory");
           asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
           mbar_expect_tx(tma.mbar[0], 2 * kBoxBytes);
           tma_load_2d(buf, tmap, u.row0 - oa, 0, tma.mbar[0]);
@@ -685,7 +690,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     }
   }
   publish_cta_writes();
-  if (tid == 0) {
+  if (release && tid == 0) {  // not for a target inside the running subtree task
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
       ring2_push_one(rings_of(a), true, t);
     }
@@ -748,7 +753,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
 }
 
 __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
-                               TcState& tc) {
+                               TcState& tc, bool release = true) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = u.s, t = u.t;
   if (!skip) {
@@ -848,7 +853,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     }
   }
   publish_cta_writes();
-  if (tid == 0) {
+  if (release && tid == 0) {  // not for a target inside the running subtree task
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
       ring2_push_one(rings_of(a), true, t);
     }
@@ -908,7 +913,7 @@ __device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
 }
 
 __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
-                               TcState& tc) {
+                               TcState& tc, bool release = true) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = u.s, t = u.t;
   if (!skip) {
@@ -1036,7 +1041,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     }
   }
   publish_cta_writes();
-  if (tid == 0) {
+  if (release && tid == 0) {  // not for a target inside the running subtree task
     if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
       ring2_push_one(rings_of(a), true, t);
     }
@@ -1062,12 +1067,12 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   __shared__ int pend[2];  // claimed, still empty ring slots (thread 0)
   if (threadIdx.x == 0) pend[0] = pend[1] = -1;
   // per-CTA task timing (thread 0 only, in shared memory so that no register
-  // stays live across the tasks), flushed once at exit: [0..3] busy ns per task
-  // type ([3]: tensor-core update tiles), [4..7] counts, [8] wait ns, [9] start
-  // of the current task
-  __shared__ unsigned long long tprof[10];
+  // stays live across the tasks), flushed once at exit: [0..4] busy ns per task
+  // type ([3]: tensor-core update tiles, [4]: subtree tasks), [5..9] counts,
+  // [10] wait ns, [11] start of the current task
+  __shared__ unsigned long long tprof[12];
   if (threadIdx.x == 0)
-    for (int k = 0; k < 10; ++k) tprof[k] = 0ull;
+    for (int k = 0; k < 12; ++k) tprof[k] = 0ull;
   // TMA staging of the CUDA-core update tiles: one mbarrier per operand buffer
   __shared__ __align__(8) uint64_t upd_mbar[2];
   __shared__ uint32_t upd_phase;
@@ -1120,8 +1125,8 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
       sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
       if (timed) {
         const uint64_t t1 = global_ns();
-        tprof[8] += t1 - t0;
-        tprof[9] = t1;
+        tprof[10] += t1 - t0;
+        tprof[11] = t1;
       }
     }
     __syncthreads();
@@ -1129,7 +1134,42 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
     const bool skip = sh.skip != 0;
     if (task < 0) break;
     int type;
-    if (task < a.pv.ns) {
+    if (task >= a.pv.ns + a.n_trsm + a.n_u) {
+      // Subtree task: every panel of the subtree in postorder, in this CTA.
+      // Targets inside the subtree get their updates before their own turn
+      // (they come later in the order) and keep no counters; updates leaving
+      // the subtree release their targets as usual.  After a failed pivot the
+      // rest of the subtree skips its arithmetic.
+      type = 4;
+      const int k = task - (a.pv.ns + a.n_trsm + a.n_u);
+      const int lo = a.sub_lo[k], hi = a.sub_hi[k];
+      bool sk = skip;
+      for (int s = lo; s <= hi; ++s) {
+        task_potrf<T>(a, s, smd, sh, sk, false);
+        if (threadIdx.x == 0) sh.skip = sk || ld_relaxed(&a.ctrl[kInfo]) != INT_MAX;
+        __syncthreads();
+        sk = sh.skip != 0;
+        for (int kt = 0; kt < a.ntrsm[s]; ++kt) {
+          task_trsm<T, MODE>(a, s, kt, smd, sh, sk, false);
+          __syncthreads();
+        }
+        for (int j = 0; j < a.nu[s]; ++j) {
+          const UTask u = a.ut[a.u_first[s] + j];
+          const bool out = u.t > hi;  // the target is outside the subtree
+          if constexpr (MODE == 3) {
+            if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width)
+              task_update_oz(a, u, smem_raw, sh, sk, tc, out);
+            else
+              task_update<T>(a, u, smem_raw, sh, sk, j & 7, utma, out);
+          } else if constexpr (MODE == 1) {
+            task_update_tc(a, u, smem_raw, sh, sk, tc, out);
+          } else {
+            task_update<T>(a, u, smem_raw, sh, sk, j & 7, utma, out);
+          }
+          __syncthreads();
+        }
+      }
+    } else if (task < a.pv.ns) {
       type = 0;
       task_potrf<T>(a, task, smd, sh, skip);
     } else if (task < a.pv.ns + a.n_trsm) {
@@ -1156,12 +1196,12 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
       if (a.trace) {
-        a.trace[2 * (size_t)task] = tprof[9];
+        a.trace[2 * (size_t)task] = tprof[11];
         a.trace[2 * (size_t)task + 1] = global_ns();
       }
       if (a.prof) {
-        tprof[type] += global_ns() - tprof[9];
-        tprof[4 + type] += 1;
+        tprof[type] += global_ns() - tprof[11];
+        tprof[5 + type] += 1;
       }
     }
     __syncthreads();
@@ -1169,10 +1209,12 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   if (threadIdx.x == 0 && a.prof) {
     for (int k = 0; k < 3; ++k) {
       atomicAdd(&a.prof[k], tprof[k] + (k == 2 ? tprof[3] : 0ull));
-      atomicAdd(&a.prof[4 + k], tprof[4 + k] + (k == 2 ? tprof[7] : 0ull));
+      atomicAdd(&a.prof[4 + k], tprof[5 + k] + (k == 2 ? tprof[8] : 0ull));
     }
-    atomicAdd(&a.prof[3], tprof[8]);
-    atomicAdd(&a.prof[7], tprof[3]);  // tensor-core share of the update tiles
+    atomicAdd(&a.prof[3], tprof[10]);
+    atomicAdd(&a.prof[7], tprof[3]);   // tensor-core share of the update tiles
+    atomicAdd(&a.prof[8], tprof[4]);   // subtree tasks
+    atomicAdd(&a.prof[9], tprof[9]);
   }
   if (use_tc) {
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");

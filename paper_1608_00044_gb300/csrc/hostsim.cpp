@@ -146,7 +146,8 @@ int64_t spchol_plan_len(spchol_plan_t p, int what) {
     case SPCHOL_PLAN_NU: case SPCHOL_PLAN_NST: case SPCHOL_PLAN_NUHI: return P.ns;
     case SPCHOL_PLAN_ROWS: return (int64_t)P.rows.size();
     case SPCHOL_PLAN_UTASKS: return 6 * (int64_t)P.ut.size();
-    case SPCHOL_PLAN_SCALARS: return 11;
+    case SPCHOL_PLAN_SCALARS: return 12;
+    case SPCHOL_PLAN_SUBLO: case SPCHOL_PLAN_SUBHI: return (int64_t)P.sub_lo.size();
     case SPCHOL_PLAN_ADEST: return (int64_t)P.a_dest.size();
     default: return -1;
   }
@@ -173,6 +174,8 @@ int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
     case SPCHOL_PLAN_NU: cp(P.nu); break;
     case SPCHOL_PLAN_NST: cp(P.nst); break;
     case SPCHOL_PLAN_NUHI: cp(P.nu_hi); break;
+    case SPCHOL_PLAN_SUBLO: cp(P.sub_lo); break;
+    case SPCHOL_PLAN_SUBHI: cp(P.sub_hi); break;
     case SPCHOL_PLAN_ADEST: cp(P.a_dest); break;
     case SPCHOL_PLAN_UTASKS:
       for (size_t i = 0; i < P.ut.size(); ++i) {
@@ -184,7 +187,7 @@ int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
     case SPCHOL_PLAN_SCALARS:
       dst[0] = P.n; dst[1] = P.nnz_l; dst[2] = P.ns; dst[3] = P.n_factor_tasks; dst[4] = P.n_solve_tasks;
       dst[5] = P.max_w; dst[6] = P.max_r; dst[7] = P.nnz_l_stored; dst[8] = P.n_trsm; dst[9] = P.n_u;
-      dst[10] = P.n_hi_tasks;
+      dst[10] = P.n_hi_tasks; dst[11] = P.n_sub;
       break;
     default: return -2;
   }
@@ -211,7 +214,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   // update tiles of each panel).  Every push is counted against its ring's
   // size, and each ring must receive exactly as many tasks as it holds.
   std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
-  std::vector<char> ran(P.n_factor_tasks, 0);
+  std::vector<char> ran(P.n_task_ids, 0);
   Ready hi, lo;
   const int64_t n_hi = P.n_hi_tasks, n_lo = (int64_t)P.n_factor_tasks - P.n_hi_tasks;
   int64_t hi_pushed = 0, lo_pushed = 0;
@@ -225,28 +228,50 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       overflow |= ++lo_pushed > n_lo;
     }
   };
+  const int sub0 = ns + P.n_trsm + P.n_u;  // first subtree task id
+  for (int k = 0; k < P.n_sub; ++k) push(true, sub0 + k);
   for (int s = 0; s < ns; ++s)
-    if (dep[s] == 0) push(true, s);
+    if (dep[s] == 0 && P.in_sub[s] < 0) push(true, s);
   int done = 0;
   while (!hi.empty() || !lo.empty()) {
     if (overflow) return SPCHOL_EINTERNAL;
     const bool from_hi = !hi.empty() && (lo.empty() || (rng.next() & 1));
     const int task = from_hi ? hi.pop(rng) : lo.pop(rng);
-    if (task < 0 || task >= P.n_factor_tasks || ran[task]) return SPCHOL_EINTERNAL;
+    if (task < 0 || task >= P.n_task_ids || ran[task]) return SPCHOL_EINTERNAL;
     ran[task] = 1;
     ++done;
     const bool skip = sim.info != 0;
-    if (task < ns) {
+    if (task >= sub0) {  // subtree task: its panels in order; counters only for targets outside
+      const int k = task - sub0, lo = P.sub_lo[k], hi = P.sub_hi[k];
+      for (int s = lo; s <= hi; ++s) {
+        if (P.in_sub[s] != k) return SPCHOL_EINTERNAL;
+        if (sim.info == 0) sim.potrf(s);
+        for (int kt = 0; kt < P.ntrsm[s]; ++kt)
+          if (sim.info == 0) sim.trsm(s, kt);
+        for (int j = 0; j < P.nu[s]; ++j) {
+          const UTask& u = P.ut[P.u_first[s] + j];
+          if (sim.info == 0) sim.update(u);
+          if (u.t > hi) {
+            if (P.in_sub[u.t] >= 0) return SPCHOL_EINTERNAL;  // an outside target is never in another subtree
+            if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
+            if (dep[u.t] == 0) push(true, u.t);
+          }
+        }
+      }
+    } else if (task < ns) {
+      if (P.in_sub[task] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.potrf(task);
       for (int k = 0; k < P.ntrsm[task]; ++k) push(true, ns + P.trsm_first[task] + k);
     } else if (task < ns + P.n_trsm) {
       const int kt = task - ns, s = P.trsm_sn[kt];
+      if (P.in_sub[s] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.trsm(s, kt - P.trsm_first[s]);
       if (--tleft[s] < 0) return SPCHOL_EINTERNAL;
       if (tleft[s] == 0)
         for (int k = 0; k < P.nu[s]; ++k) push(k < P.nu_hi[s], ns + P.n_trsm + P.u_first[s] + k);
     } else {
       const UTask& u = P.ut[task - ns - P.n_trsm];
+      if (P.in_sub[u.s] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.update(u);
       if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
       if (dep[u.t] == 0) push(true, u.t);

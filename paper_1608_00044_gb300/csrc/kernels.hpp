@@ -41,6 +41,8 @@ struct FactorArgs {
   const int32_t* relpos;  // relative row indices of the update tiles (UTask::rel)
   const unsigned char* tmaps;  // optional: one 128-byte TMA tensor map per panel (2-D view, see kUpdBox*)
   const int32_t* nu_hi;  // leading update tiles of each panel that go to the high-priority ring
+  const int32_t* sub_lo;  // subtree tasks: first and last panel of each
+  const int32_t* sub_hi;
   int32_t n_trsm, n_u, ntask, trsm_rows;
   int32_t n_hi;          // high-priority ring size: ring[0, n_hi); the other ring is ring[n_hi, ntask)
   int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products);
@@ -57,7 +59,8 @@ struct FactorArgs {
   void* pool;          // double* or float*
   double* inv;         // per panel: L11^{-1} (w x w, column-major, lower part)
   const int64_t* invoff;
-  unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts
+  unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts,
+                             // [7] tensor-core update ns, [8] subtree-task ns, [9] subtree tasks
   unsigned long long* trace; // optional: per task id, start and end ns
 };
 

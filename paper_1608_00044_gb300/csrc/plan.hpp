@@ -38,6 +38,9 @@ struct PlanParams {
   int tc_min_width = 0;
   int tc_tile_rows = 128;
   bool slice_fp64 = false;  // FP64 tensor-core mode: split those panels into BF16 digits
+  // Subtree tasks: a maximal subtree of the panel etree whose factorization
+  // costs at most subtree_flops runs as one task (0: none).
+  double subtree_flops = 1e6;
 };
 
 struct Plan {
@@ -79,7 +82,15 @@ struct Plan {
   // top_depth of the root), go to the high-priority ready ring; n_hi_tasks of
   // them in all.  The remaining update tiles go to the other ring.
   std::vector<int32_t> nu_hi;
-  int32_t n_trsm = 0, n_u = 0, n_factor_tasks = 0, n_hi_tasks = 0;
+  // Subtree tasks: task ns + n_trsm + n_u + k factors panels sub_lo[k] ..
+  // sub_hi[k] (a whole subtree: panels are numbered in postorder) in order in
+  // one CTA; the panel-level tasks of those panels are never scheduled.
+  // in_sub[s]: the subtree task of panel s, or -1.
+  std::vector<int32_t> sub_lo, sub_hi, in_sub;
+  int32_t n_trsm = 0, n_u = 0, n_sub = 0;
+  int32_t n_task_ids = 0;      // size of the task id space: ns + n_trsm + n_u + n_sub
+  int32_t n_factor_tasks = 0;  // tasks that are scheduled (pushed to a ring) in one factorization
+  int32_t n_hi_tasks = 0;
 
   // solve tasks
   std::vector<int32_t> st_first, nst, st_sn, st_rows;  // st_rows: solve tile rows per panel

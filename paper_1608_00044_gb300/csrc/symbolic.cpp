@@ -371,9 +371,48 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   }
   P.n_trsm = (int32_t)P.trsm_sn.size();
   P.n_u = (int32_t)P.ut.size();
-  P.n_factor_tasks = ns + P.n_trsm + P.n_u;
-  P.n_hi_tasks = ns + P.n_trsm;
-  for (int32_t s = 0; s < ns; ++s) P.n_hi_tasks += P.nu_hi[s];
+
+  // ---- subtree tasks ------------------------------------------------------------
+  // Flops of each panel's own tasks, summed over subtrees (children precede
+  // their parents in the postorder); maximal subtrees within the budget become
+  // one task each.  A subtree is the contiguous panel range from its first
+  // descendant to its root.
+  std::vector<double> sub_fl(ns, 0.0);
+  for (int32_t s = 0; s < ns; ++s) {
+    const double w = P.fcol[s + 1] - P.fcol[s], nb = P.nrows[s] - w;
+    sub_fl[s] += w * w * w / 3.0 + nb * w * w;
+  }
+  for (const UTask& u : P.ut) sub_fl[u.s] += 2.0 * (P.fcol[u.s + 1] - P.fcol[u.s]) * u.rowlen * u.seglen;
+  std::vector<int32_t> first_desc(ns);
+  for (int32_t s = 0; s < ns; ++s) first_desc[s] = s;
+  for (int32_t s = 0; s < ns; ++s)
+    if (P.parent[s] >= 0) {
+      sub_fl[P.parent[s]] += sub_fl[s];
+      first_desc[P.parent[s]] = std::min(first_desc[P.parent[s]], first_desc[s]);
+    }
+  P.sub_lo.clear();
+  P.sub_hi.clear();
+  P.in_sub.assign(ns, -1);
+  if (prm.subtree_flops > 0.0)
+    for (int32_t s = 0; s < ns; ++s) {
+      const bool small = sub_fl[s] <= prm.subtree_flops;
+      const bool root = small && (P.parent[s] < 0 || sub_fl[P.parent[s]] > prm.subtree_flops);
+      if (root && s > first_desc[s]) {  // a subtree of one panel gains nothing
+        const int32_t k = (int32_t)P.sub_lo.size();
+        P.sub_lo.push_back(first_desc[s]);
+        P.sub_hi.push_back(s);
+        for (int32_t q = first_desc[s]; q <= s; ++q) P.in_sub[q] = k;
+      }
+    }
+  P.n_sub = (int32_t)P.sub_lo.size();
+  P.n_task_ids = ns + P.n_trsm + P.n_u + P.n_sub;
+  P.n_factor_tasks = P.n_sub;
+  P.n_hi_tasks = P.n_sub;
+  for (int32_t s = 0; s < ns; ++s)
+    if (P.in_sub[s] < 0) {
+      P.n_factor_tasks += 1 + P.ntrsm[s] + P.nu[s];
+      P.n_hi_tasks += 1 + P.ntrsm[s] + P.nu_hi[s];
+    }
 
   // ---- solve tasks ------------------------------------------------------------
   // near the root (the critical path of both sweeps) the tiles are shorter

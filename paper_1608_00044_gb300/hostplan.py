@@ -12,7 +12,8 @@ from .spchol import Options, default_options_host
 _HERE = os.path.dirname(os.path.abspath(__file__))
 HOST_LIB_PATH = os.path.join(_HERE, "libspchol_host.so")
 
-PERM, COLCOUNT, ETREE, FCOL, NROWS, ROWOFF, ROWS, PARENT, DEPF, NTRSM, NU, UTASKS, NST, SCALARS, ADEST, NUHI = range(16)
+(PERM, COLCOUNT, ETREE, FCOL, NROWS, ROWOFF, ROWS, PARENT, DEPF, NTRSM, NU, UTASKS, NST, SCALARS, ADEST, NUHI, SUBLO,
+ SUBHI) = range(18)
 
 _vp = ctypes.c_void_p
 SIGNATURES = [
@@ -76,7 +77,7 @@ class HostPlan:
     def scalars(self) -> dict:
         v = self.get(SCALARS)
         keys = ["n", "nnz_l", "ns", "factor_tasks", "solve_tasks", "max_w", "max_r", "nnz_l_stored", "n_trsm", "n_u",
-                "n_hi_tasks"]
+                "n_hi_tasks", "n_sub"]
         return dict(zip(keys, (int(x) for x in v)))
 
     def simulate(self, values, B=None, seed=0, want_pool=False):

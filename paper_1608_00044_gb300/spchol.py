@@ -63,6 +63,9 @@ class Stats(ctypes.Structure):
         ("grid_factor", ctypes.c_int),
         ("grid_solve", ctypes.c_int),
         ("tma_staging", ctypes.c_int),
+        ("n_subtrees", ctypes.c_int),
+        ("factor_subtree_ms", ctypes.c_double),
+        ("factor_subtree_count", ctypes.c_int64),
     ]
 
     def as_dict(self):

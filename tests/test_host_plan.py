@@ -191,6 +191,68 @@ def test_high_priority_tiles_are_parent_tiles_near_the_root(name, W):
         n_par = int(np.sum(tiles[:, 1] == par[s])) if par[s] >= 0 else 0
         assert nuhi[s] == (n_par if depth[s] < 128 else 0)
         assert np.all(tiles[:nuhi[s], 1] == par[s])
-    assert sc["n_hi_tasks"] == ns + sc["n_trsm"] + int(nuhi.sum())
-    assert sc["factor_tasks"] == ns + sc["n_trsm"] + sc["n_u"]
+    # scheduled tasks: one per subtree task, and for each panel outside the
+    # subtree tasks its diagonal task, panel-solve tiles and update tiles (the
+    # leading parent tiles near the root in the high-priority ring)
+    ntr = P.get(hp.NTRSM)
+    lo, hi = P.get(hp.SUBLO), P.get(hp.SUBHI)
+    inside = np.zeros(ns, bool)
+    for a, b in zip(lo, hi):
+        inside[a:b + 1] = True
+    out = ~inside
+    assert sc["n_sub"] == len(lo)
+    assert sc["n_hi_tasks"] == len(lo) + int((1 + ntr[out] + nuhi[out]).sum())
+    assert sc["factor_tasks"] == len(lo) + int((1 + ntr[out] + nu[out]).sum())
     assert 0 < sc["n_hi_tasks"] <= sc["factor_tasks"]
+
+
+
+@pytest.mark.parametrize("name,W", [("lap3d_20", 8), ("lap2d_64", 16), ("diff3d_9", 64)])
+def test_subtree_tasks_are_maximal_small_subtrees(name, W):
+    """Subtree tasks are disjoint, each exactly the set of descendants of its
+    root (a contiguous range in the postorder), within the flop budget of 1e6,
+    and maximal: the root's parent's subtree exceeds the budget."""
+    A, perm, b = gridgen.workload(name)
+    P = _plan(A, perm, max_width=W)
+    par, fcol, nrows = P.get(hp.PARENT), P.get(hp.FCOL), P.get(hp.NROWS)
+    ut = P.get(hp.UTASKS).reshape(-1, 6)
+    lo, hi = P.get(hp.SUBLO), P.get(hp.SUBHI)
+    ns = len(par)
+    w = np.diff(fcol).astype(float)
+    fl = w ** 3 / 3 + (nrows - w) * w ** 2
+    np.add.at(fl, ut[:, 0], 2.0 * w[ut[:, 0]] * ut[:, 5] * ut[:, 3])
+    sub = fl.copy()
+    for s in range(ns):
+        if par[s] >= 0:
+            sub[par[s]] += sub[s]
+    seen = np.zeros(ns, bool)
+    assert len(lo) > 0
+    for a, r in zip(lo, hi):
+        assert a < r and not seen[a:r + 1].any()
+        seen[a:r + 1] = True
+        # descendants of r: walk every panel of the range up to r
+        for q in range(a, r + 1):
+            x = q
+            while x != r:
+                x = par[x]
+                assert a <= x <= r
+        if a > 0:  # the panel before the range is not a descendant of r
+            x = a - 1
+            while x >= 0 and x != r:
+                x = par[x]
+            assert x != r
+        assert sub[r] <= 1e6 * (1 + 1e-9)
+        assert par[r] < 0 or sub[par[r]] > 1e6
+
+
+def test_random_order_with_subtree_tasks():
+    """A plan with subtree tasks runs the protocol (subtree tasks alongside the
+    panel-level tasks of the rest) to the oracle's accuracy."""
+    A, perm, b = gridgen.workload("lap3d_20")
+    P = _plan(A, perm, max_width=16)
+    assert P.scalars()["n_sub"] > 0
+    B = gridgen.rhs_uniform(A.n, 2, seed=3)
+    for seed in range(3):
+        rc, X, pool = P.simulate(A.values, B, seed=seed)
+        assert rc == 0
+        assert oracle.berr(A, X, B) <= 1e-14
