@@ -1111,97 +1111,140 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   // that the claim's round trip overlaps the current task; it joins pend[1] at
   // the next claim (a deep ring fills it long before).
   int ahead = -1;
+  // Subtree task cursor (thread 0): a claimed subtree task is run as a
+  // sequence of panel-level steps through the same dispatch as the ring's
+  // tasks -- diagonal, panel-solve tiles, update tiles of each panel in
+  // postorder -- with counters only for targets outside the subtree.
+  __shared__ int cur_task, cur_lo, cur_hi, cur_s, cur_ph, cur_i, cur_skip;
+  __shared__ int step_kind, step_s, step_i, step_release, step_last;
+  if (threadIdx.x == 0) cur_task = -1;
+  const int sub0 = a.pv.ns + a.n_trsm + a.n_u;  // first subtree task id
   for (;;) {
     if (threadIdx.x == 0) {
       const bool timed = a.prof || a.trace;
-      const uint64_t t0 = timed ? global_ns() : 0;
-      if (ahead >= 0) {
-        pend[1] = ahead < q.n_lo ? ahead : -1;
-        ahead = -1;
+      if (cur_task < 0) {
+        const uint64_t t0 = timed ? global_ns() : 0;
+        if (ahead >= 0) {
+          pend[1] = ahead < q.n_lo ? ahead : -1;
+          ahead = -1;
+        }
+        int lo_ready;
+        sh.task = ring2_claim(q, pend, &lo_ready);
+        if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
+        sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
+        if (timed) {
+          const uint64_t t1 = global_ns();
+          tprof[10] += t1 - t0;
+          tprof[11] = t1;
+        }
+        if (sh.task >= sub0) {
+          const int k = sh.task - sub0;
+          cur_task = sh.task;
+          cur_lo = a.sub_lo[k];
+          cur_hi = a.sub_hi[k];
+          cur_s = cur_lo;
+          cur_ph = 0;
+          cur_i = 0;
+          cur_skip = sh.skip;
+        }
       }
-      int lo_ready;
-      sh.task = ring2_claim(q, pend, &lo_ready);
-      if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
-      sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
-      if (timed) {
-        const uint64_t t1 = global_ns();
-        tprof[10] += t1 - t0;
-        tprof[11] = t1;
+      if (cur_task >= 0) {  // the next step of the subtree, then advance the cursor
+        const int s = cur_s;
+        step_kind = cur_ph;
+        step_s = s;
+        step_i = cur_i;
+        step_release = cur_ph == 2 ? (a.ut[a.u_first[s] + cur_i].t > cur_hi) : 0;
+        sh.skip = cur_skip;
+        sh.task = cur_task;
+        int ph = cur_ph, i = cur_i + 1;
+        if (ph == 0) {
+          ph = 1;
+          i = 0;
+        }
+        if (ph == 1 && i >= a.ntrsm[s]) {
+          ph = 2;
+          i = 0;
+        }
+        step_last = 0;
+        if (ph == 2 && i >= a.nu[s]) {
+          if (s < cur_hi) {
+            cur_s = s + 1;
+            ph = 0;
+            i = 0;
+          } else {
+            step_last = 1;
+          }
+        }
+        cur_ph = ph;
+        cur_i = i;
+      } else if (sh.task >= 0) {  // a task of the rings
+        const int task = sh.task;
+        step_release = 1;
+        step_last = 1;
+        if (task < a.pv.ns) {
+          step_kind = 0;
+          step_s = task;
+          step_i = 0;
+        } else if (task < a.pv.ns + a.n_trsm) {
+          const int kt = task - a.pv.ns;
+          step_kind = 1;
+          step_s = a.trsm_sn[kt];
+          step_i = kt - a.trsm_first[step_s];
+        } else {
+          step_kind = 3;  // an update tile by its global index
+          step_s = -1;
+          step_i = task - a.pv.ns - a.n_trsm;
+        }
       }
     }
     __syncthreads();
     const int task = sh.task;
-    const bool skip = sh.skip != 0;
     if (task < 0) break;
+    const bool skip = sh.skip != 0;
+    const int kind = step_kind, s = step_s, si = step_i;
+    const bool release = step_release != 0;
     int type;
-    if (task >= a.pv.ns + a.n_trsm + a.n_u) {
-      // Subtree task: every panel of the subtree in postorder, in this CTA.
-      // Targets inside the subtree get their updates before their own turn
-      // (they come later in the order) and keep no counters; updates leaving
-      // the subtree release their targets as usual.  After a failed pivot the
-      // rest of the subtree skips its arithmetic.
-      type = 4;
-      const int k = task - (a.pv.ns + a.n_trsm + a.n_u);
-      const int lo = a.sub_lo[k], hi = a.sub_hi[k];
-      bool sk = skip;
-      for (int s = lo; s <= hi; ++s) {
-        task_potrf<T>(a, s, smd, sh, sk, false);
-        if (threadIdx.x == 0) sh.skip = sk || ld_relaxed(&a.ctrl[kInfo]) != INT_MAX;
-        __syncthreads();
-        sk = sh.skip != 0;
-        for (int kt = 0; kt < a.ntrsm[s]; ++kt) {
-          task_trsm<T, MODE>(a, s, kt, smd, sh, sk, false);
-          __syncthreads();
-        }
-        for (int j = 0; j < a.nu[s]; ++j) {
-          const UTask u = a.ut[a.u_first[s] + j];
-          const bool out = u.t > hi;  // the target is outside the subtree
-          if constexpr (MODE == 3) {
-            if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width)
-              task_update_oz(a, u, smem_raw, sh, sk, tc, out);
-            else
-              task_update<T>(a, u, smem_raw, sh, sk, j & 7, utma, out);
-          } else if constexpr (MODE == 1) {
-            task_update_tc(a, u, smem_raw, sh, sk, tc, out);
-          } else {
-            task_update<T>(a, u, smem_raw, sh, sk, j & 7, utma, out);
-          }
-          __syncthreads();
-        }
-      }
-    } else if (task < a.pv.ns) {
+    if (kind == 0) {
       type = 0;
-      task_potrf<T>(a, task, smd, sh, skip);
-    } else if (task < a.pv.ns + a.n_trsm) {
+      task_potrf<T>(a, s, smd, sh, skip, release);
+    } else if (kind == 1) {
       type = 1;
-      const int kt = task - a.pv.ns;
-      const int s = a.trsm_sn[kt];
-      task_trsm<T, MODE>(a, s, kt - a.trsm_first[s], smd, sh, skip);
+      task_trsm<T, MODE>(a, s, si, smd, sh, skip, release);
     } else {
       type = 2;
+      const int ui = kind == 2 ? a.u_first[s] + si : si;
+      const UTask u = a.ut[ui];
       if constexpr (MODE == 3) {
-        const UTask u = a.ut[task - a.pv.ns - a.n_trsm];
         if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width) {
           type = 3;
-          task_update_oz(a, u, smem_raw, sh, skip, tc);
+          task_update_oz(a, u, smem_raw, sh, skip, tc, release);
         } else {
-          task_update<T>(a, u, smem_raw, sh, skip, task & 7, utma);
+          task_update<T>(a, u, smem_raw, sh, skip, ui & 7, utma, release);
         }
+      } else if constexpr (MODE == 1) {
+        task_update_tc(a, u, smem_raw, sh, skip, tc, release);
+      } else {
+        task_update<T>(a, u, smem_raw, sh, skip, ui & 7, utma, release);
       }
-      else if constexpr (MODE == 1)
-        task_update_tc(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, tc);
-      else
-        task_update<T>(a, a.ut[task - a.pv.ns - a.n_trsm], smem_raw, sh, skip, task & 7, utma);
     }
     if (threadIdx.x == 0) {
-      atomicAdd(&a.ctrl[kDone], 1);
-      if (a.trace) {
-        a.trace[2 * (size_t)task] = tprof[11];
-        a.trace[2 * (size_t)task + 1] = global_ns();
+      const bool in_sub = cur_task >= 0;
+      if (in_sub) {
+        type = 4;
+        // after a failed pivot the rest of the subtree skips its arithmetic
+        if (kind == 0 && ld_relaxed(&a.ctrl[kInfo]) != INT_MAX) cur_skip = 1;
       }
-      if (a.prof) {
-        tprof[type] += global_ns() - tprof[11];
-        tprof[5 + type] += 1;
+      if (step_last) {
+        atomicAdd(&a.ctrl[kDone], 1);
+        if (a.trace) {
+          a.trace[2 * (size_t)task] = tprof[11];
+          a.trace[2 * (size_t)task + 1] = global_ns();
+        }
+        if (a.prof) {
+          tprof[type] += global_ns() - tprof[11];
+          tprof[5 + type] += 1;
+        }
+        if (in_sub) cur_task = -1;
       }
     }
     __syncthreads();
