@@ -39,7 +39,8 @@ struct PlanParams {
   int tc_tile_rows = 128;
   bool slice_fp64 = false;  // FP64 tensor-core mode: split those panels into BF16 digits
   // Subtree tasks: a maximal subtree of the panel etree whose factorization
-  // costs at most subtree_flops runs as one task (0: none).
+  // costs at most min(subtree_flops, total flops / 4096) runs as one task
+  // (0: none).
   double subtree_flops = 1e6;
 };
 

@@ -393,10 +393,17 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.sub_lo.clear();
   P.sub_hi.clear();
   P.in_sub.assign(ns, -1);
+  // A subtree task runs serially in one CTA, so the budget is also capped at
+  // 1/4096 of the whole factorization: a small problem keeps enough
+  // independent pieces of work to spread over the GPU.
+  double total = 0.0;
+  for (int32_t s = 0; s < ns; ++s)
+    if (P.parent[s] < 0) total += sub_fl[s];
+  const double budget = std::min(prm.subtree_flops, total / 4096.0);
   if (prm.subtree_flops > 0.0)
     for (int32_t s = 0; s < ns; ++s) {
-      const bool small = sub_fl[s] <= prm.subtree_flops;
-      const bool root = small && (P.parent[s] < 0 || sub_fl[P.parent[s]] > prm.subtree_flops);
+      const bool small = sub_fl[s] <= budget;
+      const bool root = small && (P.parent[s] < 0 || sub_fl[P.parent[s]] > budget);
       if (root && s > first_desc[s]) {  // a subtree of one panel gains nothing
         const int32_t k = (int32_t)P.sub_lo.size();
         P.sub_lo.push_back(first_desc[s]);
