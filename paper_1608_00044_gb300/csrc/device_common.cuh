@@ -13,11 +13,11 @@ enum CtrlWord : int {
   kTail = 1,     // next ring slot to fill
   kErr = 2,      // 0, or an SPCHOL_E* code (timeout, internal check)
   kInfo = 3,     // smallest failing pivot column + 1, INT32_MAX if none
-  kDone = 4,     // tasks completed (consistency check)
   kWhere = 5,    // diagnostic: task id where a wait gave up
-  kHiHead = 32,  // the factorization's high-priority ring, in its own 128-byte line
+  kHiHead = 32,  // the high-priority ring, in its own 128-byte line
   kHiTail = 33,
-  kCtrlWords = 64
+  kDone = 64,    // tasks completed: the end test, updated by every task, in a line of its own
+  kCtrlWords = 96
 };
 
 __device__ __forceinline__ int ld_acquire(const int* p) {

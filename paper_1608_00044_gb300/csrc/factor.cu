@@ -1129,7 +1129,7 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
           ahead = -1;
         }
         int lo_ready;
-        sh.task = ring2_claim(q, pend, &lo_ready);
+        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
         if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
         sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
         if (timed) {

@@ -293,13 +293,24 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   std::vector<int> ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
   std::vector<char> sran(P.n_solve_tasks, 0);
   // Two rings as in the GPU kernel: the seeds (panels with no incoming forward
-  // tile) fill the normal-priority ring; every task made ready by another
-  // goes to the high-priority ring, which must receive exactly the rest.
+  // tile) fill the normal-priority ring; a task made ready by another is kept
+  // as the releasing CTA's next task when that slot is free (continuation),
+  // else goes to the high-priority ring.  Kept and pushed tasks must together
+  // be exactly the non-seed tasks.
   Ready q, qs;
-  int64_t s_seeds = 0, s_pushed = 0;
+  int64_t s_seeds = 0, s_pushed = 0, s_kept = 0;
+  int next = -1;
   auto spush = [&](int t) {
     q.push(t);
     ++s_pushed;
+  };
+  auto skeep = [&](int t) {
+    if (next < 0) {
+      next = t;
+      ++s_kept;
+    } else {
+      spush(t);
+    }
   };
   for (int s = 0; s < ns; ++s)
     if (fdep[s] == 0) {
@@ -307,9 +318,14 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       ++s_seeds;
     }
   int sdone = 0;
-  while (!q.empty() || !qs.empty()) {
-    const bool from_hi = !q.empty() && (qs.empty() || (rng.next() & 1));
-    const int task = from_hi ? q.pop(rng) : qs.pop(rng);
+  while (next >= 0 || !q.empty() || !qs.empty()) {
+    int task = next;
+    if (task >= 0) {
+      next = -1;
+    } else {
+      const bool from_hi = !q.empty() && (qs.empty() || (rng.next() & 1));
+      task = from_hi ? q.pop(rng) : qs.pop(rng);
+    }
     if (task < 0 || task >= P.n_solve_tasks || sran[task]) return SPCHOL_EINTERNAL;
     sran[task] = 1;
     ++sdone;
@@ -323,10 +339,11 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           for (int i = j + 1; i < w; ++i) y[i] -= L[i + (size_t)j * ld] * y[j];
         }
       }
+      // the first forward tile (or the backward diagonal task) continues here
       if (P.nst[s] > 0)
-        for (int k = 0; k < P.nst[s]; ++k) spush(ns + P.st_first[s] + k);
+        for (int k = 0; k < P.nst[s]; ++k) skeep(ns + P.st_first[s] + k);
       else
-        spush(ns + 2 * nst + s);
+        skeep(ns + 2 * nst + s);
     } else if (task < ns + nst) {  // FWD_T
       const int kt = task - ns, s = P.st_sn[kt], k = kt - P.st_first[s];
       const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
@@ -342,13 +359,13 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       for (int e = P.st_tptr[kt]; e < P.st_tptr[kt + 1]; ++e) {
         const int t = P.st_tgt[e];
         if (--fdep[t] < 0) return SPCHOL_EINTERNAL;
-        if (fdep[t] == 0) spush(t);
+        if (fdep[t] == 0) skeep(t);
       }
       if (--ft[s] < 0) return SPCHOL_EINTERNAL;
       if (ft[s] == 0)
         for (int k2 = 0; k2 < P.nst[s]; ++k2) {
           const int tile = P.st_first[s] + k2;
-          if (--bdep[tile] == 0) spush(ns + nst + tile);
+          if (--bdep[tile] == 0) skeep(ns + nst + tile);
         }
     } else if (task < ns + 2 * nst) {  // BWD_T
       const int kt = task - ns - nst, s = P.st_sn[kt], k = kt - P.st_first[s];
@@ -363,7 +380,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           Y[f + j + (size_t)r * n] -= acc;
         }
       if (--bt[s] < 0) return SPCHOL_EINTERNAL;
-      if (bt[s] == 0) spush(ns + 2 * nst + s);
+      if (bt[s] == 0) skeep(ns + 2 * nst + s);
     } else {  // BWD_D
       const int s = task - ns - 2 * nst, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
       const double* L = sim.panel(s);
@@ -377,11 +394,11 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       for (int e = P.rt_ptr[s]; e < P.rt_ptr[s + 1]; ++e) {
         const int tile = P.rt_tile[e];
         if (--bdep[tile] < 0) return SPCHOL_EINTERNAL;
-        if (bdep[tile] == 0) spush(ns + nst + tile);
+        if (bdep[tile] == 0) skeep(ns + nst + tile);
       }
     }
   }
-  if (sdone != P.n_solve_tasks || s_pushed != P.n_solve_tasks - s_seeds) return SPCHOL_EINTERNAL;
+  if (sdone != P.n_solve_tasks || s_pushed + s_kept != P.n_solve_tasks - s_seeds) return SPCHOL_EINTERNAL;
   for (int r = 0; r < nrhs; ++r)
     for (int64_t i = 0; i < n; ++i) B[P.perm[i] + (size_t)r * ldb] = Y[i + (size_t)r * n];
   return 0;

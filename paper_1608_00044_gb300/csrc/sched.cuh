@@ -107,7 +107,7 @@ struct Ring2 {
 // has been claimed, another CTA reported an error, or the wait ran out.
 // *lo_ready: unclaimed slots of the normal-priority ring at the last look (0
 // if the task came from the high-priority ring before the other was read).
-__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_ready) {
+__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_ready, int ntask_total) {
   *lo_ready = 0;
   const uint64_t t0 = global_ns();
   const uint64_t max_iter = (uint64_t)(q.budget_ns / 32) + 100000;
@@ -144,7 +144,13 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
     // An idle grid polls these words from every CTA: the error word is read on
     // every 8th round only, and the backoff grows to 2 us, so that the polling
     // does not queue up the claims and pushes on the same L2 lines.
-    if ((it & 7) == 7 && ld_relaxed(&q.ctrl[kErr]) != 0) return -1;
+    if ((it & 7) == 7) {
+      if (ld_relaxed(&q.ctrl[kErr]) != 0) return -1;
+      // a task made ready may run in the CTA that released it without passing
+      // through a ring, so the rings' slot counts do not tell the end: the
+      // completed-task count does
+      if (ld_relaxed(&q.ctrl[kDone]) >= ntask_total) return -1;
+    }
     if (it > max_iter || (int64_t)(global_ns() - t0) > q.budget_ns) {
       atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
       atomicExch(&q.ctrl[kWhere], pend[0] >= 0 ? pend[0] : pend[1]);
@@ -176,7 +182,7 @@ __device__ __forceinline__ void ring2_push_range(const Ring2& q, bool hi, int fi
   __syncthreads();
 }
 
-// Thread 0 only: push one ready task to one ring of a Ring2.
+// Any thread: push one ready task to one ring of a Ring2.
 __device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task) {
   const int slot = atomicAdd(&q.ctrl[hi ? kHiTail : kTail], 1);
   if (slot < (hi ? q.n_hi : q.n_lo)) {
@@ -184,6 +190,13 @@ __device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task
   } else {
     atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
   }
+}
+
+// Continuation: a task made ready by the running one is kept for this CTA's
+// next turn if none is kept yet (*next, shared memory, -1 when empty), else
+// pushed to the high-priority ring.  Any thread; next == nullptr: always push.
+__device__ __forceinline__ void keep_or_push(const Ring2& q, int* next, int task) {
+  if (next == nullptr || atomicCAS(next, -1, task) != -1) ring2_push_one(q, true, task);
 }
 
 // Make this CTA's global writes visible before a counter update or a push.

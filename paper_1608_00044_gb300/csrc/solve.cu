@@ -30,6 +30,7 @@ struct SolveShared {
   int task;
   int flag;
   int base;
+  int next;  // continuation: a task this CTA made ready and runs next (-1: none)
 };
 
 template <typename T>
@@ -287,7 +288,7 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
 // Whole CTA; each thread issues its decrements in batches of 8 whose round
 // trips overlap (a panel near the root releases thousands of tiles).
 __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* list, int e0, int e1, int32_t* cnt,
-                                              int task0) {
+                                              int task0, int* next) {
   for (int base = e0 + threadIdx.x; base < e1; base += 8 * blockDim.x) {
     int id[8], old[8];
 #pragma unroll
@@ -299,7 +300,7 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
     for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_acqrel(&cnt[id[u]], -1) : 0;
 #pragma unroll
     for (int u = 0; u < 8; ++u)
-      if (id[u] >= 0 && old[u] == 1) ring2_push_one(q, true, task0 + id[u]);
+      if (id[u] >= 0 && old[u] == 1) keep_or_push(q, next, task0 + id[u]);
   }
 }
 
@@ -313,15 +314,23 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
   // every leaf.
   const Ring2 q{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
   __shared__ int pend[2];
-  if (threadIdx.x == 0) pend[0] = pend[1] = -1;
+  if (threadIdx.x == 0) {
+    pend[0] = pend[1] = -1;
+    sh.next = -1;
+  }
   const int ns = a.pv.ns, nst = a.n_st;
   unsigned long long busy[4] = {0, 0, 0, 0}, wait = 0;
   for (;;) {
     uint64_t t1 = 0;
     if (threadIdx.x == 0) {
       const uint64_t t0 = a.prof ? global_ns() : 0;
-      int lo_ready;
-      sh.task = ring2_claim(q, pend, &lo_ready);
+      if (sh.next >= 0) {  // continue with a task this CTA made ready
+        sh.task = sh.next;
+        sh.next = -1;
+      } else {
+        int lo_ready;
+        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
+      }
       if (a.prof) {
         t1 = global_ns();
         wait += t1 - t0;
@@ -335,10 +344,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       const int s = task;
       fwd_diag(a, s, sm);
       publish_cta_writes();
+      // continue with the first forward tile (the rows of the parent) and
+      // release the others
       if (a.nst[s] > 0) {
-        ring2_push_range(q, true, ns + a.st_first[s], a.nst[s], &sh.base);
+        if (threadIdx.x == 0) sh.next = ns + a.st_first[s];
+        ring2_push_range(q, true, ns + a.st_first[s] + 1, a.nst[s] - 1, &sh.base);
       } else if (threadIdx.x == 0) {
-        ring2_push_one(q, true, ns + 2 * nst + s);
+        sh.next = ns + 2 * nst + s;
       }
     } else if (task < ns + nst) {
       const int kt = task - ns, s = a.st_sn[kt];
@@ -348,21 +360,21 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       // root has thousands of dependent tiles, and they sit on the critical path.
       for (int e = a.st_tptr[kt] + threadIdx.x; e < a.st_tptr[kt + 1]; e += blockDim.x) {
         const int t = a.st_tgt[e];
-        if (atom_add_acqrel(&a.fdep[t], -1) == 1) ring2_push_one(q, true, t);
+        if (atom_add_acqrel(&a.fdep[t], -1) == 1) keep_or_push(q, &sh.next, t);
       }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
-      if (sh.flag) release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst);
+      if (sh.flag) release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, &sh.next);
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
-      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) ring2_push_one(q, true, ns + 2 * nst + s);
+      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) keep_or_push(q, &sh.next, ns + 2 * nst + s);
     } else {
       const int s = task - ns - 2 * nst;
       bwd_diag(a, s, sm);
       publish_cta_writes();
-      release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst);
+      release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, &sh.next);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
