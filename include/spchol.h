@@ -70,7 +70,12 @@ extern "C" {
 #define SPCHOL_FP64_TC 4 /* FP64 panels and FP64 result; the update GEMMs of panels at least 16 columns
                             wide run on BF16 tensor cores (tcgen05.mma kind::f16) on an exact 7-way
                             8-bit split of each FP64 row (Ozaki-style error-free transformation),
-                            recombined exactly in integers; narrower panels keep DFMA tiles */
+                            recombined exactly in integers; narrower panels keep DFMA tiles.  The
+                            solves' panel tiles (panels 16..64 wide) run the same split on the
+                            BF16 tensor cores (mma.sync).  The error of a split product is bounded
+                            by 2^-56 max|row| max|column| per term, not per product: FP64 backward
+                            error, but rows and columns of very different scales lose forward
+                            accuracy that SPCHOL_FP64 keeps */
 
 typedef struct spchol_handle_s* spchol_handle_t;
 

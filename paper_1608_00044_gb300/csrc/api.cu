@@ -391,7 +391,7 @@ int setup_device(spchol_handle_t h) {
     CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
     h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 5 + 1024);
   }
-  h->smem_solve = solve_smem_bytes(wmax);
+  h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), h->smem_factor, &bf));
   CU(solve_configure(h->fp32, h->smem_solve, &bs));
@@ -616,6 +616,7 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.Y = Y;
   a.ldy = P.n;
   a.nrhs = nrhs;
+  a.tc_tiles = h->opt.precision == SPCHOL_FP64_TC ? 1 : 0;
   a.prof = h->opt.profile ? h->d_prof + 16 : nullptr;
   a.trace = h->d_trace_s;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof + 16, 0, 8 * sizeof(unsigned long long), st));
@@ -899,6 +900,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.Y = Y;
   a.ldy = n;
   a.nrhs = nrhs;
+  a.tc_tiles = h->opt.precision == SPCHOL_FP64_TC ? 1 : 0;
   a.prof = nullptr;
   a.trace = nullptr;
   CU(launch_solve(false, a, h->grid_solve, h->smem_solve, st));

@@ -91,6 +91,7 @@ struct SolveArgs {
   double* Y;        // n x nrhs, permuted order
   int64_t ldy;
   int nrhs;
+  int tc_tiles;     // 1: FP64 panel tiles 16..64 wide as split products on the tensor cores (FP64_TC mode)
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
   unsigned long long* trace; // optional: per task id, start and end ns
 };
@@ -103,7 +104,7 @@ cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st);
 
 // solve.cu
-size_t solve_smem_bytes(int max_w);
+size_t solve_smem_bytes(int max_w, bool tc_tiles);
 cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm);
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,

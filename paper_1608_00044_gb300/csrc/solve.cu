@@ -38,6 +38,282 @@ __device__ __forceinline__ const T* spanel(const SolveArgs& a, int s) {
   return reinterpret_cast<const T*>(a.pool) + a.pv.valoff[s];
 }
 
+// ---------------------------------------------------------------- FP64 products on the BF16 tensor cores
+// The panel tiles' products C = A B (A: up to 64 x 64 of L21 or its
+// transpose, B: up to 64 x 8 right-hand sides) cost w FP64 FMAs per output,
+// and the FP64 pipe retires 2 FMAs per clock per SM.  For FP64 panels 16 to 64
+// wide they run instead as exact integer products on the BF16 tensor
+// cores (the splitting of Ozaki, Ogita, Oishi and Rump, "Error-free
+// transformations of matrix multiplication by using fast routines of matrix
+// multiplication", Numer. Algorithms 2012): with e_i the smallest integer such
+// that every |A_ik| of row i is below 2^e_i, A_ik 2^(56 - e_i) truncated to an
+// integer q_ik < 2^56 is cut into kOzSl 8-bit digits; digit p, with the sign of
+// A_ik, is an integer in [-255, 255] (exact in BF16) of weight
+// 2^(e_i - 8(p + 1)).  B is split the same way per column.  Products of digit
+// p of A and digit q of B with p + q = d are summed (mma.sync m16n8k8, FP32
+// accumulation) into group d; for K <= 64 a group d <= 3 stays below 2^24 and
+// is exact, the others round at most 2^-56 relative to the leading group.
+// Products with p + q >= kOzSl weigh below 2^-56 and are dropped.  The seven
+// group sums are combined exactly into two integers and converted to FP64 with
+// one rounding.  The result differs from the exact product by at most a few
+// units of 2^-56 max_k|A_ik| max_k|B_kj| K, the size of an FP64 dot
+// product's own rounding bound.
+constexpr int kOzSl = 7;     // digits per value
+constexpr int kOzLda = 65;   // staged A: row m at As[m * kOzLda] (odd: no bank conflicts down a column)
+constexpr int kOzBLd = 72;   // staged B digits: (slice q, column n) row of 64 + 8 BF16 (no bank conflicts)
+constexpr int kOzMaxK = 64;  // K and M of one pass (the exactness bound above)
+constexpr int kOzMinW = 16;  // narrower panels keep the FP64 FMA path (their products are tiny)
+
+struct OzBuf {
+  double* As;   // [64][kOzLda]; its first 14 KB also hold the second K half's group sums
+  double* Bs;   // [8][64]: B column n at Bs[n * 64]
+  uint16_t* Bd; // [kOzSl][8][kOzBLd]
+  int* eA;      // [64] biased exponent bits of each A row's largest entry (0: zero row)
+  int* eB;      // [8]
+};
+
+__device__ __forceinline__ OzBuf oz_carve(double* sm) {
+  OzBuf b;
+  b.As = sm;
+  b.Bs = b.As + 64 * kOzLda;
+  b.Bd = reinterpret_cast<uint16_t*>(b.Bs + 8 * 64);
+  b.eA = reinterpret_cast<int*>(b.Bd + kOzSl * 8 * kOzBLd);
+  b.eB = b.eA + 64;
+  return b;
+}
+
+constexpr size_t kOzSmemBytes =
+    (64 * kOzLda + 8 * 64) * sizeof(double) + kOzSl * 8 * kOzBLd * sizeof(uint16_t) + 72 * sizeof(int);
+
+__device__ __forceinline__ int exp_bits(double x) { return (int)((__double_as_longlong(x) >> 52) & 0x7FF); }
+
+// |x| 2^(56 - e), e = emax - 1022, truncated to an integer below 2^56, as its
+// bits 32..55 (hi) and 0..31 (lo).  emax: the biased exponent bits of the
+// largest |x| of the row; subnormal x count as zero.
+__device__ __forceinline__ void oz_fix(double x, int emax, uint32_t& hi, uint32_t& lo) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7FF);
+  unsigned long long q = 0ull;
+  if (ex != 0) {
+    const unsigned long long mant = (b & 0xFFFFFFFFFFFFFull) | (1ull << 52);
+    const int sh = ex - emax + 3;  // at most 3
+    q = sh >= 0 ? (mant << sh) : (sh > -64 ? (mant >> (-sh)) : 0ull);
+  }
+  hi = (uint32_t)(q >> 32);
+  lo = (uint32_t)q;
+}
+
+// Digit p (0 most significant) of the 56-bit integer (hi, lo).
+template <int P>
+__device__ __forceinline__ uint32_t oz_digit(uint32_t hi, uint32_t lo) {
+  if constexpr (P < 3)
+    return (hi >> (16 - 8 * P)) & 0xFFu;
+  else
+    return (lo >> (24 - 8 * (P - 3))) & 0xFFu;
+}
+
+// Two digits d0, d1 < 256 as a BF16 pair (d0 in the low half), signs from
+// sgn (bit 15: d0, bit 31: d1).  2^23 + d is exact in FP32 and subtracting
+// 2^23 leaves d, whose FP32 bits have zeros in their low half: the high half is
+// d in BF16.
+__device__ __forceinline__ uint32_t oz_pair(uint32_t d0, uint32_t d1, uint32_t sgn) {
+  const float f0 = __uint_as_float(0x4B000000u | d0) - 8388608.0f;
+  const float f1 = __uint_as_float(0x4B000000u | d1) - 8388608.0f;
+  return __byte_perm(__float_as_uint(f0), __float_as_uint(f1), 0x7632) ^ sgn;
+}
+
+__device__ __forceinline__ uint32_t oz_signs(double x0, double x1) {
+  return ((uint32_t)((unsigned long long)__double_as_longlong(x0) >> 63) << 15) |
+         ((uint32_t)((unsigned long long)__double_as_longlong(x1) >> 63) << 31);
+}
+
+__device__ __forceinline__ void mma_bf16_1688(float (&c)[4], uint32_t a0, uint32_t a1, uint32_t b0) {
+  asm volatile("mma.sync.aligned.m16n8k8.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5}, {%6}, {%0,%1,%2,%3};"
+               : "+f"(c[0]), "+f"(c[1]), "+f"(c[2]), "+f"(c[3])
+               : "r"(a0), "r"(a1), "r"(b0));
+}
+
+// One warp: the group sums of the 16 x 8 block of C whose rows are m0 .. m0+15,
+// over the k blocks kb0 <= kb < kb1 of 16, each as two m16n8k8 steps.
+// Fragment layout of m16n8k8 (g = lane / 4, t = lane % 4): A elements (g |
+// g+8, 2t | 2t+1), B elements (2t | 2t+1, g), C elements acc[d][0..3] at (g,
+// 2t), (g, 2t+1), (g+8, 2t), (g+8, 2t+1).
+__device__ __forceinline__ void oz_block(const OzBuf& b, int m0, int kb0, int kb1, float (&acc)[kOzSl][4]) {
+  const int lane = threadIdx.x & 31, g = lane >> 2, t = lane & 3;
+  const int e0 = b.eA[m0 + g], e1 = b.eA[m0 + g + 8];
+  const double* r0 = b.As + (m0 + g) * kOzLda + 2 * t;
+  const double* r1 = b.As + (m0 + g + 8) * kOzLda + 2 * t;
+  const uint16_t* bg = b.Bd + g * kOzBLd + 2 * t;
+  for (int k8 = 2 * kb0; k8 < 2 * kb1; ++k8) {
+    const int c0 = 8 * k8;
+    const double x[4] = {r0[c0], r0[c0 + 1], r1[c0], r1[c0 + 1]};
+    // hi carries the sign in bit 31 (its digits use bits 0..23)
+    uint32_t hi[4], lo[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      oz_fix(x[e], (e & 2) ? e1 : e0, hi[e], lo[e]);
+      hi[e] |= (uint32_t)((unsigned long long)__double_as_longlong(x[e]) >> 63) << 31;
+    }
+    const uint16_t* bk = bg + c0;
+#define SPCHOL_OZ_SLICE(P)                                                                               \
+  {                                                                                                     \
+    uint32_t a0 = oz_pair(oz_digit<P>(hi[0], lo[0]), oz_digit<P>(hi[1], lo[1]),                          \
+                          ((hi[0] >> 31) << 15) | (hi[1] & 0x80000000u));                               \
+    uint32_t a1 = oz_pair(oz_digit<P>(hi[2], lo[2]), oz_digit<P>(hi[3], lo[3]),                          \
+                          ((hi[2] >> 31) << 15) | (hi[3] & 0x80000000u));                               \
+    _Pragma("unroll") for (int q = 0; q < kOzSl - P; ++q)                                               \
+        mma_bf16_1688(acc[P + q], a0, a1, *reinterpret_cast<const uint32_t*>(bk + q * 8 * kOzBLd));      \
+  }
+    SPCHOL_OZ_SLICE(0)
+    SPCHOL_OZ_SLICE(1)
+    SPCHOL_OZ_SLICE(2)
+    SPCHOL_OZ_SLICE(3)
+    SPCHOL_OZ_SLICE(4)
+    SPCHOL_OZ_SLICE(5)
+    SPCHOL_OZ_SLICE(6)
+#undef SPCHOL_OZ_SLICE
+  }
+}
+
+// Exact integer x (|x| < 2^51) as a double: x + 2^52 + 2^51 in the mantissa field.
+__device__ __forceinline__ double oz_i2d(long long x) {
+  return __longlong_as_double(x + 0x4338000000000000LL) - 6755399441055744.0;
+}
+
+// The value of output c of this thread: t = sum_d G_d 2^(8 (6 - d)) (G_0..G_2
+// and G_3..G_6 combined exactly in two integers below 2^42 and 2^50, one
+// rounding in the final FMA), times 2^(ea + eb - 2108) for the biased
+// exponent bits ea, eb of the row of A and the column of B.
+__device__ __forceinline__ double oz_value(const float (&acc)[kOzSl][4], int c, int ea, int eb) {
+  if (ea == 0 || eb == 0) return 0.0;
+  long long h = __float2int_rn(acc[0][c]);
+  h = h * 256 + __float2int_rn(acc[1][c]);
+  h = h * 256 + __float2int_rn(acc[2][c]);
+  long long l = __float2int_rn(acc[3][c]);
+  l = l * 256 + __float2int_rn(acc[4][c]);
+  l = l * 256 + __float2int_rn(acc[5][c]);
+  l = l * 256 + __float2int_rn(acc[6][c]);
+  const double tv = fma(oz_i2d(h), 4294967296.0, oz_i2d(l));
+  const int E = ea + eb - 2108;
+  if (E >= -1022 && E <= 1023) return tv * __longlong_as_double((long long)(E + 1023) << 52);
+  return ldexp(tv, E);
+}
+
+// Digits of the staged B (K x 8, K <= 64, column n at Bs[n * 64]) into Bd,
+// with each column's exponent in eB; entries k >= K (up to K rounded up to 16)
+// are zero.  All threads; ends with a barrier.
+__device__ __forceinline__ void oz_split_b(const OzBuf& b, int K) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int kpad = (K + 15) & ~15;
+  for (int n = warp; n < 8; n += kSolveThreads / 32) {
+    int e = 0;
+    for (int k = lane; k < K; k += 32) e = max(e, exp_bits(b.Bs[n * 64 + k]));
+    e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    if (lane == 0) b.eB[n] = e;
+  }
+  __syncthreads();
+  for (int idx = threadIdx.x; idx < 8 * (kpad / 2); idx += blockDim.x) {
+    const int n = idx / (kpad / 2), k = 2 * (idx - n * (kpad / 2));
+    const double x0 = k < K ? b.Bs[n * 64 + k] : 0.0, x1 = k + 1 < K ? b.Bs[n * 64 + k + 1] : 0.0;
+    uint32_t h0, l0, h1, l1;
+    oz_fix(x0, b.eB[n], h0, l0);
+    oz_fix(x1, b.eB[n], h1, l1);
+    const uint32_t sg = oz_signs(x0, x1);
+    uint32_t* dst = reinterpret_cast<uint32_t*>(b.Bd + n * kOzBLd + k);
+    dst[0 * 8 * kOzBLd / 2] = oz_pair(oz_digit<0>(h0, l0), oz_digit<0>(h1, l1), sg);
+    dst[1 * 8 * kOzBLd / 2] = oz_pair(oz_digit<1>(h0, l0), oz_digit<1>(h1, l1), sg);
+    dst[2 * 8 * kOzBLd / 2] = oz_pair(oz_digit<2>(h0, l0), oz_digit<2>(h1, l1), sg);
+    dst[3 * 8 * kOzBLd / 2] = oz_pair(oz_digit<3>(h0, l0), oz_digit<3>(h1, l1), sg);
+    dst[4 * 8 * kOzBLd / 2] = oz_pair(oz_digit<4>(h0, l0), oz_digit<4>(h1, l1), sg);
+    dst[5 * 8 * kOzBLd / 2] = oz_pair(oz_digit<5>(h0, l0), oz_digit<5>(h1, l1), sg);
+    dst[6 * 8 * kOzBLd / 2] = oz_pair(oz_digit<6>(h0, l0), oz_digit<6>(h1, l1), sg);
+  }
+  __syncthreads();
+}
+
+// C = A B for the staged A (M x K, M, K <= 64, zero past M and K up to their
+// multiples of 16) and the split B: out(c, m, n, value) for every output m < M,
+// n < nrc, called by the thread that owns it (c: its slot 0..3, fixed per
+// thread for a given M and K).  Warps w and w + 4 take m block w % 4 and the
+// lower and upper halves of the k blocks; the upper half's group sums are
+// added exactly to the lower's through shared memory (they are integers with
+// an exact sum below 2^24 in the exact groups).  All threads; begins after the
+// staging barrier and ends with one; A is overwritten.
+template <class Out>
+__device__ __forceinline__ void oz_product(const OzBuf& b, int M, int K, int nrc, Out out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // row exponents: warp w takes rows w, w + 8, ...
+  for (int m = warp; m < M; m += kSolveThreads / 32) {
+    int e = 0;
+    for (int k = lane; k < K; k += 32) e = max(e, exp_bits(b.As[m * kOzLda + k]));
+    e = (int)__reduce_max_sync(0xffffffffu, (unsigned)e);
+    if (lane == 0) b.eA[m] = e;
+  }
+  __syncthreads();
+  const int mb = warp & 3, half = warp >> 2, m0 = 16 * mb;
+  const int nkb = (K + 15) >> 4, split = (nkb + 1) >> 1;
+  float acc[kOzSl][4];
+#pragma unroll
+  for (int d = 0; d < kOzSl; ++d)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) acc[d][c] = 0.0f;
+  const bool active = m0 < M;
+  if (active) oz_block(b, m0, half ? split : 0, half ? nkb : split, acc);
+  __syncthreads();  // A is read; its space takes the upper half's sums
+  float* gx = reinterpret_cast<float*>(b.As) + (size_t)mb * (kOzSl * 4 * 32);
+  if (active && half && split < nkb) {
+#pragma unroll
+    for (int d = 0; d < kOzSl; ++d)
+#pragma unroll
+      for (int c = 0; c < 4; ++c) gx[(d * 4 + c) * 32 + lane] = acc[d][c];
+  }
+  __syncthreads();
+  if (active && !half) {
+    if (split < nkb) {
+#pragma unroll
+      for (int d = 0; d < kOzSl; ++d)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[d][c] += gx[(d * 4 + c) * 32 + lane];
+    }
+    const int g = lane >> 2, t = lane & 3;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int m = m0 + g + ((c & 2) ? 8 : 0), n = 2 * t + (c & 1);
+      if (m < M && n < nrc) out(c, m, n, oz_value(acc, c, b.eA[m], b.eB[n]));
+    }
+  }
+  __syncthreads();
+}
+
+// Zero the staged A outside its M x K corner, up to 64 rows and K rounded up to 16.
+__device__ __forceinline__ void oz_zero_pad(const OzBuf& b, int M, int K) {
+  const int kpad = (K + 15) & ~15, mpad = (M + 15) & ~15;
+  for (int idx = threadIdx.x; idx < mpad * kpad; idx += blockDim.x) {
+    const int m = idx / kpad, k = idx - m * kpad;
+    if (m >= M || k >= K) b.As[m * kOzLda + k] = 0.0;
+  }
+}
+
+// dst(i, src(i)) for i < total, the loads issued in batches of 8 per thread so
+// that their latencies overlap (a load followed by its store, one at a time,
+// costs a full memory round trip per element).
+template <class Src, class Dst>
+__device__ __forceinline__ void copy_batched(int total, Src src, Dst dst) {
+  for (int base = threadIdx.x; base < total; base += 8 * blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      v[u] = idx < total ? src(idx) : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < 8; ++u) {
+      const int idx = base + u * blockDim.x;
+      if (idx < total) dst(idx, v[u]);
+    }
+  }
+}
+
 // L11^{-1} (w x w, column-major, read-only here) into shared memory with
 // leading dimension lx, the lower triangle only; loads in batches of 8.
 __device__ __forceinline__ void stage_inverse(const double* __restrict__ X, int w, double* __restrict__ Xs, int lx) {
@@ -61,6 +337,22 @@ __device__ __forceinline__ void stage_inverse(const double* __restrict__ X, int 
 // every entry is an independent dot product, no sequential substitution.
 // Thread (r, c) computes rows c and w - 1 - c for right-hand side r: i + 1
 // and w - i terms, w + 1 in all, so every thread and warp does the same work.
+// Stage y_s (w entries of right-hand sides r0 .. r0+nrc-1) as the B operand.
+__device__ __forceinline__ void oz_stage_ys(const SolveArgs& a, const OzBuf& b, int f, int w, int r0, int nrc) {
+  const double* Y = a.Y + f + (size_t)r0 * a.ldy;
+  const int64_t ldy = a.ldy;
+  copy_batched(
+      8 * w,
+      [&](int idx) {
+        const int n = idx / w;
+        return n < nrc ? ldcg(Y + (idx - n * w) + n * ldy) : 0.0;
+      },
+      [&](int idx, double v) {
+        const int n = idx / w;
+        b.Bs[n * 64 + (idx - n * w)] = v;
+      });
+}
+
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
@@ -185,6 +477,33 @@ __device__ void fwd_tile_rows(const SolveArgs& a, const T* P, int ld, int row0, 
   }
 }
 
+// y[rows of tile] -= L21[tile] y_s on the tensor cores (FP64 panels, 16 <= w
+// <= 64): the tile's rows in passes of 64.
+__device__ void fwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row0, int cnt, const int32_t* R, int f,
+                            int w, double* sm) {
+  const OzBuf b = oz_carve(sm);
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    __syncthreads();
+    oz_stage_ys(a, b, f, w, r0, nrc);
+    __syncthreads();
+    oz_split_b(b, w);
+    for (int c0 = 0; c0 < cnt; c0 += kOzMaxK) {
+      const int mc = min(kOzMaxK, cnt - c0);
+      const double* Pc = P + row0 + c0;
+      copy_batched(
+          mc * w, [&](int idx) { return Pc[idx % mc + (size_t)(idx / mc) * ld]; },
+          [&](int idx, double v) { b.As[(idx % mc) * kOzLda + idx / mc] = v; });
+      oz_zero_pad(b, mc, w);
+      __syncthreads();
+      double* Y = a.Y + (size_t)r0 * a.ldy;
+      const int64_t ldy = a.ldy;
+      const int32_t* Rc = R + row0 + c0;
+      oz_product(b, mc, w, nrc, [&](int, int m, int n, double v) { red_add(Y + Rc[m] + n * ldy, -v); });
+    }
+  }
+}
+
 template <typename T>
 __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
@@ -192,6 +511,12 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  if constexpr (sizeof(T) == 8) {
+    if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
+      fwd_tile_oz(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm);
+      return;
+    }
+  }
   double* Ys = sm;  // [kSolveNRC][w], zero past nrc
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
@@ -217,6 +542,50 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
 // column j of the chunk against x with four accumulators.
 constexpr int kBwdCH = 64;
 
+// y_s -= L21[tile]^T x[rows of tile] on the tensor cores (FP64 panels, 16 <= w
+// <= 64): A = L21[tile]^T (w x rows), the tile's rows in passes of 64, each with
+// its own exponents; the passes' results are summed in FP64 by the owning
+// threads and subtracted once.
+__device__ void bwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row0, int cnt, const int32_t* R, int f,
+                            int w, double* sm) {
+  const OzBuf b = oz_carve(sm);
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    double part[4] = {0.0, 0.0, 0.0, 0.0};
+    for (int c0 = 0; c0 < cnt; c0 += kOzMaxK) {
+      const int kc = min(kOzMaxK, cnt - c0);
+      __syncthreads();
+      const double* Pc = P + row0 + c0;
+      copy_batched(
+          kc * w, [&](int idx) { return Pc[idx % kc + (size_t)(idx / kc) * ld]; },
+          [&](int idx, double v) { b.As[(idx / kc) * kOzLda + idx % kc] = v; });
+      oz_zero_pad(b, w, kc);
+      const int32_t* Rc = R + row0 + c0;
+      const double* Y = a.Y + (size_t)r0 * a.ldy;
+      const int64_t ldy = a.ldy;
+      copy_batched(
+          8 * kc,
+          [&](int idx) {
+            const int n = idx / kc;
+            return n < nrc ? ldcg(Y + Rc[idx - n * kc] + n * ldy) : 0.0;
+          },
+          [&](int idx, double v) { b.Bs[(idx / kc) * 64 + idx % kc] = v; });
+      __syncthreads();
+      oz_split_b(b, kc);
+      oz_product(b, w, kc, nrc, [&](int c, int, int, double v) { part[c] += v; });
+    }
+    // the outputs this thread owns (as in oz_product)
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (warp < 4) {
+#pragma unroll
+      for (int c = 0; c < 4; ++c) {
+        const int m = 16 * warp + (lane >> 2) + ((c & 2) ? 8 : 0), n = 2 * (lane & 3) + (c & 1);
+        if (m < w && n < nrc) red_add(a.Y + f + m + (size_t)(r0 + n) * a.ldy, -part[c]);
+      }
+    }
+  }
+}
+
 template <typename T>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
@@ -224,6 +593,12 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  if constexpr (sizeof(T) == 8) {
+    if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
+      bwd_tile_oz(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm);
+      return;
+    }
+  }
   constexpr int CH = kBwdCH, LD = CH + 1;
   double* Lc = sm;                 // [w][LD]: Lc[i + j LD] = L21[c0 + i][j]
   double* Xc = Lc + w * LD;        // [nrc][CH]
@@ -412,10 +787,12 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 
 }  // namespace
 
-size_t solve_smem_bytes(int max_w) {
+size_t solve_smem_bytes(int max_w, bool tc_tiles) {
   const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double);
   const size_t tile = ((size_t)max_w * (kBwdCH + 1) + kBwdCH * kSolveNRC) * sizeof(double);
-  return diag > tile ? diag : tile;
+  size_t need = diag > tile ? diag : tile;
+  if (tc_tiles && max_w >= kOzMinW && need < kOzSmemBytes) need = kOzSmemBytes;
+  return need;
 }
 
 cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm) {

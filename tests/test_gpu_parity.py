@@ -139,6 +139,47 @@ def test_nrhs_and_host_pointers(nrhs):
         spchol.destroy(h)
 
 
+def _scaled_lap3d_12(seed):
+    """lap3d_12 scaled symmetrically by D = diag(10^[-4, 4]): the rows of L = D L0
+    span eight orders of magnitude."""
+    A0, perm, _ = gridgen.workload("lap3d_12")
+    d = 10.0 ** np.random.default_rng(seed).uniform(-4, 4, A0.n)
+    cols = np.repeat(np.arange(A0.n), np.diff(A0.colptr))
+    return gridgen.CscLower(A0.n, A0.colptr, A0.rowind, A0.values * d[A0.rowind] * d[cols]), perm, d
+
+
+def test_fp64_solve_keeps_forward_accuracy_under_scaling():
+    """The FP64 path's solves (Section II-A) round each product on its own: on a
+    diagonally scaled system every component of D x agrees with the oracle's to
+    the conditioning of the unscaled matrix."""
+    A, perm, d = _scaled_lap3d_12(11)
+    B = gridgen.rhs_uniform(A.n, 3, seed=3)
+    rc, X, st, h = gpu_factor_solve(A, perm, B)
+    assert rc == 0
+    assert oracle.berr(A, X, B) <= BERR_FP64
+    spchol.destroy(h)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    Xo = f.solve(B)
+    err = np.abs((X - Xo) * d[:, None]).max()
+    assert err <= 1e-11 * np.abs(Xo * d[:, None]).max(), err
+
+
+@pytest.mark.parametrize("nrhs", [1, 3, 11])
+def test_fp64_tc_solve_tiles_on_tensor_cores(nrhs):
+    """FP64_TC mode also runs the solves' panel tiles as split products on the
+    tensor cores: FP64 backward error, also with rows spanning eight orders of
+    magnitude, and with one, three and eleven right-hand sides (a partial and
+    a second group of eight)."""
+    for A, perm in (gridgen.workload("lap3d_12")[:2], _scaled_lap3d_12(12)[:2]):
+        B = gridgen.rhs_uniform(A.n, nrhs, seed=nrhs)
+        rc, X, st, h = gpu_factor_solve(A, perm, B, precision=spchol.FP64_TC)
+        assert rc == 0
+        assert st["max_width"] >= 16
+        assert oracle.berr(A, X, B) <= BERR_FP64
+        spchol.destroy(h)
+
+
 def test_repeat_solve_and_refactorize():
     A, perm, _ = gridgen.workload("diff3d_10")
     o = spchol.default_options()
