@@ -900,12 +900,13 @@ __device__ __forceinline__ double fixed64_to_double(long long t, int k) {
       (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// The MMA is M = 128 x N = 16; a tile has at most kOzRows = 64 rows, whose
-// digits are the only A rows kept in shared memory: the MMA's rows 64..127 read
-// whatever follows (in bounds) and land in TMEM lanes that are never read
-// back.  7 groups x 16 columns fit 128 TMEM columns, and a CTA needs 73 KB of
-// shared memory, so three CTAs share an SM.
-constexpr int kOzM = 128, kOzN = 16, kOzRows = 64;
+// The MMA is M = 64 x N = 16, the tile's at most kOzRows = 64 rows: each MMA
+// reads 2 KB of A digits from shared memory (an M = 128 MMA over the same rows
+// read 4 KB, half of it past the tile, and the MMA phase was bound by those
+// reads).  With M = 64 the accumulator's row 16 q + i (i < 16) sits in TMEM
+// lane 32 q + i, columns as N.  7 groups x 16 columns fit 128 TMEM columns,
+// and a CTA needs 73 KB of shared memory, so three CTAs share an SM.
+constexpr int kOzM = 64, kOzN = 16, kOzRows = 64;
 constexpr int kOzCols = 128;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
 
 __device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
@@ -995,13 +996,14 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
       tc.phase ^= 1u;
       if (!ok && tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      // Epilogue: warp w reads TMEM lanes 32*(w%4).. (tile rows) and a column
-      // half; warps whose rows or columns are all unused skip (tcgen05.ld is
-      // warp-collective, so the condition is warp-uniform).
+      // Epilogue: warp w reads TMEM lanes 32*(w%4).. (lanes 0..15 of them hold
+      // tile rows 16*(w%4)..) and a column half; warps whose rows or columns
+      // are all unused skip (tcgen05.ld is warp-collective, so the condition
+      // is warp-uniform).
       const int quad = warp & 3, half = warp >> 2;
-      const int row = 32 * quad + lane;
+      const int row = 16 * quad + lane;
       constexpr int kHalf = kOzN / 2;
-      if (32 * quad < u.rowlen) {
+      if (16 * quad < u.rowlen) {
         for (int c0 = half * kHalf; c0 < half * kHalf + kHalf && c0 < ncol; c0 += 8) {
           uint32_t v[kSlices][8];
 #pragma unroll
@@ -1013,7 +1015,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
                          : "r"(taddr));
           }
           asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-          if (ok && row < u.rowlen && pos[row] >= 0) {
+          if (ok && lane < 16 && row < u.rowlen && pos[row] >= 0) {
 #pragma unroll
             for (int q = 0; q < 8; ++q) {
               const int j = c0 + q;
@@ -1129,9 +1131,12 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
           ahead = -1;
         }
         int lo_ready;
+        // the failure word is read before the claim, so that its round trip
+        // overlaps the claim's (it only lets later tasks skip their arithmetic)
+        const int info = ld_relaxed(&a.ctrl[kInfo]);
         sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
         if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
-        sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
+        sh.skip = (info != INT_MAX);
         if (timed) {
           const uint64_t t1 = global_ns();
           tprof[10] += t1 - t0;

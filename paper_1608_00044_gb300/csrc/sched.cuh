@@ -113,7 +113,14 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
   const uint64_t max_iter = (uint64_t)(q.budget_ns / 32) + 100000;
   unsigned backoff = 32;
   for (uint64_t it = 0;; ++it) {
+    // Both rings' (head, tail) and the normal-priority slot this CTA already
+    // holds, in one round trip: the relaxed loads are issued first and the
+    // acquiring load of the slot last, so none waits for another (a claim with
+    // a slot held ahead -- the common case -- used to take three round trips).
     const int2 hi = ld_relaxed_pair(&q.ctrl[kHiHead]);  // (head, tail)
+    const int2 lo = ld_relaxed_pair(&q.ctrl[kHead]);
+    const int v1 = pend[1] >= 0 ? ld_acquire(&q.lo[pend[1]]) : -1;
+    *lo_ready = lo.y - lo.x;
     if (pend[0] < 0 && hi.x < hi.y && hi.x < q.n_hi) {
       const int s = atomicAdd(&q.ctrl[kHiHead], 1);
       pend[0] = s < q.n_hi ? s : -1;
@@ -126,18 +133,21 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
         return v;
       }
     }
-    const int2 lo = ld_relaxed_pair(&q.ctrl[kHead]);
-    *lo_ready = lo.y - lo.x;
+    if (v1 >= 0) {
+      pend[1] = -1;
+      __threadfence();
+      return v1;
+    }
     if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
       const int s = atomicAdd(&q.ctrl[kHead], 1);
       pend[1] = s < q.n_lo ? s : -1;
-    }
-    if (pend[1] >= 0) {
-      const int v = ld_acquire(&q.lo[pend[1]]);
-      if (v >= 0) {
-        pend[1] = -1;
-        __threadfence();
-        return v;
+      if (pend[1] >= 0) {
+        const int v = ld_acquire(&q.lo[pend[1]]);
+        if (v >= 0) {
+          pend[1] = -1;
+          __threadfence();
+          return v;
+        }
       }
     }
     if (pend[0] < 0 && pend[1] < 0 && hi.x >= q.n_hi && lo.x >= q.n_lo) return -1;  // all claimed
