@@ -91,9 +91,11 @@ __device__ __forceinline__ void ring_push_range(const Ring& q, int first, int co
 // that is still empty only after losing a race for the last one, and a ready
 // task never waits behind a busy CTA for longer than such a race.  Every
 // claimed slot is filled eventually (a pusher reserves slots in order, so the
-// lowest claimed empty slot is the next to be filled), and a CTA waiting on a
-// claimed empty slot keeps serving the other ring: no CTA blocks the progress
-// of another.
+// lowest claimed empty slot is the next to be filled).  A CTA holding a
+// claimed empty slot below the tail waits for the push that is filling it; one
+// holding a slot past the tail keeps serving the other ring, since the push
+// that fills it may need that ring's tasks: no CTA blocks the progress of
+// another.
 struct Ring2 {
   int* hi;  // n_hi slots, -1 while empty
   int* lo;  // n_lo slots
@@ -133,12 +135,18 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
         return v;
       }
     }
-    if (v1 >= 0) {
+    if (pend[0] >= 0 && pend[0] < hi.y) {
+      // The slot lies below the tail: a push that reserved it is storing into
+      // it now, so wait for it rather than start a normal-priority task,
+      // whose continuations could hold this reservation -- and delay its task
+      // -- for milliseconds (one such solve tile waited 3.6 ms).  A slot past
+      // the tail (a lost race for the last one) is filled only by a future
+      // push, which may need the other ring's tasks: keep serving that ring.
+    } else if (v1 >= 0) {
       pend[1] = -1;
       __threadfence();
       return v1;
-    }
-    if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
+    } else if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
       const int s = atomicAdd(&q.ctrl[kHead], 1);
       pend[1] = s < q.n_lo ? s : -1;
       if (pend[1] >= 0) {

@@ -31,6 +31,7 @@ struct SolveShared {
   int flag;
   int base;
   int next;  // continuation: a task this CTA made ready and runs next (-1: none)
+  int hold;  // this CTA holds a claimed, still empty ring slot: no continuation
 };
 
 template <typename T>
@@ -706,6 +707,9 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
         int lo_ready;
         sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
       }
+      // While this CTA holds a claimed slot whose task is not yet pushed, it
+      // takes no continuation: it comes back for that task after this one.
+      sh.hold = pend[0] >= 0 || pend[1] >= 0;
       if (a.prof) {
         t1 = global_ns();
         wait += t1 - t0;
@@ -722,10 +726,11 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       // continue with the first forward tile (the rows of the parent) and
       // release the others
       if (a.nst[s] > 0) {
-        if (threadIdx.x == 0) sh.next = ns + a.st_first[s];
-        ring2_push_range(q, true, ns + a.st_first[s] + 1, a.nst[s] - 1, &sh.base);
+        const int keep = sh.hold ? 0 : 1;
+        if (keep && threadIdx.x == 0) sh.next = ns + a.st_first[s];
+        ring2_push_range(q, true, ns + a.st_first[s] + keep, a.nst[s] - keep, &sh.base);
       } else if (threadIdx.x == 0) {
-        sh.next = ns + 2 * nst + s;
+        keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + 2 * nst + s);
       }
     } else if (task < ns + nst) {
       const int kt = task - ns, s = a.st_sn[kt];
@@ -735,21 +740,23 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       // root has thousands of dependent tiles, and they sit on the critical path.
       for (int e = a.st_tptr[kt] + threadIdx.x; e < a.st_tptr[kt + 1]; e += blockDim.x) {
         const int t = a.st_tgt[e];
-        if (atom_add_acqrel(&a.fdep[t], -1) == 1) keep_or_push(q, &sh.next, t);
+        if (atom_add_acqrel(&a.fdep[t], -1) == 1) keep_or_push(q, sh.hold ? nullptr : &sh.next, t);
       }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
-      if (sh.flag) release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, &sh.next);
+      if (sh.flag)
+        release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
-      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) keep_or_push(q, &sh.next, ns + 2 * nst + s);
+      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1)
+        keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + 2 * nst + s);
     } else {
       const int s = task - ns - 2 * nst;
       bwd_diag(a, s, sm);
       publish_cta_writes();
-      release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, &sh.next);
+      release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     }
     if (threadIdx.x == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
