@@ -288,6 +288,44 @@ def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, wi
                     "exact sum c_j^2, the same numerator as the headline"}
 
 
+def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, width=64, relax=4):
+    """General-ordering row: the headline matrix with its rows and columns in a
+    random order (seed 11), ordered by spchol_order_nd (nested dissection by
+    level structures) instead of the grid's geometric dissection: host time of
+    the ordering, its exact flops against the geometric ordering's, FP64 factor
+    time (median of 3) and the backward error of an 8-RHS solve."""
+    import scipy.sparse as sp
+
+    import gridgen
+
+    q = np.random.default_rng(11).permutation(A0.n)
+    L0 = sp.csc_matrix((A0.values, A0.rowind, A0.colptr), shape=(A0.n, A0.n))
+    M = (L0 + sp.tril(L0, -1).T).tocsc()[q][:, q]
+    L = sp.csc_matrix(sp.tril(M))
+    L.sort_indices()
+    A = gridgen.CscLower(A0.n, L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.astype(np.float64))
+    bq = np.ascontiguousarray(b[q])
+    t0 = time.perf_counter()
+    perm = spchol.order_nd(A.n, A.colptr, A.rowind)
+    t_order = time.perf_counter() - t0
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(max_width=width, relax_zeros=relax))
+    vals = torch.from_numpy(A.values).to(dev)
+    times = []
+    for it in range(4):
+        spchol.factorize(h, vals)
+        if it >= 1:
+            times.append(spchol.stats(h)["factor_ms"])
+    X = torch.from_numpy(np.ascontiguousarray(bq.T)).to(dev)
+    spchol.solve(h, X, A.n, bq.shape[1])
+    be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), bq)
+    st = spchol.stats(h)
+    spchol.destroy(h)
+    ms = statistics.median(times)
+    return {"workload": "the headline matrix in a random row/column order (seed 11), ordered by spchol_order_nd",
+            "order_s": t_order, "flops": st["flops"], "flops_vs_geometric_nd": st["flops"] / flops_geo,
+            "nnz_l": st["nnz_l"], "factor_ms": ms, "tflops": st["flops"] / (ms * 1e-3) / 1e12, "berr": be}
+
+
 def measure_small(spchol, oracle, torch, dev, width=64):
     """Latency row: 2D 5-point 64x64 (+1e-2 I), one RHS: factor + solve time,
     median of 50 after 5 warm-ups, and the backward error."""
@@ -580,6 +618,8 @@ def run_ours(args):
         if args.precision == "fp64" and args.workload == "lap3d_64":
             line["fp64_tensor_core_row"] = measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops,
                                                            peak_fp64, width=args.width, relax=args.relax)
+            line["ordering_row"] = measure_ordering(spchol, oracle, torch, dev, A, perm, b, flops,
+                                                    width=args.width, relax=args.relax)
         line["mixed_precision_row"] = measure_mixed(spchol, oracle, torch, dev, width=args.width)
         line["batch_row"] = measure_batch(spchol, oracle, torch, dev, width=args.width)
         line["serving_row"] = measure_serving(full=args.serve_full)

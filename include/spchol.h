@@ -152,6 +152,25 @@ int spchol_analyze(int64_t n, const int64_t* colptr, const int32_t* rowind, cons
                    const spchol_options* opt, spchol_handle_t* out);
 
 /*
+ * Fill-reducing ordering for a general sparse symmetric pattern, for inputs
+ * that come without one (Section V applies a fill-reducing permutation first;
+ * the paper takes it from Scotch).  Nested dissection by breadth-first level
+ * structures (George 1973; George and Liu 1978): a connected set is rooted at a
+ * pseudo-peripheral vertex and cut at its smallest level that leaves 35-65 % of
+ * the set below; the two parts are ordered first, recursively, and the
+ * separator last; sets of at most 64 vertices are ordered by minimum degree.
+ * Host code; needs no GPU.
+ *   n         matrix order, >= 0                                (argument 1)
+ *   colptr    host int64[n+1], as in spchol_analyze             (argument 2)
+ *   rowind    host int32[colptr[n]], as in spchol_analyze       (argument 3)
+ *   perm_out  host int64[n]: receives the ordering, new -> old,
+ *             ready to pass to spchol_analyze                   (argument 4)
+ * Only the pattern is read.  Returns 0 or -k for an invalid argument k (the
+ * same checks as spchol_analyze).
+ */
+int spchol_order_nd(int64_t n, const int64_t* colptr, const int32_t* rowind, int64_t* perm_out);
+
+/*
  * Numeric factorization P A P^T = L L^T (Eq. 1) with the structure of analyze.
  * values: colptr[n] doubles of A's lower triangle in analyze's order, host or
  * device.  The factor stays resident in the handle for later solves.

@@ -17,10 +17,10 @@ ROOT = os.path.dirname(HERE)
 BUILD = os.path.join(HERE, "_build")
 LIB = os.path.join(HERE, "libspchol.so")
 HOST_LIB = os.path.join(HERE, "libspchol_host.so")
-HOST_SOURCES = ["symbolic.cpp", "hostsim.cpp"]
+HOST_SOURCES = ["symbolic.cpp", "hostsim.cpp", "ordering.cpp"]
 
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["api.cu", "factor.cu", "solve.cu", "mixed.cu", "symbolic.cpp"]  # peak_probe.cu is a separate program
+SOURCES = ["api.cu", "factor.cu", "solve.cu", "mixed.cu", "symbolic.cpp", "ordering.cpp"]  # peak_probe.cu is a separate program
 
 
 def _nvcc() -> str:

@@ -24,6 +24,7 @@ SIGNATURES = [
     ("spchol_plan_simulate", ctypes.c_int, [_vp, _vp, _vp, ctypes.c_int64, ctypes.c_int, ctypes.c_uint64, _vp]),
     ("spchol_plan_pool_len", ctypes.c_int64, [_vp]),
     ("spchol_plan_destroy", None, [_vp]),
+    ("spchol_order_nd", ctypes.c_int, [ctypes.c_int64, _vp, _vp, _vp]),
 ]
 _lib = None
 
@@ -40,6 +41,18 @@ def load():
             fn.argtypes = args
         _lib = lib
     return _lib
+
+
+def order_nd(n, colptr, rowind) -> np.ndarray:
+    """spchol_order_nd from the host library (the same code as libspchol.so's)."""
+    lib = load()
+    colptr = np.ascontiguousarray(colptr, np.int64)
+    rowind = np.ascontiguousarray(rowind, np.int32)
+    perm = np.empty(max(int(n), 0), np.int64)
+    rc = lib.spchol_order_nd(int(n), colptr.ctypes.data, rowind.ctypes.data, perm.ctypes.data if n > 0 else None)
+    if rc != 0:
+        raise ValueError(f"spchol_order_nd failed with code {rc}")
+    return perm
 
 
 class HostPlan:

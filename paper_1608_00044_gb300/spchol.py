@@ -93,6 +93,7 @@ _i64 = ctypes.c_int64
 SIGNATURES = [
     ("spchol_default_options", None, [ctypes.POINTER(Options)]),
     ("spchol_analyze", ctypes.c_int, [_i64, _vp, _vp, _vp, ctypes.POINTER(Options), ctypes.POINTER(_vp)]),
+    ("spchol_order_nd", ctypes.c_int, [_i64, _vp, _vp, _vp]),
     ("spchol_factorize", ctypes.c_int, [_vp, _vp, _vp]),
     ("spchol_factorize_enqueue", ctypes.c_int, [_vp, _vp, _vp]),
     ("spchol_factorize_status", ctypes.c_int, [_vp]),
@@ -208,6 +209,19 @@ def analyze(n, colptr, rowind, perm=None, opt: Options | None = None):
     if rc != 0:
         raise SpcholError(rc, "spchol_analyze")
     return h
+
+
+def order_nd(n, colptr, rowind) -> np.ndarray:
+    """spchol_order_nd: a nested-dissection ordering (new -> old, int64) of a
+    lower-triangle CSC pattern, for matrices that come without one."""
+    lib = load()
+    colptr = _host(colptr, np.int64)
+    rowind = _host(rowind, np.int32)
+    perm = np.empty(max(int(n), 0), np.int64)
+    rc = lib.spchol_order_nd(int(n), colptr.ctypes.data, rowind.ctypes.data, perm.ctypes.data if n > 0 else None)
+    if rc != 0:
+        raise SpcholError(rc, "spchol_order_nd")
+    return perm
 
 
 def factorize(h, values, stream=None) -> int:

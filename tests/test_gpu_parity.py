@@ -180,6 +180,34 @@ def test_fp64_tc_solve_tiles_on_tensor_cores(nrhs):
         spchol.destroy(h)
 
 
+@pytest.mark.parametrize("case", ["scrambled_lap3d_12", "scrambled_diff3d_9", "random"])
+def test_general_ordering_through_the_library(case):
+    """spchol_order_nd (Section V's fill-reducing permutation, for inputs without
+    one) feeds spchol_analyze: FP64 backward error against the same b."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(21)
+    if case == "random":
+        R = sp.random(1500, 1500, density=0.004, random_state=rng, format="csc")
+        S = R + R.T
+        S.data[:] = -np.abs(S.data)
+        M = (S + sp.diags(np.asarray(np.abs(S).sum(axis=1)).ravel() + 1.0)).tocsc()
+    else:
+        A0 = gridgen.workload(case.split("_", 1)[1])[0]
+        L = sp.csc_matrix((A0.values, A0.rowind, A0.colptr), shape=(A0.n, A0.n))
+        q = rng.permutation(A0.n)
+        M = (L + sp.tril(L, -1).T).tocsc()[q][:, q]
+    L = sp.csc_matrix(sp.tril(M))
+    L.sort_indices()
+    A = gridgen.CscLower(M.shape[0], L.indptr.astype(np.int64), L.indices.astype(np.int32), L.data.astype(np.float64))
+    perm = spchol.order_nd(A.n, A.colptr, A.rowind)
+    B = gridgen.rhs_uniform(A.n, 3, seed=4)
+    rc, X, st, h = gpu_factor_solve(A, perm, B)
+    assert rc == 0
+    assert oracle.berr(A, X, B) <= BERR_FP64
+    spchol.destroy(h)
+
+
 def test_repeat_solve_and_refactorize():
     A, perm, _ = gridgen.workload("diff3d_10")
     o = spchol.default_options()
