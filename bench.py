@@ -326,6 +326,36 @@ def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, wid
             "nnz_l": st["nnz_l"], "factor_ms": ms, "tflops": st["flops"] / (ms * 1e-3) / 1e12, "berr": be}
 
 
+def measure_scheduling(spchol, oracle, torch, dev, name="lap3d_40", width=64):
+    """Scheduling-policy row (Section IV-B's static schedule against the dynamic
+    one, restated for one GPU): the same matrix factored and solved with the
+    default dynamic two-priority rings and with the deterministic static
+    (target, source) order; median factor time of 3, solve time, backward
+    errors, and whether two static runs agree bitwise."""
+    A, perm, b = _workload(name)
+    vals = torch.from_numpy(A.values).to(dev)
+    out = {"workload": f"{name}: 3D 7-point {A.dims}, n={A.n}, {b.shape[1]} RHS"}
+    for label, det in (("dynamic", 0), ("static", 1)):
+        h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(max_width=width, deterministic=det))
+        times, xs = [], []
+        for it in range(4):
+            spchol.factorize(h, vals)
+            if it >= 1:
+                times.append(spchol.stats(h)["factor_ms"])
+        s_ms = []
+        for it in range(2):
+            X = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
+            spchol.solve(h, X, A.n, b.shape[1])
+            s_ms.append(spchol.stats(h)["solve_ms"])
+            xs.append(X.cpu().numpy())
+        be = oracle.berr(A, np.asfortranarray(xs[0].T), b)
+        spchol.destroy(h)
+        out[label] = {"factor_ms": statistics.median(times), "solve_ms": min(s_ms), "berr": be,
+                      "runs_bitwise_equal": bool(np.array_equal(xs[0], xs[1]))}
+    out["static_over_dynamic_factor"] = out["static"]["factor_ms"] / out["dynamic"]["factor_ms"]
+    return out
+
+
 def measure_small(spchol, oracle, torch, dev, width=64):
     """Latency row: 2D 5-point 64x64 (+1e-2 I), one RHS: factor + solve time,
     median of 50 after 5 warm-ups, and the backward error."""
@@ -620,6 +650,7 @@ def run_ours(args):
                                                            peak_fp64, width=args.width, relax=args.relax)
             line["ordering_row"] = measure_ordering(spchol, oracle, torch, dev, A, perm, b, flops,
                                                     width=args.width, relax=args.relax)
+        line["scheduling_row"] = measure_scheduling(spchol, oracle, torch, dev, width=args.width)
         line["mixed_precision_row"] = measure_mixed(spchol, oracle, torch, dev, width=args.width)
         line["batch_row"] = measure_batch(spchol, oracle, torch, dev, width=args.width)
         line["serving_row"] = measure_serving(full=args.serve_full)

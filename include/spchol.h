@@ -88,7 +88,12 @@ typedef struct spchol_options {
   int tile_rows;          /* rows per update tile, 1..64; 0 = default (64).  The tensor-core tiles
                              ignore it: 128 rows for TF32, 64 for SPCHOL_FP64_TC */
   int ctas_per_sm;        /* persistent-kernel CTAs per SM; 0 = as many as fit */
-  int deterministic;      /* reserved: 0 */
+  int deterministic;      /* 1: the static (target, source) order of Section IV-B: the update tiles
+                             into each target panel, and the solve tiles into each panel's
+                             entries, run one after another in (source, tile) order, so every
+                             sum lands in one fixed order and the factor and solution are
+                             bitwise reproducible (run to run, alone or in a batch); slower.
+                             0 (default): dynamic order, results equal up to rounding */
   int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
   int ir_max_iter;        /* mixed precision: refinement steps; default 10 */
   double ir_tol;          /* mixed precision: target backward error; default 1e-12 */

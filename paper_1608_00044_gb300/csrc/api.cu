@@ -76,6 +76,10 @@ struct spchol_handle_s {
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
   int32_t *d_st_tptr = nullptr, *d_st_tgt = nullptr, *d_rt_ptr = nullptr, *d_rt_tile = nullptr;
   int32_t *d_fdep0 = nullptr, *d_bdep0 = nullptr, *d_bdep = nullptr;
+  // deterministic order (options.deterministic): the chains of Plan::u_next and
+  // Plan::ft_sptr, their initial counters and the live counters
+  int32_t *d_u_next = nullptr, *d_u_dep0 = nullptr, *d_u_dep = nullptr;
+  int32_t *d_ft_sptr = nullptr, *d_ft_succ = nullptr, *d_ft_dep0 = nullptr, *d_ftdep = nullptr;
   int32_t *d_sseeds = nullptr;
   int nsseeds = 0;
   int32_t* d_perm = nullptr;
@@ -225,6 +229,11 @@ int setup_device(spchol_handle_t h) {
          o_rtt = r32(P.rt_tile.size()), o_fd0 = r32(ns), o_bd0 = r32(P.n_st), o_bd = r32(P.n_st);
   size_t o_nki = r32(ns), o_fk = r32(ns), o_ft = r32(ns), o_bt = r32(ns), o_sseeds = r32(sseeds.size());
   size_t o_perm = r32(P.n);
+  const bool det = P.params.deterministic;
+  size_t o_unx = det ? r32(P.u_next.size()) : 0, o_ud0 = det ? r32(P.u_dep0.size()) : 0,
+         o_ud = det ? r32(P.u_dep0.size()) : 0, o_fsp = det ? r32(P.ft_sptr.size()) : 0,
+         o_fsu = det ? r32(P.ft_succ.size()) : 0, o_fd0d = det ? r32(P.ft_dep0.size()) : 0,
+         o_fdd = det ? r32(P.ft_dep0.size()) : 0;
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
   size_t o_prof = A.reserve(24 * sizeof(unsigned long long));
@@ -315,6 +324,15 @@ int setup_device(spchol_handle_t h) {
   h->d_bdep0 = (int32_t*)(b + o_bd0);
   h->d_bdep = (int32_t*)(b + o_bd);
   h->nsseeds = (int)sseeds.size();
+  if (det) {
+    h->d_u_next = (int32_t*)(b + o_unx);
+    h->d_u_dep0 = (int32_t*)(b + o_ud0);
+    h->d_u_dep = (int32_t*)(b + o_ud);
+    h->d_ft_sptr = (int32_t*)(b + o_fsp);
+    h->d_ft_succ = (int32_t*)(b + o_fsu);
+    h->d_ft_dep0 = (int32_t*)(b + o_fd0d);
+    h->d_ftdep = (int32_t*)(b + o_fdd);
+  }
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
   h->d_ctrl = (int*)(b + o_ctrl);
@@ -352,6 +370,10 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_rt_ptr, P.rt_ptr)) || (rc = upload(h, h->d_rt_tile, P.rt_tile)) ||
       (rc = upload(h, h->d_fdep0, P.fdep0)) || (rc = upload(h, h->d_bdep0, P.bdep0)) ||
       (rc = upload(h, h->d_perm, perm32)))
+    return rc;
+  if (det && ((rc = upload(h, h->d_u_next, P.u_next)) || (rc = upload(h, h->d_u_dep0, P.u_dep0)) ||
+              (rc = upload(h, h->d_ft_sptr, P.ft_sptr)) || (rc = upload(h, h->d_ft_succ, P.ft_succ)) ||
+              (rc = upload(h, h->d_ft_dep0, P.ft_dep0))))
     return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
@@ -519,6 +541,11 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.tc_min_width = P.params.tc_min_width;
   a.dep_f = h->d_dep;
   a.trsm_left = h->d_trsm_left;
+  if (P.params.deterministic && P.n_u > 0) {
+    CU(cudaMemcpyAsync(h->d_u_dep, h->d_u_dep0, (size_t)P.n_u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    a.u_next = h->d_u_next;
+    a.u_dep = h->d_u_dep;
+  }
   a.ring = h->d_ring;
   a.ctrl = h->d_ctrl;
   a.budget_ns = h->opt.wait_budget_ns;
@@ -607,6 +634,12 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.bdep = h->d_bdep;
   a.ftiles = h->d_ftiles;
   a.btiles = h->d_btiles;
+  if (P.params.deterministic && P.n_st > 0) {
+    CU(cudaMemcpyAsync(h->d_ftdep, h->d_ft_dep0, (size_t)P.n_st * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    a.ft_sptr = h->d_ft_sptr;
+    a.ft_succ = h->d_ft_succ;
+    a.ftdep = h->d_ftdep;
+  }
   a.ring = h->d_ring;
   a.ctrl = h->d_ctrl;
   a.budget_ns = h->opt.wait_budget_ns;
@@ -853,7 +886,9 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   const size_t ring_bytes = up((size_t)P.n_solve_tasks * sizeof(int));
   const size_t cnt_bytes = up((size_t)P.ns * sizeof(int32_t));
   const size_t tile_bytes = up((size_t)P.n_st * sizeof(int32_t));
-  const size_t need = y_bytes + ring_bytes + 3 * cnt_bytes + tile_bytes + up(kCtrlWords * sizeof(int));
+  const bool det = P.params.deterministic && P.n_st > 0;
+  const size_t need =
+      y_bytes + ring_bytes + 3 * cnt_bytes + (det ? 2 : 1) * tile_bytes + up(kCtrlWords * sizeof(int));
   if (need > kNoallocScratchBytes) return SPCHOL_ESCRATCH;
   void* base = nullptr;
   CU(noalloc_scratch(h->device, &base));
@@ -865,6 +900,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   int32_t* btiles = (int32_t*)((char*)ftiles + cnt_bytes);
   int32_t* bdep = (int32_t*)((char*)btiles + cnt_bytes);
   int* ctrl = (int*)((char*)bdep + tile_bytes);
+  int32_t* ftdep = det ? (int32_t*)((char*)ctrl + up(kCtrlWords * sizeof(int))) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the reset kernel re-initialises
   // the ring, the counters and the control words before every launch
@@ -891,6 +927,12 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.bdep = bdep;
   a.ftiles = ftiles;
   a.btiles = btiles;
+  if (det) {
+    CU(cudaMemcpyAsync(ftdep, h->d_ft_dep0, (size_t)P.n_st * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    a.ft_sptr = h->d_ft_sptr;
+    a.ft_succ = h->d_ft_succ;
+    a.ftdep = ftdep;
+  }
   a.ring = ring;
   a.ctrl = ctrl;
   a.budget_ns = h->opt.wait_budget_ns;

@@ -393,8 +393,13 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
   if (sh.flag) {
     const Ring2 q = rings_of(a);
     const int first = a.pv.ns + a.n_trsm + a.u_first[s], nhi = a.nu_hi[s];
-    ring2_push_range(q, true, first, nhi, &sh.base);
-    ring2_push_range(q, false, first + nhi, a.nu[s] - nhi, &sh.base);
+    if (a.u_dep) {  // deterministic order: a tile also waits for its predecessor into the same target
+      for (int i = threadIdx.x; i < a.nu[s]; i += blockDim.x)
+        if (atom_add_acqrel(&a.u_dep[a.u_first[s] + i], -1) == 1) ring2_push_one(q, i < nhi, first + i);
+    } else {
+      ring2_push_range(q, true, first, nhi, &sh.base);
+      ring2_push_range(q, false, first + nhi, a.nu[s] - nhi, &sh.base);
+    }
   }
 }
 
@@ -1230,6 +1235,15 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
         task_update_tc(a, u, smem_raw, sh, skip, tc, release);
       } else {
         task_update<T>(a, u, smem_raw, sh, skip, ui & 7, utma, release);
+      }
+      // deterministic order: the next tile into the same target may start
+      // (the tile's scatter-adds were published before its own release)
+      if (a.u_next && release && threadIdx.x == 0) {
+        const int nx = a.u_next[ui];
+        if (nx >= 0 && atom_add_acqrel(&a.u_dep[nx], -1) == 1) {
+          const int sx = a.ut[nx].s;
+          ring2_push_one(rings_of(a), nx - a.u_first[sx] < a.nu_hi[sx], a.pv.ns + a.n_trsm + nx);
+        }
       }
     }
     if (threadIdx.x == 0) {

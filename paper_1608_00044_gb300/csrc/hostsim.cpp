@@ -214,6 +214,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   // update tiles of each panel).  Every push is counted against its ring's
   // size, and each ring must receive exactly as many tasks as it holds.
   std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
+  // deterministic order: update tiles chained per target (Plan::u_next)
+  const bool det = !P.u_next.empty();
+  std::vector<int> udep(P.u_dep0.begin(), P.u_dep0.end());
+  const int u0 = ns + P.n_trsm;  // first update tile id
   std::vector<char> ran(P.n_task_ids, 0);
   Ready hi, lo;
   const int64_t n_hi = P.n_hi_tasks, n_lo = (int64_t)P.n_factor_tasks - P.n_hi_tasks;
@@ -268,13 +272,26 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       if (!skip) sim.trsm(s, kt - P.trsm_first[s]);
       if (--tleft[s] < 0) return SPCHOL_EINTERNAL;
       if (tleft[s] == 0)
-        for (int k = 0; k < P.nu[s]; ++k) push(k < P.nu_hi[s], ns + P.n_trsm + P.u_first[s] + k);
+        for (int k = 0; k < P.nu[s]; ++k) {
+          const int u = P.u_first[s] + k;
+          if (det && --udep[u] != 0) {
+            if (udep[u] < 0) return SPCHOL_EINTERNAL;
+            continue;  // waits for its predecessor into the same target
+          }
+          push(k < P.nu_hi[s], u0 + u);
+        }
     } else {
-      const UTask& u = P.ut[task - ns - P.n_trsm];
+      const int ui = task - u0;
+      const UTask& u = P.ut[ui];
       if (P.in_sub[u.s] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.update(u);
       if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
       if (dep[u.t] == 0) push(true, u.t);
+      if (det && P.u_next[ui] >= 0) {
+        const int nx = P.u_next[ui], sx = P.ut[nx].s;
+        if (--udep[nx] < 0) return SPCHOL_EINTERNAL;
+        if (udep[nx] == 0) push(nx - P.u_first[sx] < P.nu_hi[sx], u0 + nx);
+      }
     }
     if (sim.info < 0) return SPCHOL_EINTERNAL;
   }
@@ -291,6 +308,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   const int nst = P.n_st;
   std::vector<int> fdep(P.fdep0.begin(), P.fdep0.end()), bdep(P.bdep0.begin(), P.bdep0.end());
   std::vector<int> ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
+  std::vector<int> ftdep(P.ft_dep0.begin(), P.ft_dep0.end());  // deterministic order only
   std::vector<char> sran(P.n_solve_tasks, 0);
   // Two rings as in the GPU kernel: the seeds (panels with no incoming forward
   // tile) fill the normal-priority ring; a task made ready by another is kept
@@ -340,10 +358,18 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
         }
       }
       // the first forward tile (or the backward diagonal task) continues here
-      if (P.nst[s] > 0)
-        for (int k = 0; k < P.nst[s]; ++k) skeep(ns + P.st_first[s] + k);
-      else
+      if (P.nst[s] > 0) {
+        for (int k = 0; k < P.nst[s]; ++k) {
+          const int tile = P.st_first[s] + k;
+          if (det) {  // also waits for its predecessors into the same panels
+            if (--ftdep[tile] < 0) return SPCHOL_EINTERNAL;
+            if (ftdep[tile] != 0) continue;
+          }
+          skeep(ns + tile);
+        }
+      } else {
         skeep(ns + 2 * nst + s);
+      }
     } else if (task < ns + nst) {  // FWD_T
       const int kt = task - ns, s = P.st_sn[kt], k = kt - P.st_first[s];
       const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
@@ -361,6 +387,12 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
         if (--fdep[t] < 0) return SPCHOL_EINTERNAL;
         if (fdep[t] == 0) skeep(t);
       }
+      if (det)
+        for (int q2 = P.ft_sptr[kt]; q2 < P.ft_sptr[kt + 1]; ++q2) {
+          const int nx = P.ft_succ[q2];
+          if (--ftdep[nx] < 0) return SPCHOL_EINTERNAL;
+          if (ftdep[nx] == 0) skeep(ns + nx);
+        }
       if (--ft[s] < 0) return SPCHOL_EINTERNAL;
       if (ft[s] == 0)
         for (int k2 = 0; k2 < P.nst[s]; ++k2) {
@@ -379,6 +411,11 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           for (int i = row0; i < row0 + cnt; ++i) acc += L[i + (size_t)j * ld] * Y[R[i] + (size_t)r * n];
           Y[f + j + (size_t)r * n] -= acc;
         }
+      if (det && k + 1 < P.nst[s]) {  // the panel's next backward tile
+        const int nx = P.st_first[s] + k + 1;
+        if (--bdep[nx] < 0) return SPCHOL_EINTERNAL;
+        if (bdep[nx] == 0) skeep(ns + nst + nx);
+      }
       if (--bt[s] < 0) return SPCHOL_EINTERNAL;
       if (bt[s] == 0) skeep(ns + 2 * nst + s);
     } else {  // BWD_D

@@ -53,6 +53,11 @@ struct FactorArgs {
   int32_t tc_min_width;  // mode 3: update tiles of panels at least this wide run on the tensor cores
   int32_t* dep_f;      // update tiles still to land in each panel
   int32_t* trsm_left;  // panel-solve tiles still to finish in each panel
+  // deterministic order (null otherwise): next update tile into the same
+  // target (-1 at the end) and each tile's live counter (its source's
+  // panel-solve tiles + its predecessor)
+  const int32_t* u_next;
+  int32_t* u_dep;
   int* ring;
   int* ctrl;
   int64_t budget_ns;
@@ -92,6 +97,13 @@ struct SolveArgs {
   int64_t ldy;
   int nrhs;
   int tc_tiles;     // 1: FP64 panel tiles 16..64 wide as split products on the tensor cores (FP64_TC mode)
+  // deterministic order (null otherwise): each forward tile's successors in the
+  // chains of its target panels (CSR) and the live counters (own diagonal
+  // solve + predecessors); the backward tiles of a panel chain in tile order
+  // through bdep
+  const int32_t* ft_sptr;
+  const int32_t* ft_succ;
+  int32_t* ftdep;
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
   unsigned long long* trace; // optional: per task id, start and end ns
 };

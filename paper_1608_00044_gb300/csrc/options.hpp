@@ -33,7 +33,8 @@ inline bool options_valid(const spchol_options& o) {
   return o.precision >= SPCHOL_FP64 && o.precision <= SPCHOL_FP64_TC && o.max_width >= 1 &&
          o.max_width <= (tc ? 64 : 128) &&
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
-         o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 &&
+         o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 && o.deterministic >= 0 &&
+         o.deterministic <= 1 &&
          o.profile >= 0 && o.profile <= 2;
 }
 
@@ -53,6 +54,10 @@ inline PlanParams params_from(const spchol_options& o) {
   }
   p.trsm_rows = kTrsmTileRows;
   p.solve_rows = kSolveTileRows;
+  if (o.deterministic) {
+    p.deterministic = true;
+    p.subtree_flops = 0.0;
+  }
   return p;
 }
 

@@ -42,6 +42,9 @@ struct PlanParams {
   // costs at most min(subtree_flops, total flops / 4096) runs as one task
   // (0: none).
   double subtree_flops = 1e6;
+  // Deterministic order (the static (target, source) order of Section IV-B):
+  // see Plan::u_next.  Subtree tasks are off in this mode.
+  bool deterministic = false;
 };
 
 struct Plan {
@@ -102,6 +105,19 @@ struct Plan {
   // (targets + 1 for "every forward tile of the tile's own panel is done")
   std::vector<int32_t> st_tptr, st_tgt, rt_ptr, rt_tile, fdep0, bdep0;
   int32_t n_st = 0, n_solve_tasks = 0;
+
+  // Deterministic order (params.deterministic; empty otherwise).  The update
+  // tiles into each target panel form a chain in (source panel, row tile)
+  // order, and a tile becomes ready only when its source's panel-solve tiles
+  // and its predecessor in the chain are done, so the scatter-adds into every
+  // entry land in one fixed order: u_next (next tile into the same target, -1
+  // at the end) and u_dep0 (1 + 1 with a predecessor).  Likewise the forward
+  // solve tiles that subtract from each panel's rows chain in tile order
+  // (ft_sptr / ft_succ: each tile's successors, one per target panel chain;
+  // ft_dep0: 1 for its panel's diagonal solve + its predecessors), and the
+  // backward tiles of a panel, which all subtract from that panel's entries,
+  // chain in tile order (bdep0 counts the predecessor).
+  std::vector<int32_t> u_next, u_dep0, ft_sptr, ft_succ, ft_dep0;
 
   PlanParams params;
 };

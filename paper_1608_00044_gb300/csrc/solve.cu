@@ -725,7 +725,13 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       publish_cta_writes();
       // continue with the first forward tile (the rows of the parent) and
       // release the others
-      if (a.nst[s] > 0) {
+      if (a.nst[s] > 0 && a.ftdep) {
+        // deterministic order: a tile also waits for its predecessors into the same panels
+        for (int i = threadIdx.x; i < a.nst[s]; i += blockDim.x) {
+          const int tile = a.st_first[s] + i;
+          if (atom_add_acqrel(&a.ftdep[tile], -1) == 1) keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + tile);
+        }
+      } else if (a.nst[s] > 0) {
         const int keep = sh.hold ? 0 : 1;
         if (keep && threadIdx.x == 0) sh.next = ns + a.st_first[s];
         ring2_push_range(q, true, ns + a.st_first[s] + keep, a.nst[s] - keep, &sh.base);
@@ -742,6 +748,11 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
         const int t = a.st_tgt[e];
         if (atom_add_acqrel(&a.fdep[t], -1) == 1) keep_or_push(q, sh.hold ? nullptr : &sh.next, t);
       }
+      if (a.ftdep)  // deterministic order: the next tiles into the same panels
+        for (int e = a.ft_sptr[kt] + threadIdx.x; e < a.ft_sptr[kt + 1]; e += blockDim.x) {
+          const int nx = a.ft_succ[e];
+          if (atom_add_acqrel(&a.ftdep[nx], -1) == 1) keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + nx);
+        }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
       if (sh.flag)
@@ -750,6 +761,10 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
+      // deterministic order: the panel's next backward tile
+      if (a.ftdep && threadIdx.x == 0 && kt + 1 < a.st_first[s] + a.nst[s] &&
+          atom_add_acqrel(&a.bdep[kt + 1], -1) == 1)
+        keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + nst + kt + 1);
       if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1)
         keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + 2 * nst + s);
     } else {

@@ -371,6 +371,23 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   }
   P.n_trsm = (int32_t)P.trsm_sn.size();
   P.n_u = (int32_t)P.ut.size();
+  P.u_next.clear();
+  P.u_dep0.clear();
+  if (prm.deterministic) {
+    // tiles are numbered by source panel, then by target, then by row tile:
+    // in that order each target's tiles form its chain
+    P.u_next.assign(P.n_u, -1);
+    P.u_dep0.assign(P.n_u, 1);
+    std::vector<int32_t> last(ns, -1);
+    for (int32_t u = 0; u < P.n_u; ++u) {
+      const int32_t t = P.ut[u].t;
+      if (last[t] >= 0) {
+        P.u_next[last[t]] = u;
+        P.u_dep0[u] = 2;
+      }
+      last[t] = u;
+    }
+  }
 
   // ---- subtree tasks ------------------------------------------------------------
   // Flops of each panel's own tasks, summed over subtrees (children precede
@@ -461,6 +478,33 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       P.st_tptr[tile + 1] = (int32_t)P.st_tgt.size();
       P.bdep0[tile] = (P.st_tptr[tile + 1] - P.st_tptr[tile]) + 1;
     }
+  }
+  P.ft_sptr.clear();
+  P.ft_succ.clear();
+  P.ft_dep0.clear();
+  if (prm.deterministic) {
+    // forward tiles: one chain per target panel, in tile order
+    P.ft_dep0.assign(P.n_st, 1);
+    std::vector<int32_t> last(ns, -1), npred_of(P.n_st, 0);
+    std::vector<std::pair<int32_t, int32_t>> edges;  // (predecessor, successor)
+    for (int32_t tile = 0; tile < P.n_st; ++tile)
+      for (int32_t q = P.st_tptr[tile]; q < P.st_tptr[tile + 1]; ++q) {
+        const int32_t t = P.st_tgt[q];
+        if (last[t] >= 0) {
+          edges.push_back({last[t], tile});
+          P.ft_dep0[tile]++;
+        }
+        last[t] = tile;
+      }
+    P.ft_sptr.assign(P.n_st + 1, 0);
+    for (const auto& e : edges) P.ft_sptr[e.first + 1]++;
+    for (int32_t i = 0; i < P.n_st; ++i) P.ft_sptr[i + 1] += P.ft_sptr[i];
+    P.ft_succ.resize(edges.size());
+    std::vector<int32_t> fill(P.ft_sptr.begin(), P.ft_sptr.end() - 1);
+    for (const auto& e : edges) P.ft_succ[fill[e.first]++] = e.second;
+    // backward tiles of a panel: a chain in tile order
+    for (int32_t s = 0; s < ns; ++s)
+      for (int32_t k = 1; k < P.nst[s]; ++k) P.bdep0[P.st_first[s] + k]++;
   }
   P.rt_ptr.assign(ns + 1, 0);
   for (int32_t t : P.st_tgt) P.rt_ptr[t + 1]++;

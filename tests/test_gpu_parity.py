@@ -208,6 +208,48 @@ def test_general_ordering_through_the_library(case):
     spchol.destroy(h)
 
 
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_deterministic_mode_is_bitwise_reproducible(precision):
+    """options.deterministic (the static (target, source) order, Section IV-B):
+    the factor and the solution are bitwise equal across runs and across
+    launch geometries (1 and all CTAs per SM), and the backward error is the
+    mode's."""
+    A, perm, _ = gridgen.workload("diff3d_12")
+    B = gridgen.rhs_uniform(A.n, 3, seed=8)
+    prec = getattr(spchol, precision)
+    runs = []
+    for cps in (0, 1, 0):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=1, ctas_per_sm=cps, precision=prec)
+        assert rc == 0
+        assert oracle.berr(A, X, B) <= (BERR_FP64 if precision == "FP64" else 1e-12)
+        Lx = spchol.export_factor(h)[2] if precision == "FP64" else None
+        runs.append((X, Lx))
+        spchol.destroy(h)
+    for X, Lx in runs[1:]:
+        assert np.array_equal(X, runs[0][0])
+        if Lx is not None:
+            assert np.array_equal(Lx, runs[0][1])
+
+
+def test_deterministic_batch_matches_solo_bitwise():
+    """In deterministic mode each matrix of a batch gets bitwise the solution
+    it gets alone."""
+    mats = [gridgen.diffusion_2d_5pt(sd, sigma=1.0, seed=60 + i) for i, sd in enumerate((17, 30, 24))]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=70 + i) for i, M in enumerate(mats)]
+    o = spchol.default_options(deterministic=1)
+    hb = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.batch_factorize(hb, [M.values for M in mats]) == 0
+    Xb = [Bi.copy(order="F") for Bi in Bs]
+    spchol.batch_solve(hb, Xb, [M.n for M in mats], [Bi.shape[1] for Bi in Bs])
+    spchol.destroy(hb)
+    for M, p, Bi, Xi in zip(mats, perms, Bs, Xb):
+        rc, X, st, h = gpu_factor_solve(M, p, Bi, deterministic=1)
+        assert rc == 0
+        assert np.array_equal(X, Xi)
+        spchol.destroy(h)
+
+
 def test_repeat_solve_and_refactorize():
     A, perm, _ = gridgen.workload("diff3d_10")
     o = spchol.default_options()

@@ -258,3 +258,29 @@ def test_random_order_with_subtree_tasks():
         rc, X, pool = P.simulate(A.values, B, seed=seed)
         assert rc == 0
         assert oracle.berr(A, X, B) <= 1e-14
+
+
+@pytest.mark.parametrize("name,W", [("diff3d_8", 16), ("lap3d_12", 64), ("lap2d_24", 8)])
+def test_deterministic_order_is_bitwise_stable(name, W):
+    """Deterministic mode (the static (target, source) order of Section IV-B):
+    the update tiles into a target and the solve tiles into a panel run in one
+    fixed order, so the simulated factor and solution are bitwise equal in
+    every random ready order -- and still match the oracle.  The dynamic mode
+    differs between orders in the last bits (a check that the test can see a
+    difference)."""
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=2)
+    results = {}
+    for det in (0, 1):
+        P = _plan(A, perm, deterministic=det, max_width=W)
+        if det:
+            assert P.scalars()["n_sub"] == 0  # no subtree tasks in this mode
+        outs = []
+        for seed in range(4):
+            rc, X, pool = P.simulate(A.values, B, seed=seed, want_pool=True)
+            assert rc == 0
+            assert oracle.berr(A, X, B) <= 1e-14
+            outs.append((X, pool))
+        results[det] = all(np.array_equal(outs[0][0], o[0]) and np.array_equal(outs[0][1], o[1]) for o in outs[1:])
+    assert results[1]
+    assert not results[0]
