@@ -13,6 +13,7 @@ from .grids import (
     laplacian_3d,
     diffusion_2d_5pt,
     diffusion_3d_27pt,
+    neumann_laplacian_3d,
     lognormal_kappa,
     rhs_uniform,
     batch_sides,
@@ -26,6 +27,7 @@ __all__ = [
     "laplacian_3d",
     "diffusion_2d_5pt",
     "diffusion_3d_27pt",
+    "neumann_laplacian_3d",
     "lognormal_kappa",
     "rhs_uniform",
     "batch_sides",

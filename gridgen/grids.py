@@ -196,6 +196,29 @@ def diffusion_3d_27pt(nx: int, sigma: float = 2.0, seed: int = 1,
     return _diffusion(dims, kappa, True, "diff3d27", {"sigma": sigma, "seed": seed})
 
 
+def neumann_laplacian_3d(nx: int, eps: float) -> CscLower:
+    """3D 7-point graph Laplacian of the nx^3 grid (each diagonal entry the
+    vertex's neighbour count: no Dirichlet boundary) plus eps * I: SPD with
+    smallest eigenvalue eps (the constant vector), so kappa ~ 12 / eps --
+    an ill-conditioned case for low-precision factors."""
+    dims = (nx, nx, nx)
+    n = nx ** 3
+    I, J, V = [], [], []
+    deg = np.zeros(n)
+    for off in _half_offsets(3, full=False):
+        u, v = _neighbour_pairs(dims, off)
+        I.append(v)
+        J.append(u)
+        V.append(-np.ones(len(u)))
+        np.add.at(deg, u, 1.0)
+        np.add.at(deg, v, 1.0)
+    I.append(np.arange(n))
+    J.append(np.arange(n))
+    V.append(deg + eps)
+    return _from_triplets(n, np.concatenate(I), np.concatenate(J), np.concatenate(V), dims, "neumann3d",
+                          {"eps": eps})
+
+
 def diffusion_2d_5pt(nx: int, sigma: float = 1.0, seed: int = 1,
                      ny: int | None = None) -> CscLower:
     """2D 5-point variable-coefficient diffusion (harmonic-mean face weights)."""

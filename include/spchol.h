@@ -135,6 +135,8 @@ typedef struct spchol_stats {
   int n_subtrees;             /* subtree tasks: small subtrees of the panel tree factored by one CTA each */
   double factor_subtree_ms;   /* profile: time in subtree tasks (summed over CTAs) */
   int64_t factor_subtree_count;
+  int ir_gmres_iters;         /* mixed precision: GMRES-IR steps of the last solve (0 when classic
+                                 refinement reached the target) */
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */

@@ -106,6 +106,14 @@ struct spchol_handle_s {
   int norms_cap = 0;                      // right-hand sides the norm buffers hold
   double* d_X = nullptr;
   double* d_R = nullptr;
+  // GMRES-IR workspace (allocated at its first use): Krylov basis (n x
+  // (kGmresRestart + 1)), one work vector, reduction partials, Hessenberg
+  // column buffers on the device and in pinned host memory
+  double* d_gmV = nullptr;
+  double* d_gmW = nullptr;
+  double* d_gmPart = nullptr;
+  double* d_gmH = nullptr;
+  double* h_gmH = nullptr;
   unsigned long long* d_prof = nullptr;  // [0..9] factorization, [16..23] solve
   unsigned long long* d_trace_f = nullptr;  // profile = 2: per factorization task start/end
   unsigned long long* d_trace_s = nullptr;  // profile = 2: per solve task start/end
@@ -664,8 +672,112 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   return rc;
 }
 
+// dst = M^{-1} src for one vector in the original order: M = P^T L L^T P the
+// low-precision factor.
+int apply_factor_inverse(spchol_handle_t h, const double* src, double* dst, cudaStream_t st) {
+  const int64_t n = h->plan.n;
+  CU(launch_permute_in(src, n, h->d_Y, n, h->d_perm, n, 1, st));
+  int rc = solve_permuted(h, h->d_Y, 1, st);
+  if (rc) return rc;
+  CU(launch_permute_out(h->d_Y, n, dst, n, h->d_perm, n, 1, st));
+  return 0;
+}
+
+int ensure_gmres(spchol_handle_t h) {
+  if (h->d_gmV) return 0;
+  const int64_t n = h->plan.n;
+  CU(cudaMalloc(&h->d_gmV, (size_t)n * (kGmresRestart + 1) * sizeof(double)));
+  CU(cudaMalloc(&h->d_gmW, (size_t)n * sizeof(double)));
+  CU(cudaMalloc(&h->d_gmPart, (size_t)kGmresBlocks * (kGmresRestart + 1) * sizeof(double)));
+  CU(cudaMalloc(&h->d_gmH, 3 * (kGmresRestart + 2) * sizeof(double)));
+  CU(cudaMallocHost(&h->h_gmH, 3 * (kGmresRestart + 2) * sizeof(double)));
+  return 0;
+}
+
+// One GMRES-IR correction (Carson and Higham, "Accelerating the solution of
+// linear systems by iterative refinement in three precisions", SIAM J. Sci.
+// Comput. 40, 2018, restated with two precisions): the correction equation
+// A d = r of right-hand side c is solved by GMRES in FP64 on M^{-1} A d =
+// M^{-1} r, left-preconditioned by the low-precision factor, instead of by one
+// application of M^{-1}; it converges where the classic step's contraction
+// u_f kappa(A) exceeds one.  Arnoldi by classical Gram-Schmidt applied twice;
+// Givens rotations on the host; one cycle of at most kGmresRestart steps, to
+// a preconditioned residual reduction of 1e-10.  x_c += d.  *steps: the
+// Arnoldi steps taken.
+int gmres_correction(spchol_handle_t h, int c, cudaStream_t st, int* steps) {
+  const int64_t n = h->plan.n;
+  const int m = kGmresRestart;
+  double* V = h->d_gmV;
+  double* hd = h->d_gmH;  // [0, m+1): first pass, [m+2, 2m+3): second pass, [2m+4]: norm
+  double* hh = h->h_gmH;
+  int rc = apply_factor_inverse(h, h->d_R + (size_t)c * n, V, st);
+  if (rc) return rc;
+  CU(launch_dots(n, 1, V, n, V, h->d_gmPart, hd, st));
+  CU(cudaMemcpyAsync(hh, hd, sizeof(double), cudaMemcpyDeviceToHost, st));
+  CU(cudaStreamSynchronize(st));
+  const double beta = std::sqrt(hh[0]);
+  *steps = 0;
+  if (!(beta > 0.0) || !std::isfinite(beta)) return 0;
+  CU(launch_scale(n, 1.0 / beta, V, V, st));
+  std::vector<double> H((size_t)(m + 1) * m, 0.0), cs(m), sn(m), g(m + 1, 0.0);
+  g[0] = beta;
+  int k = 0;
+  for (; k < m; ++k) {
+    double* vk = V + (size_t)k * n;
+    double* z = V + (size_t)(k + 1) * n;
+    CU(launch_spmv(n, h->d_csr_rp, h->d_csr_ci, h->d_csr_vmap, h->d_vals, vk, h->d_gmW, st));
+    rc = apply_factor_inverse(h, h->d_gmW, z, st);
+    if (rc) return rc;
+    for (int pass = 0; pass < 2; ++pass) {
+      double* hp = hd + pass * (m + 2);
+      CU(launch_dots(n, k + 1, V, n, z, h->d_gmPart, hp, st));
+      CU(launch_axpy_multi(n, k + 1, V, n, hp, -1.0, z, st));
+    }
+    CU(launch_dots(n, 1, z, n, z, h->d_gmPart, hd + 2 * (m + 2), st));
+    CU(cudaMemcpyAsync(hh, hd, 3 * (m + 2) * sizeof(double), cudaMemcpyDeviceToHost, st));
+    CU(cudaStreamSynchronize(st));
+    double* col = H.data() + (size_t)k * (m + 1);
+    for (int j = 0; j <= k; ++j) col[j] = hh[j] + hh[(m + 2) + j];
+    const double hk1 = std::sqrt(hh[2 * (m + 2)]);
+    col[k + 1] = hk1;
+    if (hk1 > 0.0) CU(launch_scale(n, 1.0 / hk1, z, z, st));
+    for (int j = 0; j < k; ++j) {  // earlier rotations
+      const double a = col[j], b = col[j + 1];
+      col[j] = cs[j] * a + sn[j] * b;
+      col[j + 1] = -sn[j] * a + cs[j] * b;
+    }
+    const double r = std::hypot(col[k], col[k + 1]);
+    cs[k] = r > 0.0 ? col[k] / r : 1.0;
+    sn[k] = r > 0.0 ? col[k + 1] / r : 0.0;
+    col[k] = r;
+    col[k + 1] = 0.0;
+    g[k + 1] = -sn[k] * g[k];
+    g[k] = cs[k] * g[k];
+    if (!(std::fabs(g[k + 1]) > 1e-10 * beta) || !(hk1 > 0.0)) {
+      ++k;
+      break;
+    }
+  }
+  if (k > m) k = m;
+  // y = R^{-1} g (upper triangular), then x_c += V y
+  std::vector<double> y(k, 0.0);
+  for (int i = k - 1; i >= 0; --i) {
+    double s = g[i];
+    for (int j = i + 1; j < k; ++j) s -= H[(size_t)j * (m + 1) + i] * y[j];
+    const double d = H[(size_t)i * (m + 1) + i];
+    y[i] = d != 0.0 ? s / d : 0.0;
+  }
+  for (int i = 0; i < k; ++i) hh[i] = y[i];
+  CU(cudaMemcpyAsync(hd, hh, (size_t)std::max(k, 1) * sizeof(double), cudaMemcpyHostToDevice, st));
+  CU(launch_axpy_multi(n, k, V, n, hd, 1.0, h->d_X + (size_t)c * n, st));
+  *steps = k;
+  return 0;
+}
+
 // Mixed precision: X = A^{-1} B by the low-precision factor plus FP64
 // refinement.  B0 = d_B (original order, ld n, nrhs columns); X ends in d_B.
+// Classic refinement first; if it stops contracting, GMRES-IR continues from
+// the current iterate.
 int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
   Plan& P = h->plan;
   const int64_t n = P.n;
@@ -677,7 +789,8 @@ int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
   CU(cudaMemsetAsync(h->d_X, 0, n * nrhs * sizeof(double), st));
   CU(launch_correct(h->d_Y, n, h->d_X, n, h->d_perm, n, nrhs, st));
   double prev = INFINITY, berr = INFINITY;
-  int iters = 0;
+  int iters = 0, gmres_outer = 0, gmres_steps = 0;
+  bool gmres = false;
   rc = 0;
   for (;;) {
     CU(launch_residual(n, nrhs, h->d_csr_rp, h->d_csr_ci, h->d_csr_vmap, h->d_vals, h->d_X, n, h->d_B, n, h->d_R, n,
@@ -697,9 +810,32 @@ int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
       if (!(e <= berr)) berr = e;  // NaN propagates
     }
     if (berr <= h->opt.ir_tol) break;
-    if (!(berr == berr) || iters >= h->opt.ir_max_iter || berr > 0.5 * prev) {
-      rc = SPCHOL_ENOCONV;
-      break;
+    if (!gmres && (!(berr == berr) || iters >= h->opt.ir_max_iter || berr > 0.5 * prev)) {
+      // classic refinement stopped contracting: GMRES-IR from here (from zero
+      // if the iterate is no longer finite)
+      gmres = true;
+      if (!(berr == berr) || std::isinf(berr)) {
+        CU(cudaMemsetAsync(h->d_X, 0, n * nrhs * sizeof(double), st));
+        prev = INFINITY;
+        continue;
+      }
+    }
+    if (gmres) {
+      if (gmres_outer >= h->opt.ir_max_iter || !(berr == berr) || (gmres_outer > 0 && berr > 0.5 * prev)) {
+        rc = SPCHOL_ENOCONV;
+        break;
+      }
+      prev = berr;
+      if ((rc = ensure_gmres(h)) != 0) return rc;
+      for (int c = 0; c < nrhs; ++c) {
+        int steps = 0;
+        int r2 = gmres_correction(h, c, st, &steps);
+        if (r2) return r2;
+        gmres_steps += steps;
+      }
+      ++gmres_outer;
+      ++iters;
+      continue;
     }
     prev = berr;
     CU(launch_permute_in(h->d_R, n, h->d_Y, n, h->d_perm, n, nrhs, st));
@@ -709,6 +845,7 @@ int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
     ++iters;
   }
   h->stats.ir_iters = iters;
+  h->stats.ir_gmres_iters = gmres_steps;
   h->stats.berr = berr;
   CU(cudaMemcpyAsync(h->d_B, h->d_X, n * nrhs * sizeof(double), cudaMemcpyDeviceToDevice, st));
   return rc;
@@ -1039,6 +1176,9 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->h_prof) cudaFreeHost(h->h_prof);
   if (h->d_X) cudaFree(h->d_X);
   if (h->d_R) cudaFree(h->d_R);
+  for (double* p : {h->d_gmV, h->d_gmW, h->d_gmPart, h->d_gmH})
+    if (p) cudaFree(p);
+  if (h->h_gmH) cudaFreeHost(h->h_gmH);
   if (h->d_norms) cudaFree(h->d_norms);
   if (h->h_norms) cudaFreeHost(h->h_norms);
   if (h->ev0) cudaEventDestroy(h->ev0);

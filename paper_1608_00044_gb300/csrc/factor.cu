@@ -1136,12 +1136,14 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
           ahead = -1;
         }
         int lo_ready;
-        // the failure word is read before the claim, so that its round trip
-        // overlaps the claim's (it only lets later tasks skip their arithmetic)
-        const int info = ld_relaxed(&a.ctrl[kInfo]);
         sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
         if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
-        sh.skip = (info != INT_MAX);
+        // The failure word is read after the claim's acquire: a task whose
+        // inputs were skipped by tasks that saw a failed pivot (their release
+        // precedes this claim) then sees it too and skips as well.  Read
+        // before the claim, a diagonal task could factor a panel missing
+        // skipped updates and report a pivot failure that is not there.
+        sh.skip = (ld_relaxed(&a.ctrl[kInfo]) != INT_MAX);
         if (timed) {
           const uint64_t t1 = global_ns();
           tprof[10] += t1 - t0;

@@ -136,6 +136,17 @@ cudaError_t launch_anorm(int64_t n, const int64_t* rp, const int64_t* vmap, cons
                          unsigned long long* out, cudaStream_t st);
 cudaError_t launch_correct(const double* Y, int64_t ldy, double* X, int64_t ldx, const int32_t* perm, int64_t n,
                            int nrhs, cudaStream_t st);
+// GMRES-IR: y = A x; out[j] = V_j . z (j < k, fixed-order reductions; partial
+// holds kGmresBlocks * k doubles); z += alpha V h; y = alpha x.
+constexpr int kGmresThreads = 256, kGmresBlocks = 304;
+constexpr int kGmresRestart = 30;  // Krylov vectors per GMRES cycle
+cudaError_t launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const int64_t* vmap, const double* aval,
+                        const double* x, double* y, cudaStream_t st);
+cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ldv, const double* z, double* partial,
+                        double* out, cudaStream_t st);
+cudaError_t launch_axpy_multi(int64_t n, int k, const double* V, int64_t ldv, const double* h, double alpha, double* z,
+                              cudaStream_t st);
+cudaError_t launch_scale(int64_t n, double alpha, const double* x, double* y, cudaStream_t st);
 
 // sched.cu
 cudaError_t launch_relpos(const UTask* ut, int n_u, const int32_t* rows, const int64_t* rowoff,

@@ -76,6 +76,79 @@ int blocks_for(int64_t n, int threads) {
   return g < 1 ? 1 : (int)g;
 }
 
+// ---- GMRES-IR vector kernels (FP64; every reduction in one fixed order, so
+// the refinement stays bitwise reproducible in deterministic mode)
+
+// y = A x over the full symmetric pattern, one thread per row.
+__global__ void spmv_kernel(int64_t n, const int64_t* __restrict__ rp, const int32_t* __restrict__ ci,
+                            const int64_t* __restrict__ vmap, const double* __restrict__ aval,
+                            const double* __restrict__ x, double* __restrict__ y) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  double acc = 0.0;
+  for (int64_t k = rp[i]; k < rp[i + 1]; ++k) acc += aval[vmap[k]] * x[ci[k]];
+  y[i] = acc;
+}
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// partial[b * k + j] = block b's share of V_j . z for j < k (V_j at V + j ldv).
+__global__ void dots_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv, const double* __restrict__ z,
+                            double* __restrict__ partial) {
+  __shared__ double red[kGmresThreads / 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int j = 0; j < k; ++j) {
+    const double* v = V + j * ldv;
+    double acc = 0.0;
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+      acc += v[i] * z[i];
+    acc = warp_sum(acc);
+    if (lane == 0) red[warp] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int w = 0; w < kGmresThreads / 32; ++w) s += red[w];
+      partial[blockIdx.x * k + j] = s;
+    }
+    __syncthreads();
+  }
+}
+
+// out[j] = sum over blocks b (in order) of partial[b * k + j].
+__global__ void dots_finish_kernel(int nb, int k, const double* __restrict__ partial, double* __restrict__ out) {
+  for (int j = threadIdx.x; j < k; j += blockDim.x) {
+    double s = 0.0;
+    for (int b = 0; b < nb; ++b) s += partial[b * k + j];
+    out[j] = s;
+  }
+}
+
+// z += alpha * sum_j V_j h_j, j < k.
+__global__ void axpy_multi_kernel(int64_t n, int k, const double* __restrict__ V, int64_t ldv,
+                                  const double* __restrict__ h, double alpha, double* __restrict__ z) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    double acc = 0.0;
+    for (int j = 0; j < k; ++j) acc += V[j * ldv + i] * h[j];
+    z[i] += alpha * acc;
+  }
+}
+
+// y = alpha x
+__global__ void scale_kernel(int64_t n, double alpha, const double* __restrict__ x, double* __restrict__ y) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    y[i] = alpha * x[i];
+}
+
+int grid_stride_blocks(int64_t n) {
+  int64_t g = (n + kGmresThreads - 1) / kGmresThreads;
+  if (g > kGmresBlocks) g = kGmresBlocks;
+  return g < 1 ? 1 : (int)g;
+}
+
 }  // namespace
 
 cudaError_t launch_residual(int64_t n, int nrhs, const int64_t* rp, const int32_t* ci, const int64_t* vmap,
@@ -94,6 +167,35 @@ cudaError_t launch_anorm(int64_t n, const int64_t* rp, const int64_t* vmap, cons
   if (e != cudaSuccess) return e;
   if (n == 0) return cudaSuccess;
   anorm_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, rp, vmap, aval, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_spmv(int64_t n, const int64_t* rp, const int32_t* ci, const int64_t* vmap, const double* aval,
+                        const double* x, double* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  spmv_kernel<<<blocks_for(n, 256), 256, 0, st>>>(n, rp, ci, vmap, aval, x, y);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_dots(int64_t n, int k, const double* V, int64_t ldv, const double* z, double* partial,
+                        double* out, cudaStream_t st) {
+  if (k == 0) return cudaSuccess;
+  const int nb = grid_stride_blocks(n);
+  dots_kernel<<<nb, kGmresThreads, 0, st>>>(n, k, V, ldv, z, partial);
+  dots_finish_kernel<<<1, 64, 0, st>>>(nb, k, partial, out);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_axpy_multi(int64_t n, int k, const double* V, int64_t ldv, const double* h, double alpha, double* z,
+                              cudaStream_t st) {
+  if (n == 0 || k == 0) return cudaSuccess;
+  axpy_multi_kernel<<<grid_stride_blocks(n), kGmresThreads, 0, st>>>(n, k, V, ldv, h, alpha, z);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_scale(int64_t n, double alpha, const double* x, double* y, cudaStream_t st) {
+  if (n == 0) return cudaSuccess;
+  scale_kernel<<<grid_stride_blocks(n), kGmresThreads, 0, st>>>(n, alpha, x, y);
   return cudaGetLastError();
 }
 

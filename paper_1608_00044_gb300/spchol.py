@@ -66,6 +66,7 @@ class Stats(ctypes.Structure):
         ("n_subtrees", ctypes.c_int),
         ("factor_subtree_ms", ctypes.c_double),
         ("factor_subtree_count", ctypes.c_int64),
+        ("ir_gmres_iters", ctypes.c_int),
     ]
 
     def as_dict(self):

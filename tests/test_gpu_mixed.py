@@ -62,6 +62,53 @@ def test_refinement_reports_non_convergence():
     spchol.destroy(h)
 
 
+def test_gmres_ir_takes_over_when_classic_refinement_stalls():
+    """A TF32 factor of the Neumann Laplacian + 1e-4 I (kappa ~ 1.2e5, so
+    u_f kappa >> 1): classic refinement stops contracting, and GMRES-IR -- FP64
+    GMRES on the system left-preconditioned by the low-precision factor
+    (Carson and Higham 2018) -- continues from its iterate to the target."""
+    A = gridgen.neumann_laplacian_3d(16, 1e-4)
+    perm = gridgen.geometric_nd(A.dims)
+    B = gridgen.rhs_uniform(A.n, 2, seed=5)
+    rc, X, st, h = gpu_factor_solve(A, perm, B, precision=spchol.TF32)
+    assert rc == 0
+    assert st["ir_gmres_iters"] > 0, st
+    assert oracle.berr(A, X, B) <= BERR_MIXED
+    assert st["berr"] <= BERR_MIXED
+    spchol.destroy(h)
+
+
+@pytest.mark.parametrize("name", ["diff3d_12", "lap3d_16"])
+def test_gmres_ir_after_one_classic_step(name):
+    """With one classic step allowed, a TF32 factor (which needs more) hands
+    over to GMRES-IR, one right-hand side at a time; the result reaches the
+    target and agrees with the oracle's FP64 solution."""
+    A, perm, _ = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=6)
+    rc, X, st, h = gpu_factor_solve(A, perm, B, precision=spchol.TF32, ir_max_iter=1)
+    assert rc == 0
+    assert st["ir_gmres_iters"] > 0, st
+    assert oracle.berr(A, X, B) <= BERR_MIXED
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    np.testing.assert_allclose(X, f.solve(B), rtol=1e-9, atol=1e-11)
+    spchol.destroy(h)
+
+
+def test_gmres_ir_is_bitwise_reproducible_in_deterministic_mode():
+    """GMRES-IR's reductions run in one fixed order, so with the deterministic
+    factor and solve the refined solution is bitwise equal run to run."""
+    A, perm, _ = gridgen.workload("lap3d_16")
+    B = gridgen.rhs_uniform(A.n, 1, seed=7)
+    xs = []
+    for _ in range(2):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, precision=spchol.TF32, deterministic=1, ir_max_iter=1)
+        assert rc == 0 and st["ir_gmres_iters"] > 0
+        xs.append(X)
+        spchol.destroy(h)
+    assert np.array_equal(xs[0], xs[1])
+
+
 def test_mixed_batch():
     sides = [12, 20, 7, 33]
     mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
