@@ -121,6 +121,14 @@ class ClockSampler:
         return out
 
 
+def _describe(A):
+    """Human-readable name of a generated grid matrix, from its kind and dims."""
+    dims = "x".join(str(d) for d in A.dims)
+    return {"lap2d5": f"2D 5-point Laplacian {dims}", "lap3d7": f"3D 7-point Laplacian {dims}",
+            "diff3d27": f"3D 27-point variable-coefficient diffusion {dims}",
+            "diff2d5": f"2D 5-point variable-coefficient diffusion {dims}"}.get(A.kind, f"{A.kind} {dims}")
+
+
 def _workload(name):
     import gridgen
 
@@ -652,7 +660,7 @@ def run_ours(args):
         "dtype": {"fp64": "f64", "fp32": "f32", "tf32": "tf32", "tf32x3": "tf32x3",
                   "fp64tc": "f64 (updates: bf16 tensor cores on exact 7-way split)"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": f"{args.workload}: 3D 7-point Laplacian 64^3, n={A.n}, nnz(lower)={A.nnz}, "
+        "config": {"workload": f"{args.workload}: {_describe(A)}, n={A.n}, nnz(lower)={A.nnz}, "
                                f"geometric ND, relax {args.relax} zeros/col, {nrhs} RHS",
                    "max_width": args.width, "relax_zeros": args.relax, "precision": args.precision, "nrhs": nrhs,
                    "l2": "inputs larger than L2 (value pool %.2f GB)" % (st0["footprint_bytes"] / 1e9),
