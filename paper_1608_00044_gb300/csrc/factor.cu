@@ -905,12 +905,14 @@ __device__ __forceinline__ double fixed64_to_double(long long t, int k) {
       (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// The MMA is M = 64 x N = 16, the tile's at most kOzRows = 64 rows: each MMA
-// reads 2 KB of A digits from shared memory (an M = 128 MMA over the same rows
-// read 4 KB, half of it past the tile, and the MMA phase was bound by those
-// reads).  With M = 64 the accumulator's row 16 q + i (i < 16) sits in TMEM
-// lane 32 q + i, columns as N.  7 groups x 16 columns fit 128 TMEM columns,
-// and a CTA needs 73 KB of shared memory, so three CTAs share an SM.
+// The MMA is M = 64 x N = 16, the tile's at most kOzRows = 64 rows.  With
+// M = 64 the accumulator's row 16 q + i (i < 16) sits in TMEM lane 32 q + i,
+// columns as N.  7 groups x 16 columns fit 128 TMEM columns, a quarter of the
+// SM's, and a CTA needs 73 KB of shared memory, so three CTAs share an SM.
+// A tcgen05.mma costs about the same to issue whatever its M and N (~48
+// clocks from one thread, ~28 SM-wide when several issue), so the MMA phase is
+// bound by the instruction count; a wider N needs more TMEM and shared memory
+// than three CTAs per SM allow, and two CTAs per SM with N = 32 were slower.
 constexpr int kOzM = 64, kOzN = 16, kOzRows = 64;
 constexpr int kOzCols = 128;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
 
