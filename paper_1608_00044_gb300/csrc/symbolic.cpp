@@ -511,8 +511,11 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   for (int32_t s = 0; s < ns; ++s) P.rt_ptr[s + 1] += P.rt_ptr[s];
   P.rt_tile.resize(P.st_tgt.size());
   {
+    // each panel's list in descending tile order: the tiles of the nearest
+    // descendants -- the next steps of the backward chain -- are released
+    // first (and the first becomes the releasing CTA's continuation)
     std::vector<int32_t> fill(P.rt_ptr.begin(), P.rt_ptr.end() - 1);
-    for (int32_t tile = 0; tile < P.n_st; ++tile)
+    for (int32_t tile = P.n_st - 1; tile >= 0; --tile)
       for (int32_t q = P.st_tptr[tile]; q < P.st_tptr[tile + 1]; ++q) P.rt_tile[fill[P.st_tgt[q]]++] = tile;
   }
   P.kid_ptr.assign(ns + 1, 0);
