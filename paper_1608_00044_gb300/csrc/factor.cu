@@ -1073,8 +1073,8 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   __shared__ FactorShared sh;
   double* smd = reinterpret_cast<double*>(smem_raw);
   const Ring2 q = rings_of(a);
-  __shared__ int pend[2];  // claimed, still empty ring slots (thread 0)
-  if (threadIdx.x == 0) pend[0] = pend[1] = -1;
+  __shared__ int pend[3];  // claimed, not yet taken ring slots (thread 0)
+  if (threadIdx.x == 0) pend[0] = pend[1] = pend[2] = -1;
   // per-CTA task timing (thread 0 only, in shared memory so that no register
   // stays live across the tasks), flushed once at exit: [0..4] busy ns per task
   // type ([3]: tensor-core update tiles, [4]: subtree tasks), [5..9] counts,
@@ -1118,8 +1118,11 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   }
   // Thread 0: a normal-priority slot claimed ahead while the ring is deep, so
   // that the claim's round trip overlaps the current task; it joins pend[1] at
-  // the next claim (a deep ring fills it long before).
-  int ahead = -1;
+  // the next claim (a deep ring fills it long before).  Two adjacent slots are
+  // claimed ahead at a time: the next claim reads both in one round trip and
+  // the second task (the stash) then runs without a claim of its own.
+  int ahead = -1, stash = -1;
+  bool deep = false;
   // Subtree task cursor (thread 0): a claimed subtree task is run as a
   // sequence of panel-level steps through the same dispatch as the ring's
   // tasks -- diagonal, panel-solve tiles, update tiles of each panel in
@@ -1133,13 +1136,22 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
       const bool timed = a.prof || a.trace;
       if (cur_task < 0) {
         const uint64_t t0 = timed ? global_ns() : 0;
-        if (ahead >= 0) {
-          pend[1] = ahead < q.n_lo ? ahead : -1;
-          ahead = -1;
+        const bool idle = pend[1] < 0 && pend[2] < 0;
+        if (stash >= 0) {  // acquired by the previous claim
+          sh.task = stash;
+          stash = -1;
+          if (deep && idle) ahead = atomicAdd(&q.ctrl[kHead], 2);
+        } else {
+          if (ahead >= 0) {
+            pend[1] = ahead < q.n_lo ? ahead : -1;
+            pend[2] = ahead + 1 < q.n_lo ? ahead + 1 : -1;
+            ahead = -1;
+          }
+          int lo_ready;
+          sh.task = ring2_claim(q, pend, &lo_ready, a.ntask, &stash);
+          deep = lo_ready > 4 * (int)gridDim.x;
+          if (sh.task >= 0 && pend[1] < 0 && pend[2] < 0 && stash < 0 && deep) ahead = atomicAdd(&q.ctrl[kHead], 2);
         }
-        int lo_ready;
-        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
-        if (sh.task >= 0 && pend[1] < 0 && lo_ready > 2 * (int)gridDim.x) ahead = atomicAdd(&q.ctrl[kHead], 1);
         // The failure word is read after the claim's acquire: a task whose
         // inputs were skipped by tasks that saw a failed pivot (their release
         // precedes this claim) then sees it too and skips as well.  Read

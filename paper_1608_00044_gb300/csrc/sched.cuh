@@ -104,24 +104,32 @@ struct Ring2 {
   int64_t budget_ns;
 };
 
-// Thread 0 only.  pend[0..1]: this CTA's claimed, not yet filled slot of each
-// ring (-1 none), kept across calls.  Returns a task id, or -1 when every task
-// has been claimed, another CTA reported an error, or the wait ran out.
-// *lo_ready: unclaimed slots of the normal-priority ring at the last look (0
-// if the task came from the high-priority ring before the other was read).
-__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_ready, int ntask_total) {
+// Thread 0 only.  pend[0]: this CTA's claimed, not yet taken slot of the
+// high-priority ring; pend[1], pend[2]: of the normal-priority ring, taken in
+// that order (-1 none); all kept across calls.  Returns a task id, or -1 when
+// every task has been claimed, another CTA reported an error, or the wait ran
+// out.  *lo_ready: unclaimed slots of the normal-priority ring at the last
+// look (0 if the task came from the high-priority ring before the other was
+// read).  When the task comes from pend[1] and pend[2] is filled as well, and
+// stash is given, pend[2]'s task is acquired too and returned in *stash, for
+// the caller to run next without a claim.
+__device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_ready, int ntask_total,
+                                           int* stash = nullptr) {
   *lo_ready = 0;
   const uint64_t t0 = global_ns();
   const uint64_t max_iter = (uint64_t)(q.budget_ns / 32) + 100000;
   unsigned backoff = 32;
   for (uint64_t it = 0;; ++it) {
-    // Both rings' (head, tail) and the normal-priority slot this CTA already
-    // holds, in one round trip: the relaxed loads are issued first and the
-    // acquiring load of the slot last, so none waits for another (a claim with
-    // a slot held ahead -- the common case -- used to take three round trips).
+    // Both rings' (head, tail) and the normal-priority slots this CTA already
+    // holds, in one round trip: relaxed loads, none waiting for another (a
+    // claim with slots held ahead -- the common case -- used to take three
+    // round trips).  A slot value is used only after the fence below: a
+    // relaxed load that sees the pusher's release store, then the fence, is
+    // an acquire.
     const int2 hi = ld_relaxed_pair(&q.ctrl[kHiHead]);  // (head, tail)
     const int2 lo = ld_relaxed_pair(&q.ctrl[kHead]);
-    const int v1 = pend[1] >= 0 ? ld_acquire(&q.lo[pend[1]]) : -1;
+    const int v1 = pend[1] >= 0 ? ld_relaxed(&q.lo[pend[1]]) : -1;
+    const int v2 = pend[2] >= 0 ? ld_relaxed(&q.lo[pend[2]]) : -1;
     *lo_ready = lo.y - lo.x;
     if (pend[0] < 0 && hi.x < hi.y && hi.x < q.n_hi) {
       const int s = atomicAdd(&q.ctrl[kHiHead], 1);
@@ -144,6 +152,13 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
       // push, which may need the other ring's tasks: keep serving that ring.
     } else if (v1 >= 0) {
       pend[1] = -1;
+      if (v2 >= 0 && stash) {
+        *stash = v2;
+        pend[2] = -1;
+      } else if (pend[2] >= 0) {
+        pend[1] = pend[2];
+        pend[2] = -1;
+      }
       __threadfence();
       return v1;
     } else if (pend[1] < 0 && lo.x < lo.y && lo.x < q.n_lo) {
@@ -158,7 +173,7 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
         }
       }
     }
-    if (pend[0] < 0 && pend[1] < 0 && hi.x >= q.n_hi && lo.x >= q.n_lo) return -1;  // all claimed
+    if (pend[0] < 0 && pend[1] < 0 && pend[2] < 0 && hi.x >= q.n_hi && lo.x >= q.n_lo) return -1;  // all claimed
     // An idle grid polls these words from every CTA: the error word is read on
     // every 8th round only, and the backoff grows to 2 us, so that the polling
     // does not queue up the claims and pushes on the same L2 lines.

@@ -689,9 +689,9 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
   // the seeds, so that chains up the tree advance instead of queueing behind
   // every leaf.
   const Ring2 q{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
-  __shared__ int pend[2];
+  __shared__ int pend[3];
   if (threadIdx.x == 0) {
-    pend[0] = pend[1] = -1;
+    pend[0] = pend[1] = pend[2] = -1;
     sh.next = -1;
   }
   const int ns = a.pv.ns, nst = a.n_st;
