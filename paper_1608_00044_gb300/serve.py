@@ -45,6 +45,12 @@ class Request:
     done: float = 0.0
     rc: int = 0
     factored: bool = False
+    # where the latency went (seconds): symbolic analysis of a new pattern, wait
+    # for the pattern's handle, numeric factorization, solve and copy back
+    t_analyze: float = 0.0
+    t_lock: float = 0.0
+    t_factor: float = 0.0
+    t_solve: float = 0.0
 
 
 class _Resident:
@@ -129,13 +135,19 @@ class Server:
         req.start = time.perf_counter() - t0
         A, perm = req.payload if req.payload is not None else req.make()
         req.payload = None  # the matrix is not kept after its request
+        ta = time.perf_counter()
         r, fresh = self._acquire(req, A, perm)
+        tb = time.perf_counter()
+        req.t_analyze = tb - ta
         try:
             with r.lock:  # one slot at a time per handle
+                tc = time.perf_counter()
+                req.t_lock = tc - tb
                 with torch.cuda.stream(stream):
                     if r.vkey != req.vkey:
                         vals = torch.from_numpy(np.ascontiguousarray(A.values)).cuda(non_blocking=True)
                         rc = spchol.factorize(r.h, vals, stream=stream)
+                        req.t_factor = time.perf_counter() - tc
                         r.vkey = req.vkey if rc == 0 else None
                         req.factored = True
                         with self.mem_cv:
@@ -143,6 +155,7 @@ class Server:
                         if rc != 0:
                             req.rc = rc
                             return
+                    td = time.perf_counter()
                     nrhs = req.B.shape[1]
                     Bt = torch.from_numpy(np.ascontiguousarray(req.B.T)).cuda(non_blocking=True)
                     try:
@@ -152,6 +165,7 @@ class Server:
                             raise
                         req.rc = e.code
                     req.X = np.asfortranarray(Bt.cpu().numpy().T)
+                    req.t_solve = time.perf_counter() - td
         finally:
             self._release(r)
             req.done = time.perf_counter() - t0
@@ -222,6 +236,13 @@ def latency_summary(reqs: list[Request]) -> dict:
     if rep.size:
         out["repeat_p50_ms"] = float(np.percentile(rep, 50))
         out["repeat_p99_ms"] = float(np.percentile(rep, 99))
+    # mean breakdown of the slowest 5 % (arrival to start = wait for a slot)
+    tail = [q for q, l in zip(reqs, lat) if l >= np.percentile(lat, 95)]
+    if tail:
+        parts = {"queue": [q.start - q.arrival for q in tail], "analyze": [q.t_analyze for q in tail],
+                 "handle_wait": [q.t_lock for q in tail], "factor": [q.t_factor for q in tail],
+                 "solve": [q.t_solve for q in tail]}
+        out["tail5_ms"] = {k: float(np.mean(v)) * 1e3 for k, v in parts.items()}
     return out
 
 
