@@ -336,31 +336,34 @@ def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, wid
 
 def measure_scheduling(spchol, oracle, torch, dev, name="lap3d_40", width=64):
     """Scheduling-policy row (Section IV-B's static schedule against the dynamic
-    one, restated for one GPU): the same matrix factored and solved with the
-    default dynamic two-priority rings and with the deterministic static
-    (target, source) order; median factor time of 3, solve time, backward
-    errors, and whether two static runs agree bitwise."""
+    one, restated for one GPU), with the fan-in aggregation (Section II-C's
+    fan-in family) as the fast deterministic mode: the same matrix factored and
+    solved with the default dynamic two-priority rings, with the static
+    (target, source) order, and with fan-in buffers; median factor time of 3,
+    solve time, backward errors, device footprint, and whether the first and
+    the last of four factor + solve runs agree bitwise."""
     A, perm, b = _workload(name)
     vals = torch.from_numpy(A.values).to(dev)
     out = {"workload": f"{name}: 3D 7-point {A.dims}, n={A.n}, {b.shape[1]} RHS"}
-    for label, det in (("dynamic", 0), ("static", 1)):
+    for label, det in (("dynamic", 0), ("static", 1), ("fanin", 2)):
         h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(max_width=width, deterministic=det))
-        times, xs = [], []
+        times, xs, s_ms = [], [], []
         for it in range(4):
             spchol.factorize(h, vals)
             if it >= 1:
                 times.append(spchol.stats(h)["factor_ms"])
-        s_ms = []
-        for it in range(2):
-            X = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
-            spchol.solve(h, X, A.n, b.shape[1])
-            s_ms.append(spchol.stats(h)["solve_ms"])
-            xs.append(X.cpu().numpy())
+            if it in (0, 3):
+                X = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
+                spchol.solve(h, X, A.n, b.shape[1])
+                s_ms.append(spchol.stats(h)["solve_ms"])
+                xs.append(X.cpu().numpy())
         be = oracle.berr(A, np.asfortranarray(xs[0].T), b)
+        fp = spchol.stats(h)["footprint_bytes"]
         spchol.destroy(h)
         out[label] = {"factor_ms": statistics.median(times), "solve_ms": min(s_ms), "berr": be,
-                      "runs_bitwise_equal": bool(np.array_equal(xs[0], xs[1]))}
+                      "footprint_bytes": int(fp), "runs_bitwise_equal": bool(np.array_equal(xs[0], xs[1]))}
     out["static_over_dynamic_factor"] = out["static"]["factor_ms"] / out["dynamic"]["factor_ms"]
+    out["fanin_over_dynamic_factor"] = out["fanin"]["factor_ms"] / out["dynamic"]["factor_ms"]
     return out
 
 

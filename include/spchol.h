@@ -93,6 +93,15 @@ typedef struct spchol_options {
                              entries, run one after another in (source, tile) order, so every
                              sum lands in one fixed order and the factor and solution are
                              bitwise reproducible (run to run, alone or in a batch); slower.
+                             2: bitwise reproducible by fan-in aggregation (Section II-C's
+                             fan-in family): every update tile stores its product in a private
+                             buffer, and each panel adds the buffers into its rows in one fixed
+                             (tile) order when it is factored, so the update tiles themselves
+                             run in any order.  Every entry receives its updates in the same
+                             order as with 1, so the results are bitwise those of 1, at a
+                             fraction of 1's time; the
+                             buffers cost (sum over update tiles of rows x columns) values of
+                             device memory, in footprint_bytes.  The solves run as with 1.
                              0 (default): dynamic order, results equal up to rounding */
   int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
   int ir_max_iter;        /* mixed precision: refinement steps; default 10 */

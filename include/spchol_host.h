@@ -45,7 +45,12 @@ enum {
   SPCHOL_PLAN_ADEST = 14,    /* nnz(A): pool index of each entry of A */
   SPCHOL_PLAN_NUHI = 15,     /* ns: leading update tiles of each panel scheduled with high priority */
   SPCHOL_PLAN_SUBLO = 16,    /* subtree tasks: first panel of each (a subtree is a contiguous range) */
-  SPCHOL_PLAN_SUBHI = 17     /* subtree tasks: last panel (the subtree's root) of each */
+  SPCHOL_PLAN_SUBHI = 17,    /* subtree tasks: last panel (the subtree's root) of each */
+  /* fan-in mode (options.deterministic = 2; length 0 otherwise) */
+  SPCHOL_PLAN_FANOFF = 18,   /* n_u+1: offset of each update tile's private buffer (values) */
+  SPCHOL_PLAN_FANTASK = 19,  /* ns+n_trsm: first row piece of each diagonal task, then of each panel-solve tile */
+  SPCHOL_PLAN_FANPTR = 20,   /* pieces+1: offsets into FANENT */
+  SPCHOL_PLAN_FANENT = 21    /* 3 * entries: (update tile, first row, end row) per gather-list entry */
 };
 
 /* Host-only analysis; same arguments and return codes as spchol_analyze. */

@@ -80,6 +80,14 @@ struct spchol_handle_s {
   // Plan::ft_sptr, their initial counters and the live counters
   int32_t *d_u_next = nullptr, *d_u_dep0 = nullptr, *d_u_dep = nullptr;
   int32_t *d_ft_sptr = nullptr, *d_ft_succ = nullptr, *d_ft_dep0 = nullptr, *d_ftdep = nullptr;
+  // fan-in mode (options.deterministic = 2): Plan::fan_* and the update
+  // tiles' private buffers (a separate allocation, in the panels' type)
+  int64_t *d_fan_off = nullptr, *d_fan_ptr = nullptr;
+  int32_t* d_fan_task = nullptr;
+  FanEnt* d_fan_ent = nullptr;
+  void* d_fan_buf = nullptr;
+  size_t fan_buf_bytes = 0;
+  int fan_cap = 0;
   int32_t *d_sseeds = nullptr;
   int nsseeds = 0;
   int32_t* d_perm = nullptr;
@@ -242,6 +250,10 @@ int setup_device(spchol_handle_t h) {
          o_ud = det ? r32(P.u_dep0.size()) : 0, o_fsp = det ? r32(P.ft_sptr.size()) : 0,
          o_fsu = det ? r32(P.ft_succ.size()) : 0, o_fd0d = det ? r32(P.ft_dep0.size()) : 0,
          o_fdd = det ? r32(P.ft_dep0.size()) : 0;
+  const bool fan = P.params.fanin;
+  size_t o_fano = fan ? r64(P.fan_off.size()) : 0, o_fant = fan ? r32(P.fan_task.size()) : 0,
+         o_fanp = fan ? r64(P.fan_ptr.size()) : 0,
+         o_fane = fan ? A.reserve(std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanEnt)) : 0;
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
   size_t o_prof = A.reserve(24 * sizeof(unsigned long long));
@@ -341,6 +353,12 @@ int setup_device(spchol_handle_t h) {
     h->d_ft_dep0 = (int32_t*)(b + o_fd0d);
     h->d_ftdep = (int32_t*)(b + o_fdd);
   }
+  if (fan) {
+    h->d_fan_off = (int64_t*)(b + o_fano);
+    h->d_fan_task = (int32_t*)(b + o_fant);
+    h->d_fan_ptr = (int64_t*)(b + o_fanp);
+    h->d_fan_ent = (FanEnt*)(b + o_fane);
+  }
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
   h->d_ctrl = (int*)(b + o_ctrl);
@@ -383,7 +401,14 @@ int setup_device(spchol_handle_t h) {
               (rc = upload(h, h->d_ft_sptr, P.ft_sptr)) || (rc = upload(h, h->d_ft_succ, P.ft_succ)) ||
               (rc = upload(h, h->d_ft_dep0, P.ft_dep0))))
     return rc;
+  if (fan && ((rc = upload(h, h->d_fan_off, P.fan_off)) || (rc = upload(h, h->d_fan_task, P.fan_task)) ||
+              (rc = upload(h, h->d_fan_ptr, P.fan_ptr)) || (rc = upload(h, h->d_fan_ent, P.fan_ent))))
+    return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
+  if (fan) {  // never read before written: no initialisation
+    h->fan_buf_bytes = std::max<size_t>((size_t)P.fan_off.back() * esz, 256);
+    CU(cudaMalloc(&h->d_fan_buf, h->fan_buf_bytes));
+  }
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
   CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
@@ -421,9 +446,10 @@ int setup_device(spchol_handle_t h) {
     CU(cudaDeviceGetAttribute(&smem_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, h->device));
     h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 5 + 1024);
   }
+  if (fan) h->smem_factor = std::max(h->smem_factor, fanin_smem_bytes(wmax, h->fp32, &h->fan_cap));
   h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC);
   int bf = 0, bs = 0;
-  CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), h->smem_factor, &bf));
+  CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
   CU(solve_configure(h->fp32, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
   if (h->opt.ctas_per_sm > 0) {
@@ -434,7 +460,7 @@ int setup_device(spchol_handle_t h) {
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
   h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
                                        (size_t)P.n_rel * sizeof(int32_t) + (size_t)P.ns * (h->d_tmaps ? 128 : 0) +
-                                       (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0));
+                                       (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0) + h->fan_buf_bytes);
   h->stats.grid_factor = h->grid_factor;
   h->stats.grid_solve = h->grid_solve;
   h->stats.tma_staging = h->d_tmaps != nullptr ? 1 : 0;
@@ -549,10 +575,18 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.tc_min_width = P.params.tc_min_width;
   a.dep_f = h->d_dep;
   a.trsm_left = h->d_trsm_left;
-  if (P.params.deterministic && P.n_u > 0) {
+  if (P.params.deterministic && !P.params.fanin && P.n_u > 0) {
     CU(cudaMemcpyAsync(h->d_u_dep, h->d_u_dep0, (size_t)P.n_u * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     a.u_next = h->d_u_next;
     a.u_dep = h->d_u_dep;
+  }
+  if (P.params.fanin) {
+    a.fan_buf = h->d_fan_buf;
+    a.fan_off = h->d_fan_off;
+    a.fan_task = h->d_fan_task;
+    a.fan_ptr = h->d_fan_ptr;
+    a.fan_ent = h->d_fan_ent;
+    a.fan_cap = h->fan_cap;
   }
   a.ring = h->d_ring;
   a.ctrl = h->d_ctrl;
@@ -1164,6 +1198,7 @@ int spchol_destroy(spchol_handle_t h) {
   DeviceGuard g(h->device);
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
+  if (h->d_fan_buf) cudaFree(h->d_fan_buf);
   if (h->d_inv) cudaFree(h->d_inv);
   if (h->d_relpos) cudaFree(h->d_relpos);
   if (h->d_tmaps) cudaFree(h->d_tmaps);

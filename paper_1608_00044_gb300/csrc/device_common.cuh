@@ -94,4 +94,15 @@ __device__ __forceinline__ void stage_lower(const T* __restrict__ src, int w, in
 cudaError_t ensure_smem_limit(const void* fn, size_t need);
 __device__ __forceinline__ void red_add(float* p, float v) { atomicAdd(p, v); }
 
+// An update value into its destination: an atomic add into a target panel
+// that other tiles update too, or a plain store into a buffer that only this
+// tile writes (the fan-in mode of the factorization).
+template <typename T>
+__device__ __forceinline__ void scatter_put(T* p, T v, bool store) {
+  if (store)
+    *p = v;
+  else
+    red_add(p, v);
+}
+
 }  // namespace spchol

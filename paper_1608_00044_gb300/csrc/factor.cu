@@ -86,6 +86,122 @@ __device__ __forceinline__ double pivot_recip(double d) {
   return 1.0 / d;
 }
 
+// ---------------------------------------------------------------- fan-in gather
+// Deterministic fan-in mode (the fan-in family of Section II-C, restated for
+// one GPU): update tiles store their products in private buffers, and the task
+// that owns a piece of a target panel's rows (at most kFanPieceRows rows, all
+// columns) adds them in before it factors or solves those rows, tile after
+// tile in the piece's list order, so every entry of L receives its updates in
+// one fixed order whatever the schedule.  The piece sits in shared memory.  A
+// batch of tiles at a time: warp 0 reads the next list entries and their
+// tiles and cuts the batch where their values would overflow the staging
+// area; all threads then fetch the batch's values and target offsets
+// (independent loads, many in flight); the values are added tile by tile.
+struct FanMeta {
+  long long fo;   // the tile's buffer offset
+  long long rel;  // its relative row indices
+  long long rs;   // its segment's row numbers (index into the row lists)
+  int rowlen, i0, ni, pre;  // buffer rows; first row and row count in the piece; first staged value
+};
+constexpr int kFanBatch = 32;
+constexpr size_t kFanMetaBytes = kFanBatch * sizeof(FanMeta) + 16;
+
+template <typename T>
+__device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np, unsigned char* smraw) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int ft = a.pv.fcol[t], wt = a.pv.fcol[t + 1] - ft, ldt = a.pv.ld[t];
+  T* Pt = panel_ptr<T>(a, t);
+  const T* F = reinterpret_cast<const T*>(a.fan_buf);
+  const int cap = a.fan_cap;  // a multiple of 8, at least kFanPieceRows x the widest panel
+  unsigned char* base = smraw + ((16u - (smem_addr(smraw) & 15u)) & 15u);
+  FanMeta* meta = reinterpret_cast<FanMeta*>(base);
+  int* scal = reinterpret_cast<int*>(meta + kFanBatch);  // [0] tiles in the batch, [1] their values
+  int16_t* tg = reinterpret_cast<int16_t*>(base + kFanMetaBytes);  // target offset in S, or -1
+  T* Bs = reinterpret_cast<T*>(tg + cap);
+  T* S = Bs + cap;  // the piece: np rows x wt columns, leading dimension kFanPieceRows
+  long long e = a.fan_ptr[pc];
+  const long long e1 = a.fan_ptr[pc + 1];
+  if (e == e1) return;  // nothing lands in these rows
+  for (int idx = tid; idx < np * wt; idx += nt) {
+    const int p = idx % np, c = idx / np;
+    S[p + kFanPieceRows * c] = ldcg(Pt + p0 + p + (size_t)c * ldt);
+  }
+  while (e < e1) {
+    __syncthreads();  // the piece is loaded, or the previous batch is added
+    if (tid < 32) {
+      FanMeta mm{};
+      int n = 0;
+      if (e + tid < e1) {
+        const FanEnt fe = a.fan_ent[e + tid];
+        const UTask u = a.ut[fe.u];
+        mm.fo = a.fan_off[fe.u];
+        mm.rel = u.rel;
+        mm.rs = a.pv.rowoff[u.s] + u.seg0;
+        mm.rowlen = u.rowlen;
+        mm.i0 = fe.i0;
+        mm.ni = fe.i1 - fe.i0;
+        n = mm.ni * u.seglen;
+      }
+      int inc = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, inc, o);
+        if (tid >= o) inc += y;
+      }
+      // the tiles whose values fit form a prefix; the first one always fits
+      const int nb = max(1, __popc(__ballot_sync(0xffffffffu, n > 0 && inc <= cap)));
+      if (tid < nb) {
+        mm.pre = inc - n;
+        meta[tid] = mm;
+      }
+      if (tid == nb - 1) {
+        scal[0] = nb;
+        scal[1] = inc;
+      }
+    }
+    __syncthreads();
+    const int nb = scal[0];
+    int total = scal[1];
+    if (total > cap) {  // cannot happen for a consistent plan: stage nothing past the area
+      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      total = 0;
+    }
+    for (int idx = tid; idx < total; idx += nt) {
+      int k = 0;
+#pragma unroll
+      for (int b = kFanBatch / 2; b > 0; b >>= 1)
+        if (k + b < nb && meta[k + b].pre <= idx) k += b;
+      const FanMeta& mk = meta[k];
+      const int le = idx - mk.pre, i = mk.i0 + le % mk.ni, j = le / mk.ni;
+      const int p = __ldg(a.relpos + mk.rel + i) - p0;
+      const int c = __ldg(a.pv.rows + mk.rs + j) - ft;
+      // lower triangle of the target (rows below its diagonal block always are)
+      bool lower = p0 + p >= wt || p0 + p >= c;
+      if (p < 0 || p >= np || c < 0 || c >= wt) {  // outside the piece: an inconsistent plan
+        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+        lower = false;
+      }
+      tg[idx] = lower ? (int16_t)(p + kFanPieceRows * c) : (int16_t)-1;
+      if (lower) Bs[idx] = ldcg(F + mk.fo + i + (size_t)j * mk.rowlen);
+    }
+    __syncthreads();
+    for (int k = 0; k < nb; ++k) {  // one tile at a time: an entry's updates land in list order
+      const int k0 = meta[k].pre, k1 = k + 1 < nb ? meta[k + 1].pre : total;
+      for (int idx = k0 + tid; idx < k1; idx += nt) {
+        const int g = tg[idx];
+        if (g >= 0) S[g] += Bs[idx];
+      }
+      __syncthreads();
+    }
+    e += nb;
+  }
+  for (int idx = tid; idx < np * wt; idx += nt) {
+    const int p = idx % np, c = idx / np;
+    Pt[p0 + p + (size_t)c * ldt] = S[p + kFanPieceRows * c];
+  }
+  __syncthreads();  // the task reads these rows next, and reuses the shared memory
+}
+
 template <typename T>
 __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip, bool release = true) {
   const int tid = threadIdx.x;
@@ -409,9 +525,18 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
 // update, Section III-A).  They are fixed by the structure, so one kernel at
 // analysis time finds them for every row of every update tile (a binary search
 // each), and an update tile only loads its rowlen of them.
+// In the fan-in mode the tile writes its own buffer instead, addressed as a
+// panel whose rows are the tile's rows and whose columns are the segment's:
+// position i for row i, and the source's own row numbers for the lower-
+// triangle test (the row lists are increasing, so it gives the same answer).
 __device__ __forceinline__ void load_relpos(const FactorArgs& a, const UTask& u, int* pos, int* grow,
-                                            const int32_t* Rs) {
+                                            const int32_t* Rs, bool fan) {
   for (int i = threadIdx.x; i < u.rowlen; i += blockDim.x) {
+    if (fan) {
+      pos[i] = i;
+      grow[i] = u.row0 + i;
+      continue;
+    }
     const int p = __ldg(a.relpos + u.rel + i);
     if (p < 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // cannot happen for a consistent plan
     pos[i] = p;
@@ -565,9 +690,9 @@ __device__ __forceinline__ void upd_strip_nc(int nc, const acc_t* As, const acc_
   }
 }
 
-template <typename T>
+template <typename T, bool FAN>
 __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh,
-                            bool skip, int rot, const UpdTma& tma, bool release = true) {
+                            bool skip, int rot, const UpdTma& tma, long long fo, bool release = true) {
   using acc_t = T;
   constexpr int STR = Stage<T>::kStr, E = Stage<T>::E;
   constexpr uint32_t kBoxBytes = (uint32_t)(kUpdKC * STR * sizeof(T));
@@ -575,9 +700,10 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
   const int s = u.s, t = u.t;
   if (!skip) {
     const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, lds = a.pv.ld[s];
-    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t];
+    constexpr bool fan = FAN;  // fan-in mode: the tile's buffer at fo (see load_relpos)
+    const int ft = fan ? u.seg0 : a.pv.fcol[t], ldt = fan ? u.rowlen : a.pv.ld[t];
     const T* Ps = panel_ptr<T>(a, s);
-    T* Pt = panel_ptr<T>(a, t);
+    T* Pt = fan ? reinterpret_cast<T*>(a.fan_buf) + fo : panel_ptr<T>(a, t);
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
 
     // [2][A, B][kUpdKC][STR], 128-byte aligned (each chunk is a multiple of 128 bytes)
@@ -591,7 +717,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
 
     // Relative row indices (computed once per analysis): position of each
     // row of the tile in t's sorted row list.
-    load_relpos(a, u, pos, grow, Rs);
+    load_relpos(a, u, pos, grow, Rs, fan);
     // Warp slot q' = (warp - rot) % 8 (tiles of few strips load the four SM
     // sub-partitions, warp % 4, evenly over many tasks).  A tile of S strips
     // gives each strip C = 8 / S (rounded down to a power of two) warps, which
@@ -618,7 +744,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       const int ncb = dd < 0 ? 0 : max(0, min(min(nall, b0 + nper), dd / 8 + 1) - b0);
       const bool active = srows > 0 && ncb > 0;
       __syncthreads();  // the previous pass is done with the buffers and gcol
-      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[c0 + j];
+      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = fan ? c0 + j : Rs[c0 + j];
       acc_t acc[2][8];
 #pragma unroll
       for (int rr = 0; rr < 2; ++rr)
@@ -688,7 +814,8 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
 #pragma unroll
           for (int cc = 0; cc < 8; ++cc) {
             const int j = lc + 8 * (b0 + cc);
-            if (cc < ncb && j < ncol && gi >= gcol[j]) red_add(dst + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]));
+            if (cc < ncb && j < ncol && gi >= gcol[j])
+              scatter_put(dst + (size_t)(gcol[j] - ft) * ldt, (T)(-acc[rr][cc]), fan);
           }
         }
       }
@@ -757,15 +884,17 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint32_t mbar, uint32_t phase)
   return false;
 }
 
+template <bool FAN>
 __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
-                               TcState& tc, bool release = true) {
+                               TcState& tc, long long fo, bool release = true) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = u.s, t = u.t;
   if (!skip) {
     const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, lds = a.pv.ld[s];
-    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
+    constexpr bool fan = FAN;  // fan-in mode: the tile's buffer at fo (see load_relpos)
+    const int ft = fan ? u.seg0 : a.pv.fcol[t], ldt = fan ? u.rowlen : a.pv.ld[t];
     const float* Ps = reinterpret_cast<const float*>(a.pool) + a.pv.valoff[s];
-    float* Pt = reinterpret_cast<float*>(a.pool) + a.pv.valoff[t];
+    float* Pt = fan ? reinterpret_cast<float*>(a.fan_buf) + fo : reinterpret_cast<float*>(a.pool) + a.pv.valoff[t];
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
     const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
     const int split = a.mma_mode == 2 ? 1 : 0;
@@ -780,7 +909,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     int* grow = pos + kTcM;
     int* gcol = grow + kTcM;
 
-    load_relpos(a, u, pos, grow, Rs);
+    load_relpos(a, u, pos, grow, Rs, fan);
     // A: tile rows x k (rows >= rowlen and k >= ws are zero)
     for (int idx = tid; idx < kTcM * kpad; idx += blockDim.x) {
       const int i = idx % kTcM, k = idx / kTcM;
@@ -792,7 +921,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     for (int cb = 0; cb < u.seglen; cb += kTcN) {
       const int ncol = min(kTcN, u.seglen - cb);
       const int npad = kTcN;  // the MMA always spans the full accumulator width; unused B rows are zero
-      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = Rs[u.seg0 + cb + j];
+      for (int j = tid; j < ncol; j += blockDim.x) gcol[j] = fan ? u.seg0 + cb + j : Rs[u.seg0 + cb + j];
       for (int idx = tid; idx < npad * kpad; idx += blockDim.x) {
         const int j = idx % npad, k = idx / npad;
         const float v = (j < ncol && k < ws) ? ldcg(Ps + (u.seg0 + cb + j) + (size_t)k * lds) : 0.f;
@@ -849,7 +978,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
           for (int q = 0; q < 16; ++q) {
             const int j = c0 + q;
             if (j < ncol && grow[row] >= gcol[j])
-              atomicAdd(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -__uint_as_float(v[q]));
+              scatter_put(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -__uint_as_float(v[q]), fan);
           }
         }
       }
@@ -920,14 +1049,16 @@ __device__ __forceinline__ uint32_t bf16_idesc(int m, int n) {
   return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+template <bool FAN>
 __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char* smraw, FactorShared& sh, bool skip,
-                               TcState& tc, bool release = true) {
+                               TcState& tc, long long fo, bool release = true) {
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   const int s = u.s, t = u.t;
   if (!skip) {
     const int fs = a.pv.fcol[s], ws = a.pv.fcol[s + 1] - fs, rs = a.pv.nrows[s];
-    const int ft = a.pv.fcol[t], ldt = a.pv.ld[t], rt = a.pv.nrows[t];
-    double* Pt = reinterpret_cast<double*>(a.pool) + a.pv.valoff[t];
+    constexpr bool fan = FAN;  // fan-in mode: the tile's buffer at fo (see load_relpos)
+    const int ft = fan ? u.seg0 : a.pv.fcol[t], ldt = fan ? u.rowlen : a.pv.ld[t];
+    double* Pt = fan ? reinterpret_cast<double*>(a.fan_buf) + fo : reinterpret_cast<double*>(a.pool) + a.pv.valoff[t];
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
     const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
     const int32_t* ex = a.rexp + a.pv.rowoff[s];
@@ -944,7 +1075,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     const uint32_t sbo = (uint32_t)kpad * 16;  // 8 rows x (kpad bf16) bytes
     const int chunks = kpad / 8;               // 16-byte chunks per row
 
-    load_relpos(a, u, pos, grow, Rs);
+    load_relpos(a, u, pos, grow, Rs, fan);
     for (int i = tid; i < u.rowlen; i += blockDim.x) ea[i] = ldcg(ex + u.row0 + i);
     // A digits: kSlices x rowlen rows x kpad, K-major core matrices (8 rows x
     // 16 bytes).  Rows past rowlen are left as they are: they only feed rows
@@ -963,7 +1094,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     for (int cb = 0; cb < u.seglen; cb += kOzN) {
       const int ncol = min(kOzN, u.seglen - cb);
       for (int j = tid; j < ncol; j += blockDim.x) {
-        gcol[j] = Rs[u.seg0 + cb + j];
+        gcol[j] = fan ? u.seg0 + cb + j : Rs[u.seg0 + cb + j];
         eb[j] = ldcg(ex + u.seg0 + cb + j);
       }
       for (int idx = tid; idx < kSlices * ncol * chunks; idx += blockDim.x) {
@@ -1039,7 +1170,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
                 for (int d = 3; d < kSlices; ++d) lo = lo * 256 + __float2int_rn(__uint_as_float(v[d][q]));
                 const long long t12 = hi * (1ll << 20) + (lo >> 12);  // floor((hi 2^32 + lo) / 2^12)
                 const double c = fixed64_to_double(t12, ea[row] + eb[j] - 52);
-                red_add(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -c);
+                scatter_put(Pt + pos[row] + (size_t)(gcol[j] - ft) * ldt, -c, fan);
               }
             }
           }
@@ -1066,7 +1197,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // four).  The TF32 mode runs two CTAs per SM and the BF16-split mode three, as
 // their operand tiles' shared memory allows (a BF16-split CTA holds 128 of the
 // SM's 512 TMEM columns).
-template <typename T, int MODE>
+template <typename T, int MODE, bool FAN>
 __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 : sizeof(T) == 4 ? 6 : 5)
     factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1230,6 +1361,17 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
     const int kind = step_kind, s = step_s, si = step_i;
     const bool release = step_release != 0;
     int type;
+    if (FAN && !skip && kind <= 1) {
+      // fan-in mode: the buffered updates of the rows this diagonal or
+      // panel-solve task factors or solves, first
+      const int w = a.pv.fcol[s + 1] - a.pv.fcol[s], tr = a.trsm_rows_of[s];
+      const int r0 = kind == 0 ? 0 : w + si * tr;
+      const int r1 = kind == 0 ? w : min(a.pv.nrows[s], r0 + tr);
+      const int pc0 = a.fan_task[kind == 0 ? s : a.pv.ns + a.trsm_first[s] + si];
+      for (int m = 0; r0 + m * kFanPieceRows < r1; ++m)
+        fanin_gather<T>(a, s, pc0 + m, r0 + m * kFanPieceRows, min(kFanPieceRows, r1 - r0 - m * kFanPieceRows),
+                        smem_raw);
+    }
     if (kind == 0) {
       type = 0;
       task_potrf<T>(a, s, smd, sh, skip, release);
@@ -1240,17 +1382,18 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
       type = 2;
       const int ui = kind == 2 ? a.u_first[s] + si : si;
       const UTask u = a.ut[ui];
+      const long long fo = FAN ? (long long)a.fan_off[ui] : -1ll;  // fan-in: the tile's buffer
       if constexpr (MODE == 3) {
         if (a.pv.fcol[u.s + 1] - a.pv.fcol[u.s] >= a.tc_min_width) {
           type = 3;
-          task_update_oz(a, u, smem_raw, sh, skip, tc, release);
+          task_update_oz<FAN>(a, u, smem_raw, sh, skip, tc, fo, release);
         } else {
-          task_update<T>(a, u, smem_raw, sh, skip, ui & 7, utma, release);
+          task_update<T, FAN>(a, u, smem_raw, sh, skip, ui & 7, utma, fo, release);
         }
       } else if constexpr (MODE == 1) {
-        task_update_tc(a, u, smem_raw, sh, skip, tc, release);
+        task_update_tc<FAN>(a, u, smem_raw, sh, skip, tc, fo, release);
       } else {
-        task_update<T>(a, u, smem_raw, sh, skip, ui & 7, utma, release);
+        task_update<T, FAN>(a, u, smem_raw, sh, skip, ui & 7, utma, fo, release);
       }
       // deterministic order: the next tile into the same target may start
       // (the tile's scatter-adds were published before its own release)
@@ -1331,13 +1474,28 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
   return tri > upd ? tri : upd;
 }
 
-static const void* factor_fn(bool fp32, int mma_mode) {
-  if (fp32) return mma_mode == 0 ? (const void*)factor_kernel<float, 0> : (const void*)factor_kernel<float, 1>;
-  return mma_mode == 3 ? (const void*)factor_kernel<double, 3> : (const void*)factor_kernel<double, 0>;
+size_t fanin_smem_bytes(int max_w, bool fp32, int* cap) {
+  const size_t es = fp32 ? sizeof(float) : sizeof(double);
+  const int c = (std::max(2048, kFanPieceRows * max_w) + 7) & ~7;
+  if (cap) *cap = c;
+  return 16 + kFanMetaBytes + (size_t)c * (sizeof(int16_t) + es) + (size_t)kFanPieceRows * max_w * es;
 }
 
-cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_per_sm) {
-  const void* fn = factor_fn(fp32, mma_mode);
+// The fan-in mode has kernels of its own, so that the other modes' update
+// tiles and dispatch carry none of its code.
+template <bool FAN>
+static const void* factor_fn_of(bool fp32, int mma_mode) {
+  if (fp32)
+    return mma_mode == 0 ? (const void*)factor_kernel<float, 0, FAN> : (const void*)factor_kernel<float, 1, FAN>;
+  return mma_mode == 3 ? (const void*)factor_kernel<double, 3, FAN> : (const void*)factor_kernel<double, 0, FAN>;
+}
+
+static const void* factor_fn(bool fp32, int mma_mode, bool fan) {
+  return fan ? factor_fn_of<true>(fp32, mma_mode) : factor_fn_of<false>(fp32, mma_mode);
+}
+
+cudaError_t factor_configure(bool fp32, int mma_mode, bool fan, size_t smem, int* blocks_per_sm) {
+  const void* fn = factor_fn(fp32, mma_mode, fan);
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kFactorThreads, smem);
@@ -1387,15 +1545,9 @@ cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest
 }
 
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st) {
-  if (fp32 && a.mma_mode == 0)
-    factor_kernel<float, 0><<<grid, kFactorThreads, smem, st>>>(a);
-  else if (fp32)
-    factor_kernel<float, 1><<<grid, kFactorThreads, smem, st>>>(a);
-  else if (a.mma_mode == 3)
-    factor_kernel<double, 3><<<grid, kFactorThreads, smem, st>>>(a);
-  else
-    factor_kernel<double, 0><<<grid, kFactorThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  void* args[] = {const_cast<FactorArgs*>(&a)};
+  return cudaLaunchKernel(factor_fn(fp32, a.mma_mode, a.fan_ptr != nullptr), dim3(grid), dim3(kFactorThreads), args,
+                          smem, st);
 }
 
 }  // namespace spchol

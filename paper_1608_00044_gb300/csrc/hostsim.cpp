@@ -53,14 +53,51 @@ struct Ready {
 struct Sim {
   const Plan& P;
   std::vector<double> pool;
+  std::vector<double> fan;  // fan-in mode: the update tiles' private buffers
   int info = 0;
-  explicit Sim(const Plan& p) : P(p), pool((size_t)p.valoff[p.ns], 0.0) {}
+  explicit Sim(const Plan& p)
+      : P(p), pool((size_t)p.valoff[p.ns], 0.0), fan(p.fan_off.empty() ? 0 : (size_t)p.fan_off.back(), 0.0) {}
   double* panel(int s) { return pool.data() + P.valoff[s]; }
   int width(int s) const { return P.fcol[s + 1] - P.fcol[s]; }
+
+  // Fan-in mode: add the buffered updates into rows [r0, r1) of panel t, whose
+  // pieces start at piece pc0, in the lists' order.
+  void gather(int t, int pc0, int r0, int r1) {
+    const int ft = P.fcol[t], ldt = P.ld[t], rt = P.nrows[t];
+    const int32_t* Rt = P.rows.data() + P.rowoff[t];
+    double* T = panel(t);
+    for (int pc = pc0, p0 = r0; p0 < r1; ++pc, p0 += kFanPieceRows) {
+      const int p1 = std::min(r1, p0 + kFanPieceRows);
+      for (int64_t e = P.fan_ptr[pc]; e < P.fan_ptr[pc + 1]; ++e) {
+        const FanEnt& fe = P.fan_ent[e];
+        const UTask& u = P.ut[fe.u];
+        const int32_t* Rs = P.rows.data() + P.rowoff[u.s];
+        const double* F = fan.data() + P.fan_off[fe.u];
+        if (u.t != t || fe.i0 < 0 || fe.i0 >= fe.i1 || fe.i1 > u.rowlen) {
+          info = -1;  // inconsistent list
+          return;
+        }
+        for (int i = fe.i0; i < fe.i1; ++i) {
+          const int gi = Rs[u.row0 + i];
+          const int pos = (int)(std::lower_bound(Rt, Rt + rt, gi) - Rt);
+          if (pos < p0 || pos >= p1 || Rt[pos] != gi) {
+            info = -1;  // the row is not in this piece
+            return;
+          }
+          for (int j = 0; j < u.seglen; ++j) {
+            const int gj = Rs[u.seg0 + j];
+            if (gi >= gj) T[pos + (size_t)(gj - ft) * ldt] += F[i + (size_t)j * u.rowlen];
+          }
+        }
+      }
+    }
+  }
 
   void potrf(int s) {
     const int w = width(s), ld = P.ld[s], f = P.fcol[s];
     double* A = panel(s);
+    if (P.params.fanin) gather(s, P.fan_task[s], 0, w);
+    if (info != 0) return;
     for (int j = 0; j < w; ++j) {
       double d = A[j + (size_t)j * ld];
       if (!(d > 0.0)) {
@@ -78,6 +115,8 @@ struct Sim {
     const int w = width(s), ld = P.ld[s], r = P.nrows[s];
     const int row0 = w + k * P.trsm_rows[s], cnt = std::min(P.trsm_rows[s], r - row0);
     double* A = panel(s);
+    if (P.params.fanin) gather(s, P.fan_task[P.ns + P.trsm_first[s] + k], row0, row0 + cnt);
+    if (info != 0) return;
     for (int i = row0; i < row0 + cnt; ++i)
       for (int j = 0; j < w; ++j) {
         double x = A[i + (size_t)j * ld];
@@ -85,7 +124,8 @@ struct Sim {
         A[i + (size_t)j * ld] = x / A[j + (size_t)j * ld];
       }
   }
-  void update(const UTask& u) {
+  void update(const UTask& u, int ui) {
+    double* F = P.params.fanin ? fan.data() + P.fan_off[ui] : nullptr;
     const int ws = width(u.s), lds = P.ld[u.s], ldt = P.ld[u.t], ft = P.fcol[u.t], rt = P.nrows[u.t];
     const int32_t* Rs = P.rows.data() + P.rowoff[u.s];
     const int32_t* Rt = P.rows.data() + P.rowoff[u.t];
@@ -103,7 +143,10 @@ struct Sim {
         if (gi < gj) continue;
         double c = 0.0;
         for (int k = 0; k < ws; ++k) c += S[(u.row0 + i) + (size_t)k * lds] * S[(u.seg0 + j) + (size_t)k * lds];
-        T[pos + (size_t)(gj - ft) * ldt] -= c;
+        if (F)
+          F[i + (size_t)j * u.rowlen] = -c;  // fan-in: the tile's private buffer
+        else
+          T[pos + (size_t)(gj - ft) * ldt] -= c;
       }
     }
   }
@@ -149,6 +192,10 @@ int64_t spchol_plan_len(spchol_plan_t p, int what) {
     case SPCHOL_PLAN_SCALARS: return 12;
     case SPCHOL_PLAN_SUBLO: case SPCHOL_PLAN_SUBHI: return (int64_t)P.sub_lo.size();
     case SPCHOL_PLAN_ADEST: return (int64_t)P.a_dest.size();
+    case SPCHOL_PLAN_FANOFF: return (int64_t)P.fan_off.size();
+    case SPCHOL_PLAN_FANTASK: return (int64_t)P.fan_task.size();
+    case SPCHOL_PLAN_FANPTR: return (int64_t)P.fan_ptr.size();
+    case SPCHOL_PLAN_FANENT: return 3 * (int64_t)P.fan_ent.size();
     default: return -1;
   }
 }
@@ -177,6 +224,16 @@ int spchol_plan_get(spchol_plan_t p, int what, int64_t* dst) {
     case SPCHOL_PLAN_SUBLO: cp(P.sub_lo); break;
     case SPCHOL_PLAN_SUBHI: cp(P.sub_hi); break;
     case SPCHOL_PLAN_ADEST: cp(P.a_dest); break;
+    case SPCHOL_PLAN_FANOFF: cp(P.fan_off); break;
+    case SPCHOL_PLAN_FANTASK: cp(P.fan_task); break;
+    case SPCHOL_PLAN_FANPTR: cp(P.fan_ptr); break;
+    case SPCHOL_PLAN_FANENT:
+      for (size_t i = 0; i < P.fan_ent.size(); ++i) {
+        dst[3 * i] = P.fan_ent[i].u;
+        dst[3 * i + 1] = P.fan_ent[i].i0;
+        dst[3 * i + 2] = P.fan_ent[i].i1;
+      }
+      break;
     case SPCHOL_PLAN_UTASKS:
       for (size_t i = 0; i < P.ut.size(); ++i) {
         const UTask& u = P.ut[i];
@@ -214,8 +271,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   // update tiles of each panel).  Every push is counted against its ring's
   // size, and each ring must receive exactly as many tasks as it holds.
   std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
-  // deterministic order: update tiles chained per target (Plan::u_next)
-  const bool det = !P.u_next.empty();
+  // deterministic order: update tiles chained per target (Plan::u_next; not
+  // in the fan-in mode, whose tiles need no order) and the solve chains
+  const bool uchain = !P.u_next.empty();
+  const bool det = P.params.deterministic;
   std::vector<int> udep(P.u_dep0.begin(), P.u_dep0.end());
   const int u0 = ns + P.n_trsm;  // first update tile id
   std::vector<char> ran(P.n_task_ids, 0);
@@ -254,7 +313,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           if (sim.info == 0) sim.trsm(s, kt);
         for (int j = 0; j < P.nu[s]; ++j) {
           const UTask& u = P.ut[P.u_first[s] + j];
-          if (sim.info == 0) sim.update(u);
+          if (sim.info == 0) sim.update(u, P.u_first[s] + j);
           if (u.t > hi) {
             if (P.in_sub[u.t] >= 0) return SPCHOL_EINTERNAL;  // an outside target is never in another subtree
             if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
@@ -274,7 +333,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       if (tleft[s] == 0)
         for (int k = 0; k < P.nu[s]; ++k) {
           const int u = P.u_first[s] + k;
-          if (det && --udep[u] != 0) {
+          if (uchain && --udep[u] != 0) {
             if (udep[u] < 0) return SPCHOL_EINTERNAL;
             continue;  // waits for its predecessor into the same target
           }
@@ -284,10 +343,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       const int ui = task - u0;
       const UTask& u = P.ut[ui];
       if (P.in_sub[u.s] >= 0) return SPCHOL_EINTERNAL;
-      if (!skip) sim.update(u);
+      if (!skip) sim.update(u, ui);
       if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
       if (dep[u.t] == 0) push(true, u.t);
-      if (det && P.u_next[ui] >= 0) {
+      if (uchain && P.u_next[ui] >= 0) {
         const int nx = P.u_next[ui], sx = P.ut[nx].s;
         if (--udep[nx] < 0) return SPCHOL_EINTERNAL;
         if (udep[nx] == 0) push(nx - P.u_first[sx] < P.nu_hi[sx], u0 + nx);

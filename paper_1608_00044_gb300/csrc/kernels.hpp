@@ -58,6 +58,16 @@ struct FactorArgs {
   // panel-solve tiles + its predecessor)
   const int32_t* u_next;
   int32_t* u_dep;
+  // fan-in mode (null otherwise, see Plan::fan_ptr): the update tiles' private
+  // buffers (panel type), each tile's offset in them, the first piece of each
+  // diagonal / panel-solve task, the pieces' gather lists, and how many values
+  // one gather batch stages in shared memory
+  void* fan_buf;
+  const int64_t* fan_off;
+  const int32_t* fan_task;
+  const int64_t* fan_ptr;
+  const FanEnt* fan_ent;
+  int32_t fan_cap;
   int* ring;
   int* ctrl;
   int64_t budget_ns;
@@ -110,7 +120,10 @@ struct SolveArgs {
 
 // factor.cu
 size_t factor_smem_bytes(int max_w, int mma_mode);
-cudaError_t factor_configure(bool fp32, int mma_mode, size_t smem, int* blocks_per_sm);
+// Fan-in mode: shared memory a gather needs for panels up to max_w wide, and
+// the values it stages per batch (*cap).
+size_t fanin_smem_bytes(int max_w, bool fp32, int* cap);
+cudaError_t factor_configure(bool fp32, int mma_mode, bool fanin, size_t smem, int* blocks_per_sm);
 cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz,
                             void* pool, cudaStream_t st);
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st);

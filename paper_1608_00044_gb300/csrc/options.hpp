@@ -34,7 +34,7 @@ inline bool options_valid(const spchol_options& o) {
          o.max_width <= (tc ? 64 : 128) &&
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
          o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 && o.deterministic >= 0 &&
-         o.deterministic <= 1 &&
+         o.deterministic <= 2 &&
          o.profile >= 0 && o.profile <= 2;
 }
 
@@ -56,6 +56,7 @@ inline PlanParams params_from(const spchol_options& o) {
   p.solve_rows = kSolveTileRows;
   if (o.deterministic) {
     p.deterministic = true;
+    p.fanin = o.deterministic == 2;
     p.subtree_flops = 0.0;
   }
   return p;

@@ -45,6 +45,20 @@ struct PlanParams {
   // Deterministic order (the static (target, source) order of Section IV-B):
   // see Plan::u_next.  Subtree tasks are off in this mode.
   bool deterministic = false;
+  // Deterministic by fan-in aggregation (the fan-in family of Section II-C, restated
+  // for one GPU) instead of the chains: see Plan::fan_ptr.  Implies
+  // deterministic (the solves keep their chains).
+  bool fanin = false;
+};
+
+// Rows of a target panel are gathered in pieces of at most this many rows.
+constexpr int kFanPieceRows = 32;
+
+// One entry of a fan-in gather list: rows [i0, i1) of update tile u fall in the
+// piece that owns the list.
+struct FanEnt {
+  int32_t u;
+  int16_t i0, i1;
 };
 
 struct Plan {
@@ -118,6 +132,24 @@ struct Plan {
   // backward tiles of a panel, which all subtract from that panel's entries,
   // chain in tile order (bdep0 counts the predecessor).
   std::vector<int32_t> u_next, u_dep0, ft_sptr, ft_succ, ft_dep0;
+
+  // Fan-in aggregation (params.fanin; empty otherwise).  Update tile u stores
+  // its product, negated, densely (column-major, rowlen rows, seglen columns,
+  // lower entries only) at fan_off[u] of a private buffer instead of adding
+  // it into the target.  The rows of each target panel are split into pieces:
+  // the diagonal block in steps of kFanPieceRows rows, then each panel-solve
+  // tile's rows in such steps.  fan_task[k] (k < ns: the diagonal task of
+  // panel k; k >= ns: panel-solve tile k - ns) is the first piece of that
+  // task's rows, whose pieces are consecutive; fan_ptr / fan_ent list, for
+  // every piece in update-tile order, the tiles with rows in it and which.
+  // The task that owns a piece adds those buffers into its rows in list
+  // order before it factors or solves them, so every entry of L receives
+  // its updates in one fixed order, and the update tiles themselves need no
+  // order among them.
+  std::vector<int64_t> fan_off;   // n_u + 1
+  std::vector<int32_t> fan_task;  // ns + n_trsm
+  std::vector<int64_t> fan_ptr;   // pieces + 1
+  std::vector<FanEnt> fan_ent;
 
   PlanParams params;
 };

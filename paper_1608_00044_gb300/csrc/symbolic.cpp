@@ -373,7 +373,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.n_u = (int32_t)P.ut.size();
   P.u_next.clear();
   P.u_dep0.clear();
-  if (prm.deterministic) {
+  if (prm.deterministic && !prm.fanin) {
     // tiles are numbered by source panel, then by target, then by row tile:
     // in that order each target's tiles form its chain
     P.u_next.assign(P.n_u, -1);
@@ -387,6 +387,71 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       }
       last[t] = u;
     }
+  }
+
+  // ---- fan-in gather lists (see Plan::fan_ptr) ---------------------------------
+  P.fan_off.clear();
+  P.fan_task.clear();
+  P.fan_ptr.clear();
+  P.fan_ent.clear();
+  if (prm.fanin) {
+    P.fan_off.assign((size_t)P.n_u + 1, 0);
+    for (int32_t u = 0; u < P.n_u; ++u)
+      P.fan_off[u + 1] = P.fan_off[u] + (int64_t)P.ut[u].rowlen * P.ut[u].seglen;
+    auto npieces = [](int32_t rows) { return (rows + kFanPieceRows - 1) / kFanPieceRows; };
+    P.fan_task.assign((size_t)ns + P.n_trsm, 0);
+    int32_t npc = 0;
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s], tr = P.trsm_rows[s];
+      P.fan_task[s] = npc;
+      npc += npieces(w);
+      for (int32_t k = 0; k < P.ntrsm[s]; ++k) {
+        P.fan_task[ns + P.trsm_first[s] + k] = npc;
+        npc += npieces(std::min(tr, r - w - k * tr));
+      }
+    }
+    // the piece holding row position p of panel t, and the first position past it
+    auto piece_of = [&](int32_t t, int32_t p, int32_t& end) -> int32_t {
+      const int32_t w = P.fcol[t + 1] - P.fcol[t], r = P.nrows[t], tr = P.trsm_rows[t];
+      if (p < w) {
+        const int32_t m = p / kFanPieceRows;
+        end = std::min(w, (m + 1) * kFanPieceRows);
+        return P.fan_task[t] + m;
+      }
+      const int32_t k = (p - w) / tr, b0 = w + k * tr, m = (p - b0) / kFanPieceRows;
+      end = std::min(std::min(r, b0 + tr), b0 + (m + 1) * kFanPieceRows);
+      return P.fan_task[ns + P.trsm_first[t] + k] + m;
+    };
+    struct Item {
+      int32_t pc;
+      FanEnt e;
+    };
+    std::vector<Item> items;
+    items.reserve((size_t)P.n_u * 2);
+    for (int32_t u = 0; u < P.n_u; ++u) {
+      const UTask& U = P.ut[u];
+      const int32_t* Rs = P.rows.data() + P.rowoff[U.s] + U.row0;
+      const int32_t* Rt = P.rows.data() + P.rowoff[U.t];
+      const int32_t rt = P.nrows[U.t];
+      for (int32_t i = 0; i < U.rowlen;) {
+        // a tile's rows are rows of its target (the structure of L is closed
+        // under updates), so the search finds each exactly
+        const int32_t p = (int32_t)(std::lower_bound(Rt, Rt + rt, Rs[i]) - Rt);
+        int32_t end = 0;
+        const int32_t pc = piece_of(U.t, p, end);
+        const int32_t i1 =
+            end >= rt ? U.rowlen : (int32_t)(std::lower_bound(Rs + i, Rs + U.rowlen, Rt[end]) - Rs);
+        items.push_back(Item{pc, FanEnt{u, (int16_t)i, (int16_t)i1}});
+        i = i1;
+      }
+    }
+    // a stable counting sort by piece keeps each list in update-tile order
+    P.fan_ptr.assign((size_t)npc + 1, 0);
+    for (const Item& it : items) P.fan_ptr[it.pc + 1]++;
+    for (int32_t k = 0; k < npc; ++k) P.fan_ptr[k + 1] += P.fan_ptr[k];
+    P.fan_ent.resize(items.size());
+    std::vector<int64_t> fill(P.fan_ptr.begin(), P.fan_ptr.end() - 1);
+    for (const Item& it : items) P.fan_ent[fill[it.pc]++] = it.e;
   }
 
   // ---- subtree tasks ------------------------------------------------------------

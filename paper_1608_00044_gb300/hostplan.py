@@ -13,7 +13,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 HOST_LIB_PATH = os.path.join(_HERE, "libspchol_host.so")
 
 (PERM, COLCOUNT, ETREE, FCOL, NROWS, ROWOFF, ROWS, PARENT, DEPF, NTRSM, NU, UTASKS, NST, SCALARS, ADEST, NUHI, SUBLO,
- SUBHI) = range(18)
+ SUBHI, FANOFF, FANTASK, FANPTR, FANENT) = range(22)
 
 _vp = ctypes.c_void_p
 SIGNATURES = [

@@ -231,6 +231,101 @@ def test_deterministic_mode_is_bitwise_reproducible(precision):
             assert np.array_equal(Lx, runs[0][1])
 
 
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "TF32", "FP64_TC"])
+def test_fanin_mode_is_bitwise_reproducible(precision):
+    """options.deterministic = 2 (fan-in aggregation, the fan-in family of
+    Section II-C): every update tile stores its product in a private buffer
+    and each panel adds the buffers into its rows in one fixed order, so the
+    factor and the solution are bitwise equal across runs and launch
+    geometries, with the mode's backward error, and the FP64 factors agree
+    with the oracle's."""
+    A, perm, _ = gridgen.workload("diff3d_12")
+    B = gridgen.rhs_uniform(A.n, 3, seed=8)
+    prec = getattr(spchol, precision)
+    fp64 = precision in ("FP64", "FP64_TC")
+    runs = []
+    for cps in (0, 1, 0):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=2, ctas_per_sm=cps, precision=prec)
+        assert rc == 0
+        assert oracle.berr(A, X, B) <= (BERR_FP64 if fp64 else 1e-12)
+        Lx = None
+        if fp64:
+            d, lmax = l_max_diff(h, A)
+            assert d <= 1e-11 * lmax, (d, lmax)
+            Lx = spchol.export_factor(h)[2]
+        runs.append((X, Lx))
+        spchol.destroy(h)
+    for X, Lx in runs[1:]:
+        assert np.array_equal(X, runs[0][0])
+        if Lx is not None:
+            assert np.array_equal(Lx, runs[0][1])
+
+
+@pytest.mark.parametrize("name,W", [("lap2d_64", 64), ("lap3d_16", 64), ("diff3d_10", 128), ("diff3d_12", 7)])
+def test_fanin_mode_matches_oracle(name, W):
+    """Fan-in mode on panels of several widths (one row piece or several in
+    the diagonal block, tall and short panel-solve tiles)."""
+    A, perm, _ = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 2, seed=5)
+    _check(A, perm, B, deterministic=2, max_width=W)
+
+
+@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+def test_fanin_reproduces_the_static_order_bitwise(precision):
+    """Fan-in aggregation adds each entry's updates in update-tile order, the
+    order of the static (target, source) chains: modes 2 and 1 give bitwise
+    the same solution (and, in FP64, the same factor)."""
+    A, perm, _ = gridgen.workload("diff3d_12")
+    B = gridgen.rhs_uniform(A.n, 2, seed=9)
+    prec = getattr(spchol, precision)
+    out = []
+    for det in (1, 2):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=det, precision=prec)
+        assert rc == 0
+        out.append((X, spchol.export_factor(h)[2] if precision == "FP64" else None))
+        spchol.destroy(h)
+    assert np.array_equal(out[0][0], out[1][0])
+    if precision == "FP64":
+        assert np.array_equal(out[0][1], out[1][1])
+
+
+def test_fanin_batch_matches_solo_bitwise():
+    """Fan-in mode: each matrix of a batch gets bitwise the solution it gets
+    alone."""
+    mats = [gridgen.diffusion_2d_5pt(sd, sigma=1.0, seed=80 + i) for i, sd in enumerate((19, 28, 23))]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=90 + i) for i, M in enumerate(mats)]
+    o = spchol.default_options(deterministic=2)
+    hb = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.batch_factorize(hb, [M.values for M in mats]) == 0
+    Xb = [Bi.copy(order="F") for Bi in Bs]
+    spchol.batch_solve(hb, Xb, [M.n for M in mats], [Bi.shape[1] for Bi in Bs])
+    spchol.destroy(hb)
+    for M, p, Bi, Xi in zip(mats, perms, Bs, Xb):
+        rc, X, st, h = gpu_factor_solve(M, p, Bi, deterministic=2)
+        assert rc == 0
+        assert np.array_equal(X, Xi)
+        spchol.destroy(h)
+
+
+def test_fanin_reports_non_spd_column():
+    """Fan-in mode: a matrix that is not positive definite reports the first
+    failing column like the other modes (the gathers of the later panels skip
+    with their tasks)."""
+    A, perm, _ = gridgen.workload("lap3d_12")
+    vals = A.values.copy()
+    diag = A.rowind[A.colptr[:-1]] == np.arange(A.n)
+    assert diag.all()
+    k = perm[A.n // 2]
+    vals[A.colptr[k]] = -1.0
+    B = gridgen.CscLower(A.n, A.colptr, A.rowind, vals)
+    rc_dyn, _, _, h = gpu_factor_solve(B, perm, None)
+    spchol.destroy(h)
+    rc_fan, _, _, h = gpu_factor_solve(B, perm, None, deterministic=2)
+    spchol.destroy(h)
+    assert rc_dyn > 0 and rc_fan == rc_dyn
+
+
 def test_deterministic_batch_matches_solo_bitwise():
     """In deterministic mode each matrix of a batch gets bitwise the solution
     it gets alone."""
