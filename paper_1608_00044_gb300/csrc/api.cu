@@ -85,6 +85,13 @@ struct spchol_handle_s {
   int64_t *d_fan_off = nullptr, *d_fan_ptr = nullptr;
   int32_t* d_fan_task = nullptr;
   FanEnt* d_fan_ent = nullptr;
+  FanRec* d_fan_rec = nullptr;  // the gather's records (a separate allocation)
+  // fan-in solves: Plan::st_zf and friends, and the tiles' buffers for up to
+  // fan_nrhs right-hand sides
+  int64_t *d_st_zf = nullptr, *d_st_zb = nullptr, *d_st_roff = nullptr;
+  int32_t* d_rt_rng = nullptr;
+  double *d_zf = nullptr, *d_zb = nullptr;
+  int fan_nrhs = 0;
   void* d_fan_buf = nullptr;
   size_t fan_buf_bytes = 0;
   int fan_cap = 0;
@@ -253,7 +260,9 @@ int setup_device(spchol_handle_t h) {
   const bool fan = P.params.fanin;
   size_t o_fano = fan ? r64(P.fan_off.size()) : 0, o_fant = fan ? r32(P.fan_task.size()) : 0,
          o_fanp = fan ? r64(P.fan_ptr.size()) : 0,
-         o_fane = fan ? A.reserve(std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanEnt)) : 0;
+         o_fane = fan ? A.reserve(std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanEnt)) : 0,
+         o_stzf = fan ? r64(P.st_zf.size()) : 0, o_stzb = fan ? r64(P.st_zb.size()) : 0,
+         o_stro = fan ? r64(P.st_roff.size()) : 0, o_rtrng = fan ? r32(P.rt_rng.size()) : 0;
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
   size_t o_prof = A.reserve(24 * sizeof(unsigned long long));
@@ -358,6 +367,10 @@ int setup_device(spchol_handle_t h) {
     h->d_fan_task = (int32_t*)(b + o_fant);
     h->d_fan_ptr = (int64_t*)(b + o_fanp);
     h->d_fan_ent = (FanEnt*)(b + o_fane);
+    h->d_st_zf = (int64_t*)(b + o_stzf);
+    h->d_st_zb = (int64_t*)(b + o_stzb);
+    h->d_st_roff = (int64_t*)(b + o_stro);
+    h->d_rt_rng = (int32_t*)(b + o_rtrng);
   }
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
@@ -402,12 +415,17 @@ int setup_device(spchol_handle_t h) {
               (rc = upload(h, h->d_ft_dep0, P.ft_dep0))))
     return rc;
   if (fan && ((rc = upload(h, h->d_fan_off, P.fan_off)) || (rc = upload(h, h->d_fan_task, P.fan_task)) ||
-              (rc = upload(h, h->d_fan_ptr, P.fan_ptr)) || (rc = upload(h, h->d_fan_ent, P.fan_ent))))
+              (rc = upload(h, h->d_fan_ptr, P.fan_ptr)) || (rc = upload(h, h->d_fan_ent, P.fan_ent)) ||
+              (rc = upload(h, h->d_st_zf, P.st_zf)) || (rc = upload(h, h->d_st_zb, P.st_zb)) ||
+              (rc = upload(h, h->d_st_roff, P.st_roff)) || (rc = upload(h, h->d_rt_rng, P.rt_rng))))
     return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   if (fan) {  // never read before written: no initialisation
     h->fan_buf_bytes = std::max<size_t>((size_t)P.fan_off.back() * esz, 256);
     CU(cudaMalloc(&h->d_fan_buf, h->fan_buf_bytes));
+    CU(cudaMalloc(&h->d_fan_rec, std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanRec)));
+    CU(launch_fanrec(h->d_fan_ent, (int64_t)P.fan_ent.size(), h->d_ut, h->d_fan_off, h->d_rowoff, h->d_fan_rec,
+                     g_upload_stream));
   }
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   CU(cudaMalloc(&h->d_pool, h->pool_bytes));
@@ -447,10 +465,10 @@ int setup_device(spchol_handle_t h) {
     h->smem_factor = std::max<size_t>(h->smem_factor, (size_t)smem_sm / 5 + 1024);
   }
   if (fan) h->smem_factor = std::max(h->smem_factor, fanin_smem_bytes(wmax, h->fp32, &h->fan_cap));
-  h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC);
+  h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC, fan);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
-  CU(solve_configure(h->fp32, h->smem_solve, &bs));
+  CU(solve_configure(h->fp32, fan, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
   if (h->opt.ctas_per_sm > 0) {
     bf = std::min(bf, h->opt.ctas_per_sm);
@@ -460,7 +478,8 @@ int setup_device(spchol_handle_t h) {
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
   h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
                                        (size_t)P.n_rel * sizeof(int32_t) + (size_t)P.ns * (h->d_tmaps ? 128 : 0) +
-                                       (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0) + h->fan_buf_bytes);
+                                       (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0) + h->fan_buf_bytes +
+                                       (h->d_fan_rec ? P.fan_ent.size() * sizeof(FanRec) : 0));
   h->stats.grid_factor = h->grid_factor;
   h->stats.grid_solve = h->grid_solve;
   h->stats.tma_staging = h->d_tmaps != nullptr ? 1 : 0;
@@ -468,6 +487,17 @@ int setup_device(spchol_handle_t h) {
 }
 
 int ensure_workspace(spchol_handle_t h, int64_t need, int nrhs) {
+  if (h->plan.params.fanin && nrhs > h->fan_nrhs) {  // the fan-in solves' tile buffers
+    for (double** p : {&h->d_zf, &h->d_zb})
+      if (*p) {
+        cudaFree(*p);
+        *p = nullptr;
+      }
+    h->fan_nrhs = 0;
+    CU(cudaMalloc(&h->d_zf, std::max<size_t>((size_t)h->plan.st_zf.back() * nrhs, 1) * sizeof(double)));
+    CU(cudaMalloc(&h->d_zb, std::max<size_t>((size_t)h->plan.st_zb.back() * nrhs, 1) * sizeof(double)));
+    h->fan_nrhs = nrhs;
+  }
   if (need > h->y_cap) {
     for (double** p : {&h->d_Y, &h->d_B, &h->d_X, &h->d_R})
       if (*p) {
@@ -585,7 +615,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
     a.fan_off = h->d_fan_off;
     a.fan_task = h->d_fan_task;
     a.fan_ptr = h->d_fan_ptr;
-    a.fan_ent = h->d_fan_ent;
+    a.fan_rec = h->d_fan_rec;
     a.fan_cap = h->fan_cap;
   }
   a.ring = h->d_ring;
@@ -676,11 +706,20 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.bdep = h->d_bdep;
   a.ftiles = h->d_ftiles;
   a.btiles = h->d_btiles;
-  if (P.params.deterministic && P.n_st > 0) {
+  if (P.params.deterministic && !P.params.fanin && P.n_st > 0) {
     CU(cudaMemcpyAsync(h->d_ftdep, h->d_ft_dep0, (size_t)P.n_st * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
     a.ft_sptr = h->d_ft_sptr;
     a.ft_succ = h->d_ft_succ;
     a.ftdep = h->d_ftdep;
+  }
+  if (P.params.fanin) {
+    if (nrhs > h->fan_nrhs) return SPCHOL_EINTERNAL;  // the caller sizes the workspace first
+    a.zf = h->d_zf;
+    a.zb = h->d_zb;
+    a.st_zf = h->d_st_zf;
+    a.st_zb = h->d_st_zb;
+    a.st_roff = h->d_st_roff;
+    a.rt_rng = h->d_rt_rng;
   }
   a.ring = h->d_ring;
   a.ctrl = h->d_ctrl;
@@ -1057,9 +1096,13 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   const size_t ring_bytes = up((size_t)P.n_solve_tasks * sizeof(int));
   const size_t cnt_bytes = up((size_t)P.ns * sizeof(int32_t));
   const size_t tile_bytes = up((size_t)P.n_st * sizeof(int32_t));
-  const bool det = P.params.deterministic && P.n_st > 0;
-  const size_t need =
-      y_bytes + ring_bytes + 3 * cnt_bytes + (det ? 2 : 1) * tile_bytes + up(kCtrlWords * sizeof(int));
+  const bool fan = P.params.fanin && P.n_st > 0;
+  const bool det = P.params.deterministic && !fan && P.n_st > 0;
+  // fan-in mode: the tiles' forward and backward buffers follow
+  const size_t zf_bytes = fan ? up((size_t)P.st_zf.back() * nrhs * sizeof(double)) : 0;
+  const size_t zb_bytes = fan ? up((size_t)P.st_zb.back() * nrhs * sizeof(double)) : 0;
+  const size_t need = y_bytes + ring_bytes + 3 * cnt_bytes + (det ? 2 : 1) * tile_bytes +
+                      up(kCtrlWords * sizeof(int)) + zf_bytes + zb_bytes;
   if (need > kNoallocScratchBytes) return SPCHOL_ESCRATCH;
   void* base = nullptr;
   CU(noalloc_scratch(h->device, &base));
@@ -1072,6 +1115,8 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   int32_t* bdep = (int32_t*)((char*)btiles + cnt_bytes);
   int* ctrl = (int*)((char*)bdep + tile_bytes);
   int32_t* ftdep = det ? (int32_t*)((char*)ctrl + up(kCtrlWords * sizeof(int))) : nullptr;
+  double* zf = fan ? (double*)((char*)ctrl + up(kCtrlWords * sizeof(int))) : nullptr;
+  double* zb = fan ? (double*)((char*)zf + zf_bytes) : nullptr;
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the reset kernel re-initialises
   // the ring, the counters and the control words before every launch
@@ -1103,6 +1148,14 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
     a.ft_sptr = h->d_ft_sptr;
     a.ft_succ = h->d_ft_succ;
     a.ftdep = ftdep;
+  }
+  if (fan) {
+    a.zf = zf;
+    a.zb = zb;
+    a.st_zf = h->d_st_zf;
+    a.st_zb = h->d_st_zb;
+    a.st_roff = h->d_st_roff;
+    a.rt_rng = h->d_rt_rng;
   }
   a.ring = ring;
   a.ctrl = ctrl;
@@ -1199,6 +1252,7 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->arena.base) cudaFree(h->arena.base);
   if (h->d_pool) cudaFree(h->d_pool);
   if (h->d_fan_buf) cudaFree(h->d_fan_buf);
+  if (h->d_fan_rec) cudaFree(h->d_fan_rec);
   if (h->d_inv) cudaFree(h->d_inv);
   if (h->d_relpos) cudaFree(h->d_relpos);
   if (h->d_tmaps) cudaFree(h->d_tmaps);
@@ -1206,6 +1260,8 @@ int spchol_destroy(spchol_handle_t h) {
   if (h->d_trace_f) cudaFree(h->d_trace_f);
   if (h->d_trace_s) cudaFree(h->d_trace_s);
   if (h->d_Y) cudaFree(h->d_Y);
+  if (h->d_zf) cudaFree(h->d_zf);
+  if (h->d_zb) cudaFree(h->d_zb);
   if (h->d_B) cudaFree(h->d_B);
   if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
   if (h->h_prof) cudaFreeHost(h->h_prof);

@@ -86,122 +86,6 @@ __device__ __forceinline__ double pivot_recip(double d) {
   return 1.0 / d;
 }
 
-// ---------------------------------------------------------------- fan-in gather
-// Deterministic fan-in mode (the fan-in family of Section II-C, restated for
-// one GPU): update tiles store their products in private buffers, and the task
-// that owns a piece of a target panel's rows (at most kFanPieceRows rows, all
-// columns) adds them in before it factors or solves those rows, tile after
-// tile in the piece's list order, so every entry of L receives its updates in
-// one fixed order whatever the schedule.  The piece sits in shared memory.  A
-// batch of tiles at a time: warp 0 reads the next list entries and their
-// tiles and cuts the batch where their values would overflow the staging
-// area; all threads then fetch the batch's values and target offsets
-// (independent loads, many in flight); the values are added tile by tile.
-struct FanMeta {
-  long long fo;   // the tile's buffer offset
-  long long rel;  // its relative row indices
-  long long rs;   // its segment's row numbers (index into the row lists)
-  int rowlen, i0, ni, pre;  // buffer rows; first row and row count in the piece; first staged value
-};
-constexpr int kFanBatch = 32;
-constexpr size_t kFanMetaBytes = kFanBatch * sizeof(FanMeta) + 16;
-
-template <typename T>
-__device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np, unsigned char* smraw) {
-  const int tid = threadIdx.x, nt = blockDim.x;
-  const int ft = a.pv.fcol[t], wt = a.pv.fcol[t + 1] - ft, ldt = a.pv.ld[t];
-  T* Pt = panel_ptr<T>(a, t);
-  const T* F = reinterpret_cast<const T*>(a.fan_buf);
-  const int cap = a.fan_cap;  // a multiple of 8, at least kFanPieceRows x the widest panel
-  unsigned char* base = smraw + ((16u - (smem_addr(smraw) & 15u)) & 15u);
-  FanMeta* meta = reinterpret_cast<FanMeta*>(base);
-  int* scal = reinterpret_cast<int*>(meta + kFanBatch);  // [0] tiles in the batch, [1] their values
-  int16_t* tg = reinterpret_cast<int16_t*>(base + kFanMetaBytes);  // target offset in S, or -1
-  T* Bs = reinterpret_cast<T*>(tg + cap);
-  T* S = Bs + cap;  // the piece: np rows x wt columns, leading dimension kFanPieceRows
-  long long e = a.fan_ptr[pc];
-  const long long e1 = a.fan_ptr[pc + 1];
-  if (e == e1) return;  // nothing lands in these rows
-  for (int idx = tid; idx < np * wt; idx += nt) {
-    const int p = idx % np, c = idx / np;
-    S[p + kFanPieceRows * c] = ldcg(Pt + p0 + p + (size_t)c * ldt);
-  }
-  while (e < e1) {
-    __syncthreads();  // the piece is loaded, or the previous batch is added
-    if (tid < 32) {
-      FanMeta mm{};
-      int n = 0;
-      if (e + tid < e1) {
-        const FanEnt fe = a.fan_ent[e + tid];
-        const UTask u = a.ut[fe.u];
-        mm.fo = a.fan_off[fe.u];
-        mm.rel = u.rel;
-        mm.rs = a.pv.rowoff[u.s] + u.seg0;
-        mm.rowlen = u.rowlen;
-        mm.i0 = fe.i0;
-        mm.ni = fe.i1 - fe.i0;
-        n = mm.ni * u.seglen;
-      }
-      int inc = n;
-#pragma unroll
-      for (int o = 1; o < 32; o <<= 1) {
-        const int y = __shfl_up_sync(0xffffffffu, inc, o);
-        if (tid >= o) inc += y;
-      }
-      // the tiles whose values fit form a prefix; the first one always fits
-      const int nb = max(1, __popc(__ballot_sync(0xffffffffu, n > 0 && inc <= cap)));
-      if (tid < nb) {
-        mm.pre = inc - n;
-        meta[tid] = mm;
-      }
-      if (tid == nb - 1) {
-        scal[0] = nb;
-        scal[1] = inc;
-      }
-    }
-    __syncthreads();
-    const int nb = scal[0];
-    int total = scal[1];
-    if (total > cap) {  // cannot happen for a consistent plan: stage nothing past the area
-      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-      total = 0;
-    }
-    for (int idx = tid; idx < total; idx += nt) {
-      int k = 0;
-#pragma unroll
-      for (int b = kFanBatch / 2; b > 0; b >>= 1)
-        if (k + b < nb && meta[k + b].pre <= idx) k += b;
-      const FanMeta& mk = meta[k];
-      const int le = idx - mk.pre, i = mk.i0 + le % mk.ni, j = le / mk.ni;
-      const int p = __ldg(a.relpos + mk.rel + i) - p0;
-      const int c = __ldg(a.pv.rows + mk.rs + j) - ft;
-      // lower triangle of the target (rows below its diagonal block always are)
-      bool lower = p0 + p >= wt || p0 + p >= c;
-      if (p < 0 || p >= np || c < 0 || c >= wt) {  // outside the piece: an inconsistent plan
-        atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-        lower = false;
-      }
-      tg[idx] = lower ? (int16_t)(p + kFanPieceRows * c) : (int16_t)-1;
-      if (lower) Bs[idx] = ldcg(F + mk.fo + i + (size_t)j * mk.rowlen);
-    }
-    __syncthreads();
-    for (int k = 0; k < nb; ++k) {  // one tile at a time: an entry's updates land in list order
-      const int k0 = meta[k].pre, k1 = k + 1 < nb ? meta[k + 1].pre : total;
-      for (int idx = k0 + tid; idx < k1; idx += nt) {
-        const int g = tg[idx];
-        if (g >= 0) S[g] += Bs[idx];
-      }
-      __syncthreads();
-    }
-    e += nb;
-  }
-  for (int idx = tid; idx < np * wt; idx += nt) {
-    const int p = idx % np, c = idx / np;
-    Pt[p0 + p + (size_t)c * ldt] = S[p + kFanPieceRows * c];
-  }
-  __syncthreads();  // the task reads these rows next, and reuses the shared memory
-}
-
 template <typename T>
 __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip, bool release = true) {
   const int tid = threadIdx.x;
@@ -896,7 +780,6 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     const float* Ps = reinterpret_cast<const float*>(a.pool) + a.pv.valoff[s];
     float* Pt = fan ? reinterpret_cast<float*>(a.fan_buf) + fo : reinterpret_cast<float*>(a.pool) + a.pv.valoff[t];
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
-    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
     const int split = a.mma_mode == 2 ? 1 : 0;
     const int kpad = (ws + 7) & ~7;
     const int abytes = kTcM * kpad * 4, bbytes = kTcN * kpad * 4;
@@ -1060,7 +943,6 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     const int ft = fan ? u.seg0 : a.pv.fcol[t], ldt = fan ? u.rowlen : a.pv.ld[t];
     double* Pt = fan ? reinterpret_cast<double*>(a.fan_buf) + fo : reinterpret_cast<double*>(a.pool) + a.pv.valoff[t];
     const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
-    const int32_t* Rt = a.pv.rows + a.pv.rowoff[t];
     const int32_t* ex = a.rexp + a.pv.rowoff[s];
     const int kpad = (ws + 15) & ~15, nb = rs - ws;
     const uint16_t* sl = a.slices + a.sliceoff[s];
@@ -1186,6 +1068,177 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
       ring2_push_one(rings_of(a), true, t);
     }
   }
+}
+
+// ---------------------------------------------------------------- fan-in gather
+// Deterministic fan-in mode (the fan-in family of Section II-C, restated for
+// one GPU): update tiles store their products in private buffers, and the task
+// that owns a piece of a target panel's rows (at most kFanPieceRows rows, all
+// columns) adds them in before it factors or solves those rows, tile after
+// tile in the piece's list order, so every entry of L receives its updates in
+// one fixed order whatever the schedule.  The piece sits in shared memory and
+// the list is consumed in batches of up to kFanBatch tiles:
+//   1. warp 0 cuts the batch where the tiles' values or their row and column
+//      positions would overflow the staging areas (its records were fetched
+//      during the previous batch);
+//   2. all threads stage the batch's row positions (in the piece) and column
+//      positions (in the panel);
+//   3. all threads fetch the values, kFanInflight loads per thread in flight,
+//      and note each value's place in the piece (-1 above the diagonal);
+//   4. the values are added tile by tile.
+// Values and the piece (written by other CTAs during the factorization) are
+// read around L1 (ld.global.cg); the records were written at analysis.
+struct FanMeta {
+  long long fo, rp, rs;  // FanRec: buffer offset of the first listed row, relative rows, segment rows
+  int pre_e, pre_v;      // first staged value and first staged position of the tile
+  int rowlen;
+  short ni, seglen;
+  float inv_ni;  // 1 / ni: value index -> (row, column) without a division
+};
+constexpr int kFanBatch = 32;
+constexpr int kFanVcap = 1024;    // staged positions per batch (a tile has at most 32 + 128)
+constexpr int kFanInflight = 4;   // value loads in flight per thread
+constexpr size_t kFanMetaBytes = ((kFanBatch * sizeof(FanMeta) + 16) + 15) & ~size_t(15);
+
+// The batch tile that staged value (values) or position (!values) idx belongs to.
+__device__ __forceinline__ int fan_tile_of(const FanMeta* meta, int nb, int idx, bool values) {
+  int k = 0;
+#pragma unroll
+  for (int b = kFanBatch / 2; b > 0; b >>= 1)
+    if (k + b < nb && (values ? meta[k + b].pre_e : meta[k + b].pre_v) <= idx) k += b;
+  return k;
+}
+
+template <typename T>
+__device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np, unsigned char* smraw) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  long long e = a.fan_ptr[pc];
+  const long long e1 = a.fan_ptr[pc + 1];
+  if (e == e1) return;  // nothing lands in these rows
+  const int ft = a.pv.fcol[t], wt = a.pv.fcol[t + 1] - ft, ldt = a.pv.ld[t];
+  T* Pt = panel_ptr<T>(a, t);
+  const T* F = reinterpret_cast<const T*>(a.fan_buf);
+  const int cap = a.fan_cap;  // a multiple of 8, at least kFanPieceRows x the widest panel
+  unsigned char* base = smraw + ((16u - (smem_addr(smraw) & 15u)) & 15u);
+  FanMeta* meta = reinterpret_cast<FanMeta*>(base);
+  int* scal = reinterpret_cast<int*>(meta + kFanBatch);  // tiles, values and positions of the batch
+  int16_t* pv = reinterpret_cast<int16_t*>(base + kFanMetaBytes);  // positions: rows in the piece, then columns
+  int16_t* tg = pv + kFanVcap;                                     // value -> place in the piece, or -1
+  T* Bs = reinterpret_cast<T*>(tg + cap);
+  T* S = Bs + cap;  // the piece: np rows x wt columns, leading dimension kFanPieceRows
+  for (int idx = tid; idx < np * wt; idx += nt) {
+    const int p = idx % np, c = idx / np;
+    S[p + kFanPieceRows * c] = ldcg(Pt + p0 + p + (size_t)c * ldt);
+  }
+  FanRec r{};  // warp 0: the records of the next batch window
+  if (tid < 32 && e + tid < e1) r = a.fan_rec[e + tid];
+  while (e < e1) {
+    __syncthreads();  // the piece is loaded, or the previous batch is added
+    int nb = 0;
+    if (tid < 32) {
+      const bool have = e + tid < e1;
+      const int n = have ? r.ni * r.seglen : 0, v = have ? r.ni + r.seglen : 0;
+      int in = n, iv = v;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, in, o), z = __shfl_up_sync(0xffffffffu, iv, o);
+        if (tid >= o) {
+          in += y;
+          iv += z;
+        }
+      }
+      // the tiles that fit form a prefix; the first one always fits
+      nb = max(1, __popc(__ballot_sync(0xffffffffu, have && in <= cap && iv <= kFanVcap)));
+      if (tid < nb) {
+        FanMeta mm;
+        mm.fo = r.fo;
+        mm.rp = r.rp;
+        mm.rs = r.rs;
+        mm.pre_e = in - n;
+        mm.pre_v = iv - v;
+        mm.rowlen = r.rowlen;
+        mm.ni = r.ni;
+        mm.seglen = r.seglen;
+        mm.inv_ni = 1.0f / (float)max(1, (int)r.ni);
+        meta[tid] = mm;
+      }
+      if (tid == nb - 1) {
+        scal[0] = nb;
+        scal[1] = in;
+        scal[2] = iv;
+      }
+      r = FanRec{};
+      if (e + nb + tid < e1) r = a.fan_rec[e + nb + tid];  // in flight during this batch
+    }
+    __syncthreads();
+    nb = scal[0];
+    int total = scal[1], npos = scal[2];
+    if (total > cap || npos > kFanVcap) {  // cannot happen for a consistent plan
+      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      total = npos = 0;
+    }
+    // 2. row positions in the piece and column positions in the panel
+    for (int idx = tid; idx < npos; idx += nt) {
+      const FanMeta& mk = meta[fan_tile_of(meta, nb, idx, false)];
+      const int lv = idx - mk.pre_v;
+      int q;
+      bool ok;
+      if (lv < mk.ni) {
+        q = __ldg(a.relpos + mk.rp + lv) - p0;
+        ok = q >= 0 && q < np;
+      } else {
+        q = __ldg(a.pv.rows + mk.rs + (lv - mk.ni)) - ft;
+        ok = q >= 0 && q < wt;
+      }
+      if (!ok) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // outside the piece: an inconsistent plan
+      pv[idx] = ok ? (int16_t)q : (int16_t)-1;
+    }
+    __syncthreads();
+    // 3. the values, kFanInflight loads in flight per thread
+    for (int b0 = 0; b0 < total; b0 += kFanInflight * nt) {
+      long long off[kFanInflight];
+      T v[kFanInflight];
+#pragma unroll
+      for (int q = 0; q < kFanInflight; ++q) {
+        const int idx = b0 + q * nt + tid;
+        off[q] = -1;
+        if (idx < total) {
+          const FanMeta& mk = meta[fan_tile_of(meta, nb, idx, true)];
+          const int le = idx - mk.pre_e;
+          // le / ni exactly: le < 2^12 and ni <= 32 leave a margin of 1 / 64 for rounding
+          const int j = (int)(((float)le + 0.5f) * mk.inv_ni), ii = le - j * mk.ni;
+          const int p = pv[mk.pre_v + ii], c = pv[mk.pre_v + mk.ni + j];
+          // lower triangle of the target (rows below its diagonal block always are)
+          const bool use = p >= 0 && c >= 0 && (p0 + p >= wt || p0 + p >= c);
+          tg[idx] = use ? (int16_t)(p + kFanPieceRows * c) : (int16_t)-1;
+          if (use) off[q] = mk.fo + ii + (long long)j * mk.rowlen;
+        }
+      }
+#pragma unroll
+      for (int q = 0; q < kFanInflight; ++q) v[q] = off[q] >= 0 ? ldcg(F + off[q]) : T(0);
+#pragma unroll
+      for (int q = 0; q < kFanInflight; ++q) {
+        const int idx = b0 + q * nt + tid;
+        if (off[q] >= 0) Bs[idx] = v[q];
+      }
+    }
+    __syncthreads();
+    // 4. tile by tile: an entry's updates land in list order
+    for (int k = 0; k < nb; ++k) {
+      const int k0 = meta[k].pre_e, k1 = k + 1 < nb ? meta[k + 1].pre_e : total;
+      for (int idx = k0 + tid; idx < k1; idx += nt) {
+        const int g = tg[idx];
+        if (g >= 0) S[g] += Bs[idx];
+      }
+      __syncthreads();
+    }
+    e += nb;
+  }
+  for (int idx = tid; idx < np * wt; idx += nt) {
+    const int p = idx % np, c = idx / np;
+    Pt[p0 + p + (size_t)c * ldt] = S[p + kFanPieceRows * c];
+  }
+  __syncthreads();  // the task reads these rows next, and reuses the shared memory
 }
 
 // MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
@@ -1478,7 +1531,8 @@ size_t fanin_smem_bytes(int max_w, bool fp32, int* cap) {
   const size_t es = fp32 ? sizeof(float) : sizeof(double);
   const int c = (std::max(2048, kFanPieceRows * max_w) + 7) & ~7;
   if (cap) *cap = c;
-  return 16 + kFanMetaBytes + (size_t)c * (sizeof(int16_t) + es) + (size_t)kFanPieceRows * max_w * es;
+  return 16 + kFanMetaBytes + kFanVcap * sizeof(int16_t) + (size_t)c * (sizeof(int16_t) + es) +
+         (size_t)kFanPieceRows * max_w * es;
 }
 
 // The fan-in mode has kernels of its own, so that the other modes' update
@@ -1541,6 +1595,31 @@ cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest
     assemble_kernel<float><<<grid, 256, 0, st>>>(values, dest, nnz, (float*)pool);
   else
     assemble_kernel<double><<<grid, 256, 0, st>>>(values, dest, nnz, (double*)pool);
+  return cudaGetLastError();
+}
+
+__global__ void fanrec_kernel(const FanEnt* __restrict__ ent, int64_t n, const UTask* __restrict__ ut,
+                              const int64_t* __restrict__ fan_off, const int64_t* __restrict__ rowoff,
+                              FanRec* __restrict__ rec) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const FanEnt fe = ent[k];
+    const UTask u = ut[fe.u];
+    FanRec r;
+    r.fo = fan_off[fe.u] + fe.i0;
+    r.rp = u.rel + fe.i0;
+    r.rs = rowoff[u.s] + u.seg0;
+    r.rowlen = u.rowlen;
+    r.ni = (int16_t)(fe.i1 - fe.i0);
+    r.seglen = (int16_t)u.seglen;
+    rec[k] = r;
+  }
+}
+
+cudaError_t launch_fanrec(const FanEnt* ent, int64_t n, const UTask* ut, const int64_t* fan_off,
+                          const int64_t* rowoff, FanRec* rec, cudaStream_t st) {
+  if (n <= 0) return cudaSuccess;
+  const int grid = (int)std::min<int64_t>((n + 255) / 256, 152 * 16);
+  fanrec_kernel<<<grid, 256, 0, st>>>(ent, n, ut, fan_off, rowoff, rec);
   return cudaGetLastError();
 }
 

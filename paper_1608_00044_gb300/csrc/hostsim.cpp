@@ -271,10 +271,11 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   // update tiles of each panel).  Every push is counted against its ring's
   // size, and each ring must receive exactly as many tasks as it holds.
   std::vector<int> dep(P.dep_f.begin(), P.dep_f.end()), tleft(P.ntrsm.begin(), P.ntrsm.end());
-  // deterministic order: update tiles chained per target (Plan::u_next; not
-  // in the fan-in mode, whose tiles need no order) and the solve chains
+  // deterministic order: update tiles chained per target (Plan::u_next) and
+  // the solve chains -- not in the fan-in mode, whose tiles need no order
   const bool uchain = !P.u_next.empty();
-  const bool det = P.params.deterministic;
+  const bool fan = P.params.fanin;
+  const bool det = P.params.deterministic && !fan;
   std::vector<int> udep(P.u_dep0.begin(), P.u_dep0.end());
   const int u0 = ns + P.n_trsm;  // first update tile id
   std::vector<char> ran(P.n_task_ids, 0);
@@ -368,6 +369,8 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   std::vector<int> fdep(P.fdep0.begin(), P.fdep0.end()), bdep(P.bdep0.begin(), P.bdep0.end());
   std::vector<int> ft(P.nst.begin(), P.nst.end()), bt(P.nst.begin(), P.nst.end());
   std::vector<int> ftdep(P.ft_dep0.begin(), P.ft_dep0.end());  // deterministic order only
+  // fan-in mode: the tiles' private buffers (Plan::st_zf)
+  std::vector<double> Zf(fan ? (size_t)P.st_zf.back() * nrhs : 0), Zb(fan ? (size_t)P.st_zb.back() * nrhs : 0);
   std::vector<char> sran(P.n_solve_tasks, 0);
   // Two rings as in the GPU kernel: the seeds (panels with no incoming forward
   // tile) fill the normal-priority ring; a task made ready by another is kept
@@ -409,6 +412,17 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
     if (task < ns) {  // FWD_D
       const int s = task, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
       const double* L = sim.panel(s);
+      if (fan)  // the forward tiles' products into these rows, in tile order
+        for (int e = P.rt_ptr[s + 1] - 1; e >= P.rt_ptr[s]; --e) {
+          const int tile = P.rt_tile[e], i0 = P.rt_rng[e] & 0xffff, i1 = P.rt_rng[e] >> 16;
+          const int cnt = (int)(P.st_zf[tile + 1] - P.st_zf[tile]);
+          const double* z = Zf.data() + (size_t)P.st_zf[tile] * nrhs;
+          for (int i = i0; i < i1; ++i) {
+            const int c = P.rows[P.st_roff[tile] + i] - f;
+            if (c < 0 || c >= w) return SPCHOL_EINTERNAL;
+            for (int r = 0; r < nrhs; ++r) Y[f + c + (size_t)r * n] += z[i + (size_t)r * cnt];
+          }
+        }
       for (int r = 0; r < nrhs; ++r) {
         double* y = Y.data() + f + (size_t)r * n;
         for (int j = 0; j < w; ++j) {
@@ -439,7 +453,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
         for (int i = row0; i < row0 + cnt; ++i) {
           double acc = 0.0;
           for (int j = 0; j < w; ++j) acc += L[i + (size_t)j * ld] * Y[f + j + (size_t)r * n];
-          Y[R[i] + (size_t)r * n] -= acc;
+          if (fan)
+            Zf[(size_t)P.st_zf[kt] * nrhs + (i - row0) + (size_t)r * cnt] = -acc;
+          else
+            Y[R[i] + (size_t)r * n] -= acc;
         }
       for (int e = P.st_tptr[kt]; e < P.st_tptr[kt + 1]; ++e) {
         const int t = P.st_tgt[e];
@@ -468,7 +485,10 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
         for (int j = 0; j < w; ++j) {
           double acc = 0.0;
           for (int i = row0; i < row0 + cnt; ++i) acc += L[i + (size_t)j * ld] * Y[R[i] + (size_t)r * n];
-          Y[f + j + (size_t)r * n] -= acc;
+          if (fan)
+            Zb[(size_t)P.st_zb[kt] * nrhs + j + (size_t)r * w] = -acc;
+          else
+            Y[f + j + (size_t)r * n] -= acc;
         }
       if (det && k + 1 < P.nst[s]) {  // the panel's next backward tile
         const int nx = P.st_first[s] + k + 1;
@@ -480,6 +500,12 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
     } else {  // BWD_D
       const int s = task - ns - 2 * nst, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
       const double* L = sim.panel(s);
+      if (fan)  // the panel's backward tiles' products, in tile order
+        for (int k = 0; k < P.nst[s]; ++k) {
+          const double* z = Zb.data() + (size_t)P.st_zb[P.st_first[s] + k] * nrhs;
+          for (int r = 0; r < nrhs; ++r)
+            for (int j = 0; j < w; ++j) Y[f + j + (size_t)r * n] += z[j + (size_t)r * w];
+        }
       for (int r = 0; r < nrhs; ++r) {
         double* y = Y.data() + f + (size_t)r * n;
         for (int j = w - 1; j >= 0; --j) {

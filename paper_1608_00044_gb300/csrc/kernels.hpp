@@ -29,6 +29,17 @@ struct PanelView {
   const int32_t* parent;
 };
 
+// Fan-in mode: one gather-list entry as the gather reads it, built on the
+// device at analysis from the list entry (FanEnt), its tile and the buffer
+// offsets: the buffer offset of its first listed row, the offset of that
+// row's relative index, the offset of its segment's row numbers (into the row
+// lists), the buffer's rows, and the listed rows and segment columns.
+struct FanRec {
+  int64_t fo, rp, rs;
+  int32_t rowlen;
+  int16_t ni, seglen;
+};
+
 struct FactorArgs {
   PanelView pv;
   const int32_t* trsm_first;
@@ -66,7 +77,7 @@ struct FactorArgs {
   const int64_t* fan_off;
   const int32_t* fan_task;
   const int64_t* fan_ptr;
-  const FanEnt* fan_ent;
+  const FanRec* fan_rec;
   int32_t fan_cap;
   int* ring;
   int* ctrl;
@@ -114,6 +125,15 @@ struct SolveArgs {
   const int32_t* ft_sptr;
   const int32_t* ft_succ;
   int32_t* ftdep;
+  // fan-in mode (null otherwise, see Plan::st_zf): the tiles' forward and
+  // backward buffers (nrhs columns each), their offsets, the tiles' first rows
+  // in the row lists and the rows of each panel's gather-list entries
+  double* zf;
+  double* zb;
+  const int64_t* st_zf;
+  const int64_t* st_zb;
+  const int64_t* st_roff;
+  const int32_t* rt_rng;
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
   unsigned long long* trace; // optional: per task id, start and end ns
 };
@@ -127,10 +147,12 @@ cudaError_t factor_configure(bool fp32, int mma_mode, bool fanin, size_t smem, i
 cudaError_t launch_assemble(bool fp32, const double* values, const int64_t* dest, int64_t nnz,
                             void* pool, cudaStream_t st);
 cudaError_t launch_factor(bool fp32, const FactorArgs& a, int grid, size_t smem, cudaStream_t st);
+cudaError_t launch_fanrec(const FanEnt* ent, int64_t n, const UTask* ut, const int64_t* fan_off,
+                          const int64_t* rowoff, FanRec* rec, cudaStream_t st);
 
 // solve.cu
-size_t solve_smem_bytes(int max_w, bool tc_tiles);
-cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm);
+size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin);
+cudaError_t solve_configure(bool fp32, bool fanin, size_t smem, int* blocks_per_sm);
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,
                               int64_t n, int nrhs, cudaStream_t st);

@@ -150,6 +150,19 @@ struct Plan {
   std::vector<int32_t> fan_task;  // ns + n_trsm
   std::vector<int64_t> fan_ptr;   // pieces + 1
   std::vector<FanEnt> fan_ent;
+  // The solves of the fan-in mode: forward tile k stores its product (its
+  // rows x nrhs, negated) at st_zf[k] * nrhs of one buffer and backward tile k
+  // its product (its panel's width x nrhs) at st_zb[k] * nrhs of another,
+  // instead of adding them into the right-hand sides.  A panel's forward
+  // diagonal task adds the forward buffers of the tiles with rows in its
+  // columns first, in tile order (its rt_tile list read from the end; rt_rng:
+  // those rows of the tile, i0 | i1 << 16; st_roff: the tile's first row in
+  // the row lists), and its backward diagonal task adds its own tiles'
+  // backward buffers in tile order: every entry of the solution receives its
+  // updates in one fixed order -- the order of the static chains.
+  std::vector<int64_t> st_zf, st_zb;  // n_st + 1
+  std::vector<int64_t> st_roff;       // n_st
+  std::vector<int32_t> rt_rng;        // like rt_tile
 
   PlanParams params;
 };

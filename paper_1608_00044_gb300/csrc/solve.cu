@@ -354,6 +354,97 @@ __device__ __forceinline__ void oz_stage_ys(const SolveArgs& a, const OzBuf& b, 
       });
 }
 
+// ---------------------------------------------------------------- fan-in gathers
+// Fan-in mode (the fan-in family of Section II-C, restated for the solves):
+// the tiles store their products in private buffers and the diagonal tasks
+// add them, in tile order, into the right-hand sides they stage in shared
+// memory.  Forward: the tiles with rows in the panel's columns, kSolveFanBatch
+// list entries at a time -- their rows are mapped to the panel's columns in
+// shared memory, then each thread adds, for the (column, right-hand side)
+// entries it owns, the batch's values in order (eight loads in flight).
+// Backward: the panel's own tiles, each thread summing its entries' values
+// over the tiles in order.
+constexpr int kSolveFanBatch = 32;
+struct SolveFanMeta {
+  long long zo, ro;  // the tile's buffer (times nrhs) and its first row in the row lists
+  int cnt, rng;      // its rows; those in the panel, i0 | i1 << 16
+};
+constexpr size_t solve_fan_smem_bytes(int max_w) {
+  return kSolveFanBatch * sizeof(SolveFanMeta) + (size_t)kSolveFanBatch * max_w * sizeof(int16_t) + 16;
+}
+
+__device__ void fwd_gather(const SolveArgs& a, int s, int f, int w, double* Ys, int r0, int nrc, unsigned char* ex) {
+  const int tid = threadIdx.x, nt = blockDim.x;
+  SolveFanMeta* meta = reinterpret_cast<SolveFanMeta*>(ex);
+  int16_t* inv = reinterpret_cast<int16_t*>(meta + kSolveFanBatch);  // [batch entry][column]: its row, or -1
+  const int e0 = a.rt_ptr[s], e1 = a.rt_ptr[s + 1];
+  for (int eb = e1; eb > e0; eb -= kSolveFanBatch) {  // ascending tile order: the list from its end
+    const int nb = min(kSolveFanBatch, eb - e0);
+    __syncthreads();  // the right-hand sides are staged, or the previous batch is added
+    if (tid < nb) {
+      const int e = eb - 1 - tid, tile = a.rt_tile[e];
+      SolveFanMeta m;
+      m.zo = a.st_zf[tile] * a.nrhs;
+      m.ro = a.st_roff[tile];
+      m.cnt = (int)(a.st_zf[tile + 1] - a.st_zf[tile]);
+      m.rng = a.rt_rng[e];
+      meta[tid] = m;
+    }
+    for (int idx = tid; idx < nb * w; idx += nt) inv[idx] = -1;
+    __syncthreads();
+    for (int idx = tid; idx < nb * w; idx += nt) {  // an entry has at most w rows in the panel
+      const int b = idx / w, i = (meta[b].rng & 0xffff) + idx % w;
+      if (i < (meta[b].rng >> 16)) {
+        const int c = __ldg(a.pv.rows + meta[b].ro + i) - f;
+        if (c >= 0 && c < w)
+          inv[b * w + c] = (int16_t)i;
+        else
+          atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // cannot happen for a consistent plan
+      }
+    }
+    __syncthreads();
+    for (int p = tid; p < w * nrc; p += nt) {
+      const int c = p % w, r = p / w;
+      double y = Ys[p];
+      for (int b0 = 0; b0 < nb; b0 += 8) {
+        double v[8];
+        int i[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          i[u] = b0 + u < nb ? inv[(b0 + u) * w + c] : -1;
+          v[u] = i[u] >= 0 ? ldcg(a.zf + meta[b0 + u].zo + i[u] + (size_t)(r0 + r) * meta[b0 + u].cnt) : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u)
+          if (i[u] >= 0) y += v[u];
+      }
+      Ys[p] = y;
+    }
+  }
+  __syncthreads();
+}
+
+__device__ void bwd_gather(const SolveArgs& a, int s, int w, double* Ys, int r0, int nrc) {
+  const int nk = a.nst[s];
+  const double* z0 = a.zb + a.st_zb[a.st_first[s]] * a.nrhs;  // the panel's tiles' buffers, w x nrhs each
+  for (int p = threadIdx.x; p < w * nrc; p += blockDim.x) {
+    const int j = p % w, r = p / w;
+    const double* z = z0 + j + (size_t)(r0 + r) * w;
+    double y = Ys[p];
+    for (int k0 = 0; k0 < nk; k0 += 8) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) v[u] = k0 + u < nk ? ldcg(z + (size_t)(k0 + u) * w * a.nrhs) : 0.0;
+#pragma unroll
+      for (int u = 0; u < 8; ++u)
+        if (k0 + u < nk) y += v[u];
+    }
+    Ys[p] = y;
+  }
+  __syncthreads();
+}
+
+template <bool FAN>
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
@@ -369,6 +460,7 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
       const int j = idx % w, r = idx / w;
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
+    if constexpr (FAN) fwd_gather(a, s, f, w, Ys, r0, nrc, reinterpret_cast<unsigned char*>(Ys + kSolveNRC * w));
     __syncthreads();
     for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
       const int c = p % half, r = p / half;
@@ -397,6 +489,7 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
 // x_s <- L11^{-T} y_s with the stored inverse: entry k is the dot product of
 // column k of L11^{-1} (rows k .. w-1) with y_s; thread (r, c) takes columns c
 // and w - 1 - c.
+template <bool FAN>
 __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
@@ -411,6 +504,10 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
     for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
       const int j = idx % w, r = idx / w;
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
+    }
+    if constexpr (FAN) {
+      __syncthreads();
+      bwd_gather(a, s, w, Ys, r0, nrc);
     }
     __syncthreads();
     for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
@@ -445,9 +542,9 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
 // the 64-row tiles near the root); with one, all threads take rows.  The group
 // is uniform in a warp and the right-hand sides a thread owns are fixed at
 // compile time, so no FMA is spent on another group's right-hand sides.
-template <typename T, int NPER>
+template <typename T, int NPER, bool FAN>
 __device__ void fwd_tile_rows(const SolveArgs& a, const T* P, int ld, int row0, int cnt, const int32_t* R, int w,
-                              const double* Ys, int r0, int nrc, int G) {
+                              const double* Ys, int r0, int nrc, int G, double* z) {
   const int rows_per = blockDim.x / G;
   const int g = threadIdx.x / rows_per, il = threadIdx.x - g * rows_per;
   int nv = 0;  // right-hand sides of this thread that exist
@@ -471,17 +568,24 @@ __device__ void fwd_tile_rows(const SolveArgs& a, const T* P, int ld, int row0, 
         for (int q = 0; q < NPER; ++q) acc[q] += l[u] * Ys[j0 + u + (g + G * q) * w];
       }
     }
-    const int gr = R[row0 + i];
+    if constexpr (FAN) {  // the tile's buffer: its rows x nrhs
 #pragma unroll
-    for (int q = 0; q < NPER; ++q)
-      if (q < nv) red_add(a.Y + gr + (size_t)(r0 + g + G * q) * a.ldy, -acc[q]);
+      for (int q = 0; q < NPER; ++q)
+        if (q < nv) z[i + (size_t)(r0 + g + G * q) * cnt] = -acc[q];
+    } else {
+      const int gr = R[row0 + i];
+#pragma unroll
+      for (int q = 0; q < NPER; ++q)
+        if (q < nv) red_add(a.Y + gr + (size_t)(r0 + g + G * q) * a.ldy, -acc[q]);
+    }
   }
 }
 
 // y[rows of tile] -= L21[tile] y_s on the tensor cores (FP64 panels, 16 <= w
 // <= 64): the tile's rows in passes of 64.
+template <bool FAN>
 __device__ void fwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row0, int cnt, const int32_t* R, int f,
-                            int w, double* sm) {
+                            int w, double* sm, double* z) {
   const OzBuf b = oz_carve(sm);
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
@@ -500,21 +604,25 @@ __device__ void fwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row
       double* Y = a.Y + (size_t)r0 * a.ldy;
       const int64_t ldy = a.ldy;
       const int32_t* Rc = R + row0 + c0;
-      oz_product(b, mc, w, nrc, [&](int, int m, int n, double v) { red_add(Y + Rc[m] + n * ldy, -v); });
+      if constexpr (FAN)
+        oz_product(b, mc, w, nrc, [&](int, int m, int n, double v) { z[c0 + m + (size_t)(r0 + n) * cnt] = -v; });
+      else
+        oz_product(b, mc, w, nrc, [&](int, int m, int n, double v) { red_add(Y + Rc[m] + n * ldy, -v); });
     }
   }
 }
 
-template <typename T>
+template <typename T, bool FAN>
 __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  double* z = FAN ? a.zf + a.st_zf[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
   if constexpr (sizeof(T) == 8) {
     if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
-      fwd_tile_oz(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm);
+      fwd_tile_oz<FAN>(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm, z);
       return;
     }
   }
@@ -528,13 +636,13 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
     }
     __syncthreads();
     if (nrc >= 5 && cnt <= 32)
-      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 8);
+      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 8, z);
     else if (nrc >= 5)
-      fwd_tile_rows<T, 2>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
+      fwd_tile_rows<T, 2, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4, z);
     else if (nrc >= 3)
-      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4);
+      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4, z);
     else
-      fwd_tile_rows<T, 1>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, nrc);
+      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, nrc, z);
   }
 }
 
@@ -547,8 +655,9 @@ constexpr int kBwdCH = 64;
 // <= 64): A = L21[tile]^T (w x rows), the tile's rows in passes of 64, each with
 // its own exponents; the passes' results are summed in FP64 by the owning
 // threads and subtracted once.
+template <bool FAN>
 __device__ void bwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row0, int cnt, const int32_t* R, int f,
-                            int w, double* sm) {
+                            int w, double* sm, double* z) {
   const OzBuf b = oz_carve(sm);
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
@@ -581,22 +690,28 @@ __device__ void bwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row
 #pragma unroll
       for (int c = 0; c < 4; ++c) {
         const int m = 16 * warp + (lane >> 2) + ((c & 2) ? 8 : 0), n = 2 * (lane & 3) + (c & 1);
-        if (m < w && n < nrc) red_add(a.Y + f + m + (size_t)(r0 + n) * a.ldy, -part[c]);
+        if (m < w && n < nrc) {
+          if constexpr (FAN)
+            z[m + (size_t)(r0 + n) * w] = -part[c];
+          else
+            red_add(a.Y + f + m + (size_t)(r0 + n) * a.ldy, -part[c]);
+        }
       }
     }
   }
 }
 
-template <typename T>
+template <typename T, bool FAN>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+  double* z = FAN ? a.zb + a.st_zb[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
   if constexpr (sizeof(T) == 8) {
     if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
-      bwd_tile_oz(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm);
+      bwd_tile_oz<FAN>(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm, z);
       return;
     }
   }
@@ -653,7 +768,10 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
       const int p = threadIdx.x + q * blockDim.x;
       if (p < w * nrc) {
         const int j = p % w, rr = p / w;
-        red_add(a.Y + f + j + (size_t)(r0 + rr) * a.ldy, -part[q]);
+        if constexpr (FAN)
+          z[j + (size_t)(r0 + rr) * w] = -part[q];
+        else
+          red_add(a.Y + f + j + (size_t)(r0 + rr) * a.ldy, -part[q]);
       }
     }
   }
@@ -680,7 +798,7 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
   }
 }
 
-template <typename T>
+template <typename T, bool FAN>
 __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveShared sh;
@@ -721,7 +839,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
     const int type = task < ns ? 0 : task < ns + nst ? 1 : task < ns + 2 * nst ? 2 : 3;
     if (task < ns) {
       const int s = task;
-      fwd_diag(a, s, sm);
+      fwd_diag<FAN>(a, s, sm);
       publish_cta_writes();
       // continue with the first forward tile (the rows of the parent) and
       // release the others
@@ -740,7 +858,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       }
     } else if (task < ns + nst) {
       const int kt = task - ns, s = a.st_sn[kt];
-      fwd_tile<T>(a, s, kt - a.st_first[s], sm);
+      fwd_tile<T, FAN>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
       // Counter updates are spread over the CTA's threads: a panel near the
       // root has thousands of dependent tiles, and they sit on the critical path.
@@ -759,7 +877,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
         release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
-      bwd_tile<T>(a, s, kt - a.st_first[s], sm);
+      bwd_tile<T, FAN>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
       // deterministic order: the panel's next backward tile
       if (a.ftdep && threadIdx.x == 0 && kt + 1 < a.st_first[s] + a.nst[s] &&
@@ -769,7 +887,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
         keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + 2 * nst + s);
     } else {
       const int s = task - ns - 2 * nst;
-      bwd_diag(a, s, sm);
+      bwd_diag<FAN>(a, s, sm);
       publish_cta_writes();
       release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     }
@@ -809,27 +927,32 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 
 }  // namespace
 
-size_t solve_smem_bytes(int max_w, bool tc_tiles) {
-  const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double);
+size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin) {
+  const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double) +
+                      (fanin ? solve_fan_smem_bytes(max_w) : 0);
   const size_t tile = ((size_t)max_w * (kBwdCH + 1) + kBwdCH * kSolveNRC) * sizeof(double);
   size_t need = diag > tile ? diag : tile;
   if (tc_tiles && max_w >= kOzMinW && need < kOzSmemBytes) need = kOzSmemBytes;
   return need;
 }
 
-cudaError_t solve_configure(bool fp32, size_t smem, int* blocks_per_sm) {
-  const void* fn = fp32 ? (const void*)solve_kernel<float> : (const void*)solve_kernel<double>;
+// The fan-in mode has kernels of its own, so that the other modes' tiles and
+// diagonal tasks carry none of its code.
+static const void* solve_fn(bool fp32, bool fan) {
+  if (fan) return fp32 ? (const void*)solve_kernel<float, true> : (const void*)solve_kernel<double, true>;
+  return fp32 ? (const void*)solve_kernel<float, false> : (const void*)solve_kernel<double, false>;
+}
+
+cudaError_t solve_configure(bool fp32, bool fanin, size_t smem, int* blocks_per_sm) {
+  const void* fn = solve_fn(fp32, fanin);
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
 }
 
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st) {
-  if (fp32)
-    solve_kernel<float><<<grid, kSolveThreads, smem, st>>>(a);
-  else
-    solve_kernel<double><<<grid, kSolveThreads, smem, st>>>(a);
-  return cudaGetLastError();
+  void* args[] = {const_cast<SolveArgs*>(&a)};
+  return cudaLaunchKernel(solve_fn(fp32, a.zf != nullptr), dim3(grid), dim3(kSolveThreads), args, smem, st);
 }
 
 cudaError_t ensure_smem_limit(const void* fn, size_t need) {

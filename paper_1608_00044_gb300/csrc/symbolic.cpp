@@ -522,6 +522,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.n_solve_tasks = 2 * ns + 2 * P.n_st;
   P.st_tptr.assign(P.n_st + 1, 0);
   P.st_tgt.clear();
+  std::vector<int32_t> st_rng;  // per st_tgt entry: the tile's rows in that panel, i0 | i1 << 16
   P.fdep0.assign(ns, 0);
   P.bdep0.assign(P.n_st, 0);
   for (int32_t s = 0; s < ns; ++s) {
@@ -535,11 +536,14 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       for (int32_t i = r0; i < r1; ++i) {
         const int32_t t = P.snode_of[R[i]];
         if (t != last) {  // rows are sorted, so each target appears as one run
+          if (last >= 0) st_rng.back() |= (i - r0) << 16;
           P.st_tgt.push_back(t);
+          st_rng.push_back(i - r0);
           P.fdep0[t]++;
           last = t;
         }
       }
+      if (last >= 0) st_rng.back() |= (r1 - r0) << 16;
       P.st_tptr[tile + 1] = (int32_t)P.st_tgt.size();
       P.bdep0[tile] = (P.st_tptr[tile + 1] - P.st_tptr[tile]) + 1;
     }
@@ -547,7 +551,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.ft_sptr.clear();
   P.ft_succ.clear();
   P.ft_dep0.clear();
-  if (prm.deterministic) {
+  if (prm.deterministic && !prm.fanin) {
     // forward tiles: one chain per target panel, in tile order
     P.ft_dep0.assign(P.n_st, 1);
     std::vector<int32_t> last(ns, -1), npred_of(P.n_st, 0);
@@ -580,8 +584,32 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     // descendants -- the next steps of the backward chain -- are released
     // first (and the first becomes the releasing CTA's continuation)
     std::vector<int32_t> fill(P.rt_ptr.begin(), P.rt_ptr.end() - 1);
+    P.rt_rng.clear();
+    if (prm.fanin) P.rt_rng.resize(P.st_tgt.size());
     for (int32_t tile = P.n_st - 1; tile >= 0; --tile)
-      for (int32_t q = P.st_tptr[tile]; q < P.st_tptr[tile + 1]; ++q) P.rt_tile[fill[P.st_tgt[q]]++] = tile;
+      for (int32_t q = P.st_tptr[tile]; q < P.st_tptr[tile + 1]; ++q) {
+        const int32_t e = fill[P.st_tgt[q]]++;
+        P.rt_tile[e] = tile;
+        if (prm.fanin) P.rt_rng[e] = st_rng[q];
+      }
+  }
+  // fan-in solves: the tiles' private buffers (Plan::st_zf)
+  P.st_zf.clear();
+  P.st_zb.clear();
+  P.st_roff.clear();
+  if (prm.fanin) {
+    P.st_zf.assign(P.n_st + 1, 0);
+    P.st_zb.assign(P.n_st + 1, 0);
+    P.st_roff.assign(P.n_st, 0);
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s], TS = P.st_rows[s];
+      for (int32_t k = 0; k < P.nst[s]; ++k) {
+        const int32_t tile = P.st_first[s] + k, r0 = w + k * TS;
+        P.st_zf[tile + 1] = P.st_zf[tile] + std::min(TS, r - r0);
+        P.st_zb[tile + 1] = P.st_zb[tile] + w;
+        P.st_roff[tile] = P.rowoff[s] + r0;
+      }
+    }
   }
   P.kid_ptr.assign(ns + 1, 0);
   for (int32_t s = 0; s < ns; ++s)

@@ -270,23 +270,26 @@ def test_fanin_mode_matches_oracle(name, W):
     _check(A, perm, B, deterministic=2, max_width=W)
 
 
-@pytest.mark.parametrize("precision", ["FP64", "FP32"])
+@pytest.mark.parametrize("precision", ["FP64", "FP32", "FP64_TC"])
 def test_fanin_reproduces_the_static_order_bitwise(precision):
     """Fan-in aggregation adds each entry's updates in update-tile order, the
-    order of the static (target, source) chains: modes 2 and 1 give bitwise
-    the same solution (and, in FP64, the same factor)."""
+    order of the static (target, source) chains, and the fan-in solves add the
+    tiles' products into each panel in tile order, the order of the solve
+    chains: modes 2 and 1 give bitwise the same solution (and, in FP64, the
+    same factor), with 1, 8 and 11 right-hand sides."""
     A, perm, _ = gridgen.workload("diff3d_12")
-    B = gridgen.rhs_uniform(A.n, 2, seed=9)
     prec = getattr(spchol, precision)
-    out = []
-    for det in (1, 2):
-        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=det, precision=prec)
-        assert rc == 0
-        out.append((X, spchol.export_factor(h)[2] if precision == "FP64" else None))
-        spchol.destroy(h)
-    assert np.array_equal(out[0][0], out[1][0])
-    if precision == "FP64":
-        assert np.array_equal(out[0][1], out[1][1])
+    for nrhs in (1, 8, 11):
+        B = gridgen.rhs_uniform(A.n, nrhs, seed=9 + nrhs)
+        out = []
+        for det in (1, 2):
+            rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=det, precision=prec)
+            assert rc == 0
+            out.append((X, spchol.export_factor(h)[2] if precision == "FP64" else None))
+            spchol.destroy(h)
+        assert np.array_equal(out[0][0], out[1][0])
+        if precision == "FP64":
+            assert np.array_equal(out[0][1], out[1][1])
 
 
 def test_fanin_batch_matches_solo_bitwise():

@@ -49,6 +49,20 @@ def test_noalloc_matches_solve_on_two_calls(precision):
     spchol.destroy(h)
 
 
+@pytest.mark.parametrize("det", [1, 2])
+def test_noalloc_deterministic_modes_match_solve_bitwise(det):
+    """In the deterministic modes (static chains, fan-in buffers in the fixed
+    array) the two entry points give bitwise the same solution."""
+    A, perm, _ = gridgen.workload("diff3d_12")
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(deterministic=det))
+    assert spchol.factorize(h, A.values) == 0
+    for nrhs, seed in ((3, 4), (8, 5)):
+        B, X, X_ref = _solve_both(h, A, nrhs, seed)
+        assert oracle.berr(A, X, B) <= 1e-13
+        assert np.array_equal(X, X_ref)
+    spchol.destroy(h)
+
+
 def test_noalloc_second_handle_after_first():
     """A different matrix right after: the reused scratch is re-initialised."""
     for name, nrhs in (("diff3d_12", 5), ("lap2d_64", 1)):
