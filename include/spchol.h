@@ -146,6 +146,10 @@ typedef struct spchol_stats {
   int64_t factor_subtree_count;
   int ir_gmres_iters;         /* mixed precision: GMRES-IR steps of the last solve (0 when classic
                                  refinement reached the target) */
+  double factor_gather_ms[3]; /* profile, deterministic = 2: time of the fan-in gathers (summed over
+                                 CTAs) cutting batches, staging them and adding them */
+  int64_t factor_gather_batches;
+  int64_t factor_gather_tiles;
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */

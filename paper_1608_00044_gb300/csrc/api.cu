@@ -421,7 +421,8 @@ int setup_device(spchol_handle_t h) {
     return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   if (fan) {  // never read before written: no initialisation
-    h->fan_buf_bytes = std::max<size_t>((size_t)P.fan_off.back() * esz, 256);
+    // + 16 bytes: the gather copies whole 16-byte pieces, up to one past the last value
+    h->fan_buf_bytes = std::max<size_t>((((size_t)P.fan_off.back() * esz + 15) & ~size_t(15)) + 16, 256);
     CU(cudaMalloc(&h->d_fan_buf, h->fan_buf_bytes));
     CU(cudaMalloc(&h->d_fan_rec, std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanRec)));
     CU(launch_fanrec(h->d_fan_ent, (int64_t)P.fan_ent.size(), h->d_ut, h->d_fan_off, h->d_rowoff, h->d_fan_rec,
@@ -626,7 +627,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.invoff = h->d_invoff;
   a.prof = profile ? h->d_prof : nullptr;
   a.trace = profile ? h->d_trace_f : nullptr;
-  if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 10 * sizeof(unsigned long long), st));
+  if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 16 * sizeof(unsigned long long), st));
   CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   return 0;
@@ -660,7 +661,7 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
   if (P.ns > 0) {
     rc = status_of(h);
     if (h->opt.profile) {
-      CU(cudaMemcpy(h->h_prof, h->d_prof, 10 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
+      CU(cudaMemcpy(h->h_prof, h->d_prof, 16 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
       for (int k = 0; k < 3; ++k) {
         h->stats.factor_task_ms[k] = h->h_prof[k] * 1e-6;
         h->stats.factor_task_count[k] = (int64_t)h->h_prof[4 + k];
@@ -669,6 +670,9 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
       h->stats.factor_tc_update_ms = h->h_prof[7] * 1e-6;
       h->stats.factor_subtree_ms = h->h_prof[8] * 1e-6;
       h->stats.factor_subtree_count = (int64_t)h->h_prof[9];
+      for (int k = 0; k < 3; ++k) h->stats.factor_gather_ms[k] = h->h_prof[10 + k] * 1e-6;
+      h->stats.factor_gather_batches = (int64_t)h->h_prof[13];
+      h->stats.factor_gather_tiles = (int64_t)h->h_prof[14];
     }
   }
   float ms = 0.f;

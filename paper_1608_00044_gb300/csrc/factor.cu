@@ -1078,39 +1078,45 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 // tile in the piece's list order, so every entry of L receives its updates in
 // one fixed order whatever the schedule.  The piece sits in shared memory and
 // the list is consumed in batches of up to kFanBatch tiles:
-//   1. warp 0 cuts the batch where the tiles' values or their row and column
-//      positions would overflow the staging areas (its records were fetched
-//      during the previous batch);
-//   2. all threads stage the batch's row positions (in the piece) and column
-//      positions (in the panel);
-//   3. all threads fetch the values, kFanInflight loads per thread in flight,
-//      and note each value's place in the piece (-1 above the diagonal);
-//   4. the values are added tile by tile.
-// Values and the piece (written by other CTAs during the factorization) are
-// read around L1 (ld.global.cg); the records were written at analysis.
+//   1. warp 0 cuts the batch where its staged values would overflow the
+//      staging area (the records were fetched during the previous batch);
+//   2. all threads copy, for each column of each tile, the 16-byte pieces that
+//      hold its rows in the piece (cp.async, L2 only: the buffers were written
+//      by other CTAs; every copy of the batch in flight at once) and load the
+//      rows' positions in the piece and the columns' positions in the panel;
+//   3. the values are added tile by tile (a barrier between tiles).
+// The piece and the buffers are read around L1; the records were written at
+// analysis.
 struct FanMeta {
   long long fo, rp, rs;  // FanRec: buffer offset of the first listed row, relative rows, segment rows
-  int pre_e, pre_v;      // first staged value and first staged position of the tile
-  int rowlen;
+  int pre_b, pre_v;      // the tile's first staged 16-byte piece and first staged position
+  int rowlen, cps;       // buffer rows; staged pieces per column
   short ni, seglen;
   float inv_ni;  // 1 / ni: value index -> (row, column) without a division
+  float inv_cps;
 };
 constexpr int kFanBatch = 32;
-constexpr int kFanVcap = 1024;    // staged positions per batch (a tile has at most 32 + 128)
-constexpr int kFanInflight = 4;   // value loads in flight per thread
+constexpr int kFanVcap = 1024;  // staged positions per batch (a tile has at most 32 + 128)
 constexpr size_t kFanMetaBytes = ((kFanBatch * sizeof(FanMeta) + 16) + 15) & ~size_t(15);
 
-// The batch tile that staged value (values) or position (!values) idx belongs to.
-__device__ __forceinline__ int fan_tile_of(const FanMeta* meta, int nb, int idx, bool values) {
+// 16-byte pieces that can hold ni consecutive values starting anywhere.
+template <typename T>
+__host__ __device__ constexpr int fan_pieces(int ni) {
+  return (ni + 16 / (int)sizeof(T) - 2) / (16 / (int)sizeof(T)) + 1;
+}
+
+// The batch tile that staged piece (pieces) or position (!pieces) idx belongs to.
+__device__ __forceinline__ int fan_tile_of(const FanMeta* meta, int nb, int idx, bool pieces) {
   int k = 0;
 #pragma unroll
   for (int b = kFanBatch / 2; b > 0; b >>= 1)
-    if (k + b < nb && (values ? meta[k + b].pre_e : meta[k + b].pre_v) <= idx) k += b;
+    if (k + b < nb && (pieces ? meta[k + b].pre_b : meta[k + b].pre_v) <= idx) k += b;
   return k;
 }
 
 template <typename T>
 __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np, unsigned char* smraw) {
+  constexpr int E = 16 / (int)sizeof(T);  // values per 16-byte piece
   const int tid = threadIdx.x, nt = blockDim.x;
   long long e = a.fan_ptr[pc];
   const long long e1 = a.fan_ptr[pc + 1];
@@ -1118,26 +1124,29 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
   const int ft = a.pv.fcol[t], wt = a.pv.fcol[t + 1] - ft, ldt = a.pv.ld[t];
   T* Pt = panel_ptr<T>(a, t);
   const T* F = reinterpret_cast<const T*>(a.fan_buf);
-  const int cap = a.fan_cap;  // a multiple of 8, at least kFanPieceRows x the widest panel
+  const int cap = a.fan_cap;  // 16-byte pieces per batch; one tile's always fit
   unsigned char* base = smraw + ((16u - (smem_addr(smraw) & 15u)) & 15u);
   FanMeta* meta = reinterpret_cast<FanMeta*>(base);
-  int* scal = reinterpret_cast<int*>(meta + kFanBatch);  // tiles, values and positions of the batch
+  int* scal = reinterpret_cast<int*>(meta + kFanBatch);  // tiles, pieces and positions of the batch
   int16_t* pv = reinterpret_cast<int16_t*>(base + kFanMetaBytes);  // positions: rows in the piece, then columns
-  int16_t* tg = pv + kFanVcap;                                     // value -> place in the piece, or -1
-  T* Bs = reinterpret_cast<T*>(tg + cap);
-  T* S = Bs + cap;  // the piece: np rows x wt columns, leading dimension kFanPieceRows
+  T* Bs = reinterpret_cast<T*>(pv + kFanVcap);                     // the staged pieces
+  T* S = Bs + (size_t)cap * E;  // the piece: np rows x wt columns, leading dimension kFanPieceRows
   for (int idx = tid; idx < np * wt; idx += nt) {
     const int p = idx % np, c = idx / np;
     S[p + kFanPieceRows * c] = ldcg(Pt + p0 + p + (size_t)c * ldt);
   }
   FanRec r{};  // warp 0: the records of the next batch window
   if (tid < 32 && e + tid < e1) r = a.fan_rec[e + tid];
+  const bool prof = a.prof != nullptr && tid == 0;
+  uint64_t tp[3] = {0, 0, 0}, tq = prof ? global_ns() : 0;
+  long long nbat = 0, ntile = 0;
   while (e < e1) {
     __syncthreads();  // the piece is loaded, or the previous batch is added
     int nb = 0;
     if (tid < 32) {
       const bool have = e + tid < e1;
-      const int n = have ? r.ni * r.seglen : 0, v = have ? r.ni + r.seglen : 0;
+      const int cps = have ? fan_pieces<T>(r.ni) : 0;
+      const int n = have ? r.seglen * cps : 0, v = have ? r.ni + r.seglen : 0;
       int in = n, iv = v;
 #pragma unroll
       for (int o = 1; o < 32; o <<= 1) {
@@ -1154,12 +1163,14 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
         mm.fo = r.fo;
         mm.rp = r.rp;
         mm.rs = r.rs;
-        mm.pre_e = in - n;
+        mm.pre_b = in - n;
         mm.pre_v = iv - v;
         mm.rowlen = r.rowlen;
+        mm.cps = cps;
         mm.ni = r.ni;
         mm.seglen = r.seglen;
         mm.inv_ni = 1.0f / (float)max(1, (int)r.ni);
+        mm.inv_cps = 1.0f / (float)max(1, cps);
         meta[tid] = mm;
       }
       if (tid == nb - 1) {
@@ -1171,13 +1182,32 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
       if (e + nb + tid < e1) r = a.fan_rec[e + nb + tid];  // in flight during this batch
     }
     __syncthreads();
-    nb = scal[0];
-    int total = scal[1], npos = scal[2];
-    if (total > cap || npos > kFanVcap) {  // cannot happen for a consistent plan
-      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
-      total = npos = 0;
+    if (prof) {
+      const uint64_t tn = global_ns();
+      tp[0] += tn - tq;
+      tq = tn;
     }
-    // 2. row positions in the piece and column positions in the panel
+    nb = scal[0];
+    int npc = scal[1], npos = scal[2];
+    if (npc > cap || npos > kFanVcap) {  // cannot happen for a consistent plan
+      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      npc = npos = 0;
+    }
+    // 2. the pieces that hold each column's rows (the 16-byte piece at or below
+    // its first value, and on), and the positions
+    for (int idx = tid; idx < npc; idx += nt) {
+      const FanMeta& mk = meta[fan_tile_of(meta, nb, idx, true)];
+      const int lp = idx - mk.pre_b;
+      // lp / cps exactly: lp < 2^12 and cps <= 17 leave a margin of 1 / 34 for rounding
+      const int j = (int)(((float)lp + 0.5f) * mk.inv_cps), q = lp - j * mk.cps;
+      const long long g0 = mk.fo + (long long)j * mk.rowlen;  // the column's first value
+      const long long a0 = (g0 & ~(long long)(E - 1)) + (long long)q * E;
+      if (a0 < g0 + mk.ni)  // a piece past the column's last value holds nothing it needs
+        asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_addr(Bs + (size_t)idx * E)),
+                     "l"(F + a0)
+                     : "memory");
+    }
+    cp_async_commit();
     for (int idx = tid; idx < npos; idx += nt) {
       const FanMeta& mk = meta[fan_tile_of(meta, nb, idx, false)];
       const int lv = idx - mk.pre_v;
@@ -1193,50 +1223,46 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
       if (!ok) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // outside the piece: an inconsistent plan
       pv[idx] = ok ? (int16_t)q : (int16_t)-1;
     }
+    cp_async_wait<0>();
     __syncthreads();
-    // 3. the values, kFanInflight loads in flight per thread
-    for (int b0 = 0; b0 < total; b0 += kFanInflight * nt) {
-      long long off[kFanInflight];
-      T v[kFanInflight];
-#pragma unroll
-      for (int q = 0; q < kFanInflight; ++q) {
-        const int idx = b0 + q * nt + tid;
-        off[q] = -1;
-        if (idx < total) {
-          const FanMeta& mk = meta[fan_tile_of(meta, nb, idx, true)];
-          const int le = idx - mk.pre_e;
-          // le / ni exactly: le < 2^12 and ni <= 32 leave a margin of 1 / 64 for rounding
-          const int j = (int)(((float)le + 0.5f) * mk.inv_ni), ii = le - j * mk.ni;
-          const int p = pv[mk.pre_v + ii], c = pv[mk.pre_v + mk.ni + j];
-          // lower triangle of the target (rows below its diagonal block always are)
-          const bool use = p >= 0 && c >= 0 && (p0 + p >= wt || p0 + p >= c);
-          tg[idx] = use ? (int16_t)(p + kFanPieceRows * c) : (int16_t)-1;
-          if (use) off[q] = mk.fo + ii + (long long)j * mk.rowlen;
+    if (prof) {
+      const uint64_t tn = global_ns();
+      tp[1] += tn - tq;
+      tq = tn;
+    }
+    // 3. tile by tile: an entry's updates land in list order
+    for (int k = 0; k < nb; ++k) {
+      const FanMeta& mk = meta[k];
+      const int ni = mk.ni, n = ni * mk.seglen;
+      for (int idx = tid; idx < n; idx += nt) {
+        // idx / ni exactly: idx < 2^12 and ni <= 32 leave a margin of 1 / 64 for rounding
+        const int j = (int)(((float)idx + 0.5f) * mk.inv_ni), ii = idx - j * ni;
+        const int p = pv[mk.pre_v + ii], c = pv[mk.pre_v + ni + j];
+        // lower triangle of the target (rows below its diagonal block always are)
+        if (p >= 0 && c >= 0 && (p0 + p >= wt || p0 + p >= c)) {
+          const int sub = (int)((mk.fo + (long long)j * mk.rowlen) & (E - 1));
+          S[p + kFanPieceRows * c] += Bs[(size_t)(mk.pre_b + j * mk.cps) * E + sub + ii];
         }
       }
-#pragma unroll
-      for (int q = 0; q < kFanInflight; ++q) v[q] = off[q] >= 0 ? ldcg(F + off[q]) : T(0);
-#pragma unroll
-      for (int q = 0; q < kFanInflight; ++q) {
-        const int idx = b0 + q * nt + tid;
-        if (off[q] >= 0) Bs[idx] = v[q];
-      }
-    }
-    __syncthreads();
-    // 4. tile by tile: an entry's updates land in list order
-    for (int k = 0; k < nb; ++k) {
-      const int k0 = meta[k].pre_e, k1 = k + 1 < nb ? meta[k + 1].pre_e : total;
-      for (int idx = k0 + tid; idx < k1; idx += nt) {
-        const int g = tg[idx];
-        if (g >= 0) S[g] += Bs[idx];
-      }
       __syncthreads();
+    }
+    if (prof) {
+      const uint64_t tn = global_ns();
+      tp[2] += tn - tq;
+      tq = tn;
+      ++nbat;
+      ntile += nb;
     }
     e += nb;
   }
   for (int idx = tid; idx < np * wt; idx += nt) {
     const int p = idx % np, c = idx / np;
     Pt[p0 + p + (size_t)c * ldt] = S[p + kFanPieceRows * c];
+  }
+  if (prof) {
+    for (int k = 0; k < 3; ++k) atomicAdd(&a.prof[10 + k], (unsigned long long)tp[k]);
+    atomicAdd(&a.prof[13], (unsigned long long)nbat);
+    atomicAdd(&a.prof[14], (unsigned long long)ntile);
   }
   __syncthreads();  // the task reads these rows next, and reuses the shared memory
 }
@@ -1249,9 +1275,10 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
 // other's latencies (measured: FP32 factor -12 %, FP64 -0.8 % for five against
 // four).  The TF32 mode runs two CTAs per SM and the BF16-split mode three, as
 // their operand tiles' shared memory allows (a BF16-split CTA holds 128 of the
-// SM's 512 TMEM columns).
+// SM's 512 TMEM columns).  The fan-in mode's CUDA-core kernels run four: the
+// gather's staging area takes a quarter of the SM's shared memory.
 template <typename T, int MODE, bool FAN>
-__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 : sizeof(T) == 4 ? 6 : 5)
+__global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 : FAN ? 4 : sizeof(T) == 4 ? 6 : 5)
     factor_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ FactorShared sh;
@@ -1529,10 +1556,10 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
 
 size_t fanin_smem_bytes(int max_w, bool fp32, int* cap) {
   const size_t es = fp32 ? sizeof(float) : sizeof(double);
-  const int c = (std::max(2048, kFanPieceRows * max_w) + 7) & ~7;
+  const int per_col = fp32 ? fan_pieces<float>(kFanPieceRows) : fan_pieces<double>(kFanPieceRows);
+  const int c = std::max(2048, per_col * max_w);  // 32 KB of pieces, and never less than one tile
   if (cap) *cap = c;
-  return 16 + kFanMetaBytes + kFanVcap * sizeof(int16_t) + (size_t)c * (sizeof(int16_t) + es) +
-         (size_t)kFanPieceRows * max_w * es;
+  return 16 + kFanMetaBytes + kFanVcap * sizeof(int16_t) + (size_t)c * 16 + (size_t)kFanPieceRows * max_w * es;
 }
 
 // The fan-in mode has kernels of its own, so that the other modes' update

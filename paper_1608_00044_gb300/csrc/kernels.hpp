@@ -86,7 +86,9 @@ struct FactorArgs {
   double* inv;         // per panel: L11^{-1} (w x w, column-major, lower part)
   const int64_t* invoff;
   unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts,
-                             // [7] tensor-core update ns, [8] subtree-task ns, [9] subtree tasks
+                             // [7] tensor-core update ns, [8] subtree-task ns, [9] subtree tasks,
+                             // [10..12] fan-in gather ns (batch cuts, staging, adding), [13] its
+                             // batches, [14] its tiles
   unsigned long long* trace; // optional: per task id, start and end ns
 };
 

@@ -67,6 +67,9 @@ class Stats(ctypes.Structure):
         ("factor_subtree_ms", ctypes.c_double),
         ("factor_subtree_count", ctypes.c_int64),
         ("ir_gmres_iters", ctypes.c_int),
+        ("factor_gather_ms", ctypes.c_double * 3),
+        ("factor_gather_batches", ctypes.c_int64),
+        ("factor_gather_tiles", ctypes.c_int64),
     ]
 
     def as_dict(self):
