@@ -554,7 +554,7 @@ def run_ours(args):
     A, perm, b = _workload(args.workload)
     nrhs = b.shape[1]
     opt = spchol.default_options(precision=prec, max_width=args.width, relax_zeros=args.relax,
-                                 profile=1 if args.profile else 0)
+                                 deterministic=args.deterministic, profile=1 if args.profile else 0)
     h = spchol.analyze(A.n, A.colptr, A.rowind, perm, opt)
     st0 = spchol.stats(h)
     flops = st0["flops"]
@@ -666,6 +666,7 @@ def run_ours(args):
         "config": {"workload": f"{args.workload}: {_describe(A)}, n={A.n}, nnz(lower)={A.nnz}, "
                                f"geometric ND, relax {args.relax} zeros/col, {nrhs} RHS",
                    "max_width": args.width, "relax_zeros": args.relax, "precision": args.precision, "nrhs": nrhs,
+                   "order": ["dynamic", "static (target, source) chains", "fan-in buffers"][args.deterministic],
                    "l2": "inputs larger than L2 (value pool %.2f GB)" % (st0["footprint_bytes"] / 1e9),
                    "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU"},
         "fp64_peak_frac": value / peak_fp64,
@@ -678,8 +679,8 @@ def run_ours(args):
         "nnz_l": st0["nnz_l"],
         "roofline": {"bound": "alu", "achieved": achieved, "peak": peak_fp64, "unit": UNIT,
                      "frac": achieved / peak_fp64,
-                     "traffic": _measured_traffic("factor_kernel<double, 0>")
-                     if args.precision == "fp64" and args.workload == "lap3d_64" else None,
+                     "traffic": _measured_traffic("factor_kernel<double, 0, false>")
+                     if args.precision == "fp64" and args.workload == "lap3d_64" and args.deterministic == 0 else None,
                      "kernel": "factor_kernel<double> (persistent; includes assembly)",
                      "peak_note": "derived: 152 SMs x 2 DFMA/clk x 2 flop x max SM clock (NVIDIA's 1.25 TFLOP/s FP64 "
                                   "figure); the probe's measured DFMA rate is in peak_measured",
@@ -732,6 +733,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end loop")
     ap.add_argument("--profile", action="store_true", help="time every task inside the persistent kernels")
+    ap.add_argument("--deterministic", type=int, default=0, choices=[0, 1, 2],
+                    help="order of the headline factorization: 0 dynamic, 1 static chains, 2 fan-in buffers")
     ap.add_argument("--no-rows", action="store_true", help="skip the mixed-precision, batch and serving rows")
     ap.add_argument("--measure-peaks", action="store_true", help="run the DFMA / DMMA / FFMA throughput probe")
     ap.add_argument("--serve-full", action="store_true", help="serving row with 2000 requests at 4 rates")
