@@ -89,6 +89,9 @@ struct spchol_handle_s {
   // fan-in solves: Plan::st_zf and friends, and the tiles' buffers for up to
   // fan_nrhs right-hand sides
   int64_t *d_st_zf = nullptr, *d_st_zb = nullptr, *d_st_roff = nullptr;
+  // fan-in gather tasks: Plan::gat_first and friends, and the live counters
+  int32_t *d_gat_first = nullptr, *d_gat_pc = nullptr, *d_pc_owner = nullptr, *d_gdiag0 = nullptr,
+          *d_tdep0 = nullptr, *d_gdiag = nullptr, *d_tdep = nullptr;
   int32_t* d_rt_rng = nullptr;
   double *d_zf = nullptr, *d_zb = nullptr;
   int fan_nrhs = 0;
@@ -262,7 +265,11 @@ int setup_device(spchol_handle_t h) {
          o_fanp = fan ? r64(P.fan_ptr.size()) : 0,
          o_fane = fan ? A.reserve(std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanEnt)) : 0,
          o_stzf = fan ? r64(P.st_zf.size()) : 0, o_stzb = fan ? r64(P.st_zb.size()) : 0,
-         o_stro = fan ? r64(P.st_roff.size()) : 0, o_rtrng = fan ? r32(P.rt_rng.size()) : 0;
+         o_stro = fan ? r64(P.st_roff.size()) : 0, o_rtrng = fan ? r32(P.rt_rng.size()) : 0,
+         o_gatf = fan ? r32(P.gat_first.size()) : 0, o_gatp = fan ? r32(P.gat_pc.size()) : 0,
+         o_pco = fan ? r32(P.pc_owner.size()) : 0, o_gd0 = fan ? r32(P.gdiag0.size()) : 0,
+         o_td0 = fan ? r32(P.tdep0.size()) : 0, o_gd = fan ? r32(P.gdiag0.size()) : 0,
+         o_td = fan ? r32(P.tdep0.size()) : 0;
   const int ring_n = std::max(P.n_factor_tasks, P.n_solve_tasks);
   size_t o_ring = r32(ring_n), o_ctrl = r32(kCtrlWords);
   size_t o_prof = A.reserve(24 * sizeof(unsigned long long));
@@ -371,6 +378,13 @@ int setup_device(spchol_handle_t h) {
     h->d_st_zb = (int64_t*)(b + o_stzb);
     h->d_st_roff = (int64_t*)(b + o_stro);
     h->d_rt_rng = (int32_t*)(b + o_rtrng);
+    h->d_gat_first = (int32_t*)(b + o_gatf);
+    h->d_gat_pc = (int32_t*)(b + o_gatp);
+    h->d_pc_owner = (int32_t*)(b + o_pco);
+    h->d_gdiag0 = (int32_t*)(b + o_gd0);
+    h->d_tdep0 = (int32_t*)(b + o_td0);
+    h->d_gdiag = (int32_t*)(b + o_gd);
+    h->d_tdep = (int32_t*)(b + o_td);
   }
   h->d_perm = (int32_t*)(b + o_perm);
   h->d_ring = (int*)(b + o_ring);
@@ -417,7 +431,10 @@ int setup_device(spchol_handle_t h) {
   if (fan && ((rc = upload(h, h->d_fan_off, P.fan_off)) || (rc = upload(h, h->d_fan_task, P.fan_task)) ||
               (rc = upload(h, h->d_fan_ptr, P.fan_ptr)) || (rc = upload(h, h->d_fan_ent, P.fan_ent)) ||
               (rc = upload(h, h->d_st_zf, P.st_zf)) || (rc = upload(h, h->d_st_zb, P.st_zb)) ||
-              (rc = upload(h, h->d_st_roff, P.st_roff)) || (rc = upload(h, h->d_rt_rng, P.rt_rng))))
+              (rc = upload(h, h->d_st_roff, P.st_roff)) || (rc = upload(h, h->d_rt_rng, P.rt_rng)) ||
+              (rc = upload(h, h->d_gat_first, P.gat_first)) || (rc = upload(h, h->d_gat_pc, P.gat_pc)) ||
+              (rc = upload(h, h->d_pc_owner, P.pc_owner)) || (rc = upload(h, h->d_gdiag0, P.gdiag0)) ||
+              (rc = upload(h, h->d_tdep0, P.tdep0))))
     return rc;
   const size_t esz = h->fp32 ? sizeof(float) : sizeof(double);
   if (fan) {  // never read before written: no initialisation
@@ -581,6 +598,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
                        P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st, nullptr, nullptr, 0,
                        /*seeds_hi=*/1));
   FactorArgs a{};
+  a.gat0 = INT_MAX;  // no gather tasks outside the fan-in mode
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
   a.trsm_first = h->d_trsm_first;
   a.ntrsm = h->d_ntrsm;
@@ -617,6 +635,16 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
     a.fan_task = h->d_fan_task;
     a.fan_ptr = h->d_fan_ptr;
     a.fan_rec = h->d_fan_rec;
+    CU(cudaMemcpyAsync(h->d_gdiag, h->d_gdiag0, (size_t)P.ns * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    if (P.n_trsm > 0)
+      CU(cudaMemcpyAsync(h->d_tdep, h->d_tdep0, (size_t)P.n_trsm * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+    a.gat0 = P.ns + P.n_trsm + P.n_u + P.n_sub;
+    a.gat_first = h->d_gat_first;
+    a.gat_pc = h->d_gat_pc;
+    a.pc_owner = h->d_pc_owner;
+    a.gdiag0 = h->d_gdiag0;
+    a.gdiag = h->d_gdiag;
+    a.tdep = h->d_tdep;
     a.fan_cap = h->fan_cap;
   }
   a.ring = h->d_ring;

@@ -86,7 +86,7 @@ __device__ __forceinline__ double pivot_recip(double d) {
   return 1.0 / d;
 }
 
-template <typename T>
+template <typename T, bool FAN>
 __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared& sh, bool skip, bool release = true) {
   const int tid = threadIdx.x;
   const int warp = tid >> 5, lane = tid & 31;
@@ -178,7 +178,14 @@ __device__ void task_potrf(const FactorArgs& a, int s, double* sm, FactorShared&
       for (int i = j + lane; i < w; i += 32) P[i + (size_t)j * ld] = (T)sm[i + j * w];
   }
   publish_cta_writes();
-  if (release) ring2_push_range(rings_of(a), true, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+  if (FAN && release) {  // fan-in mode: a panel-solve tile also waits for its rows' gathers
+    for (int k = tid; k < a.ntrsm[s]; k += blockDim.x) {
+      const int kt = a.trsm_first[s] + k;
+      if (atom_add_acqrel(&a.tdep[kt], -1) == 1) ring2_push_one(rings_of(a), true, a.pv.ns + kt);
+    }
+  } else if (release) {
+    ring2_push_range(rings_of(a), true, a.pv.ns + a.trsm_first[s], a.ntrsm[s], &sh.base);
+  }
   if (!skip && ok) {
     // L11^{-1} for the solves, off the critical path (the panel-solve tiles are
     // already released).  X = L11^{-1} by right-looking forward substitution
@@ -399,6 +406,26 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
     } else {
       ring2_push_range(q, true, first, nhi, &sh.base);
       ring2_push_range(q, false, first + nhi, a.nu[s] - nhi, &sh.base);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- an update has landed
+// Count down the updates still to land in target panel t; the last one makes
+// the panel's diagonal task ready -- in the fan-in mode its gather tasks, and
+// the diagonal task too when none of them holds rows of its diagonal block.
+// Whole CTA (the fan-in mode pushes its gathers together).
+template <bool FAN>
+__device__ __forceinline__ void target_update_done(const FactorArgs& a, int t, FactorShared& sh, bool release) {
+  if constexpr (!FAN) {
+    if (release && threadIdx.x == 0 && atom_add_acqrel(&a.dep_f[t], -1) == 1) ring2_push_one(rings_of(a), true, t);
+  } else {
+    if (threadIdx.x == 0) sh.flag = release && atom_add_acqrel(&a.dep_f[t], -1) == 1;
+    __syncthreads();
+    if (sh.flag) {
+      const int g0 = a.gat_first[t], g1 = a.gat_first[t + 1];
+      ring2_push_range(rings_of(a), true, a.gat0 + g0, g1 - g0, &sh.base);
+      if (threadIdx.x == 0 && a.gdiag0[t] == 0) ring2_push_one(rings_of(a), true, t);
     }
   }
 }
@@ -706,11 +733,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     }
   }
   publish_cta_writes();
-  if (release && tid == 0) {  // not for a target inside the running subtree task
-    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      ring2_push_one(rings_of(a), true, t);
-    }
-  }
+  target_update_done<FAN>(a, t, sh, release);  // not for a target inside the running subtree task
 }
 
 // ---------------------------------------------------------------- UPD on tensor cores (FP32 panels)
@@ -870,11 +893,7 @@ __device__ void task_update_tc(const FactorArgs& a, const UTask u, unsigned char
     }
   }
   publish_cta_writes();
-  if (release && tid == 0) {  // not for a target inside the running subtree task
-    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      ring2_push_one(rings_of(a), true, t);
-    }
-  }
+  target_update_done<FAN>(a, t, sh, release);  // not for a target inside the running subtree task
 }
 
 // ---------------------------------------------------------------- UPD, FP64 on BF16 tensor cores
@@ -1063,11 +1082,7 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
     }
   }
   publish_cta_writes();
-  if (release && tid == 0) {  // not for a target inside the running subtree task
-    if (atom_add_acqrel(&a.dep_f[t], -1) == 1) {
-      ring2_push_one(rings_of(a), true, t);
-    }
-  }
+  target_update_done<FAN>(a, t, sh, release);  // not for a target inside the running subtree task
 }
 
 // ---------------------------------------------------------------- fan-in gather
@@ -1374,7 +1389,7 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
           tprof[10] += t1 - t0;
           tprof[11] = t1;
         }
-        if (sh.task >= sub0) {
+        if (sh.task >= sub0 && (!FAN || sh.task < a.gat0)) {
           const int k = sh.task - sub0;
           cur_task = sh.task;
           cur_lo = a.sub_lo[k];
@@ -1427,6 +1442,10 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
           step_kind = 1;
           step_s = a.trsm_sn[kt];
           step_i = kt - a.trsm_first[step_s];
+        } else if (FAN && task >= a.gat0) {
+          step_kind = 4;  // a gather task (fan-in mode)
+          step_s = -1;
+          step_i = task - a.gat0;
         } else {
           step_kind = 3;  // an update tile by its global index
           step_s = -1;
@@ -1441,20 +1460,34 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
     const int kind = step_kind, s = step_s, si = step_i;
     const bool release = step_release != 0;
     int type;
-    if (FAN && !skip && kind <= 1) {
-      // fan-in mode: the buffered updates of the rows this diagonal or
-      // panel-solve task factors or solves, first
-      const int w = a.pv.fcol[s + 1] - a.pv.fcol[s], tr = a.trsm_rows_of[s];
-      const int r0 = kind == 0 ? 0 : w + si * tr;
-      const int r1 = kind == 0 ? w : min(a.pv.nrows[s], r0 + tr);
-      const int pc0 = a.fan_task[kind == 0 ? s : a.pv.ns + a.trsm_first[s] + si];
-      for (int m = 0; r0 + m * kFanPieceRows < r1; ++m)
-        fanin_gather<T>(a, s, pc0 + m, r0 + m * kFanPieceRows, min(kFanPieceRows, r1 - r0 - m * kFanPieceRows),
-                        smem_raw);
-    }
-    if (kind == 0) {
+    if (FAN && kind == 4) {
+      // fan-in mode: a gather task adds the buffered updates of one row piece
+      // of a panel, then counts down the task that owns those rows
       type = 0;
-      task_potrf<T>(a, s, smd, sh, skip, release);
+      const int pc = a.gat_pc[si], o = a.pc_owner[pc];
+      const int t = o < a.pv.ns ? o : a.trsm_sn[o - a.pv.ns];
+      const int w = a.pv.fcol[t + 1] - a.pv.fcol[t];
+      int p0, p1;
+      if (o < a.pv.ns) {
+        p0 = (pc - a.fan_task[t]) * kFanPieceRows;
+        p1 = min(w, p0 + kFanPieceRows);
+      } else {
+        const int tr = a.trsm_rows_of[t], r0 = w + (o - a.pv.ns - a.trsm_first[t]) * tr;
+        p0 = r0 + (pc - a.fan_task[o]) * kFanPieceRows;
+        p1 = min(min(a.pv.nrows[t], r0 + tr), p0 + kFanPieceRows);
+      }
+      if (!skip) fanin_gather<T>(a, t, pc, p0, p1 - p0, smem_raw);
+      publish_cta_writes();
+      if (threadIdx.x == 0) {
+        if (o < a.pv.ns) {
+          if (atom_add_acqrel(&a.gdiag[t], -1) == 1) ring2_push_one(rings_of(a), true, t);
+        } else if (atom_add_acqrel(&a.tdep[o - a.pv.ns], -1) == 1) {
+          ring2_push_one(rings_of(a), true, o);
+        }
+      }
+    } else if (kind == 0) {
+      type = 0;
+      task_potrf<T, FAN>(a, s, smd, sh, skip, release);
     } else if (kind == 1) {
       type = 1;
       task_trsm<T, MODE>(a, s, si, smd, sh, skip, release);

@@ -96,8 +96,6 @@ struct Sim {
   void potrf(int s) {
     const int w = width(s), ld = P.ld[s], f = P.fcol[s];
     double* A = panel(s);
-    if (P.params.fanin) gather(s, P.fan_task[s], 0, w);
-    if (info != 0) return;
     for (int j = 0; j < w; ++j) {
       double d = A[j + (size_t)j * ld];
       if (!(d > 0.0)) {
@@ -115,8 +113,6 @@ struct Sim {
     const int w = width(s), ld = P.ld[s], r = P.nrows[s];
     const int row0 = w + k * P.trsm_rows[s], cnt = std::min(P.trsm_rows[s], r - row0);
     double* A = panel(s);
-    if (P.params.fanin) gather(s, P.fan_task[P.ns + P.trsm_first[s] + k], row0, row0 + cnt);
-    if (info != 0) return;
     for (int i = row0; i < row0 + cnt; ++i)
       for (int j = 0; j < w; ++j) {
         double x = A[i + (size_t)j * ld];
@@ -277,6 +273,9 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
   const bool fan = P.params.fanin;
   const bool det = P.params.deterministic && !fan;
   std::vector<int> udep(P.u_dep0.begin(), P.u_dep0.end());
+  // fan-in mode: gather tasks (Plan::gat_first) and the counters they feed
+  std::vector<int> gd(P.gdiag0.begin(), P.gdiag0.end()), td(P.tdep0.begin(), P.tdep0.end());
+  const int gat0 = ns + P.n_trsm + P.n_u + P.n_sub;  // first gather task id
   const int u0 = ns + P.n_trsm;  // first update tile id
   std::vector<char> ran(P.n_task_ids, 0);
   Ready hi, lo;
@@ -293,6 +292,16 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
     }
   };
   const int sub0 = ns + P.n_trsm + P.n_u;  // first subtree task id
+  // the last update into panel t has landed: its gathers (fan-in mode) and, when
+  // none holds rows of its diagonal block, its diagonal task
+  auto landed = [&](int t) {
+    if (fan) {
+      for (int g = P.gat_first[t]; g < P.gat_first[t + 1]; ++g) push(true, gat0 + g);
+      if (P.gdiag0[t] == 0) push(true, t);
+    } else {
+      push(true, t);
+    }
+  };
   for (int k = 0; k < P.n_sub; ++k) push(true, sub0 + k);
   for (int s = 0; s < ns; ++s)
     if (dep[s] == 0 && P.in_sub[s] < 0) push(true, s);
@@ -305,7 +314,28 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
     ran[task] = 1;
     ++done;
     const bool skip = sim.info != 0;
-    if (task >= sub0) {  // subtree task: its panels in order; counters only for targets outside
+    if (task >= gat0) {  // gather task (fan-in mode): one row piece of a panel
+      const int pc = P.gat_pc[task - gat0], o = P.pc_owner[pc];
+      const int t = o < ns ? o : P.trsm_sn[o - ns];
+      const int w = sim.width(t);
+      int p0, p1;
+      if (o < ns) {
+        p0 = (pc - P.fan_task[t]) * kFanPieceRows;
+        p1 = std::min(w, p0 + kFanPieceRows);
+      } else {
+        const int k = o - ns - P.trsm_first[t], tr = P.trsm_rows[t], r0 = w + k * tr;
+        p0 = r0 + (pc - P.fan_task[o]) * kFanPieceRows;
+        p1 = std::min(std::min(P.nrows[t], r0 + tr), p0 + kFanPieceRows);
+      }
+      if (!skip) sim.gather(t, pc, p0, p1);
+      if (o < ns) {
+        if (--gd[t] < 0) return SPCHOL_EINTERNAL;
+        if (gd[t] == 0) push(true, t);
+      } else {
+        if (--td[o - ns] < 0) return SPCHOL_EINTERNAL;
+        if (td[o - ns] == 0) push(true, o);
+      }
+    } else if (task >= sub0) {  // subtree task: its panels in order; counters only for targets outside
       const int k = task - sub0, lo = P.sub_lo[k], hi = P.sub_hi[k];
       for (int s = lo; s <= hi; ++s) {
         if (P.in_sub[s] != k) return SPCHOL_EINTERNAL;
@@ -318,14 +348,21 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           if (u.t > hi) {
             if (P.in_sub[u.t] >= 0) return SPCHOL_EINTERNAL;  // an outside target is never in another subtree
             if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
-            if (dep[u.t] == 0) push(true, u.t);
+            if (dep[u.t] == 0) landed(u.t);
           }
         }
       }
     } else if (task < ns) {
       if (P.in_sub[task] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.potrf(task);
-      for (int k = 0; k < P.ntrsm[task]; ++k) push(true, ns + P.trsm_first[task] + k);
+      for (int k = 0; k < P.ntrsm[task]; ++k) {
+        const int kt = P.trsm_first[task] + k;
+        if (fan && --td[kt] != 0) {  // also waits for its rows' gathers
+          if (td[kt] < 0) return SPCHOL_EINTERNAL;
+          continue;
+        }
+        push(true, ns + kt);
+      }
     } else if (task < ns + P.n_trsm) {
       const int kt = task - ns, s = P.trsm_sn[kt];
       if (P.in_sub[s] >= 0) return SPCHOL_EINTERNAL;
@@ -346,7 +383,7 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       if (P.in_sub[u.s] >= 0) return SPCHOL_EINTERNAL;
       if (!skip) sim.update(u, ui);
       if (--dep[u.t] < 0) return SPCHOL_EINTERNAL;
-      if (dep[u.t] == 0) push(true, u.t);
+      if (dep[u.t] == 0) landed(u.t);
       if (uchain && P.u_next[ui] >= 0) {
         const int nx = P.u_next[ui], sx = P.ut[nx].s;
         if (--udep[nx] < 0) return SPCHOL_EINTERNAL;

@@ -79,6 +79,16 @@ struct FactorArgs {
   const int64_t* fan_ptr;
   const FanRec* fan_rec;
   int32_t fan_cap;
+  // its gather tasks (Plan::gat_first): ids gat0 + g (INT32_MAX: none), each
+  // panel's range, their pieces, the pieces' owners, the diagonal tasks'
+  // initial and live gather counts and the panel-solve tiles' live counters
+  int32_t gat0;
+  const int32_t* gat_first;
+  const int32_t* gat_pc;
+  const int32_t* pc_owner;
+  const int32_t* gdiag0;
+  int32_t* gdiag;
+  int32_t* tdep;
   int* ring;
   int* ctrl;
   int64_t budget_ns;

@@ -160,6 +160,15 @@ struct Plan {
   // the row lists), and its backward diagonal task adds its own tiles'
   // backward buffers in tile order: every entry of the solution receives its
   // updates in one fixed order -- the order of the static chains.
+  // Gather tasks (fan-in mode): one per row piece that receives updates, task
+  // id ns + n_trsm + n_u + n_sub + g for g in [gat_first[t], gat_first[t + 1])
+  // of panel t, piece gat_pc[g], all made ready when the panel's last update
+  // tile lands.  pc_owner[piece]: the task whose rows it holds (t: the
+  // diagonal task, ns + k: panel-solve tile k).  The diagonal task waits for
+  // its gathers (gdiag0[t] of them; none: it is ready with the updates), each
+  // panel-solve tile for the diagonal task and its own gathers (tdep0[k]).
+  std::vector<int32_t> gat_first, gat_pc, pc_owner, gdiag0, tdep0;
+  int32_t n_gat = 0;
   std::vector<int64_t> st_zf, st_zb;  // n_st + 1
   std::vector<int64_t> st_roff;       // n_st
   std::vector<int32_t> rt_rng;        // like rt_tile

@@ -502,6 +502,48 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       P.n_factor_tasks += 1 + P.ntrsm[s] + P.nu[s];
       P.n_hi_tasks += 1 + P.ntrsm[s] + P.nu_hi[s];
     }
+  // ---- gather tasks of the fan-in mode (see Plan::gat_first) ---------------------
+  P.gat_first.clear();
+  P.gat_pc.clear();
+  P.pc_owner.clear();
+  P.gdiag0.clear();
+  P.tdep0.clear();
+  P.n_gat = 0;
+  if (prm.fanin) {
+    const int32_t npc = (int32_t)P.fan_ptr.size() - 1;
+    auto npieces = [](int32_t rows) { return (rows + kFanPieceRows - 1) / kFanPieceRows; };
+    P.pc_owner.assign(npc, -1);
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s], tr = P.trsm_rows[s];
+      for (int32_t m = 0; m < npieces(w); ++m) P.pc_owner[P.fan_task[s] + m] = s;
+      for (int32_t k = 0; k < P.ntrsm[s]; ++k) {
+        const int32_t kt = P.trsm_first[s] + k;
+        for (int32_t m = 0; m < npieces(std::min(tr, r - w - k * tr)); ++m) P.pc_owner[P.fan_task[ns + kt] + m] = ns + kt;
+      }
+    }
+    P.gat_first.assign(ns + 1, 0);
+    P.gdiag0.assign(ns, 0);
+    P.tdep0.assign(P.n_trsm, 1);
+    for (int32_t s = 0; s < ns; ++s) {
+      // a panel's pieces are numbered consecutively, from its diagonal block's
+      P.gat_first[s] = (int32_t)P.gat_pc.size();
+      const int32_t pc_end = s + 1 < ns ? P.fan_task[s + 1] : npc;
+      for (int32_t pc = P.fan_task[s]; pc < pc_end; ++pc)
+        if (P.fan_ptr[pc + 1] > P.fan_ptr[pc]) {
+          P.gat_pc.push_back(pc);
+          const int32_t o = P.pc_owner[pc];
+          if (o < ns)
+            P.gdiag0[s]++;
+          else
+            P.tdep0[o - ns]++;
+        }
+    }
+    P.gat_first[ns] = (int32_t)P.gat_pc.size();
+    P.n_gat = (int32_t)P.gat_pc.size();
+    P.n_task_ids += P.n_gat;
+    P.n_factor_tasks += P.n_gat;
+    P.n_hi_tasks += P.n_gat;
+  }
 
   // ---- solve tasks ------------------------------------------------------------
   // near the root (the critical path of both sweeps) the tiles are shorter
