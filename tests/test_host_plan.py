@@ -338,6 +338,10 @@ def test_fanin_gather_lists(name, W):
         c.sort()
         assert c[0][0] == 0 and c[-1][1] == ut[u, 5]
         assert all(a[1] == b_[0] for a, b_ in zip(c, c[1:]))
+    # one gather task per piece that receives updates, on top of the static
+    # order's tasks (which has no subtree tasks either)
+    static = _plan(A, perm, deterministic=1, max_width=W).scalars()["factor_tasks"]
+    assert P.scalars()["factor_tasks"] == static + int(np.count_nonzero(np.diff(ptr)))
 
 
 @pytest.mark.parametrize("name,W", [("diff3d_8", 16), ("lap3d_12", 64), ("lap2d_24", 128)])
