@@ -146,6 +146,7 @@ struct SolveArgs {
   const int64_t* st_zb;
   const int64_t* st_roff;
   const int32_t* rt_rng;
+  const Plan::SolveFanRec* rt_rec;
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
   unsigned long long* trace; // optional: per task id, start and end ns
 };

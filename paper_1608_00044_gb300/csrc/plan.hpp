@@ -170,6 +170,15 @@ struct Plan {
   std::vector<int32_t> gat_first, gat_pc, pc_owner, gdiag0, tdep0;
   int32_t n_gat = 0;
   std::vector<int64_t> st_zf, st_zb;  // n_st + 1
+  // the forward gather's record of each rt_tile entry: the tile's buffer (in
+  // rows: st_zf), its first listed row's place in the row lists, the tile's
+  // rows, its first listed row and how many are listed
+  struct SolveFanRec {
+    int64_t z, ro;
+    int32_t cnt;
+    int16_t i0, ni;
+  };
+  std::vector<SolveFanRec> rt_rec;
   std::vector<int64_t> st_roff;       // n_st
   std::vector<int32_t> rt_rng;        // like rt_tile
 

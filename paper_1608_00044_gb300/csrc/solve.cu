@@ -358,68 +358,121 @@ __device__ __forceinline__ void oz_stage_ys(const SolveArgs& a, const OzBuf& b, 
 // Fan-in mode (the fan-in family of Section II-C, restated for the solves):
 // the tiles store their products in private buffers and the diagonal tasks
 // add them, in tile order, into the right-hand sides they stage in shared
-// memory.  Forward: the tiles with rows in the panel's columns, kSolveFanBatch
-// list entries at a time -- their rows are mapped to the panel's columns in
-// shared memory, then each thread adds, for the (column, right-hand side)
-// entries it owns, the batch's values in order (eight loads in flight).
-// Backward: the panel's own tiles, each thread summing its entries' values
-// over the tiles in order.
+// memory.  Forward: the tiles with rows in the panel's columns, up to
+// kSolveFanBatch list entries at a time: warp 0 cuts the batch where its
+// values would overflow the staging area (the entries' records were fetched
+// during the previous batch); all threads load the batch's values (eight
+// loads in flight each) and map each entry's rows to the panel's columns;
+// then each thread adds, for the (column, right-hand side) entries it owns,
+// the batch's values in order from shared memory.  Backward: the panel's own
+// tiles, each thread summing its entries' values over the tiles in order.
+using SolveFanRec = Plan::SolveFanRec;
 constexpr int kSolveFanBatch = 32;
+constexpr int kSolveFanVals = 2048;  // staged values per batch (an entry has at most 64 x 8)
 struct SolveFanMeta {
-  long long zo, ro;  // the tile's buffer (times nrhs) and its first row in the row lists
-  int cnt, rng;      // its rows; those in the panel, i0 | i1 << 16
+  long long zo, ro;  // the entry's first value of this pass in the buffer; its first row in the row lists
+  int cnt, ni, pre;  // the tile's rows; the entry's rows; its first staged value
+  float inv_ni;      // 1 / ni: value index -> (row, right-hand side) without a division
 };
 constexpr size_t solve_fan_smem_bytes(int max_w) {
-  return kSolveFanBatch * sizeof(SolveFanMeta) + (size_t)kSolveFanBatch * max_w * sizeof(int16_t) + 16;
+  return kSolveFanBatch * sizeof(SolveFanMeta) + 16 + (((size_t)kSolveFanBatch * max_w * sizeof(int16_t) + 15) & ~size_t(15)) +
+         kSolveFanVals * sizeof(double);
 }
 
 __device__ void fwd_gather(const SolveArgs& a, int s, int f, int w, double* Ys, int r0, int nrc, unsigned char* ex) {
   const int tid = threadIdx.x, nt = blockDim.x;
   SolveFanMeta* meta = reinterpret_cast<SolveFanMeta*>(ex);
-  int16_t* inv = reinterpret_cast<int16_t*>(meta + kSolveFanBatch);  // [batch entry][column]: its row, or -1
+  int* scal = reinterpret_cast<int*>(meta + kSolveFanBatch);  // entries and values of the batch
+  int16_t* inv = reinterpret_cast<int16_t*>(scal + 4);        // [batch entry][column]: its row, or -1
+  double* Bv = reinterpret_cast<double*>(reinterpret_cast<unsigned char*>(inv) +
+                                         (((size_t)kSolveFanBatch * w * sizeof(int16_t) + 15) & ~size_t(15)));
   const int e0 = a.rt_ptr[s], e1 = a.rt_ptr[s + 1];
-  for (int eb = e1; eb > e0; eb -= kSolveFanBatch) {  // ascending tile order: the list from its end
-    const int nb = min(kSolveFanBatch, eb - e0);
+  // ascending tile order: the list from its end; warp 0 holds the next window's records
+  SolveFanRec rec{};
+  if (tid < 32 && e1 - 1 - tid >= e0) rec = a.rt_rec[e1 - 1 - tid];
+  for (int eb = e1; eb > e0;) {
     __syncthreads();  // the right-hand sides are staged, or the previous batch is added
-    if (tid < nb) {
-      const int e = eb - 1 - tid, tile = a.rt_tile[e];
-      SolveFanMeta m;
-      m.zo = a.st_zf[tile] * a.nrhs;
-      m.ro = a.st_roff[tile];
-      m.cnt = (int)(a.st_zf[tile + 1] - a.st_zf[tile]);
-      m.rng = a.rt_rng[e];
-      meta[tid] = m;
+    for (int idx = tid; idx < kSolveFanBatch * w; idx += nt) inv[idx] = -1;
+    if (tid < 32) {
+      const bool have = eb - 1 - tid >= e0;
+      const int n = have ? rec.ni * nrc : 0;
+      int in = n;
+#pragma unroll
+      for (int o = 1; o < 32; o <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, in, o);
+        if (tid >= o) in += y;
+      }
+      const int nb = max(1, __popc(__ballot_sync(0xffffffffu, have && in <= kSolveFanVals)));
+      if (tid < nb) {
+        SolveFanMeta m;
+        m.zo = rec.z * a.nrhs + rec.i0 + (long long)r0 * rec.cnt;
+        m.ro = rec.ro;
+        m.cnt = rec.cnt;
+        m.ni = rec.ni;
+        m.pre = in - n;
+        m.inv_ni = 1.0f / (float)max(1, (int)rec.ni);
+        meta[tid] = m;
+      }
+      if (tid == nb - 1) {
+        scal[0] = nb;
+        scal[1] = in;
+      }
+      rec = SolveFanRec{};
+      if (eb - nb - 1 - tid >= e0) rec = a.rt_rec[eb - nb - 1 - tid];  // in flight during this batch
     }
-    for (int idx = tid; idx < nb * w; idx += nt) inv[idx] = -1;
     __syncthreads();
-    for (int idx = tid; idx < nb * w; idx += nt) {  // an entry has at most w rows in the panel
-      const int b = idx / w, i = (meta[b].rng & 0xffff) + idx % w;
-      if (i < (meta[b].rng >> 16)) {
+    const int nb = scal[0];
+    int total = scal[1];
+    if (total > kSolveFanVals) {  // cannot happen for a consistent plan
+      if (tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      total = 0;
+    }
+    // the entries' rows mapped to the panel's columns ...
+    for (int idx = tid; idx < nb * w; idx += nt) {
+      const int b = idx / w, i = idx - b * w;
+      if (i < meta[b].ni) {
         const int c = __ldg(a.pv.rows + meta[b].ro + i) - f;
         if (c >= 0 && c < w)
           inv[b * w + c] = (int16_t)i;
         else
-          atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);  // cannot happen for a consistent plan
+          atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      }
+    }
+    // ... and their values, eight loads in flight per thread
+    for (int v0 = 0; v0 < total; v0 += 8 * nt) {
+      double v[8];
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = v0 + u * nt + tid;
+        v[u] = 0.0;
+        if (idx < total) {
+          int b = 0;
+#pragma unroll
+          for (int h = kSolveFanBatch / 2; h > 0; h >>= 1)
+            if (b + h < nb && meta[b + h].pre <= idx) b += h;
+          const int lv = idx - meta[b].pre;
+          // lv / ni exactly: lv < 2^9 and ni <= 64 leave a margin of 1 / 128 for rounding
+          const int r = (int)(((float)lv + 0.5f) * meta[b].inv_ni), i = lv - r * meta[b].ni;
+          v[u] = ldcg(a.zf + meta[b].zo + i + (size_t)r * meta[b].cnt);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 8; ++u) {
+        const int idx = v0 + u * nt + tid;
+        if (idx < total) Bv[idx] = v[u];
       }
     }
     __syncthreads();
     for (int p = tid; p < w * nrc; p += nt) {
       const int c = p % w, r = p / w;
       double y = Ys[p];
-      for (int b0 = 0; b0 < nb; b0 += 8) {
-        double v[8];
-        int i[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          i[u] = b0 + u < nb ? inv[(b0 + u) * w + c] : -1;
-          v[u] = i[u] >= 0 ? ldcg(a.zf + meta[b0 + u].zo + i[u] + (size_t)(r0 + r) * meta[b0 + u].cnt) : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u)
-          if (i[u] >= 0) y += v[u];
+      for (int b = 0; b < nb; ++b) {
+        const int i = inv[b * w + c];
+        if (i >= 0) y += Bv[meta[b].pre + r * meta[b].ni + i];
       }
       Ys[p] = y;
     }
+    eb -= nb;
   }
   __syncthreads();
 }

@@ -639,6 +639,7 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.st_zf.clear();
   P.st_zb.clear();
   P.st_roff.clear();
+  P.rt_rec.clear();
   if (prm.fanin) {
     P.st_zf.assign(P.n_st + 1, 0);
     P.st_zb.assign(P.n_st + 1, 0);
@@ -651,6 +652,12 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
         P.st_zb[tile + 1] = P.st_zb[tile] + w;
         P.st_roff[tile] = P.rowoff[s] + r0;
       }
+    }
+    P.rt_rec.resize(P.rt_tile.size());
+    for (size_t e = 0; e < P.rt_tile.size(); ++e) {
+      const int32_t tile = P.rt_tile[e], i0 = P.rt_rng[e] & 0xffff, i1 = P.rt_rng[e] >> 16;
+      P.rt_rec[e] = Plan::SolveFanRec{P.st_zf[tile], P.st_roff[tile] + i0, (int32_t)(P.st_zf[tile + 1] - P.st_zf[tile]),
+                                       (int16_t)i0, (int16_t)(i1 - i0)};
     }
   }
   P.kid_ptr.assign(ns + 1, 0);
