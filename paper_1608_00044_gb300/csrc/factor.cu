@@ -1087,12 +1087,13 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
 
 // ---------------------------------------------------------------- fan-in gather
 // Deterministic fan-in mode (the fan-in family of Section II-C, restated for
-// one GPU): update tiles store their products in private buffers, and the task
-// that owns a piece of a target panel's rows (at most kFanPieceRows rows, all
-// columns) adds them in before it factors or solves those rows, tile after
-// tile in the piece's list order, so every entry of L receives its updates in
-// one fixed order whatever the schedule.  The piece sits in shared memory and
-// the list is consumed in batches of up to kFanBatch tiles:
+// one GPU): update tiles store their products in private buffers, and a
+// gather task per piece of a target panel's rows (at most kFanPieceRows rows,
+// all columns) adds them in, tile after tile in the piece's list order, before
+// the task that owns those rows factors or solves them; every entry of L thus
+// receives its updates in one fixed order whatever the schedule, and the
+// pieces of one panel are gathered in parallel.  The piece sits in shared
+// memory and the list is consumed in batches of up to kFanBatch tiles:
 //   1. warp 0 cuts the batch where its staged values would overflow the
 //      staging area (the records were fetched during the previous batch);
 //   2. all threads copy, for each column of each tile, the 16-byte pieces that
