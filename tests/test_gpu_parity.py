@@ -580,6 +580,26 @@ def test_factorization_captured_in_a_cuda_graph():
     spchol.destroy(h)
 
 
+def test_fanin_factorization_captured_in_a_cuda_graph():
+    """Fan-in mode through a captured graph: its counters are reset inside the
+    graph, so every replay gives bitwise the eager factor."""
+    A, perm, b = gridgen.workload("diff3d_10")
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(deterministic=2))
+    vals = torch.from_numpy(A.values).cuda()
+    assert spchol.factorize(h, vals) == 0
+    L0 = spchol.export_factor(h)[2]
+    g = _capture_factorization(h, vals)
+    for _ in range(3):
+        g.replay()
+        torch.cuda.synchronize()
+        assert spchol.factorize_status(h) == 0
+        assert np.array_equal(spchol.export_factor(h)[2], L0)
+    X = b.copy(order="F")
+    spchol.solve(h, X, A.n, b.shape[1])
+    assert oracle.berr(A, X, b) <= BERR_FP64
+    spchol.destroy(h)
+
+
 def test_batch_factorization_captured_in_a_cuda_graph():
     sides = [9, 20, 13, 31]
     mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=s) for s in sides]
