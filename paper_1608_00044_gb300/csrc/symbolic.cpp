@@ -94,20 +94,57 @@ void postorder(int64_t n, const std::vector<int32_t>& parent, std::vector<int64_
   }
 }
 
-// Column counts by marking the row subtrees: row i of L is the set of nodes on
-// the etree paths from each k with b_ik != 0 up to i.
+// Column counts without forming L (Gilbert, Ng and Peyton, "An efficient
+// algorithm to compute row and column counts for sparse Cholesky
+// factorization", SIAM J. Matrix Anal. Appl. 15, 1994), restated.  c_j is the
+// number of row subtrees T(i) (the union of the etree paths from each k with
+// b_ik != 0 up to i, and i itself) that contain j.  With the columns in
+// postorder, a weight per node -- +1 at each leaf of each T(i), -1 at the
+// least common ancestor of two consecutive leaves of the same T(i), -1 at
+// parent(i) for every row i -- sums over the subtree of j to exactly c_j.
+// Column j is a leaf of T(i) when no earlier column of row i lies in j's
+// subtree (the columns of j's subtree are first(j) .. j); the common
+// ancestors come from a disjoint-set forest in which every finished column
+// is joined to its parent (for columns p < j, the root of p's set is then the
+// least common ancestor of p and j).  O(nnz(A) alpha(n)); requires the
+// postorder numbering, which build_plan establishes first.
 void column_counts(int64_t n, const Pattern& B, const std::vector<int32_t>& parent,
                    std::vector<int64_t>& cc) {
-  cc.assign(n, 1);
-  std::vector<int32_t> mark(n, -1);
-  for (int64_t i = 0; i < n; ++i) {
-    mark[i] = (int32_t)i;
-    for (int64_t p = B.rp[i]; p < B.rp[i + 1]; ++p)
-      for (int32_t j = B.ri[p]; mark[j] != i; j = parent[j]) {
-        mark[j] = (int32_t)i;
-        cc[j]++;
-      }
+  std::vector<int32_t> first(n, -1), prevnz(n, -1), prevleaf(n, -1), anc(n);
+  cc.assign(n, 0);
+  for (int64_t j = 0; j < n; ++j)
+    for (int64_t k = j; k != -1 && first[k] == -1; k = parent[k]) first[k] = (int32_t)j;
+  for (int64_t j = 0; j < n; ++j) {
+    anc[j] = (int32_t)j;
+    if (parent[j] != -1) cc[parent[j]]--;
   }
+  auto find = [&](int32_t x) {
+    int32_t r = x;
+    while (anc[r] != r) r = anc[r];
+    while (anc[x] != r) {  // path compression
+      const int32_t nx = anc[x];
+      anc[x] = r;
+      x = nx;
+    }
+    return r;
+  };
+  // row i has a nonzero in column j <= i (columns visited in increasing order)
+  auto visit = [&](int32_t i, int32_t j) {
+    const bool leaf = first[j] > prevnz[i];
+    prevnz[i] = j;
+    if (!leaf) return;
+    cc[j]++;
+    if (prevleaf[i] != -1) cc[find(prevleaf[i])]--;
+    prevleaf[i] = j;
+  };
+  for (int64_t j = 0; j < n; ++j) {
+    visit((int32_t)j, (int32_t)j);  // the diagonal: T(j) contains j
+    for (int64_t p = B.cp[j]; p < B.cp[j + 1]; ++p)
+      if (B.ci[p] != j) visit(B.ci[p], (int32_t)j);
+    if (parent[j] != -1) anc[j] = parent[j];
+  }
+  for (int64_t j = 0; j < n; ++j)
+    if (parent[j] != -1) cc[parent[j]] += cc[j];
 }
 
 inline int64_t round4(int64_t x) { return (x + 3) & ~int64_t(3); }

@@ -32,6 +32,38 @@ def test_counts_and_etree_match_oracle(name, W):
     assert P.scalars()["nnz_l"] == f.nnzL
 
 
+@pytest.mark.parametrize("seed", range(8))
+def test_counts_on_random_patterns_match_oracle(seed):
+    """Column counts (computed without forming L) against the oracle's symbolic
+    elimination on random patterns: forests, dense blocks, isolated columns,
+    some diagonal entries absent from the pattern, random orderings."""
+    import scipy.sparse as sp
+
+    rng = np.random.default_rng(900 + seed)
+    n = int(rng.integers(1, 400))
+    M = sp.random(n, n, density=float(rng.uniform(0.0, 0.03)), random_state=rng, format="csc")
+    M = (M + M.T).tocsc()
+    if seed % 2 == 0:  # a dense block
+        k = int(rng.integers(1, min(n, 40) + 1))
+        o = int(rng.integers(0, n - k + 1))
+        D = sp.lil_matrix((n, n))
+        D[o:o + k, o:o + k] = 1.0
+        M = (M + D.tocsc()).tocsc()
+    d = np.ones(n)
+    if seed % 3 == 0:  # some diagonal entries absent
+        d[rng.random(n) < 0.2] = 0.0
+    M = (sp.tril(M, -1) + sp.diags(d)).tocsc()
+    M.eliminate_zeros()
+    M.sort_indices()
+    A = gridgen.CscLower(n, M.indptr.astype(np.int64), M.indices.astype(np.int32), np.ones(M.nnz))
+    P = _plan(A, rng.permutation(n), max_width=int(rng.choice([1, 16, 64])))
+    fperm = P.get(hp.PERM)
+    f = oracle.OracleFactor.from_csc(A, fperm)
+    parent, cc = f.structure()
+    assert np.array_equal(P.get(hp.COLCOUNT), cc)
+    assert np.array_equal(P.get(hp.ETREE), parent)
+
+
 def test_fig1_supernodes_without_amalgamation():
     n, a_pat, fill, blocks, edges = fig1.load()
     colptr, rowind, vals = fig1.spd_from_pattern(n, a_pat)
