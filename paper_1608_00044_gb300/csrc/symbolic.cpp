@@ -2,6 +2,7 @@
 // column counts, supernodes, relaxed amalgamation, width cap, row structures,
 // storage layout and the task graph.
 #include <algorithm>
+#include <iterator>
 #include <cstring>
 #include <numeric>
 
@@ -297,9 +298,10 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     }
   std::vector<std::vector<int32_t>> below(ns);
   std::vector<int32_t> mark(n, -1);
-  std::vector<int32_t> buf;
+  std::vector<int32_t> buf, tmp;
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t f = P.fcol[s], l = P.fcol[s + 1] - 1;
+    // B's own rows past the panel (a few per column), sorted ...
     buf.clear();
     for (int32_t j = f; j <= l; ++j)
       for (int64_t p = B.cp[j]; p < B.cp[j + 1]; ++p) {
@@ -309,14 +311,15 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
           buf.push_back(r);
         }
       }
-    for (int32_t c = kid_head[s]; c != -1; c = kid_next[c]) {
-      for (int32_t r : below[c])
-        if (r > l && mark[r] != s) {
-          mark[r] = s;
-          buf.push_back(r);
-        }
-    }
     std::sort(buf.begin(), buf.end());
+    // ... merged with each child's sorted list past the panel (linear merges)
+    for (int32_t c = kid_head[s]; c != -1; c = kid_next[c]) {
+      const std::vector<int32_t>& bc = below[c];
+      auto from = std::upper_bound(bc.begin(), bc.end(), l);
+      tmp.clear();
+      std::set_union(buf.begin(), buf.end(), from, bc.end(), std::back_inserter(tmp));
+      buf.swap(tmp);
+    }
     below[s] = buf;
     // a child's list is needed only by its parent
     for (int32_t c = kid_head[s]; c != -1; c = kid_next[c]) std::vector<int32_t>().swap(below[c]);
@@ -375,6 +378,29 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   P.trsm_sn.clear();
   P.ut.clear();
   P.n_rel = 0;
+  {
+    // the tile count first (the same walk), so that the tile list is built in
+    // place: millions of tiles on the large grids
+    int64_t nt = 0, ntr = 0;
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
+      const bool top = depth[s] < prm.top_depth;
+      const bool tc = prm.tc_min_width > 0 && w >= prm.tc_min_width;
+      const int TU = std::max(1, tc ? prm.tc_tile_rows : top ? std::min(prm.top_tile_rows, prm.tile_rows) : prm.tile_rows);
+      const int TR = std::max(1, top ? std::min(prm.top_trsm_rows, prm.trsm_rows) : prm.trsm_rows);
+      ntr += (r - w + TR - 1) / TR;
+      const int32_t* R = P.rows.data() + P.rowoff[s];
+      for (int32_t a = w; a < r;) {
+        const int32_t t = P.snode_of[R[a]];
+        int32_t e = a;
+        while (e < r && R[e] < P.fcol[t + 1]) ++e;
+        nt += (r - a + TU - 1) / TU;
+        a = e;
+      }
+    }
+    P.ut.reserve((size_t)nt);
+    P.trsm_sn.reserve((size_t)ntr);
+  }
   for (int32_t s = 0; s < ns; ++s) {
     const int32_t w = P.fcol[s + 1] - P.fcol[s], r = P.nrows[s];
     const int32_t nb = r - w;
