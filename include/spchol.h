@@ -59,7 +59,8 @@ extern "C" {
 #define SPCHOL_ENOCONV (-1004)  /* refinement did not reach ir_tol; X holds the best iterate */
 #define SPCHOL_ECUDA (-1005)    /* a CUDA runtime call failed */
 #define SPCHOL_EINTERNAL (-1006)/* a device-side consistency check failed */
-#define SPCHOL_ESCRATCH (-1007) /* spchol_solve_noalloc: n * nrhs too large for its fixed scratch */
+#define SPCHOL_ESCRATCH (-1007) /* spchol_solve_noalloc: n * nrhs (and, with deterministic = 2,
+                                   the solves' buffers) too large for its fixed scratch */
 
 /* Arithmetic of the factor. */
 #define SPCHOL_FP64 0  /* everything in FP64 */
@@ -97,11 +98,14 @@ typedef struct spchol_options {
                              fan-in family): every update tile stores its product in a private
                              buffer, and each panel adds the buffers into its rows in one fixed
                              (tile) order when it is factored, so the update tiles themselves
-                             run in any order.  Every entry receives its updates in the same
-                             order as with 1, so the results are bitwise those of 1, at a
-                             fraction of 1's time; the
-                             buffers cost (sum over update tiles of rows x columns) values of
-                             device memory, in footprint_bytes.  The solves run as with 1.
+                             run in any order; a panel's row pieces are gathered by tasks of
+                             their own, in parallel.  The solves aggregate the same way (each
+                             solve tile's product in a buffer, added by the diagonal tasks in
+                             tile order).  Every entry receives its updates in the same order
+                             as with 1, so the results are bitwise those of 1, at a fraction of
+                             1's time.  The factor's buffers cost (sum over update tiles of
+                             rows x columns) values of device memory, in footprint_bytes; the
+                             solves' (sum of solve tile rows + widths) x nrhs more.
                              0 (default): dynamic order, results equal up to rounding */
   int64_t wait_budget_ns; /* bound on any single device-side wait; default 2e9 (2 s) */
   int ir_max_iter;        /* mixed precision: refinement steps; default 10 */
