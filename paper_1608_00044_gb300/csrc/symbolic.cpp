@@ -491,15 +491,30 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     };
     std::vector<Item> items;
     items.reserve((size_t)P.n_u * 2);
+    int32_t hint_s = -1, hint_t = -1, hint = 0;  // the last position found for this (source, target)
     for (int32_t u = 0; u < P.n_u; ++u) {
       const UTask& U = P.ut[u];
       const int32_t* Rs = P.rows.data() + P.rowoff[U.s] + U.row0;
       const int32_t* Rt = P.rows.data() + P.rowoff[U.t];
       const int32_t rt = P.nrows[U.t];
+      if (U.s != hint_s || U.t != hint_t) {
+        hint_s = U.s;
+        hint_t = U.t;
+        hint = 0;
+      }
       for (int32_t i = 0; i < U.rowlen;) {
         // a tile's rows are rows of its target (the structure of L is closed
-        // under updates), so the search finds each exactly
-        const int32_t p = (int32_t)(std::lower_bound(Rt, Rt + rt, Rs[i]) - Rt);
+        // under updates), so the search finds each exactly; the rows of one
+        // (source, target) pair come in increasing order, so it gallops
+        // forward from the last position found
+        int32_t lo = hint, step = 1;
+        while (lo + step < rt && Rt[lo + step] < Rs[i]) {
+          lo += step;
+          step *= 2;
+        }
+        const int32_t p =
+            (int32_t)(std::lower_bound(Rt + lo, Rt + std::min(rt, lo + step + 1), Rs[i]) - Rt);
+        hint = p;
         int32_t end = 0;
         const int32_t pc = piece_of(U.t, p, end);
         const int32_t i1 =
