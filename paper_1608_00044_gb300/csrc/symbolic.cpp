@@ -212,7 +212,15 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     P.perm.swap(np);
     for (int64_t k = 0; k < n; ++k) P.pinv[P.perm[k]] = k;
     permuted_pattern(n, colptr, rowind, P.pinv, B);
-    etree_liu(n, B, parent);
+    // a postorder is a topological order of the elimination tree, under which
+    // the tree is unchanged: relabel it instead of computing it again
+    std::vector<int32_t> newpos(n), relabeled(n);
+    for (int64_t k = 0; k < n; ++k) newpos[post[k]] = (int32_t)k;
+    for (int64_t k = 0; k < n; ++k) {
+      const int32_t q = parent[post[k]];
+      relabeled[k] = q < 0 ? -1 : newpos[q];
+    }
+    parent.swap(relabeled);
   }
   column_counts(n, B, parent, P.colcount);
   P.etree = parent;
