@@ -362,32 +362,16 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   }
 
   // ---- where each entry of A lands in the pool --------------------------------
-  // Entries grouped by their panel (a counting sort), then each panel's rows
-  // given their positions in a scratch array: linear in nnz(A) + the rows.
   P.a_dest.resize(nnz);
-  {
-    std::vector<int64_t> head(ns + 1, 0), order(nnz);
-    std::vector<int32_t> lo_of(nnz), hi_of(nnz);
-    for (int64_t c = 0; c < n; ++c)
-      for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
-        const int64_t a = P.pinv[rowind[p]], b = P.pinv[c];
-        lo_of[p] = (int32_t)std::min(a, b);
-        hi_of[p] = (int32_t)std::max(a, b);
-        head[P.snode_of[lo_of[p]] + 1]++;
-      }
-    for (int32_t k = 0; k < ns; ++k) head[k + 1] += head[k];
-    std::vector<int64_t> fill(head.begin(), head.end() - 1);
-    for (int64_t p = 0; p < nnz; ++p) order[fill[P.snode_of[lo_of[p]]]++] = p;
-    std::vector<int32_t> pos(n, -1);
-    for (int32_t s = 0; s < ns; ++s) {
+  for (int64_t c = 0; c < n; ++c)
+    for (int64_t p = colptr[c]; p < colptr[c + 1]; ++p) {
+      int64_t a = P.pinv[rowind[p]], b = P.pinv[c];
+      int32_t lo = (int32_t)std::min(a, b), hi = (int32_t)std::max(a, b);
+      int32_t s = P.snode_of[lo];
       const int32_t* R = P.rows.data() + P.rowoff[s];
-      for (int32_t i = 0; i < P.nrows[s]; ++i) pos[R[i]] = i;
-      for (int64_t q = head[s]; q < head[s + 1]; ++q) {
-        const int64_t p = order[q];
-        P.a_dest[p] = P.valoff[s] + pos[hi_of[p]] + (int64_t)(lo_of[p] - P.fcol[s]) * P.ld[s];
-      }
+      int32_t pos = (int32_t)(std::lower_bound(R, R + P.nrows[s], hi) - R);
+      P.a_dest[p] = P.valoff[s] + pos + (int64_t)(lo - P.fcol[s]) * P.ld[s];
     }
-  }
 
   // ---- factorization tasks ------------------------------------------------------
   std::vector<int32_t> depth(ns, 0);
