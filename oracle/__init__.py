@@ -61,6 +61,8 @@ def _load():
                                      _f64p, ctypes.c_int64, ctypes.c_int]
             lib.orc_fact_err.restype = ctypes.c_double
             lib.orc_fact_err.argtypes = [ctypes.c_void_p]
+            lib.orc_fact_err_csc.restype = ctypes.c_double
+            lib.orc_fact_err_csc.argtypes = [ctypes.c_int64, _i64p, _i64p, _f64p, _i64p, _i64p, _f64p]
             _lib = lib
     return _lib
 
@@ -167,3 +169,18 @@ def berr(A, X, B) -> float:
     values = np.ascontiguousarray(A.values, np.float64)
     return float(lib.orc_berr(A.n, _p(colptr, _i64p), _p(rowind, _i32p), _p(values, _f64p),
                               _p(X, _f64p), X.shape[0], _p(B, _f64p), B.shape[0], X.shape[1]))
+
+
+def fact_err_csc(n, Lp, Li, Lx, Bp, Bi, Bx) -> float:
+    """||L L^T - B||_F / ||B||_F for a lower CSC factor L and the lower CSC of a symmetric B.
+
+    Rows ascending inside each column.  +inf when a product entry or an entry of
+    B lies outside L's pattern.
+    """
+    lib = _load()
+    arr = [np.ascontiguousarray(a, np.int64) for a in (Lp, Li)]
+    lx = np.ascontiguousarray(Lx, np.float64)
+    brr = [np.ascontiguousarray(a, np.int64) for a in (Bp, Bi)]
+    bx = np.ascontiguousarray(Bx, np.float64)
+    return float(lib.orc_fact_err_csc(int(n), _p(arr[0], _i64p), _p(arr[1], _i64p), _p(lx, _f64p),
+                                      _p(brr[0], _i64p), _p(brr[1], _i64p), _p(bx, _f64p)))

@@ -360,14 +360,17 @@ double orc_berr(int64_t n, const int64_t *Ap, const int32_t *Ai, const double *A
 }
 
 /*
- * ||L L^T - P A P^T||_F / ||A||_F.  L L^T is accumulated on the pattern of L; a
- * product entry that falls outside that pattern makes the result +inf.
+ * ||L L^T - B||_F / ||B||_F for a lower-triangular L and the lower triangle of a
+ * symmetric B, both CSC with rows sorted ascending in each column (diagonal
+ * first).  Off-diagonal entries count twice in both norms: they stand for the
+ * (i, j) and (j, i) entries of the full symmetric matrices.  L L^T is
+ * accumulated on the pattern of L; a product entry, or an entry of B, that falls
+ * outside that pattern makes the result +inf (for a factor from the symbolic
+ * pass the fill theorem of Section II-B rules both out).
  */
-double orc_fact_err(void *hv) {
-    orc_handle *h = hv;
-    int64_t n = h->n;
-    if (!h->factored) return NAN;
-    int64_t nz = h->Lp[n];
+double orc_fact_err_csc(int64_t n, const int64_t *Lp, const int64_t *Li, const double *Lx,
+                        const int64_t *Bp, const int64_t *Bi, const double *Bx) {
+    int64_t nz = Lp[n];
     double *M = calloc((size_t)(nz ? nz : 1), sizeof(double));
     int64_t *pos = malloc((size_t)(n ? n : 1) * sizeof(int64_t));
     double *bcol = calloc((size_t)(n ? n : 1), sizeof(double));
@@ -384,49 +387,56 @@ double orc_fact_err(void *hv) {
     int64_t *rp = malloc((size_t)(nz ? nz : 1) * sizeof(int64_t));
     if (!rcnt || !rk || !rp) { free(M); free(pos); free(bcol); free(start); free(rcnt); free(rk); free(rp); return NAN; }
     for (int64_t k = 0; k < n; ++k)
-        for (int64_t p = h->Lp[k]; p < h->Lp[k + 1]; ++p) rcnt[h->Li[p] + 1]++;
+        for (int64_t p = Lp[k]; p < Lp[k + 1]; ++p) rcnt[Li[p] + 1]++;
     for (int64_t j = 0; j < n; ++j) rcnt[j + 1] += rcnt[j];
     for (int64_t j = 0; j < n; ++j) start[j] = rcnt[j];
     for (int64_t k = 0; k < n; ++k)
-        for (int64_t p = h->Lp[k]; p < h->Lp[k + 1]; ++p) {
-            int64_t r = h->Li[p];
+        for (int64_t p = Lp[k]; p < Lp[k + 1]; ++p) {
+            int64_t r = Li[p];
             rk[start[r]] = k;
             rp[start[r]] = p;
             start[r]++;
         }
     for (int64_t j = 0; j < n; ++j) {
-        for (int64_t p = h->Lp[j]; p < h->Lp[j + 1]; ++p) pos[h->Li[p]] = p;
+        for (int64_t p = Lp[j]; p < Lp[j + 1]; ++p) pos[Li[p]] = p;
         for (int64_t q = rcnt[j]; q < rcnt[j + 1]; ++q) {
             int64_t k = rk[q], pj = rp[q];
-            double ljk = h->Lx[pj];
-            for (int64_t p = pj; p < h->Lp[k + 1]; ++p) {
-                int64_t at = pos[h->Li[p]];
+            double ljk = Lx[pj];
+            for (int64_t p = pj; p < Lp[k + 1]; ++p) {
+                int64_t at = pos[Li[p]];
                 if (at < 0) { outside = 1; continue; }
-                M[at] += h->Lx[p] * ljk;
+                M[at] += Lx[p] * ljk;
             }
         }
-        for (int64_t p = h->Lp[j]; p < h->Lp[j + 1]; ++p) pos[h->Li[p]] = -1;
+        for (int64_t p = Lp[j]; p < Lp[j + 1]; ++p) pos[Li[p]] = -1;
     }
     double diff = 0.0, anorm = 0.0;
     for (int64_t j = 0; j < n; ++j) {
-        for (int64_t p = h->Bp[j]; p < h->Bp[j + 1]; ++p) {
-            bcol[h->Bi[p]] = h->Bx[p];
-            double a2 = h->Bx[p] * h->Bx[p];
-            anorm += (h->Bi[p] == j) ? a2 : 2.0 * a2;
+        for (int64_t p = Bp[j]; p < Bp[j + 1]; ++p) {
+            bcol[Bi[p]] = Bx[p];
+            double a2 = Bx[p] * Bx[p];
+            anorm += (Bi[p] == j) ? a2 : 2.0 * a2;
         }
-        for (int64_t p = h->Lp[j]; p < h->Lp[j + 1]; ++p) {
-            int64_t i = h->Li[p];
+        for (int64_t p = Lp[j]; p < Lp[j + 1]; ++p) {
+            int64_t i = Li[p];
             double d = M[p] - bcol[i];
             diff += (i == j) ? d * d : 2.0 * d * d;
             bcol[i] = 0.0;
         }
-        for (int64_t p = h->Bp[j]; p < h->Bp[j + 1]; ++p) {
+        for (int64_t p = Bp[j]; p < Bp[j + 1]; ++p) {
             /* entries of B outside L's pattern cannot exist (fill theorem); flag if they do */
-            if (bcol[h->Bi[p]] != 0.0) outside = 1;
-            bcol[h->Bi[p]] = 0.0;
+            if (bcol[Bi[p]] != 0.0) outside = 1;
+            bcol[Bi[p]] = 0.0;
         }
     }
     free(M); free(pos); free(bcol); free(start); free(rcnt); free(rk); free(rp);
     if (outside) return INFINITY;
     return anorm > 0.0 ? sqrt(diff) / sqrt(anorm) : sqrt(diff);
+}
+
+/* ||L L^T - P A P^T||_F / ||A||_F of the handle's factor (Eq. 1 checked entrywise). */
+double orc_fact_err(void *hv) {
+    orc_handle *h = hv;
+    if (!h->factored) return NAN;
+    return orc_fact_err_csc(h->n, h->Lp, h->Li, h->Lx, h->Bp, h->Bi, h->Bx);
 }

@@ -8,6 +8,10 @@
 * Closed forms: the 1D Laplacian factor, diagonal matrices, and an exactly
   representable factor.
 * Non-SPD detection at a known column, berr against a dense recomputation.
+* fact_err of perturbed factors against the dense product formed by numpy /
+  scipy, closed forms with exact arithmetic, and +inf outside the pattern.
+* Symbolic counts of the nested-dissection grids against reference counts
+  computed independently (``golden/nd_counts.txt``).
 """
 import numpy as np
 import pytest
@@ -267,3 +271,136 @@ def test_nd_fill_far_below_natural_order():
     nd = oracle.OracleFactor.from_csc(A, gridgen.geometric_nd(A.dims))
     nat = oracle.OracleFactor.from_csc(A, None)
     assert nd.nnzL < 0.8 * nat.nnzL
+
+
+# --------------------------------------------------------------------------- fact_err
+
+
+def _dense_lower_csc(M):
+    """Every lower entry of M as a structural entry (a dense lower pattern)."""
+    n = M.shape[0]
+    Lp = np.zeros(n + 1, np.int64)
+    Li, Lx = [], []
+    for j in range(n):
+        for i in range(j, n):
+            Li.append(i)
+            Lx.append(M[i, j])
+        Lp[j + 1] = len(Li)
+    return Lp, np.array(Li, np.int64), np.array(Lx, np.float64)
+
+
+@pytest.mark.parametrize("seed", range(4))
+def test_fact_err_perturbed_dense_vs_numpy(seed):
+    # A perturbed Cholesky factor has a known, nonzero ||LL^T - A||_F / ||A||_F,
+    # computed here from the full dense matrices with numpy.  A value off by the
+    # weight of the mirrored off-diagonal entries, by a wrong norm of A or by a
+    # constant zero fails this.
+    rng = np.random.default_rng(seed)
+    n = 7
+    G = rng.standard_normal((n, n))
+    A = G @ G.T + n * np.eye(n)
+    L = np.linalg.cholesky(A)
+    L[4, 1] += 1e-3 * (1 + seed)
+    L[5, 5] *= 1 + 2e-3
+    L[6, 0] -= 5e-4
+    want = np.linalg.norm(L @ L.T - A, "fro") / np.linalg.norm(A, "fro")
+    Lp, Li, Lx = _dense_lower_csc(L)
+    Bp, Bi, Bx = _dense_lower_csc(A)
+    got = oracle.fact_err_csc(n, Lp, Li, Lx, Bp, Bi, Bx)
+    assert want > 1e-5
+    assert abs(got - want) <= 1e-12 * want
+
+
+def test_fact_err_only_off_diagonal_and_only_diagonal_perturbations():
+    # The two halves of the sum separately: an error only off the diagonal of
+    # LL^T (counted twice in the Frobenius norm of the symmetric difference) and
+    # an error only on it.
+    A = np.diag([4.0, 9.0, 16.0])
+    Bp, Bi, Bx = _dense_lower_csc(A)
+    # L = diag(2, 3, 4) with l_10 = d: (LL^T)_{10} = 2d, (LL^T)_{11} = 9 + d^2.
+    d = 2.0**-10  # powers of two: every product and difference is exact
+    L = np.diag([2.0, 3.0, 4.0])
+    L[1, 0] = d
+    Lp, Li, Lx = _dense_lower_csc(L)
+    want = np.sqrt(2 * (2 * d) ** 2 + d**4) / np.sqrt(16 + 81 + 256)
+    assert abs(oracle.fact_err_csc(3, Lp, Li, Lx, Bp, Bi, Bx) - want) <= 1e-14 * want
+    # only the diagonal: l_22 = 4 + e gives (LL^T)_{22} - 16 = 8e + e^2.
+    e = 2.0**-13
+    L = np.diag([2.0, 3.0, 4.0 + e])
+    Lp, Li, Lx = _dense_lower_csc(L)
+    want = abs(8 * e + e * e) / np.sqrt(16 + 81 + 256)
+    assert abs(oracle.fact_err_csc(3, Lp, Li, Lx, Bp, Bi, Bx) - want) <= 1e-12 * want
+
+
+def test_fact_err_of_handle_equals_csc_form_and_perturbed_sparse_factor():
+    A, perm, _ = gridgen.workload("lap2d_16")
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    Lp, Li, Lx = f.L()
+    Bp, Bi, Bx = f.B()
+    n = A.n
+    assert oracle.fact_err_csc(n, Lp, Li, Lx, Bp, Bi, Bx) == f.fact_err()
+    # perturb one off-diagonal and one diagonal entry of the sparse factor and
+    # compare with the product formed by scipy on the full symmetric matrices
+    Lx2 = Lx.copy()
+    off = next(p for j in range(n // 2, n) for p in range(Lp[j] + 1, Lp[j + 1]))
+    Lx2[off] += 1e-6
+    Lx2[Lp[n // 3]] *= 1 + 1e-7
+    Ls = sp.csc_matrix((Lx2, Li, Lp), shape=(n, n))
+    Bl = sp.csc_matrix((Bx, Bi, Bp), shape=(n, n))
+    Bfull = Bl + Bl.T - sp.diags(Bl.diagonal())
+    D = (Ls @ Ls.T - Bfull).toarray()
+    want = np.linalg.norm(D, "fro") / np.linalg.norm(Bfull.toarray(), "fro")
+    got = oracle.fact_err_csc(n, Lp, Li, Lx2, Bp, Bi, Bx)
+    assert want > 1e-8
+    assert abs(got - want) <= 1e-9 * want
+
+
+def test_fact_err_outside_pattern_is_inf():
+    # A product entry outside L's pattern: column 0 holds rows 0, 1, 2, so
+    # l_20 l_10 lands at (2, 1), which column 1 (row 1 only) does not hold.
+    Lp = np.array([0, 3, 4, 5], np.int64)
+    Li = np.array([0, 1, 2, 1, 2], np.int64)
+    Lx = np.array([2.0, 0.5, 0.25, 3.0, 4.0])
+    Bp, Bi, Bx = _dense_lower_csc(np.diag([4.0, 9.0, 16.0]))
+    assert oracle.fact_err_csc(3, Lp, Li, Lx, Bp, Bi, Bx) == np.inf
+    # An entry of B outside L's pattern (L diagonal, b_10 != 0).
+    Lp = np.array([0, 1, 2, 3], np.int64)
+    Li = np.array([0, 1, 2], np.int64)
+    Lx = np.array([2.0, 3.0, 4.0])
+    B = np.diag([4.0, 9.0, 16.0])
+    B[1, 0] = B[0, 1] = 1.0
+    Bp, Bi, Bx = _dense_lower_csc(B)
+    Bx[Bx == 0] = 0.0
+    assert oracle.fact_err_csc(3, Lp, Li, Lx, Bp, Bi, Bx) == np.inf
+
+
+# --------------------------------------------------------------------------- ND counts
+
+
+def _golden_nd_counts():
+    import os
+    path = os.path.join(os.path.dirname(__file__), "golden", "nd_counts.txt")
+    rows = []
+    for line in open(path):
+        line = line.split("#", 1)[0].split()
+        if line:
+            rows.append((line[0], float(line[1]), float(line[2])))
+    return rows
+
+
+def _sig4(x):
+    return float(f"{x:.3e}")
+
+
+@pytest.mark.parametrize("name,nnzl,flops", _golden_nd_counts())
+def test_nd_reference_counts(name, nnzl, flops):
+    # The geometric dissection of the grid recipe and the oracle's symbolic
+    # pass together reproduce counts computed independently of this code.
+    A, perm, _ = gridgen.workload(name)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    if name == "lap2d_8":
+        assert f.nnzL == int(nnzl) and int(f.flops) == int(flops)
+    else:
+        assert _sig4(f.nnzL) == nnzl
+        assert _sig4(f.flops) == flops
