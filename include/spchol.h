@@ -34,7 +34,8 @@
  *     word of their launch has been read back, so results are complete on
  *     return.
  *   - A handle owns all device memory it allocates and frees it in
- *     spchol_destroy.  A handle is not safe for concurrent use from two host
+ *     spchol_destroy (through the caller's allocator when spchol_options
+ *     gives one, else stream-ordered from the device's memory pool).  A handle is not safe for concurrent use from two host
  *     threads; distinct handles are independent.
  *
  * Return codes: 0 on success; -k when argument k (1-based) is invalid;
@@ -116,6 +117,37 @@ typedef struct spchol_options {
   int profile;            /* 1: the persistent kernels time every task (per-type busy time and the
                              time spent waiting for a ready task, summed over CTAs) into the stats;
                              2: additionally record each task's start and end (spchol_trace_get) */
+  int sched;              /* which ready task runs first in the dynamic schedules (deterministic 0,
+                             and the update tiles of 2) -- the question of Section V-A:
+                             0 (default): two ready rings; the diagonal and panel-solve tasks and,
+                             near the root, the update tiles into the etree parent (the critical
+                             path) go ahead of the other update tiles; in the solve, tasks made ready
+                             by other tasks go ahead of the leaves.
+                             1: one FIFO ring: every ready task runs in the order it became ready */
+  /*
+   * Device memory of the handle.  With dev_alloc = dev_free = NULL (the default)
+   * the library allocates with stream-ordered cudaMallocAsync / cudaFreeAsync
+   * from the device's default memory pool, so that neither spchol_destroy nor
+   * a solve that grows its workspace waits for work that other streams are
+   * running.  Otherwise every device allocation of the handle goes through the
+   * caller's allocator (e.g. PyTorch's caching allocator):
+   *   dev_alloc(bytes, stream, ctx): device memory on the handle's device (the
+   *     current device during the call), at least 256-byte aligned, or NULL on
+   *     failure (the library then returns SPCHOL_ENOMEM).  stream: the stream
+   *     of the call that needs the memory, which first uses it in that stream's
+   *     order; NULL from spchol_analyze, whose memory is complete when analyze
+   *     returns and is then used on any stream.
+   *   dev_free(ptr, bytes, stream, ctx): called only when no work of the
+   *     library that uses ptr is pending -- every entry point except
+   *     spchol_factorize_enqueue has finished its device work when it returns;
+   *     destroy a handle only after the stream of its last enqueued
+   *     factorization has completed.  stream: as for dev_alloc (NULL from
+   *     spchol_destroy).
+   * Set both or neither (-5 from analyze otherwise).  Pinned host memory for
+   * status words is the library's own, recycled across handles. */
+  void* (*dev_alloc)(size_t bytes, void* stream, void* ctx);
+  void (*dev_free)(void* ptr, size_t bytes, void* stream, void* ctx);
+  void* alloc_ctx;        /* passed to dev_alloc / dev_free as ctx */
 } spchol_options;
 
 typedef struct spchol_stats {

@@ -6,7 +6,11 @@
 #include <cmath>
 #include <cstdio>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
+#include <type_traits>
+#include <unordered_map>
 #include <vector>
 
 #include <cuda.h>  // CUtensorMap and its encoder's signature (called through the runtime's driver entry point)
@@ -142,6 +146,10 @@ struct spchol_handle_s {
   cudaEvent_t ev0 = nullptr, ev1 = nullptr;
   size_t smem_factor = 0, smem_solve = 0;
   int grid_factor = 0, grid_solve = 0;
+  // sizes of the live device allocations (the caller's dev_free takes the size)
+  std::unordered_map<void*, size_t> dev_bytes;
+  // pinned host blocks (recycled through the process-wide cache) and their sizes
+  size_t h_norms_bytes = 0;
 };
 
 namespace {
@@ -167,6 +175,139 @@ inline void clear_stale_error() { (void)cudaGetLastError(); }
 // Structure uploads go through a private non-blocking stream so that analyze
 // never orders itself behind work that other threads run on other streams.
 thread_local cudaStream_t g_upload_stream = nullptr;
+
+// ---- device memory of a handle
+// Through the caller's allocator (spchol_options.dev_alloc / dev_free), else
+// stream-ordered from the device's default memory pool.  cudaFree waits for
+// the whole device, so one handle's release or workspace growth would stall
+// every other stream's persistent kernel; cudaFreeAsync does not.  Every
+// release happens when the library has no pending work on the memory (its
+// calls synchronise their stream before returning), so the stream a block is
+// released on only orders the release itself.
+bool pools_supported(int dev) {
+  static std::mutex mu;
+  static std::map<int, bool> known;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = known.find(dev);
+  if (it != known.end()) return it->second;
+  int v = 0;
+  if (cudaDeviceGetAttribute(&v, cudaDevAttrMemoryPoolsSupported, dev) != cudaSuccess) {
+    cudaGetLastError();
+    v = 0;
+  }
+  known[dev] = v != 0;
+  return v != 0;
+}
+
+// One non-blocking stream per device on which spchol_destroy releases memory.
+cudaStream_t release_stream(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  cudaStream_t st = nullptr;
+  if (cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    st = nullptr;  // the legacy stream, which orders the release after prior work
+  }
+  streams[dev] = st;
+  return st;
+}
+
+// stream: where the memory is first used (nullptr: analyze, any stream after it
+// returns; the pool path then allocates on the upload stream, synchronised
+// before analyze returns).
+int dalloc_impl(spchol_handle_t h, void** out, size_t bytes, cudaStream_t stream, const char* what, int line) {
+  *out = nullptr;
+  bytes = std::max<size_t>((bytes + 255) & ~size_t(255), 256);
+  void* p = nullptr;
+  if (h->opt.dev_alloc) {
+    p = h->opt.dev_alloc(bytes, (void*)stream, h->opt.alloc_ctx);
+    if (!p || ((uintptr_t)p & 255) != 0) {
+      if (p) h->opt.dev_free(p, bytes, (void*)stream, h->opt.alloc_ctx);
+      snprintf(g_cuda_err, sizeof(g_cuda_err), "dev_alloc %s %zu bytes at api.cu:%d for %s",
+               p ? "returned memory not 256-byte aligned for" : "returned NULL for", bytes, line, what);
+      return SPCHOL_ENOMEM;
+    }
+  } else if (pools_supported(h->device)) {
+    cudaError_t e = cudaMallocAsync(&p, bytes, stream ? stream : g_upload_stream);
+    if (e != cudaSuccess) return cuda_fail(e, what, line);
+  } else {
+    cudaError_t e = cudaMalloc(&p, bytes);
+    if (e != cudaSuccess) return cuda_fail(e, what, line);
+  }
+  h->dev_bytes[p] = bytes;
+  *out = p;
+  return 0;
+}
+
+void dfree(spchol_handle_t h, void* p, cudaStream_t stream) {
+  if (!p) return;
+  auto it = h->dev_bytes.find(p);
+  const size_t bytes = it != h->dev_bytes.end() ? it->second : 0;
+  if (it != h->dev_bytes.end()) h->dev_bytes.erase(it);
+  if (h->opt.dev_free) {
+    h->opt.dev_free(p, bytes, (void*)stream, h->opt.alloc_ctx);
+  } else if (pools_supported(h->device)) {
+    if (cudaFreeAsync(p, stream ? stream : release_stream(h->device)) != cudaSuccess) cudaGetLastError();
+  } else {
+    cudaFree(p);
+  }
+}
+
+#define DALLOC(ptr, bytes, stream)                                                                       \
+  do {                                                                                                   \
+    void* p_ = nullptr;                                                                                  \
+    int rc_ = dalloc_impl(h, &p_, (bytes), (stream), #ptr, __LINE__);                                    \
+    if (rc_) return rc_;                                                                                 \
+    (ptr) = reinterpret_cast<std::remove_reference<decltype(ptr)>::type>(p_);                            \
+  } while (0)
+
+// ---- pinned host blocks (status words, small read-backs), recycled for the
+// life of the process: cudaFreeHost may wait for the device, which would stall
+// other streams' work whenever a handle is destroyed.  Size classes are powers
+// of two from 256 bytes.
+std::mutex g_pinned_mu;
+std::map<size_t, std::vector<void*>> g_pinned_free;
+
+size_t pinned_class(size_t bytes) {
+  size_t c = 256;
+  while (c < bytes) c <<= 1;
+  return c;
+}
+
+int pinned_get(void** out, size_t bytes, int line) {
+  const size_t c = pinned_class(bytes);
+  {
+    std::lock_guard<std::mutex> lock(g_pinned_mu);
+    auto& v = g_pinned_free[c];
+    if (!v.empty()) {
+      *out = v.back();
+      v.pop_back();
+      return 0;
+    }
+  }
+  cudaError_t e = cudaHostAlloc(out, c, cudaHostAllocPortable);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaHostAlloc", line);
+  return 0;
+}
+
+void pinned_put(void* p, size_t bytes) {
+  if (!p) return;
+  std::lock_guard<std::mutex> lock(g_pinned_mu);
+  g_pinned_free[pinned_class(bytes)].push_back(p);
+}
+
+#define PINNED(ptr, bytes)                                            \
+  do {                                                                \
+    void* p_ = nullptr;                                               \
+    int rc_ = pinned_get(&p_, (bytes), __LINE__);                     \
+    if (rc_) return rc_;                                              \
+    (ptr) = reinterpret_cast<std::remove_reference<decltype(ptr)>::type>(p_); \
+  } while (0)
+
+constexpr size_t kProfWords = 24;
 
 template <typename V>
 int upload(spchol_handle_t h, V* dst, const std::vector<V>& src) {
@@ -304,7 +445,6 @@ int setup_device(spchol_handle_t h) {
     o_cci = r32(cci.size());
     o_cvm = r64(cvm.size());
   }
-  CU(cudaMalloc(&A.base, A.bytes));
   CU(cudaStreamCreateWithFlags(&g_upload_stream, cudaStreamNonBlocking));
   struct StreamGuard {
     ~StreamGuard() {
@@ -315,6 +455,7 @@ int setup_device(spchol_handle_t h) {
       }
     }
   } upload_guard;
+  DALLOC(A.base, A.bytes, nullptr);
   char* b = A.base;
   h->d_fcol = (int32_t*)(b + o_fcol);
   h->d_nrows = (int32_t*)(b + o_nrows);
@@ -443,32 +584,32 @@ int setup_device(spchol_handle_t h) {
   if (fan) {  // never read before written: no initialisation
     // + 16 bytes: the gather copies whole 16-byte pieces, up to one past the last value
     h->fan_buf_bytes = std::max<size_t>((((size_t)P.fan_off.back() * esz + 15) & ~size_t(15)) + 16, 256);
-    CU(cudaMalloc(&h->d_fan_buf, h->fan_buf_bytes));
-    CU(cudaMalloc(&h->d_fan_rec, std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanRec)));
+    DALLOC(h->d_fan_buf, h->fan_buf_bytes, nullptr);
+    DALLOC(h->d_fan_rec, std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanRec), nullptr);
     CU(launch_fanrec(h->d_fan_ent, (int64_t)P.fan_ent.size(), h->d_ut, h->d_fan_off, h->d_rowoff, h->d_fan_rec,
                      g_upload_stream));
   }
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
-  CU(cudaMalloc(&h->d_pool, h->pool_bytes));
-  CU(cudaMalloc(&h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256)));
+  DALLOC(h->d_pool, h->pool_bytes, nullptr);
+  DALLOC(h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256), nullptr);
   if (mma_mode_of(h->opt.precision) != 1 && mma_mode_of(h->opt.precision) != 2 && P.ns > 0) {
     std::vector<CUtensorMap> maps;
     if (build_tensor_maps(h, maps)) {
       static_assert(sizeof(CUtensorMap) == 128, "tensor map size");
-      CU(cudaMalloc(&h->d_tmaps, maps.size() * sizeof(CUtensorMap)));
+      DALLOC(h->d_tmaps, maps.size() * sizeof(CUtensorMap), nullptr);
       CU(cudaMemcpyAsync(h->d_tmaps, maps.data(), maps.size() * sizeof(CUtensorMap), cudaMemcpyHostToDevice,
                          g_upload_stream));
       CU(cudaStreamSynchronize(g_upload_stream));  // the host vector goes out of scope
     }
   }
-  CU(cudaMalloc(&h->d_relpos, std::max<size_t>((size_t)P.n_rel * sizeof(int32_t), 256)));
+  DALLOC(h->d_relpos, std::max<size_t>((size_t)P.n_rel * sizeof(int32_t), 256), nullptr);
   CU(launch_relpos(h->d_ut, P.n_u, h->d_rows, h->d_rowoff, h->d_nrows, h->d_relpos, g_upload_stream));
-  if (oz) CU(cudaMalloc(&h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256)));
-  CU(cudaMallocHost(&h->h_ctrl, kCtrlWords * sizeof(int)));
-  CU(cudaMallocHost(&h->h_prof, 24 * sizeof(unsigned long long)));
+  if (oz) DALLOC(h->d_slices, std::max<size_t>((size_t)P.sliceoff[ns] * sizeof(uint16_t), 256), nullptr);
+  PINNED(h->h_ctrl, kCtrlWords * sizeof(int));
+  PINNED(h->h_prof, kProfWords * sizeof(unsigned long long));
   if (h->opt.profile == 2) {
-    CU(cudaMalloc(&h->d_trace_f, 2 * (size_t)std::max(P.n_task_ids, 1) * sizeof(unsigned long long)));
-    CU(cudaMalloc(&h->d_trace_s, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long)));
+    DALLOC(h->d_trace_f, 2 * (size_t)std::max(P.n_task_ids, 1) * sizeof(unsigned long long), nullptr);
+    DALLOC(h->d_trace_s, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long), nullptr);
   }
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));
@@ -507,41 +648,43 @@ int setup_device(spchol_handle_t h) {
   return 0;
 }
 
-int ensure_workspace(spchol_handle_t h, int64_t need, int nrhs) {
+// The solve's workspace for n x nrhs right-hand sides, grown on demand.  The old
+// buffers' last users (earlier calls) have completed, so they are released at
+// once, stream-ordered on st, and the new ones allocated on st.
+int ensure_workspace(spchol_handle_t h, int64_t need, int nrhs, cudaStream_t st) {
   if (h->plan.params.fanin && nrhs > h->fan_nrhs) {  // the fan-in solves' tile buffers
-    for (double** p : {&h->d_zf, &h->d_zb})
-      if (*p) {
-        cudaFree(*p);
-        *p = nullptr;
-      }
+    for (double** p : {&h->d_zf, &h->d_zb}) {
+      dfree(h, *p, st);
+      *p = nullptr;
+    }
     h->fan_nrhs = 0;
-    CU(cudaMalloc(&h->d_zf, std::max<size_t>((size_t)h->plan.st_zf.back() * nrhs, 1) * sizeof(double)));
-    CU(cudaMalloc(&h->d_zb, std::max<size_t>((size_t)h->plan.st_zb.back() * nrhs, 1) * sizeof(double)));
+    DALLOC(h->d_zf, std::max<size_t>((size_t)h->plan.st_zf.back() * nrhs, 1) * sizeof(double), st);
+    DALLOC(h->d_zb, std::max<size_t>((size_t)h->plan.st_zb.back() * nrhs, 1) * sizeof(double), st);
     h->fan_nrhs = nrhs;
   }
   if (need > h->y_cap) {
-    for (double** p : {&h->d_Y, &h->d_B, &h->d_X, &h->d_R})
-      if (*p) {
-        cudaFree(*p);
-        *p = nullptr;
-      }
+    for (double** p : {&h->d_Y, &h->d_B, &h->d_X, &h->d_R}) {
+      dfree(h, *p, st);
+      *p = nullptr;
+    }
     h->y_cap = 0;
-    CU(cudaMalloc(&h->d_Y, need * sizeof(double)));
-    CU(cudaMalloc(&h->d_B, need * sizeof(double)));
+    DALLOC(h->d_Y, need * sizeof(double), st);
+    DALLOC(h->d_B, need * sizeof(double), st);
     if (h->fp32) {
-      CU(cudaMalloc(&h->d_X, need * sizeof(double)));
-      CU(cudaMalloc(&h->d_R, need * sizeof(double)));
+      DALLOC(h->d_X, need * sizeof(double), st);
+      DALLOC(h->d_R, need * sizeof(double), st);
     }
     h->y_cap = need;
   }
   if (h->fp32 && nrhs > h->norms_cap) {
-    if (h->d_norms) cudaFree(h->d_norms);
-    if (h->h_norms) cudaFreeHost(h->h_norms);
+    dfree(h, h->d_norms, st);
+    pinned_put(h->h_norms, h->h_norms_bytes);
     h->d_norms = nullptr;
     h->h_norms = nullptr;
     h->norms_cap = 0;
-    CU(cudaMalloc(&h->d_norms, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long)));
-    CU(cudaMallocHost(&h->h_norms, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long)));
+    DALLOC(h->d_norms, (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long), st);
+    h->h_norms_bytes = (1 + 3 * (size_t)nrhs) * sizeof(unsigned long long);
+    PINNED(h->h_norms, h->h_norms_bytes);
     h->norms_cap = nrhs;
   }
   return 0;
@@ -597,9 +740,10 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   CU(cudaMemsetAsync(h->d_pool, 0, h->pool_bytes, st));
   CU(launch_assemble(h->fp32, vals, h->d_adest, P.nnz_a, h->d_pool, st));
   if (P.ns == 0) return 0;
+  const bool fifo = P.params.fifo;  // one FIFO ring: no high-priority slots, seeds at the front
   CU(launch_ring_reset(h->d_ring, P.n_factor_tasks, h->d_fseeds, h->nfseeds, h->d_ctrl, h->d_dep, h->d_dep_init,
                        P.ns, h->d_trsm_left, h->d_trsm_init, P.ns, nullptr, nullptr, 0, st, nullptr, nullptr, 0,
-                       /*seeds_hi=*/1));
+                       /*seeds_hi=*/fifo ? 0 : 1));
   FactorArgs a{};
   a.gat0 = INT_MAX;  // no gather tasks outside the fan-in mode
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
@@ -614,7 +758,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.sub_hi = h->d_sub_hi;
   a.relpos = h->d_relpos;
   a.tmaps = h->d_tmaps;
-  a.n_hi = P.n_hi_tasks;
+  a.n_hi = fifo ? 0 : P.n_hi_tasks;
   a.ut = h->d_ut;
   a.n_trsm = P.n_trsm;
   a.n_u = P.n_u;
@@ -718,7 +862,8 @@ int factorize_impl(spchol_handle_t h, const double* values_dev_or_null, const do
 int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   Plan& P = h->plan;
   if (P.ns == 0 || nrhs == 0) return 0;
-  const int n_hi = P.n_solve_tasks - h->nsseeds;  // seeds: the normal-priority ring, after the other
+  // seeds: the normal-priority ring, after the other (one FIFO ring: no high-priority slots)
+  const int n_hi = P.params.fifo ? 0 : P.n_solve_tasks - h->nsseeds;
   CU(launch_ring_reset(h->d_ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, h->d_ctrl, h->d_fkids, h->d_fdep0,
                        P.ns, h->d_ftiles, h->d_nst, P.ns, h->d_btiles, h->d_nst, P.ns, st, h->d_bdep, h->d_bdep0,
                        P.n_st, /*seeds_hi=*/0, /*seed_off=*/n_hi));
@@ -732,7 +877,7 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
   a.st_rows = h->d_st_rows;
-  a.n_hi = P.n_solve_tasks - h->nsseeds;
+  a.n_hi = n_hi;
   a.st_tptr = h->d_st_tptr;
   a.st_tgt = h->d_st_tgt;
   a.rt_ptr = h->d_rt_ptr;
@@ -792,14 +937,14 @@ int apply_factor_inverse(spchol_handle_t h, const double* src, double* dst, cuda
   return 0;
 }
 
-int ensure_gmres(spchol_handle_t h) {
+int ensure_gmres(spchol_handle_t h, cudaStream_t st) {
   if (h->d_gmV) return 0;
   const int64_t n = h->plan.n;
-  CU(cudaMalloc(&h->d_gmV, (size_t)n * (kGmresRestart + 1) * sizeof(double)));
-  CU(cudaMalloc(&h->d_gmW, (size_t)n * sizeof(double)));
-  CU(cudaMalloc(&h->d_gmPart, (size_t)kGmresBlocks * (kGmresRestart + 1) * sizeof(double)));
-  CU(cudaMalloc(&h->d_gmH, 3 * (kGmresRestart + 2) * sizeof(double)));
-  CU(cudaMallocHost(&h->h_gmH, 3 * (kGmresRestart + 2) * sizeof(double)));
+  DALLOC(h->d_gmV, (size_t)n * (kGmresRestart + 1) * sizeof(double), st);
+  DALLOC(h->d_gmW, (size_t)n * sizeof(double), st);
+  DALLOC(h->d_gmPart, (size_t)kGmresBlocks * (kGmresRestart + 1) * sizeof(double), st);
+  DALLOC(h->d_gmH, 3 * (kGmresRestart + 2) * sizeof(double), st);
+  PINNED(h->h_gmH, 3 * (kGmresRestart + 2) * sizeof(double));
   return 0;
 }
 
@@ -935,7 +1080,7 @@ int solve_refined(spchol_handle_t h, int nrhs, cudaStream_t st) {
         break;
       }
       prev = berr;
-      if ((rc = ensure_gmres(h)) != 0) return rc;
+      if ((rc = ensure_gmres(h, st)) != 0) return rc;
       for (int c = 0; c < nrhs; ++c) {
         int steps = 0;
         int r2 = gmres_correction(h, c, st, &steps);
@@ -1078,7 +1223,7 @@ int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stre
   clear_stale_error();
   cudaStream_t st = (cudaStream_t)stream;
   const int64_t n = h->plan.n;
-  int rc = ensure_workspace(h, n * nrhs, nrhs);
+  int rc = ensure_workspace(h, n * nrhs, nrhs, st);
   if (rc) return rc;
   const bool dev = is_device_ptr(B);
   CU(cudaEventRecord(h->ev0, st));
@@ -1156,9 +1301,10 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the reset kernel re-initialises
   // the ring, the counters and the control words before every launch
+  const int n_hi = P.params.fifo ? 0 : P.n_solve_tasks - h->nsseeds;
   CU(launch_ring_reset(ring, P.n_solve_tasks, h->d_sseeds, h->nsseeds, ctrl, fdep, h->d_fdep0, P.ns, ftiles,
                        h->d_nst, P.ns, btiles, h->d_nst, P.ns, st, bdep, h->d_bdep0, P.n_st, /*seeds_hi=*/0,
-                       /*seed_off=*/P.n_solve_tasks - h->nsseeds));
+                       /*seed_off=*/n_hi));
   CU(launch_permute_in(B, ldb, Y, n, h->d_perm, n, nrhs, st));
   SolveArgs a{};
   a.pv = PanelView{P.ns, h->d_fcol, h->d_nrows, h->d_ld, h->d_rowoff, h->d_rows, h->d_valoff, h->d_parent};
@@ -1170,7 +1316,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.n_st = P.n_st;
   a.ntask = P.n_solve_tasks;
   a.st_rows = h->d_st_rows;
-  a.n_hi = P.n_solve_tasks - h->nsseeds;
+  a.n_hi = n_hi;
   a.st_tptr = h->d_st_tptr;
   a.st_tgt = h->d_st_tgt;
   a.rt_ptr = h->d_rt_ptr;
@@ -1286,29 +1432,18 @@ int spchol_trace_get(spchol_handle_t h, int which, uint64_t* out, int64_t* count
 int spchol_destroy(spchol_handle_t h) {
   if (!h) return 0;
   DeviceGuard g(h->device);
-  if (h->arena.base) cudaFree(h->arena.base);
-  if (h->d_pool) cudaFree(h->d_pool);
-  if (h->d_fan_buf) cudaFree(h->d_fan_buf);
-  if (h->d_fan_rec) cudaFree(h->d_fan_rec);
-  if (h->d_inv) cudaFree(h->d_inv);
-  if (h->d_relpos) cudaFree(h->d_relpos);
-  if (h->d_tmaps) cudaFree(h->d_tmaps);
-  if (h->d_slices) cudaFree(h->d_slices);
-  if (h->d_trace_f) cudaFree(h->d_trace_f);
-  if (h->d_trace_s) cudaFree(h->d_trace_s);
-  if (h->d_Y) cudaFree(h->d_Y);
-  if (h->d_zf) cudaFree(h->d_zf);
-  if (h->d_zb) cudaFree(h->d_zb);
-  if (h->d_B) cudaFree(h->d_B);
-  if (h->h_ctrl) cudaFreeHost(h->h_ctrl);
-  if (h->h_prof) cudaFreeHost(h->h_prof);
-  if (h->d_X) cudaFree(h->d_X);
-  if (h->d_R) cudaFree(h->d_R);
-  for (double* p : {h->d_gmV, h->d_gmW, h->d_gmPart, h->d_gmH})
-    if (p) cudaFree(p);
-  if (h->h_gmH) cudaFreeHost(h->h_gmH);
-  if (h->d_norms) cudaFree(h->d_norms);
-  if (h->h_norms) cudaFreeHost(h->h_norms);
+  // Nothing here waits for the device: the memory goes back stream-ordered (or
+  // to the caller's allocator), the pinned blocks to the process-wide cache.
+  for (void* p : {(void*)h->arena.base, h->d_pool, h->d_fan_buf, (void*)h->d_fan_rec, (void*)h->d_inv,
+                  (void*)h->d_relpos, (void*)h->d_tmaps, (void*)h->d_slices, (void*)h->d_trace_f,
+                  (void*)h->d_trace_s, (void*)h->d_Y, (void*)h->d_zf, (void*)h->d_zb, (void*)h->d_B,
+                  (void*)h->d_X, (void*)h->d_R, (void*)h->d_gmV, (void*)h->d_gmW, (void*)h->d_gmPart,
+                  (void*)h->d_gmH, (void*)h->d_norms})
+    dfree(h, p, nullptr);
+  pinned_put(h->h_ctrl, kCtrlWords * sizeof(int));
+  pinned_put(h->h_prof, kProfWords * sizeof(unsigned long long));
+  pinned_put(h->h_gmH, 3 * (kGmresRestart + 2) * sizeof(double));
+  pinned_put(h->h_norms, h->h_norms_bytes);
   if (h->ev0) cudaEventDestroy(h->ev0);
   if (h->ev1) cudaEventDestroy(h->ev1);
   delete h;
@@ -1398,7 +1533,7 @@ int spchol_batch_solve(spchol_handle_t h, double* const* B, const int64_t* ldb, 
   }
   if (maxr == 0) return 0;
   const int64_t N = h->plan.n;
-  int rc = ensure_workspace(h, N * maxr, maxr);
+  int rc = ensure_workspace(h, N * maxr, maxr, st);
   if (rc) return rc;
   // Gather every matrix's RHS into one N x maxr block (zero columns where a
   // matrix has fewer right-hand sides), solve once, scatter back.

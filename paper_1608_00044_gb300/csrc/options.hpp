@@ -26,6 +26,10 @@ inline void default_options(spchol_options* o) {
   o->ir_tol = 1e-12;
   o->fault_inject = 0;
   o->profile = 0;
+  o->sched = 0;
+  o->dev_alloc = nullptr;
+  o->dev_free = nullptr;
+  o->alloc_ctx = nullptr;
 }
 
 inline bool options_valid(const spchol_options& o) {
@@ -35,7 +39,8 @@ inline bool options_valid(const spchol_options& o) {
          o.relax_zeros >= 0 && o.wait_budget_ns > 0 && o.ir_max_iter >= 0 && o.tile_rows >= 0 && o.tile_rows <= 64 &&
          o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 && o.deterministic >= 0 &&
          o.deterministic <= 2 &&
-         o.profile >= 0 && o.profile <= 2;
+         o.profile >= 0 && o.profile <= 2 && o.sched >= 0 && o.sched <= 1 &&
+         (o.dev_alloc == nullptr) == (o.dev_free == nullptr);
 }
 
 inline PlanParams params_from(const spchol_options& o) {
@@ -53,6 +58,7 @@ inline PlanParams params_from(const spchol_options& o) {
     p.slice_fp64 = true;
   }
   p.trsm_rows = kTrsmTileRows;
+  p.fifo = o.sched == 1;
   p.solve_rows = kSolveTileRows;
   if (o.deterministic) {
     p.deterministic = true;

@@ -49,6 +49,10 @@ struct PlanParams {
   // for one GPU) instead of the chains: see Plan::fan_ptr.  Implies
   // deterministic (the solves keep their chains).
   bool fanin = false;
+  // One FIFO ready ring instead of the two priority rings (spchol_options.sched
+  // = 1): the launch gives the high-priority ring no slots, and every push goes
+  // to the other ring.  The plan itself is the same.
+  bool fifo = false;
 };
 
 // Rows of a target panel are gathered in pieces of at most this many rows.

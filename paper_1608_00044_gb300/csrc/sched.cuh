@@ -195,10 +195,12 @@ __device__ __forceinline__ int ring2_claim(const Ring2& q, int* pend, int* lo_re
 }
 
 // Push ready tasks first .. first+count-1 to one ring of a Ring2 (hi: the
-// high-priority one).  Whole CTA; s_base is a shared int.  Same visibility
+// high-priority one; a Ring2 with n_hi = 0 is a single FIFO ring, and every
+// push goes to it).  Whole CTA; s_base is a shared int.  Same visibility
 // precondition as ring_push_one.
 __device__ __forceinline__ void ring2_push_range(const Ring2& q, bool hi, int first, int count, int* s_base) {
   if (count <= 0) return;
+  hi = hi && q.n_hi > 0;  // a launch without a high-priority ring: one FIFO ring
   int* tail = &q.ctrl[hi ? kHiTail : kTail];
   int* slots = hi ? q.hi : q.lo;
   const int n = hi ? q.n_hi : q.n_lo;
@@ -217,6 +219,7 @@ __device__ __forceinline__ void ring2_push_range(const Ring2& q, bool hi, int fi
 
 // Any thread: push one ready task to one ring of a Ring2.
 __device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task) {
+  hi = hi && q.n_hi > 0;
   const int slot = atomicAdd(&q.ctrl[hi ? kHiTail : kTail], 1);
   if (slot < (hi ? q.n_hi : q.n_lo)) {
     st_release(&(hi ? q.hi : q.lo)[slot], task);

@@ -12,6 +12,14 @@ of it, against 33.7 req/s and 355 ms with grids capped at one CTA per SM, the
 other setting, `ctas_per_sm`).  A request is admitted when a slot
 is free and the device bytes of all resident factors plus its own stay within
 the memory budget; least-recently-used idle factors are evicted to make room.
+A request whose own footprint exceeds the whole budget is rejected
+(``spchol.ENOMEM``) instead of waiting.  A handle's footprint is charged with
+the solve workspace of the most right-hand sides a request may bring
+(``max_nrhs``), so a later repeat solve with more of them stays inside the
+budget.  The handles' device memory comes from PyTorch's caching allocator
+(``spchol.torch_allocator``) by default: evicting a factor or growing a solve
+workspace returns memory to the cache and never calls cudaFree, which would
+wait for every other slot's kernels.
 Latency is measured from arrival to the moment the result is on the host.  A
 request's matrix is client data: a producer thread materializes each request's
 matrix ahead of its arrival (if it falls behind, the wait counts as latency).
@@ -65,7 +73,8 @@ class _Resident:
 
 class Server:
     def __init__(self, slots: int = 4, budget_bytes: int | None = None, ctas_per_sm: int = 0,
-                 precision: int = spchol.FP64, max_width: int = 64, device: int = 0):
+                 precision: int = spchol.FP64, max_width: int = 64, device: int = 0, max_nrhs: int = 16,
+                 allocator="torch"):
         import torch
 
         self.torch = torch
@@ -76,7 +85,10 @@ class Server:
             budget_bytes = int(0.8 * free)
         self.budget = budget_bytes
         self.slots = slots
-        self.opt_kw = dict(precision=precision, max_width=max_width, ctas_per_sm=ctas_per_sm)
+        self.opt_kw = dict(precision=precision, max_width=max_width, ctas_per_sm=ctas_per_sm, allocator=allocator)
+        self.max_nrhs = max_nrhs
+        self.fp32 = precision in (spchol.FP32, spchol.TF32, spchol.TF32X3)
+        self.rejected = 0
         self.resident: dict[str, _Resident] = collections.OrderedDict()
         self.used = 0
         self.mem_cv = threading.Condition()
@@ -105,7 +117,15 @@ class Server:
                 r.last_use = time.perf_counter()
                 return r, False
         h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(**self.opt_kw))
-        fp = spchol.stats(h)["footprint_bytes"] + 2 * A.n * max(req.B.shape[1], 1) * 8 * 2
+        # the factor plus the solve workspace (Y and B; X and R too with refinement)
+        # for the most right-hand sides any request may bring
+        nrhs = max(self.max_nrhs, req.B.shape[1], 1)
+        fp = spchol.stats(h)["footprint_bytes"] + (4 if self.fp32 else 2) * A.n * nrhs * 8
+        if fp > self.budget:  # could never fit, even with every other factor evicted
+            spchol.destroy(h)
+            with self.mem_cv:
+                self.rejected += 1
+            return None, False
         with self.mem_cv:
             while True:
                 r = self.resident.get(req.key)
@@ -139,6 +159,10 @@ class Server:
         r, fresh = self._acquire(req, A, perm)
         tb = time.perf_counter()
         req.t_analyze = tb - ta
+        if r is None:  # larger than the whole memory budget
+            req.rc = spchol.ENOMEM
+            req.done = time.perf_counter() - t0
+            return
         try:
             with r.lock:  # one slot at a time per handle
                 tc = time.perf_counter()

@@ -9,6 +9,7 @@ from __future__ import annotations
 
 import ctypes
 import os
+import threading
 
 import numpy as np
 
@@ -33,6 +34,10 @@ class Options(ctypes.Structure):
         ("ir_tol", ctypes.c_double),
         ("fault_inject", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("sched", ctypes.c_int),
+        ("dev_alloc", ctypes.c_void_p),  # function pointers (DEV_ALLOC_FN / DEV_FREE_FN), NULL = the pool
+        ("dev_free", ctypes.c_void_p),
+        ("alloc_ctx", ctypes.c_void_p),
     ]
 
 
@@ -138,21 +143,104 @@ def strerror(code: int) -> str:
     return load().spchol_strerror(int(code)).decode()
 
 
-def default_options(**kw) -> Options:
+def default_options(allocator=None, **kw) -> Options:
+    """spchol_default_options, then the given fields.  allocator="torch" routes the
+    handle's device memory through PyTorch's caching allocator (TorchAllocator)."""
     o = Options()
     load().spchol_default_options(ctypes.byref(o))
     for k, v in kw.items():
         setattr(o, k, v)
+    if allocator == "torch":
+        torch_allocator().install(o)
+    elif allocator is not None:
+        allocator.install(o)
     return o
 
 
 def default_options_host(**kw) -> Options:
     """The defaults of include/spchol.h filled without loading the GPU library."""
     o = Options(precision=FP64, max_width=64, relax_zeros=4, tile_rows=0, ctas_per_sm=0, deterministic=0,
-                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0)
+                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0, sched=0,
+                dev_alloc=None, dev_free=None, alloc_ctx=None)
     for k, v in kw.items():
         setattr(o, k, v)
     return o
+
+
+# ------------------------------------------------------------------ device memory hook
+
+DEV_ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+DEV_FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class TorchAllocator:
+    """spchol_options.dev_alloc / dev_free served by PyTorch's caching allocator.
+
+    The library asks for its device memory here instead of allocating it itself,
+    so a handle's memory comes from (and returns to) the same cache as the
+    caller's tensors: destroying a handle or growing a solve workspace never
+    calls cudaFree, which would wait for every stream on the device.  A block
+    is requested on the stream of the call that first uses it (the current
+    stream when the library passes none).  The library releases a block only
+    after its own work on it has completed, so returning it to the cache at once
+    is safe.  One instance per process (``torch_allocator()``): the callbacks
+    must outlive every handle that uses them.
+    """
+
+    def __init__(self):
+        import torch
+
+        self._torch = torch
+        self._lock = threading.Lock()
+        self.live = {}  # address -> bytes of the blocks the library holds
+        self.failures = 0
+        self._alloc_cb = DEV_ALLOC_FN(self._alloc)
+        self._free_cb = DEV_FREE_FN(self._free)
+
+    def _alloc(self, nbytes, stream, ctx):
+        torch = self._torch
+        try:
+            dev = torch.cuda.current_device()  # the library makes the handle's device current
+            st = int(stream) if stream else torch.cuda.current_stream(dev).cuda_stream
+            p = int(torch.cuda.caching_allocator_alloc(int(nbytes), dev, st))
+        except Exception:  # out of memory, or torch refused: the library returns SPCHOL_ENOMEM
+            with self._lock:
+                self.failures += 1
+            return None
+        with self._lock:
+            self.live[p] = int(nbytes)
+        return p
+
+    def _free(self, ptr, nbytes, stream, ctx):
+        with self._lock:
+            self.live.pop(int(ptr), None)
+        try:
+            self._torch.cuda.caching_allocator_delete(int(ptr))
+        except Exception:
+            pass
+
+    def held_bytes(self) -> int:
+        with self._lock:
+            return sum(self.live.values())
+
+    def install(self, opt: Options) -> Options:
+        opt.dev_alloc = ctypes.cast(self._alloc_cb, ctypes.c_void_p).value
+        opt.dev_free = ctypes.cast(self._free_cb, ctypes.c_void_p).value
+        opt.alloc_ctx = None
+        return opt
+
+
+_torch_alloc = None
+_torch_alloc_lock = threading.Lock()
+
+
+def torch_allocator() -> TorchAllocator:
+    """The process-wide TorchAllocator (created on first use)."""
+    global _torch_alloc
+    with _torch_alloc_lock:
+        if _torch_alloc is None:
+            _torch_alloc = TorchAllocator()
+        return _torch_alloc
 
 
 # ------------------------------------------------------------------ marshalling

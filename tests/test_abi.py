@@ -65,6 +65,13 @@ def test_analyze_argument_checks_precede_device_work():
     ri = np.array([0], np.int32)
     assert lib.spchol_analyze(1, cp.ctypes.data, ri.ctypes.data, None, ctypes.byref(bad_opt), ctypes.byref(h)) == -5
     assert lib.spchol_analyze(1, cp.ctypes.data, ri.ctypes.data, None, None, None) == -6
+    # the schedule switch and the allocator hook pair are checked with the options
+    for bad in (spchol.default_options(sched=2), spchol.default_options(sched=-1)):
+        assert lib.spchol_analyze(1, cp.ctypes.data, ri.ctypes.data, None, ctypes.byref(bad), ctypes.byref(h)) == -5
+    cb = spchol.DEV_ALLOC_FN(lambda n, s, c: None)
+    half = spchol.default_options()
+    half.dev_alloc = ctypes.cast(cb, ctypes.c_void_p).value  # dev_free left NULL
+    assert lib.spchol_analyze(1, cp.ctypes.data, ri.ctypes.data, None, ctypes.byref(half), ctypes.byref(h)) == -5
 
 
 def test_no_cpu_fallback_in_the_product_library():

@@ -91,3 +91,28 @@ def test_poisson_stream_latency_summary():
     s.close()
     assert out["requests"] == 24 and out["p99_ms"] >= out["p50_ms"] > 0
     assert all(q.done >= q.arrival for q in reqs)
+
+
+def test_request_larger_than_the_budget_is_rejected_not_hung():
+    # a budget smaller than any single footprint: every request is refused with
+    # ENOMEM at once (the slot does not wait for memory that can never free up)
+    reqs = serve.make_stream(6, rate=0, seed=13, patterns=3, small=True)
+    s = serve.Server(slots=2, budget_bytes=4096)
+    s.run(reqs)
+    assert all(q.rc == spchol.ENOMEM for q in reqs)
+    assert s.rejected == len(reqs) and s.used == 0 and not s.resident
+    s.close()
+
+
+def test_repeat_solve_with_more_rhs_stays_inside_the_budget():
+    # the footprint charged at admission covers the largest workspace a request
+    # may bring, so repeat solves with up to max_nrhs right-hand sides fit
+    reqs = serve.make_stream(12, rate=0, seed=17, patterns=2, small=True, repeat_frac=0.5)
+    s = serve.Server(slots=2, max_nrhs=16)
+    s.run(reqs)
+    assert all(q.rc == 0 for q in reqs)
+    for r in s.resident.values():
+        st = spchol.stats(r.h)
+        assert r.footprint >= st["footprint_bytes"] + 2 * st["n"] * 16 * 8
+    assert s.peak_used <= s.budget
+    s.close()
