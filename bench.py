@@ -30,7 +30,8 @@ METRIC = "factor TFLOP/s (%FP64 peak) on 64^3 Laplacian; FP32+IR speedup; p50/p9
 UNIT = "TFLOP/s"
 # FP64 roofline denominator: 152 SMs x 2 DFMA/clk/SM x 2 flop x SM clock.  The
 # DFMA rate per SM follows from NVIDIA's 1.25 TFLOP/s FP64 figure at the
-# 2070 MHz maximum clock; a DFMA throughput probe on this GPU measured 1.19.
+# 2070 MHz maximum clock; the DFMA throughput probe (peak_probe.cu, run by
+# default, reported as roofline.peak_measured) measures 1.2545 on this GPU.
 FP64_FLOP_PER_CLK = 152 * 2 * 2
 
 
@@ -136,18 +137,127 @@ def _workload(name):
     return A, perm, b
 
 
-def _oracle_sample(name, reps=1):
-    """Time the oracle (single-threaded scalar C) on a bounded sample workload."""
+def _berr(A, X, B):
+    """Backward error max_c ||b_c - A x_c||_inf / (||A||_inf ||x_c||_inf + ||b_c||_inf) of a solution,
+    from the full symmetric matrix with scipy (the bench's own check, not the oracle)."""
+    M = A.to_scipy_full()
+    X = np.asarray(X, dtype=np.float64).reshape(A.n, -1, order="F")
+    B = np.asarray(B, dtype=np.float64).reshape(A.n, -1, order="F")
+    R = B - M @ X
+    an = float(abs(M).sum(axis=1).max()) if A.n else 0.0
+    worst = 0.0
+    for c in range(X.shape[1]):
+        den = an * float(np.abs(X[:, c]).max(initial=0.0)) + float(np.abs(B[:, c]).max(initial=0.0))
+        rn = float(np.abs(R[:, c]).max(initial=0.0))
+        e = rn / den if den > 0 else (np.inf if rn > 0 else 0.0)
+        if not e <= worst:
+            worst = e
+    return worst
+
+
+def _host_cpu():
+    """Model name and logical core count of the host running the bench."""
+    import platform
+
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for line in out.splitlines():
+            if line.strip().lower().startswith("model name"):
+                model = line.split(":", 1)[1].strip()
+                break
+    except Exception:
+        pass
+    if not model:
+        try:
+            for line in open("/proc/cpuinfo"):
+                if line.lower().startswith("model name"):
+                    model = line.split(":", 1)[1].strip()
+                    break
+        except Exception:
+            pass
+    return {"model": model or platform.processor() or platform.machine(), "arch": platform.machine(),
+            "nproc": os.cpu_count()}
+
+
+def _oracle_sample(name, reps=1, detail=False):
+    """Time the oracle (single-threaded scalar C) on a bounded sample workload:
+    symbolic analysis, numeric factorization and solve, each separately."""
     import oracle
 
     A, perm, b = _workload(name)
-    t0 = time.perf_counter()
+    t_sym = t_num = t_sol = 0.0
     for _ in range(reps):
+        t0 = time.perf_counter()
         f = oracle.OracleFactor.from_csc(A, perm)
+        t1 = time.perf_counter()
         info = f.factor()
+        t2 = time.perf_counter()
         x = f.solve(b)
-    dt = (time.perf_counter() - t0) / reps
+        t3 = time.perf_counter()
+        t_sym += t1 - t0
+        t_num += t2 - t1
+        t_sol += t3 - t2
+    dt = (t_sym + t_num + t_sol) / reps
+    if detail:
+        return {"flops": f.flops, "total_s": dt, "symbolic_s": t_sym / reps, "numeric_s": t_num / reps,
+                "solve_s": t_sol / reps, "info": info, "berr": oracle.berr(A, x, b),
+                "numeric_gflops": f.flops / (t_num / reps) / 1e9 if t_num > 0 else None}
     return f.flops, dt, info, oracle.berr(A, x, b)
+
+
+def _oracle_batch_worker(args):
+    """One host core's share of the batch for the all-cores oracle timing: build
+    its matrices, wait for the other workers, then time the oracle on them."""
+    idx, sides, barrier = args
+    import gridgen
+    import oracle
+
+    mats = [gridgen.diffusion_2d_5pt(int(sides[i]), sigma=1.0, seed=1000 + i) for i in idx]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    rhs = [gridgen.rhs_uniform(M.n, 1, seed=i) for i, M in zip(idx, mats)]
+    oracle.build()
+    barrier.wait(600)
+    t0 = time.time()
+    flops = 0.0
+    for M, p, b in zip(mats, perms, rhs):
+        f = oracle.OracleFactor.from_csc(M, p)
+        f.factor()
+        f.solve(b)
+        flops += f.flops
+    return t0, time.time(), flops
+
+
+def oracle_batch_all_cores(count=512):
+    """The oracle over all host cores on the 512-matrix batch (one process per
+    core, matrices split by their size, each process timing its own share after
+    all have built their inputs): wall time from the first start to the last
+    end, and flops over it."""
+    import multiprocessing as mp
+
+    import gridgen
+
+    sides = gridgen.batch_sides(count)
+    cores = os.cpu_count() or 1
+    order = sorted(range(count), key=lambda i: -int(sides[i]) ** 3)
+    load = [0] * cores
+    parts = [[] for _ in range(cores)]
+    for i in order:  # largest first to the least loaded core (cost ~ side^3 for 2D nested dissection)
+        k = min(range(cores), key=lambda c: (load[c], c))
+        parts[k].append(i)
+        load[k] += int(sides[i]) ** 3
+    ctx = mp.get_context("spawn")
+    with ctx.Manager() as man:
+        barrier = man.Barrier(cores)
+        with ctx.Pool(cores) as pool:
+            res = pool.map(_oracle_batch_worker, [(p, sides, barrier) for p in parts], chunksize=1)
+    t0 = min(r[0] for r in res)
+    t1 = max(r[1] for r in res)
+    flops = sum(r[2] for r in res)
+    return {"value": flops / (t1 - t0) / 1e12, "unit": UNIT, "cores": cores, "kind": "oracle",
+            "seconds": t1 - t0, "flops": flops,
+            "sample": f"the whole {count}-matrix batch (2D 5-point variable-coefficient grids), one process per "
+                      f"host core, matrices split by size; analyze + factor + 1-RHS solve each"}
 
 
 def run_reference(args):
@@ -183,7 +293,8 @@ def run_reference(args):
         "config": {"workload": f"{args.workload} (reference steps run the bounded sample {sample})",
                    "sample": sample, "nrhs": 8},
         "cpu_baseline": {"value": value, "unit": UNIT, "cores": 1, "kind": "oracle",
-                         "sample": f"{sample}: scalar left-looking FP64 factor + 8-RHS solve, single thread"},
+                         "sample": f"{sample}: scalar left-looking FP64 factor + 8-RHS solve, single thread",
+                         "host": _host_cpu()},
         "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
         "berr": be,
     }
@@ -194,7 +305,7 @@ def run_reference(args):
 MIXED_CANDIDATES = [(64, 4, 64), (64, 16, 64), (64, 64, 64), (32, 64, 64)]
 
 
-def measure_mixed(spchol, oracle, torch, dev, name="diff3d_48", width=64, tune=True):
+def measure_mixed(spchol, torch, dev, name="diff3d_48", width=64, tune=True):
     """Mixed-precision row: FP64 factor+solve vs FP32 factor + solve + FP64 refinement to 1e-12,
     same matrix and right-hand side, device time of each.  Each precision runs
     with the default plan (W 64, relax 4, 64-row tiles) and with the plan the
@@ -225,7 +336,7 @@ def measure_mixed(spchol, oracle, torch, dev, name="diff3d_48", width=64, tune=T
             st = spchol.stats(h)
             if it >= 1:
                 times.append(st["factor_ms"] + st["solve_ms"])
-        be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), b)
+        be = _berr(A, np.asfortranarray(X.cpu().numpy().T), b)
         spchol.destroy(h)
         return {"ms": sum(times) / len(times), "factor_ms": st["factor_ms"], "solve_ms": st["solve_ms"],
                 "berr": be, "ir_iters": st["ir_iters"], "converged": bool(ok and be <= 1e-12),
@@ -268,11 +379,11 @@ def _flops_of(spchol, A, perm):
     return f
 
 
-def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, width=64, relax=4):
+def measure_fp64_tc(spchol, torch, dev, A, perm, b, flops, peak_fp64, width=64, relax=4):
     """FP64 factorization of the headline matrix with the update tiles of panels
     at least 16 wide on the BF16 tensor cores (7-way digit split, FP64-accurate
     result; `SPCHOL_FP64_TC`): factor time, the same flop count over it, and the
-    backward error of an 8-RHS solve against the oracle's definition."""
+    backward error of an 8-RHS solve."""
     o = spchol.default_options(precision=spchol.FP64_TC, max_width=min(width, 64), relax_zeros=relax)
     h = spchol.analyze(A.n, A.colptr, A.rowind, perm, o)
     vals = torch.from_numpy(A.values).to(dev)
@@ -283,7 +394,7 @@ def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, wi
             times.append(spchol.stats(h)["factor_ms"])
     X = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
     spchol.solve(h, X, A.n, b.shape[1])
-    be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), b)
+    be = _berr(A, np.asfortranarray(X.cpu().numpy().T), b)
     st = spchol.stats(h)
     spchol.destroy(h)
     ms = statistics.median(times)
@@ -296,7 +407,7 @@ def measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops, peak_fp64, wi
                     "exact sum c_j^2, the same numerator as the headline"}
 
 
-def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, width=64, relax=4):
+def measure_ordering(spchol, torch, dev, A0, perm_geo, b, flops_geo, width=64, relax=4):
     """General-ordering row: the headline matrix with its rows and columns in a
     random order (seed 11), ordered by spchol_order_nd (nested dissection by
     level structures) instead of the grid's geometric dissection: host time of
@@ -325,7 +436,7 @@ def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, wid
             times.append(spchol.stats(h)["factor_ms"])
     X = torch.from_numpy(np.ascontiguousarray(bq.T)).to(dev)
     spchol.solve(h, X, A.n, bq.shape[1])
-    be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), bq)
+    be = _berr(A, np.asfortranarray(X.cpu().numpy().T), bq)
     st = spchol.stats(h)
     spchol.destroy(h)
     ms = statistics.median(times)
@@ -334,40 +445,45 @@ def measure_ordering(spchol, oracle, torch, dev, A0, perm_geo, b, flops_geo, wid
             "nnz_l": st["nnz_l"], "factor_ms": ms, "tflops": st["flops"] / (ms * 1e-3) / 1e12, "berr": be}
 
 
-def measure_scheduling(spchol, oracle, torch, dev, name="lap3d_40", width=64):
-    """Scheduling-policy row (Section IV-B's static schedule against the dynamic
-    one, restated for one GPU), with the fan-in aggregation (Section II-C's
-    fan-in family) as the fast deterministic mode: the same matrix factored and
-    solved with the default dynamic two-priority rings, with the static
-    (target, source) order, and with fan-in buffers; median factor time of 3,
-    solve time, backward errors, device footprint, and whether the first and
-    the last of four factor + solve runs agree bitwise."""
+def measure_scheduling(spchol, torch, dev, name="lap3d_40", width=64):
+    """Scheduling-policy row (the Section V-A question of which ready task runs
+    first, and Section IV-B's static schedule against the dynamic one, restated
+    for one GPU), with the fan-in aggregation (Section II-C's fan-in family) as
+    the fast deterministic mode: the same matrix factored and solved with the
+    default dynamic two rings (critical-path priority), with one FIFO ring (no
+    priority), with the static (target, source) order, and with fan-in buffers;
+    median factor time, solve time, backward errors, device footprint, and
+    whether the first and the last factor + solve runs agree bitwise."""
     A, perm, b = _workload(name)
     vals = torch.from_numpy(A.values).to(dev)
     out = {"workload": f"{name}: 3D 7-point {A.dims}, n={A.n}, {b.shape[1]} RHS"}
-    for label, det in (("dynamic", 0), ("static", 1), ("fanin", 2)):
-        h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(max_width=width, deterministic=det))
+    arms = (("dynamic_priority", 0, 0), ("dynamic_fifo", 0, 1), ("static", 1, 0), ("fanin", 2, 0))
+    for label, det, sched in arms:
+        h = spchol.analyze(A.n, A.colptr, A.rowind, perm,
+                           spchol.default_options(max_width=width, deterministic=det, sched=sched))
+        runs = 3 if det == 1 else 4  # the static chains take seconds at 64^3
         times, xs, s_ms = [], [], []
-        for it in range(4):
+        for it in range(runs):
             spchol.factorize(h, vals)
             if it >= 1:
                 times.append(spchol.stats(h)["factor_ms"])
-            if it in (0, 3):
+            if it in (0, runs - 1):
                 X = torch.from_numpy(np.ascontiguousarray(b.T)).to(dev)
                 spchol.solve(h, X, A.n, b.shape[1])
                 s_ms.append(spchol.stats(h)["solve_ms"])
                 xs.append(X.cpu().numpy())
-        be = oracle.berr(A, np.asfortranarray(xs[0].T), b)
+        be = _berr(A, np.asfortranarray(xs[0].T), b)
         fp = spchol.stats(h)["footprint_bytes"]
         spchol.destroy(h)
         out[label] = {"factor_ms": statistics.median(times), "solve_ms": min(s_ms), "berr": be,
                       "footprint_bytes": int(fp), "runs_bitwise_equal": bool(np.array_equal(xs[0], xs[1]))}
-    out["static_over_dynamic_factor"] = out["static"]["factor_ms"] / out["dynamic"]["factor_ms"]
-    out["fanin_over_dynamic_factor"] = out["fanin"]["factor_ms"] / out["dynamic"]["factor_ms"]
+    base = out["dynamic_priority"]["factor_ms"]
+    for label in ("dynamic_fifo", "static", "fanin"):
+        out[f"{label}_over_priority_factor"] = out[label]["factor_ms"] / base
     return out
 
 
-def measure_gmres_ir(spchol, oracle, torch, dev, nx=32, eps=1e-4, width=64):
+def measure_gmres_ir(spchol, torch, dev, nx=32, eps=1e-4, width=64):
     """GMRES-IR row: the Neumann 3D Laplacian + eps I (kappa ~ 12 / eps), where a
     TF32 factor stalls classic refinement (u_f kappa >> 1) and GMRES-IR takes
     over; time to the 1e-12 target against the plain FP64 factor + solve."""
@@ -395,7 +511,7 @@ def measure_gmres_ir(spchol, oracle, torch, dev, nx=32, eps=1e-4, width=64):
             st = spchol.stats(h)
             rec = {"ms": ms, "factor_ms": st["factor_ms"], "solve_ms": st["solve_ms"], "factor_rc": rc,
                    "converged": ok, "ir_iters": st["ir_iters"], "gmres_steps": st["ir_gmres_iters"],
-                   "berr": oracle.berr(A, X, b)}
+                   "berr": _berr(A, X, b)}
             if best is None or rec["ms"] < best["ms"]:
                 best = rec
         spchol.destroy(h)
@@ -403,7 +519,7 @@ def measure_gmres_ir(spchol, oracle, torch, dev, nx=32, eps=1e-4, width=64):
     return out
 
 
-def measure_small(spchol, oracle, torch, dev, width=64):
+def measure_small(spchol, torch, dev, width=64):
     """Latency row: 2D 5-point 64x64 (+1e-2 I), one RHS: factor + solve time,
     median of 50 after 5 warm-ups, and the backward error."""
     A, perm, b = _workload("lap2d_64")
@@ -422,13 +538,13 @@ def measure_small(spchol, oracle, torch, dev, width=64):
         if it >= 5:
             times.append((t1 - t0) * 1e3)
             dev_ms.append(st["factor_ms"] + st["solve_ms"])
-    be = oracle.berr(A, np.asfortranarray(X.cpu().numpy().T), b)
+    be = _berr(A, np.asfortranarray(X.cpu().numpy().T), b)
     spchol.destroy(h)
     return {"workload": f"lap2d_64: 2D 5-point 64x64 + 1e-2 I, n={A.n}, 1 RHS", "median_ms": statistics.median(times),
             "median_device_ms": statistics.median(dev_ms), "berr": be}
 
 
-def measure_batch(spchol, oracle, torch, dev, count=512, width=64):
+def measure_batch(spchol, torch, dev, count=512, width=64):
     """Batch row: 512 independent 2D 5-point variable-coefficient grids (sides from
     default_rng(1234) in [16, 128]) factored in ONE persistent launch."""
     import gridgen
@@ -483,7 +599,7 @@ def measure_batch(spchol, oracle, torch, dev, count=512, width=64):
         except spchol.SpcholError:
             pass
         st = spchol.stats(h)
-        worst = max(oracle.berr(M, X, B) for M, X, B in zip(mats, Xs, Bs))
+        worst = max(_berr(M, X, B) for M, X, B in zip(mats, Xs, Bs))
         ms = sum(fms) / len(fms)
         out[label] = {"factor_ms_one_launch": ms, "tflops": st0["flops"] / (ms * 1e-3) / 1e12,
                       "graph_replay_ms": statistics.median(gms), "autotuned": {k: tuned[k] for k in
@@ -501,8 +617,8 @@ def measure_serving(full=False, slots=4):
     throughput is measured closed-loop first, then the stream runs at fractions of it."""
     from paper_1608_00044_gb300 import serve
 
-    n_req, warm = (2000, 200) if full else (160, 40)
-    fracs = (0.25, 0.5, 0.75, 0.9) if full else (0.5,)
+    n_req, warm = (2000, 200) if full else (300, 50)
+    fracs = (0.25, 0.5, 0.75, 0.9)
     srv = serve.Server(slots=slots)
     # closed loop: all requests at t = 0 (warm-up part discarded)
     reqs = serve.make_stream(n_req + warm, rate=0, seed=4321)
@@ -529,6 +645,102 @@ def measure_serving(full=False, slots=4):
     return out
 
 
+def measure_batch_sharded(spchol, torch, dist, count=512, width=64):
+    """Multi-GPU batch row (N > 1): the 512-matrix batch split over the ranks by
+    exact flops, each rank factoring and solving its share in one persistent
+    launch on its own GPU, solutions gathered on rank 0.  Aggregate TFLOP/s =
+    the batch's flops / the slowest rank's factorization time."""
+    import gridgen
+    from paper_1608_00044_gb300 import shard
+
+    sides = gridgen.batch_sides(count)
+    mats = [gridgen.diffusion_2d_5pt(int(sd), sigma=1.0, seed=1000 + i) for i, sd in enumerate(sides)]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    rhs = [gridgen.rhs_uniform(M.n, 1, seed=i) for i, M in enumerate(mats)]
+    opts = dict(max_width=32, relax_zeros=64)  # the autotuner's choice for this batch on one GPU
+    costs = shard.matrix_flops(mats, perms, **opts)
+    shard.run_sharded(mats, perms, rhs, engine="gpu", costs=costs, **opts)  # warm-up
+    dist.barrier()
+    X, summ = shard.run_sharded(mats, perms, rhs, engine="gpu", costs=costs, **opts)
+    if X is None:
+        return None
+    worst = max(_berr(M, x, B) for M, x, B in zip(mats, X, rhs))
+    slowest = max(r.factor_ms for r in summ)
+    return {"ranks": len(summ), "factor_ms_slowest_rank": slowest,
+            "aggregate_tflops": float(sum(costs)) / (slowest * 1e-3) / 1e12,
+            "per_rank": [{"rank": r.rank, "matrices": len(r.indices), "flops": r.flops, "factor_ms": r.factor_ms}
+                         for r in summ],
+            "worst_berr": worst, "plan": opts}
+
+
+def trace_summary(args):
+    """Per-task trace of one factorization per scheduling arm (profile = 2: every
+    task's start and end on the device clock), summarised: makespan, busy time
+    per task type, average and starved concurrency, and the span of the top
+    separator's chain of panels (the critical path near the root).  Traced runs
+    are slower than untraced ones; compare the arms with each other."""
+    import torch
+
+    from __graft_entry__ import build
+
+    build()
+    from paper_1608_00044_gb300 import hostplan, spchol
+
+    torch.cuda.set_device(0)
+    A, perm, b = _workload(args.workload)
+    vals = torch.from_numpy(A.values).cuda()
+    out = {"mode": "trace-summary", "workload": f"{args.workload}: {_describe(A)}, n={A.n}", "arms": {}}
+    arms = (("dynamic_priority", 0, 0), ("dynamic_fifo", 0, 1), ("static", 1, 0), ("fanin", 2, 0))
+    for label, det, sched in arms:
+        kw = dict(max_width=args.width, deterministic=det, sched=sched)
+        plan = hostplan.HostPlan(A.n, A.colptr, A.rowind, perm, **kw)
+        sc = plan.scalars()
+        parent = plan.get(hostplan.PARENT)
+        fcol = plan.get(hostplan.FCOL)
+        plan.close()
+        h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(profile=2, **kw))
+        for _ in range(2):
+            spchol.factorize(h, vals)
+        st = spchol.stats(h)
+        tr = spchol.trace_get(h, 0).astype(np.int64)
+        spchol.destroy(h)
+        ns, nt, nu, nsub = sc["ns"], sc["n_trsm"], sc["n_u"], sc["n_sub"]
+        ran = tr[:, 1] > tr[:, 0]
+        t0 = tr[ran, 0].min()
+        t1 = tr[ran, 1].max()
+        dur = np.where(ran, tr[:, 1] - tr[:, 0], 0)
+        bounds = {"diagonal": (0, ns), "panel_solve": (ns, ns + nt), "update": (ns + nt, ns + nt + nu),
+                  "subtree": (ns + nt + nu, ns + nt + nu + nsub), "gather": (ns + nt + nu + nsub, len(tr))}
+        busy = {k: float(dur[a:b].sum()) / 1e6 for k, (a, b) in bounds.items() if b > a}
+        # concurrency over time: +1 at each start, -1 at each end
+        ev = np.concatenate([tr[ran, 0], tr[ran, 1]])
+        dv = np.concatenate([np.ones(ran.sum(), np.int64), -np.ones(ran.sum(), np.int64)])
+        o = np.argsort(ev, kind="stable")
+        ev, conc = ev[o], np.cumsum(dv[o])
+        seg = np.diff(ev)
+        grid = st["grid_factor"]
+        starved = float(seg[conc[:-1] < 0.1 * grid].sum()) / 1e6
+        # the chain of panels from the root down through the top separator: the
+        # panels whose first column lies in the root's separator block
+        root = int(np.where(parent[:ns] < 0)[0].max())
+        chain = [root]
+        while True:
+            kids = np.where(parent[:ns] == chain[-1])[0]
+            if len(kids) != 1:
+                break
+            chain.append(int(kids[0]))
+        top = chain[-1]
+        span = float(tr[root, 1] - tr[top, 0]) / 1e6
+        out["arms"][label] = {
+            "makespan_ms": float(t1 - t0) / 1e6, "factor_ms": st["factor_ms"], "grid": grid,
+            "tasks": int(ran.sum()), "busy_cta_ms": busy, "avg_concurrency": float(dur.sum()) / float(t1 - t0),
+            "starved_ms_below_10pct_of_grid": starved,
+            "top_chain": {"panels": len(chain), "columns": int(fcol[root + 1] - fcol[top]), "span_ms": span,
+                          "diagonal_busy_ms": float(dur[chain].sum()) / 1e6}}
+    print(json.dumps(out))
+    return 0
+
+
 def run_ours(args):
     import torch
 
@@ -546,7 +758,6 @@ def run_ours(args):
     from __graft_entry__ import build
 
     build()
-    import oracle
     from paper_1608_00044_gb300 import spchol
 
     prec = {"fp64": spchol.FP64, "fp32": spchol.FP32, "tf32": spchol.TF32, "tf32x3": spchol.TF32X3,
@@ -601,7 +812,7 @@ def run_ours(args):
 
     # parity of the last step's solution
     Xh = np.asfortranarray(X.cpu().numpy().T)
-    be = oracle.berr(A, Xh, b)
+    be = _berr(A, Xh, b)
 
     # repeat solves on the resident factor: p50 / p99 latency (device time)
     lat = []
@@ -635,14 +846,23 @@ def run_ours(args):
 
     cpu = None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+
         oracle.build()
-        fl, dt, info, cbe = _oracle_sample(args.cpu_sample)
-        cpu = {"value": fl / dt / 1e12, "unit": UNIT, "cores": 1, "kind": "oracle",
+        d = _oracle_sample(args.cpu_sample, detail=True)
+        cpu = {"value": d["flops"] / d["total_s"] / 1e12, "unit": UNIT, "cores": 1, "kind": "oracle",
                "sample": f"{args.cpu_sample}: scalar left-looking FP64 factor + 8-RHS solve, single thread, "
-                         f"{dt:.1f} s, {fl:.3e} flops"}
+                         f"{d['total_s']:.1f} s, {d['flops']:.3e} flops",
+               "symbolic_s": d["symbolic_s"], "numeric_s": d["numeric_s"], "solve_s": d["solve_s"],
+               "numeric_only_value": d["flops"] / d["numeric_s"] / 1e12, "host": _host_cpu(),
+               "note": "the oracle is a plain correctness reference, not a tuned CPU solver"}
+        if not args.no_rows:
+            cpu["batch_all_cores"] = oracle_batch_all_cores()
+        if args.cpu_full:  # the stated configurations in full: minutes of CPU time
+            cpu["full_configs"] = {nm: _oracle_sample(nm, detail=True) for nm in ("lap3d_64", "diff3d_48")}
 
     probe = None
-    if args.measure_peaks and rank == 0:
+    if not args.no_measure_peaks and rank == 0:
         from paper_1608_00044_gb300 import build as _b
 
         try:
@@ -692,16 +912,19 @@ def run_ours(args):
     if cpu is not None:
         line["cpu_baseline"] = cpu
     if not args.no_rows:
-        line["small_latency_row"] = measure_small(spchol, oracle, torch, dev, width=args.width)
+        line["small_latency_row"] = measure_small(spchol, torch, dev, width=args.width)
         if args.precision == "fp64" and args.workload == "lap3d_64":
-            line["fp64_tensor_core_row"] = measure_fp64_tc(spchol, oracle, torch, dev, A, perm, b, flops,
+            line["fp64_tensor_core_row"] = measure_fp64_tc(spchol, torch, dev, A, perm, b, flops,
                                                            peak_fp64, width=args.width, relax=args.relax)
-            line["ordering_row"] = measure_ordering(spchol, oracle, torch, dev, A, perm, b, flops,
+            line["ordering_row"] = measure_ordering(spchol, torch, dev, A, perm, b, flops,
                                                     width=args.width, relax=args.relax)
-        line["scheduling_row"] = measure_scheduling(spchol, oracle, torch, dev, width=args.width)
-        line["mixed_precision_row"] = measure_mixed(spchol, oracle, torch, dev, width=args.width)
-        line["gmres_ir_row"] = measure_gmres_ir(spchol, oracle, torch, dev, width=args.width)
-        line["batch_row"] = measure_batch(spchol, oracle, torch, dev, width=args.width)
+        line["scheduling_row"] = measure_scheduling(spchol, torch, dev, width=args.width,
+                                                    name="lap3d_64" if args.workload == "lap3d_64" else "lap3d_40")
+        line["mixed_precision_row"] = measure_mixed(spchol, torch, dev, width=args.width)
+        line["gmres_ir_row"] = measure_gmres_ir(spchol, torch, dev, width=args.width)
+        line["batch_row"] = measure_batch(spchol, torch, dev, width=args.width)
+        if ws > 1:
+            line["batch_row"]["sharded"] = measure_batch_sharded(spchol, torch, dist, width=args.width)
         line["serving_row"] = measure_serving(full=args.serve_full)
     if args.profile:
         sp = spchol.stats(h)
@@ -736,11 +959,18 @@ def main():
     ap.add_argument("--deterministic", type=int, default=0, choices=[0, 1, 2],
                     help="order of the headline factorization: 0 dynamic, 1 static chains, 2 fan-in buffers")
     ap.add_argument("--no-rows", action="store_true", help="skip the mixed-precision, batch and serving rows")
-    ap.add_argument("--measure-peaks", action="store_true", help="run the DFMA / DMMA / FFMA throughput probe")
-    ap.add_argument("--serve-full", action="store_true", help="serving row with 2000 requests at 4 rates")
+    ap.add_argument("--no-measure-peaks", action="store_true", help="skip the DFMA / DMMA / FFMA throughput probe")
+    ap.add_argument("--serve-full", action="store_true",
+                    help="serving row with 2000 requests per rate after 200 warm-up (default: 300 after 50)")
+    ap.add_argument("--trace-summary", action="store_true",
+                    help="instead of the bench line: per-task trace summaries of the scheduling arms")
+    ap.add_argument("--cpu-full", action="store_true",
+                    help="also time the oracle once on the full 64^3 Laplacian and 48^3 diffusion (minutes)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
+    if args.trace_summary:
+        return trace_summary(args)
     return run_ours(args)
 
 

@@ -299,8 +299,10 @@ int spchol_export_factor(spchol_handle_t h, int64_t* nnz, int64_t* Lp, int64_t* 
  * recorded when spchol_options.profile = 2: out[2*i] and out[2*i+1] are the
  * device-clock start and end (ns, %globaltimer) of task i, in the task
  * numbering of the launch (factorization: diagonal tasks, then panel-solve
- * tiles, then update tiles).  Query form: out = NULL sets *count to the number
- * of tasks.  Returns 0, -2 for a bad `which`, SPCHOL_ESTATE if not traced.
+ * tiles, then update tiles, then subtree tasks, then the fan-in mode's gather
+ * tasks; a task that never runs on its own -- a panel inside a subtree task --
+ * reads 0 / 0).  Query form: out = NULL sets *count to the number of tasks.
+ * Returns 0, -2 for a bad `which`, SPCHOL_ESTATE if not traced.
  */
 int spchol_trace_get(spchol_handle_t h, int which, uint64_t* out, int64_t* count);
 

@@ -610,6 +610,11 @@ int setup_device(spchol_handle_t h) {
   if (h->opt.profile == 2) {
     DALLOC(h->d_trace_f, 2 * (size_t)std::max(P.n_task_ids, 1) * sizeof(unsigned long long), nullptr);
     DALLOC(h->d_trace_s, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long), nullptr);
+    // tasks that never run on their own (panels inside subtree tasks) keep 0 / 0
+    CU(cudaMemsetAsync(h->d_trace_f, 0, 2 * (size_t)std::max(P.n_task_ids, 1) * sizeof(unsigned long long),
+                       g_upload_stream));
+    CU(cudaMemsetAsync(h->d_trace_s, 0, 2 * (size_t)std::max(P.n_solve_tasks, 1) * sizeof(unsigned long long),
+                       g_upload_stream));
   }
   CU(cudaEventCreate(&h->ev0));
   CU(cudaEventCreate(&h->ev1));

@@ -251,6 +251,73 @@ class Server:
             self.used = 0
 
 
+class MultiServer:
+    """One Server per GPU of the node behind a dispatcher.
+
+    Requests are independent units, so a stream splits over the GPUs with no
+    exchange between them: each device runs its own Server (its own slots,
+    streams, resident factors and admission against its own memory budget),
+    and the dispatcher decides the device of every request before it arrives.
+    A sparsity pattern stays on the device that first took it, where its
+    analysis and factors are resident, so repeat solves find their factor; a
+    new pattern goes to the device with the least work assigned so far.  The
+    work of a request is estimated from its size alone, before its matrix
+    exists: n^1.5 for a factorization (the flops of a nested-dissection
+    factor grow like n^1.5 in 2D and n^2 in 3D) plus n x nrhs for the solve.
+    """
+
+    def __init__(self, devices, slots: int = 4, budget_bytes: int | None = None, **kw):
+        self.devices = list(devices)
+        self.servers = [Server(slots=slots, budget_bytes=budget_bytes, device=d, **kw) for d in self.devices]
+
+    @staticmethod
+    def assign(requests: list[Request], ndev: int) -> list[int]:
+        """Device index of each request (in the order given), by arrival time."""
+        dev_of_key: dict[str, int] = {}
+        load = [0.0] * ndev
+        out = [0] * len(requests)
+        for i in sorted(range(len(requests)), key=lambda k: (requests[k].arrival, k)):
+            q = requests[i]
+            n, nrhs = q.B.shape[0], (q.B.shape[1] if q.B.ndim > 1 else 1)
+            d = dev_of_key.get(q.key)
+            if d is None:
+                d = min(range(ndev), key=lambda k: (load[k], k))
+                dev_of_key[q.key] = d
+            out[i] = d
+            load[d] += (0.0 if q.repeat else float(n) ** 1.5) + float(n) * nrhs
+        return out
+
+    def run(self, requests: list[Request]) -> list[Request]:
+        where = self.assign(requests, len(self.servers))
+        shares = [[q for q, d in zip(requests, where) if d == k] for k in range(len(self.servers))]
+        errors = []
+
+        def drive(srv, reqs):
+            try:
+                if reqs:
+                    srv.run(reqs)
+            except Exception as e:  # surface to the caller
+                errors.append(e)
+
+        ths = [threading.Thread(target=drive, args=(srv, reqs), daemon=True)
+               for srv, reqs in zip(self.servers, shares)]
+        for th in ths:
+            th.start()
+        for th in ths:
+            th.join()
+        if errors:
+            raise errors[0]
+        return requests
+
+    @property
+    def factorizations(self) -> int:
+        return sum(s.factorizations for s in self.servers)
+
+    def close(self):
+        for s in self.servers:
+            s.close()
+
+
 def latency_summary(reqs: list[Request]) -> dict:
     lat = np.array([q.done - q.arrival for q in reqs]) * 1e3
     rep = np.array([q.done - q.arrival for q in reqs if q.repeat]) * 1e3
