@@ -117,6 +117,8 @@ typedef struct spchol_options {
   int profile;            /* 1: the persistent kernels time every task (per-type busy time and the
                              time spent waiting for a ready task, summed over CTAs) into the stats;
                              2: additionally record each task's start and end (spchol_trace_get) */
+  int solve_tile_rows;    /* rows per triangular-solve tile of the panels more than 128 levels below
+                             the root, 8..256; 0 = default (64).  Panels nearer the root take 32 */
   int sched;              /* which ready task runs first in the dynamic schedules (deterministic 0,
                              and the update tiles of 2) -- the question of Section V-A:
                              0 (default): two ready rings; the diagonal and panel-solve tasks and,
@@ -275,9 +277,12 @@ int spchol_solve(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stre
  * (about n * nrhs <= 3.5e6 for grid matrices), SPCHOL_ETIMEOUT, SPCHOL_ECUDA.
  * The first call on a device looks up the array's device address (a CUDA
  * runtime query, no allocation); make that first call before any stream
- * capture.  All calls share the one array: calls whose work overlaps on the
- * GPU (different streams, threads or handles at the same time) race on it and
- * must be serialised by the caller.
+ * capture.  The address is kept for the life of the process (it assumes the
+ * device is not reset meanwhile).  Like spchol_solve, the call returns after
+ * its stream's work, and the read-back of its status, have completed.  All
+ * calls share the one array: calls whose work overlaps on the GPU (different
+ * streams, threads or handles at the same time) race on it and must be
+ * serialised by the caller.
  */
 int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, void* stream);
 

@@ -92,11 +92,10 @@ struct spchol_handle_s {
   FanRec* d_fan_rec = nullptr;  // the gather's records (a separate allocation)
   // fan-in solves: Plan::st_zf and friends, and the tiles' buffers for up to
   // fan_nrhs right-hand sides
-  int64_t *d_st_zf = nullptr, *d_st_zb = nullptr, *d_st_roff = nullptr;
+  int64_t *d_st_zf = nullptr, *d_st_zb = nullptr;
   // fan-in gather tasks: Plan::gat_first and friends, and the live counters
   int32_t *d_gat_first = nullptr, *d_gat_pc = nullptr, *d_pc_owner = nullptr, *d_gdiag0 = nullptr,
           *d_tdep0 = nullptr, *d_gdiag = nullptr, *d_tdep = nullptr;
-  int32_t* d_rt_rng = nullptr;
   Plan::SolveFanRec* d_rt_rec = nullptr;
   double *d_zf = nullptr, *d_zb = nullptr;
   int fan_nrhs = 0;
@@ -407,7 +406,6 @@ int setup_device(spchol_handle_t h) {
          o_fanp = fan ? r64(P.fan_ptr.size()) : 0,
          o_fane = fan ? A.reserve(std::max<size_t>(P.fan_ent.size(), 1) * sizeof(FanEnt)) : 0,
          o_stzf = fan ? r64(P.st_zf.size()) : 0, o_stzb = fan ? r64(P.st_zb.size()) : 0,
-         o_stro = fan ? r64(P.st_roff.size()) : 0, o_rtrng = fan ? r32(P.rt_rng.size()) : 0,
          o_rtrec = fan ? A.reserve(std::max<size_t>(P.rt_rec.size(), 1) * sizeof(Plan::SolveFanRec)) : 0,
          o_gatf = fan ? r32(P.gat_first.size()) : 0, o_gatp = fan ? r32(P.gat_pc.size()) : 0,
          o_pco = fan ? r32(P.pc_owner.size()) : 0, o_gd0 = fan ? r32(P.gdiag0.size()) : 0,
@@ -519,8 +517,6 @@ int setup_device(spchol_handle_t h) {
     h->d_fan_ent = (FanEnt*)(b + o_fane);
     h->d_st_zf = (int64_t*)(b + o_stzf);
     h->d_st_zb = (int64_t*)(b + o_stzb);
-    h->d_st_roff = (int64_t*)(b + o_stro);
-    h->d_rt_rng = (int32_t*)(b + o_rtrng);
     h->d_rt_rec = (Plan::SolveFanRec*)(b + o_rtrec);
     h->d_gat_first = (int32_t*)(b + o_gatf);
     h->d_gat_pc = (int32_t*)(b + o_gatp);
@@ -575,7 +571,6 @@ int setup_device(spchol_handle_t h) {
   if (fan && ((rc = upload(h, h->d_fan_off, P.fan_off)) || (rc = upload(h, h->d_fan_task, P.fan_task)) ||
               (rc = upload(h, h->d_fan_ptr, P.fan_ptr)) || (rc = upload(h, h->d_fan_ent, P.fan_ent)) ||
               (rc = upload(h, h->d_st_zf, P.st_zf)) || (rc = upload(h, h->d_st_zb, P.st_zb)) ||
-              (rc = upload(h, h->d_st_roff, P.st_roff)) || (rc = upload(h, h->d_rt_rng, P.rt_rng)) ||
               (rc = upload(h, h->d_gat_first, P.gat_first)) || (rc = upload(h, h->d_gat_pc, P.gat_pc)) ||
               (rc = upload(h, h->d_pc_owner, P.pc_owner)) || (rc = upload(h, h->d_gdiag0, P.gdiag0)) ||
               (rc = upload(h, h->d_tdep0, P.tdep0)) || (rc = upload(h, h->d_rt_rec, P.rt_rec))))
@@ -903,8 +898,6 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
     a.zb = h->d_zb;
     a.st_zf = h->d_st_zf;
     a.st_zb = h->d_st_zb;
-    a.st_roff = h->d_st_roff;
-    a.rt_rng = h->d_rt_rng;
     a.rt_rec = h->d_rt_rec;
   }
   a.ring = h->d_ring;
@@ -1341,8 +1334,6 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
     a.zb = zb;
     a.st_zf = h->d_st_zf;
     a.st_zb = h->d_st_zb;
-    a.st_roff = h->d_st_roff;
-    a.rt_rng = h->d_rt_rng;
     a.rt_rec = h->d_rt_rec;
   }
   a.ring = ring;

@@ -138,14 +138,12 @@ struct SolveArgs {
   const int32_t* ft_succ;
   int32_t* ftdep;
   // fan-in mode (null otherwise, see Plan::st_zf): the tiles' forward and
-  // backward buffers (nrhs columns each), their offsets, the tiles' first rows
-  // in the row lists and the rows of each panel's gather-list entries
+  // backward buffers (nrhs columns each), their offsets, and the records of
+  // each panel's forward gather list
   double* zf;
   double* zb;
   const int64_t* st_zf;
   const int64_t* st_zb;
-  const int64_t* st_roff;
-  const int32_t* rt_rng;
   const Plan::SolveFanRec* rt_rec;
   unsigned long long* prof;  // optional: [0..3] busy ns per task type, [4] wait ns
   unsigned long long* trace; // optional: per task id, start and end ns

@@ -9,7 +9,7 @@
 
 namespace spchol {
 
-constexpr int kSolveTileRows = 256;  // one row per thread of a solve CTA
+constexpr int kSolveTileRows = 64;  // rows per solve tile below the near-root band (staged in 32-row chunks)
 constexpr int kTrsmTileRows = 64;
 constexpr int kFp64TcMinWidth = 16;
 
@@ -26,6 +26,7 @@ inline void default_options(spchol_options* o) {
   o->ir_tol = 1e-12;
   o->fault_inject = 0;
   o->profile = 0;
+  o->solve_tile_rows = 0;
   o->sched = 0;
   o->dev_alloc = nullptr;
   o->dev_free = nullptr;
@@ -40,6 +41,7 @@ inline bool options_valid(const spchol_options& o) {
          o.ctas_per_sm >= 0 && o.fault_inject >= 0 && o.fault_inject <= 1 && o.deterministic >= 0 &&
          o.deterministic <= 2 &&
          o.profile >= 0 && o.profile <= 2 && o.sched >= 0 && o.sched <= 1 &&
+         (o.solve_tile_rows == 0 || (o.solve_tile_rows >= 8 && o.solve_tile_rows <= 256)) &&
          (o.dev_alloc == nullptr) == (o.dev_free == nullptr);
 }
 
@@ -59,7 +61,7 @@ inline PlanParams params_from(const spchol_options& o) {
   }
   p.trsm_rows = kTrsmTileRows;
   p.fifo = o.sched == 1;
-  p.solve_rows = kSolveTileRows;
+  p.solve_rows = o.solve_tile_rows > 0 ? o.solve_tile_rows : kSolveTileRows;
   if (o.deterministic) {
     p.deterministic = true;
     p.fanin = o.deterministic == 2;

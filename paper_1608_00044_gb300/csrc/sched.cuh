@@ -228,6 +228,44 @@ __device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task
   }
 }
 
+// Whole warp, all 32 lanes converged: push the ready tasks the lanes hold
+// (t[u] >= 0, u < N) to one ring of a Ring2, with one reservation of slots
+// per warp instead of one contended tail update per task (a backward
+// diagonal task near the root releases thousands of tiles).  Same visibility
+// precondition as ring_push_one.
+template <int N>
+__device__ __forceinline__ void ring2_push_warp(const Ring2& q, bool hi, const int (&t)[N]) {
+  hi = hi && q.n_hi > 0;
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  int cnt = 0;
+#pragma unroll
+  for (int u = 0; u < N; ++u) cnt += t[u] >= 0 ? 1 : 0;
+  int incl = cnt;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int v = __shfl_up_sync(full, incl, d);
+    if (lane >= d) incl += v;
+  }
+  const int total = __shfl_sync(full, incl, 31);
+  if (total == 0) return;
+  int base = 0;
+  if (lane == 31) base = atomicAdd(&q.ctrl[hi ? kHiTail : kTail], total);
+  base = __shfl_sync(full, base, 31) + incl - cnt;
+  int* slots = hi ? q.hi : q.lo;
+  const int n = hi ? q.n_hi : q.n_lo;
+#pragma unroll
+  for (int u = 0; u < N; ++u)
+    if (t[u] >= 0) {
+      if (base < n) {
+        st_release(&slots[base], t[u]);
+      } else {
+        atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+      }
+      ++base;
+    }
+}
+
 // Continuation: a task made ready by the running one is kept for this CTA's
 // next turn if none is kept yet (*next, shared memory, -1 when empty), else
 // pushed to the high-priority ring.  Any thread; next == nullptr: always push.

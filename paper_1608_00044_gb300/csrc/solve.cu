@@ -315,22 +315,48 @@ __device__ __forceinline__ void copy_batched(int total, Src src, Dst dst) {
   }
 }
 
-// L11^{-1} (w x w, column-major, read-only here) into shared memory with
-// leading dimension lx, the lower triangle only; loads in batches of 8.
+// ---------------------------------------------------------------- asynchronous staging of the factor
+// The factor (the panels and the diagonal-block inverses) was written by the
+// factorization, an earlier launch, and is only read here, so it may come
+// through L1.  Element-sized cp.async copies put every load of a block in
+// flight at once (a thread issues them all before waiting), where plain loads
+// in batches of eight cost one memory round trip per batch, and they allow an
+// odd leading dimension in shared memory, which keeps both a row walk and a
+// column walk free of bank conflicts.
+__device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+template <typename T>
+__device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
+  if constexpr (sizeof(T) == 8)
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(sm_u32(dst)), "l"(src) : "memory");
+  else
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(sm_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// L11^{-1} (w x w, column-major) into shared memory with leading dimension lx,
+// all copies in flight; the caller commits, waits and synchronises.  Only the
+// lower triangle is read later.
 __device__ __forceinline__ void stage_inverse(const double* __restrict__ X, int w, double* __restrict__ Xs, int lx) {
-  const int total = w * w, nt = blockDim.x;
-  for (int base = threadIdx.x; base < total; base += 8 * nt) {
-    double v[8];
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * nt, i = idx % w, j = idx / w;
-      v[u] = (idx < total && i >= j) ? X[idx] : 0.0;
-    }
-#pragma unroll
-    for (int u = 0; u < 8; ++u) {
-      const int idx = base + u * nt, i = idx % w, j = idx / w;
-      if (idx < total) Xs[i + j * lx] = v[u];
-    }
+  const int total = w * w;
+  for (int idx = threadIdx.x; idx < total; idx += blockDim.x) {
+    const int i = idx % w, j = idx / w;
+    if (i >= j) cp_async_elem(Xs + i + j * lx, X + idx);
+  }
+  cp_async_commit_group();
+}
+
+// Rows row0 .. row0 + cnt - 1 of the w columns of a column-major panel into
+// Ls[i + j * lds]; the caller commits.
+template <typename T>
+__device__ __forceinline__ void stage_rows(const T* __restrict__ P, int ld, int row0, int cnt, int w, T* Ls, int lds) {
+  for (int idx = threadIdx.x; idx < cnt * w; idx += blockDim.x) {
+    const int i = idx % cnt, j = idx / cnt;
+    cp_async_elem(Ls + i + j * lds, P + row0 + i + (size_t)j * ld);
   }
 }
 
@@ -514,6 +540,7 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     if constexpr (FAN) fwd_gather(a, s, f, w, Ys, r0, nrc, reinterpret_cast<unsigned char*>(Ys + kSolveNRC * w));
+    cp_async_wait_group<0>();  // the inverse (first pass)
     __syncthreads();
     for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
       const int c = p % half, r = p / half;
@@ -562,6 +589,7 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
       __syncthreads();
       bwd_gather(a, s, w, Ys, r0, nrc);
     }
+    cp_async_wait_group<0>();  // the inverse (first pass)
     __syncthreads();
     for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
       const int c = p % half, r = p / half;
@@ -589,47 +617,80 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
   }
 }
 
-// y[rows of tile] -= L21[tile] y_s.  A thread owns one row and NPER of the
-// right-hand sides, g + G q (q < NPER) for its group g of G: with 8
-// right-hand sides, four groups of 64 threads take two each (every warp busy on
-// the 64-row tiles near the root); with one, all threads take rows.  The group
-// is uniform in a warp and the right-hand sides a thread owns are fixed at
-// compile time, so no FMA is spent on another group's right-hand sides.
-template <typename T, int NPER, bool FAN>
-__device__ void fwd_tile_rows(const SolveArgs& a, const T* P, int ld, int row0, int cnt, const int32_t* R, int w,
-                              const double* Ys, int r0, int nrc, int G, double* z) {
-  const int rows_per = blockDim.x / G;
-  const int g = threadIdx.x / rows_per, il = threadIdx.x - g * rows_per;
-  int nv = 0;  // right-hand sides of this thread that exist
-#pragma unroll
-  for (int q = 0; q < NPER; ++q) nv += (g + G * q < nrc) ? 1 : 0;
-  if (nv == 0) return;
-  for (int i = il; i < cnt; i += rows_per) {
-    const T* Pi = P + row0 + i;
-    double acc[NPER];
-#pragma unroll
-    for (int q = 0; q < NPER; ++q) acc[q] = 0.0;
-    // the row's entries in batches of 8 independent loads, so that their
-    // latencies overlap instead of following one another
-    for (int j0 = 0; j0 < w; j0 += 8) {
-      double l[8];
-#pragma unroll
-      for (int u = 0; u < 8; ++u) l[u] = (j0 + u < w) ? (double)Pi[(size_t)(j0 + u) * ld] : 0.0;
-      const int nu = min(8, w - j0);
-      for (int u = 0; u < nu; ++u) {
-#pragma unroll
-        for (int q = 0; q < NPER; ++q) acc[q] += l[u] * Ys[j0 + u + (g + G * q) * w];
-      }
+// ---------------------------------------------------------------- panel tiles on the FP64 / FP32 pipes
+// A tile's rows go through shared memory in chunks of kTileCH rows, double
+// buffered: the copies of chunk c + 1 are in flight while chunk c is used.
+// The work of a chunk is spread over the eight warps by right-hand side and,
+// when there are fewer than eight right-hand sides, by a split of the dot
+// products' range (parts = 8 / the right-hand sides rounded up to a power of
+// two), whose partial sums meet in shared memory.
+constexpr int kTileCH = 32;          // rows per chunk: one per lane
+constexpr int kTileLD = kTileCH + 1;  // odd: a lane per row or a lane per column, both conflict free
+
+__device__ __forceinline__ int tile_groups(int nrc) { return nrc > 4 ? 8 : nrc > 2 ? 4 : nrc > 1 ? 2 : 1; }
+
+// y[rows of tile] -= L21[tile] y_s.  Warp wp takes right-hand side wp % G and
+// part wp / G of the columns; lane i the chunk's row i.
+template <typename T, bool FAN>
+__device__ void fwd_tile_fma(const SolveArgs& a, const T* P, int ld, int row0, int cnt, const int32_t* R, int f,
+                             int w, double* sm, double* z) {
+  double* Ys = sm;                                                   // [kSolveNRC][w]
+  double* Red = Ys + kSolveNRC * w;                                  // [8][kTileCH] partial sums
+  T* Lb = reinterpret_cast<T*>(Red + 8 * kTileCH);                   // [2][w][kTileLD]
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int nchunk = (cnt + kTileCH - 1) / kTileCH;
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    const int G = tile_groups(nrc), parts = 8 / G;
+    const int g = warp % G, part = warp / G;
+    const int k0 = part * w / parts, k1 = (part + 1) * w / parts;
+    __syncthreads();  // the previous pass is done with Ys and the buffers
+    stage_rows(P, ld, row0, min(kTileCH, cnt), w, Lb, kTileLD);
+    cp_async_commit_group();
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, rr = idx / w;
+      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy);
     }
-    if constexpr (FAN) {  // the tile's buffer: its rows x nrhs
-#pragma unroll
-      for (int q = 0; q < NPER; ++q)
-        if (q < nv) z[i + (size_t)(r0 + g + G * q) * cnt] = -acc[q];
-    } else {
-      const int gr = R[row0 + i];
-#pragma unroll
-      for (int q = 0; q < NPER; ++q)
-        if (q < nv) red_add(a.Y + gr + (size_t)(r0 + g + G * q) * a.ldy, -acc[q]);
+    for (int c = 0; c < nchunk; ++c) {
+      const int c0 = c * kTileCH, nc = min(kTileCH, cnt - c0);
+      if (c + 1 < nchunk) {
+        stage_rows(P, ld, row0 + c0 + kTileCH, min(kTileCH, cnt - c0 - kTileCH), w,
+                   Lb + ((c + 1) & 1) * w * kTileLD, kTileLD);
+        cp_async_commit_group();
+        cp_async_wait_group<1>();  // chunk c has landed (this thread's copies)
+      } else {
+        cp_async_wait_group<0>();
+      }
+      __syncthreads();  // ... and every thread's
+      const T* L = Lb + (c & 1) * w * kTileLD + lane;
+      double acc = 0.0;
+      if (g < nrc && lane < nc) {
+        const double* y = Ys + g * w;
+        double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+        int k = k0;
+        for (; k + 3 < k1; k += 4) {
+          s0 += (double)L[k * kTileLD] * y[k];
+          s1 += (double)L[(k + 1) * kTileLD] * y[k + 1];
+          s2 += (double)L[(k + 2) * kTileLD] * y[k + 2];
+          s3 += (double)L[(k + 3) * kTileLD] * y[k + 3];
+        }
+        for (; k < k1; ++k) s0 += (double)L[k * kTileLD] * y[k];
+        acc = (s0 + s1) + (s2 + s3);
+      }
+      if (parts > 1) {
+        Red[warp * kTileCH + lane] = acc;
+        __syncthreads();
+        acc = 0.0;
+        if (part == 0)
+          for (int q = 0; q < parts; ++q) acc += Red[(g + q * G) * kTileCH + lane];
+      }
+      if (part == 0 && g < nrc && lane < nc) {
+        if constexpr (FAN)  // the tile's buffer: its rows x nrhs
+          z[c0 + lane + (size_t)(r0 + g) * cnt] = -acc;
+        else
+          red_add(a.Y + R[row0 + c0 + lane] + (size_t)(r0 + g) * a.ldy, -acc);
+      }
+      __syncthreads();  // buffer c & 1 (and Red) are refilled next
     }
   }
 }
@@ -679,30 +740,8 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
       return;
     }
   }
-  double* Ys = sm;  // [kSolveNRC][w], zero past nrc
-  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
-    const int nrc = min(kSolveNRC, a.nrhs - r0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < w * kSolveNRC; idx += blockDim.x) {
-      const int j = idx % w, rr = idx / w;
-      Ys[idx] = rr < nrc ? ldcg(a.Y + f + j + (size_t)(r0 + rr) * a.ldy) : 0.0;
-    }
-    __syncthreads();
-    if (nrc >= 5 && cnt <= 32)
-      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 8, z);
-    else if (nrc >= 5)
-      fwd_tile_rows<T, 2, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4, z);
-    else if (nrc >= 3)
-      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, 4, z);
-    else
-      fwd_tile_rows<T, 1, FAN>(a, P, ld, row0, cnt, R, w, Ys, r0, nrc, nrc, z);
-  }
+  fwd_tile_fma<T, FAN>(a, P, ld, row0, cnt, R, f, w, sm, z);
 }
-
-// y_s -= L21[tile]^T x[rows of tile]: rows staged kBwdCH at a time in shared
-// memory (one batched pass and one barrier per chunk); thread (j, rr) sums
-// column j of the chunk against x with four accumulators.
-constexpr int kBwdCH = 64;
 
 // y_s -= L21[tile]^T x[rows of tile] on the tensor cores (FP64 panels, 16 <= w
 // <= 64): A = L21[tile]^T (w x rows), the tile's rows in passes of 64, each with
@@ -754,6 +793,90 @@ __device__ void bwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row
   }
 }
 
+// y_s -= L21[tile]^T x[rows of tile], the tile's rows in chunks as in the
+// forward tile, with x of the next chunk loaded into registers while the
+// current one is used.  Output (j, g) is a dot product over the tile's rows;
+// with few outputs (few right-hand sides) RG thread groups take a share of
+// each chunk's rows each and their partial sums meet in shared memory.
+template <typename T, bool FAN>
+__device__ void bwd_tile_fma(const SolveArgs& a, const T* P, int ld, int row0, int cnt, const int32_t* R, int f,
+                             int w, double* sm, double* z) {
+  double* Xc = sm;                                     // [2][kSolveNRC][kTileCH]
+  double* Red = Xc + 2 * kSolveNRC * kTileCH;          // [kSolveThreads]
+  T* Lb = reinterpret_cast<T*>(Red + kSolveThreads);   // [2][w][kTileLD]
+  const int tid = threadIdx.x;
+  const int nchunk = (cnt + kTileCH - 1) / kTileCH;
+  const int xi = tid % kTileCH, xr = tid / kTileCH;    // the x entry this thread loads (256 = 8 x 32)
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    const int O = w * nrc;
+    const int RG = O <= 64 ? 4 : O <= 128 ? 2 : 1;
+    const int per = blockDim.x / RG, rg = tid / per, u = tid - rg * per;
+    const int ri0 = rg * (kTileCH / RG), ri1 = ri0 + kTileCH / RG;
+    double part[2] = {0.0, 0.0};
+    __syncthreads();  // the previous pass is done with the buffers
+    stage_rows(P, ld, row0, min(kTileCH, cnt), w, Lb, kTileLD);
+    cp_async_commit_group();
+    if (xr < nrc)
+      Xc[xr * kTileCH + xi] = xi < min(kTileCH, cnt) ? ldcg(a.Y + R[row0 + xi] + (size_t)(r0 + xr) * a.ldy) : 0.0;
+    for (int c = 0; c < nchunk; ++c) {
+      const int c0 = c * kTileCH, nc = min(kTileCH, cnt - c0);
+      const int c1 = c0 + kTileCH, nc1 = min(kTileCH, cnt - c1);
+      if (c + 1 < nchunk) {
+        stage_rows(P, ld, row0 + c1, nc1, w, Lb + ((c + 1) & 1) * w * kTileLD, kTileLD);
+        cp_async_commit_group();
+        cp_async_wait_group<1>();
+      } else {
+        cp_async_wait_group<0>();
+      }
+      double xn = 0.0;  // x of the next chunk, loaded while this one is used
+      if (c + 1 < nchunk && xr < nrc && xi < nc1) xn = ldcg(a.Y + R[row0 + c1 + xi] + (size_t)(r0 + xr) * a.ldy);
+      __syncthreads();
+      const T* L = Lb + (c & 1) * w * kTileLD;
+      const double* X = Xc + (c & 1) * kSolveNRC * kTileCH;
+      const int i1 = min(ri1, nc);
+#pragma unroll
+      for (int q = 0; q < 2; ++q) {
+        const int p = u + q * per;
+        if (p < O) {
+          const int j = p % w, g = p / w;
+          const T* lj = L + j * kTileLD;
+          const double* xg = X + g * kTileCH;
+          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+          int i = ri0;
+          for (; i + 3 < i1; i += 4) {
+            s0 += (double)lj[i] * xg[i];
+            s1 += (double)lj[i + 1] * xg[i + 1];
+            s2 += (double)lj[i + 2] * xg[i + 2];
+            s3 += (double)lj[i + 3] * xg[i + 3];
+          }
+          for (; i < i1; ++i) s0 += (double)lj[i] * xg[i];
+          part[q] += (s0 + s1) + (s2 + s3);
+        }
+      }
+      if (c + 1 < nchunk && xr < nrc) Xc[((c + 1) & 1) * kSolveNRC * kTileCH + xr * kTileCH + xi] = xn;
+      __syncthreads();  // buffer c & 1 is refilled next
+    }
+    if (RG > 1) {  // per >= O here: one output per thread of each group
+      Red[tid] = part[0];
+      __syncthreads();
+      if (rg == 0)
+        for (int k = 1; k < RG; ++k) part[0] += Red[u + k * per];
+    }
+#pragma unroll
+    for (int q = 0; q < 2; ++q) {
+      const int p = u + q * per;
+      if (rg == 0 && p < O) {
+        const int j = p % w, g = p / w;
+        if constexpr (FAN)
+          z[j + (size_t)(r0 + g) * w] = -part[q];
+        else
+          red_add(a.Y + f + j + (size_t)(r0 + g) * a.ldy, -part[q]);
+      }
+    }
+  }
+}
+
 template <typename T, bool FAN>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
@@ -768,86 +891,34 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
       return;
     }
   }
-  constexpr int CH = kBwdCH, LD = CH + 1;
-  double* Lc = sm;                 // [w][LD]: Lc[i + j LD] = L21[c0 + i][j]
-  double* Xc = Lc + w * LD;        // [nrc][CH]
-  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
-    const int nrc = min(kSolveNRC, a.nrhs - r0);
-    // each thread owns (j, rr) pairs p = tid + q * blockDim
-    double part[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) part[q] = 0.0;
-    for (int c0 = 0; c0 < cnt; c0 += CH) {
-      const int nc = min(CH, cnt - c0);
-      __syncthreads();
-      for (int base = threadIdx.x; base < CH * w; base += 8 * blockDim.x) {
-        double v[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int idx = base + u * blockDim.x, i = idx % CH, j = idx / CH;
-          v[u] = (idx < CH * w && i < nc) ? (double)P[row0 + c0 + i + (size_t)j * ld] : 0.0;
-        }
-#pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          const int idx = base + u * blockDim.x, i = idx % CH, j = idx / CH;
-          if (idx < CH * w) Lc[i + j * LD] = v[u];
-        }
-      }
-      for (int idx = threadIdx.x; idx < CH * nrc; idx += blockDim.x) {
-        const int i = idx % CH, rr = idx / CH;
-        Xc[rr * CH + i] = (i < nc) ? ldcg(a.Y + R[row0 + c0 + i] + (size_t)(r0 + rr) * a.ldy) : 0.0;
-      }
-      __syncthreads();
-#pragma unroll
-      for (int q = 0; q < 4; ++q) {
-        const int p = threadIdx.x + q * blockDim.x;
-        if (p < w * nrc) {
-          const int j = p % w, rr = p / w;
-          const double* lj = Lc + j * LD;
-          const double* xr = Xc + rr * CH;
-          double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
-          for (int i = 0; i < nc; i += 4) {  // rows past nc are zero in both
-            s0 += lj[i] * xr[i];
-            s1 += lj[i + 1] * xr[i + 1];
-            s2 += lj[i + 2] * xr[i + 2];
-            s3 += lj[i + 3] * xr[i + 3];
-          }
-          part[q] += (s0 + s1) + (s2 + s3);
-        }
-      }
-    }
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const int p = threadIdx.x + q * blockDim.x;
-      if (p < w * nrc) {
-        const int j = p % w, rr = p / w;
-        if constexpr (FAN)
-          z[j + (size_t)(r0 + rr) * w] = -part[q];
-        else
-          red_add(a.Y + f + j + (size_t)(r0 + rr) * a.ldy, -part[q]);
-      }
-    }
-  }
+  bwd_tile_fma<T, FAN>(a, P, ld, row0, cnt, R, f, w, sm, z);
 }
 
 // Lower the counters cnt[id] of ids list[e] (or e itself when list is null),
-// e in [e0, e1), by one, and push task task0 + id for each that reaches zero.
-// Whole CTA; each thread issues its decrements in batches of 8 whose round
-// trips overlap (a panel near the root releases thousands of tiles).
+// e in [e0, e1), by one, and push task task0 + id for each that reaches zero
+// (the first one kept as the CTA's continuation if next is given and free).
+// Whole CTA, all threads through the same iterations; each thread issues its
+// decrements in batches of 8 whose round trips overlap, and each warp
+// reserves ring slots for its ready tasks at once (a panel near the root
+// releases thousands of tiles).
 __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* list, int e0, int e1, int32_t* cnt,
                                               int task0, int* next) {
-  for (int base = e0 + threadIdx.x; base < e1; base += 8 * blockDim.x) {
+  for (int b0 = e0; b0 < e1; b0 += 8 * blockDim.x) {
     int id[8], old[8];
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
-      const int e = base + u * blockDim.x;
+      const int e = b0 + threadIdx.x + u * blockDim.x;
       id[u] = e < e1 ? (list ? list[e] : e) : -1;
     }
 #pragma unroll
     for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_acqrel(&cnt[id[u]], -1) : 0;
+    int ready[8];
 #pragma unroll
-    for (int u = 0; u < 8; ++u)
-      if (id[u] >= 0 && old[u] == 1) keep_or_push(q, next, task0 + id[u]);
+    for (int u = 0; u < 8; ++u) {
+      ready[u] = (id[u] >= 0 && old[u] == 1) ? task0 + id[u] : -1;
+      if (ready[u] >= 0 && next != nullptr && atomicCAS(next, -1, ready[u]) == -1) ready[u] = -1;  // kept
+    }
+    ring2_push_warp(q, true, ready);
   }
 }
 
@@ -983,7 +1054,13 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin) {
   const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double) +
                       (fanin ? solve_fan_smem_bytes(max_w) : 0);
-  const size_t tile = ((size_t)max_w * (kBwdCH + 1) + kBwdCH * kSolveNRC) * sizeof(double);
+  // panel tiles: two chunk buffers of max_w x kTileLD (FP64 bound) plus, forward,
+  // the right-hand sides and the partial sums, backward, two x chunks and the
+  // partial sums
+  const size_t bufs = 2 * (size_t)max_w * kTileLD * sizeof(double);
+  const size_t fwd = ((size_t)kSolveNRC * max_w + 8 * kTileCH) * sizeof(double);
+  const size_t bwd = (2 * (size_t)kSolveNRC * kTileCH + kSolveThreads) * sizeof(double);
+  const size_t tile = bufs + (fwd > bwd ? fwd : bwd);
   size_t need = diag > tile ? diag : tile;
   if (tc_tiles && max_w >= kOzMinW && need < kOzSmemBytes) need = kOzSmemBytes;
   return need;

@@ -34,6 +34,7 @@ class Options(ctypes.Structure):
         ("ir_tol", ctypes.c_double),
         ("fault_inject", ctypes.c_int),
         ("profile", ctypes.c_int),
+        ("solve_tile_rows", ctypes.c_int),
         ("sched", ctypes.c_int),
         ("dev_alloc", ctypes.c_void_p),  # function pointers (DEV_ALLOC_FN / DEV_FREE_FN), NULL = the pool
         ("dev_free", ctypes.c_void_p),
@@ -160,7 +161,7 @@ def default_options(allocator=None, **kw) -> Options:
 def default_options_host(**kw) -> Options:
     """The defaults of include/spchol.h filled without loading the GPU library."""
     o = Options(precision=FP64, max_width=64, relax_zeros=4, tile_rows=0, ctas_per_sm=0, deterministic=0,
-                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0, sched=0,
+                wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0, solve_tile_rows=0, sched=0,
                 dev_alloc=None, dev_free=None, alloc_ctx=None)
     for k, v in kw.items():
         setattr(o, k, v)

@@ -634,3 +634,21 @@ def test_autotuner_picks_a_working_configuration(tmp_path):
     h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
     assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
     spchol.destroy(h)
+
+
+@pytest.mark.parametrize("name,W,precision,det", [
+    ("lap3d_32", 16, "FP64", 0), ("lap3d_24", 8, "FP64", 0), ("lap2d_256", 4, "FP64", 0),
+    ("lap3d_40", 32, "FP64", 0), ("lap3d_32", 16, "FP64_TC", 0), ("lap3d_24", 8, "FP64", 2),
+])
+def test_deep_panel_trees_elementwise(name, W, precision, det):
+    # Panel trees deeper than the 128 levels near the root whose panels get the
+    # short tiles: the 64-row update and panel-solve tiles and the 256-row solve
+    # tiles of the deeper panels are compared with the oracle entry by entry
+    # (L within 1e-11 of max |L|) and through the solution (within 1e-10 of
+    # the oracle's, berr <= 1e-13).
+    A, perm, B = gridgen.workload(name)
+    X, st = _check(A, perm, B, max_width=W, precision=getattr(spchol, precision), deterministic=det)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    Xo = f.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-10 * np.abs(Xo).max()
