@@ -689,11 +689,16 @@ def trace_summary(args):
     torch.cuda.set_device(0)
     A, perm, b = _workload(args.workload)
     vals = torch.from_numpy(A.values).cuda()
-    out = {"mode": "trace-summary", "workload": f"{args.workload}: {_describe(A)}, n={A.n}", "arms": {}}
+    prec = {"fp64": spchol.FP64, "fp32": spchol.FP32, "tf32": spchol.TF32, "tf32x3": spchol.TF32X3,
+            "fp64tc": spchol.FP64_TC}[args.precision]
+    out = {"mode": "trace-summary", "workload": f"{args.workload}: {_describe(A)}, n={A.n}",
+           "precision": args.precision, "arms": {}}
     arms = (("dynamic_priority", 0, 0), ("dynamic_fifo", 0, 1), ("static", 1, 0), ("fanin", 2, 0))
+    if args.deterministic:  # one arm only
+        arms = tuple(x for x in arms if x[1] == args.deterministic)
     for label, det, sched in arms:
-        kw = dict(max_width=args.width, deterministic=det, sched=sched)
-        plan = hostplan.HostPlan(A.n, A.colptr, A.rowind, perm, **kw)
+        kw = dict(max_width=args.width, deterministic=det, sched=sched, precision=prec)
+        plan = hostplan.HostPlan(A.n, A.colptr, A.rowind, perm, **{k: v for k, v in kw.items() if k != "precision"})
         sc = plan.scalars()
         parent = plan.get(hostplan.PARENT)
         fcol = plan.get(hostplan.FCOL)

@@ -325,6 +325,12 @@ __device__ __forceinline__ void copy_batched(int total, Src src, Dst dst) {
 // column walk free of bank conflicts.
 __device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
+__device__ __forceinline__ int atom_add_relaxed(int* p, int v) {
+  int old;
+  asm volatile("atom.relaxed.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
   if constexpr (sizeof(T) == 8)
@@ -360,10 +366,6 @@ __device__ __forceinline__ void stage_rows(const T* __restrict__ P, int ld, int 
   }
 }
 
-// y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
-// every entry is an independent dot product, no sequential substitution.
-// Thread (r, c) computes rows c and w - 1 - c for right-hand side r: i + 1
-// and w - i terms, w + 1 in all, so every thread and warp does the same work.
 // Stage y_s (w entries of right-hand sides r0 .. r0+nrc-1) as the B operand.
 __device__ __forceinline__ void oz_stage_ys(const SolveArgs& a, const OzBuf& b, int f, int w, int r0, int nrc) {
   const double* Y = a.Y + f + (size_t)r0 * a.ldy;
@@ -523,6 +525,15 @@ __device__ void bwd_gather(const SolveArgs& a, int s, int w, double* Ys, int r0,
   __syncthreads();
 }
 
+// Lanes per dot product of the diagonal solves: the 256 threads cover
+// (w / 2) row pairs x nrc right-hand sides x P parts.
+__device__ __forceinline__ int diag_parts(int nrc) { return nrc == 1 ? 8 : nrc == 2 ? 4 : nrc <= 4 ? 2 : 1; }
+
+// y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
+// every entry is an independent dot product, no sequential substitution.
+// Lanes (r, c, q) compute rows c and w - 1 - c for right-hand side r, terms
+// k = q mod P: i + 1 and w - i terms, w + 1 in all, so every thread and warp
+// does the same work.
 template <bool FAN>
 __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
@@ -542,33 +553,50 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
     if constexpr (FAN) fwd_gather(a, s, f, w, Ys, r0, nrc, reinterpret_cast<unsigned char*>(Ys + kSolveNRC * w));
     cp_async_wait_group<0>();  // the inverse (first pass)
     __syncthreads();
-    for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
-      const int c = p % half, r = p / half;
+    // With few right-hand sides each dot product is split over P lanes (k = q,
+    // q + P, ...), so that every warp -- and every sub-partition's FP64 pipe --
+    // takes a share; the parts meet by shuffles within the P lanes.
+    const int P = diag_parts(nrc);
+    const int total = (half * nrc * P + 31) & ~31;  // whole warps: every lane takes part in the shuffles
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+      const int q = p % P, cr = p / P, c = cr % half, r = cr / half;
+      const bool valid = cr < half * nrc;
       const double* y = Ys + r * w;
       const int i1 = c, i2 = w - 1 - c;
-      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-      int k = 0;
-      for (; k + 1 <= i1; k += 2) {
-        a0 += Xs[i1 + k * lx] * y[k];
-        a1 += Xs[i1 + (k + 1) * lx] * y[k + 1];
-      }
-      if (k <= i1) a0 += Xs[i1 + k * lx] * y[k];
-      if (i2 != i1) {
-        for (k = 0; k + 1 <= i2; k += 2) {
-          b0 += Xs[i2 + k * lx] * y[k];
-          b1 += Xs[i2 + (k + 1) * lx] * y[k + 1];
+      double a0 = 0.0, b0 = 0.0;
+      if (valid) {
+        double a1 = 0.0, b1 = 0.0;
+        int k = q;
+        for (; k + P <= i1; k += 2 * P) {
+          a0 += Xs[i1 + k * lx] * y[k];
+          a1 += Xs[i1 + (k + P) * lx] * y[k + P];
         }
-        if (k <= i2) b0 += Xs[i2 + k * lx] * y[k];
+        if (k <= i1) a0 += Xs[i1 + k * lx] * y[k];
+        if (i2 != i1) {
+          for (k = q; k + P <= i2; k += 2 * P) {
+            b0 += Xs[i2 + k * lx] * y[k];
+            b1 += Xs[i2 + (k + P) * lx] * y[k + P];
+          }
+          if (k <= i2) b0 += Xs[i2 + k * lx] * y[k];
+        }
+        a0 += a1;
+        b0 += b1;
       }
-      a.Y[f + i1 + (size_t)(r0 + r) * a.ldy] = a0 + a1;
-      if (i2 != i1) a.Y[f + i2 + (size_t)(r0 + r) * a.ldy] = b0 + b1;
+      for (int d = 1; d < P; d <<= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, d);
+        b0 += __shfl_xor_sync(0xffffffffu, b0, d);
+      }
+      if (valid && q == 0) {
+        a.Y[f + i1 + (size_t)(r0 + r) * a.ldy] = a0;
+        if (i2 != i1) a.Y[f + i2 + (size_t)(r0 + r) * a.ldy] = b0;
+      }
     }
   }
 }
 
 // x_s <- L11^{-T} y_s with the stored inverse: entry k is the dot product of
-// column k of L11^{-1} (rows k .. w-1) with y_s; thread (r, c) takes columns c
-// and w - 1 - c.
+// column k of L11^{-1} (rows k .. w-1) with y_s; lanes (r, c, q) take columns c
+// and w - 1 - c, rows k + q mod P.
 template <bool FAN>
 __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
@@ -591,28 +619,42 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
     }
     cp_async_wait_group<0>();  // the inverse (first pass)
     __syncthreads();
-    for (int p = threadIdx.x; p < half * nrc; p += blockDim.x) {
-      const int c = p % half, r = p / half;
+    const int P = diag_parts(nrc);  // as in the forward solve: dot products split over P lanes
+    const int total = (half * nrc * P + 31) & ~31;
+    for (int p = threadIdx.x; p < total; p += blockDim.x) {
+      const int q = p % P, cr = p / P, c = cr % half, r = cr / half;
+      const bool valid = cr < half * nrc;
       const double* y = Ys + r * w;
       const int k1 = c, k2 = w - 1 - c;
-      double a0 = 0.0, a1 = 0.0, b0 = 0.0, b1 = 0.0;
-      const double* x1 = Xs + k1 * lx;
-      int i = k1;
-      for (; i + 1 < w; i += 2) {
-        a0 += x1[i] * y[i];
-        a1 += x1[i + 1] * y[i + 1];
-      }
-      if (i < w) a0 += x1[i] * y[i];
-      if (k2 != k1) {
-        const double* x2 = Xs + k2 * lx;
-        for (i = k2; i + 1 < w; i += 2) {
-          b0 += x2[i] * y[i];
-          b1 += x2[i + 1] * y[i + 1];
+      double a0 = 0.0, b0 = 0.0;
+      if (valid) {
+        double a1 = 0.0, b1 = 0.0;
+        const double* x1 = Xs + k1 * lx;
+        int i = k1 + q;
+        for (; i + P < w; i += 2 * P) {
+          a0 += x1[i] * y[i];
+          a1 += x1[i + P] * y[i + P];
         }
-        if (i < w) b0 += x2[i] * y[i];
+        if (i < w) a0 += x1[i] * y[i];
+        if (k2 != k1) {
+          const double* x2 = Xs + k2 * lx;
+          for (i = k2 + q; i + P < w; i += 2 * P) {
+            b0 += x2[i] * y[i];
+            b1 += x2[i + P] * y[i + P];
+          }
+          if (i < w) b0 += x2[i] * y[i];
+        }
+        a0 += a1;
+        b0 += b1;
       }
-      a.Y[f + k1 + (size_t)(r0 + r) * a.ldy] = a0 + a1;
-      if (k2 != k1) a.Y[f + k2 + (size_t)(r0 + r) * a.ldy] = b0 + b1;
+      for (int d = 1; d < P; d <<= 1) {
+        a0 += __shfl_xor_sync(0xffffffffu, a0, d);
+        b0 += __shfl_xor_sync(0xffffffffu, b0, d);
+      }
+      if (valid && q == 0) {
+        a.Y[f + k1 + (size_t)(r0 + r) * a.ldy] = a0;
+        if (k2 != k1) a.Y[f + k2 + (size_t)(r0 + r) * a.ldy] = b0;
+      }
     }
   }
 }
@@ -910,14 +952,23 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
       const int e = b0 + threadIdx.x + u * blockDim.x;
       id[u] = e < e1 ? (list ? list[e] : e) : -1;
     }
+    // Relaxed decrements: every producer published its writes with a fence
+    // before its decrement, and the thread that brings a counter to zero
+    // fences before it pushes (or keeps) the task, so the fences order the
+    // producers' writes before the consumer's reads.
 #pragma unroll
-    for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_acqrel(&cnt[id[u]], -1) : 0;
+    for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_relaxed(&cnt[id[u]], -1) : 0;
     int ready[8];
+    bool any = false;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       ready[u] = (id[u] >= 0 && old[u] == 1) ? task0 + id[u] : -1;
-      if (ready[u] >= 0 && next != nullptr && atomicCAS(next, -1, ready[u]) == -1) ready[u] = -1;  // kept
+      any |= ready[u] >= 0;
     }
+    if (any) __threadfence();
+#pragma unroll
+    for (int u = 0; u < 8; ++u)
+      if (ready[u] >= 0 && next != nullptr && atomicCAS(next, -1, ready[u]) == -1) ready[u] = -1;  // kept
     ring2_push_warp(q, true, ready);
   }
 }
