@@ -622,7 +622,10 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
     const void* tmap = a.tmaps ? (const void*)(a.tmaps + 128 * (size_t)s) : nullptr;
     uint32_t ph = tmap ? *tma.phase : 0u;
     constexpr int kBuf = 2 * kUpdKC * STR;                // one buffer: A and B chunks
-    int* pos = reinterpret_cast<int*>(buf + 2 * kBuf);    // [kUpdTileM] row position in t
+    // FP32 panels: the shared memory sized for two FP64 buffers holds four FP32
+    // ones, so a tile of K <= 64 stages its whole K at once and waits once
+    constexpr int kSlots = sizeof(T) == 4 ? 4 : 2;
+    int* pos = reinterpret_cast<int*>(buf + kSlots * kBuf);  // [kUpdTileM] row position in t
     int* grow = pos + kUpdTileM;                          // [kUpdTileM] global row
     int* gcol = grow + kUpdTileM;                         // [kUpdTileN] global column (pass-local)
 
@@ -661,6 +664,43 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
       for (int rr = 0; rr < 2; ++rr)
 #pragma unroll
         for (int cc = 0; cc < 8; ++cc) acc[rr][cc] = acc_t(0);
+      if (sizeof(T) == 4 && nchunk <= kSlots) {
+        // every k-chunk in flight at once, one wait, then the arithmetic in
+        // the same chunk order as below (the same sums)
+        if (tmap) {
+          if (tid == 0) {
+            asm volatile("fence.proxy.async.global;" ::: "memory");
+            asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+            mbar_expect_tx(tma.mbar[0], 2 * kBoxBytes * (uint32_t)nchunk);
+            for (int c = 0; c < nchunk; ++c) {
+              tma_load_2d(buf + c * kBuf, tmap, u.row0 - oa, c * kUpdKC, tma.mbar[0]);
+              tma_load_2d(buf + c * kBuf + kUpdKC * STR, tmap, c0 - ob, c * kUpdKC, tma.mbar[0]);
+            }
+          }
+          if (!mbar_wait_parity(tma.mbar[0], ph & 1u) && tid == 0) atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_ETIMEOUT);
+          ph ^= 1u;
+        } else {
+          for (int c = 0; c < nchunk; ++c) {
+            const int k0 = c * kUpdKC, kc = min(kUpdKC, ws - k0);
+            stage_cols(Ps, lds, u.row0, u.rowlen, k0, kc, buf + c * kBuf);
+            stage_cols(Ps, lds, c0, ncol, k0, kc, buf + c * kBuf + kUpdKC * STR);
+          }
+          cp_async_commit();
+          cp_async_wait<0>();
+        }
+        __syncthreads();
+        if (active)
+          for (int c = 0; c < nchunk; ++c) {
+            const int kc = min(kUpdKC, ws - c * kUpdKC);
+            const T* As = buf + c * kBuf;
+            const T* Bs = As + kUpdKC * STR + ob + 8 * b0;
+            if (nr == 2)
+              upd_strip_nc<acc_t, 2>(ncb, As, Bs, kc, r0, lc, acc);
+            else
+              upd_strip_nc<acc_t, 1>(ncb, As, Bs, kc, r0, lc, acc);
+          }
+        __syncthreads();  // the buffers are refilled by the next pass or tile
+      } else {
       // chunk 0 into buffer 0
       if (tmap) {
         if (tid == 0) {
@@ -712,6 +752,7 @@ __device__ void task_update(const FactorArgs& a, const UTask u, unsigned char* s
             upd_strip_nc<acc_t, 1>(ncb, As, Bs, kc, r0, lc, acc);
         }
         __syncthreads();  // buffer c & 1 is refilled by the next iteration's copies
+      }
       }
       if (tmap && tid == 0) *tma.phase = ph;  // every thread has waited on the last chunk
       // Scatter-subtract into panel t: only the lower triangle (row >= column).
@@ -1583,8 +1624,11 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
     const size_t tcb = 2 * (kTcM + kTcN) * kpad * 4 + (2 * kTcM + kTcN) * sizeof(int) + 1024;
     if (tcb > tri) tri = tcb;
   }
-  size_t upd = (size_t)4 * kUpdKC * Stage<double>::kStr * sizeof(double) + 128 +
-               (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
+  // update tiles: two FP64 chunk buffers, or four FP32 ones (A and B each),
+  // then the row positions, rows and columns
+  const size_t bufs = std::max((size_t)2 * 2 * kUpdKC * Stage<double>::kStr * sizeof(double),
+                               (size_t)4 * 2 * kUpdKC * Stage<float>::kStr * sizeof(float));
+  size_t upd = bufs + 128 + (size_t)(2 * kUpdTileM + kUpdTileN) * sizeof(int);
   return tri > upd ? tri : upd;
 }
 
