@@ -977,14 +977,16 @@ __device__ __forceinline__ double fixed64_to_double(long long t, int k) {
       (long long)(((unsigned long long)neg << 63) | ((unsigned long long)be << 52) | (m & ((1ull << 52) - 1))));
 }
 
-// The MMA is M = 64 x N = 16, the tile's at most kOzRows = 64 rows.  With
-// M = 64 the accumulator's row 16 q + i (i < 16) sits in TMEM lane 32 q + i,
-// columns as N.  7 groups x 16 columns fit 128 TMEM columns, a quarter of the
-// SM's, and a CTA needs 73 KB of shared memory, so three CTAs share an SM.
-// A tcgen05.mma costs about the same to issue whatever its M and N (~48
-// clocks from one thread, ~28 SM-wide when several issue), so the MMA phase is
-// bound by the instruction count; a wider N needs more TMEM and shared memory
-// than three CTAs per SM allow, and two CTAs per SM with N = 32 were slower.
+// The MMAs have M = 64 (the tile's at most kOzRows = 64 rows) and cover one
+// 16-column block of the segment: the accumulator of group d is TMEM columns
+// 16 d .. 16 d + 15.  With M = 64 the accumulator's row 16 q + i (i < 16) sits
+// in TMEM lane 32 q + i, columns as N.  7 groups x 16 columns fit 128 TMEM
+// columns, a quarter of the SM's, and a CTA needs 73 KB of shared memory, so
+// three CTAs share an SM.  A tcgen05.mma costs about the same to issue whatever
+// its M and N (~48 clocks from one thread, ~28 SM-wide when several issue), so
+// the MMA phase is bound by the instruction count: each A digit p is issued
+// once per K step against the stacked B digits 0 .. 6 - p (N up to 112),
+// 28 MMAs per block instead of 112 single products.
 constexpr int kOzM = 64, kOzN = 16, kOzRows = 64;
 constexpr int kOzCols = 128;  // TMEM columns: kSlices groups x kOzN, rounded to a power of two
 
@@ -1053,22 +1055,26 @@ __device__ void task_update_oz(const FactorArgs& a, const UTask u, unsigned char
       __syncthreads();
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       if (tid == 0) {
-        const uint32_t idesc = bf16_idesc(kOzM, kOzN);
+        // One MMA per A digit p and K step: its B operand is the run of B
+        // digits 0 .. 6 - p (N = (7 - p) x 16 rows, contiguous in shared
+        // memory), its accumulator starts at group p's columns, so the product
+        // with B digit q lands in group p + q.  28 MMAs per block instead of
+        // one per (p, q) pair (112); the first (p = 0, all groups) initialises.
         const uint32_t a0 = smem_addr(A0), b0 = smem_addr(B0);
-        for (int p = 0; p < kSlices; ++p)
-          for (int q = 0; p + q < kSlices; ++q) {
-            const uint32_t dcol = tc.tmem + (uint32_t)((p + q) * kOzN);
-            for (int k0 = 0; k0 < kpad; k0 += 16) {
-              const uint32_t off = (uint32_t)(k0 >> 3) * 128;  // 16 bf16 = two K-adjacent core matrices
-              const uint64_t ad = kmajor_desc(a0 + p * arow + off, 128, sbo);
-              const uint64_t bd = kmajor_desc(b0 + q * brow + off, 128, sbo);
-              const uint32_t acc = (p == 0 && k0 == 0) ? 0u : 1u;  // first product of group p+q
-              asm volatile("{\n.reg .pred pp;\nsetp.ne.u32 pp, %4, 0;\n"
-                           "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}" ::"r"(dcol),
-                           "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
-                           : "memory");
-            }
+        for (int p = 0; p < kSlices; ++p) {
+          const uint32_t idesc = bf16_idesc(kOzM, (kSlices - p) * kOzN);
+          const uint32_t dcol = tc.tmem + (uint32_t)(p * kOzN);
+          for (int k0 = 0; k0 < kpad; k0 += 16) {
+            const uint32_t off = (uint32_t)(k0 >> 3) * 128;  // 16 bf16 = two K-adjacent core matrices
+            const uint64_t ad = kmajor_desc(a0 + p * arow + off, 128, sbo);
+            const uint64_t bd = kmajor_desc(b0 + off, 128, sbo);
+            const uint32_t acc = (p == 0 && k0 == 0) ? 0u : 1u;
+            asm volatile("{\n.reg .pred pp;\nsetp.ne.u32 pp, %4, 0;\n"
+                         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, pp;\n}" ::"r"(dcol),
+                         "l"(ad), "l"(bd), "r"(idesc), "r"(acc)
+                         : "memory");
           }
+        }
         asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(tc.mbar)
                      : "memory");
       }
