@@ -652,3 +652,31 @@ def test_deep_panel_trees_elementwise(name, W, precision, det):
     assert f.factor() == 0
     Xo = f.solve(B)
     assert np.abs(X - Xo).max() <= 1e-10 * np.abs(Xo).max()
+
+
+@pytest.mark.parametrize("rows", [8, 32, 256])
+@pytest.mark.parametrize("nrhs", [1, 8, 11])
+def test_solve_tile_rows_extremes(rows, nrhs):
+    # The deep panels' solve tiles from 8 to 256 rows (chunks of 32 rows staged
+    # in shared memory, k-split over warps for few right-hand sides, more than
+    # one pass of eight right-hand sides): solutions within 1e-10 of the
+    # oracle's, berr <= 1e-13.
+    A, perm, _ = gridgen.workload("lap3d_24")
+    B = gridgen.rhs_uniform(A.n, nrhs, seed=rows + nrhs)
+    X, st = _check(A, perm, B, max_width=8, solve_tile_rows=rows)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    Xo = f.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-10 * np.abs(Xo).max()
+
+
+def test_fifo_schedule_with_static_chains_is_bitwise_reproducible():
+    A, perm, B = gridgen.workload("lap3d_14")
+    res = []
+    for sched in (0, 1, 1):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=1, sched=sched)
+        assert rc == 0
+        res.append((spchol.export_factor(h)[2], X))
+        spchol.destroy(h)
+    for Lx, X in res[1:]:  # the static order fixes every sum: the ring's order does not matter
+        assert np.array_equal(Lx, res[0][0]) and np.array_equal(X, res[0][1])
