@@ -241,3 +241,54 @@ def test_fifo_fanin_bitwise_equals_priority_fanin(precision):
         spchol.destroy(h)
     assert np.array_equal(res[0][0], res[1][0])
     assert np.array_equal(res[0][1], res[1][1])
+
+
+def test_torch_allocator_with_gmres_refinement_and_growth():
+    # A TF32 factor in the static order with one classic refinement step
+    # allowed: GMRES-IR takes over and allocates its Krylov workspace during the
+    # solve; with the PyTorch allocator the results are bitwise those of the
+    # default pool, and the handle returns every byte on destroy.
+    alloc = spchol.torch_allocator()
+    held0 = alloc.held_bytes()
+    A, perm, _ = gridgen.workload("lap3d_16")
+    res = []
+    for allocator in (None, "torch"):
+        out = []
+        rc, X, st, h = gpu_factor_solve(A, perm, gridgen.rhs_uniform(A.n, 3, seed=2), precision=spchol.TF32,
+                                        deterministic=1, ir_max_iter=1, allocator=allocator)
+        assert rc == 0 and st["ir_gmres_iters"] > 0
+        out.append(X)
+        B9 = gridgen.rhs_uniform(A.n, 9, seed=4)  # more right-hand sides: the workspace grows
+        X9 = B9.copy(order="F")
+        spchol.solve(h, X9, A.n, 9)
+        out.append(X9)
+        res.append(out)
+        spchol.destroy(h)
+    for a_, b_ in zip(res[0], res[1]):
+        assert np.array_equal(a_, b_)
+    assert alloc.held_bytes() == held0
+
+
+def test_torch_allocator_batch_handle():
+    sides = gridgen.batch_sides(12)
+    mats = [gridgen.diffusion_2d_5pt(int(s), sigma=1.0, seed=50 + i) for i, s in enumerate(sides)]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    alloc = spchol.torch_allocator()
+    held0 = alloc.held_bytes()
+    Xs_all = []
+    for allocator in (None, "torch"):
+        h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms,
+                                 spchol.default_options(deterministic=2, allocator=allocator))
+        assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+        Bs = [gridgen.rhs_uniform(M.n, 2, seed=i) for i, M in enumerate(mats)]
+        Xs = [B.copy(order="F") for B in Bs]
+        spchol.batch_solve(h, Xs, [M.n for M in mats], [2] * len(mats))
+        if allocator == "torch":
+            assert alloc.held_bytes() > held0
+        spchol.destroy(h)
+        Xs_all.append(Xs)
+        for M, X, B in zip(mats, Xs, Bs):
+            assert oracle.berr(M, X, B) <= BERR_FP64
+    for a_, b_ in zip(*Xs_all):
+        assert np.array_equal(a_, b_)
+    assert alloc.held_bytes() == held0
