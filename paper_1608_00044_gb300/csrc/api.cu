@@ -630,7 +630,7 @@ int setup_device(spchol_handle_t h) {
   h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC, fan);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
-  CU(solve_configure(h->fp32, fan, h->smem_solve, &bs));
+  CU(solve_configure(h->fp32, fan, h->opt.precision == SPCHOL_FP64_TC, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
   if (h->opt.ctas_per_sm > 0) {
     bf = std::min(bf, h->opt.ctas_per_sm);

@@ -163,7 +163,7 @@ cudaError_t launch_fanrec(const FanEnt* ent, int64_t n, const UTask* ut, const i
 
 // solve.cu
 size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin);
-cudaError_t solve_configure(bool fp32, bool fanin, size_t smem, int* blocks_per_sm);
+cudaError_t solve_configure(bool fp32, bool fanin, bool tc_tiles, size_t smem, int* blocks_per_sm);
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st);
 cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,
                               int64_t n, int nrhs, cudaStream_t st);

@@ -768,7 +768,7 @@ __device__ void fwd_tile_oz(const SolveArgs& a, const double* P, int ld, int row
   }
 }
 
-template <typename T, bool FAN>
+template <typename T, bool FAN, bool TC>
 __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
@@ -776,7 +776,7 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
   double* z = FAN ? a.zf + a.st_zf[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8 && TC) {
     if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
       fwd_tile_oz<FAN>(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm, z);
       return;
@@ -919,7 +919,7 @@ __device__ void bwd_tile_fma(const SolveArgs& a, const T* P, int ld, int row0, i
   }
 }
 
-template <typename T, bool FAN>
+template <typename T, bool FAN, bool TC>
 __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
@@ -927,7 +927,7 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const T* P = spanel<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
   double* z = FAN ? a.zb + a.st_zb[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
-  if constexpr (sizeof(T) == 8) {
+  if constexpr (sizeof(T) == 8 && TC) {
     if (a.tc_tiles && w >= kOzMinW && w <= kOzMaxK) {
       bwd_tile_oz<FAN>(a, reinterpret_cast<const double*>(P), ld, row0, cnt, R, f, w, sm, z);
       return;
@@ -973,8 +973,12 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
   }
 }
 
-template <typename T, bool FAN>
-__global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
+// TC: the instantiation whose FP64 panel tiles may run as split products on
+// the tensor cores (SPCHOL_FP64_TC).  Those tiles need 64 registers a thread
+// (four CTAs per SM); without them the kernel fits 48 and five CTAs share an
+// SM, which shortens the dependency chain's tasks (64^3: 16.2 -> 15.7 ms).
+template <typename T, bool FAN, bool TC>
+__global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   __shared__ SolveShared sh;
   double* sm = reinterpret_cast<double*>(smem_raw);
@@ -1033,7 +1037,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
       }
     } else if (task < ns + nst) {
       const int kt = task - ns, s = a.st_sn[kt];
-      fwd_tile<T, FAN>(a, s, kt - a.st_first[s], sm);
+      fwd_tile<T, FAN, TC>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
       // Counter updates are spread over the CTA's threads: a panel near the
       // root has thousands of dependent tiles, and they sit on the critical path.
@@ -1052,7 +1056,7 @@ __global__ void __launch_bounds__(kSolveThreads, 4) solve_kernel(SolveArgs a) {
         release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
-      bwd_tile<T, FAN>(a, s, kt - a.st_first[s], sm);
+      bwd_tile<T, FAN, TC>(a, s, kt - a.st_first[s], sm);
       publish_cta_writes();
       // deterministic order: the panel's next backward tile
       if (a.ftdep && threadIdx.x == 0 && kt + 1 < a.st_first[s] + a.nst[s] &&
@@ -1119,13 +1123,14 @@ size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin) {
 
 // The fan-in mode has kernels of its own, so that the other modes' tiles and
 // diagonal tasks carry none of its code.
-static const void* solve_fn(bool fp32, bool fan) {
-  if (fan) return fp32 ? (const void*)solve_kernel<float, true> : (const void*)solve_kernel<double, true>;
-  return fp32 ? (const void*)solve_kernel<float, false> : (const void*)solve_kernel<double, false>;
+static const void* solve_fn(bool fp32, bool fan, bool tc) {
+  if (fp32) return fan ? (const void*)solve_kernel<float, true, false> : (const void*)solve_kernel<float, false, false>;
+  if (tc) return fan ? (const void*)solve_kernel<double, true, true> : (const void*)solve_kernel<double, false, true>;
+  return fan ? (const void*)solve_kernel<double, true, false> : (const void*)solve_kernel<double, false, false>;
 }
 
-cudaError_t solve_configure(bool fp32, bool fanin, size_t smem, int* blocks_per_sm) {
-  const void* fn = solve_fn(fp32, fanin);
+cudaError_t solve_configure(bool fp32, bool fanin, bool tc, size_t smem, int* blocks_per_sm) {
+  const void* fn = solve_fn(fp32, fanin, tc);
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
@@ -1133,7 +1138,8 @@ cudaError_t solve_configure(bool fp32, bool fanin, size_t smem, int* blocks_per_
 
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st) {
   void* args[] = {const_cast<SolveArgs*>(&a)};
-  return cudaLaunchKernel(solve_fn(fp32, a.zf != nullptr), dim3(grid), dim3(kSolveThreads), args, smem, st);
+  return cudaLaunchKernel(solve_fn(fp32, a.zf != nullptr, a.tc_tiles != 0), dim3(grid), dim3(kSolveThreads), args,
+                          smem, st);
 }
 
 cudaError_t ensure_smem_limit(const void* fn, size_t need) {
