@@ -601,7 +601,12 @@ def measure_batch(spchol, torch, dev, count=512, width=64):
         st = spchol.stats(h)
         worst = max(_berr(M, X, B) for M, X, B in zip(mats, Xs, Bs))
         ms = sum(fms) / len(fms)
+        # algorithmic bytes of the factorization: A's values and destinations read
+        # once, the stored factor (with its amalgamation zeros) written once
+        esz = 4 if prec == spchol.FP32 else 8
+        fbytes = st0["nnz_a"] * 16 + st0["nnz_l_stored"] * esz
         out[label] = {"factor_ms_one_launch": ms, "tflops": st0["flops"] / (ms * 1e-3) / 1e12,
+                      "achieved_gbs": fbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes": int(fbytes),
                       "graph_replay_ms": statistics.median(gms), "autotuned": {k: tuned[k] for k in
                       ("max_width", "relax_zeros", "tile_rows", "tried_ms")},
                       "solve_ms": st["solve_ms"], "worst_berr": worst, "analyze_s": ana, "rc": rc,
