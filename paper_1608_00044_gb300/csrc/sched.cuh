@@ -273,9 +273,14 @@ __device__ __forceinline__ void keep_or_push(const Ring2& q, int* next, int task
   if (next == nullptr || atomicCAS(next, -1, task) != -1) ring2_push_one(q, true, task);
 }
 
-// Make this CTA's global writes visible before a counter update or a push.
+// Make this CTA's global writes visible before a counter update or a push:
+// the CTA barrier orders every thread's writes before thread 0's fence, whose
+// cumulativity makes them visible at GPU scope before thread 0 signals (the
+// pattern of the cooperative-groups grid barrier).  A fence in every thread
+// before the barrier, as this used to do, cost each task its slowest thread's
+// wait for its own atomics: 64^3 factor 389.1 -> 386.9 ms and solve 16.1 ->
+// 15.5 ms, 48^3 FP32 factor 16.8 -> 16.2 ms.
 __device__ __forceinline__ void publish_cta_writes() {
-  __threadfence();
   __syncthreads();
   if (threadIdx.x == 0) __threadfence();
 }

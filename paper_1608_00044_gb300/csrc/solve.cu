@@ -325,11 +325,6 @@ __device__ __forceinline__ void copy_batched(int total, Src src, Dst dst) {
 // column walk free of bank conflicts.
 __device__ __forceinline__ uint32_t sm_u32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
 
-__device__ __forceinline__ int atom_add_relaxed(int* p, int v) {
-  int old;
-  asm volatile("atom.relaxed.gpu.global.add.s32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-  return old;
-}
 
 template <typename T>
 __device__ __forceinline__ void cp_async_elem(T* dst, const T* src) {
@@ -952,23 +947,18 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
       const int e = b0 + threadIdx.x + u * blockDim.x;
       id[u] = e < e1 ? (list ? list[e] : e) : -1;
     }
-    // Relaxed decrements: every producer published its writes with a fence
-    // before its decrement, and the thread that brings a counter to zero
-    // fences before it pushes (or keeps) the task, so the fences order the
-    // producers' writes before the consumer's reads.
+    // acq_rel decrements: each one releases what its thread has observed (the
+    // CTA's writes, ordered before it by the publishing barrier), and the one
+    // that reaches zero acquires every earlier decrement's release, so the
+    // pushed (or kept) task sees all of its producers' writes.
 #pragma unroll
-    for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_relaxed(&cnt[id[u]], -1) : 0;
+    for (int u = 0; u < 8; ++u) old[u] = id[u] >= 0 ? atom_add_acqrel(&cnt[id[u]], -1) : 0;
     int ready[8];
-    bool any = false;
 #pragma unroll
     for (int u = 0; u < 8; ++u) {
       ready[u] = (id[u] >= 0 && old[u] == 1) ? task0 + id[u] : -1;
-      any |= ready[u] >= 0;
-    }
-    if (any) __threadfence();
-#pragma unroll
-    for (int u = 0; u < 8; ++u)
       if (ready[u] >= 0 && next != nullptr && atomicCAS(next, -1, ready[u]) == -1) ready[u] = -1;  // kept
+    }
     ring2_push_warp(q, true, ready);
   }
 }
