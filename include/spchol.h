@@ -150,6 +150,16 @@ typedef struct spchol_options {
   void* (*dev_alloc)(size_t bytes, void* stream, void* ctx);
   void (*dev_free)(void* ptr, size_t bytes, void* stream, void* ctx);
   void* alloc_ctx;        /* passed to dev_alloc / dev_free as ctx */
+  int solve_w_depth;      /* the solves' near-root steps (Section II-A's triangular solves, restated):
+                             panels within this many levels of the root of the panel elimination
+                             tree (up to 64 columns wide, outside subtree tasks) also keep
+                             W = L21 L11^{-1}, formed by the factorization after each L21 tile,
+                             so that a forward step is y_below -= W b_s and a backward step
+                             x_s -= W^T x_below, with no diagonal solve between two steps of the
+                             chain.  Costs the W buffer (the footprint counts it) and
+                             2 (rows below) w^2 flops per such panel in the factorization.
+                             0 = default (32 for spchol_analyze, none for spchol_batch_analyze);
+                             -1 = none; not used with deterministic != 0 */
 } spchol_options;
 
 typedef struct spchol_stats {

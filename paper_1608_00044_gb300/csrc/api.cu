@@ -112,6 +112,8 @@ struct spchol_handle_s {
   void* d_pool = nullptr;
   size_t pool_bytes = 0;
   double* d_inv = nullptr;  // diagonal-block inverses (FP64)
+  void* d_wbuf = nullptr;   // W = L21 L11^{-1} of the W panels (Plan::woff), in the panels' precision
+  int64_t* d_woff = nullptr;
   uint16_t* d_slices = nullptr;  // FP64_TC: BF16 digit slices of the rows below each diagonal block
   int32_t* d_rexp = nullptr;     // FP64_TC: row exponents
   int64_t* d_sliceoff = nullptr;
@@ -367,6 +369,7 @@ int setup_device(spchol_handle_t h) {
   auto r64 = [&](size_t n) { return A.reserve(std::max<size_t>(n, 1) * sizeof(int64_t)); };
   size_t o_fcol = r32(ns + 1), o_nrows = r32(ns), o_ld = r32(ns), o_rows = r32(P.rows.size()), o_parent = r32(ns);
   size_t o_rowoff = r64(ns + 1), o_valoff = r64(ns + 1), o_adest = r64(P.a_dest.size()), o_invoff = r64(ns + 1);
+  size_t o_woff = r64(ns);
   const bool oz = h->opt.precision == SPCHOL_FP64_TC;
   size_t o_sliceoff = r64(ns + 1), o_rexp = oz ? r32(P.rows.size()) : 0;
   size_t o_tf = r32(ns), o_nt = r32(ns), o_tsn = r32(P.trsm_sn.size()), o_uf = r32(ns), o_nu = r32(ns);
@@ -390,7 +393,12 @@ int setup_device(spchol_handle_t h) {
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
     nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
-    if (P.fdep0[s] == 0) sseeds.push_back(s);
+    if (P.fdep0[s] == 0) {
+      if (P.woff[s] >= 0)  // a W panel starts with its forward tiles
+        for (int k = 0; k < P.nst[s]; ++k) sseeds.push_back(ns + P.st_first[s] + k);
+      else
+        sseeds.push_back(s);
+    }
   }
   size_t o_sttp = r32(P.st_tptr.size()), o_sttg = r32(P.st_tgt.size()), o_rtp = r32(P.rt_ptr.size()),
          o_rtt = r32(P.rt_tile.size()), o_fd0 = r32(ns), o_bd0 = r32(P.n_st), o_bd = r32(P.n_st);
@@ -464,6 +472,7 @@ int setup_device(spchol_handle_t h) {
   h->d_valoff = (int64_t*)(b + o_valoff);
   h->d_adest = (int64_t*)(b + o_adest);
   h->d_invoff = (int64_t*)(b + o_invoff);
+  h->d_woff = (int64_t*)(b + o_woff);
   h->d_sliceoff = (int64_t*)(b + o_sliceoff);
   if (oz) h->d_rexp = (int32_t*)(b + o_rexp);
   h->d_trsm_first = (int32_t*)(b + o_tf);
@@ -548,6 +557,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_parent, P.parent)) || (rc = upload(h, h->d_rowoff, P.rowoff)) ||
       (rc = upload(h, h->d_valoff, P.valoff)) || (rc = upload(h, h->d_adest, P.a_dest)) ||
       (rc = upload(h, h->d_invoff, P.invoff)) || (rc = upload(h, h->d_sliceoff, P.sliceoff)) ||
+      (rc = upload(h, h->d_woff, P.woff)) ||
       (rc = upload(h, h->d_trsm_first, P.trsm_first)) || (rc = upload(h, h->d_ntrsm, P.ntrsm)) ||
       (rc = upload(h, h->d_trsm_sn, P.trsm_sn)) || (rc = upload(h, h->d_u_first, P.u_first)) ||
       (rc = upload(h, h->d_trsm_rows, P.trsm_rows)) ||
@@ -587,6 +597,7 @@ int setup_device(spchol_handle_t h) {
   h->pool_bytes = std::max<size_t>((size_t)P.valoff[ns] * esz, 256);
   DALLOC(h->d_pool, h->pool_bytes, nullptr);
   DALLOC(h->d_inv, std::max<size_t>((size_t)P.invoff[ns] * sizeof(double), 256), nullptr);
+  if (P.n_w > 0) DALLOC(h->d_wbuf, (size_t)P.n_w * esz, nullptr);
   if (mma_mode_of(h->opt.precision) != 1 && mma_mode_of(h->opt.precision) != 2 && P.ns > 0) {
     std::vector<CUtensorMap> maps;
     if (build_tensor_maps(h, maps)) {
@@ -639,6 +650,7 @@ int setup_device(spchol_handle_t h) {
   h->grid_factor = std::max(1, std::min(bf * h->num_sms, std::max(P.n_factor_tasks, 1)));
   h->grid_solve = std::max(1, std::min(bs * h->num_sms, std::max(P.n_solve_tasks, 1)));
   h->stats.footprint_bytes = (int64_t)(A.bytes + h->pool_bytes + (size_t)P.invoff[ns] * sizeof(double) +
+                                       (size_t)P.n_w * (h->fp32 ? sizeof(float) : sizeof(double)) +
                                        (size_t)P.n_rel * sizeof(int32_t) + (size_t)P.ns * (h->d_tmaps ? 128 : 0) +
                                        (oz ? (size_t)P.sliceoff[ns] * sizeof(uint16_t) : 0) + h->fan_buf_bytes +
                                        (h->d_fan_rec ? P.fan_ent.size() * sizeof(FanRec) : 0));
@@ -800,6 +812,8 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.pool = h->d_pool;
   a.inv = h->d_inv;
   a.invoff = h->d_invoff;
+  a.wbuf = h->d_wbuf;
+  a.woff = P.n_wpan > 0 ? h->d_woff : nullptr;
   a.prof = profile ? h->d_prof : nullptr;
   a.trace = profile ? h->d_trace_f : nullptr;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 16 * sizeof(unsigned long long), st));
@@ -906,6 +920,9 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.pool = h->d_pool;
   a.inv = h->d_inv;
   a.invoff = h->d_invoff;
+  a.wbuf = h->d_wbuf;
+  a.woff = P.n_wpan > 0 ? h->d_woff : nullptr;
+  a.n_wpan = P.n_wpan;
   a.Y = Y;
   a.ldy = P.n;
   a.nrhs = nrhs;
@@ -914,7 +931,7 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.trace = h->d_trace_s;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof + 16, 0, 8 * sizeof(unsigned long long), st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
-  int rc = read_status(h, st, P.n_solve_tasks);
+  int rc = read_status(h, st, P.n_solve_tasks - P.n_wpan);
   h->traced_s = h->d_trace_s != nullptr;
   if (h->opt.profile) {
     CU(cudaMemcpy(h->h_prof + 16, h->d_prof + 16, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
@@ -1342,6 +1359,9 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.pool = h->d_pool;
   a.inv = h->d_inv;
   a.invoff = h->d_invoff;
+  a.wbuf = h->d_wbuf;
+  a.woff = P.n_wpan > 0 ? h->d_woff : nullptr;
+  a.n_wpan = P.n_wpan;
   a.Y = Y;
   a.ldy = n;
   a.nrhs = nrhs;
@@ -1354,7 +1374,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   CU(cudaStreamSynchronize(st));
   const int* c = h->h_ctrl;
   if (c[kErr] != 0) return c[kErr];
-  if (c[kDone] != P.n_solve_tasks) return SPCHOL_EINTERNAL;
+  if (c[kDone] != P.n_solve_tasks - P.n_wpan) return SPCHOL_EINTERNAL;
   return 0;
 }
 
@@ -1430,7 +1450,7 @@ int spchol_destroy(spchol_handle_t h) {
   DeviceGuard g(h->device);
   // Nothing here waits for the device: the memory goes back stream-ordered (or
   // to the caller's allocator), the pinned blocks to the process-wide cache.
-  for (void* p : {(void*)h->arena.base, h->d_pool, h->d_fan_buf, (void*)h->d_fan_rec, (void*)h->d_inv,
+  for (void* p : {(void*)h->arena.base, h->d_pool, h->d_fan_buf, (void*)h->d_fan_rec, (void*)h->d_inv, h->d_wbuf,
                   (void*)h->d_relpos, (void*)h->d_tmaps, (void*)h->d_slices, (void*)h->d_trace_f,
                   (void*)h->d_trace_s, (void*)h->d_Y, (void*)h->d_zf, (void*)h->d_zb, (void*)h->d_B,
                   (void*)h->d_X, (void*)h->d_R, (void*)h->d_gmV, (void*)h->d_gmW, (void*)h->d_gmPart,
@@ -1480,7 +1500,16 @@ int spchol_batch_analyze(int count, const int64_t* n, const int64_t* const* colp
     z += n[i] > 0 ? colptr[i][n[i]] - colptr[i][0] : 0;
     c += n[i];
   }
-  int rc = spchol_analyze(N, cp.data(), ri.data(), pm.data(), opt, out);
+  // W panels (solve_w_depth) by default only for single matrices: a batch of
+  // small trees would form W for most of its panels
+  spchol_options bo;
+  if (opt) {
+    bo = *opt;
+  } else {
+    spchol::default_options(&bo);
+  }
+  if (bo.solve_w_depth == 0) bo.solve_w_depth = -1;
+  int rc = spchol_analyze(N, cp.data(), ri.data(), pm.data(), &bo, out);
   if (rc < 0 && rc > -100) {
     // map the combined call's argument positions back to this call's
     const int map[7] = {0, -2, -3, -4, -5, -6, -7};

@@ -279,6 +279,66 @@ __device__ void slice_row(const double* Pi, int w, int ld, int kpad, int nb, int
 // ---------------------------------------------------------------- TRSM(s, k)
 // Arithmetic in the panel's type: FP64 panels solve in FP64, FP32 panels (the
 // mixed-precision modes) in FP32.
+// W = L21 L11^{-1} for rows row0 .. row0 + cnt - 1 of a W panel (Plan::woff):
+// each row w solves w L11 = l21 by back substitution, w_c = (l21_c - sum over
+// q > c of w_q l_qc) / l_cc for c = w-1 .. 0, from the rows this panel-solve
+// tile has just written and L11 (the inverse of the diagonal task is formed
+// after the release of these tiles, so it is not read here).  The layout of
+// the panel solve: warp q takes 4-row strips, lane (lr, lc) row lr at columns
+// lc + 8 cc; L11 is restaged with leading dimension 65, so that the 8 lanes of
+// a row read the entries l_c,lc+8cc of row c of L11 from distinct banks.
+template <typename T>
+__device__ void form_w_rows(const FactorArgs& a, int s, int row0, int cnt, double* smd) {
+  using ct = T;
+  constexpr int kLd = kTrsmMaxW + 1;
+  const int tid = threadIdx.x, nt = blockDim.x;
+  const int w = a.pv.fcol[s + 1] - a.pv.fcol[s], ld = a.pv.ld[s];
+  const T* P = panel_ptr<T>(a, s);
+  T* W = reinterpret_cast<T*>(a.wbuf) + a.woff[s];
+  ct* Ls = reinterpret_cast<ct*>(smd);  // Ls[q + kLd c] = l_qc for q > c
+  ct* rinv = Ls + kLd * w;              // 1 / l_cc
+  __syncthreads();                      // the panel solve is done with shared memory
+  for (int idx = tid; idx < kTrsmMaxW * w; idx += nt) {
+    const int qq = idx & (kTrsmMaxW - 1), c = idx >> 6;
+    Ls[qq + kLd * c] = (qq < w && qq > c) ? (ct)ldcg(P + qq + (size_t)c * ld) : ct(0);
+  }
+  for (int c = tid; c < w; c += nt) rinv[c] = ct(1) / (ct)ldcg(P + c + (size_t)c * ld);
+  __syncthreads();
+  const int warp = tid >> 5, lane = tid & 31, lr = lane >> 3, lc = lane & 7;
+  const int nstrip = (cnt + 3) >> 2;
+  for (int st = warp; st < nstrip; st += nt >> 5) {
+    const int rloc = 4 * st + lr;
+    const bool rv = rloc < cnt;
+    const T* Pi = P + row0 + rloc;
+    ct x[8];
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = lc + 8 * cc;
+      x[cc] = (rv && c < w) ? (ct)ldcg(Pi + (size_t)c * ld) : ct(0);
+    }
+#pragma unroll
+    for (int cbk = 7; cbk >= 0; --cbk) {
+      if (8 * cbk >= w) continue;
+      for (int c8 = 7; c8 >= 0; --c8) {
+        const int c = 8 * cbk + c8;
+        if (c >= w) continue;
+        if (lc == c8) x[cbk] *= rinv[c];
+        const ct xc = __shfl_sync(0xffffffffu, x[cbk], (lr << 3) | c8);
+        const ct* Lr = Ls + c;  // l_c,c' at Lr[kLd c'] for c' < c
+        if (lc < c8) x[cbk] -= xc * Lr[kLd * (lc + 8 * cbk)];
+#pragma unroll
+        for (int cc = 0; cc < cbk; ++cc) x[cc] -= xc * Lr[kLd * (lc + 8 * cc)];
+      }
+    }
+    T* Wi = W + row0 + rloc;
+#pragma unroll
+    for (int cc = 0; cc < 8; ++cc) {
+      const int c = lc + 8 * cc;
+      if (rv && c < w) Wi[(size_t)c * ld] = (T)x[cc];
+    }
+  }
+}
+
 template <typename T, int MODE>
 __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, FactorShared& sh, bool skip,
                           bool release = true) {
@@ -408,6 +468,9 @@ __device__ void task_trsm(const FactorArgs& a, int s, int k, double* smd, Factor
       ring2_push_range(q, false, first + nhi, a.nu[s] - nhi, &sh.base);
     }
   }
+  // W rows after the release: the updates of this panel do not wait for them
+  // (the solves, a later launch, read them)
+  if (!skip && a.woff != nullptr && a.woff[s] >= 0) form_w_rows<T>(a, s, row0, cnt, smd);
 }
 
 // ---------------------------------------------------------------- an update has landed
@@ -1620,7 +1683,8 @@ size_t factor_smem_bytes(int max_w, int mma_mode) {
   // TRSM: L11 with 64-row columns and 1 / l_cc.
   size_t tri = ((size_t)max_w * max_w + 3 * (size_t)max_w) * sizeof(double) +
                (((size_t)max_w * (max_w - 1) / 2 + 15) & ~size_t(15));
-  if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 1) * max_w * sizeof(double));
+  // (+ 1: the W rows of W panels restage L11 with leading dimension 65)
+  if (max_w <= kTrsmMaxW) tri = std::max(tri, (size_t)(kTrsmMaxW + 2) * max_w * sizeof(double));
   if (mma_mode == 3) {
     const size_t kpad = ((size_t)max_w + 15) & ~size_t(15);
     const size_t oz = (size_t)kSlices * (kOzRows + kOzN) * kpad * 2 + (3 * kOzRows + 2 * kOzN) * sizeof(int) + 1024;

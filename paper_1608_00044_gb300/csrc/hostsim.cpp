@@ -429,11 +429,33 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       spush(t);
     }
   };
+  // W panels (Plan::woff): W = L21 L11^{-1} is applied as L21 (L11^{-1} .)
+  // and L11^{-T} (L21^T .), the same products
+  auto wpan = [&](int s) { return P.woff[s] >= 0; };
   for (int s = 0; s < ns; ++s)
     if (fdep[s] == 0) {
-      qs.push(s);
-      ++s_seeds;
+      if (wpan(s)) {  // its forward tiles are ready with b_s
+        for (int k = 0; k < P.nst[s]; ++k) qs.push(ns + P.st_first[s] + k);
+        s_seeds += P.nst[s];
+      } else {
+        qs.push(s);
+        ++s_seeds;
+      }
     }
+  // L11^{-1} y (lower) and L11^{-T} y (upper) by substitution, y of length w
+  auto lsolve = [&](const double* L, int ld, int w, double* y) {
+    for (int j = 0; j < w; ++j) {
+      y[j] /= L[j + (size_t)j * ld];
+      for (int i = j + 1; i < w; ++i) y[i] -= L[i + (size_t)j * ld] * y[j];
+    }
+  };
+  auto ltsolve = [&](const double* L, int ld, int w, double* y) {
+    for (int j = w - 1; j >= 0; --j) {
+      y[j] /= L[j + (size_t)j * ld];
+      for (int i = 0; i < j; ++i) y[i] -= L[j + (size_t)i * ld] * y[j];
+    }
+  };
+  std::vector<double> tmp;
   int sdone = 0;
   while (next >= 0 || !q.empty() || !qs.empty()) {
     int task = next;
@@ -446,7 +468,20 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
     if (task < 0 || task >= P.n_solve_tasks || sran[task]) return SPCHOL_EINTERNAL;
     sran[task] = 1;
     ++sdone;
-    if (task < ns) {  // FWD_D
+    if (task < ns && wpan(task)) {  // FWD_D of a W panel: y_s <- L11^{-T} L11^{-1} b_s
+      const int s = task, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
+      const double* L = sim.panel(s);
+      if (ft[s] != 0) return SPCHOL_EINTERNAL;  // its forward tiles must have read b_s
+      for (int r = 0; r < nrhs; ++r) {
+        lsolve(L, ld, w, Y.data() + f + (size_t)r * n);
+        ltsolve(L, ld, w, Y.data() + f + (size_t)r * n);
+      }
+      for (int k = 0; k < P.nst[s]; ++k) {
+        const int tile = P.st_first[s] + k;
+        if (--bdep[tile] < 0) return SPCHOL_EINTERNAL;
+        if (bdep[tile] == 0) skeep(ns + nst + tile);
+      }
+    } else if (task < ns) {  // FWD_D
       const int s = task, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
       const double* L = sim.panel(s);
       if (fan)  // the forward tiles' products into these rows, in tile order
@@ -486,10 +521,16 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       const int TS = P.st_rows[s], row0 = w + k * TS, cnt = std::min(TS, rr - row0);
       const double* L = sim.panel(s);
       const int32_t* R = P.rows.data() + P.rowoff[s];
+      const bool wp = wpan(s);
+      tmp.assign((size_t)w * nrhs, 0.0);  // y_s, or for a W panel L11^{-1} b_s
+      for (int r = 0; r < nrhs; ++r) {
+        for (int j = 0; j < w; ++j) tmp[j + (size_t)r * w] = Y[f + j + (size_t)r * n];
+        if (wp) lsolve(L, ld, w, tmp.data() + (size_t)r * w);
+      }
       for (int r = 0; r < nrhs; ++r)
         for (int i = row0; i < row0 + cnt; ++i) {
           double acc = 0.0;
-          for (int j = 0; j < w; ++j) acc += L[i + (size_t)j * ld] * Y[f + j + (size_t)r * n];
+          for (int j = 0; j < w; ++j) acc += L[i + (size_t)j * ld] * tmp[j + (size_t)r * w];
           if (fan)
             Zf[(size_t)P.st_zf[kt] * nrhs + (i - row0) + (size_t)r * cnt] = -acc;
           else
@@ -498,7 +539,13 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       for (int e = P.st_tptr[kt]; e < P.st_tptr[kt + 1]; ++e) {
         const int t = P.st_tgt[e];
         if (--fdep[t] < 0) return SPCHOL_EINTERNAL;
-        if (fdep[t] == 0) skeep(t);
+        if (fdep[t] == 0) {
+          if (wpan(t)) {  // all of t's forward tiles, the first as the continuation
+            for (int k2 = 0; k2 < P.nst[t]; ++k2) skeep(ns + P.st_first[t] + k2);
+          } else {
+            skeep(t);
+          }
+        }
       }
       if (det)
         for (int q2 = P.ft_sptr[kt]; q2 < P.ft_sptr[kt + 1]; ++q2) {
@@ -507,33 +554,53 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
           if (ftdep[nx] == 0) skeep(ns + nx);
         }
       if (--ft[s] < 0) return SPCHOL_EINTERNAL;
-      if (ft[s] == 0)
-        for (int k2 = 0; k2 < P.nst[s]; ++k2) {
-          const int tile = P.st_first[s] + k2;
-          if (--bdep[tile] == 0) skeep(ns + nst + tile);
+      if (ft[s] == 0) {
+        if (wp) {
+          skeep(s);  // the W panel's diagonal task
+        } else {
+          for (int k2 = 0; k2 < P.nst[s]; ++k2) {
+            const int tile = P.st_first[s] + k2;
+            if (--bdep[tile] == 0) skeep(ns + nst + tile);
+          }
         }
+      }
     } else if (task < ns + 2 * nst) {  // BWD_T
       const int kt = task - ns - nst, s = P.st_sn[kt], k = kt - P.st_first[s];
       const int f = P.fcol[s], w = sim.width(s), ld = P.ld[s], rr = P.nrows[s];
       const int TS = P.st_rows[s], row0 = w + k * TS, cnt = std::min(TS, rr - row0);
       const double* L = sim.panel(s);
       const int32_t* R = P.rows.data() + P.rowoff[s];
-      for (int r = 0; r < nrhs; ++r)
+      const bool wp = wpan(s);
+      tmp.assign((size_t)w, 0.0);
+      for (int r = 0; r < nrhs; ++r) {
         for (int j = 0; j < w; ++j) {
           double acc = 0.0;
           for (int i = row0; i < row0 + cnt; ++i) acc += L[i + (size_t)j * ld] * Y[R[i] + (size_t)r * n];
-          if (fan)
-            Zb[(size_t)P.st_zb[kt] * nrhs + j + (size_t)r * w] = -acc;
-          else
-            Y[f + j + (size_t)r * n] -= acc;
+          tmp[j] = acc;
         }
+        if (wp) ltsolve(L, ld, w, tmp.data());  // W^T x = L11^{-T} (L21^T x)
+        for (int j = 0; j < w; ++j) {
+          if (fan)
+            Zb[(size_t)P.st_zb[kt] * nrhs + j + (size_t)r * w] = -tmp[j];
+          else
+            Y[f + j + (size_t)r * n] -= tmp[j];
+        }
+      }
       if (det && k + 1 < P.nst[s]) {  // the panel's next backward tile
         const int nx = P.st_first[s] + k + 1;
         if (--bdep[nx] < 0) return SPCHOL_EINTERNAL;
         if (bdep[nx] == 0) skeep(ns + nst + nx);
       }
       if (--bt[s] < 0) return SPCHOL_EINTERNAL;
-      if (bt[s] == 0) skeep(ns + 2 * nst + s);
+      if (bt[s] == 0 && wp) {  // x_s = y_s is final: release its readers
+        for (int e = P.rt_ptr[s]; e < P.rt_ptr[s + 1]; ++e) {
+          const int tile = P.rt_tile[e];
+          if (--bdep[tile] < 0) return SPCHOL_EINTERNAL;
+          if (bdep[tile] == 0) skeep(ns + nst + tile);
+        }
+      } else if (bt[s] == 0) {
+        skeep(ns + 2 * nst + s);
+      }
     } else {  // BWD_D
       const int s = task - ns - 2 * nst, f = P.fcol[s], w = sim.width(s), ld = P.ld[s];
       const double* L = sim.panel(s);
@@ -557,7 +624,8 @@ int spchol_plan_simulate(spchol_plan_t p, const double* values, double* B, int64
       }
     }
   }
-  if (sdone != P.n_solve_tasks || s_pushed + s_kept != P.n_solve_tasks - s_seeds) return SPCHOL_EINTERNAL;
+  const int64_t n_run = P.n_solve_tasks - P.n_wpan;  // W panels have no backward diagonal task
+  if (sdone != n_run || s_pushed + s_kept != n_run - s_seeds) return SPCHOL_EINTERNAL;
   for (int r = 0; r < nrhs; ++r)
     for (int64_t i = 0; i < n; ++i) B[P.perm[i] + (size_t)r * ldb] = Y[i + (size_t)r * n];
   return 0;

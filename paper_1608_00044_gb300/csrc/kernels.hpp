@@ -95,6 +95,8 @@ struct FactorArgs {
   void* pool;          // double* or float*
   double* inv;         // per panel: L11^{-1} (w x w, column-major, lower part)
   const int64_t* invoff;
+  void* wbuf;              // W = L21 L11^{-1} of the W panels (Plan::woff), double* or float*
+  const int64_t* woff;     // null: no W panels
   unsigned long long* prof;  // optional: [0..2] busy ns per task type, [3] wait ns, [4..6] counts,
                              // [7] tensor-core update ns, [8] subtree-task ns, [9] subtree tasks,
                              // [10..12] fan-in gather ns (batch cuts, staging, adding), [13] its
@@ -126,6 +128,9 @@ struct SolveArgs {
   const void* pool;
   const double* inv;     // per panel: L11^{-1}
   const int64_t* invoff;
+  const void* wbuf;      // W = L21 L11^{-1} of the W panels (Plan::woff)
+  const int64_t* woff;   // null: no W panels
+  int32_t n_wpan;        // W panels: their backward diagonal tasks never run
   double* Y;        // n x nrhs, permuted order
   int64_t ldy;
   int nrhs;

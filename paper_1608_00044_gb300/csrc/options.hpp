@@ -12,6 +12,7 @@ namespace spchol {
 constexpr int kSolveTileRows = 64;  // rows per solve tile below the near-root band (staged in 32-row chunks)
 constexpr int kTrsmTileRows = 64;
 constexpr int kFp64TcMinWidth = 16;
+constexpr int kWDepth = 32;  // W panels (PlanParams::w_depth) of a single matrix, by default
 
 inline void default_options(spchol_options* o) {
   std::memset(o, 0, sizeof(*o));
@@ -31,6 +32,7 @@ inline void default_options(spchol_options* o) {
   o->dev_alloc = nullptr;
   o->dev_free = nullptr;
   o->alloc_ctx = nullptr;
+  o->solve_w_depth = 0;
 }
 
 inline bool options_valid(const spchol_options& o) {
@@ -42,7 +44,7 @@ inline bool options_valid(const spchol_options& o) {
          o.deterministic <= 2 &&
          o.profile >= 0 && o.profile <= 2 && o.sched >= 0 && o.sched <= 1 &&
          (o.solve_tile_rows == 0 || (o.solve_tile_rows >= 8 && o.solve_tile_rows <= 256)) &&
-         (o.dev_alloc == nullptr) == (o.dev_free == nullptr);
+         (o.dev_alloc == nullptr) == (o.dev_free == nullptr) && o.solve_w_depth >= -1;
 }
 
 inline PlanParams params_from(const spchol_options& o) {
@@ -62,10 +64,12 @@ inline PlanParams params_from(const spchol_options& o) {
   p.trsm_rows = kTrsmTileRows;
   p.fifo = o.sched == 1;
   p.solve_rows = o.solve_tile_rows > 0 ? o.solve_tile_rows : kSolveTileRows;
+  p.w_depth = o.solve_w_depth > 0 ? o.solve_w_depth : o.solve_w_depth == 0 ? kWDepth : 0;
   if (o.deterministic) {
     p.deterministic = true;
     p.fanin = o.deterministic == 2;
     p.subtree_flops = 0.0;
+    p.w_depth = 0;  // the solves keep the chains of diagonal tasks and tiles
   }
   return p;
 }

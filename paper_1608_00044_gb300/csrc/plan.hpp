@@ -53,7 +53,16 @@ struct PlanParams {
   // = 1): the launch gives the high-priority ring no slots, and every push goes
   // to the other ring.  The plan itself is the same.
   bool fifo = false;
+  // Panels within w_depth of the root of the panel etree (0: none), outside
+  // subtree tasks, at most kWMaxWidth wide and with rows below their diagonal
+  // block, also keep W = L21 L11^{-1} (Plan::woff), so that their solve steps
+  // need no diagonal task on the chain: see Plan::woff.
+  int w_depth = 0;
 };
+
+// Widest panel that keeps W = L21 L11^{-1} (its packed inverse is staged in
+// shared memory by the panel-solve tiles that form W).
+constexpr int kWMaxWidth = 64;
 
 // Rows of a target panel are gathered in pieces of at most this many rows.
 constexpr int kFanPieceRows = 32;
@@ -123,6 +132,21 @@ struct Plan {
   // (targets + 1 for "every forward tile of the tile's own panel is done")
   std::vector<int32_t> st_tptr, st_tgt, rt_ptr, rt_tile, fdep0, bdep0;
   int32_t n_st = 0, n_solve_tasks = 0;
+  // W panels (PlanParams::w_depth): woff[s] >= 0 is the offset (elements) of
+  // panel s's W = L21 L11^{-1} in the W buffer, stored like the panel itself
+  // (column-major, leading dimension ld[s], rows w .. nrows-1 used); -1 for the
+  // other panels.  The panel-solve tiles of the factorization write W after
+  // their L21 rows.  The solves then take, for a W panel s, b_s = the
+  // right-hand side rows of s once every forward tile into s has landed:
+  //   forward tile k:  y[rows of k] -= W[k] b_s   (ready with b_s, no diagonal task first)
+  //   diagonal task:   y_s <- L11^{-T} L11^{-1} b_s, after every forward tile of s has read b_s
+  //   backward tile k: y_s -= W[k]^T x[rows of k], after the diagonal task
+  // and x_s = y_s once the backward tiles are done (the last one releases the
+  // dependents, the role of the backward diagonal task, which never runs):
+  // x_s = L11^{-T} (L11^{-1} b_s - L21^T x_below) = A11^{-1} b_s - W^T x_below.
+  std::vector<int64_t> woff;
+  int64_t n_w = 0;      // elements of the W buffer
+  int32_t n_wpan = 0;   // W panels (backward diagonal tasks that never run)
 
   // Deterministic order (params.deterministic; empty otherwise).  The update
   // tiles into each target panel form a chain in (source panel, row tile)

@@ -217,6 +217,24 @@ __device__ __forceinline__ void ring2_push_range(const Ring2& q, bool hi, int fi
   __syncthreads();
 }
 
+// Any thread: push the ready tasks first .. first+count-1 to one ring of a
+// Ring2 with one reservation (a W panel's forward tiles, made ready by one
+// counter).
+__device__ __forceinline__ void ring2_push_span(const Ring2& q, bool hi, int first, int count) {
+  if (count <= 0) return;
+  hi = hi && q.n_hi > 0;
+  const int base = atomicAdd(&q.ctrl[hi ? kHiTail : kTail], count);
+  int* slots = hi ? q.hi : q.lo;
+  const int n = hi ? q.n_hi : q.n_lo;
+  for (int i = 0; i < count; ++i) {
+    if (base + i < n) {
+      st_release(&slots[base + i], first + i);
+    } else {
+      atomicCAS(&q.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+    }
+  }
+}
+
 // Any thread: push one ready task to one ring of a Ring2.
 __device__ __forceinline__ void ring2_push_one(const Ring2& q, bool hi, int task) {
   hi = hi && q.n_hi > 0;

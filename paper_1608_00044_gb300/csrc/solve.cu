@@ -39,6 +39,15 @@ __device__ __forceinline__ const T* spanel(const SolveArgs& a, int s) {
   return reinterpret_cast<const T*>(a.pool) + a.pv.valoff[s];
 }
 
+// W panels (Plan::woff) keep W = L21 L11^{-1}, stored like the panel.
+__device__ __forceinline__ bool is_wpanel(const SolveArgs& a, int s) { return a.woff != nullptr && a.woff[s] >= 0; }
+
+// The operand of a panel's solve tiles: W for a W panel, else the panel (L21).
+template <typename T>
+__device__ __forceinline__ const T* tile_operand(const SolveArgs& a, int s) {
+  return is_wpanel(a, s) ? reinterpret_cast<const T*>(a.wbuf) + a.woff[s] : spanel<T>(a, s);
+}
+
 // ---------------------------------------------------------------- FP64 products on the BF16 tensor cores
 // The panel tiles' products C = A B (A: up to 64 x 64 of L21 or its
 // transpose, B: up to 64 x 8 right-hand sides) cost w FP64 FMAs per output,
@@ -524,43 +533,31 @@ __device__ void bwd_gather(const SolveArgs& a, int s, int w, double* Ys, int r0,
 // (w / 2) row pairs x nrc right-hand sides x P parts.
 __device__ __forceinline__ int diag_parts(int nrc) { return nrc == 1 ? 8 : nrc == 2 ? 4 : nrc <= 4 ? 2 : 1; }
 
-// y_s <- L11^{-1} y_s with the inverse formed by the diagonal factor task:
-// every entry is an independent dot product, no sequential substitution.
-// Lanes (r, c, q) compute rows c and w - 1 - c for right-hand side r, terms
-// k = q mod P: i + 1 and w - i terms, w + 1 in all, so every thread and warp
-// does the same work.
-template <bool FAN>
-__device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
-  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
-  const double* X = a.inv + a.invoff[s];
-  const int lx = w + 1;           // padded: lanes that walk a row or a column both avoid bank conflicts
-  double* Xs = sm;                // [w][lx] column-major, lower part
-  double* Ys = sm + w * lx;       // [nrc][w]
-  stage_inverse(X, w, Xs, lx);
+// The products of the diagonal solves with the stored inverse X = L11^{-1}
+// (staged at Xs, column-major with leading dimension lx, lower part): every
+// entry is an independent dot product, no sequential substitution.  TR =
+// false: L11^{-1} y, entry i the dot product of row i of X (columns 0 .. i)
+// with y; TR = true: L11^{-T} y, entry k that of column k of X (rows k .. w-1).
+// y: nrc right-hand sides at Ys [nrc][w].  Lanes (r, c, q) compute entries c
+// and w - 1 - c for right-hand side r, terms k = q mod P: w + 1 terms in all,
+// so every thread and warp does the same work.  With few right-hand sides each
+// dot product is split over P lanes, so that every warp -- and every
+// sub-partition's FP64 pipe -- takes a share; the parts meet by shuffles
+// within the P lanes.  out(i, r, value) is called by one lane per entry.
+template <bool TR, class Out>
+__device__ __forceinline__ void diag_product(const double* Xs, int lx, int w, const double* Ys, int nrc, Out out) {
   const int half = (w + 1) >> 1;
-  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
-    const int nrc = min(kSolveNRC, a.nrhs - r0);
-    __syncthreads();
-    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
-      const int j = idx % w, r = idx / w;
-      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
-    }
-    if constexpr (FAN) fwd_gather(a, s, f, w, Ys, r0, nrc, reinterpret_cast<unsigned char*>(Ys + kSolveNRC * w));
-    cp_async_wait_group<0>();  // the inverse (first pass)
-    __syncthreads();
-    // With few right-hand sides each dot product is split over P lanes (k = q,
-    // q + P, ...), so that every warp -- and every sub-partition's FP64 pipe --
-    // takes a share; the parts meet by shuffles within the P lanes.
-    const int P = diag_parts(nrc);
-    const int total = (half * nrc * P + 31) & ~31;  // whole warps: every lane takes part in the shuffles
-    for (int p = threadIdx.x; p < total; p += blockDim.x) {
-      const int q = p % P, cr = p / P, c = cr % half, r = cr / half;
-      const bool valid = cr < half * nrc;
-      const double* y = Ys + r * w;
-      const int i1 = c, i2 = w - 1 - c;
-      double a0 = 0.0, b0 = 0.0;
-      if (valid) {
-        double a1 = 0.0, b1 = 0.0;
+  const int P = diag_parts(nrc);
+  const int total = (half * nrc * P + 31) & ~31;  // whole warps: every lane takes part in the shuffles
+  for (int p = threadIdx.x; p < total; p += blockDim.x) {
+    const int q = p % P, cr = p / P, c = cr % half, r = cr / half;
+    const bool valid = cr < half * nrc;
+    const double* y = Ys + r * w;
+    const int i1 = c, i2 = w - 1 - c;
+    double a0 = 0.0, b0 = 0.0;
+    if (valid) {
+      double a1 = 0.0, b1 = 0.0;
+      if constexpr (!TR) {
         int k = q;
         for (; k + P <= i1; k += 2 * P) {
           a0 += Xs[i1 + k * lx] * y[k];
@@ -574,33 +571,47 @@ __device__ void fwd_diag(const SolveArgs& a, int s, double* sm) {
           }
           if (k <= i2) b0 += Xs[i2 + k * lx] * y[k];
         }
-        a0 += a1;
-        b0 += b1;
+      } else {
+        const double* x1 = Xs + i1 * lx;
+        int i = i1 + q;
+        for (; i + P < w; i += 2 * P) {
+          a0 += x1[i] * y[i];
+          a1 += x1[i + P] * y[i + P];
+        }
+        if (i < w) a0 += x1[i] * y[i];
+        if (i2 != i1) {
+          const double* x2 = Xs + i2 * lx;
+          for (i = i2 + q; i + P < w; i += 2 * P) {
+            b0 += x2[i] * y[i];
+            b1 += x2[i + P] * y[i + P];
+          }
+          if (i < w) b0 += x2[i] * y[i];
+        }
       }
-      for (int d = 1; d < P; d <<= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, d);
-        b0 += __shfl_xor_sync(0xffffffffu, b0, d);
-      }
-      if (valid && q == 0) {
-        a.Y[f + i1 + (size_t)(r0 + r) * a.ldy] = a0;
-        if (i2 != i1) a.Y[f + i2 + (size_t)(r0 + r) * a.ldy] = b0;
-      }
+      a0 += a1;
+      b0 += b1;
+    }
+    for (int d = 1; d < P; d <<= 1) {
+      a0 += __shfl_xor_sync(0xffffffffu, a0, d);
+      b0 += __shfl_xor_sync(0xffffffffu, b0, d);
+    }
+    if (valid && q == 0) {
+      out(i1, r, a0);
+      if (i2 != i1) out(i2, r, b0);
     }
   }
 }
 
-// x_s <- L11^{-T} y_s with the stored inverse: entry k is the dot product of
-// column k of L11^{-1} (rows k .. w-1) with y_s; lanes (r, c, q) take columns c
-// and w - 1 - c, rows k + q mod P.
-template <bool FAN>
-__device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
+// y_s <- L11^{-1} y_s (forward) or L11^{-T} y_s (backward, TR) with the
+// inverse formed by the diagonal factor task.
+template <bool TR, bool FAN>
+__device__ void diag_solve(const SolveArgs& a, int s, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
   const double* X = a.inv + a.invoff[s];
-  const int lx = w + 1;
-  double* Xs = sm;
-  double* Ys = sm + w * lx;
+  const int lx = w + 1;           // padded: lanes that walk a row or a column both avoid bank conflicts
+  double* Xs = sm;                // [w][lx] column-major, lower part
+  double* Ys = sm + w * lx;       // [nrc][w]
   stage_inverse(X, w, Xs, lx);
-  const int half = (w + 1) >> 1;
   for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
     const int nrc = min(kSolveNRC, a.nrhs - r0);
     __syncthreads();
@@ -609,48 +620,45 @@ __device__ void bwd_diag(const SolveArgs& a, int s, double* sm) {
       Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
     if constexpr (FAN) {
-      __syncthreads();
-      bwd_gather(a, s, w, Ys, r0, nrc);
+      if constexpr (TR) {
+        __syncthreads();
+        bwd_gather(a, s, w, Ys, r0, nrc);
+      } else {
+        fwd_gather(a, s, f, w, Ys, r0, nrc, reinterpret_cast<unsigned char*>(Ys + kSolveNRC * w));
+      }
     }
     cp_async_wait_group<0>();  // the inverse (first pass)
     __syncthreads();
-    const int P = diag_parts(nrc);  // as in the forward solve: dot products split over P lanes
-    const int total = (half * nrc * P + 31) & ~31;
-    for (int p = threadIdx.x; p < total; p += blockDim.x) {
-      const int q = p % P, cr = p / P, c = cr % half, r = cr / half;
-      const bool valid = cr < half * nrc;
-      const double* y = Ys + r * w;
-      const int k1 = c, k2 = w - 1 - c;
-      double a0 = 0.0, b0 = 0.0;
-      if (valid) {
-        double a1 = 0.0, b1 = 0.0;
-        const double* x1 = Xs + k1 * lx;
-        int i = k1 + q;
-        for (; i + P < w; i += 2 * P) {
-          a0 += x1[i] * y[i];
-          a1 += x1[i + P] * y[i + P];
-        }
-        if (i < w) a0 += x1[i] * y[i];
-        if (k2 != k1) {
-          const double* x2 = Xs + k2 * lx;
-          for (i = k2 + q; i + P < w; i += 2 * P) {
-            b0 += x2[i] * y[i];
-            b1 += x2[i + P] * y[i + P];
-          }
-          if (i < w) b0 += x2[i] * y[i];
-        }
-        a0 += a1;
-        b0 += b1;
-      }
-      for (int d = 1; d < P; d <<= 1) {
-        a0 += __shfl_xor_sync(0xffffffffu, a0, d);
-        b0 += __shfl_xor_sync(0xffffffffu, b0, d);
-      }
-      if (valid && q == 0) {
-        a.Y[f + k1 + (size_t)(r0 + r) * a.ldy] = a0;
-        if (k2 != k1) a.Y[f + k2 + (size_t)(r0 + r) * a.ldy] = b0;
-      }
+    double* Y = a.Y + f + (size_t)r0 * a.ldy;
+    const int64_t ldy = a.ldy;
+    diag_product<TR>(Xs, lx, w, Ys, nrc, [&](int i, int r, double v) { Y[i + r * ldy] = v; });
+  }
+}
+
+// The diagonal task of a W panel (Plan::woff): y_s <- L11^{-T} L11^{-1} b_s,
+// the product with L11^{-1} kept in shared memory (Ts) for the second.
+__device__ void diag_solve_w(const SolveArgs& a, int s, double* sm) {
+  const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f;
+  const double* X = a.inv + a.invoff[s];
+  const int lx = w + 1;
+  double* Xs = sm;                      // [w][lx]
+  double* Ys = sm + w * lx;             // [nrc][w]
+  double* Ts = Ys + kSolveNRC * w;      // [nrc][w]: L11^{-1} b_s
+  stage_inverse(X, w, Xs, lx);
+  for (int r0 = 0; r0 < a.nrhs; r0 += kSolveNRC) {
+    const int nrc = min(kSolveNRC, a.nrhs - r0);
+    __syncthreads();
+    for (int idx = threadIdx.x; idx < w * nrc; idx += blockDim.x) {
+      const int j = idx % w, r = idx / w;
+      Ys[idx] = ldcg(a.Y + f + j + (size_t)(r0 + r) * a.ldy);
     }
+    cp_async_wait_group<0>();
+    __syncthreads();
+    diag_product<false>(Xs, lx, w, Ys, nrc, [&](int i, int r, double v) { Ts[i + r * w] = v; });
+    __syncthreads();
+    double* Y = a.Y + f + (size_t)r0 * a.ldy;
+    const int64_t ldy = a.ldy;
+    diag_product<true>(Xs, lx, w, Ts, nrc, [&](int i, int r, double v) { Y[i + r * ldy] = v; });
   }
 }
 
@@ -768,7 +776,7 @@ __device__ void fwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
-  const T* P = spanel<T>(a, s);
+  const T* P = tile_operand<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
   double* z = FAN ? a.zf + a.st_zf[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
   if constexpr (sizeof(T) == 8 && TC) {
@@ -919,7 +927,7 @@ __device__ void bwd_tile(const SolveArgs& a, int s, int k, double* sm) {
   const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
   const int ts = a.st_rows[s];
   const int row0 = w + k * ts, cnt = min(ts, r - row0);
-  const T* P = spanel<T>(a, s);
+  const T* P = tile_operand<T>(a, s);
   const int32_t* R = a.pv.rows + a.pv.rowoff[s];
   double* z = FAN ? a.zb + a.st_zb[a.st_first[s] + k] * a.nrhs : nullptr;  // fan-in: the tile's buffer
   if constexpr (sizeof(T) == 8 && TC) {
@@ -963,6 +971,19 @@ __device__ __forceinline__ void release_tiles(const Ring2& q, const int32_t* lis
   }
 }
 
+// Thread-level: every forward tile into W panel t has landed, so all of t's
+// forward tiles are ready (they read b_t); the first (the rows of the etree
+// parent, the next step of the chain) becomes the continuation if next is
+// given and free, the others go to the high-priority ring in one reservation.
+__device__ __forceinline__ void release_w_forward(const Ring2& q, const SolveArgs& a, int t, int* next) {
+  int first = a.pv.ns + a.st_first[t], count = a.nst[t];
+  if (next != nullptr && atomicCAS(next, -1, first) == -1) {
+    ++first;
+    --count;
+  }
+  ring2_push_span(q, true, first, count);
+}
+
 // TC: the instantiation whose FP64 panel tiles may run as split products on
 // the tensor cores (SPCHOL_FP64_TC).  Those tiles need 64 registers a thread
 // (four CTAs per SM); without them the kernel fits 48 and five CTAs share an
@@ -992,7 +1013,7 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
         sh.next = -1;
       } else {
         int lo_ready;
-        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask);
+        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask - a.n_wpan);
       }
       // While this CTA holds a claimed slot whose task is not yet pushed, it
       // takes no continuation: it comes back for that task after this one.
@@ -1006,9 +1027,17 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
     const int task = sh.task;
     if (task < 0) break;
     const int type = task < ns ? 0 : task < ns + nst ? 1 : task < ns + 2 * nst ? 2 : 3;
-    if (task < ns) {
+    if (task < ns && is_wpanel(a, task)) {
+      // W panel: every forward tile has read b_s; y_s <- A11^{-1} b_s, then the
+      // backward tiles (which subtract from y_s) lose their wait for it
       const int s = task;
-      fwd_diag<FAN>(a, s, sm);
+      diag_solve_w(a, s, sm);
+      publish_cta_writes();
+      release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst,
+                    sh.hold ? nullptr : &sh.next);
+    } else if (task < ns) {
+      const int s = task;
+      diag_solve<false, FAN>(a, s, sm);
       publish_cta_writes();
       // continue with the first forward tile (the rows of the parent) and
       // release the others
@@ -1033,7 +1062,12 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
       // root has thousands of dependent tiles, and they sit on the critical path.
       for (int e = a.st_tptr[kt] + threadIdx.x; e < a.st_tptr[kt + 1]; e += blockDim.x) {
         const int t = a.st_tgt[e];
-        if (atom_add_acqrel(&a.fdep[t], -1) == 1) keep_or_push(q, sh.hold ? nullptr : &sh.next, t);
+        if (atom_add_acqrel(&a.fdep[t], -1) == 1) {
+          if (is_wpanel(a, t))
+            release_w_forward(q, a, t, sh.hold ? nullptr : &sh.next);
+          else
+            keep_or_push(q, sh.hold ? nullptr : &sh.next, t);
+        }
       }
       if (a.ftdep)  // deterministic order: the next tiles into the same panels
         for (int e = a.ft_sptr[kt] + threadIdx.x; e < a.ft_sptr[kt + 1]; e += blockDim.x) {
@@ -1042,8 +1076,14 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
         }
       if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.ftiles[s], -1) == 1);
       __syncthreads();
-      if (sh.flag)
-        release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
+      if (sh.flag) {
+        if (is_wpanel(a, s)) {  // b_s is read by all: the diagonal task may overwrite it
+          if (threadIdx.x == 0) keep_or_push(q, sh.hold ? nullptr : &sh.next, s);
+        } else {
+          release_tiles(q, nullptr, a.st_first[s], a.st_first[s] + a.nst[s], a.bdep, ns + nst,
+                        sh.hold ? nullptr : &sh.next);
+        }
+      }
     } else if (task < ns + 2 * nst) {
       const int kt = task - ns - nst, s = a.st_sn[kt];
       bwd_tile<T, FAN, TC>(a, s, kt - a.st_first[s], sm);
@@ -1052,11 +1092,20 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
       if (a.ftdep && threadIdx.x == 0 && kt + 1 < a.st_first[s] + a.nst[s] &&
           atom_add_acqrel(&a.bdep[kt + 1], -1) == 1)
         keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + nst + kt + 1);
-      if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1)
+      if (is_wpanel(a, s)) {
+        // the last backward tile completes x_s = y_s: it releases the tiles
+        // that read it (the role of the backward diagonal task, which W panels
+        // do not have)
+        if (threadIdx.x == 0) sh.flag = (atom_add_acqrel(&a.btiles[s], -1) == 1);
+        __syncthreads();
+        if (sh.flag)
+          release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
+      } else if (threadIdx.x == 0 && atom_add_acqrel(&a.btiles[s], -1) == 1) {
         keep_or_push(q, sh.hold ? nullptr : &sh.next, ns + 2 * nst + s);
+      }
     } else {
       const int s = task - ns - 2 * nst;
-      bwd_diag<FAN>(a, s, sm);
+      diag_solve<true, FAN>(a, s, sm);
       publish_cta_writes();
       release_tiles(q, a.rt_tile, a.rt_ptr[s], a.rt_ptr[s + 1], a.bdep, ns + nst, sh.hold ? nullptr : &sh.next);
     }
@@ -1097,7 +1146,9 @@ __global__ void permute_out_kernel(const double* __restrict__ Y, int64_t ldy, do
 }  // namespace
 
 size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin) {
-  const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC) * sizeof(double) +
+  // diagonal tasks: the inverse and the right-hand sides, plus (W panels, not
+  // in the fan-in mode) the product with L11^{-1}
+  const size_t diag = ((size_t)max_w * (max_w + 1) + (size_t)max_w * kSolveNRC * (fanin ? 1 : 2)) * sizeof(double) +
                       (fanin ? solve_fan_smem_bytes(max_w) : 0);
   // panel tiles: two chunk buffers of max_w x kTileLD (FP64 bound) plus, forward,
   // the right-hand sides and the partial sums, backward, two x chunks and the

@@ -648,6 +648,18 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
   }
   P.n_st = (int32_t)P.st_sn.size();
   P.n_solve_tasks = 2 * ns + 2 * P.n_st;
+  P.woff.assign(ns, -1);
+  P.n_w = 0;
+  P.n_wpan = 0;
+  if (prm.w_depth > 0 && !prm.deterministic)
+    for (int32_t s = 0; s < ns; ++s) {
+      const int32_t w = P.fcol[s + 1] - P.fcol[s];
+      if (depth[s] < prm.w_depth && P.in_sub[s] < 0 && P.nst[s] > 0 && w <= kWMaxWidth) {
+        P.woff[s] = P.n_w;
+        P.n_w += (int64_t)P.ld[s] * w;
+        P.n_wpan++;
+      }
+    }
   P.st_tptr.assign(P.n_st + 1, 0);
   P.st_tgt.clear();
   std::vector<int32_t> st_rng;  // per st_tgt entry: the tile's rows in that panel, i0 | i1 << 16

@@ -39,6 +39,7 @@ class Options(ctypes.Structure):
         ("dev_alloc", ctypes.c_void_p),  # function pointers (DEV_ALLOC_FN / DEV_FREE_FN), NULL = the pool
         ("dev_free", ctypes.c_void_p),
         ("alloc_ctx", ctypes.c_void_p),
+        ("solve_w_depth", ctypes.c_int),
     ]
 
 
@@ -162,7 +163,7 @@ def default_options_host(**kw) -> Options:
     """The defaults of include/spchol.h filled without loading the GPU library."""
     o = Options(precision=FP64, max_width=64, relax_zeros=4, tile_rows=0, ctas_per_sm=0, deterministic=0,
                 wait_budget_ns=2_000_000_000, ir_max_iter=10, ir_tol=1e-12, fault_inject=0, profile=0, solve_tile_rows=0, sched=0,
-                dev_alloc=None, dev_free=None, alloc_ctx=None)
+                dev_alloc=None, dev_free=None, alloc_ctx=None, solve_w_depth=0)
     for k, v in kw.items():
         setattr(o, k, v)
     return o

@@ -680,3 +680,54 @@ def test_fifo_schedule_with_static_chains_is_bitwise_reproducible():
         spchol.destroy(h)
     for Lx, X in res[1:]:  # the static order fixes every sum: the ring's order does not matter
         assert np.array_equal(Lx, res[0][0]) and np.array_equal(X, res[0][1])
+
+
+@pytest.mark.parametrize("depth", [-1, 4, 64, 1000])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 11])
+def test_w_panels_match_the_oracle(depth, nrhs):
+    # Panels within solve_w_depth levels of the root keep W = L21 L11^{-1}:
+    # their forward tiles subtract W b_s as soon as b_s is complete, their
+    # diagonal task forms A11^{-1} b_s off the chain, and their backward tiles
+    # subtract W^T x (the last one releasing the panel's readers).  None, a few,
+    # the default and every panel outside the subtree tasks: solutions within
+    # 1e-10 of the oracle's, berr <= 1e-13, L unchanged (within 1e-11), and the
+    # W buffer counted in the footprint.
+    A, perm, _ = gridgen.workload("lap3d_24")
+    B = gridgen.rhs_uniform(A.n, nrhs, seed=nrhs + depth)
+    X, st = _check(A, perm, B, max_width=16, solve_w_depth=depth)
+    f = oracle.OracleFactor.from_csc(A, perm)
+    assert f.factor() == 0
+    Xo = f.solve(B)
+    assert np.abs(X - Xo).max() <= 1e-10 * np.abs(Xo).max()
+    if depth != -1:
+        rc, _, st0, h0 = gpu_factor_solve(A, perm, None, max_width=16, solve_w_depth=-1)
+        spchol.destroy(h0)
+        assert st["footprint_bytes"] > st0["footprint_bytes"]
+
+
+@pytest.mark.parametrize("precision,sched", [("FP32", 0), ("FP64_TC", 0), ("TF32X3", 0), ("FP64", 1)])
+def test_w_panels_other_precisions_and_fifo(precision, sched):
+    # W in the panels' precision (FP32 for the mixed modes, whose refinement
+    # then reaches its 1e-12 target), on the tensor-core solve tiles (FP64_TC)
+    # and with the single FIFO ring.  Several handles in a row: W is formed
+    # anew by every factorization, whatever the memory held before.
+    A, perm, _ = gridgen.workload("lap3d_24")
+    B = gridgen.rhs_uniform(A.n, 4, seed=5)
+    bar = BERR_FP64 if precision.startswith("FP64") else 1e-12
+    for _ in range(3):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, max_width=32, solve_w_depth=1000,
+                                        precision=getattr(spchol, precision), sched=sched)
+        assert rc == 0, spchol.strerror(rc)
+        spchol.destroy(h)
+        assert oracle.berr(A, X, B) <= bar
+
+
+def test_w_depth_is_ignored_by_the_deterministic_modes():
+    A, perm, B = gridgen.workload("lap3d_14")
+    res = []
+    for det, depth in ((1, -1), (1, 1000), (2, 1000)):
+        rc, X, st, h = gpu_factor_solve(A, perm, B, deterministic=det, solve_w_depth=depth)
+        assert rc == 0
+        res.append(X)
+        spchol.destroy(h)
+    assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])

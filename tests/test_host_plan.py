@@ -422,3 +422,25 @@ def test_fanin_matches_dynamic_to_rounding():
     _, _, L0 = _plan(A, perm).simulate(A.values, None, seed=1, want_pool=True)
     _, _, L2 = _plan(A, perm, deterministic=2).simulate(A.values, None, seed=1, want_pool=True)
     np.testing.assert_allclose(L2, L0, rtol=1e-11, atol=1e-13)
+
+
+@pytest.mark.parametrize("name,W,depth", [("diff3d_8", 8, 1000), ("lap3d_12", 16, 1000), ("lap3d_12", 64, 3),
+                                          ("lap2d_24", 4, 1000), ("lap2d_24", 8, -1)])
+def test_w_panel_solve_protocol(name, W, depth):
+    """The solves' W panels (W = L21 L11^{-1} kept for the panels near the root):
+    their forward tiles are ready as soon as b_s is, their diagonal task runs
+    after every forward tile of the panel has read b_s, their backward tiles
+    after it, and the last backward tile releases the panel's readers.  Under
+    random ready orders the simulated protocol runs exactly the tasks it
+    should (the simulator checks every counter, and that the kept and pushed
+    tasks are the non-seed tasks) and matches the oracle's solution."""
+    A, perm, b = gridgen.workload(name)
+    B = gridgen.rhs_uniform(A.n, 3, seed=W)
+    P = _plan(A, perm, max_width=W, solve_w_depth=depth)
+    f = oracle.OracleFactor.from_csc(A, P.get(hp.PERM))
+    assert f.factor() == 0
+    Xo = f.solve(B)
+    for seed in range(4):
+        rc, X, _ = P.simulate(A.values, B, seed=seed)
+        assert rc == 0
+        np.testing.assert_allclose(X, Xo, rtol=1e-11, atol=1e-13)
