@@ -731,3 +731,29 @@ def test_w_depth_is_ignored_by_the_deterministic_modes():
         res.append(X)
         spchol.destroy(h)
     assert np.array_equal(res[0], res[1]) and np.array_equal(res[0], res[2])
+
+
+def test_batch_with_w_panels_matches_solo():
+    # A batch keeps no W panels by default; asked for them, every matrix's
+    # near-root panels get W and the batch still matches the solo solves.
+    sides = [9, 24, 17, 31]
+    mats = [gridgen.diffusion_2d_5pt(s, sigma=1.0, seed=50 + s) for s in sides]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=i) for i, M in enumerate(mats)]
+    for depth in (-1, 1000):
+        o = spchol.default_options(solve_w_depth=depth)
+        h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+        fp = spchol.stats(h)["footprint_bytes"]
+        if depth == -1:
+            fp_none = fp
+        else:
+            assert fp > fp_none
+        assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+        Xs = [B.copy(order="F") for B in Bs]
+        spchol.batch_solve(h, Xs, [M.n for M in mats], [B.shape[1] for B in Bs])
+        spchol.destroy(h)
+        for M, P, B, X in zip(mats, perms, Bs, Xs):
+            assert oracle.berr(M, X, B) <= BERR_FP64
+            rc, X1, st, h1 = gpu_factor_solve(M, P, B)
+            spchol.destroy(h1)
+            np.testing.assert_allclose(X, X1, rtol=1e-11, atol=1e-13)
