@@ -705,6 +705,112 @@ def measure_batch_sharded(spchol, torch, dist, count=512, width=64):
             "worst_berr": worst, "plan": opts}
 
 
+def solve_critical_path(spchol, hostplan, A, perm, b, vals, **opts):
+    """Critical path of one traced solve (profile = 2): every solve task's start
+    and end, walked back from the last task to finish along the latest-finishing
+    predecessor of the task protocol (forward diagonal task <- the tiles into
+    the panel; forward tile <- its diagonal task, or for a W panel the tiles
+    into the panel; backward tile <- the panels its rows fall in once final and
+    its own panel's forward tiles, or for a W panel its diagonal task; backward
+    diagonal task <- the panel's backward tiles).  Returns the path's length,
+    its running and waiting time by task kind (suffix w: a W panel's task), and
+    the path time by pass and depth band of 32 levels."""
+    import torch
+    from collections import defaultdict
+
+    plan = hostplan.HostPlan(A.n, A.colptr, A.rowind, perm,
+                             **{k: v for k, v in opts.items() if k in ("max_width", "solve_w_depth")})
+    sc = plan.scalars()
+    ns = sc["ns"]
+    fcol = plan.get(hostplan.FCOL)
+    nrows = plan.get(hostplan.NROWS)
+    rowoff = plan.get(hostplan.ROWOFF)
+    rows = plan.get(hostplan.ROWS)
+    parent = plan.get(hostplan.PARENT)
+    nst = plan.get(hostplan.NST).astype(np.int64)
+    plan.close()
+    NST = int(nst.sum())
+    h = spchol.analyze(A.n, A.colptr, A.rowind, perm, spchol.default_options(profile=2, **opts))
+    spchol.factorize(h, vals)
+    bt = torch.from_numpy(np.ascontiguousarray(b.T)).cuda()
+    ms = []
+    for _ in range(4):
+        X = bt.clone()
+        spchol.solve(h, X, A.n, b.shape[1])
+        ms.append(spchol.stats(h)["solve_ms"])
+    tr = spchol.trace_get(h, 1).astype(np.int64)
+    spchol.destroy(h)
+    ran = tr[:, 1] > 0
+    T = np.where(ran[:, None], (tr - tr[ran, 0].min()) / 1e3, np.nan)  # microseconds
+    w = np.diff(fcol)
+    depth = np.zeros(ns, np.int64)
+    for s in range(ns - 1, -1, -1):
+        depth[s] = 0 if parent[s] < 0 else depth[parent[s]] + 1
+    isw = np.array([nst[s] > 0 and not ran[ns + 2 * NST + s] for s in range(ns)])
+    st_first = np.concatenate([[0], np.cumsum(nst)[:-1]]).astype(np.int64)
+    tile_s = np.repeat(np.arange(ns), nst)
+    col2panel = np.searchsorted(fcol, np.arange(A.n), side="right") - 1
+    ts = np.zeros(ns, np.int64)  # tile rows: the near-root band's 32, else the default 64
+    for s in range(ns):
+        if nst[s] > 0:
+            ts[s] = 32 if depth[s] < 128 else 64
+            assert (nrows[s] - w[s] + ts[s] - 1) // ts[s] == nst[s]
+    tgt = []
+    for kt in range(NST):
+        s = tile_s[kt]
+        r0 = w[s] + (kt - st_first[s]) * ts[s]
+        r1 = min(nrows[s], r0 + ts[s])
+        tgt.append(np.unique(col2panel[rows[rowoff[s] + r0: rowoff[s] + r1]]))
+    tiles_into = [[] for _ in range(ns)]
+    for kt, tt in enumerate(tgt):
+        for p in tt:
+            tiles_into[p].append(kt)
+    end = lambda t: T[t, 1]
+
+    def tiles_of(s, base):
+        return [base + k for k in range(st_first[s], st_first[s] + nst[s])]
+
+    def xfinal(p):
+        return max(tiles_of(p, ns + NST), key=end) if isw[p] else ns + 2 * NST + p
+
+    def preds(t):
+        if t < ns:
+            return tiles_of(t, ns) if isw[t] else [ns + k for k in tiles_into[t]]
+        if t < ns + NST:
+            s = tile_s[t - ns]
+            return [ns + k for k in tiles_into[s]] if isw[s] else [s]
+        if t < ns + 2 * NST:
+            s = tile_s[t - ns - NST]
+            return [xfinal(q) for q in tgt[t - ns - NST]] + ([s] if isw[s] else tiles_of(s, ns))
+        s = t - ns - 2 * NST
+        return tiles_of(s, ns + NST) if nst[s] else [s]
+
+    path, cur = [], int(np.nanargmax(T[:, 1]))
+    while cur is not None:
+        path.append(cur)
+        p = [q for q in preds(cur) if ran[q]]
+        cur = max(p, key=end) if p else None
+    path.reverse()
+    kind = lambda t: "FD" if t < ns else "FT" if t < ns + NST else "BT" if t < ns + 2 * NST else "BD"
+    pan = lambda t: t if t < ns else tile_s[t - ns] if t < ns + NST else tile_s[t - ns - NST] if t < ns + 2 * NST else t - ns - 2 * NST
+    agg = defaultdict(lambda: [0, 0.0, 0.0])
+    band = defaultdict(float)
+    for j, t in enumerate(path):
+        k = kind(t) + ("w" if isw[pan(t)] else "")
+        gap = T[t, 0] - T[path[j - 1], 1] if j else 0.0
+        agg[k][0] += 1
+        agg[k][1] += T[t, 1] - T[t, 0]
+        agg[k][2] += gap
+        band[("forward" if kind(t)[0] == "F" else "backward") + f" depth {32 * min(depth[pan(t)] // 32, 7)}+"] += \
+            T[t, 1] - T[t, 0] + gap
+    return {"solve_ms_traced": [round(x, 3) for x in ms], "w_panels": int(isw.sum()),
+            "makespan_us": float(np.nanmax(T[:, 1])), "path_tasks": len(path),
+            "path_start_us": float(T[path[0], 0]),
+            "by_kind": {k: {"tasks": v[0], "running_us": round(v[1], 1), "waiting_us": round(v[2], 1),
+                            "avg_running_us": round(v[1] / v[0], 2)} for k, v in sorted(agg.items())},
+            "path_us_by_pass_and_depth": {k: round(v, 1) for k, v in sorted(band.items())}}
+
+
 def trace_summary(args):
     """Per-task trace of one factorization per scheduling arm (profile = 2: every
     task's start and end on the device clock), summarised: makespan, busy time
@@ -774,6 +880,10 @@ def trace_summary(args):
             "starved_ms_below_10pct_of_grid": starved,
             "top_chain": {"panels": len(chain), "columns": int(fcol[root + 1] - fcol[top]), "span_ms": span,
                           "diagonal_busy_ms": float(dur[chain].sum()) / 1e6}}
+    if not args.deterministic and args.precision == "fp64":
+        out["solve_critical_path"] = {
+            f"w_depth_{d}": solve_critical_path(spchol, hostplan, A, perm, b, vals, max_width=args.width, solve_w_depth=d)
+            for d in (-1, 0)}
     print(json.dumps(out))
     return 0
 
