@@ -76,6 +76,8 @@ struct spchol_handle_s {
   int32_t *d_dep_init = nullptr, *d_trsm_init = nullptr, *d_dep = nullptr, *d_trsm_left = nullptr;
   int32_t *d_fseeds = nullptr;
   int nfseeds = 0;
+  int32_t* d_wsub = nullptr;  // subtree tasks run by single warps (Plan::wsub), when used
+  int n_wsub = 0, grid_wsub = 0;
   int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_st_rows = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
   int32_t *d_st_tptr = nullptr, *d_st_tgt = nullptr, *d_rt_ptr = nullptr, *d_rt_tile = nullptr;
@@ -379,7 +381,20 @@ int setup_device(spchol_handle_t h) {
   // seeds: every subtree task, and the panels outside subtrees with no
   // incoming update
   std::vector<int32_t> fseeds;
-  for (int32_t k = 0; k < P.n_sub; ++k) fseeds.push_back(ns + P.n_trsm + P.n_u + k);
+  // the subtree tasks run by single warps (FP64 DFMA mode) in a launch of
+  // their own before the task loop, when every subtree task qualifies and the
+  // subtrees hold a good part of the work (a batch of small matrices: 30-47 %;
+  // a single large matrix: under 6 %, where the launch ahead of the task loop
+  // costs more than the warps gain; with some subtree tasks left to the CTAs
+  // the task loop would wait for that launch and then run them)
+  const bool warp_sub = !h->fp32 && mma_mode_of(h->opt.precision) == 0 && !P.params.fanin && P.n_sub > 0 &&
+                        (int32_t)P.wsub.size() == P.n_sub && P.sub_work_frac >= 0.2 &&
+                        h->opt.fault_inject == 0;
+  std::vector<char> by_warp(P.n_sub, 0);
+  if (warp_sub)
+    for (int32_t k : P.wsub) by_warp[k] = 1;
+  for (int32_t k = 0; k < P.n_sub; ++k)
+    if (!by_warp[k]) fseeds.push_back(ns + P.n_trsm + P.n_u + k);
   for (int s = 0; s < ns; ++s)
     if (P.dep_f[s] == 0 && P.in_sub[s] < 0) fseeds.push_back(s);
   if (h->opt.fault_inject == 1 && ns > 0 && P.in_sub[ns - 1] >= 0) {
@@ -388,7 +403,7 @@ int setup_device(spchol_handle_t h) {
     const int32_t missing = ns + P.n_trsm + P.n_u + P.in_sub[ns - 1];
     fseeds.erase(std::find(fseeds.begin(), fseeds.end(), missing));
   }
-  size_t o_fseeds = r32(fseeds.size());
+  size_t o_fseeds = r32(fseeds.size()), o_wsub = r32(warp_sub ? P.wsub.size() : 0);
   size_t o_stf = r32(ns), o_nst = r32(ns), o_strows = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
@@ -491,6 +506,8 @@ int setup_device(spchol_handle_t h) {
   h->d_trsm_left = (int32_t*)(b + o_trs);
   h->d_fseeds = (int32_t*)(b + o_fseeds);
   h->nfseeds = (int)fseeds.size();
+  h->d_wsub = (int32_t*)(b + o_wsub);
+  h->n_wsub = warp_sub ? (int)P.wsub.size() : 0;
   h->d_st_first = (int32_t*)(b + o_stf);
   h->d_nst = (int32_t*)(b + o_nst);
   h->d_st_sn = (int32_t*)(b + o_stsn);
@@ -565,6 +582,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_sub_lo, P.sub_lo)) || (rc = upload(h, h->d_sub_hi, P.sub_hi)) || (rc = upload(h, h->d_ut, P.ut)) ||
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
+      (h->n_wsub > 0 && (rc = upload(h, h->d_wsub, P.wsub))) ||
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
       (rc = upload(h, h->d_st_rows, P.st_rows)) ||
       (rc = upload(h, h->d_kid_ptr, P.kid_ptr)) || (rc = upload(h, h->d_kids, P.kids)) ||
@@ -641,6 +659,11 @@ int setup_device(spchol_handle_t h) {
   h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC, fan);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
+  if (h->n_wsub > 0) {
+    int bw = 0;
+    CU(warp_subtree_configure(&bw));
+    h->grid_wsub = std::max(1, std::min(std::max(bw, 1) * h->num_sms, (h->n_wsub + 3) / 4));
+  }
   CU(solve_configure(h->fp32, fan, h->opt.precision == SPCHOL_FP64_TC, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
   if (h->opt.ctas_per_sm > 0) {
@@ -734,6 +757,7 @@ int finish_analyze(spchol_handle_t h, std::chrono::steady_clock::time_point t0) 
   S.n_supernodes = P.ns;
   S.n_tasks = P.n_factor_tasks;
   S.n_subtrees = P.n_sub;
+  S.n_warp_subtrees = h->n_wsub;
   S.max_width = P.max_w;
   S.max_rows = P.max_r;
   S.analyze_ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t0).count();
@@ -768,6 +792,8 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.nu_hi = h->d_nu_hi;
   a.sub_lo = h->d_sub_lo;
   a.sub_hi = h->d_sub_hi;
+  a.wsub = h->d_wsub;
+  a.n_wsub = h->n_wsub;
   a.relpos = h->d_relpos;
   a.tmaps = h->d_tmaps;
   a.n_hi = fifo ? 0 : P.n_hi_tasks;
@@ -817,6 +843,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.prof = profile ? h->d_prof : nullptr;
   a.trace = profile ? h->d_trace_f : nullptr;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 16 * sizeof(unsigned long long), st));
+  CU(launch_warp_subtrees(a, h->grid_wsub, st));  // their tiles' counters release ring tasks
   CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   return 0;

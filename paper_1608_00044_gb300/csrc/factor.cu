@@ -1393,6 +1393,200 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
   __syncthreads();  // the task reads these rows next, and reuses the shared memory
 }
 
+// ---------------------------------------------------------------- warp-level subtree tasks
+// A subtree task whose panels are all at most kWarpSubW columns wide
+// (FactorArgs::wsub) runs on one warp, before the warps of its CTA join the
+// task loop: the many small subtrees of a batch of small matrices, or the
+// leaves of a large one, then advance kWarpExec per CTA side by side with warp
+// barriers only, where a CTA subtree task runs one of them with CTA barriers
+// at every column and step.  Per panel, in postorder:
+//   * the diagonal block in shared memory (leading dimension kWarpLd), lane i
+//     holding row i: each multiplier, update and pivot is the diagonal task's
+//     operation on the same operands in the same order, so L11 is the same;
+//   * its inverse, lane c holding column c, by the diagonal task's
+//     substitution (the same operations per entry);
+//   * the panel solve of every row below in the panel-solve tile's 4-row
+//     strips (lane (r, c) row r at columns c + 8 j), its operations and order;
+//   * the update tiles, one output per lane at a time (a dot product over the
+//     panel's columns in two chains): into panels inside the subtree by plain
+//     read-modify-write (no other task touches them), into the others by
+//     atomics, each tile then counted down on its target as a CTA subtree task
+//     does.
+// After a failed pivot (here or anywhere) the rest of the subtree skips its
+// arithmetic but still counts its outside targets down.
+constexpr int kWarpLd = kWarpSubW + 1;
+constexpr int kWarpExec = 4;                                   // warps of a CTA that run them
+constexpr int kWarpSmem = kWarpSubW * kWarpLd + kWarpSubW;     // doubles per warp: the block, 1 / l_jj
+
+__device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
+  const unsigned full = 0xffffffffu;
+  const int lane = threadIdx.x & 31;
+  const int lo = a.sub_lo[k], hi = a.sub_hi[k];
+  double* xd = ws + kWarpSubW * kWarpLd;
+  bool skip = ld_relaxed(&a.ctrl[kInfo]) != INT_MAX;
+  const Ring2 q = rings_of(a);
+  for (int s = lo; s <= hi; ++s) {
+    const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+    double* P = panel_ptr<double>(a, s);
+    if (!skip) {
+      for (int idx = lane; idx < w * w; idx += 32) {
+        const int i = idx % w, j = idx / w;
+        ws[i + j * kWarpLd] = i >= j ? ldcg(P + i + (size_t)j * ld) : 0.0;  // zeros above: the inverse goes there
+      }
+      __syncwarp();
+      double qj = 0.0;  // lane j: 1 / d_j
+      int bad = 0;
+      if (lane == 0) {
+        const double d0 = ws[0];
+        if (d0 > 0.0)
+          qj = pivot_recip(d0);
+        else
+          bad = 1;
+      }
+      if (__any_sync(full, bad)) {
+        if (lane == 0) atomicMin(&a.ctrl[kInfo], f + 1);
+        skip = true;
+      }
+      for (int j = 0; j < w && !skip; ++j) {
+        const double qv = __shfl_sync(full, qj, j);
+        const bool mine = lane > j && lane < w;
+        const double ci = mine ? ws[lane + j * kWarpLd] * qv : 0.0;  // the multiplier of row lane
+        for (int kk = j + 1; kk < w; ++kk) {
+          const double akj = ws[kk + j * kWarpLd];
+          if (lane >= kk && lane < w) ws[lane + kk * kWarpLd] = fma(-ci, akj, ws[lane + kk * kWarpLd]);
+        }
+        __syncwarp();
+        if (lane == j + 1 && lane < w) {
+          const double d = ws[lane * (kWarpLd + 1)];
+          if (d > 0.0)
+            qj = pivot_recip(d);
+          else
+            bad = 1;
+        }
+        if (mine) ws[lane + j * kWarpLd] = ci;  // column j now holds the multipliers
+        if (__any_sync(full, bad)) {
+          if (lane == 0) atomicMin(&a.ctrl[kInfo], f + j + 2);
+          skip = true;
+        }
+        __syncwarp();
+      }
+      if (!skip) {
+        // L = M D^{1/2}: l_jj = sqrt(d_j), r_j = 1 / l_jj, l_ij = m_ij l_jj
+        if (lane < w) {
+          const double l = sqrt(ws[lane * (kWarpLd + 1)]);
+          ws[lane * (kWarpLd + 1)] = l;
+          xd[lane] = 1.0 / l;
+        }
+        __syncwarp();
+        for (int j = 0; j < w; ++j) {
+          const double l = ws[j * (kWarpLd + 1)];
+          if (lane > j && lane < w) ws[lane + j * kWarpLd] *= l;
+        }
+        __syncwarp();
+        for (int idx = lane; idx < w * w; idx += 32) {
+          const int i = idx % w, j = idx / w;
+          if (i >= j) P[i + (size_t)j * ld] = ws[i + j * kWarpLd];
+        }
+        // L11^{-1}: X[i][c] (i > c) in the upper triangle at (c, i)
+        for (int kk = 0; kk < w - 1; ++kk) {
+          const double xkc = lane == kk ? xd[kk] : (lane < kk ? ws[lane + kk * kWarpLd] : 0.0);
+          if (lane <= kk)
+            for (int i = kk + 1; i < w; ++i) {
+              double v = fma(-ws[i + kk * kWarpLd], xkc, ws[lane + i * kWarpLd]);
+              if (i == kk + 1) v *= xd[i];
+              ws[lane + i * kWarpLd] = v;
+            }
+          __syncwarp();
+        }
+        double* X = a.inv + a.invoff[s];
+        for (int idx = lane; idx < w * w; idx += 32) {
+          const int i = idx % w, j = idx / w;
+          if (i >= j) X[idx] = i == j ? xd[j] : ws[j + i * kWarpLd];
+        }
+        // L21 = A21 L11^{-T}, row by row in 4-row strips
+        const int lr = lane >> 3, lc = lane & 7;
+        for (int rs = w; rs < r; rs += 4) {
+          const int row = rs + lr;
+          const bool rv = row < r;
+          double* Pi = P + row;
+          double x[4];
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = lc + 8 * cc;
+            x[cc] = (rv && c < w) ? ldcg(Pi + (size_t)c * ld) : 0.0;
+          }
+#pragma unroll
+          for (int cbk = 0; cbk < 4; ++cbk) {
+            if (8 * cbk >= w) break;
+            for (int c8 = 0; c8 < 8; ++c8) {
+              const int c = 8 * cbk + c8;
+              if (c >= w) break;
+              if (lc == c8) x[cbk] *= xd[c];
+              const double xc = __shfl_sync(full, x[cbk], (lr << 3) | c8);
+              const double* Lc = ws + c * kWarpLd;  // l_qc at Lc[q], q > c
+              if (lc > c8) x[cbk] -= xc * Lc[lc + 8 * cbk];
+#pragma unroll
+              for (int cc = cbk + 1; cc < 4; ++cc) {
+                if (8 * cc >= w) break;
+                x[cc] -= xc * Lc[lc + 8 * cc];
+              }
+            }
+          }
+#pragma unroll
+          for (int cc = 0; cc < 4; ++cc) {
+            const int c = lc + 8 * cc;
+            if (rv && c < w) Pi[(size_t)c * ld] = x[cc];
+          }
+        }
+        __syncwarp();  // the rows below are written before the update tiles read them
+      }
+    }
+    // update tiles of panel s
+    const int32_t* Rs = a.pv.rows + a.pv.rowoff[s];
+    for (int ui = a.u_first[s]; ui < a.u_first[s] + a.nu[s]; ++ui) {
+      const UTask u = a.ut[ui];
+      const bool outside = u.t > hi;
+      if (!skip) {
+        const int ft = a.pv.fcol[u.t], ldt = a.pv.ld[u.t];
+        double* Pt = panel_ptr<double>(a, u.t);
+        const int nout = u.rowlen * u.seglen;
+        for (int o = lane; o < nout; o += 32) {
+          const int i = o % u.rowlen, j = o / u.rowlen;
+          const int gi = Rs[u.row0 + i], gj = Rs[u.seg0 + j];
+          if (gi < gj) continue;  // the upper part of a target's diagonal block
+          const double* ai = P + u.row0 + i;
+          const double* bj = P + u.seg0 + j;
+          double c0 = 0.0, c1 = 0.0;
+          int kk = 0;
+          for (; kk + 1 < w; kk += 2) {
+            c0 = fma(ai[(size_t)kk * ld], bj[(size_t)kk * ld], c0);
+            c1 = fma(ai[(size_t)(kk + 1) * ld], bj[(size_t)(kk + 1) * ld], c1);
+          }
+          if (kk < w) c0 = fma(ai[(size_t)kk * ld], bj[(size_t)kk * ld], c0);
+          const int p = __ldg(a.relpos + u.rel + i);
+          if (p < 0) {  // cannot happen for a consistent plan
+            atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
+            continue;
+          }
+          double* dst = Pt + p + (size_t)(gj - ft) * ldt;
+          if (outside)
+            red_add(dst, -(c0 + c1));
+          else
+            *dst -= c0 + c1;
+        }
+      }
+      if (outside) {  // publish the warp's atomics, then count the tile down on its target
+        __syncwarp();
+        if (lane == 0) {
+          __threadfence();
+          if (atom_add_acqrel(&a.dep_f[u.t], -1) == 1) ring2_push_one(q, true, u.t);
+        }
+      }
+    }
+    __syncwarp();  // the next panel reads what this one's tiles wrote into it
+  }
+}
+
 // MODE: 0 = CUDA-core update tiles (DFMA / FFMA), 1 = TF32 tensor cores (FP32
 // panels, split or not), 3 = BF16 tensor cores on split FP64 operands.
 // Five CTAs per SM (48 registers a thread; a few live values of the update
@@ -1669,6 +1863,34 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
   }
 }
 
+// The warp-level subtree tasks, launched before the task loop's kernel (on the
+// same stream, after the ring reset): kWarpExec warps per CTA, each taking
+// the next subtree from a counter until none is left.  The tiles they count
+// down push ready tasks into the rings, which the task loop's kernel then
+// finds there; every subtree adds one to the completed-task count.
+__global__ void __launch_bounds__(32 * kWarpExec) warp_subtree_kernel(FactorArgs a) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  double* ws = reinterpret_cast<double*>(smem_raw) + warp * kWarpSmem;
+  const int sub0 = a.pv.ns + a.n_trsm + a.n_u;  // first subtree task id
+  for (;;) {
+    int e = 0;
+    if (lane == 0) e = atomicAdd(&a.ctrl[kWarpNext], 1);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e >= a.n_wsub) break;
+    const int k = a.wsub[e];
+    const unsigned long long t0 = a.trace && lane == 0 ? global_ns() : 0ull;
+    warp_subtree(a, k, ws);
+    if (lane == 0) {
+      atomicAdd(&a.ctrl[kDone], 1);
+      if (a.trace) {
+        a.trace[2 * (size_t)(sub0 + k)] = t0;
+        a.trace[2 * (size_t)(sub0 + k) + 1] = global_ns();
+      }
+    }
+  }
+}
+
 template <typename T>
 __global__ void assemble_kernel(const double* __restrict__ values, const int64_t* __restrict__ dest,
                                 int64_t nnz, T* __restrict__ pool) {
@@ -1677,6 +1899,23 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 }
 
 }  // namespace
+
+size_t warp_subtree_smem_bytes() { return (size_t)kWarpExec * kWarpSmem * sizeof(double); }
+
+cudaError_t warp_subtree_configure(int* blocks_per_sm) {
+  const size_t smem = warp_subtree_smem_bytes();
+  cudaError_t e = ensure_smem_limit((const void*)warp_subtree_kernel, smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)warp_subtree_kernel, 32 * kWarpExec,
+                                                       smem);
+}
+
+cudaError_t launch_warp_subtrees(const FactorArgs& a, int grid, cudaStream_t st) {
+  if (a.n_wsub == 0) return cudaSuccess;
+  void* args[] = {const_cast<FactorArgs*>(&a)};
+  return cudaLaunchKernel((const void*)warp_subtree_kernel, dim3(grid), dim3(32 * kWarpExec), args,
+                          warp_subtree_smem_bytes(), st);
+}
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {
   // POTRF: the block, 1 / l_jj, two scaled columns and the 8-bit pair table;

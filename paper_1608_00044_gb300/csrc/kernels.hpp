@@ -54,6 +54,10 @@ struct FactorArgs {
   const int32_t* nu_hi;  // leading update tiles of each panel that go to the high-priority ring
   const int32_t* sub_lo;  // subtree tasks: first and last panel of each
   const int32_t* sub_hi;
+  // subtree tasks run by single warps before the task loop (Plan::wsub; FP64
+  // DFMA mode only, n_wsub = 0 otherwise); they are not seeded in the rings
+  const int32_t* wsub;
+  int32_t n_wsub;
   int32_t n_trsm, n_u, ntask, trsm_rows;
   int32_t n_hi;          // high-priority ring size: ring[0, n_hi); the other ring is ring[n_hi, ntask)
   int32_t mma_mode;    // FP32 panels: 0 FFMA update tiles, 1 TF32 tensor cores, 2 split-TF32 (3 products);
@@ -156,6 +160,9 @@ struct SolveArgs {
 
 // factor.cu
 size_t factor_smem_bytes(int max_w, int mma_mode);
+size_t warp_subtree_smem_bytes();  // shared memory of a CTA of the warp-level subtree tasks
+cudaError_t warp_subtree_configure(int* blocks_per_sm);
+cudaError_t launch_warp_subtrees(const FactorArgs& a, int grid, cudaStream_t st);
 // Fan-in mode: shared memory a gather needs for panels up to max_w wide, and
 // the values it stages per batch (*cap).
 size_t fanin_smem_bytes(int max_w, bool fp32, int* cap);

@@ -60,6 +60,9 @@ struct PlanParams {
   int w_depth = 0;
 };
 
+// Widest panel of a subtree task that runs on one warp (Plan::wsub).
+constexpr int kWarpSubW = 32;
+
 // Widest panel that keeps W = L21 L11^{-1} (its packed inverse is staged in
 // shared memory by the panel-solve tiles that form W).
 constexpr int kWMaxWidth = 64;
@@ -118,6 +121,11 @@ struct Plan {
   // one CTA; the panel-level tasks of those panels are never scheduled.
   // in_sub[s]: the subtree task of panel s, or -1.
   std::vector<int32_t> sub_lo, sub_hi, in_sub;
+  // The subtree tasks whose panels are all at most kWarpSubW columns wide:
+  // the FP64 factorization runs each of them on one warp (see wsub in
+  // FactorArgs), several side by side in a CTA.
+  std::vector<int32_t> wsub;
+  double sub_work_frac = 0.0;  // the subtree tasks' share of the factorization's work
   int32_t n_trsm = 0, n_u = 0, n_sub = 0;
   int32_t n_task_ids = 0;      // size of the task id space: ns + n_trsm + n_u + n_sub
   int32_t n_factor_tasks = 0;  // tasks that are scheduled (pushed to a ring) in one factorization

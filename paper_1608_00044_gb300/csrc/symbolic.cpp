@@ -580,6 +580,17 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
       }
     }
   P.n_sub = (int32_t)P.sub_lo.size();
+  {
+    double in_sub = 0.0;
+    for (int32_t k = 0; k < P.n_sub; ++k) in_sub += sub_fl[P.sub_hi[k]];
+    P.sub_work_frac = total > 0.0 ? in_sub / total : 0.0;
+  }
+  P.wsub.clear();
+  for (int32_t k = 0; k < P.n_sub; ++k) {
+    int32_t wmax = 0;
+    for (int32_t q = P.sub_lo[k]; q <= P.sub_hi[k]; ++q) wmax = std::max(wmax, P.fcol[q + 1] - P.fcol[q]);
+    if (wmax <= kWarpSubW) P.wsub.push_back(k);
+  }
   P.n_task_ids = ns + P.n_trsm + P.n_u + P.n_sub;
   P.n_factor_tasks = P.n_sub;
   P.n_hi_tasks = P.n_sub;

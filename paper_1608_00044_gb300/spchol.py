@@ -77,6 +77,7 @@ class Stats(ctypes.Structure):
         ("factor_gather_ms", ctypes.c_double * 3),
         ("factor_gather_batches", ctypes.c_int64),
         ("factor_gather_tiles", ctypes.c_int64),
+        ("n_warp_subtrees", ctypes.c_int64),
     ]
 
     def as_dict(self):

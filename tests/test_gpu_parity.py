@@ -757,3 +757,74 @@ def test_batch_with_w_panels_matches_solo():
             rc, X1, st, h1 = gpu_factor_solve(M, P, B)
             spchol.destroy(h1)
             np.testing.assert_allclose(X, X1, rtol=1e-11, atol=1e-13)
+
+
+def _merged(mats, perms):
+    """The block-diagonal matrix of a batch (lower CSC) and its permutation."""
+    n = sum(M.n for M in mats)
+    cp, ri, vals, pm = [0], [], [], []
+    off = 0
+    for M, p in zip(mats, perms):
+        for j in range(M.n):
+            a, b = M.colptr[j], M.colptr[j + 1]
+            ri.extend((M.rowind[a:b] + off).tolist())
+            vals.extend(M.values[a:b].tolist())
+            cp.append(len(ri))
+        pm.extend((np.asarray(p) + off).tolist())
+        off += M.n
+    A = gridgen.CscLower(n, np.array(cp, np.int64), np.array(ri, np.int32), np.array(vals))
+    return A, np.array(pm, np.int64)
+
+
+def test_warp_subtrees_match_the_oracle():
+    # A batch whose subtree tasks all qualify for single warps (panels <= 32
+    # wide, most of the work in the subtrees): L entry by entry against the
+    # oracle's factor of the block-diagonal matrix (1e-11), the solutions
+    # against the oracle's (1e-10) and berr <= 1e-13; a single large matrix
+    # keeps its subtrees on CTAs.
+    sides = np.random.default_rng(7).integers(16, 64, 160)  # enough work for subtree tasks of many panels
+    mats = [gridgen.diffusion_2d_5pt(int(s), sigma=1.0, seed=300 + i) for i, s in enumerate(sides)]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    Bs = [gridgen.rhs_uniform(M.n, 2, seed=i) for i, M in enumerate(mats)]
+    o = spchol.default_options(max_width=32, relax_zeros=16, tile_rows=32)
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    st = spchol.stats(h)
+    assert st["n_subtrees"] > 0 and st["n_warp_subtrees"] == st["n_subtrees"]
+    assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+    A, _ = _merged(mats, perms)
+    d, lmax = l_max_diff(h, A)
+    assert d <= 1e-11 * lmax, (d, lmax)
+    Xs = [B.copy(order="F") for B in Bs]
+    spchol.batch_solve(h, Xs, [M.n for M in mats], [B.shape[1] for B in Bs])
+    spchol.destroy(h)
+    for M, P, B, X in zip(mats, perms, Bs, Xs):
+        assert oracle.berr(M, X, B) <= BERR_FP64
+        f = oracle.OracleFactor.from_csc(M, P)
+        assert f.factor() == 0
+        Xo = f.solve(B)
+        assert np.abs(X - Xo).max() <= 1e-10 * np.abs(Xo).max()
+    A1, p1, _ = gridgen.workload("lap3d_24")
+    h1 = spchol.analyze(A1.n, A1.colptr, A1.rowind, p1, spchol.default_options(max_width=32))
+    assert spchol.stats(h1)["n_warp_subtrees"] == 0
+    spchol.destroy(h1)
+
+
+def test_warp_subtrees_report_a_failed_pivot():
+    # A matrix of the batch that is not SPD in a column its subtree holds: the
+    # batch reports it (the smallest failing permuted column, here that
+    # matrix's), and a later factorization of the repaired values succeeds.
+    sides = np.random.default_rng(8).integers(16, 64, 160)
+    mats = [gridgen.diffusion_2d_5pt(int(s), sigma=1.0, seed=400 + i) for i, s in enumerate(sides)]
+    perms = [gridgen.geometric_nd(M.dims) for M in mats]
+    o = spchol.default_options(max_width=32, relax_zeros=16, tile_rows=32)
+    h = spchol.batch_analyze([M.n for M in mats], [M.colptr for M in mats], [M.rowind for M in mats], perms, o)
+    assert spchol.stats(h)["n_warp_subtrees"] > 0
+    bad = [M.values.copy() for M in mats]
+    j = int(perms[2][0])  # the first column eliminated in matrix 2 (a leaf of its tree)
+    bad[2][mats[2].colptr[j]] = -5.0
+    k = spchol.batch_factorize(h, bad)
+    assert k > 0
+    m, col = spchol.batch_info(h, k)
+    assert m == 2
+    assert spchol.batch_factorize(h, [M.values for M in mats]) == 0
+    spchol.destroy(h)
