@@ -387,7 +387,7 @@ int setup_device(spchol_handle_t h) {
   // a single large matrix: under 6 %, where the launch ahead of the task loop
   // costs more than the warps gain; with some subtree tasks left to the CTAs
   // the task loop would wait for that launch and then run them)
-  const bool warp_sub = !h->fp32 && mma_mode_of(h->opt.precision) == 0 && !P.params.fanin && P.n_sub > 0 &&
+  const bool warp_sub = mma_mode_of(h->opt.precision) == 0 && !P.params.fanin && P.n_sub > 0 &&
                         (int32_t)P.wsub.size() == P.n_sub && P.sub_work_frac >= 0.2 &&
                         h->opt.fault_inject == 0;
   std::vector<char> by_warp(P.n_sub, 0);
@@ -661,7 +661,7 @@ int setup_device(spchol_handle_t h) {
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
   if (h->n_wsub > 0) {
     int bw = 0;
-    CU(warp_subtree_configure(&bw));
+    CU(warp_subtree_configure(h->fp32, &bw));
     h->grid_wsub = std::max(1, std::min(std::max(bw, 1) * h->num_sms, (h->n_wsub + 3) / 4));
   }
   CU(solve_configure(h->fp32, fan, h->opt.precision == SPCHOL_FP64_TC, h->smem_solve, &bs));
@@ -843,7 +843,7 @@ int enqueue_factor(spchol_handle_t h, const double* vals, cudaStream_t st, bool 
   a.prof = profile ? h->d_prof : nullptr;
   a.trace = profile ? h->d_trace_f : nullptr;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof, 0, 16 * sizeof(unsigned long long), st));
-  CU(launch_warp_subtrees(a, h->grid_wsub, st));  // their tiles' counters release ring tasks
+  CU(launch_warp_subtrees(h->fp32, a, h->grid_wsub, st));  // their tiles' counters release ring tasks
   CU(launch_factor(h->fp32, a, h->grid_factor, h->smem_factor, st));
   CU(cudaMemcpyAsync(h->h_ctrl, h->d_ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   return 0;

@@ -1418,6 +1418,7 @@ constexpr int kWarpLd = kWarpSubW + 1;
 constexpr int kWarpExec = 4;                                   // warps of a CTA that run them
 constexpr int kWarpSmem = kWarpSubW * kWarpLd + kWarpSubW;     // doubles per warp: the block, 1 / l_jj
 
+template <typename T>
 __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
   const unsigned full = 0xffffffffu;
   const int lane = threadIdx.x & 31;
@@ -1427,11 +1428,11 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
   const Ring2 q = rings_of(a);
   for (int s = lo; s <= hi; ++s) {
     const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
-    double* P = panel_ptr<double>(a, s);
+    T* P = panel_ptr<T>(a, s);
     if (!skip) {
       for (int idx = lane; idx < w * w; idx += 32) {
         const int i = idx % w, j = idx / w;
-        ws[i + j * kWarpLd] = i >= j ? ldcg(P + i + (size_t)j * ld) : 0.0;  // zeros above: the inverse goes there
+        ws[i + j * kWarpLd] = i >= j ? (double)ldcg(P + i + (size_t)j * ld) : 0.0;  // zeros above: the inverse goes there
       }
       __syncwarp();
       double qj = 0.0;  // lane j: 1 / d_j
@@ -1485,7 +1486,7 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
         __syncwarp();
         for (int idx = lane; idx < w * w; idx += 32) {
           const int i = idx % w, j = idx / w;
-          if (i >= j) P[i + (size_t)j * ld] = ws[i + j * kWarpLd];
+          if (i >= j) P[i + (size_t)j * ld] = (T)ws[i + j * kWarpLd];
         }
         // L11^{-1}: X[i][c] (i > c) in the upper triangle at (c, i)
         for (int kk = 0; kk < w - 1; ++kk) {
@@ -1503,17 +1504,19 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
           const int i = idx % w, j = idx / w;
           if (i >= j) X[idx] = i == j ? xd[j] : ws[j + i * kWarpLd];
         }
-        // L21 = A21 L11^{-T}, row by row in 4-row strips
+        // L21 = A21 L11^{-T}, row by row in 4-row strips, in the panels'
+        // precision against the stored L11 (as the panel-solve tile)
+        using ct = T;
         const int lr = lane >> 3, lc = lane & 7;
         for (int rs = w; rs < r; rs += 4) {
           const int row = rs + lr;
           const bool rv = row < r;
-          double* Pi = P + row;
-          double x[4];
+          T* Pi = P + row;
+          ct x[4];
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int c = lc + 8 * cc;
-            x[cc] = (rv && c < w) ? ldcg(Pi + (size_t)c * ld) : 0.0;
+            x[cc] = (rv && c < w) ? (ct)ldcg(Pi + (size_t)c * ld) : ct(0);
           }
 #pragma unroll
           for (int cbk = 0; cbk < 4; ++cbk) {
@@ -1521,21 +1524,21 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
             for (int c8 = 0; c8 < 8; ++c8) {
               const int c = 8 * cbk + c8;
               if (c >= w) break;
-              if (lc == c8) x[cbk] *= xd[c];
-              const double xc = __shfl_sync(full, x[cbk], (lr << 3) | c8);
+              if (lc == c8) x[cbk] *= sizeof(T) == 8 ? (ct)xd[c] : ct(1) / (ct)ws[c * (kWarpLd + 1)];
+              const ct xc = __shfl_sync(full, x[cbk], (lr << 3) | c8);
               const double* Lc = ws + c * kWarpLd;  // l_qc at Lc[q], q > c
-              if (lc > c8) x[cbk] -= xc * Lc[lc + 8 * cbk];
+              if (lc > c8) x[cbk] -= xc * (ct)Lc[lc + 8 * cbk];
 #pragma unroll
               for (int cc = cbk + 1; cc < 4; ++cc) {
                 if (8 * cc >= w) break;
-                x[cc] -= xc * Lc[lc + 8 * cc];
+                x[cc] -= xc * (ct)Lc[lc + 8 * cc];
               }
             }
           }
 #pragma unroll
           for (int cc = 0; cc < 4; ++cc) {
             const int c = lc + 8 * cc;
-            if (rv && c < w) Pi[(size_t)c * ld] = x[cc];
+            if (rv && c < w) Pi[(size_t)c * ld] = (T)x[cc];
           }
         }
         __syncwarp();  // the rows below are written before the update tiles read them
@@ -1548,15 +1551,15 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
       const bool outside = u.t > hi;
       if (!skip) {
         const int ft = a.pv.fcol[u.t], ldt = a.pv.ld[u.t];
-        double* Pt = panel_ptr<double>(a, u.t);
+        T* Pt = panel_ptr<T>(a, u.t);
         const int nout = u.rowlen * u.seglen;
         for (int o = lane; o < nout; o += 32) {
           const int i = o % u.rowlen, j = o / u.rowlen;
           const int gi = Rs[u.row0 + i], gj = Rs[u.seg0 + j];
           if (gi < gj) continue;  // the upper part of a target's diagonal block
-          const double* ai = P + u.row0 + i;
-          const double* bj = P + u.seg0 + j;
-          double c0 = 0.0, c1 = 0.0;
+          const T* ai = P + u.row0 + i;
+          const T* bj = P + u.seg0 + j;
+          T c0 = T(0), c1 = T(0);
           int kk = 0;
           for (; kk + 1 < w; kk += 2) {
             c0 = fma(ai[(size_t)kk * ld], bj[(size_t)kk * ld], c0);
@@ -1568,7 +1571,7 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
             atomicCAS(&a.ctrl[kErr], 0, SPCHOL_DEV_EINTERNAL);
             continue;
           }
-          double* dst = Pt + p + (size_t)(gj - ft) * ldt;
+          T* dst = Pt + p + (size_t)(gj - ft) * ldt;
           if (outside)
             red_add(dst, -(c0 + c1));
           else
@@ -1868,6 +1871,7 @@ __global__ void __launch_bounds__(kFactorThreads, MODE == 3 ? 3 : MODE != 0 ? 2 
 // the next subtree from a counter until none is left.  The tiles they count
 // down push ready tasks into the rings, which the task loop's kernel then
 // finds there; every subtree adds one to the completed-task count.
+template <typename T>
 __global__ void __launch_bounds__(32 * kWarpExec) warp_subtree_kernel(FactorArgs a) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
@@ -1880,7 +1884,7 @@ __global__ void __launch_bounds__(32 * kWarpExec) warp_subtree_kernel(FactorArgs
     if (e >= a.n_wsub) break;
     const int k = a.wsub[e];
     const unsigned long long t0 = a.trace && lane == 0 ? global_ns() : 0ull;
-    warp_subtree(a, k, ws);
+    warp_subtree<T>(a, k, ws);
     if (lane == 0) {
       atomicAdd(&a.ctrl[kDone], 1);
       if (a.trace) {
@@ -1902,19 +1906,22 @@ __global__ void assemble_kernel(const double* __restrict__ values, const int64_t
 
 size_t warp_subtree_smem_bytes() { return (size_t)kWarpExec * kWarpSmem * sizeof(double); }
 
-cudaError_t warp_subtree_configure(int* blocks_per_sm) {
-  const size_t smem = warp_subtree_smem_bytes();
-  cudaError_t e = ensure_smem_limit((const void*)warp_subtree_kernel, smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, (const void*)warp_subtree_kernel, 32 * kWarpExec,
-                                                       smem);
+static const void* warp_subtree_fn(bool fp32) {
+  return fp32 ? (const void*)warp_subtree_kernel<float> : (const void*)warp_subtree_kernel<double>;
 }
 
-cudaError_t launch_warp_subtrees(const FactorArgs& a, int grid, cudaStream_t st) {
+cudaError_t warp_subtree_configure(bool fp32, int* blocks_per_sm) {
+  const size_t smem = warp_subtree_smem_bytes();
+  cudaError_t e = ensure_smem_limit(warp_subtree_fn(fp32), smem);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, warp_subtree_fn(fp32), 32 * kWarpExec, smem);
+}
+
+cudaError_t launch_warp_subtrees(bool fp32, const FactorArgs& a, int grid, cudaStream_t st) {
   if (a.n_wsub == 0) return cudaSuccess;
   void* args[] = {const_cast<FactorArgs*>(&a)};
-  return cudaLaunchKernel((const void*)warp_subtree_kernel, dim3(grid), dim3(32 * kWarpExec), args,
-                          warp_subtree_smem_bytes(), st);
+  return cudaLaunchKernel(warp_subtree_fn(fp32), dim3(grid), dim3(32 * kWarpExec), args, warp_subtree_smem_bytes(),
+                          st);
 }
 
 size_t factor_smem_bytes(int max_w, int mma_mode) {

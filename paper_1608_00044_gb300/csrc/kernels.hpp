@@ -161,8 +161,8 @@ struct SolveArgs {
 // factor.cu
 size_t factor_smem_bytes(int max_w, int mma_mode);
 size_t warp_subtree_smem_bytes();  // shared memory of a CTA of the warp-level subtree tasks
-cudaError_t warp_subtree_configure(int* blocks_per_sm);
-cudaError_t launch_warp_subtrees(const FactorArgs& a, int grid, cudaStream_t st);
+cudaError_t warp_subtree_configure(bool fp32, int* blocks_per_sm);
+cudaError_t launch_warp_subtrees(bool fp32, const FactorArgs& a, int grid, cudaStream_t st);
 // Fan-in mode: shared memory a gather needs for panels up to max_w wide, and
 // the values it stages per batch (*cap).
 size_t fanin_smem_bytes(int max_w, bool fp32, int* cap);
