@@ -23,6 +23,7 @@ DEFAULT_CANDIDATES = [
     (64, 4, 64),
     (64, 16, 64),
     (64, 64, 64),
+    (32, 8, 16),
     (32, 16, 32),
     (32, 64, 64),
     (128, 64, 64),

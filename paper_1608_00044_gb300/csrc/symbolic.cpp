@@ -591,6 +591,10 @@ int build_plan(int64_t n, const int64_t* colptr, const int32_t* rowind, const in
     for (int32_t q = P.sub_lo[k]; q <= P.sub_hi[k]; ++q) wmax = std::max(wmax, P.fcol[q + 1] - P.fcol[q]);
     if (wmax <= kWarpSubW) P.wsub.push_back(k);
   }
+  // the most work first: each warp takes the next, so the last to start are
+  // the smallest (a large subtree started late would hold its launch open)
+  std::stable_sort(P.wsub.begin(), P.wsub.end(),
+                   [&](int32_t x, int32_t y) { return sub_fl[P.sub_hi[x]] > sub_fl[P.sub_hi[y]]; });
   P.n_task_ids = ns + P.n_trsm + P.n_u + P.n_sub;
   P.n_factor_tasks = P.n_sub;
   P.n_hi_tasks = P.n_sub;
