@@ -635,7 +635,8 @@ def measure_batch(spchol, torch, dev, count=512, width=64):
         out[label] = {"factor_ms_one_launch": ms, "tflops": st0["flops"] / (ms * 1e-3) / 1e12,
                       "achieved_gbs": fbytes / (ms * 1e-3) / 1e9, "algorithmic_bytes": int(fbytes),
                       "graph_replay_ms": statistics.median(gms), "autotuned": {k: tuned[k] for k in
-                      ("max_width", "relax_zeros", "tile_rows", "tried_ms")},
+                      ("max_width", "relax_zeros", "tile_rows", "objective", "tried_ms", "tried_factor_ms",
+                       "tried_solve_ms") if k in tuned},
                       "solve_ms": st["solve_ms"], "worst_berr": worst, "analyze_s": ana, "rc": rc,
                       "panels": st0["n_supernodes"], "tasks": st0["n_tasks"]}
         spchol.destroy(h)
