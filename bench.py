@@ -690,7 +690,7 @@ def measure_batch_sharded(spchol, torch, dist, count=512, width=64):
     mats = [gridgen.diffusion_2d_5pt(int(sd), sigma=1.0, seed=1000 + i) for i, sd in enumerate(sides)]
     perms = [gridgen.geometric_nd(M.dims) for M in mats]
     rhs = [gridgen.rhs_uniform(M.n, 1, seed=i) for i, M in enumerate(mats)]
-    opts = dict(max_width=32, relax_zeros=64)  # the autotuner's choice for this batch on one GPU
+    opts = dict(max_width=32, relax_zeros=16, tile_rows=32)  # the autotuner's choice for this batch on one GPU
     costs = shard.matrix_flops(mats, perms, **opts)
     shard.run_sharded(mats, perms, rhs, engine="gpu", costs=costs, **opts)  # warm-up
     dist.barrier()

@@ -78,6 +78,7 @@ struct spchol_handle_s {
   int nfseeds = 0;
   int32_t* d_wsub = nullptr;  // subtree tasks run by single warps (Plan::wsub), when used
   int n_wsub = 0, grid_wsub = 0;
+  int solve_done = 0;  // SolveArgs::ntask_done
   int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_st_rows = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
   int32_t *d_st_tptr = nullptr, *d_st_tgt = nullptr, *d_rt_ptr = nullptr, *d_rt_tile = nullptr;
@@ -405,10 +406,24 @@ int setup_device(spchol_handle_t h) {
   }
   size_t o_fseeds = r32(fseeds.size()), o_wsub = r32(warp_sub ? P.wsub.size() : 0);
   size_t o_stf = r32(ns), o_nst = r32(ns), o_strows = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
+  // the panels of the warp subtrees: solved by the subtree solve launches, so
+  // none of their tasks is seeded, and their backward tiles' counters start
+  // out of reach of the task loop
+  std::vector<char> in_wsub(ns, 0);
+  std::vector<int32_t> bdep0 = P.bdep0;
+  int64_t sub_tasks = 0;
+  if (warp_sub)
+    for (int32_t k : P.wsub)
+      for (int32_t q = P.sub_lo[k]; q <= P.sub_hi[k]; ++q) {
+        in_wsub[q] = 1;
+        sub_tasks += 2 + 2 * (int64_t)P.nst[q];
+        for (int32_t kt = P.st_first[q]; kt < P.st_first[q] + P.nst[q]; ++kt) bdep0[kt] = 1 << 30;
+      }
+  h->solve_done = (int)((int64_t)P.n_solve_tasks - P.n_wpan - sub_tasks + (warp_sub ? (int64_t)P.wsub.size() : 0));
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
     nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
-    if (P.fdep0[s] == 0) {
+    if (P.fdep0[s] == 0 && !in_wsub[s]) {
       if (P.woff[s] >= 0)  // a W panel starts with its forward tiles
         for (int k = 0; k < P.nst[s]; ++k) sseeds.push_back(ns + P.st_first[s] + k);
       else
@@ -589,7 +604,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_nkids_init, nkids)) || (rc = upload(h, h->d_sseeds, sseeds)) ||
       (rc = upload(h, h->d_st_tptr, P.st_tptr)) || (rc = upload(h, h->d_st_tgt, P.st_tgt)) ||
       (rc = upload(h, h->d_rt_ptr, P.rt_ptr)) || (rc = upload(h, h->d_rt_tile, P.rt_tile)) ||
-      (rc = upload(h, h->d_fdep0, P.fdep0)) || (rc = upload(h, h->d_bdep0, P.bdep0)) ||
+      (rc = upload(h, h->d_fdep0, P.fdep0)) || (rc = upload(h, h->d_bdep0, bdep0)) ||
       (rc = upload(h, h->d_perm, perm32)))
     return rc;
   if (det && ((rc = upload(h, h->d_u_next, P.u_next)) || (rc = upload(h, h->d_u_dep0, P.u_dep0)) ||
@@ -950,6 +965,11 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.wbuf = h->d_wbuf;
   a.woff = P.n_wpan > 0 ? h->d_woff : nullptr;
   a.n_wpan = P.n_wpan;
+  a.sub_lo = h->d_sub_lo;
+  a.sub_hi = h->d_sub_hi;
+  a.wsub = h->d_wsub;
+  a.n_wsub = h->n_wsub;
+  a.ntask_done = h->solve_done;
   a.Y = Y;
   a.ldy = P.n;
   a.nrhs = nrhs;
@@ -957,8 +977,10 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.prof = h->opt.profile ? h->d_prof + 16 : nullptr;
   a.trace = h->d_trace_s;
   if (a.prof) CU(cudaMemsetAsync(h->d_prof + 16, 0, 8 * sizeof(unsigned long long), st));
+  CU(launch_subtree_solve(h->fp32, true, a, h->grid_wsub, st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
-  int rc = read_status(h, st, P.n_solve_tasks - P.n_wpan);
+  CU(launch_subtree_solve(h->fp32, false, a, h->grid_wsub, st));
+  int rc = read_status(h, st, h->solve_done + h->n_wsub);
   h->traced_s = h->d_trace_s != nullptr;
   if (h->opt.profile) {
     CU(cudaMemcpy(h->h_prof + 16, h->d_prof + 16, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
@@ -1389,19 +1411,26 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.wbuf = h->d_wbuf;
   a.woff = P.n_wpan > 0 ? h->d_woff : nullptr;
   a.n_wpan = P.n_wpan;
+  a.sub_lo = h->d_sub_lo;
+  a.sub_hi = h->d_sub_hi;
+  a.wsub = h->d_wsub;
+  a.n_wsub = h->n_wsub;
+  a.ntask_done = h->solve_done;
   a.Y = Y;
   a.ldy = n;
   a.nrhs = nrhs;
   a.tc_tiles = h->opt.precision == SPCHOL_FP64_TC ? 1 : 0;
   a.prof = nullptr;
   a.trace = nullptr;
+  CU(launch_subtree_solve(false, true, a, h->grid_wsub, st));
   CU(launch_solve(false, a, h->grid_solve, h->smem_solve, st));
+  CU(launch_subtree_solve(false, false, a, h->grid_wsub, st));
   CU(launch_permute_out(Y, n, B, ldb, h->d_perm, n, nrhs, st));
   CU(cudaMemcpyAsync(h->h_ctrl, ctrl, kCtrlWords * sizeof(int), cudaMemcpyDeviceToHost, st));
   CU(cudaStreamSynchronize(st));
   const int* c = h->h_ctrl;
   if (c[kErr] != 0) return c[kErr];
-  if (c[kDone] != P.n_solve_tasks - P.n_wpan) return SPCHOL_EINTERNAL;
+  if (c[kDone] != h->solve_done + h->n_wsub) return SPCHOL_EINTERNAL;
   return 0;
 }
 

@@ -14,7 +14,8 @@ enum CtrlWord : int {
   kErr = 2,      // 0, or an SPCHOL_E* code (timeout, internal check)
   kInfo = 3,     // smallest failing pivot column + 1, INT32_MAX if none
   kWhere = 5,    // diagnostic: task id where a wait gave up
-  kWarpNext = 6, // the factorization's next warp-level subtree task (FactorArgs::wsub)
+  kWarpNext = 6, // the next warp-level subtree task (FactorArgs::wsub; the solves' forward launch)
+  kWarpNextB = 7, // the solves' backward launch's next warp-level subtree
   kHiHead = 32,  // the high-priority ring, in its own 128-byte line
   kHiTail = 33,
   kDone = 64,    // tasks completed: the end test, updated by every task, in a line of its own

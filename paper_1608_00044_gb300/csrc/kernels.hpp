@@ -135,6 +135,16 @@ struct SolveArgs {
   const void* wbuf;      // W = L21 L11^{-1} of the W panels (Plan::woff)
   const int64_t* woff;   // null: no W panels
   int32_t n_wpan;        // W panels: their backward diagonal tasks never run
+  // The subtree tasks the factorization ran on single warps (FactorArgs::wsub),
+  // solved by single warps too: their forward solves in a launch before the
+  // task loop, their backward solves in one after it (subtree_solve_kernel).
+  // ntask_done: the tasks completed when the task loop may end (its own and
+  // the forward subtrees).
+  const int32_t* sub_lo;
+  const int32_t* sub_hi;
+  const int32_t* wsub;
+  int32_t n_wsub;
+  int32_t ntask_done;
   double* Y;        // n x nrhs, permuted order
   int64_t ldy;
   int nrhs;
@@ -177,6 +187,9 @@ cudaError_t launch_fanrec(const FanEnt* ent, int64_t n, const UTask* ut, const i
 size_t solve_smem_bytes(int max_w, bool tc_tiles, bool fanin);
 cudaError_t solve_configure(bool fp32, bool fanin, bool tc_tiles, size_t smem, int* blocks_per_sm);
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st);
+// the forward (before the task loop) or backward (after it) solves of the
+// subtree tasks run by single warps (SolveArgs::wsub)
+cudaError_t launch_subtree_solve(bool fp32, bool forward, const SolveArgs& a, int grid, cudaStream_t st);
 cudaError_t launch_permute_in(const double* B, int64_t ldb, double* Y, int64_t ldy, const int32_t* perm,
                               int64_t n, int nrhs, cudaStream_t st);
 cudaError_t launch_permute_out(const double* Y, int64_t ldy, double* B, int64_t ldb, const int32_t* perm,

@@ -1013,7 +1013,7 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
         sh.next = -1;
       } else {
         int lo_ready;
-        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask - a.n_wpan);
+        sh.task = ring2_claim(q, pend, &lo_ready, a.ntask_done);
       }
       // While this CTA holds a claimed slot whose task is not yet pushed, it
       // takes no continuation: it comes back for that task after this one.
@@ -1125,6 +1125,152 @@ __global__ void __launch_bounds__(kSolveThreads, TC ? 4 : 5) solve_kernel(SolveA
   }
 }
 
+// ---------------------------------------------------------------- subtree solves on single warps
+// The subtree tasks the factorization ran on single warps (SolveArgs::wsub)
+// are solved by single warps too.  A launch before the task loop runs every
+// such subtree's forward solve, one warp per subtree, panels in postorder:
+// y_s <- L11^{-1} y_s, then every tile of s, y[rows] -= L21 y_s, by plain
+// read-modify-writes for rows inside the subtree and atomics for the others,
+// whose panels' counters it then counts down (pushing the diagonal tasks that
+// become ready).  The task loop runs everything outside those subtrees: their
+// own tasks never become ready there (no forward tile from outside reaches
+// their panels, and their backward tiles' counters start out of reach).  A
+// launch after it runs each subtree's backward solve, panels in reverse
+// postorder: y_s -= L21^T x[rows] over its tiles, then x_s <- L11^{-T} y_s;
+// every x it reads is final by then (outside: the task loop has ended;
+// inside: an ancestor in the subtree, solved earlier by the same warp).
+constexpr int kWsWarps = 4;  // warps per CTA of the subtree solve launches
+constexpr int kWsNrc = 8;    // right-hand sides per pass (a panel is at most 32 wide)
+
+template <typename T>
+__device__ void subtree_forward(const SolveArgs& a, int k, double* ys, double* zs) {
+  const int lane = threadIdx.x & 31;
+  const int lo = a.sub_lo[k], hi = a.sub_hi[k];
+  const int gend = a.pv.fcol[hi + 1];  // rows from here on lie outside the subtree
+  const Ring2 q{a.ring, a.ring + a.n_hi, a.n_hi, a.ntask - a.n_hi, a.ctrl, a.budget_ns};
+  for (int s = lo; s <= hi; ++s) {
+    const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+    const T* P = spanel<T>(a, s);
+    const double* X = a.inv + a.invoff[s];
+    const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+    const int ts = a.st_rows[s];
+    bool outside = false;
+    for (int r0 = 0; r0 < a.nrhs; r0 += kWsNrc) {
+      const int nrc = min(kWsNrc, a.nrhs - r0);
+      double* Y = a.Y + (size_t)r0 * a.ldy;
+      for (int o = lane; o < w * nrc; o += 32) ys[o] = ldcg(Y + f + o % w + (size_t)(o / w) * a.ldy);
+      __syncwarp();
+      for (int o = lane; o < w * nrc; o += 32) {  // y_s <- L11^{-1} y_s
+        const int i = o % w, c = o / w;
+        double acc = 0.0;
+        for (int kk = 0; kk <= i; ++kk) acc = fma(X[i + kk * w], ys[kk + c * w], acc);
+        zs[o] = acc;
+        Y[f + i + (size_t)c * a.ldy] = acc;
+      }
+      __syncwarp();
+      for (int kt = 0; kt < a.nst[s]; ++kt) {  // y[rows] -= L21 y_s
+        const int row0 = w + kt * ts, cnt = min(ts, r - row0);
+        for (int o = lane; o < cnt * nrc; o += 32) {
+          const int i = o % cnt, c = o / cnt;
+          const T* Li = P + row0 + i;
+          double acc0 = 0.0, acc1 = 0.0;
+          int kk = 0;
+          for (; kk + 1 < w; kk += 2) {
+            acc0 = fma((double)Li[(size_t)kk * ld], zs[kk + c * w], acc0);
+            acc1 = fma((double)Li[(size_t)(kk + 1) * ld], zs[kk + 1 + c * w], acc1);
+          }
+          if (kk < w) acc0 = fma((double)Li[(size_t)kk * ld], zs[kk + c * w], acc0);
+          const int g = R[row0 + i];
+          double* dst = Y + g + (size_t)c * a.ldy;
+          if (g < gend) {
+            *dst -= acc0 + acc1;
+          } else {
+            red_add(dst, -(acc0 + acc1));
+            outside = true;
+          }
+        }
+      }
+      __syncwarp();  // the next pass reuses ys and zs; the next panel reads these rows
+    }
+    // count the tiles down on the panels outside the subtree that they reach
+    if (__any_sync(0xffffffffu, outside)) {
+      if (lane == 0) {
+        __threadfence();
+        for (int kt = a.st_first[s]; kt < a.st_first[s] + a.nst[s]; ++kt)
+          for (int e = a.st_tptr[kt]; e < a.st_tptr[kt + 1]; ++e) {
+            const int t = a.st_tgt[e];
+            if (t > hi && atom_add_acqrel(&a.fdep[t], -1) == 1) {
+              if (is_wpanel(a, t))
+                release_w_forward(q, a, t, nullptr);
+              else
+                ring2_push_one(q, true, t);
+            }
+          }
+      }
+      __syncwarp();
+    }
+  }
+}
+
+template <typename T>
+__device__ void subtree_backward(const SolveArgs& a, int k, double* ys) {
+  const int lane = threadIdx.x & 31;
+  const int lo = a.sub_lo[k], hi = a.sub_hi[k];
+  for (int s = hi; s >= lo; --s) {
+    const int f = a.pv.fcol[s], w = a.pv.fcol[s + 1] - f, ld = a.pv.ld[s], r = a.pv.nrows[s];
+    const T* P = spanel<T>(a, s);
+    const double* X = a.inv + a.invoff[s];
+    const int32_t* R = a.pv.rows + a.pv.rowoff[s];
+    const int ts = a.st_rows[s];
+    for (int r0 = 0; r0 < a.nrhs; r0 += kWsNrc) {
+      const int nrc = min(kWsNrc, a.nrhs - r0);
+      double* Y = a.Y + (size_t)r0 * a.ldy;
+      for (int o = lane; o < w * nrc; o += 32) ys[o] = ldcg(Y + f + o % w + (size_t)(o / w) * a.ldy);
+      __syncwarp();
+      for (int kt = 0; kt < a.nst[s]; ++kt) {  // y_s -= L21^T x[rows]
+        const int row0 = w + kt * ts, cnt = min(ts, r - row0);
+        for (int o = lane; o < w * nrc; o += 32) {
+          const int j = o % w, c = o / w;
+          const T* Lj = P + row0 + (size_t)j * ld;
+          double acc0 = 0.0, acc1 = 0.0;
+          int i = 0;
+          for (; i + 1 < cnt; i += 2) {
+            acc0 = fma((double)Lj[i], ldcg(Y + R[row0 + i] + (size_t)c * a.ldy), acc0);
+            acc1 = fma((double)Lj[i + 1], ldcg(Y + R[row0 + i + 1] + (size_t)c * a.ldy), acc1);
+          }
+          if (i < cnt) acc0 = fma((double)Lj[i], ldcg(Y + R[row0 + i] + (size_t)c * a.ldy), acc0);
+          ys[o] -= acc0 + acc1;
+        }
+      }
+      __syncwarp();
+      for (int o = lane; o < w * nrc; o += 32) {  // x_s <- L11^{-T} y_s
+        const int j = o % w, c = o / w;
+        double acc = 0.0;
+        for (int i = j; i < w; ++i) acc = fma(X[i + j * w], ys[i + c * w], acc);
+        Y[f + j + (size_t)c * a.ldy] = acc;
+      }
+      __syncwarp();  // the next pass reuses ys; the next panels read x_s
+    }
+  }
+}
+
+template <typename T, bool FWD>
+__global__ void __launch_bounds__(32 * kWsWarps) subtree_solve_kernel(SolveArgs a) {
+  __shared__ double buf[kWsWarps][2][kWsNrc * 32];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (;;) {
+    int e = 0;
+    if (lane == 0) e = atomicAdd(&a.ctrl[FWD ? kWarpNext : kWarpNextB], 1);
+    e = __shfl_sync(0xffffffffu, e, 0);
+    if (e >= a.n_wsub) break;
+    if constexpr (FWD)
+      subtree_forward<T>(a, a.wsub[e], buf[warp][0], buf[warp][1]);
+    else
+      subtree_backward<T>(a, a.wsub[e], buf[warp][0]);
+    if (lane == 0) atomicAdd(&a.ctrl[kDone], 1);
+  }
+}
+
 __global__ void permute_in_kernel(const double* __restrict__ B, int64_t ldb, double* __restrict__ Y, int64_t ldy,
                                   const int32_t* __restrict__ perm, int64_t n, int nrhs) {
   const int64_t total = n * nrhs;
@@ -1175,6 +1321,14 @@ cudaError_t solve_configure(bool fp32, bool fanin, bool tc, size_t smem, int* bl
   cudaError_t e = ensure_smem_limit(fn, smem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, fn, kSolveThreads, smem);
+}
+
+cudaError_t launch_subtree_solve(bool fp32, bool forward, const SolveArgs& a, int grid, cudaStream_t st) {
+  if (a.n_wsub == 0) return cudaSuccess;
+  void* args[] = {const_cast<SolveArgs*>(&a)};
+  const void* fn = fp32 ? (forward ? (const void*)subtree_solve_kernel<float, true> : (const void*)subtree_solve_kernel<float, false>)
+                        : (forward ? (const void*)subtree_solve_kernel<double, true> : (const void*)subtree_solve_kernel<double, false>);
+  return cudaLaunchKernel(fn, dim3(grid), dim3(32 * kWsWarps), args, 0, st);
 }
 
 cudaError_t launch_solve(bool fp32, const SolveArgs& a, int grid, size_t smem, cudaStream_t st) {
