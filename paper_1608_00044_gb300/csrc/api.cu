@@ -77,7 +77,8 @@ struct spchol_handle_s {
   int32_t *d_fseeds = nullptr;
   int nfseeds = 0;
   int32_t* d_wsub = nullptr;  // subtree tasks run by single warps (Plan::wsub), when used
-  int n_wsub = 0, grid_wsub = 0;
+  int n_wsub = 0, grid_wsub = 0;  // the factorization's warp subtrees (0: none)
+  int n_wsub_solve = 0;            // the solves' (0: none)
   int solve_done = 0;  // SolveArgs::ntask_done
   int32_t *d_st_first = nullptr, *d_nst = nullptr, *d_st_sn = nullptr, *d_st_rows = nullptr, *d_kid_ptr = nullptr, *d_kids = nullptr;
   int32_t *d_nkids_init = nullptr, *d_fkids = nullptr, *d_ftiles = nullptr, *d_btiles = nullptr;
@@ -394,6 +395,12 @@ int setup_device(spchol_handle_t h) {
   std::vector<char> by_warp(P.n_sub, 0);
   if (warp_sub)
     for (int32_t k : P.wsub) by_warp[k] = 1;
+  // the solves take the same subtrees on single warps under the same
+  // condition.  (Whenever the subtrees qualify, whatever their share of the
+  // work, was measured too: 48^3 diffusion, one right-hand side, 4.2 -> 3.8
+  // ms, but 40^3 with eight 4.5 -> 6.1 ms: a large subtree's solve on one warp
+  // then holds the task loop back.)
+  const bool warp_solve = warp_sub;
   for (int32_t k = 0; k < P.n_sub; ++k)
     if (!by_warp[k]) fseeds.push_back(ns + P.n_trsm + P.n_u + k);
   for (int s = 0; s < ns; ++s)
@@ -404,7 +411,7 @@ int setup_device(spchol_handle_t h) {
     const int32_t missing = ns + P.n_trsm + P.n_u + P.in_sub[ns - 1];
     fseeds.erase(std::find(fseeds.begin(), fseeds.end(), missing));
   }
-  size_t o_fseeds = r32(fseeds.size()), o_wsub = r32(warp_sub ? P.wsub.size() : 0);
+  size_t o_fseeds = r32(fseeds.size()), o_wsub = r32(warp_sub || warp_solve ? P.wsub.size() : 0);
   size_t o_stf = r32(ns), o_nst = r32(ns), o_strows = r32(ns), o_stsn = r32(P.st_sn.size()), o_kp = r32(ns + 1), o_k = r32(P.kids.size());
   // the panels of the warp subtrees: solved by the subtree solve launches, so
   // none of their tasks is seeded, and their backward tiles' counters start
@@ -412,14 +419,14 @@ int setup_device(spchol_handle_t h) {
   std::vector<char> in_wsub(ns, 0);
   std::vector<int32_t> bdep0 = P.bdep0;
   int64_t sub_tasks = 0;
-  if (warp_sub)
+  if (warp_solve)
     for (int32_t k : P.wsub)
       for (int32_t q = P.sub_lo[k]; q <= P.sub_hi[k]; ++q) {
         in_wsub[q] = 1;
         sub_tasks += 2 + 2 * (int64_t)P.nst[q];
         for (int32_t kt = P.st_first[q]; kt < P.st_first[q] + P.nst[q]; ++kt) bdep0[kt] = 1 << 30;
       }
-  h->solve_done = (int)((int64_t)P.n_solve_tasks - P.n_wpan - sub_tasks + (warp_sub ? (int64_t)P.wsub.size() : 0));
+  h->solve_done = (int)((int64_t)P.n_solve_tasks - P.n_wpan - sub_tasks + (warp_solve ? (int64_t)P.wsub.size() : 0));
   std::vector<int32_t> nkids(ns, 0), sseeds;
   for (int s = 0; s < ns; ++s) {
     nkids[s] = P.kid_ptr[s + 1] - P.kid_ptr[s];
@@ -523,6 +530,7 @@ int setup_device(spchol_handle_t h) {
   h->nfseeds = (int)fseeds.size();
   h->d_wsub = (int32_t*)(b + o_wsub);
   h->n_wsub = warp_sub ? (int)P.wsub.size() : 0;
+  h->n_wsub_solve = warp_solve ? (int)P.wsub.size() : 0;
   h->d_st_first = (int32_t*)(b + o_stf);
   h->d_nst = (int32_t*)(b + o_nst);
   h->d_st_sn = (int32_t*)(b + o_stsn);
@@ -597,7 +605,7 @@ int setup_device(spchol_handle_t h) {
       (rc = upload(h, h->d_sub_lo, P.sub_lo)) || (rc = upload(h, h->d_sub_hi, P.sub_hi)) || (rc = upload(h, h->d_ut, P.ut)) ||
       (rc = upload(h, h->d_dep_init, P.dep_f)) || (rc = upload(h, h->d_trsm_init, P.ntrsm)) ||
       (rc = upload(h, h->d_fseeds, fseeds)) || (rc = upload(h, h->d_st_first, P.st_first)) ||
-      (h->n_wsub > 0 && (rc = upload(h, h->d_wsub, P.wsub))) ||
+      ((warp_sub || warp_solve) && (rc = upload(h, h->d_wsub, P.wsub))) ||
       (rc = upload(h, h->d_nst, P.nst)) || (rc = upload(h, h->d_st_sn, P.st_sn)) ||
       (rc = upload(h, h->d_st_rows, P.st_rows)) ||
       (rc = upload(h, h->d_kid_ptr, P.kid_ptr)) || (rc = upload(h, h->d_kids, P.kids)) ||
@@ -674,10 +682,10 @@ int setup_device(spchol_handle_t h) {
   h->smem_solve = solve_smem_bytes(wmax, h->opt.precision == SPCHOL_FP64_TC, fan);
   int bf = 0, bs = 0;
   CU(factor_configure(h->fp32, mma_mode_of(h->opt.precision), fan, h->smem_factor, &bf));
-  if (h->n_wsub > 0) {
+  if (h->n_wsub > 0 || h->n_wsub_solve > 0) {
     int bw = 0;
     CU(warp_subtree_configure(h->fp32, &bw));
-    h->grid_wsub = std::max(1, std::min(std::max(bw, 1) * h->num_sms, (h->n_wsub + 3) / 4));
+    h->grid_wsub = std::max(1, std::min(std::max(bw, 1) * h->num_sms, ((int)P.wsub.size() + 3) / 4));
   }
   CU(solve_configure(h->fp32, fan, h->opt.precision == SPCHOL_FP64_TC, h->smem_solve, &bs));
   if (bf < 1 || bs < 1) return SPCHOL_ECUDA;
@@ -968,7 +976,7 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   a.sub_lo = h->d_sub_lo;
   a.sub_hi = h->d_sub_hi;
   a.wsub = h->d_wsub;
-  a.n_wsub = h->n_wsub;
+  a.n_wsub = h->n_wsub_solve;
   a.ntask_done = h->solve_done;
   a.Y = Y;
   a.ldy = P.n;
@@ -980,7 +988,7 @@ int solve_permuted(spchol_handle_t h, double* Y, int nrhs, cudaStream_t st) {
   CU(launch_subtree_solve(h->fp32, true, a, h->grid_wsub, st));
   CU(launch_solve(h->fp32, a, h->grid_solve, h->smem_solve, st));
   CU(launch_subtree_solve(h->fp32, false, a, h->grid_wsub, st));
-  int rc = read_status(h, st, h->solve_done + h->n_wsub);
+  int rc = read_status(h, st, h->solve_done + h->n_wsub_solve);
   h->traced_s = h->d_trace_s != nullptr;
   if (h->opt.profile) {
     CU(cudaMemcpy(h->h_prof + 16, h->d_prof + 16, 8 * sizeof(unsigned long long), cudaMemcpyDeviceToHost));
@@ -1414,7 +1422,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   a.sub_lo = h->d_sub_lo;
   a.sub_hi = h->d_sub_hi;
   a.wsub = h->d_wsub;
-  a.n_wsub = h->n_wsub;
+  a.n_wsub = h->n_wsub_solve;
   a.ntask_done = h->solve_done;
   a.Y = Y;
   a.ldy = n;
@@ -1430,7 +1438,7 @@ int spchol_solve_noalloc(spchol_handle_t h, double* B, int64_t ldb, int nrhs, vo
   CU(cudaStreamSynchronize(st));
   const int* c = h->h_ctrl;
   if (c[kErr] != 0) return c[kErr];
-  if (c[kDone] != h->solve_done + h->n_wsub) return SPCHOL_EINTERNAL;
+  if (c[kDone] != h->solve_done + h->n_wsub_solve) return SPCHOL_EINTERNAL;
   return 0;
 }
 
