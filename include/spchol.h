@@ -198,8 +198,9 @@ typedef struct spchol_stats {
                                  CTAs) cutting batches, staging them and adding them */
   int64_t factor_gather_batches;
   int64_t factor_gather_tiles;
-  int64_t n_warp_subtrees;   /* subtree tasks run by single warps (panels at most 32 wide, FP64, when
-                                the subtrees hold a good part of the work: batches of small matrices) */
+  int64_t n_warp_subtrees;   /* subtree tasks whose factorization and solves run on single warps (panels
+                                at most 32 wide, FP64 or FP32 updates, when the subtrees hold a good
+                                part of the work: batches of small matrices) */
 } spchol_stats;
 
 /* Fill *opt with the defaults listed above. */
