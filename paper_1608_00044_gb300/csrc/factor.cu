@@ -1399,14 +1399,19 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
 // task loop: the many small subtrees of a batch of small matrices, or the
 // leaves of a large one, then advance kWarpExec per CTA side by side with warp
 // barriers only, where a CTA subtree task runs one of them with CTA barriers
-// at every column and step.  Per panel, in postorder:
-//   * the diagonal block in shared memory (leading dimension kWarpLd), lane i
-//     holding row i: each multiplier, update and pivot is the diagonal task's
-//     operation on the same operands in the same order, so L11 is the same;
-//   * its inverse, lane c holding column c, by the diagonal task's
-//     substitution (the same operations per entry);
-//   * the panel solve of every row below in the panel-solve tile's 4-row
-//     strips (lane (r, c) row r at columns c + 8 j), its operations and order;
+// at every column and step.  A warp-wide FP64 instruction holds the SM's FP64
+// pipe as long whatever its active lanes (the pipe bounds these warps), so
+// each step spreads its entries over the lanes.  Per panel, in postorder:
+//   * the diagonal block in shared memory (leading dimension kWarpLd): each
+//     multiplier, update and pivot is the diagonal task's operation on the
+//     same operands in the same order, so L11 is the same; the lane of row i
+//     forms its multiplier, then the trailing triangle's updates take one
+//     entry per lane and pass, as does the scaling L = M D^{1/2};
+//   * its inverse by the diagonal task's substitution (the same operations
+//     per entry), each step's entries one per lane and pass;
+//   * the panel solve by that inverse, l_rc = sum_{k <= c} a_rk X_ck, one
+//     output per lane and pass (the panel-solve tiles of the task loop solve
+//     by substitution instead: they run before the inverse exists);
 //   * the update tiles, one output per lane at a time (a dot product over the
 //     panel's columns in two chains): into panels inside the subtree by plain
 //     read-modify-write (no other task touches them), into the others by
@@ -1414,6 +1419,17 @@ __device__ void fanin_gather(const FactorArgs& a, int t, int pc, int p0, int np,
 //     does.
 // After a failed pivot (here or anywhere) the rest of the subtree skips its
 // arithmetic but still counts its outside targets down.
+// Entry p of a lower triangle numbered row by row (p = a (a + 1) / 2 + b,
+// 0 <= b <= a): row a, column b.  The float square root is exact at the
+// triangular numbers; the two corrections absorb its rounding elsewhere.
+__device__ __forceinline__ void tri_decode(int p, int& ra, int& cb) {
+  int t = (int)((sqrtf(8.0f * (float)p + 1.0f) - 1.0f) * 0.5f);
+  if ((t + 1) * (t + 2) / 2 <= p) ++t;
+  if (t * (t + 1) / 2 > p) --t;
+  ra = t;
+  cb = p - t * (t + 1) / 2;
+}
+
 constexpr int kWarpLd = kWarpSubW + 1;
 constexpr int kWarpExec = 4;                                   // warps of a CTA that run them
 constexpr int kWarpSmem = kWarpSubW * kWarpLd + kWarpSubW;     // doubles per warp: the block, 1 / l_jj
@@ -1452,9 +1468,16 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
         const double qv = __shfl_sync(full, qj, j);
         const bool mine = lane > j && lane < w;
         const double ci = mine ? ws[lane + j * kWarpLd] * qv : 0.0;  // the multiplier of row lane
-        for (int kk = j + 1; kk < w; ++kk) {
-          const double akj = ws[kk + j * kWarpLd];
-          if (lane >= kk && lane < w) ws[lane + kk * kWarpLd] = fma(-ci, akj, ws[lane + kk * kWarpLd]);
+        // the trailing triangle a_ik -= c_i a_kj (j < k <= i < w), one entry
+        // per lane and pass; column j is read here and rewritten only below
+        const int m = w - j - 1, ntri = m * (m + 1) / 2;
+        for (int p0 = 0; p0 < ntri; p0 += 32) {
+          const int p = p0 + lane;
+          int ta, tb;
+          tri_decode(p < ntri ? p : 0, ta, tb);
+          const int i = j + 1 + ta, kk = j + 1 + tb;
+          const double c = __shfl_sync(full, ci, i);
+          if (p < ntri) ws[i + kk * kWarpLd] = fma(-c, ws[kk + j * kWarpLd], ws[i + kk * kWarpLd]);
         }
         __syncwarp();
         if (lane == j + 1 && lane < w) {
@@ -1472,31 +1495,36 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
         __syncwarp();
       }
       if (!skip) {
-        // L = M D^{1/2}: l_jj = sqrt(d_j), r_j = 1 / l_jj, l_ij = m_ij l_jj
+        // L = M D^{1/2}: l_jj = sqrt(d_j), r_j = 1 / l_jj, l_ij = m_ij l_jj (one
+        // entry of the strictly lower triangle per lane and pass)
         if (lane < w) {
           const double l = sqrt(ws[lane * (kWarpLd + 1)]);
           ws[lane * (kWarpLd + 1)] = l;
           xd[lane] = 1.0 / l;
         }
         __syncwarp();
-        for (int j = 0; j < w; ++j) {
-          const double l = ws[j * (kWarpLd + 1)];
-          if (lane > j && lane < w) ws[lane + j * kWarpLd] *= l;
+        for (int p = lane; p < w * (w - 1) / 2; p += 32) {
+          int ta, tb;
+          tri_decode(p, ta, tb);
+          ws[ta + 1 + tb * kWarpLd] *= ws[tb * (kWarpLd + 1)];
         }
         __syncwarp();
         for (int idx = lane; idx < w * w; idx += 32) {
           const int i = idx % w, j = idx / w;
           if (i >= j) P[i + (size_t)j * ld] = (T)ws[i + j * kWarpLd];
         }
-        // L11^{-1}: X[i][c] (i > c) in the upper triangle at (c, i)
+        // L11^{-1}: X_ic (i > c) in the upper triangle at (c, i); step kk adds
+        // -l_ik X_kc to every X_ic with c <= kk < i (one per lane and pass) and
+        // completes X_{kk+1,c} by 1 / l_{kk+1,kk+1}
         for (int kk = 0; kk < w - 1; ++kk) {
-          const double xkc = lane == kk ? xd[kk] : (lane < kk ? ws[lane + kk * kWarpLd] : 0.0);
-          if (lane <= kk)
-            for (int i = kk + 1; i < w; ++i) {
-              double v = fma(-ws[i + kk * kWarpLd], xkc, ws[lane + i * kWarpLd]);
-              if (i == kk + 1) v *= xd[i];
-              ws[lane + i * kWarpLd] = v;
-            }
+          const int nc = kk + 1, n = nc * (w - kk - 1);
+          for (int p = lane; p < n; p += 32) {
+            const int c = p % nc, i = kk + 1 + p / nc;
+            const double xkc = c == kk ? xd[kk] : ws[c + kk * kWarpLd];
+            double v = fma(-ws[i + kk * kWarpLd], xkc, ws[c + i * kWarpLd]);
+            if (i == kk + 1) v *= xd[i];
+            ws[c + i * kWarpLd] = v;
+          }
           __syncwarp();
         }
         double* X = a.inv + a.invoff[s];
@@ -1504,42 +1532,24 @@ __device__ void warp_subtree(const FactorArgs& a, int k, double* ws) {
           const int i = idx % w, j = idx / w;
           if (i >= j) X[idx] = i == j ? xd[j] : ws[j + i * kWarpLd];
         }
-        // L21 = A21 L11^{-T}, row by row in 4-row strips, in the panels'
-        // precision against the stored L11 (as the panel-solve tile)
+        // L21 = A21 L11^{-T} by the inverse, in the panels' precision:
+        // l_rc = sum_{k <= c} a_rk X_ck, one output per lane and pass, columns
+        // in decreasing order, so that a_rc is overwritten only after every
+        // output that reads it (its row's higher columns: an earlier pass, or
+        // this one, whose reads all precede its writes)
         using ct = T;
-        const int lr = lane >> 3, lc = lane & 7;
-        for (int rs = w; rs < r; rs += 4) {
-          const int row = rs + lr;
-          const bool rv = row < r;
-          T* Pi = P + row;
-          ct x[4];
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const int c = lc + 8 * cc;
-            x[cc] = (rv && c < w) ? (ct)ldcg(Pi + (size_t)c * ld) : ct(0);
-          }
-#pragma unroll
-          for (int cbk = 0; cbk < 4; ++cbk) {
-            if (8 * cbk >= w) break;
-            for (int c8 = 0; c8 < 8; ++c8) {
-              const int c = 8 * cbk + c8;
-              if (c >= w) break;
-              if (lc == c8) x[cbk] *= sizeof(T) == 8 ? (ct)xd[c] : ct(1) / (ct)ws[c * (kWarpLd + 1)];
-              const ct xc = __shfl_sync(full, x[cbk], (lr << 3) | c8);
-              const double* Lc = ws + c * kWarpLd;  // l_qc at Lc[q], q > c
-              if (lc > c8) x[cbk] -= xc * (ct)Lc[lc + 8 * cbk];
-#pragma unroll
-              for (int cc = cbk + 1; cc < 4; ++cc) {
-                if (8 * cc >= w) break;
-                x[cc] -= xc * (ct)Lc[lc + 8 * cc];
-              }
-            }
-          }
-#pragma unroll
-          for (int cc = 0; cc < 4; ++cc) {
-            const int c = lc + 8 * cc;
-            if (rv && c < w) Pi[(size_t)c * ld] = (T)x[cc];
-          }
+        const int rb = r - w, nout = rb * w;
+        for (int o0 = 0; o0 < nout; o0 += 32) {
+          const int o = o0 + lane;
+          const bool ov = o < nout;
+          const int c = ov ? w - 1 - o / rb : 0, rr = ov ? o % rb : 0;
+          T* Pr = P + w + rr;
+          ct acc = ct(0);
+          if (ov)
+            for (int k = 0; k <= c; ++k)
+              acc = fma((ct)ldcg(Pr + (size_t)k * ld), k == c ? (ct)xd[c] : (ct)ws[k + c * kWarpLd], acc);
+          __syncwarp();
+          if (ov) Pr[(size_t)c * ld] = (T)acc;
         }
         __syncwarp();  // the rows below are written before the update tiles read them
       }
