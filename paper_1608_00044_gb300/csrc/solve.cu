@@ -1192,20 +1192,21 @@ __device__ void subtree_forward(const SolveArgs& a, int k, double* ys, double* z
       }
       __syncwarp();  // the next pass reuses ys and zs; the next panel reads these rows
     }
-    // count the tiles down on the panels outside the subtree that they reach
+    // count the tiles down on the panels outside the subtree that they reach,
+    // one (tile, target) entry per lane: the warp barrier orders every lane's
+    // writes before each lane's acq_rel decrement (and lane 0's fence)
     if (__any_sync(0xffffffffu, outside)) {
-      if (lane == 0) {
-        __threadfence();
-        for (int kt = a.st_first[s]; kt < a.st_first[s] + a.nst[s]; ++kt)
-          for (int e = a.st_tptr[kt]; e < a.st_tptr[kt + 1]; ++e) {
-            const int t = a.st_tgt[e];
-            if (t > hi && atom_add_acqrel(&a.fdep[t], -1) == 1) {
-              if (is_wpanel(a, t))
-                release_w_forward(q, a, t, nullptr);
-              else
-                ring2_push_one(q, true, t);
-            }
-          }
+      if (lane == 0) __threadfence();
+      __syncwarp();
+      const int e0 = a.st_tptr[a.st_first[s]], e1 = a.st_tptr[a.st_first[s] + a.nst[s]];
+      for (int e = e0 + lane; e < e1; e += 32) {
+        const int t = a.st_tgt[e];
+        if (t > hi && atom_add_acqrel(&a.fdep[t], -1) == 1) {
+          if (is_wpanel(a, t))
+            release_w_forward(q, a, t, nullptr);
+          else
+            ring2_push_one(q, true, t);
+        }
       }
       __syncwarp();
     }
