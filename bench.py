@@ -44,22 +44,39 @@ def _peaks():
 
 
 KERNEL_SOURCES = ["factor.cu", "device_common.cuh", "sched.cuh", "kernels.hpp", "plan.hpp"]
+# The warp-level subtree tasks are a kernel of their own (warp_subtree_kernel,
+# which single large matrices do not launch); their section of factor.cu is
+# left out of factor_kernel's sources.
+WARP_SECTION = ("// ---------------------------------------------------------------- warp-level subtree tasks",
+                "// MODE: 0 = CUDA-core update tiles")
+
+
+def kernel_sources_sha1() -> str:
+    """Digest of factor_kernel's sources (KERNEL_SOURCES, factor.cu without the
+    warp-level subtree section)."""
+    import hashlib
+
+    h = hashlib.sha1()
+    for f in KERNEL_SOURCES:
+        with open(os.path.join(ROOT, "paper_1608_00044_gb300", "csrc", f), "rb") as fh:
+            data = fh.read()
+        if f == "factor.cu":
+            text = data.decode()
+            i = text.index(WARP_SECTION[0])
+            j = text.index(WARP_SECTION[1], i)
+            data = (text[:i] + text[j:]).encode()
+        h.update(data)
+    return h.hexdigest()
 
 
 def _measured_traffic(kernel: str):
     """DRAM bytes per launch of `kernel` from the committed ncu capture, or None
-    when the kernel sources changed since that capture."""
-    import hashlib
-
+    when the kernel's sources changed since that capture."""
     try:
         rec = json.load(open(os.path.join(ROOT, "profiles", "traffic.json")))[kernel]
+        return rec["bytes_per_launch"] if kernel_sources_sha1() == rec["kernel_sources_sha1"] else None
     except Exception:
         return None
-    h = hashlib.sha1()
-    for f in KERNEL_SOURCES:
-        with open(os.path.join(ROOT, "paper_1608_00044_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
-    return rec["bytes_per_launch"] if h.hexdigest() == rec["kernel_sources_sha1"] else None
 
 
 def _dist():
